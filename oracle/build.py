@@ -1,0 +1,26 @@
+"""Compile the C oracle (ckks_oracle.c) into oracle/liboracle.so with gcc.
+
+Building the checker is not using it: ``__graft_entry__.build()`` calls this so
+that the oracle exists on a fresh machine, nothing in the product loads it.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "ckks_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+
+def build_oracle(force: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_oracle(force=True))

@@ -1,0 +1,151 @@
+"""Alg. 2 (HE CutMax) and Alg. 3 (one-shot nucleus sampling) on oracle CKKS ops.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Scale rule.  Every ciphertext carries its exact scale.  A multiplication by a
+real constant c at level l (prime q = q_l) towards a target scale `target`
+encodes E = (target*q)/scale, multiplies by K = rint(c*E), sets the scale to
+scale*E and rescales (scale/q).  Adding a constant c adds rint(c*scale) to
+the constant coefficient.  Ciphertext products multiply scales, rescale
+divides by q_l.  These float64 steps are written in exactly this order on both
+implementations.
+
+Circuit (iteration t; Y at level l):
+  S  = rotsum(Y)                       sum_i Y_i in every slot (App. D)
+  D  = n*Y - S                         n*(Y - mu), no level
+  E  = rescale(D*D)
+  V  = rotsum(E) [- m*rescale(S*S)]    n^3 sigma^2 (m zero-padded slots)
+  h  = Goldschmidt 1/(2 sqrt(kappa V)) in k iterations, 2 levels each
+  D' = D * 2 sqrt(kappa n)/c           (times the 0/1 slot mask when padded)
+  u  = D' * h + 1 (+ mask when padded) = (Y - mu)/(c sigma) + 1     (Alg. 2)
+  Y  = u^p                             square and multiply
+Final (Alg. 2 last step): S = rotsum(Y); a = 1 - kappa_f S;
+  F = prod_{i<=d} (1 + a^(2^i)); Z = (kappa_f Y) * F.
+"""
+import math
+
+import numpy as np
+
+from . import encoding as enc
+
+
+class HE:
+    """Helpers implementing the scale rule over an oracle Context."""
+
+    def __init__(self, ctx, delta):
+        self.ctx = ctx
+        self.delta = float(delta)
+
+    def q(self, level):
+        return self.ctx.primes[level]
+
+    def mcr(self, ct, c, target=None):
+        target = self.delta if target is None else target
+        q = float(self.q(ct.level))
+        E = (target * q) / ct.scale
+        K = float(np.rint(c * E))
+        t = self.ctx.mul_intd(ct, K, ct.scale * E)
+        return self.ctx.rescale(t)
+
+    def add_const(self, ct, c):
+        return self.ctx.add_intd(ct, float(np.rint(c * ct.scale)))
+
+    def neg(self, ct):
+        return self.ctx.mul_int(ct, -1)
+
+    def mul_rescale(self, a, b):
+        ctx = self.ctx
+        l = min(a.level, b.level)
+        if a.level > l:
+            a = ctx.drop(a, l)
+        if b.level > l:
+            b = ctx.drop(b, l)
+        return ctx.rescale(ctx.mul(a, b))
+
+    def mul_plain_rescale(self, ct, vec, target=None):
+        target = self.delta if target is None else target
+        q = float(self.q(ct.level))
+        E = (target * q) / ct.scale
+        pt = enc.encode(vec, self.ctx.log_n, E)
+        t = self.ctx.mul_plain(ct, pt, ct.scale * E)
+        return self.ctx.rescale(t)
+
+    def add_plain_vec(self, ct, vec):
+        pt = enc.encode(vec, self.ctx.log_n, ct.scale)
+        return self.ctx.add_plain(ct, pt)
+
+    def rotsum(self, ct, steps):
+        for i in range(steps):
+            ct = self.ctx.add(ct, self.ctx.rotate(ct, 1 << i))
+        return ct
+
+    def power(self, u, p):
+        sq, acc, pp = u, None, int(p)
+        while True:
+            if pp & 1:
+                acc = sq if acc is None else self.mul_rescale(acc, sq)
+            pp >>= 1
+            if pp == 0:
+                break
+            sq = self.mul_rescale(sq, sq)
+        return acc
+
+
+def required_rotations(plan):
+    return [1 << i for i in range(plan.rotsum_steps)]
+
+
+def invsqrt_goldschmidt(he, V, kappa, y0, k):
+    """h ~ 1/(2 sqrt(kappa V)), coupled Goldschmidt, 2k levels."""
+    a = he.add_const(he.mcr(V, -kappa * y0 * y0 / 2.0), 1.5)
+    h = he.mcr(a, y0 / 2.0)
+    g = he.mul_rescale(he.mcr(V, kappa * y0), a) if k >= 2 else None
+    for i in range(2, k + 1):
+        a = he.add_const(he.neg(he.mul_rescale(g, h)), 1.5)
+        if i < k:
+            g = he.mul_rescale(g, a)
+        h = he.mul_rescale(h, a)
+    return h
+
+
+def inverse_goldschmidt(he, S, kappa_f, d):
+    """F ~ 1/(kappa_f S) by prod_{i<=d}(1 + (1 - kappa_f S)^(2^i)); d + 2 levels."""
+    a = he.add_const(he.mcr(S, -kappa_f), 1.0)
+    F = he.add_const(a, 1.0)
+    sq = a
+    for _ in range(d):
+        sq = he.mul_rescale(sq, sq)
+        F = he.mul_rescale(F, he.add_const(sq, 1.0))
+    return F
+
+
+def cutmax_he(he, ct, plan, bootstrap=None):
+    """Alg. 2 over one ciphertext packed by ``plan.packing``."""
+    ctx = he.ctx
+    n, steps, m = plan.n, plan.rotsum_steps, plan.pad
+    mask = None
+    if m:
+        mask = np.zeros(plan.slots)
+        mask[:n] = 1.0
+    Y = ct
+    for t in range(plan.T):
+        S = he.rotsum(Y, steps)
+        D = ctx.sub(ctx.mul_int(Y, n), S)
+        E = he.mul_rescale(D, D)
+        V = he.rotsum(E, steps)
+        if m:
+            V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
+        h = invsqrt_goldschmidt(he, V, plan.kappa[t], plan.y0[t], plan.k[t])
+        coef = 2.0 * math.sqrt(plan.kappa[t] * n) / plan.c[t]
+        Dp = he.mul_plain_rescale(D, coef * mask) if m else he.mcr(D, coef)
+        u = he.mul_rescale(Dp, h)
+        u = he.add_plain_vec(u, mask) if m else he.add_const(u, 1.0)
+        Y = he.power(u, plan.p[t])
+    S = he.rotsum(Y, steps)
+    F = inverse_goldschmidt(he, S, plan.kappa_f, plan.d)
+    return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
+
+
+def nucleus_he(he, ct_logits, ct_noise, plan):
+    """Alg. 3: X~ = X + G (G = U^(1/alpha) supplied encrypted), then CutMax."""
+    return cutmax_he(he, he.ctx.add(ct_logits, ct_noise), plan)

@@ -1,0 +1,173 @@
+"""CutMax circuit plan: the constants that make Alg. 2 polynomial and in range.
+
+Sect. 3.2 of the paper requires two obligations of any encrypted CutMax:
+(i) no intermediate exceeds the scheme bound and (ii) the inputs of the
+inverse-square-root and inverse approximations stay inside their convergence
+ranges, which is achieved by range scaling x -> x/b with a known bound b.
+This module picks those constants from FP64 statistics of the input
+distribution (client side, never on encrypted data):
+
+  kappa[t]  range scale of the iteration-t variance sum V_t = sum (n*y - S)^2
+            (= n^3 sigma_t^2); the Goldschmidt input is kappa[t] * V_t
+  y0[t]     Goldschmidt initial guess for 1/sqrt(kappa[t] V_t)
+  k[t]      Goldschmidt inverse-square-root iterations (2 levels each)
+  kappa_f   range scale of the final sum S_T for the Goldschmidt inverse
+  d         degree of the Goldschmidt inverse (product of d+1 factors)
+
+S_c is scale invariant (Def. of c-semi-standardisation, App. E.1) and so is
+the final normalisation, so only the spread of V_t and S_T across inputs
+matters, not their absolute size.
+"""
+import math
+from dataclasses import dataclass, field, asdict
+from typing import List
+
+import numpy as np
+
+
+@dataclass
+class CutMaxPlan:
+    n: int                      # real entries (vocabulary size) per ciphertext
+    slots: int                  # N/2
+    packing: str                # "replicate" (n | slots, n power of two) or "pad"
+    T: int
+    p: List[int]
+    c: List[float]
+    k: List[int]
+    kappa: List[float]
+    y0: List[float]
+    d: int
+    kappa_f: float
+    bootstrap: bool = False
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def rotsum_steps(self) -> int:
+        m = self.n if self.packing == "replicate" else self.slots
+        return int(round(math.log2(m)))
+
+    @property
+    def pad(self) -> int:
+        return 0 if self.packing == "replicate" else self.slots - self.n
+
+    def depth(self) -> int:
+        """Levels consumed without bootstrapping (see the circuit description)."""
+        dep = 0
+        for t in range(self.T):
+            dep += 2 + 2 * self.k[t] + power_depth(self.p[t])
+        return dep + self.d + 3
+
+    def to_dict(self):
+        return asdict(self)
+
+
+def power_depth(p: int) -> int:
+    """Depth of y^p by square-and-multiply: ceil(log2 p)."""
+    p = int(p)
+    if p <= 1:
+        return 0
+    return (p - 1).bit_length()
+
+
+def packing_for(n: int, slots: int) -> str:
+    if n > slots:
+        raise ValueError("n > slots needs several ciphertexts")
+    if slots % n == 0 and (n & (n - 1)) == 0:
+        return "replicate"
+    return "pad"
+
+
+def pack(x, slots: int, packing: str) -> np.ndarray:
+    """Slot vector for one ciphertext."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros(slots)
+    if packing == "replicate":
+        out[:] = np.tile(x, slots // len(x))
+    else:
+        out[: len(x)] = x
+    return out
+
+
+def _exact_stats(x, T, p, c):
+    """V_t = sum (n y - S)^2 for t < T and S_T = sum y_T under Alg. 1."""
+    y = np.asarray(x, dtype=np.float64).copy()
+    n = len(y)
+    Vs = []
+    for t in range(T):
+        S = y.sum()
+        D = n * y - S
+        V = float((D * D).sum())
+        Vs.append(V)
+        mu = S / n
+        sig = math.sqrt(V / n ** 3)
+        y = ((y - mu) / (c[t] * sig) + 1.0) ** p[t]
+    return Vs, float(y.sum())
+
+
+def _invsqrt_err(x, k, y0):
+    a = 1.5 - (y0 * y0 / 2.0) * x
+    h = (y0 / 2.0) * a
+    g = (x * y0) * a
+    for i in range(2, k + 1):
+        a = 1.5 - g * h
+        if i < k:
+            g = g * a
+        h = h * a
+    return np.abs(2.0 * h * np.sqrt(x) - 1.0).max()
+
+
+def _inv_err(x, d):
+    a = 1.0 - x
+    f = 1.0 + a
+    sq = a
+    for _ in range(d):
+        sq = sq * sq
+        f = f * (1.0 + sq)
+    return np.abs(x * f - 1.0).max()
+
+
+def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1e-7,
+              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False):
+    """Pick kappa/y0/k and kappa_f/d from `n_cal` draws of ``sample(i)``."""
+    p = [int(v) for v in (p if not np.isscalar(p) else [p] * T)]
+    c = [float(v) for v in (c if not np.isscalar(c) else [c] * T)]
+    Vs, Ss = [], []
+    for i in range(n_cal):
+        v, s = _exact_stats(sample(i), T, p, c)
+        Vs.append(v)
+        Ss.append(s)
+    Vs = np.asarray(Vs)
+    Ss = np.asarray(Ss)
+    kappa, y0s, ks = [], [], []
+    for t in range(T):
+        a, b = Vs[:, t].min() / margin, Vs[:, t].max() * margin
+        kap = 1.0 / math.sqrt(a * b)
+        xs = np.geomspace(a * kap, b * kap, 2001)
+        y0 = 1.0 if xs[-1] < 2.5 else math.sqrt(2.5 / xs[-1])
+        if k_fixed is not None:
+            k = int(k_fixed if np.isscalar(k_fixed) else k_fixed[t])
+        else:
+            k = k_max
+            for kk in range(1, k_max + 1):
+                if _invsqrt_err(xs, kk, y0) < tol_k:
+                    k = kk
+                    break
+        kappa.append(kap)
+        y0s.append(y0)
+        ks.append(k)
+    af, bf = Ss.min() / margin, Ss.max() * margin
+    kf = 2.0 / (af + bf)
+    xs = np.linspace(af * kf, bf * kf, 2001)
+    if d_fixed is not None:
+        d = int(d_fixed)
+    else:
+        d = d_max
+        for dd in range(1, d_max + 1):
+            if _inv_err(xs, dd) < tol_d:
+                d = dd
+                break
+    return CutMaxPlan(n=n, slots=slots, packing=packing_for(n, slots), T=T, p=p, c=c, k=ks,
+                      kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap,
+                      extra={"V_range": [[float(Vs[:, t].min()), float(Vs[:, t].max())] for t in range(T)],
+                             "S_range": [float(Ss.min()), float(Ss.max())], "margin": margin,
+                             "n_cal": n_cal})

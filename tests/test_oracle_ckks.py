@@ -1,0 +1,298 @@
+"""Pins of the CKKS oracle against things other than itself.
+
+Each test checks the oracle against a textbook definition computed another
+way (Python big integers, sympy, schoolbook products, brute-force sums) or
+against an identity the mathematics fixes, chosen so that a dropped term, a
+wrong sign, a wrong index or a transposed operand fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import sympy
+
+from oracle import ckks
+from oracle import encoding as enc
+
+
+# ------------------------------------------------------------- primes / psi
+@pytest.mark.parametrize("log_n,bits", [(4, [30, 30, 31]), (11, [60, 40, 40, 60]), (14, [60] + [40] * 5 + [60, 60])])
+def test_prime_chain_rule(log_n, bits):
+    ps = [int(p) for p in ckks.gen_primes(log_n, bits)]
+    two_n = 2 << log_n
+    assert len(set(ps)) == len(ps)
+    for b in sorted(set(bits)):
+        chosen = [p for p, bb in zip(ps, bits) if bb == b]
+        # every candidate k*2N+1 in (min chosen, 2^b) that is prime must be chosen
+        k_hi = ((1 << b) - 1) // two_n
+        k_lo = (min(chosen) - 1) // two_n
+        expect = [k * two_n + 1 for k in range(k_hi, k_lo - 1, -1) if sympy.isprime(k * two_n + 1)]
+        assert chosen == expect
+        for p in chosen:
+            assert p % two_n == 1 and p.bit_length() == b
+
+
+@pytest.mark.parametrize("log_n", [3, 10, 16])
+def test_psi_is_canonical_primitive_root(log_n):
+    q = int(ckks.gen_primes(log_n, [50])[0])
+    psi = int(ckks.lib().or_find_psi(q, log_n))
+    n = 1 << log_n
+    assert pow(psi, n, q) == q - 1 and pow(psi, 2 * n, q) == 1
+    # first x = 2,3,... whose (q-1)/2N power has order 2N
+    for x in range(2, 200):
+        c = pow(x, (q - 1) // (2 * n), q)
+        if pow(c, n, q) == q - 1:
+            assert c == psi
+            break
+
+
+# ------------------------------------------------------------- NTT
+@pytest.mark.parametrize("log_n", [3, 4, 6])
+def test_ntt_matches_evaluation_definition_bigint(log_n):
+    n = 1 << log_n
+    q = int(ckks.gen_primes(log_n, [40])[0])
+    psi = int(ckks.lib().or_find_psi(q, log_n))
+    rng = np.random.default_rng(log_n)
+    a = rng.integers(0, q, n, dtype=np.uint64)
+    A = ckks.ntt(a, log_n, q)
+    for i in range(n):
+        e = 2 * int(format(i, f"0{log_n}b")[::-1], 2) + 1
+        x = pow(psi, e, q)
+        assert int(A[i]) == sum(int(a[k]) * pow(x, k, q) for k in range(n)) % q
+    assert (ckks.ntt_def(a, log_n, q, psi) == A).all()
+
+
+@pytest.mark.parametrize("log_n", [3, 4, 6])
+def test_ntt_product_is_negacyclic_convolution(log_n):
+    n = 1 << log_n
+    q = int(ckks.gen_primes(log_n, [59])[0])
+    rng = np.random.default_rng(7 + log_n)
+    a = rng.integers(0, q, n, dtype=np.uint64)
+    b = rng.integers(0, q, n, dtype=np.uint64)
+    A, B = ckks.ntt(a, log_n, q), ckks.ntt(b, log_n, q)
+    prod = ckks.intt(np.array([(int(x) * int(y)) % q for x, y in zip(A, B)], dtype=np.uint64), log_n, q)
+    # Python big-int negacyclic convolution
+    ref = [0] * n
+    for i in range(n):
+        for j in range(n):
+            k = i + j
+            if k < n:
+                ref[k] += int(a[i]) * int(b[j])
+            else:
+                ref[k - n] -= int(a[i]) * int(b[j])
+    assert [int(v) for v in prod] == [v % q for v in ref]
+    assert (ckks.schoolbook(a, b, log_n, q) == prod).all()
+
+
+@pytest.mark.parametrize("log_n", [10, 14, 16])
+def test_ntt_inverse_roundtrip(log_n):
+    q = int(ckks.gen_primes(log_n, [61])[0])
+    rng = np.random.default_rng(log_n)
+    a = rng.integers(0, q, 1 << log_n, dtype=np.uint64)
+    assert (ckks.intt(ckks.ntt(a, log_n, q), log_n, q) == a).all()
+
+
+# ------------------------------------------------------------- randomness
+def test_philox_bijective_and_uniform():
+    key = [0x1234, 0xABCD]
+    outs = np.array([ckks.philox([i, 0, 0, 0], key) for i in range(4096)])
+    assert len({tuple(o) for o in outs}) == 4096
+    bits = np.unpackbits(outs.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.01
+    # changing one counter word or key word changes ~half the output bits
+    a = ckks.philox([5, 6, 7, 8], key)
+    for ctr, k in [([5, 6, 7, 9], key), ([5, 6, 7, 8], [0x1235, 0xABCD])]:
+        b = ckks.philox(ctr, k)
+        flips = np.unpackbits((a ^ b).view(np.uint8)).sum()
+        assert 30 < flips < 98
+
+
+def test_secret_distributions():
+    s = ckks.sample_secret(11, 14, 0)
+    counts = np.bincount(s.astype(np.int64) + 1, minlength=3) / len(s)
+    assert np.allclose(counts, 1 / 3, atol=0.02)
+    sp = ckks.sample_secret(11, 14, 192)
+    assert (np.abs(sp) == 1).sum() == 192 and set(np.unique(sp)) <= {-1, 0, 1}
+
+
+def test_gaussian_moments():
+    e = ckks.sample_gauss(5, 3, 2, 3.2, 16)
+    assert abs(e.mean()) < 0.06
+    assert abs(e.std() - 3.2) < 0.05
+    assert np.abs(e).max() <= 19
+
+
+# ------------------------------------------------------------- encoding
+@pytest.mark.parametrize("log_n", [4, 8, 10])
+def test_encode_decode_match_defining_sums(log_n):
+    rng = np.random.default_rng(log_n)
+    h = (1 << log_n) // 2
+    z = rng.normal(size=h) + 1j * rng.normal(size=h)
+    m_fft = enc.encode_real_values(z, log_n, 2.0 ** 30)
+    m_bf = enc.encode_bruteforce(z, log_n, 2.0 ** 30)
+    assert np.abs(m_fft - m_bf).max() < 1e-3
+    m = np.rint(m_fft)
+    assert np.abs(enc.decode(m, log_n, 2.0 ** 30) - enc.decode_bruteforce(m, log_n, 2.0 ** 30)).max() < 1e-9
+    # decoding the real-coefficient polynomial returns the slots
+    assert np.abs(enc.decode(m, log_n, 2.0 ** 30) - z).max() < 1e-6
+
+
+def test_slot_rotation_is_automorphism():
+    """m(X) -> m(X^(5^r)) rotates the slots left by r (plaintext identity)."""
+    log_n, n = 8, 256
+    rng = np.random.default_rng(3)
+    z = rng.normal(size=n // 2)
+    m = enc.encode(z, log_n, 2.0 ** 30)
+    for r in [1, 5, 64]:
+        g = ckks.rot_galois(log_n, r)
+        assert g == pow(5, r, 2 * n)
+        out = np.zeros(n)
+        for k in range(n):
+            e = (k * g) % (2 * n)
+            if e < n:
+                out[e] = m[k]
+            else:
+                out[e - n] = -m[k]
+        assert np.abs(enc.decode(out, log_n, 2.0 ** 30).real - np.roll(z, -r)).max() < 1e-6
+
+
+# ------------------------------------------------------------- encryption / ops
+@pytest.fixture(scope="module")
+def small_ctx():
+    ctx = ckks.Context(10, [60, 40, 40, 40], [60, 60], dnum=2, seed=21)
+    ctx.gen_relin_key()
+    for r in [1, 2, 3]:
+        ctx.gen_rot_key(r)
+    ctx.gen_galois_key(ctx.conj_galois())
+    return ctx
+
+
+def _enc_vec(ctx, z, ctr, scale=2.0 ** 40):
+    return ctx.encrypt(enc.encode(z, ctx.log_n, scale), scale, ctr)
+
+
+def test_decrypt_is_message_plus_small_error(small_ctx):
+    """Dec(Enc(m)) = m + e with |e| bounded by the Gaussian tail (Sect. 2.1)."""
+    ctx = small_ctx
+    rng = np.random.default_rng(1)
+    m = np.rint(rng.normal(size=ctx.n) * 2.0 ** 35)
+    ct = ctx.encrypt(m, 2.0 ** 35, 9)
+    e = ctx.decrypt(ct) - m
+    assert np.abs(e).max() <= 19 and np.abs(e).std() > 1.0
+    # c0 + c1*s with the exported secret, in big integers, limb 0
+    s = ctx.secret().astype(np.int64)
+    c = ct.export()
+    q0 = ctx.primes[0]
+    c0 = [int(v) for v in c[0, 0]]
+    c1 = [int(v) for v in c[1, 0]]
+    n = ctx.n
+    acc = list(c0)
+    for i in range(n):
+        if c1[i] == 0:
+            continue
+        for j in np.nonzero(s)[0]:
+            k = i + int(j)
+            v = c1[i] * int(s[j])
+            if k < n:
+                acc[k] += v
+            else:
+                acc[k - n] -= v
+    acc = [((v % q0) + q0 // 2) % q0 - q0 // 2 for v in acc[:64]]
+    assert np.array_equal(np.array(acc, dtype=np.float64), ctx.decrypt(ct)[:64])
+
+
+def test_homomorphic_add_mul_rotate_conj(small_ctx):
+    ctx = small_ctx
+    rng = np.random.default_rng(2)
+    h = ctx.slots
+    a = rng.normal(size=h)
+    b = rng.normal(size=h) + 1j * rng.normal(size=h)
+    ca, cb = _enc_vec(ctx, a, 1), _enc_vec(ctx, b, 2)
+    dec = lambda ct: enc.decode(ctx.decrypt(ct), ctx.log_n, ct.scale)
+    assert np.abs(dec(ctx.add(ca, cb)) - (a + b)).max() < 1e-8
+    assert np.abs(dec(ctx.sub(ca, cb)) - (a - b)).max() < 1e-8
+    prod = ctx.rescale(ctx.mul(ca, cb))
+    assert prod.level == ctx.top_level - 1
+    assert abs(prod.scale - 2.0 ** 80 / ctx.primes[ctx.top_level]) < 1e-6 * prod.scale
+    assert np.abs(dec(prod) - a * b).max() < 1e-7
+    assert np.abs(dec(ctx.rotate(cb, 3)) - np.roll(b, -3)).max() < 1e-7
+    assert np.abs(dec(ctx.conj(cb)) - np.conj(b)).max() < 1e-7
+    assert np.abs(dec(ctx.mul_int(ca, -7)) - (-7 * a)).max() < 1e-7
+    # multiplying by the monomial X^(N/2) multiplies every slot by i
+    assert np.abs(dec(ctx.mul_monomial(cb, ctx.n // 2)) - 1j * b).max() < 1e-8
+
+
+def test_keyswitch_relation(small_ctx):
+    """(o0, o1) = KS(d) satisfies o0 + o1*s = d*s^2 + small (mod q_i), every limb."""
+    ctx = small_ctx
+    l, n = ctx.top_level, ctx.n
+    rng = np.random.default_rng(4)
+    d = np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in ctx.primes[: l + 1]])
+    o0, o1 = ctx.keyswitch(d, l, 0)
+    s = ctx.secret().astype(np.int64)
+    for i in range(l + 1):
+        q = ctx.primes[i]
+        sq = ckks.ntt(np.mod(s, q).astype(np.uint64), ctx.log_n, q)
+        s2 = np.array([(int(x) * int(x)) % q for x in sq], dtype=np.uint64)
+        mul = lambda x, y: ckks.intt(np.array([(int(u) * int(v)) % q for u, v in
+                                               zip(ckks.ntt(x, ctx.log_n, q), y)], dtype=np.uint64), ctx.log_n, q)
+        lhs = (o0[i].astype(object) + mul(o1[i], sq).astype(object)) % q
+        rhs = mul(d[i], s2).astype(object)
+        diff = np.array([((int(x) - int(y)) % q + q // 2) % q - q // 2 for x, y in zip(lhs, rhs)])
+        # key-switching noise: far below q_i
+        assert np.abs(diff).max() < 2 ** 20
+
+
+def test_rescale_divides_by_last_prime(small_ctx):
+    ctx = small_ctx
+    rng = np.random.default_rng(5)
+    m = np.rint(rng.normal(size=ctx.n) * 2.0 ** 50)
+    ct = ctx.encrypt(m, 2.0 ** 50, 3)
+    r = ctx.rescale(ct)
+    ql = ctx.primes[ctx.top_level]
+    # each rounded coefficient errs by <= 1/2, so Dec errs by <= (1 + |s|_1)/2
+    bound = 0.5 * (1 + np.abs(ctx.secret()).sum()) + 20.0 / ql
+    err = np.abs(ctx.decrypt(r) - m / ql)
+    assert err.max() <= bound and r.scale == 2.0 ** 50 / ql
+
+
+def test_mod_raise_adds_multiple_of_q0():
+    """ModRaise of a level-0 ciphertext decrypts, over Q, to m + e + q0*I with
+    |I| <= (|s|_1 + 1)/2 (centred lift), checked exactly in big integers."""
+    h = 16
+    ctx = ckks.Context(10, [60, 40, 40], [60], dnum=3, h=h, seed=8)
+    rng = np.random.default_rng(6)
+    m = np.rint(rng.normal(size=ctx.n) * 2.0 ** 30)
+    ct0 = ctx.encrypt(m, 2.0 ** 30, 4, level=0)
+    up = ctx.mod_raise(ct0, 2)
+    s = ctx.secret().astype(np.int64)
+    assert np.abs(s).sum() == h
+    n, q = ctx.n, ctx.primes
+    c = up.export()
+    lo = ctx.decrypt(ct0)                     # m + e, exact (fits a double)
+    assert np.abs(lo - m).max() <= 19
+    Q = q[0] * q[1] * q[2]
+    # CRT of each lifted coefficient, then c0 + c1*s over the integers mod Q
+    def crt(limbs):
+        out = []
+        for k in range(n):
+            v = 0
+            for i in range(3):
+                Mi = Q // q[i]
+                v += int(limbs[i][k]) * Mi * pow(Mi, -1, q[i])
+            v %= Q
+            out.append(v - Q if v > Q // 2 else v)
+        return out
+    c0, c1 = crt(c[0]), crt(c[1])
+    t = list(c0)
+    for j in np.nonzero(s)[0]:
+        for k in range(n):
+            idx = k + int(j)
+            if idx < n:
+                t[idx] += c1[k] * int(s[j])
+            else:
+                t[idx - n] -= c1[k] * int(s[j])
+    t = [((v % Q) + Q // 2) % Q - Q // 2 for v in t]
+    for k in range(n):
+        I, r = divmod(t[k] - int(lo[k]), q[0])
+        assert r == 0 and abs(I) <= (h + 1) // 2 + 1
