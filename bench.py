@@ -1,0 +1,258 @@
+"""Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2]
+
+One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
+vector.  `value` times the device work with CUDA events on the library's
+stream (inputs already encrypted and resident in HBM, L2 flushed between
+steps); `e2e` times the public C-ABI path from pinned host logits to host
+results (encode + encrypt + CutMax + decrypt + decode, copies included).
+Multi-GPU: independent replicas per rank (no data-path collective).
+--impl reference times the CPU oracle on the machine's host cores.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted CutMax decodes/sec (vocab 32k, N=2^16), 1 GB300"
+
+
+def workload(name):
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    if name == "cfg1":
+        log_n, qb, pb, dnum = 14, [60] + [40] * 21, [60, 60], 11
+        n = 1024
+        pl = P.calibrate(lambda i: synth.logits_gaussian(1000 + i, n=n), 100, n, 1 << (log_n - 1), 2, 3, 5.0,
+                         k_fixed=2, d_fixed=2)
+        gen = lambda s: synth.logits_gaussian(s, n=n)
+        desc = {"workload": "CutMax T=2 p=3 c=5, 1024 logits N(0,4) replicated in N=2^14 slots, leveled "
+                            "(L=21, 40-bit scale, dnum=11)", "log_n": log_n, "n": n, "T": 2}
+        return log_n, qb, pb, dnum, pl, gen, desc
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, rank, ws
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on this machine's host cores."""
+    dist, rank, ws = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import ckks as ock
+    from oracle import encoding as oenc
+    from oracle.circuit import HE, cutmax_he, required_rotations
+    from paper_2509_08383_gb300 import plan as P
+    log_n, qb, pb, dnum, pl, gen, desc = workload(args.workload)
+    o = ock.Context(log_n, qb, pb, dnum, seed=1)
+    o.gen_relin_key()
+    for r in required_rotations(pl):
+        o.gen_rot_key(r)
+    delta = 2.0 ** 40
+    times = []
+    for step in range(args.warmup + args.steps):
+        x = gen(50000 + step)
+        t0 = time.perf_counter()
+        ct = o.encrypt(oenc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, step)
+        z = cutmax_he(HE(o, delta), ct, pl)
+        oenc.decode(o.decrypt(z), log_n, z.scale)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    T = sum(times)
+    cores = len(os.sched_getaffinity(0))
+    val = args.steps / T
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "decodes/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": desc,
+           "cpu_baseline": {"value": val, "unit": "decodes/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} full CutMax decodes (encrypt+CutMax+decrypt) on the oracle"},
+           "e2e": {"value": val, "unit": "decodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def cpu_baseline(args, desc):
+    """Bounded oracle sample: one full CutMax of the same workload on host cores."""
+    from oracle import ckks as ock
+    from oracle import encoding as oenc
+    from oracle.circuit import HE, cutmax_he, required_rotations
+    from paper_2509_08383_gb300 import plan as P
+    log_n, qb, pb, dnum, pl, gen, _ = workload(args.workload)
+    o = ock.Context(log_n, qb, pb, dnum, seed=1)
+    o.gen_relin_key()
+    for r in required_rotations(pl):
+        o.gen_rot_key(r)
+    delta = 2.0 ** 40
+    x = gen(777)
+    ct = o.encrypt(oenc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, 1)
+    t0 = time.perf_counter()
+    cutmax_he(HE(o, delta), ct, pl)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "decodes/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": "1 full CutMax decode of the bench workload on the oracle (device-resident equivalent: "
+                      "ciphertext already encrypted)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg1")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    dist, rank, ws = dist_setup(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2509_08383_gb300 import build, he
+    from paper_2509_08383_gb300 import plan as P
+    build.build_library()
+    log_n, qb, pb, dnum, pl, gen, desc = workload(args.workload)
+    g = he.Context(log_n, qb, pb, dnum, seed=1 + rank)
+    g.cutmax_prepare(pl)
+    slots = 1 << (log_n - 1)
+    stream = torch.cuda.current_stream()
+    nsteps = args.warmup + args.steps
+    cts = [g.encrypt(P.pack(gen(10000 * rank + s), slots, pl.packing), g.delta, s) for s in range(nsteps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = he.launch_count()
+    with ClockSampler(local) as clk:
+        for s in range(nsteps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            z = g.cutmax(cts[s], pl)
+            ev[s][1].record(stream)
+            if s == args.warmup - 1:
+                torch.cuda.synchronize()
+                l0 = he.launch_count()
+            del z
+        torch.cuda.synchronize()
+    launches = he.launch_count() - l0
+    ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = ws * 1000.0 / ms
+
+    # end to end through the C ABI: pinned host logits -> host outputs
+    pin = torch.empty(slots, dtype=torch.float64).pin_memory()
+    out = np.zeros(pl.n)
+    e2e_times = []
+    for s in range(nsteps):
+        pin.numpy()[:] = P.pack(gen(20000 + s), slots, pl.packing)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ct = g.encrypt(pin.numpy(), g.delta, 100000 + s)
+        z = g.cutmax(ct, pl)
+        out[:] = g.decrypt(z, pl.n)
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e = ws * args.steps / sum(e2e_times)
+    if dist:
+        t = torch.tensor([sum(e2e_times)], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = ws * args.steps / float(t.item())
+
+    res = {"metric": METRIC, "value": value, "unit": "decodes/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": dict(desc, l2="flushed between steps (256 MiB write)", parallelism=f"replicas x{ws}"),
+           "clocks": clk.summary(),
+           "e2e": {"value": e2e, "unit": "decodes/s", "h2d_bytes_per_step": slots * 8,
+                   "d2h_bytes_per_step": pl.n * 8},
+           "gpu_launches": int(launches), "roofline": None}
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            res["cpu_baseline"] = cpu_baseline(args, desc)
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * he_cutmax.h -- C ABI of the GB300 (sm_103a) homomorphic CutMax library.
+ *
+ * What it computes.  CutMax (arXiv 2509.08383, Alg. 1) is a comparison-free
+ * argmax: T iterations of mean and variance, an inverse square root, an
+ * elementwise power, then a final normalisation.  Alg. 2 ("CutMax_HE") runs
+ * it over CKKS ciphertexts with rotate-and-sum reductions (App. D) and
+ * Goldschmidt inverse / inverse-square-root polynomials (App. B.1).  Alg. 3
+ * (Sect. 3.3, "Nucleus One-Shot Sampling") adds Beta(alpha,1) cut noise to the
+ * logits and calls CutMax once.  The HE interface itself (Enc, Dec, add,
+ * mult, rotate) is the one assumed in Sect. 2.1 ("HE Preliminaries").
+ *
+ * Conventions for every call.
+ *  - Every function returns int: HE_OK (0) or one of the HE_E* codes below.
+ *    On error, he_last_error(ctx) gives a one-line message; outputs are not
+ *    written and no object is leaked.
+ *  - he_ctx and he_ct are opaque, library-owned.  The caller owns every he_ct*
+ *    it receives and frees it with he_ct_free.  Input ciphertexts are never
+ *    modified.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the current device.  All GPU work is issued on the
+ *    context's stream (he_ctx_set_stream); calls that return host data
+ *    synchronise that stream before returning.
+ *  - Ring degree N = 2^log_n, slots = N/2.  Ring elements are RNS vectors of
+ *    64-bit words, limb-major: limb i holds the residues modulo prime i.
+ *    Exported ciphertexts are in COEFFICIENT form, natural order, layout
+ *    [2][level+1][N] (c0 then c1), residues in [0, q_i).
+ *  - Integer plaintexts are passed as float64 arrays of N integer values.
+ */
+#ifndef HE_CUTMAX_H
+#define HE_CUTMAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HE_OK = 0,
+    HE_EINVAL = 1,   /* bad argument, shape or parameter */
+    HE_ENOMEM = 2,   /* device arena or host allocation exhausted */
+    HE_ELEVEL = 3,   /* not enough levels left and bootstrapping disabled */
+    HE_ERANGE = 4,   /* plan constants out of the approximations' range */
+    HE_ECUDA = 5,    /* a CUDA call failed */
+    HE_ETIMEOUT = 6, /* a bounded device wait gave up */
+    HE_ENOKEY = 7    /* a needed evaluation key has not been generated */
+};
+
+typedef struct he_ctx he_ctx;
+typedef struct he_ct he_ct;
+
+/* Scheme parameters.  Primes: q_bits[i] (i < n_q) for the ciphertext chain
+ * q_0..q_{n_q-1}, p_bits[k] for the key-switching primes.  Primes of b bits
+ * are the NTT-friendly q = k*2N+1 < 2^b in decreasing order, one cursor per
+ * bit size, assigned in request order (Q first, then P).  dnum = number of
+ * key-switching digits at the top level; alpha = ceil(n_q/dnum) primes per
+ * digit.  secret_hw = 0 selects a dense ternary secret, h > 0 a ternary
+ * secret of Hamming weight h.  sigma is the rounded-Gaussian error width.
+ * log_scale is log2 of the default encoding / target scale Delta. */
+typedef struct {
+    uint32_t log_n, n_q, n_p, dnum;
+    const int32_t *q_bits;
+    const int32_t *p_bits;
+    double log_scale;
+    double sigma;
+    uint32_t secret_hw;
+    uint64_t seed;
+    int32_t enable_bootstrap;
+} he_params;
+
+/* Create a context on the current CUDA device.  dev_arena/arena_bytes: a
+ * caller-owned device buffer the library sub-allocates for keys, tables and
+ * ciphertexts (must outlive the context); pass NULL/0 to let the library
+ * cudaMalloc its own arena of arena_bytes (0 -> a size derived from the
+ * parameters).  Generates the secret (from seed) and all static tables. */
+int he_ctx_create(const he_params *params, void *dev_arena, size_t arena_bytes, he_ctx **out);
+void he_ctx_destroy(he_ctx *ctx);
+/* stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream). */
+int he_ctx_set_stream(he_ctx *ctx, void *stream);
+/* host out[n_q + n_p]: the prime chain. */
+int he_ctx_primes(const he_ctx *ctx, uint64_t *out);
+/* bytes of the arena in use / high-water mark. */
+int he_ctx_memory(const he_ctx *ctx, size_t *in_use, size_t *peak);
+const char *he_last_error(const he_ctx *ctx);
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all contexts); used to count launches inside a timed region. */
+uint64_t he_launch_count(void);
+
+/* ---- keys (Sect. 2.1 rotations; hybrid key switching) ---------------- */
+int he_keygen_relin(he_ctx *ctx);
+/* Galois key for X -> X^g (g odd, < 2N); rotation by r uses g = 5^r mod 2N,
+ * conjugation g = 2N-1. */
+int he_keygen_galois(he_ctx *ctx, uint64_t g);
+int he_keygen_rotations(he_ctx *ctx, const int32_t *steps, size_t n_steps);
+/* host out[N]: the secret's coefficients in {-1,0,1}. */
+int he_export_secret(const he_ctx *ctx, int8_t *out);
+/* host out[(n_q+n_p)*N]: digit `digit` of key g (g = 0: relinearisation),
+ * which = 0 -> b part, 1 -> a part, coefficient form. */
+int he_export_key(he_ctx *ctx, uint64_t g, uint32_t digit, int32_t which, uint64_t *out);
+
+/* ---- encode / encrypt / decrypt (Sect. 2.1) ---------------------------- */
+/* Canonical-embedding encoding on the GPU (float64 FFT): host re/im[n_slots]
+ * (im may be NULL; missing slots are zero) -> host out[N] integer values
+ * round(scale * coefficient). */
+int he_encode(he_ctx *ctx, const double *re, const double *im, size_t n_slots, double scale, double *out);
+/* Secret-key encryption c1 = a, c0 = -a*s + e + m at `level` (-1 = top).
+ * ctr: 32-bit counter naming this encryption's randomness. */
+int he_encrypt(he_ctx *ctx, const double *re, const double *im, size_t n_slots, double scale,
+               uint32_t ctr, int32_t level, he_ct **out);
+/* Same with an integer plaintext polynomial host m[N]. */
+int he_encrypt_poly(he_ctx *ctx, const double *m, double scale, uint32_t ctr, int32_t level, he_ct **out);
+/* Decrypt and decode: host re/im[n_slots] (im may be NULL). */
+int he_decrypt(he_ctx *ctx, const he_ct *ct, double *re, double *im, size_t n_slots);
+/* Decrypt to the centred integer plaintext (modulo q0*q1, or q0 at level 0):
+ * host out[N]. */
+int he_decrypt_poly(he_ctx *ctx, const he_ct *ct, double *out);
+
+/* ---- ciphertext objects ------------------------------------------------ */
+/* host out[cap >= 2*(level+1)*N], coefficient form. */
+int he_ct_export(he_ctx *ctx, const he_ct *ct, uint64_t *out, size_t cap);
+int he_ct_import(he_ctx *ctx, const uint64_t *in, uint32_t level, double scale, he_ct **out);
+int he_ct_info(const he_ct *ct, uint32_t *level, double *scale);
+/* device pointer of c0 limb 0 (NTT form) and the element stride between
+ * c0 and c1, for zero-copy inspection. */
+int he_ct_device(const he_ct *ct, uint64_t **dev, size_t *poly_stride);
+void he_ct_free(he_ct *ct);
+
+/* ---- homomorphic operations ------------------------------------------ */
+int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+int he_sub(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+/* multiply by an integer (scale unchanged) */
+int he_mul_int(he_ctx *ctx, const he_ct *a, int64_t k, he_ct **out);
+/* multiply by a real constant c towards scale `target` and rescale:
+ * E = target*q_l/scale, K = rint(c*E), scale -> (scale*E)/q_l. */
+int he_mul_const(he_ctx *ctx, const he_ct *a, double c, double target, he_ct **out);
+/* add a real constant to every slot: + rint(c*scale) */
+int he_add_const(he_ctx *ctx, const he_ct *a, double c, he_ct **out);
+/* tensor product and relinearisation, no rescale */
+int he_mul(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out);
+int he_drop(he_ctx *ctx, const he_ct *a, uint32_t level, he_ct **out);
+/* left slot rotation by r (g = 5^r mod 2N); conjugation; general X -> X^g */
+int he_rotate(he_ctx *ctx, const he_ct *a, int32_t r, he_ct **out);
+int he_conjugate(he_ctx *ctx, const he_ct *a, he_ct **out);
+int he_automorphism(he_ctx *ctx, const he_ct *a, uint64_t g, he_ct **out);
+/* rotate-and-sum over 2^steps consecutive slots (App. D): log2 rotations */
+int he_rotsum(he_ctx *ctx, const he_ct *a, uint32_t steps, he_ct **out);
+/* Hybrid key switch of a raw polynomial: host d[(level+1)*N] coefficient
+ * form -> host out0/out1[(level+1)*N] coefficient form, with key g. */
+int he_keyswitch_raw(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out0, uint64_t *out1);
+/* Negacyclic NTT (inverse != 0: INTT) in place on DEVICE data[n_limbs][N];
+ * limb t uses prime prime_idx0 + t.  NTT form: position i holds
+ * a(psi^(2 brv(i) + 1)), psi the canonical 2N-th root of that prime. */
+int he_ntt_device(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, uint32_t prime_idx0, int32_t inverse);
+
+/* ---- CutMax (Alg. 2) and nucleus sampling (Alg. 3) ------------------- */
+/* Circuit plan: the range-scaling constants of Sect. 3.2's obligations.
+ * n real entries per ciphertext; packing 0 = replicate (n a power of two
+ * dividing N/2, slot j = x[j mod n]), 1 = zero-pad (slots n.. are zero).
+ * Per iteration t < T: power[t] (p), c[t], k[t] Goldschmidt inverse-sqrt
+ * iterations, kappa[t] range scale of V_t = sum (n y - S)^2, y0[t] initial
+ * guess.  Final normalisation: Goldschmidt inverse of degree d on
+ * kappa_f * sum(Y). */
+typedef struct {
+    uint32_t n, packing, T;
+    const uint32_t *power;
+    const double *c;
+    const uint32_t *k;
+    const double *kappa;
+    const double *y0;
+    uint32_t d;
+    double kappa_f;
+} he_cutmax_plan;
+
+/* Generate every key the plan needs (rotations 2^i, relinearisation and,
+ * with bootstrapping, its rotations and conjugation). */
+int he_cutmax_prepare(he_ctx *ctx, const he_cutmax_plan *plan);
+/* CutMax_HE (Alg. 2): out = encrypted near-one-hot of argmax(in). */
+int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out);
+/* Nucleus one-shot sampling (Alg. 3): out = CutMax(logits + rand_ct), where
+ * rand_ct encrypts the cut noise G_i = U_i^(1/alpha), alpha = ln(1-q)/ln(p)
+ * (Lemma 2 / Observation 1), drawn and encrypted by the client. */
+int nucleus_sample(he_ctx *ctx, const he_ct *logits, const he_ct *rand_ct,
+                   const he_cutmax_plan *plan, he_ct **out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HE_CUTMAX_H */

@@ -1,0 +1,364 @@
+// extern "C" entry points declared in include/he_cutmax.h.
+#include <cstring>
+#include <new>
+
+#include "context.h"
+
+using namespace he;
+
+#define API_TRY \
+    he::t_slot = cx->slot; \
+    try {
+#define API_CATCH(cx)                                                   \
+    }                                                                   \
+    catch (const Error &e) {                                            \
+        if (cx) const_cast<he_ctx *>(cx)->err = e.msg;                  \
+        return e.code;                                                  \
+    }                                                                   \
+    catch (const std::bad_alloc &) {                                    \
+        if (cx) const_cast<he_ctx *>(cx)->err = "host allocation failed"; \
+        return HE_ENOMEM;                                               \
+    }                                                                   \
+    return HE_OK;
+
+static void sync(he_ctx *cx, const char *what) {
+    check_cuda(cudaGetLastError(), what);
+    check_cuda(cudaStreamSynchronize(cx->stream), what);
+}
+static void need(bool ok, const char *msg) {
+    if (!ok) throw Error{HE_EINVAL, msg};
+}
+static void launched(he_ctx *cx, const char *what) { check_cuda(cudaGetLastError(), what); }
+
+extern "C" {
+
+int he_ctx_create(const he_params *params, void *dev_arena, size_t arena_bytes, he_ctx **out) {
+    if (!out) return HE_EINVAL;
+    he_ctx *cx = nullptr;
+    try {
+        cx = new he_ctx();
+        ctx_init(cx, params, dev_arena, arena_bytes);
+        *out = cx;
+        return HE_OK;
+    } catch (const Error &e) {
+        delete cx;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        delete cx;
+        return HE_ENOMEM;
+    }
+}
+
+void he_ctx_destroy(he_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+}
+
+int he_ctx_set_stream(he_ctx *cx, void *stream) {
+    if (!cx) return HE_EINVAL;
+    API_TRY
+    sync(cx, "stream switch");
+    cx->stream = (cudaStream_t)stream;
+    upload_constants(cx->slot, cx->pc, cx->cdt, cx->n_cdt, cx->stream);
+    sync(cx, "stream switch");
+    API_CATCH(cx)
+}
+
+int he_ctx_primes(const he_ctx *cx, uint64_t *out) {
+    if (!cx || !out) return HE_EINVAL;
+    memcpy(out, cx->primes.data(), cx->primes.size() * 8);
+    return HE_OK;
+}
+
+int he_ctx_memory(const he_ctx *cx, size_t *in_use, size_t *peak) {
+    if (!cx) return HE_EINVAL;
+    if (in_use) *in_use = cx->arena.in_use;
+    if (peak) *peak = cx->arena.peak;
+    return HE_OK;
+}
+
+const char *he_last_error(const he_ctx *cx) { return cx ? cx->err.c_str() : "null context"; }
+
+uint64_t he_launch_count(void) { return (uint64_t)launch_count(); }
+
+int he_keygen_relin(he_ctx *cx) {
+    if (!cx) return HE_EINVAL;
+    API_TRY
+    gen_relin_key(cx);
+    sync(cx, "relinearisation key");
+    API_CATCH(cx)
+}
+
+int he_keygen_galois(he_ctx *cx, uint64_t g) {
+    if (!cx) return HE_EINVAL;
+    API_TRY
+    gen_galois_key(cx, g);
+    sync(cx, "Galois key");
+    API_CATCH(cx)
+}
+
+int he_keygen_rotations(he_ctx *cx, const int32_t *steps, size_t n) {
+    if (!cx || (n && !steps)) return HE_EINVAL;
+    API_TRY
+    for (size_t i = 0; i < n; i++) gen_galois_key(cx, rot_galois(cx, steps[i]));
+    sync(cx, "rotation keys");
+    API_CATCH(cx)
+}
+
+int he_export_secret(const he_ctx *cx, int8_t *out) {
+    if (!cx || !out) return HE_EINVAL;
+    memcpy(out, cx->sk_host.data(), cx->N());
+    return HE_OK;
+}
+
+int he_export_key(he_ctx *cx, uint64_t g, uint32_t digit, int32_t which, uint64_t *out) {
+    if (!cx || !out) return HE_EINVAL;
+    API_TRY
+    const KeyDev *k = find_key(cx, g);
+    if (!k) throw Error{HE_ENOKEY, "key not generated"};
+    need((int)digit < cx->beta && (which == 0 || which == 1), "bad key digit / part");
+    const int tot = cx->nq + cx->np;
+    const size_t N = cx->N();
+    Rows tmp = make_rows(cx->ks_acc, 0, tot, cx->nq, cx->nq);
+    Rows src = make_rows(k->data + (size_t)(2 * digit + which) * tot * N, 0, tot, cx->nq, cx->nq);
+    ew_copy(tmp, src, tot, cx->log_n, cx->stream);
+    ntt_inverse(tmp, tot, cx->tw, cx->log_n, cx->stream);
+    check_cuda(cudaMemcpyAsync(out, cx->ks_acc, (size_t)tot * N * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    sync(cx, "export key");
+    API_CATCH(cx)
+}
+
+int he_encode(he_ctx *cx, const double *re, const double *im, size_t n_slots, double scale, double *out) {
+    if (!cx || !re || !out) return HE_EINVAL;
+    API_TRY
+    const size_t N = cx->N();
+    need(n_slots <= N / 2, "more values than slots");
+    double *d_re = cx->d_dbl, *d_im = im ? cx->d_dbl + N / 2 : nullptr, *d_out = cx->d_dbl + N;
+    check_cuda(cudaMemcpyAsync(d_re, re, n_slots * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    if (im) check_cuda(cudaMemcpyAsync(d_im, im, n_slots * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    encode_dev(cx, d_re, d_im, (int)n_slots, scale, d_out);
+    check_cuda(cudaMemcpyAsync(out, d_out, N * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    sync(cx, "encode");
+    API_CATCH(cx)
+}
+
+int he_encrypt(he_ctx *cx, const double *re, const double *im, size_t n_slots, double scale, uint32_t ctr,
+               int32_t level, he_ct **out) {
+    if (!cx || !re || !out) return HE_EINVAL;
+    API_TRY
+    const size_t N = cx->N();
+    need(n_slots <= N / 2, "more values than slots");
+    double *d_re = cx->d_dbl, *d_im = im ? cx->d_dbl + N / 2 : nullptr, *d_pt = cx->d_dbl + N;
+    check_cuda(cudaMemcpyAsync(d_re, re, n_slots * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    if (im) check_cuda(cudaMemcpyAsync(d_im, im, n_slots * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    encode_dev(cx, d_re, d_im, (int)n_slots, scale, d_pt);
+    Ct ct(encrypt_dev(cx, d_pt, scale, ctr, level));
+    sync(cx, "encrypt");
+    *out = ct.release();
+    API_CATCH(cx)
+}
+
+int he_encrypt_poly(he_ctx *cx, const double *m, double scale, uint32_t ctr, int32_t level, he_ct **out) {
+    if (!cx || !m || !out) return HE_EINVAL;
+    API_TRY
+    double *d_pt = cx->d_dbl + cx->N();
+    check_cuda(cudaMemcpyAsync(d_pt, m, cx->N() * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    Ct ct(encrypt_dev(cx, d_pt, scale, ctr, level));
+    sync(cx, "encrypt");
+    *out = ct.release();
+    API_CATCH(cx)
+}
+
+int he_decrypt(he_ctx *cx, const he_ct *ct, double *re, double *im, size_t n_slots) {
+    if (!cx || !ct || !re) return HE_EINVAL;
+    API_TRY
+    const size_t N = cx->N();
+    need(n_slots <= N / 2, "more values than slots");
+    double *d_c = cx->d_dbl + N, *d_re = cx->d_dbl, *d_im = cx->d_dbl + N / 2;
+    decrypt_dev(cx, ct, d_c);
+    decode_dev(cx, d_c, ct->scale, d_re, d_im);
+    check_cuda(cudaMemcpyAsync(re, d_re, n_slots * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    if (im) check_cuda(cudaMemcpyAsync(im, d_im, n_slots * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    sync(cx, "decrypt");
+    API_CATCH(cx)
+}
+
+int he_decrypt_poly(he_ctx *cx, const he_ct *ct, double *out) {
+    if (!cx || !ct || !out) return HE_EINVAL;
+    API_TRY
+    double *d_c = cx->d_dbl + cx->N();
+    decrypt_dev(cx, ct, d_c);
+    check_cuda(cudaMemcpyAsync(out, d_c, cx->N() * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    sync(cx, "decrypt");
+    API_CATCH(cx)
+}
+
+int he_ct_export(he_ctx *cx, const he_ct *ct, uint64_t *out, size_t cap) {
+    if (!cx || !ct || !out) return HE_EINVAL;
+    API_TRY
+    const size_t N = cx->N(), m = (size_t)(ct->level + 1) * N;
+    need(cap >= 2 * m, "export buffer too small");
+    u64 *tmp = (u64 *)cx->arena.alloc(2 * m * 8);
+    try {
+        Rows t = make_rows(tmp, m, ct->level + 1, ct->level + 1, cx->nq);
+        ew_copy(t, ct_rows(ct), 2 * (ct->level + 1), cx->log_n, cx->stream);
+        ntt_inverse(t, 2 * (ct->level + 1), cx->tw, cx->log_n, cx->stream);
+        check_cuda(cudaMemcpyAsync(out, tmp, 2 * m * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+        sync(cx, "export");
+    } catch (...) {
+        cx->arena.release(tmp, 2 * m * 8);
+        throw;
+    }
+    cx->arena.release(tmp, 2 * m * 8);
+    API_CATCH(cx)
+}
+
+int he_ct_import(he_ctx *cx, const uint64_t *in, uint32_t level, double scale, he_ct **out) {
+    if (!cx || !in || !out) return HE_EINVAL;
+    API_TRY
+    need((int)level < cx->nq, "level out of range");
+    Ct ct(ct_alloc(cx, (int)level, scale));
+    size_t m = (size_t)(level + 1) * cx->N();
+    check_cuda(cudaMemcpyAsync(ct->d, in, 2 * m * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    ntt_forward(ct_rows(ct.get()), 2 * (level + 1), cx->tw, cx->log_n, cx->stream);
+    sync(cx, "import");
+    *out = ct.release();
+    API_CATCH(cx)
+}
+
+int he_ct_info(const he_ct *ct, uint32_t *level, double *scale) {
+    if (!ct) return HE_EINVAL;
+    if (level) *level = (uint32_t)ct->level;
+    if (scale) *scale = ct->scale;
+    return HE_OK;
+}
+
+int he_ct_device(const he_ct *ct, uint64_t **dev, size_t *poly_stride) {
+    if (!ct) return HE_EINVAL;
+    if (dev) *dev = ct->d;
+    if (poly_stride) *poly_stride = (size_t)ct->cap * ct->ctx->N();
+    return HE_OK;
+}
+
+void he_ct_free(he_ct *ct) { ct_release(ct); }
+
+#define UNARY_OP(name, expr)                                     \
+    int name {                                                   \
+        if (!cx || !a || !out) return HE_EINVAL;                 \
+        API_TRY                                                  \
+        Ct res_ = expr;                                          \
+        launched(cx, #name);                                     \
+        *out = res_.release();                                   \
+        API_CATCH(cx)                                            \
+    }
+
+UNARY_OP(he_add(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), op_add(cx, a, b, false)))
+UNARY_OP(he_sub(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), op_add(cx, a, b, true)))
+UNARY_OP(he_mul_int(he_ctx *cx, const he_ct *a, int64_t k, he_ct **out), op_mul_int(cx, a, k))
+UNARY_OP(he_mul(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), op_mul(cx, a, b)))
+UNARY_OP(he_rescale(he_ctx *cx, const he_ct *a, he_ct **out), op_rescale(cx, a))
+UNARY_OP(he_drop(he_ctx *cx, const he_ct *a, uint32_t level, he_ct **out), op_drop(cx, a, (int)level))
+UNARY_OP(he_rotate(he_ctx *cx, const he_ct *a, int32_t r, he_ct **out), op_automorph(cx, a, rot_galois(cx, r)))
+UNARY_OP(he_conjugate(he_ctx *cx, const he_ct *a, he_ct **out), op_automorph(cx, a, 2 * cx->N() - 1))
+UNARY_OP(he_automorphism(he_ctx *cx, const he_ct *a, uint64_t g, he_ct **out), op_automorph(cx, a, g))
+
+int he_mul_const(he_ctx *cx, const he_ct *a, double c, double target, he_ct **out) {
+    if (!cx || !a || !out) return HE_EINVAL;
+    API_TRY
+    double E = (target * (double)cx->primes[a->level]) / a->scale;
+    double K = std::rint(c * E);
+    Ct t = op_mul_intd(cx, a, K, a->scale * E);
+    Ct r = op_rescale(cx, t.get());
+    launched(cx, "mul_const");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_add_const(he_ctx *cx, const he_ct *a, double c, he_ct **out) {
+    if (!cx || !a || !out) return HE_EINVAL;
+    API_TRY
+    Ct r = op_add_intd(cx, a, std::rint(c * a->scale));
+    launched(cx, "add_const");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_rotsum(he_ctx *cx, const he_ct *a, uint32_t steps, he_ct **out) {
+    if (!cx || !a || !out) return HE_EINVAL;
+    API_TRY
+    Ct cur = op_copy(cx, a);
+    for (uint32_t i = 0; i < steps; i++) {
+        Ct r = op_automorph(cx, cur.get(), rot_galois(cx, (i64)1 << i));
+        cur = op_add(cx, cur.get(), r.get(), false);
+    }
+    launched(cx, "rotsum");
+    *out = cur.release();
+    API_CATCH(cx)
+}
+
+int he_keyswitch_raw(he_ctx *cx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out0, uint64_t *out1) {
+    if (!cx || !d || !out0 || !out1) return HE_EINVAL;
+    API_TRY
+    need((int)level < cx->nq, "level out of range");
+    const KeyDev *k = find_key(cx, g);
+    if (!k) throw Error{HE_ENOKEY, "key not generated"};
+    const size_t N = cx->N(), m = (size_t)(level + 1) * N;
+    int l = (int)level;
+    check_cuda(cudaMemcpyAsync(cx->sc_a, d, m * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    Rows in = make_rows(cx->sc_a, 0, l + 1, l + 1, cx->nq);
+    ntt_forward(in, l + 1, cx->tw, cx->log_n, cx->stream);
+    Rows o = make_rows(cx->sc_b, m, l + 1, l + 1, cx->nq);
+    keyswitch(cx, cx->sc_a, l, *k, o, o, 0);
+    ntt_inverse(o, 2 * (l + 1), cx->tw, cx->log_n, cx->stream);
+    check_cuda(cudaMemcpyAsync(out0, cx->sc_b, m * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    check_cuda(cudaMemcpyAsync(out1, cx->sc_b + m, m * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    sync(cx, "keyswitch");
+    API_CATCH(cx)
+}
+
+int he_ntt_device(he_ctx *cx, uint64_t *data, uint32_t n_limbs, uint32_t prime_idx0, int32_t inverse) {
+    if (!cx || !data) return HE_EINVAL;
+    API_TRY
+    need(prime_idx0 + n_limbs <= (uint32_t)(cx->nq + cx->np), "prime range out of bounds");
+    Rows r = make_rows(data, 0, (int)n_limbs, (int)n_limbs, cx->nq, (int)prime_idx0);
+    if (inverse) ntt_inverse(r, (int)n_limbs, cx->tw, cx->log_n, cx->stream);
+    else ntt_forward(r, (int)n_limbs, cx->tw, cx->log_n, cx->stream);
+    launched(cx, "ntt");
+    API_CATCH(cx)
+}
+
+int he_cutmax_prepare(he_ctx *cx, const he_cutmax_plan *plan) {
+    if (!cx) return HE_EINVAL;
+    API_TRY
+    Plan pl = plan_from(plan);
+    std::vector<u64> gs;
+    plan_keys(cx, pl, gs);
+    gen_relin_key(cx);
+    for (u64 g : gs) gen_galois_key(cx, g);
+    sync(cx, "cutmax keys");
+    API_CATCH(cx)
+}
+
+int cutmax(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out) {
+    if (!cx || !in || !out) return HE_EINVAL;
+    API_TRY
+    Plan pl = plan_from(plan);
+    Ct r = cutmax_ct(cx, in, pl);
+    launched(cx, "cutmax");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int nucleus_sample(he_ctx *cx, const he_ct *logits, const he_ct *rand_ct, const he_cutmax_plan *plan, he_ct **out) {
+    if (!cx || !logits || !rand_ct || !out) return HE_EINVAL;
+    API_TRY
+    Plan pl = plan_from(plan);
+    Ct x = op_add(cx, logits, rand_ct, false);
+    Ct r = cutmax_ct(cx, x.get(), pl);
+    launched(cx, "nucleus_sample");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+}  // extern "C"

@@ -1,0 +1,778 @@
+// Host side of the CKKS context: prime chain, tables, device arena, keys,
+// encryption and the elementary homomorphic operations.  Every operation on
+// ring data is a launch of a kernel from kernels.cu on the context stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "context.h"
+
+namespace he {
+
+typedef unsigned __int128 u128;
+
+static std::mutex g_slot_mu;
+static bool g_slot_used[HE_MAX_CTX];
+
+static int take_slot() {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    for (int i = 0; i < HE_MAX_CTX; i++)
+        if (!g_slot_used[i]) { g_slot_used[i] = true; return i; }
+    throw Error{HE_ENOMEM, "too many live contexts (at most 8)"};
+}
+static void give_slot(int i) {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    if (i >= 0 && i < HE_MAX_CTX) g_slot_used[i] = false;
+}
+void release_slot(int i) { give_slot(i); }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw Error{HE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+// ---------------------------------------------------------------- arena
+void *Arena::alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    auto it = free_blocks.find(bytes);
+    size_t off;
+    if (it != free_blocks.end()) {
+        off = it->second;
+        free_blocks.erase(it);
+    } else {
+        if (top + bytes > cap) throw Error{HE_ENOMEM, "device arena exhausted"};
+        off = top;
+        top += bytes;
+    }
+    in_use += bytes;
+    peak = std::max(peak, in_use);
+    return base + off;
+}
+void Arena::release(void *p, size_t bytes) {
+    if (!p) return;
+    bytes = (bytes + 255) & ~(size_t)255;
+    free_blocks.emplace(bytes, (size_t)((char *)p - base));
+    in_use -= bytes;
+}
+
+// ---------------------------------------------------------------- host arithmetic
+u64 mulmod_host(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+u64 powmod_host(u64 a, u64 e, u64 q) {
+    u64 r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = mulmod_host(r, a, q);
+        a = mulmod_host(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+static u64 invmod_host(u64 a, u64 q) { return powmod_host(a, q - 2, q); }
+u64 shoup_host(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+static bool is_prime_host(u64 n) {
+    static const u64 bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (u64 b : bases)
+        if (n % b == 0) return n == b;
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) { d >>= 1; s++; }
+    for (u64 b : bases) {
+        u64 x = powmod_host(b, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool composite = true;
+        for (int r = 1; r < s && composite; r++) {
+            x = mulmod_host(x, x, n);
+            if (x == n - 1) composite = false;
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
+// Primes of b bits: q = k*2N+1 < 2^b, decreasing, one cursor per bit size.
+static std::vector<u64> make_primes(int log_n, const std::vector<int> &bits) {
+    u64 two_n = 2ull << log_n;
+    std::map<int, u64> cursor;
+    std::vector<u64> out;
+    for (int b : bits) {
+        if (b < 31 || b > 61) throw Error{HE_EINVAL, "prime bit sizes must lie in [31, 61]"};
+        if (!cursor.count(b)) cursor[b] = ((1ull << b) - 1) / two_n;
+        for (;;) {
+            u64 k = cursor[b]--;
+            u64 q = k * two_n + 1;
+            if (q < (1ull << (b - 1))) throw Error{HE_EINVAL, "ran out of NTT-friendly primes"};
+            if (is_prime_host(q)) { out.push_back(q); break; }
+        }
+    }
+    return out;
+}
+
+static u64 find_psi(u64 q, int log_n) {
+    u64 two_n = 2ull << log_n, n = 1ull << log_n;
+    for (u64 x = 2;; x++) {
+        u64 c = powmod_host(x, (q - 1) / two_n, q);
+        if (powmod_host(c, n, q) == q - 1) return c;
+    }
+}
+
+static inline u32 brv_host(u32 x, int bits) {
+    u32 r = 0;
+    for (int i = 0; i < bits; i++) { r = (r << 1) | (x & 1); x >>= 1; }
+    return r;
+}
+
+u64 intd_mod_host(double x, u64 q) {
+    if (std::fabs(x) < 9.2e18) {
+        i64 v = (i64)x;
+        i64 r = v % (i64)q;
+        return r < 0 ? (u64)(r + (i64)q) : (u64)r;
+    }
+    int e;
+    double m = std::frexp(x, &e);
+    i64 mi = (i64)std::ldexp(m, 53);
+    e -= 53;
+    i64 r0 = mi % (i64)q;
+    u64 r = r0 < 0 ? (u64)(r0 + (i64)q) : (u64)r0;
+    return mulmod_host(r, powmod_host(2, (u64)e, q), q);
+}
+
+ScalarTab scalar_int(he_ctx *cx, i64 k, int n_limbs) {
+    ScalarTab t;
+    memset(&t, 0, sizeof(t));
+    int tot = cx->nq + cx->np;
+    for (int i = 0; i < tot && i < HE_MAX_PRIMES; i++) {
+        u64 q = cx->primes[i];
+        i64 r = k % (i64)q;
+        t.v[i] = r < 0 ? (u64)(r + (i64)q) : (u64)r;
+        t.s[i] = shoup_host(t.v[i], q);
+    }
+    (void)n_limbs;
+    return t;
+}
+ScalarTab scalar_intd(he_ctx *cx, double K, int n_limbs) {
+    ScalarTab t;
+    memset(&t, 0, sizeof(t));
+    int tot = cx->nq + cx->np;
+    for (int i = 0; i < tot; i++) {
+        u64 q = cx->primes[i];
+        t.v[i] = intd_mod_host(K, q);
+        t.s[i] = shoup_host(t.v[i], q);
+    }
+    (void)n_limbs;
+    return t;
+}
+
+// ---------------------------------------------------------------- ciphertexts
+void CtDel::operator()(he_ct *c) const { ct_release(c); }
+
+he_ct *ct_alloc(he_ctx *cx, int level, double scale) {
+    he_ct *ct = new he_ct;
+    ct->ctx = cx;
+    ct->level = level;
+    ct->scale = scale;
+    ct->cap = level + 1;
+    ct->bytes = (size_t)2 * ct->cap * cx->N() * 8;
+    try {
+        ct->d = (u64 *)cx->arena.alloc(ct->bytes);
+    } catch (...) {
+        delete ct;
+        throw;
+    }
+    return ct;
+}
+void ct_release(he_ct *ct) {
+    if (!ct) return;
+    ct->ctx->arena.release(ct->d, ct->bytes);
+    delete ct;
+}
+Rows ct_rows(const he_ct *ct, int level) {
+    int l = level < 0 ? ct->level : level;
+    return make_rows(ct->d, (size_t)ct->cap * ct->ctx->N(), l + 1, l + 1, ct->ctx->nq);
+}
+u64 *ct_poly(const he_ct *ct, int k) { return ct->d + (size_t)k * ct->cap * ct->ctx->N(); }
+
+
+// ---------------------------------------------------------------- setup
+static void gauss_cdt(double sigma, u64 *table) {
+    const int B = 19;
+    double rho[B + 1], z = 0.0;
+    for (int k = 0; k <= B; k++) {
+        rho[k] = std::exp(-((double)k * (double)k) / (2.0 * sigma * sigma));
+        z += (k == 0 ? 1.0 : 2.0) * rho[k];
+    }
+    double cdf = 0.0;
+    for (int k = 0; k < B; k++) {
+        cdf += (k == 0 ? 1.0 : 2.0) * rho[k] / z;
+        table[k] = (u64)std::ldexp(cdf, 64);
+    }
+}
+
+// Philox4x32-10 (host copy for the sparse secret's Fisher-Yates draws)
+static void philox_host(u32 c[4], u32 k0, u32 k1) {
+    const u32 M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    for (int r = 0; r < 10; r++) {
+        if (r) { k0 += W0; k1 += W1; }
+        u64 p0 = (u64)M0 * c[0], p1 = (u64)M1 * c[2];
+        u32 n0 = (u32)(p1 >> 32) ^ c[1] ^ k0, n2 = (u32)(p0 >> 32) ^ c[3] ^ k1;
+        c[0] = n0; c[1] = (u32)p1; c[2] = n2; c[3] = (u32)p0;
+    }
+}
+
+static void make_secret(he_ctx *cx) {
+    size_t n = cx->N();
+    cx->sk_host.assign(n, 0);
+    u32 k0 = (u32)cx->seed, k1 = (u32)(cx->seed >> 32);
+    if (cx->h == 0) {
+        for (size_t k = 0; k < n; k++) {
+            u32 c[4] = {(u32)k, 0, 0, DOM_SECRET};
+            philox_host(c, k0, k1);
+            cx->sk_host[k] = (int8_t)((int)(((u64)c[0] * 3) >> 32) - 1);
+        }
+        return;
+    }
+    std::vector<u32> perm(n);
+    for (size_t k = 0; k < n; k++) perm[k] = (u32)k;
+    for (int i = 0; i < cx->h; i++) {
+        u32 c[4] = {(u32)i, 0, 0, DOM_SPARSE};
+        philox_host(c, k0, k1);
+        u64 j = (u64)i + (((u64)c[0] * (n - (u64)i)) >> 32);
+        std::swap(perm[i], perm[j]);
+        cx->sk_host[perm[i]] = (c[1] & 1) ? -1 : 1;
+    }
+}
+
+void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
+    if (!p || p->log_n < 10 || p->log_n > 16 || p->n_q < 2 || p->n_p < 1 || p->dnum < 1 ||
+        p->n_q + p->n_p > HE_MAX_PRIMES || !p->q_bits || !p->p_bits)
+        throw Error{HE_EINVAL, "invalid parameters (log_n in [10,16], n_q >= 2, n_p >= 1, n_q+n_p <= 64)"};
+    cx->log_n = p->log_n;
+    cx->n = 1 << p->log_n;
+    cx->nq = p->n_q;
+    cx->np = p->n_p;
+    cx->dnum = p->dnum;
+    cx->alpha = (cx->nq + cx->dnum - 1) / cx->dnum;
+    cx->beta = (cx->nq + cx->alpha - 1) / cx->alpha;
+    if (cx->alpha > 16 || cx->np > 16) throw Error{HE_EINVAL, "at most 16 primes per digit and 16 special primes"};
+    cx->h = (int)p->secret_hw;
+    cx->sigma = p->sigma > 0 ? p->sigma : 3.2;
+    cx->delta = std::ldexp(1.0, 0) * std::pow(2.0, p->log_scale);
+    cx->seed = p->seed;
+    cx->boot = p->enable_bootstrap != 0;
+    std::vector<int> bits;
+    for (uint32_t i = 0; i < p->n_q; i++) bits.push_back(p->q_bits[i]);
+    for (uint32_t i = 0; i < p->n_p; i++) bits.push_back(p->p_bits[i]);
+    cx->primes = make_primes(cx->log_n, bits);
+    const int tot = cx->nq + cx->np;
+    const size_t N = cx->N();
+
+    // arena
+    size_t key_bytes = (size_t)cx->beta * 2 * tot * N * 8;
+    size_t ct_bytes = (size_t)2 * cx->nq * N * 8;
+    if (arena) {
+        cx->arena.base = (char *)arena;
+        cx->arena.cap = arena_bytes;
+    } else {
+        size_t want = arena_bytes ? arena_bytes : (key_bytes * 48 + ct_bytes * 256 + ((size_t)64 << 20));
+        size_t fr = 0, totm = 0;
+        check_cuda(cudaMemGetInfo(&fr, &totm), "cudaMemGetInfo");
+        if (!arena_bytes && want > fr * 7 / 10) want = fr * 7 / 10;
+        check_cuda(cudaMalloc(&cx->arena.base, want), "cudaMalloc(arena)");
+        cx->arena.cap = want;
+        cx->arena.owned = true;
+    }
+
+    // per-prime constants
+    memset(&cx->pc, 0, sizeof(cx->pc));
+    for (int i = 0; i < tot; i++) {
+        u64 q = cx->primes[i];
+        int b = 64 - __builtin_clzll(q);
+        cx->pc.m[i].q = q;
+        cx->pc.m[i].b = (u32)b;
+        cx->pc.m[i].mu = (u64)(((u128)1 << (2 * b + 1)) / q);
+        u64 ni = invmod_host(N % q, q);
+        cx->pc.n_inv[i] = ni;
+        cx->pc.n_inv_shoup[i] = shoup_host(ni, q);
+    }
+    gauss_cdt(cx->sigma, cx->cdt);
+    cx->slot = take_slot();
+    t_slot = cx->slot;
+    upload_constants(cx->slot, cx->pc, cx->cdt, cx->n_cdt, cx->stream);
+
+    // twiddles: fwd[k] = psi^brv(k), inv[k] = psi^-brv(k)
+    cx->d_tw = (u64 *)cx->arena.alloc((size_t)4 * tot * N * 8);
+    {
+        std::vector<u64> h((size_t)4 * tot * N);
+        std::vector<u64> pw(N), ipw(N);
+        for (int i = 0; i < tot; i++) {
+            u64 q = cx->primes[i], psi = find_psi(q, cx->log_n), ipsi = invmod_host(psi, q);
+            pw[0] = ipw[0] = 1;
+            for (size_t k = 1; k < N; k++) {
+                pw[k] = mulmod_host(pw[k - 1], psi, q);
+                ipw[k] = mulmod_host(ipw[k - 1], ipsi, q);
+            }
+            u64 *f = &h[(size_t)i * N], *fs = &h[((size_t)tot + i) * N];
+            u64 *v = &h[((size_t)2 * tot + i) * N], *vs = &h[((size_t)3 * tot + i) * N];
+            for (size_t k = 0; k < N; k++) {
+                u32 b = brv_host((u32)k, cx->log_n);
+                f[k] = pw[b];
+                fs[k] = shoup_host(f[k], q);
+                v[k] = ipw[b];
+                vs[k] = shoup_host(v[k], q);
+            }
+        }
+        check_cuda(cudaMemcpy(cx->d_tw, h.data(), h.size() * 8, cudaMemcpyHostToDevice), "upload twiddles");
+        cx->tw.fwd = cx->d_tw;
+        cx->tw.fwd_sh = cx->d_tw + (size_t)tot * N;
+        cx->tw.inv = cx->d_tw + (size_t)2 * tot * N;
+        cx->tw.inv_sh = cx->d_tw + (size_t)3 * tot * N;
+    }
+
+    // scratch
+    cx->ks_coef = (u64 *)cx->arena.alloc((size_t)cx->nq * N * 8);
+    cx->ks_ext = (u64 *)cx->arena.alloc((size_t)cx->beta * tot * N * 8);
+    cx->ks_acc = (u64 *)cx->arena.alloc((size_t)2 * tot * N * 8);
+    cx->ks_conv = (u64 *)cx->arena.alloc((size_t)2 * cx->nq * N * 8);
+    cx->sc_a = (u64 *)cx->arena.alloc((size_t)2 * tot * N * 8);
+    cx->sc_b = (u64 *)cx->arena.alloc((size_t)2 * tot * N * 8);
+    cx->d_fft = (Cplx *)cx->arena.alloc(N / 2 * sizeof(Cplx));
+    cx->d_dbl = (double *)cx->arena.alloc(3 * N * sizeof(double));
+    cx->d_slot_l = (int *)cx->arena.alloc(N / 2 * sizeof(int));
+    {
+        std::vector<int> sl(N / 2);
+        u64 g = 1, two_n = 2 * N;
+        for (size_t j = 0; j < N / 2; j++) {
+            sl[j] = (int)((g - 1) / 4);
+            g = (g * 5) % two_n;
+        }
+        check_cuda(cudaMemcpy(cx->d_slot_l, sl.data(), sl.size() * sizeof(int), cudaMemcpyHostToDevice),
+                   "upload slot map");
+    }
+
+    // basis-conversion tables, per level
+    std::vector<u64> tab;  // host staging
+    struct Pending { int l, j; size_t qhinv, qhat; int n_in, n_out; };
+    std::vector<Pending> pend;
+    std::vector<int2> desc_all;
+    std::vector<size_t> desc_off(cx->nq);
+    cx->lv.resize(cx->nq);
+    const int K = cx->np;
+    for (int l = 0; l < cx->nq; l++) {
+        LevelTabs &T = cx->lv[l];
+        T.n_ext = l + 1 + K;
+        T.beta = (l + 1 + cx->alpha - 1) / cx->alpha;
+        desc_off[l] = desc_all.size();
+        for (int j = 0; j < T.beta; j++) {
+            int lo = j * cx->alpha, cnt = std::min(cx->alpha, l + 1 - lo);
+            T.digit_lo.push_back(lo);
+            T.digit_cnt.push_back(cnt);
+            T.digit_off.push_back((int)(desc_all.size() - desc_off[l]));
+            std::vector<int> targets;
+            for (int t = 0; t < T.n_ext; t++)
+                if (t < lo || t >= lo + cnt) targets.push_back(t);
+            T.digit_nout.push_back((int)targets.size());
+            for (int t : targets) {
+                int pt = t <= l ? t : cx->nq + (t - l - 1);
+                desc_all.push_back(make_int2(j * T.n_ext + t, pt));
+            }
+            Pending pd{l, j, tab.size(), 0, cnt, (int)targets.size()};
+            for (int a = 0; a < cnt; a++) {
+                u64 qa = cx->primes[lo + a], v = 1;
+                for (int b = 0; b < cnt; b++)
+                    if (b != a) v = mulmod_host(v, cx->primes[lo + b] % qa, qa);
+                u64 inv = invmod_host(v, qa);
+                tab.push_back(inv);
+            }
+            for (int a = 0; a < cnt; a++) tab.push_back(shoup_host(tab[pd.qhinv + a], cx->primes[lo + a]));
+            pd.qhat = tab.size();
+            std::vector<u64> qh((size_t)cnt * targets.size());
+            for (int a = 0; a < cnt; a++)
+                for (size_t u = 0; u < targets.size(); u++) {
+                    int t = targets[u];
+                    u64 pt = cx->primes[t <= l ? t : cx->nq + (t - l - 1)], v = 1;
+                    for (int b = 0; b < cnt; b++)
+                        if (b != a) v = mulmod_host(v, cx->primes[lo + b] % pt, pt);
+                    qh[(size_t)a * targets.size() + u] = v;
+                }
+            for (u64 v : qh) tab.push_back(v);
+            for (int a = 0; a < cnt; a++)
+                for (size_t u = 0; u < targets.size(); u++) {
+                    int t = targets[u];
+                    u64 pt = cx->primes[t <= l ? t : cx->nq + (t - l - 1)];
+                    tab.push_back(shoup_host(qh[(size_t)a * targets.size() + u], pt));
+                }
+            pend.push_back(pd);
+        }
+        T.n_desc = (int)(desc_all.size() - desc_off[l]);
+        if (l >= 1) {
+            memset(&T.ql_inv, 0, sizeof(T.ql_inv));
+            u64 ql = cx->primes[l];
+            for (int i = 0; i < l; i++) {
+                u64 q = cx->primes[i];
+                T.ql_inv.v[i] = invmod_host(ql % q, q);
+                T.ql_inv.s[i] = shoup_host(T.ql_inv.v[i], q);
+            }
+        }
+    }
+    // ModDown: P -> Q
+    size_t md_off = tab.size();
+    for (int a = 0; a < K; a++) {
+        u64 pa = cx->primes[cx->nq + a], v = 1;
+        for (int b = 0; b < K; b++)
+            if (b != a) v = mulmod_host(v, cx->primes[cx->nq + b] % pa, pa);
+        tab.push_back(invmod_host(v, pa));
+    }
+    for (int a = 0; a < K; a++) tab.push_back(shoup_host(tab[md_off + a], cx->primes[cx->nq + a]));
+    size_t md_qhat = tab.size();
+    for (int a = 0; a < K; a++)
+        for (int i = 0; i < cx->nq; i++) {
+            u64 q = cx->primes[i], v = 1;
+            for (int b = 0; b < K; b++)
+                if (b != a) v = mulmod_host(v, cx->primes[cx->nq + b] % q, q);
+            tab.push_back(v);
+        }
+    for (int a = 0; a < K; a++)
+        for (int i = 0; i < cx->nq; i++) tab.push_back(shoup_host(tab[md_qhat + (size_t)a * cx->nq + i], cx->primes[i]));
+    memset(&cx->p_inv, 0, sizeof(cx->p_inv));
+    memset(&cx->p_mod, 0, sizeof(cx->p_mod));
+    for (int i = 0; i < cx->nq; i++) {
+        u64 q = cx->primes[i], P = 1;
+        for (int b = 0; b < K; b++) P = mulmod_host(P, cx->primes[cx->nq + b] % q, q);
+        cx->p_mod.v[i] = P;
+        cx->p_mod.s[i] = shoup_host(P, q);
+        cx->p_inv.v[i] = invmod_host(P, q);
+        cx->p_inv.s[i] = shoup_host(cx->p_inv.v[i], q);
+    }
+    size_t desc_bytes = desc_all.size() * sizeof(int2);
+    cx->d_tabs = (u64 *)cx->arena.alloc(tab.size() * 8 + desc_bytes + 16);
+    check_cuda(cudaMemcpy(cx->d_tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice), "upload tables");
+    int2 *d_desc = (int2 *)(cx->d_tabs + tab.size());
+    check_cuda(cudaMemcpy(d_desc, desc_all.data(), desc_bytes, cudaMemcpyHostToDevice), "upload descriptors");
+    for (auto &pd : pend) {
+        LevelTabs &T = cx->lv[pd.l];
+        BConvTab bt;
+        bt.qhinv = cx->d_tabs + pd.qhinv;
+        bt.qhinv_sh = cx->d_tabs + pd.qhinv + pd.n_in;
+        bt.qhat = cx->d_tabs + pd.qhat;
+        bt.qhat_sh = cx->d_tabs + pd.qhat + (size_t)pd.n_in * pd.n_out;
+        bt.n_in = pd.n_in;
+        bt.n_out = pd.n_out;
+        bt.stride = pd.n_out;
+        T.modup.push_back(bt);
+    }
+    for (int l = 0; l < cx->nq; l++) cx->lv[l].desc = d_desc + desc_off[l];
+    cx->moddown.qhinv = cx->d_tabs + md_off;
+    cx->moddown.qhinv_sh = cx->d_tabs + md_off + K;
+    cx->moddown.qhat = cx->d_tabs + md_qhat;
+    cx->moddown.qhat_sh = cx->d_tabs + md_qhat + (size_t)K * cx->nq;
+    cx->moddown.n_in = K;
+    cx->moddown.n_out = cx->nq;
+    cx->moddown.stride = cx->nq;
+
+    // secret
+    make_secret(cx);
+    cx->d_sk_small = (int8_t *)cx->arena.alloc(N);
+    check_cuda(cudaMemcpy(cx->d_sk_small, cx->sk_host.data(), N, cudaMemcpyHostToDevice), "upload secret");
+    cx->d_sk_ntt = (u64 *)cx->arena.alloc((size_t)tot * N * 8);
+    Rows sk = make_rows(cx->d_sk_ntt, 0, tot, cx->nq, cx->nq);
+    load_small(sk, tot, cx->d_sk_small, cx->log_n, cx->stream);
+    ntt_forward(sk, tot, cx->tw, cx->log_n, cx->stream);
+    check_cuda(cudaStreamSynchronize(cx->stream), "context setup");
+}
+
+// ---------------------------------------------------------------- keys
+const KeyDev *find_key(he_ctx *cx, u64 g) {
+    for (auto &k : cx->keys)
+        if (k.g == g) return &k;
+    return nullptr;
+}
+
+// b_j = -a_j s + e_j + [i in digit j] P s'  (all primes of Q and P, NTT form)
+static void build_key(he_ctx *cx, u64 g, const u64 *d_sp /*[(nq+np)][N] NTT*/) {
+    const int tot = cx->nq + cx->np;
+    const size_t N = cx->N();
+    KeyDev k;
+    k.g = g;
+    k.bytes = (size_t)cx->beta * 2 * tot * N * 8;
+    k.data = (u64 *)cx->arena.alloc(k.bytes);
+    cudaStream_t s = cx->stream;
+    for (int j = 0; j < cx->beta; j++) {
+        u32 obj = ((u32)g << 8) | (u32)j;
+        u64 *b = k.data + (size_t)(2 * j) * tot * N, *a = k.data + (size_t)(2 * j + 1) * tot * N;
+        Rows rb = make_rows(b, 0, tot, cx->nq, cx->nq), ra = make_rows(a, 0, tot, cx->nq, cx->nq);
+        Rows sk = make_rows(cx->d_sk_ntt, 0, tot, cx->nq, cx->nq);
+        Rows tmp = make_rows(cx->sc_a, 0, tot, cx->nq, cx->nq);
+        sample_uniform(ra, tot, cx->seed, obj, DOM_KEY_A, cx->log_n, s);
+        sample_error_plus(rb, tot, cx->seed, obj, DOM_KEY_E, nullptr, cx->log_n, s);
+        ntt_forward(rb, tot, cx->tw, cx->log_n, s);
+        ew_mul(tmp, ra, sk, tot, cx->log_n, s);
+        ew_add(rb, rb, tmp, tot, 1, cx->log_n, s);
+        int lo = j * cx->alpha, cnt = std::min(cx->alpha, cx->nq - lo);
+        Rows dig = make_rows(b + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
+        Rows sp = make_rows((u64 *)d_sp + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
+        Rows t2 = make_rows(cx->sc_a, 0, cnt, cnt, cx->nq, lo);
+        ew_mul_scalar(t2, sp, cx->p_mod, cnt, cx->log_n, s);
+        ew_add(dig, dig, t2, cnt, 0, cx->log_n, s);
+    }
+    check_cuda(cudaGetLastError(), "key generation");
+    cx->keys.push_back(k);
+}
+
+void gen_relin_key(he_ctx *cx) {
+    if (find_key(cx, 0)) return;
+    const int tot = cx->nq + cx->np;
+    Rows sk = make_rows(cx->d_sk_ntt, 0, tot, cx->nq, cx->nq);
+    Rows s2 = make_rows(cx->sc_b, 0, tot, cx->nq, cx->nq);
+    ew_mul(s2, sk, sk, tot, cx->log_n, cx->stream);
+    build_key(cx, 0, cx->sc_b);
+}
+
+void gen_galois_key(he_ctx *cx, u64 g) {
+    if (g == 0 || (g & 1) == 0 || g >= 2 * cx->N()) throw Error{HE_EINVAL, "Galois element must be odd and < 2N"};
+    if (find_key(cx, g)) return;
+    const int tot = cx->nq + cx->np;
+    Rows sk = make_rows(cx->d_sk_ntt, 0, tot, cx->nq, cx->nq);
+    Rows sg = make_rows(cx->sc_b, 0, tot, cx->nq, cx->nq);
+    ew_automorph_ntt(sg, sk, tot, g, cx->log_n, cx->stream);
+    build_key(cx, g, cx->sc_b);
+}
+
+u64 rot_galois(he_ctx *cx, i64 r) {
+    u64 two_n = 2 * cx->N(), slots = cx->N() / 2;
+    i64 rr = r % (i64)slots;
+    if (rr < 0) rr += (i64)slots;
+    return powmod_host(5, (u64)rr, two_n);
+}
+
+// ---------------------------------------------------------------- encryption
+he_ct *encrypt_dev(he_ctx *cx, const double *d_pt, double scale, u32 ctr, int level) {
+    if (level < 0) level = cx->nq - 1;
+    if (level >= cx->nq) throw Error{HE_EINVAL, "level out of range"};
+    he_ct *ct = ct_alloc(cx, level, scale);
+    cudaStream_t s = cx->stream;
+    Rows c0 = make_rows(ct_poly(ct, 0), 0, level + 1, level + 1, cx->nq);
+    Rows c1 = make_rows(ct_poly(ct, 1), 0, level + 1, level + 1, cx->nq);
+    Rows sk = make_rows(cx->d_sk_ntt, 0, level + 1, level + 1, cx->nq);
+    Rows tmp = make_rows(cx->sc_a, 0, level + 1, level + 1, cx->nq);
+    sample_uniform(c1, level + 1, cx->seed, ctr, DOM_UNIFORM, cx->log_n, s);
+    sample_error_plus(c0, level + 1, cx->seed, ctr, DOM_ERROR, d_pt, cx->log_n, s);
+    ntt_forward(c0, level + 1, cx->tw, cx->log_n, s);
+    ew_mul(tmp, c1, sk, level + 1, cx->log_n, s);
+    ew_add(c0, c0, tmp, level + 1, 1, cx->log_n, s);
+    return ct;
+}
+
+void decrypt_dev(he_ctx *cx, const he_ct *ct, double *d_out) {
+    int nl = ct->level >= 1 ? 2 : 1;
+    cudaStream_t s = cx->stream;
+    Rows m = make_rows(cx->sc_a, 0, nl, nl, cx->nq);
+    Rows c0 = make_rows(ct_poly(ct, 0), 0, nl, nl, cx->nq);
+    Rows c1 = make_rows(ct_poly(ct, 1), 0, nl, nl, cx->nq);
+    Rows sk = make_rows(cx->d_sk_ntt, 0, nl, nl, cx->nq);
+    decrypt_rows(m, c0, c1, sk, nl, cx->log_n, s);
+    ntt_inverse(m, nl, cx->tw, cx->log_n, s);
+    u64 q0 = cx->primes[0], q1 = cx->primes[1];
+    u64 q0inv = invmod_host(q0 % q1, q1);
+    crt_to_double(d_out, cx->sc_a, cx->sc_a + cx->N(), q0, q1, q0inv, nl == 2, cx->log_n, s);
+}
+
+void encode_dev(he_ctx *cx, const double *d_re, const double *d_im, int n_slots, double scale, double *d_out) {
+    encode_slots(d_out, d_re, d_im, n_slots, scale, cx->d_slot_l, cx->d_fft, cx->log_n, cx->stream);
+}
+void decode_dev(he_ctx *cx, const double *d_coeff, double scale, double *d_re, double *d_im) {
+    decode_coeffs(d_re, d_im, d_coeff, scale, cx->d_slot_l, cx->d_fft, cx->log_n, cx->stream);
+}
+
+// ---------------------------------------------------------------- evaluator
+Ct op_copy(he_ctx *cx, const he_ct *a) {
+    Ct out(ct_alloc(cx, a->level, a->scale));
+    ew_copy(ct_rows(out.get()), ct_rows(a), 2 * (a->level + 1), cx->log_n, cx->stream);
+    return out;
+}
+
+Ct op_add(he_ctx *cx, const he_ct *a, const he_ct *b, bool sub) {
+    int l = std::min(a->level, b->level);
+    Ct out(ct_alloc(cx, l, a->scale));
+    ew_add(ct_rows(out.get()), ct_rows(a, l), ct_rows(b, l), 2 * (l + 1), sub ? 1 : 0, cx->log_n, cx->stream);
+    return out;
+}
+
+Ct op_mul_int(he_ctx *cx, const he_ct *a, i64 k) {
+    Ct out(ct_alloc(cx, a->level, a->scale));
+    ew_mul_scalar(ct_rows(out.get()), ct_rows(a), scalar_int(cx, k, a->level + 1), 2 * (a->level + 1), cx->log_n,
+                  cx->stream);
+    return out;
+}
+
+Ct op_mul_intd(he_ctx *cx, const he_ct *a, double K, double scale_out) {
+    Ct out(ct_alloc(cx, a->level, scale_out));
+    ew_mul_scalar(ct_rows(out.get()), ct_rows(a), scalar_intd(cx, K, a->level + 1), 2 * (a->level + 1), cx->log_n,
+                  cx->stream);
+    return out;
+}
+
+Ct op_add_intd(he_ctx *cx, const he_ct *a, double K) {
+    Ct out(ct_alloc(cx, a->level, a->scale));
+    int l = a->level;
+    Rows o0 = make_rows(ct_poly(out.get(), 0), 0, l + 1, l + 1, cx->nq);
+    Rows a0 = make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq);
+    Rows o1 = make_rows(ct_poly(out.get(), 1), 0, l + 1, l + 1, cx->nq);
+    Rows a1 = make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq);
+    ew_add_scalar(o0, a0, scalar_intd(cx, K, l + 1), l + 1, cx->log_n, cx->stream);
+    ew_copy(o1, a1, l + 1, cx->log_n, cx->stream);
+    return out;
+}
+
+// integer plaintext (device doubles, N) -> NTT rows in scratch sc_b
+static Rows plain_rows(he_ctx *cx, const double *d_pt, int l) {
+    Rows pt = make_rows(cx->sc_b, 0, l + 1, l + 1, cx->nq);
+    load_intd(pt, l + 1, d_pt, cx->log_n, cx->stream);
+    ntt_forward(pt, l + 1, cx->tw, cx->log_n, cx->stream);
+    return pt;
+}
+
+Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out) {
+    int l = a->level;
+    Rows pt = plain_rows(cx, d_pt, l);
+    Ct out(ct_alloc(cx, l, scale_out));
+    for (int k = 0; k < 2; k++) {
+        Rows o = make_rows(ct_poly(out.get(), k), 0, l + 1, l + 1, cx->nq);
+        Rows x = make_rows(ct_poly(a, k), 0, l + 1, l + 1, cx->nq);
+        ew_mul(o, x, pt, l + 1, cx->log_n, cx->stream);
+    }
+    return out;
+}
+
+Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt) {
+    int l = a->level;
+    Rows pt = plain_rows(cx, d_pt, l);
+    Ct out = op_copy(cx, a);
+    Rows o = make_rows(ct_poly(out.get(), 0), 0, l + 1, l + 1, cx->nq);
+    ew_add(o, o, pt, l + 1, 0, cx->log_n, cx->stream);
+    return out;
+}
+
+void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask) {
+    const int K = cx->np, log_n = cx->log_n;
+    const size_t N = cx->N();
+    const LevelTabs &T = cx->lv[l];
+    cudaStream_t s = cx->stream;
+    // 1. coefficient form of d
+    Rows coef = make_rows(cx->ks_coef, 0, l + 1, l + 1, cx->nq);
+    ew_copy(coef, make_rows((u64 *)d_ntt, 0, l + 1, l + 1, cx->nq), l + 1, log_n, s);
+    ntt_inverse(coef, l + 1, cx->tw, log_n, s);
+    // 2. ModUp: approximate basis conversion of every digit
+    for (int j = 0; j < T.beta; j++) {
+        int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
+        Rows in = make_rows(cx->ks_coef + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
+        Rows o = desc_rows(cx->ks_ext, T.desc + T.digit_off[j]);
+        bconv(o, in, T.modup[j], 1, log_n, s);
+    }
+    // 3. NTT of all extension rows
+    ntt_forward(desc_rows(cx->ks_ext, T.desc), T.n_desc, cx->tw, log_n, s);
+    // 4. inner product with the key
+    KeyIP kp;
+    kp.d_ntt = d_ntt;
+    kp.ext = cx->ks_ext;
+    kp.key = key.data;
+    kp.acc = cx->ks_acc;
+    kp.n_rows = T.n_ext;
+    kp.l1 = l + 1;
+    kp.nq = cx->nq;
+    kp.np = K;
+    kp.alpha = cx->alpha;
+    kp.beta = T.beta;
+    kp.key_limbs = cx->nq + cx->np;
+    kp.slot = cx->slot;
+    keyswitch_inner(kp, log_n, s);
+    // 5. ModDown: INTT of the P rows, conversion P -> Q_l, NTT, subtract and scale
+    Rows accP = make_rows(cx->ks_acc + (size_t)(l + 1) * N, (size_t)T.n_ext * N, K, 0, cx->nq);
+    ntt_inverse(accP, 2 * K, cx->tw, log_n, s);
+    BConvTab md = cx->moddown;
+    md.n_out = l + 1;
+    Rows conv = make_rows(cx->ks_conv, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    bconv(conv, accP, md, 2, log_n, s);
+    ntt_forward(conv, 2 * (l + 1), cx->tw, log_n, s);
+    Rows accQ = make_rows(cx->ks_acc, (size_t)T.n_ext * N, l + 1, l + 1, cx->nq);
+    moddown_finish(out, accQ, conv, cx->p_inv, 2 * (l + 1), add, add_mask, log_n, s);
+}
+
+Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
+    const KeyDev *rk = find_key(cx, 0);
+    if (!rk) throw Error{HE_ENOKEY, "relinearisation key not generated"};
+    int l = std::min(a->level, b->level);
+    Ct out(ct_alloc(cx, l, a->scale * b->scale));
+    Rows d0 = make_rows(ct_poly(out.get(), 0), 0, l + 1, l + 1, cx->nq);
+    Rows d1 = make_rows(ct_poly(out.get(), 1), 0, l + 1, l + 1, cx->nq);
+    Rows d2 = make_rows(cx->sc_a, 0, l + 1, l + 1, cx->nq);
+    Rows a0 = make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq), a1 = make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq);
+    Rows b0 = make_rows(ct_poly(b, 0), 0, l + 1, l + 1, cx->nq), b1 = make_rows(ct_poly(b, 1), 0, l + 1, l + 1, cx->nq);
+    ew_tensor(d0, d1, d2, a0, a1, b0, b1, l + 1, cx->log_n, cx->stream);
+    Rows o = ct_rows(out.get());
+    keyswitch(cx, cx->sc_a, l, *rk, o, o, 3);
+    return out;
+}
+
+Ct op_rescale(he_ctx *cx, const he_ct *a) {
+    int l = a->level;
+    if (l < 1) throw Error{HE_ELEVEL, "cannot rescale a level-0 ciphertext"};
+    const size_t N = cx->N();
+    cudaStream_t s = cx->stream;
+    u64 ql = cx->primes[l];
+    Ct out(ct_alloc(cx, l - 1, a->scale / (double)ql));
+    // last limbs of c0, c1 -> coefficient form (scratch rows 0, 1)
+    Rows last = make_rows(cx->sc_a, N, 1, 1, cx->nq, l);
+    Rows src = make_rows(ct_poly(a, 0) + (size_t)l * N, (size_t)a->cap * N, 1, 1, cx->nq, l);
+    ew_copy(last, src, 2, cx->log_n, s);
+    ntt_inverse(last, 2, cx->tw, cx->log_n, s);
+    Rows lift = make_rows(cx->sc_b, (size_t)l * N, l, l, cx->nq);
+    rescale_lift(lift, cx->sc_a, cx->sc_a + N, ql, l, cx->log_n, s);
+    ntt_forward(lift, 2 * l, cx->tw, cx->log_n, s);
+    rescale_finish(ct_rows(out.get()), ct_rows(a, l - 1), lift, cx->lv[l].ql_inv, 2 * l, cx->log_n, s);
+    return out;
+}
+
+Ct op_drop(he_ctx *cx, const he_ct *a, int level) {
+    if (level > a->level || level < 0) throw Error{HE_EINVAL, "drop to an invalid level"};
+    Ct out(ct_alloc(cx, level, a->scale));
+    ew_copy(ct_rows(out.get()), ct_rows(a, level), 2 * (level + 1), cx->log_n, cx->stream);
+    return out;
+}
+
+Ct op_automorph(he_ctx *cx, const he_ct *a, u64 g) {
+    const KeyDev *k = find_key(cx, g);
+    if (!k) throw Error{HE_ENOKEY, "Galois key not generated for element " + std::to_string(g)};
+    int l = a->level;
+    const size_t N = cx->N();
+    Ct out(ct_alloc(cx, l, a->scale));
+    // sigma(c0) -> scratch a, sigma(c1) -> scratch b
+    Rows sa = make_rows(cx->sc_a, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    Rows sb = make_rows(cx->sc_b, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    ew_automorph_ntt(sa, make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
+    ew_automorph_ntt(sb, make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
+    keyswitch(cx, cx->sc_b, l, *k, ct_rows(out.get()), sa, 1);
+    return out;
+}
+
+Ct op_mod_raise(he_ctx *cx, const he_ct *a, int level) {
+    if (a->level != 0) throw Error{HE_EINVAL, "mod raise expects a level-0 ciphertext"};
+    const size_t N = cx->N();
+    cudaStream_t s = cx->stream;
+    Rows last = make_rows(cx->sc_a, N, 1, 1, cx->nq, 0);
+    ew_copy(last, make_rows(ct_poly(a, 0), (size_t)a->cap * N, 1, 1, cx->nq, 0), 2, cx->log_n, s);
+    ntt_inverse(last, 2, cx->tw, cx->log_n, s);
+    Ct out(ct_alloc(cx, level, a->scale));
+    Rows o = ct_rows(out.get());
+    modraise_lift(o, cx->sc_a, cx->sc_a + N, cx->primes[0], 2 * (level + 1), cx->log_n, s);
+    ntt_forward(o, 2 * (level + 1), cx->tw, cx->log_n, s);
+    return out;
+}
+
+}  // namespace he
+
+he_ctx::~he_ctx() {
+    he::release_slot(slot);
+    for (auto &k : keys) arena.release(k.data, k.bytes);
+    if (arena.owned && arena.base) cudaFree(arena.base);
+}

@@ -1,0 +1,708 @@
+// CUDA kernels of the homomorphic CutMax library (sm_103a).
+//
+// Everything that touches ring data runs here: negacyclic NTT / INTT,
+// pointwise modular arithmetic, the hybrid key-switching pieces (basis
+// conversion, key inner product, ModDown), rescale, automorphisms, the
+// Philox samplers and the float64 canonical-embedding FFT.
+#include <atomic>
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace he {
+
+thread_local int t_slot = 0;
+__constant__ PrimeConsts c_pcs[HE_MAX_CTX];
+
+void upload_constants(int slot, const PrimeConsts &pc_in, const u64 *cdt, int n_cdt, cudaStream_t s) {
+    PrimeConsts pc = pc_in;
+    for (int i = 0; i < HE_MAX_PRIMES; i++) {
+        u64 q = pc.m[i].q;
+        pc.r64[i] = q ? (u64)(((unsigned __int128)1 << 64) % q) : 0;
+    }
+    for (int i = 0; i < n_cdt && i < 24; i++) pc.cdt[i] = cdt[i];
+    pc.ncdt = n_cdt;
+    cudaMemcpyToSymbolAsync(c_pcs, &pc, sizeof(pc), sizeof(PrimeConsts) * slot, cudaMemcpyHostToDevice, s);
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launch_count() { return g_launches.load(); }
+
+static inline unsigned grid_for(size_t total, int per_block) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    size_t g = (total + per_block - 1) / per_block;
+    return (unsigned)(g > 0x7fffffff ? 0x7fffffff : g);
+}
+
+// ------------------------------------------------------------------ NTT
+// N = R*C with R = 2^LOGR, C = 2^LOGC.  Forward (Cooley-Tukey with the
+// psi twist merged, Harvey lazy butterflies in [0,4q)): stages 0..LOGR-1
+// pair rows of one column (column pass), the rest pair entries of one row
+// (row pass).  Stage with m groups uses twiddle psi^brv(m + j/(2t)).
+// Inverse (Gentleman-Sande, [0,2q)) runs the same stages in reverse, then
+// multiplies by N^-1.
+constexpr int NTT_TILE = 16;
+constexpr int NTT_THREADS = 256;
+
+template <int LOGR, int LOGC, bool FWD>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_cols(Rows rows, NttTables tw) {
+    const PrimeConsts &pc = c_pcs[rows.slot];
+    constexpr int R = 1 << LOGR, C = 1 << LOGC, LOGN = LOGR + LOGC, TC = NTT_TILE;
+    __shared__ u64 sm[R * TC];
+    const int rb = blockIdx.y;
+    u64 *x = rows.row(rb, LOGN);
+    const int p = rows.prime(rb);
+    const u64 q = pc.m[p].q, q2 = 2 * q;
+    const int c0 = blockIdx.x * TC;
+    for (int idx = threadIdx.x; idx < R * TC; idx += NTT_THREADS) {
+        int r = idx / TC, cc = idx % TC;
+        sm[idx] = x[(size_t)r * C + c0 + cc];
+    }
+    __syncthreads();
+    const u64 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
+    const u64 *Ws = (FWD ? tw.fwd_sh : tw.inv_sh) + ((size_t)p << LOGN);
+#pragma unroll 1
+    for (int st = 0; st < LOGR; st++) {
+        const int s = FWD ? st : LOGR - 1 - st;
+        const int m = 1 << s, tr = R >> (s + 1);
+        for (int b = threadIdx.x; b < (R / 2) * TC; b += NTT_THREADS) {
+            int cc = b % TC, bi = b / TC;
+            int grp = bi / tr, pos = bi % tr;
+            int r0 = grp * 2 * tr + pos;
+            u64 w = W[m + grp], ws = Ws[m + grp];
+            u64 X = sm[r0 * TC + cc], Y = sm[(r0 + tr) * TC + cc];
+            if (FWD) {
+                if (X >= q2) X -= q2;
+                u64 T = shoup_mul_lazy(Y, w, ws, q);
+                sm[r0 * TC + cc] = X + T;
+                sm[(r0 + tr) * TC + cc] = X - T + q2;
+            } else {
+                u64 S = X + Y;
+                if (S >= q2) S -= q2;
+                sm[r0 * TC + cc] = S;
+                sm[(r0 + tr) * TC + cc] = shoup_mul_lazy(X - Y + q2, w, ws, q);
+            }
+        }
+        __syncthreads();
+    }
+    if (FWD) {
+        for (int idx = threadIdx.x; idx < R * TC; idx += NTT_THREADS) {
+            int r = idx / TC, cc = idx % TC;
+            x[(size_t)r * C + c0 + cc] = sm[idx];  // lazy, finished by the row pass
+        }
+    } else {
+        const u64 ni = pc.n_inv[p], nis = pc.n_inv_shoup[p];
+        for (int idx = threadIdx.x; idx < R * TC; idx += NTT_THREADS) {
+            int r = idx / TC, cc = idx % TC;
+            x[(size_t)r * C + c0 + cc] = shoup_mul(sm[idx], ni, nis, q);
+        }
+    }
+}
+
+template <int LOGR, int LOGC, bool FWD>
+__global__ void __launch_bounds__(NTT_THREADS) k_ntt_rows(Rows rows, NttTables tw) {
+    const PrimeConsts &pc = c_pcs[rows.slot];
+    constexpr int C = 1 << LOGC, LOGN = LOGR + LOGC, TR = NTT_TILE;
+    __shared__ u64 sm[TR * C];
+    const int rb = blockIdx.y;
+    u64 *x = rows.row(rb, LOGN) + (size_t)blockIdx.x * TR * C;
+    const int p = rows.prime(rb);
+    const u64 q = pc.m[p].q, q2 = 2 * q;
+    for (int idx = threadIdx.x; idx < TR * C; idx += NTT_THREADS) sm[idx] = x[idx];
+    __syncthreads();
+    const u64 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
+    const u64 *Ws = (FWD ? tw.fwd_sh : tw.inv_sh) + ((size_t)p << LOGN);
+    const int rbase = blockIdx.x * TR;
+#pragma unroll 1
+    for (int st = 0; st < LOGC; st++) {
+        const int s = FWD ? st : LOGC - 1 - st;  // stage inside the row
+        const int t = C >> (s + 1);
+        const int m = (1 << LOGR) << s;
+        for (int b = threadIdx.x; b < TR * (C / 2); b += NTT_THREADS) {
+            int rr = b / (C / 2), bi = b % (C / 2);
+            int grp = bi / t, pos = bi % t;
+            int c0 = grp * 2 * t + pos;
+            int ti = m + ((rbase + rr) << s) + grp;
+            u64 w = W[ti], ws = Ws[ti];
+            u64 *pa = &sm[rr * C + c0];
+            u64 X = pa[0], Y = pa[t];
+            if (FWD) {
+                if (X >= q2) X -= q2;
+                u64 T = shoup_mul_lazy(Y, w, ws, q);
+                pa[0] = X + T;
+                pa[t] = X - T + q2;
+            } else {
+                u64 S = X + Y;
+                if (S >= q2) S -= q2;
+                pa[0] = S;
+                pa[t] = shoup_mul_lazy(X - Y + q2, w, ws, q);
+            }
+        }
+        __syncthreads();
+    }
+    if (FWD) {
+        for (int idx = threadIdx.x; idx < TR * C; idx += NTT_THREADS) {
+            u64 v = sm[idx];
+            if (v >= q2) v -= q2;
+            if (v >= q) v -= q;
+            x[idx] = v;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < TR * C; idx += NTT_THREADS) x[idx] = sm[idx];  // [0,2q), column pass ends it
+    }
+}
+
+template <int LOGR, int LOGC>
+static void ntt_launch(const Rows &rows, int n_rows, const NttTables &tw, bool fwd, cudaStream_t s) {
+    constexpr int R = 1 << LOGR, C = 1 << LOGC;
+    dim3 gc(C / NTT_TILE, n_rows), gr(R / NTT_TILE, n_rows);
+    g_launches.fetch_add(2, std::memory_order_relaxed);
+    if (fwd) {
+        k_ntt_cols<LOGR, LOGC, true><<<gc, NTT_THREADS, 0, s>>>(rows, tw);
+        k_ntt_rows<LOGR, LOGC, true><<<gr, NTT_THREADS, 0, s>>>(rows, tw);
+    } else {
+        k_ntt_rows<LOGR, LOGC, false><<<gr, NTT_THREADS, 0, s>>>(rows, tw);
+        k_ntt_cols<LOGR, LOGC, false><<<gc, NTT_THREADS, 0, s>>>(rows, tw);
+    }
+}
+
+static void ntt_dispatch(const Rows &rows, int n_rows, const NttTables &tw, int log_n, bool fwd, cudaStream_t s) {
+    if (n_rows <= 0) return;
+    switch (log_n) {
+        case 10: ntt_launch<5, 5>(rows, n_rows, tw, fwd, s); break;
+        case 11: ntt_launch<5, 6>(rows, n_rows, tw, fwd, s); break;
+        case 12: ntt_launch<6, 6>(rows, n_rows, tw, fwd, s); break;
+        case 13: ntt_launch<6, 7>(rows, n_rows, tw, fwd, s); break;
+        case 14: ntt_launch<7, 7>(rows, n_rows, tw, fwd, s); break;
+        case 15: ntt_launch<7, 8>(rows, n_rows, tw, fwd, s); break;
+        case 16: ntt_launch<8, 8>(rows, n_rows, tw, fwd, s); break;
+        default: break;
+    }
+}
+void ntt_forward(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s) {
+    ntt_dispatch(rows, n_rows, tw, log_n, true, s);
+}
+void ntt_inverse(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s) {
+    ntt_dispatch(rows, n_rows, tw, log_n, false, s);
+}
+
+// ------------------------------------------------------------------ elementwise
+#define EW_LOOP(total)                                                                 \
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (total);      \
+         gi += (size_t)gridDim.x * blockDim.x)
+
+__global__ void k_add(Rows out, Rows a, Rows b, int n_rows, int sub, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        u64 q = pc.m[out.prime(r)].q;
+        u64 x = a.row(r, log_n)[k], y = b.row(r, log_n)[k];
+        out.row(r, log_n)[k] = sub ? sub_mod(x, y, q) : add_mod(x, y, q);
+    }
+}
+__global__ void k_neg(Rows out, Rows a, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        u64 q = pc.m[out.prime(r)].q, x = a.row(r, log_n)[k];
+        out.row(r, log_n)[k] = x ? q - x : 0;
+    }
+}
+__global__ void k_copy(Rows out, Rows a, int n_rows, int log_n) {
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        out.row(r, log_n)[k] = a.row(r, log_n)[k];
+    }
+}
+__global__ void k_mul_scalar(Rows out, Rows a, ScalarTab kt, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        int p = out.prime(r);
+        out.row(r, log_n)[k] = shoup_mul(a.row(r, log_n)[k], kt.v[p], kt.s[p], pc.m[p].q);
+    }
+}
+__global__ void k_add_scalar(Rows out, Rows a, ScalarTab kt, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        int p = out.prime(r);
+        out.row(r, log_n)[k] = add_mod(a.row(r, log_n)[k], kt.v[p], pc.m[p].q);
+    }
+}
+__global__ void k_mul(Rows out, Rows a, Rows b, int n_rows, int acc, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        const ModQ &m = pc.m[out.prime(r)];
+        u64 v = mul_mod(a.row(r, log_n)[k], b.row(r, log_n)[k], m);
+        u64 *o = out.row(r, log_n) + k;
+        *o = acc ? add_mod(*o, v, m.q) : v;
+    }
+}
+__global__ void k_tensor(Rows d0, Rows d1, Rows d2, Rows a0, Rows a1, Rows b0, Rows b1, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[d0.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        const ModQ &m = pc.m[d0.prime(r)];
+        u64 x0 = a0.row(r, log_n)[k], x1 = a1.row(r, log_n)[k];
+        u64 y0 = b0.row(r, log_n)[k], y1 = b1.row(r, log_n)[k];
+        d0.row(r, log_n)[k] = mul_mod(x0, y0, m);
+        d1.row(r, log_n)[k] = mul_add_mod(x0, y1, x1, y0, m);
+        d2.row(r, log_n)[k] = mul_mod(x1, y1, m);
+    }
+}
+__global__ void k_automorph(Rows out, Rows a, int n_rows, u64 g, int log_n) {
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    const u64 two_n_mask = (2ull << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        u32 i = (u32)(gi & mask);
+        u64 e = 2ull * (__brev(i) >> (32 - log_n)) + 1;
+        u64 e2 = (e * g) & two_n_mask;
+        u32 src = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
+        out.row(r, log_n)[i] = a.row(r, log_n)[src];
+    }
+}
+
+void ew_add(const Rows &out, const Rows &a, const Rows &b, int n_rows, int sub, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_add<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, sub, log_n);
+}
+void ew_neg(const Rows &out, const Rows &a, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_neg<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, log_n);
+}
+void ew_copy(const Rows &out, const Rows &a, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_copy<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, log_n);
+}
+void ew_mul_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_mul_scalar<<<grid_for(t, 256), 256, 0, s>>>(out, a, k, n_rows, log_n);
+}
+void ew_add_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_add_scalar<<<grid_for(t, 256), 256, 0, s>>>(out, a, k, n_rows, log_n);
+}
+void ew_mul(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_mul<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, 0, log_n);
+}
+void ew_mul_acc(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_mul<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, 1, log_n);
+}
+void ew_tensor(const Rows &d0, const Rows &d1, const Rows &d2, const Rows &a0, const Rows &a1, const Rows &b0,
+               const Rows &b1, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_tensor<<<grid_for(t, 256), 256, 0, s>>>(d0, d1, d2, a0, a1, b0, b1, n_rows, log_n);
+}
+void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_automorph<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, g, log_n);
+}
+
+// ------------------------------------------------------------------ key switching
+// Approximate basis conversion: for every coefficient, y_a = [x_a*qhinv_a]_{q_a},
+// out_t = sum_a y_a * qhat[a][t] mod p_t.
+__global__ void k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = (size_t)n_polys * n;
+    EW_LOOP(total) {
+        int poly = (int)(gi >> log_n);
+        size_t k = gi & (n - 1);
+        u64 y[16];
+        for (int a = 0; a < tab.n_in; a++) {
+            int r = poly * tab.n_in + a;
+            u64 x = in.row(r, log_n)[k];
+            y[a] = shoup_mul(x, tab.qhinv[a], tab.qhinv_sh[a], pc.m[in.prime(r)].q);
+        }
+        for (int t = 0; t < tab.n_out; t++) {
+            int r = poly * tab.n_out + t;
+            u64 qt = pc.m[out.prime(r)].q, s = 0;
+            for (int a = 0; a < tab.n_in; a++)
+                s = add_mod(s, shoup_mul(y[a], tab.qhat[a * tab.stride + t], tab.qhat_sh[a * tab.stride + t], qt), qt);
+            out.row(r, log_n)[k] = s;
+        }
+    }
+}
+void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_polys << log_n;
+    k_bconv<<<grid_for(t, 128), 128, 0, s>>>(out, in, tab, n_polys, log_n);
+}
+
+__global__ void k_keyswitch_inner(KeyIP kp, int log_n) {
+    const PrimeConsts &pc = c_pcs[kp.slot];
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = (size_t)kp.n_rows * n;
+    EW_LOOP(total) {
+        int t = (int)(gi >> log_n);
+        size_t k = gi & (n - 1);
+        int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
+        const ModQ &m = pc.m[p];
+        int jt = t < kp.l1 ? t / kp.alpha : -1;
+        u64 a0 = 0, a1 = 0;
+        for (int j = 0; j < kp.beta; j++) {
+            u64 x = (j == jt) ? kp.d_ntt[((size_t)t << log_n) + k]
+                              : kp.ext[(((size_t)j * kp.n_rows + t) << log_n) + k];
+            const u64 *kb = kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n);
+            const u64 *ka = kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n);
+            a0 = add_mod(a0, mul_mod(x, kb[k], m), m.q);
+            a1 = add_mod(a1, mul_mod(x, ka[k], m), m.q);
+        }
+        kp.acc[((size_t)t << log_n) + k] = a0;
+        kp.acc[(((size_t)kp.n_rows + t) << log_n) + k] = a1;
+    }
+}
+void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
+    size_t t = (size_t)k.n_rows << log_n;
+    k_keyswitch_inner<<<grid_for(t, 256), 256, 0, s>>>(k, log_n);
+}
+
+__global__ void k_moddown_finish(Rows out, Rows acc, Rows conv, ScalarTab pinv, int n_rows, Rows add_to,
+                                 int add_mask, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        int p = out.prime(r);
+        u64 q = pc.m[p].q;
+        u64 v = shoup_mul(sub_mod(acc.row(r, log_n)[k], conv.row(r, log_n)[k], q), pinv.v[p], pinv.s[p], q);
+        int poly = r / out.lpp;
+        if ((add_mask >> poly) & 1) v = add_mod(v, add_to.row(r, log_n)[k], q);
+        out.row(r, log_n)[k] = v;
+    }
+}
+void moddown_finish(const Rows &out, const Rows &acc, const Rows &conv, const ScalarTab &pinv, int n_rows,
+                    const Rows &add_to, int add_mask, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_moddown_finish<<<grid_for(t, 256), 256, 0, s>>>(out, acc, conv, pinv, n_rows, add_to, add_mask, log_n);
+}
+
+// ------------------------------------------------------------------ rescale / mod raise
+__global__ void k_rescale_lift(Rows lift, const u64 *l0, const u64 *l1, u64 ql, int l, int log_n) {
+    const PrimeConsts &pc = c_pcs[lift.slot];
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = (size_t)2 * l * n;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);  // 0..2l-1: poly r / l, target prime r % l
+        size_t k = gi & (n - 1);
+        int poly = r / l, i = r % l;
+        const ModQ &m = pc.m[i];
+        u64 v = (poly ? l1 : l0)[k];
+        u64 vm = barrett_reduce(v, 0, m);
+        if (v > (ql - 1) / 2) vm = sub_mod(vm, barrett_reduce(ql, 0, m), m.q);
+        lift.row(r, log_n)[k] = vm;
+    }
+}
+void rescale_lift(const Rows &lift, const u64 *last0, const u64 *last1, u64 ql, int l, int log_n, cudaStream_t s) {
+    size_t t = (size_t)2 * l << log_n;
+    k_rescale_lift<<<grid_for(t, 256), 256, 0, s>>>(lift, last0, last1, ql, l, log_n);
+}
+__global__ void k_rescale_finish(Rows out, Rows in, Rows lift, ScalarTab qlinv, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        int p = out.prime(r);
+        u64 q = pc.m[p].q;
+        out.row(r, log_n)[k] =
+            shoup_mul(sub_mod(in.row(r, log_n)[k], lift.row(r, log_n)[k], q), qlinv.v[p], qlinv.s[p], q);
+    }
+}
+void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const ScalarTab &qlinv, int n_rows,
+                    int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_rescale_finish<<<grid_for(t, 256), 256, 0, s>>>(out, in, lift, qlinv, n_rows, log_n);
+}
+__global__ void k_modraise_lift(Rows out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = (size_t)n_rows * n;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & (n - 1);
+        int poly = r / out.lpp;
+        const ModQ &m = pc.m[out.prime(r)];
+        u64 v = (poly ? c1 : c0)[k];
+        u64 vm = barrett_reduce(v, 0, m);
+        if (v > (q0 - 1) / 2) vm = sub_mod(vm, barrett_reduce(q0, 0, m), m.q);
+        out.row(r, log_n)[k] = vm;
+    }
+}
+void modraise_lift(const Rows &out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_modraise_lift<<<grid_for(t, 256), 256, 0, s>>>(out, c0, c1, q0, n_rows, log_n);
+}
+
+// ------------------------------------------------------------------ sampling
+__device__ __forceinline__ void philox4x32_10(u32 c[4], u32 k0, u32 k1) {
+    const u32 M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) { k0 += W0; k1 += W1; }
+        u32 hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+        u32 hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+        u32 n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+__global__ void k_sample_uniform(Rows out, int n_rows, u64 seed, u32 object, u32 domain, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        u32 k = (u32)(gi & mask);
+        int p = out.prime(r);
+        u32 c[4] = {k, (u32)p, object, domain};
+        philox4x32_10(c, (u32)seed, (u32)(seed >> 32));
+        const ModQ &m = pc.m[p];
+        u64 lo = ((u64)c[1] << 32) | c[0], hi = ((u64)c[3] << 32) | c[2];
+        u64 h = mul_mod(barrett_reduce(hi, 0, m), pc.r64[p], m);
+        out.row(r, log_n)[k] = add_mod(h, barrett_reduce(lo, 0, m), m.q);
+    }
+}
+void sample_uniform(const Rows &out, int n_rows, u64 seed, u32 object, u32 domain, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_sample_uniform<<<grid_for(t, 256), 256, 0, s>>>(out, n_rows, seed, object, domain, log_n);
+}
+
+__device__ __forceinline__ u64 intd_mod(double x, const ModQ &m) {
+    // x integer-valued; exact residue for any magnitude
+    if (fabs(x) < 9.2e18) {
+        i64 v = (i64)x;
+        u64 a = v < 0 ? (u64)(-v) : (u64)v;
+        u64 r = barrett_reduce(a, 0, m);
+        return (v < 0 && r) ? m.q - r : r;
+    }
+    int e;
+    double mant = frexp(x, &e);
+    i64 mi = (i64)ldexp(mant, 53);
+    e -= 53;
+    u64 a = mi < 0 ? (u64)(-mi) : (u64)mi;
+    u64 r = barrett_reduce(a, 0, m);
+    // r * 2^e mod q by repeated doubling (e < 1024)
+    for (int i = 0; i < e; i++) r = add_mod(r, r, m.q);
+    return (mi < 0 && r) ? m.q - r : r;
+}
+
+__global__ void k_sample_error_plus(Rows out, int n_rows, u64 seed, u32 object, u32 domain, const double *pt,
+                                    int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t n = (size_t)1 << log_n;
+    EW_LOOP(n) {
+        u32 k = (u32)gi;
+        u32 c[4] = {k, 0u, object, domain};
+        philox4x32_10(c, (u32)seed, (u32)(seed >> 32));
+        u64 u = ((u64)c[1] << 32) | c[0];
+        i64 mag = 0;
+        for (int i = 0; i < pc.ncdt; i++) mag += (pc.cdt[i] <= u);
+        i64 e = (c[2] & 1) ? -mag : mag;
+        double mv = pt ? pt[k] : 0.0;
+        for (int r = 0; r < n_rows; r++) {
+            const ModQ &m = pc.m[out.prime(r)];
+            u64 em = e < 0 ? (e == 0 ? 0 : m.q - (u64)(-e)) : (u64)e;
+            u64 v = pt ? add_mod(em, intd_mod(mv, m), m.q) : em;
+            out.row(r, log_n)[k] = v;
+        }
+    }
+}
+void sample_error_plus(const Rows &out, int n_rows, u64 seed, u32 object, u32 domain, const double *pt, int log_n,
+                       cudaStream_t s) {
+    size_t t = (size_t)1 << log_n;
+    k_sample_error_plus<<<grid_for(t, 256), 256, 0, s>>>(out, n_rows, seed, object, domain, pt, log_n);
+}
+
+__global__ void k_load_small(Rows out, int n_rows, const int8_t *v, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        u64 q = pc.m[out.prime(r)].q;
+        int x = v[k];
+        out.row(r, log_n)[k] = x < 0 ? q - (u64)(-x) : (u64)x;
+    }
+}
+void load_small(const Rows &out, int n_rows, const int8_t *v, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_load_small<<<grid_for(t, 256), 256, 0, s>>>(out, n_rows, v, log_n);
+}
+__global__ void k_load_intd(Rows out, int n_rows, const double *v, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        out.row(r, log_n)[k] = intd_mod(v[k], pc.m[out.prime(r)]);
+    }
+}
+void load_intd(const Rows &out, int n_rows, const double *v, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_load_intd<<<grid_for(t, 256), 256, 0, s>>>(out, n_rows, v, log_n);
+}
+
+// ------------------------------------------------------------------ encoding (float64)
+// Slot j sits at DFT index l(j) = (5^j mod 2N - 1)/4 of the length-h (= N/2)
+// transform of the twisted coefficients b_k = (m_k + i m_{k+h}) zeta^k.
+__device__ __forceinline__ u32 brv_bits(u32 x, int bits) { return __brev(x) >> (32 - bits); }
+
+__global__ void k_enc_scatter(Cplx *A, const double *re, const double *im, int n_slots, const int *slot_l,
+                              int log_h) {
+    const size_t h = (size_t)1 << log_h;
+    EW_LOOP(h) {
+        int j = (int)gi;
+        Cplx z = {0.0, 0.0};
+        if (j < n_slots) { z.re = re[j]; z.im = im ? im[j] : 0.0; }
+        A[brv_bits((u32)slot_l[j], log_h)] = z;  // bit-reversed for the DIT stages
+    }
+}
+// one radix-2 decimation-in-time stage; sign = -1 forward (e^{-2 pi i}), +1 backward
+__global__ void k_fft_stage(Cplx *a, int log_h, int len, int sign) {
+    const size_t h = (size_t)1 << log_h;
+    const int half = len >> 1;
+    EW_LOOP(h / 2) {
+        size_t blk = gi / half, k = gi % half;
+        size_t i0 = blk * len + k, i1 = i0 + half;
+        double sn, cs;
+        sincospi((double)sign * 2.0 * (double)k / (double)len, &sn, &cs);
+        Cplx u = a[i0], v = a[i1];
+        double vr = v.re * cs - v.im * sn, vi = v.re * sn + v.im * cs;
+        a[i0] = {u.re + vr, u.im + vi};
+        a[i1] = {u.re - vr, u.im - vi};
+    }
+}
+__global__ void k_enc_untwist(double *out, const Cplx *b, double scale, int log_n) {
+    const size_t n = (size_t)1 << log_n, h = n / 2;
+    EW_LOOP(h) {
+        size_t k = gi;
+        double sn, cs;
+        sincospi(-(double)k / (double)n, &sn, &cs);
+        double f = scale / (double)h;
+        double wr = (b[k].re * cs - b[k].im * sn) * f;
+        double wi = (b[k].re * sn + b[k].im * cs) * f;
+        out[k] = rint(wr);
+        out[k + h] = rint(wi);
+    }
+}
+void encode_slots(double *out_coeff, const double *re, const double *im, int n_slots, double scale,
+                  const int *slot_l, Cplx *work, int log_n, cudaStream_t s) {
+    int log_h = log_n - 1;
+    size_t h = (size_t)1 << log_h;
+    k_enc_scatter<<<grid_for(h, 256), 256, 0, s>>>(work, re, im, n_slots, slot_l, log_h);
+    for (int len = 2; len <= (int)h; len <<= 1)
+        k_fft_stage<<<grid_for(h / 2, 256), 256, 0, s>>>(work, log_h, len, -1);
+    k_enc_untwist<<<grid_for(h, 256), 256, 0, s>>>(out_coeff, work, scale, log_n);
+}
+
+__global__ void k_dec_twist(Cplx *A, const double *m, int log_n) {
+    const size_t n = (size_t)1 << log_n, h = n / 2;
+    EW_LOOP(h) {
+        size_t k = gi;
+        double sn, cs;
+        sincospi((double)k / (double)n, &sn, &cs);
+        double wr = m[k], wi = m[k + h];
+        A[brv_bits((u32)k, log_n - 1)] = {wr * cs - wi * sn, wr * sn + wi * cs};
+    }
+}
+__global__ void k_dec_gather(double *re, double *im, const Cplx *A, double scale, const int *slot_l, int log_n) {
+    const size_t h = (size_t)1 << (log_n - 1);
+    EW_LOOP(h) {
+        Cplx v = A[slot_l[gi]];
+        re[gi] = v.re / scale;
+        if (im) im[gi] = v.im / scale;
+    }
+}
+void decode_coeffs(double *re, double *im, const double *coeff, double scale, const int *slot_l, Cplx *work,
+                   int log_n, cudaStream_t s) {
+    size_t h = (size_t)1 << (log_n - 1);
+    k_dec_twist<<<grid_for(h, 256), 256, 0, s>>>(work, coeff, log_n);
+    for (int len = 2; len <= (int)h; len <<= 1)
+        k_fft_stage<<<grid_for(h / 2, 256), 256, 0, s>>>(work, log_n - 1, len, +1);
+    k_dec_gather<<<grid_for(h, 256), 256, 0, s>>>(re, im, work, scale, slot_l, log_n);
+}
+
+// correctly rounded unsigned 128-bit -> double
+__device__ __forceinline__ double u128_to_double(u64 hi, u64 lo) {
+    if (hi == 0) return __ull2double_rn(lo);
+    int lz = __clzll(hi);
+    int shift = 64 - lz;  // bits beyond the top 64
+    u64 top, sticky;
+    if (shift == 64) { top = hi; sticky = lo != 0; }
+    else { top = (hi << lz) | (lo >> shift); sticky = (lo << (64 - shift)) != 0; }
+    top |= sticky;
+    return ldexp(__ull2double_rn(top), shift);
+}
+__global__ void k_crt2(double *out, const u64 *r0, const u64 *r1, u64 q0, u64 q1, u64 q0inv, int two, int log_n,
+                       int slot) {
+    const PrimeConsts &pc = c_pcs[slot];
+    const size_t n = (size_t)1 << log_n;
+    EW_LOOP(n) {
+        u64 x0 = r0[gi];
+        if (!two) {
+            out[gi] = x0 > q0 / 2 ? -(double)(q0 - x0) : (double)x0;
+            continue;
+        }
+        const ModQ &m1 = pc.m[1];
+        u64 x1 = r1[gi];
+        u64 k = mul_mod(sub_mod(x1, barrett_reduce(x0, 0, m1), q1), q0inv, m1);
+        // v = x0 + q0*k < q0 q1
+        u64 lo = q0 * k, hi = __umul64hi(q0, k);
+        u64 lo2 = lo + x0;
+        hi += (lo2 < lo);
+        lo = lo2;
+        // Q = q0 q1
+        u64 Qlo = q0 * q1, Qhi = __umul64hi(q0, q1);
+        // half = Q/2 (floor)
+        u64 Hlo = (Qlo >> 1) | (Qhi << 63), Hhi = Qhi >> 1;
+        bool neg = (hi > Hhi) || (hi == Hhi && lo > Hlo);
+        if (neg) {
+            u64 dlo = Qlo - lo, dhi = Qhi - hi - (Qlo < lo);
+            out[gi] = -u128_to_double(dhi, dlo);
+        } else {
+            out[gi] = u128_to_double(hi, lo);
+        }
+    }
+}
+void crt_to_double(double *out, const u64 *r0, const u64 *r1, u64 q0, u64 q1, u64 q0inv_mod_q1, int two, int log_n,
+                   cudaStream_t s) {
+    size_t t = (size_t)1 << log_n;
+    k_crt2<<<grid_for(t, 256), 256, 0, s>>>(out, r0, r1, q0, q1, q0inv_mod_q1, two, log_n, t_slot);
+}
+
+__global__ void k_decrypt_rows(Rows out, Rows c0, Rows c1, Rows sk, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        const ModQ &m = pc.m[out.prime(r)];
+        out.row(r, log_n)[k] = add_mod(c0.row(r, log_n)[k], mul_mod(c1.row(r, log_n)[k], sk.row(r, log_n)[k], m), m.q);
+    }
+}
+void decrypt_rows(const Rows &out, const Rows &c0, const Rows &c1, const Rows &sk, int n_rows, int log_n,
+                  cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_decrypt_rows<<<grid_for(t, 256), 256, 0, s>>>(out, c0, c1, sk, n_rows, log_n);
+}
+
+}  // namespace he

@@ -1,0 +1,106 @@
+// Host-callable launchers of the library's CUDA kernels (kernels.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace he {
+
+struct NttTables {
+    const u64 *fwd, *fwd_sh, *inv, *inv_sh;  // [prime][N]
+};
+
+// Residues of one constant for every prime (value and Shoup companion).
+struct ScalarTab {
+    u64 v[HE_MAX_PRIMES];
+    u64 s[HE_MAX_PRIMES];
+};
+
+// Basis-conversion table: for input a < n_in and output row t < n_out,
+// qhat[a*stride + t] (+ Shoup) and qhinv[a] (+ Shoup), device memory.
+struct BConvTab {
+    const u64 *qhinv, *qhinv_sh;  // [n_in]
+    const u64 *qhat, *qhat_sh;    // [n_in][stride]
+    int n_in, n_out, stride;
+};
+
+// number of kernels launched by this library so far (all contexts)
+unsigned long long launch_count();
+
+void upload_constants(int slot, const PrimeConsts &pc, const u64 *cdt, int n_cdt, cudaStream_t s);
+
+// NTT / INTT of n_rows limb rows in place.
+void ntt_forward(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s);
+void ntt_inverse(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s);
+
+// out = a + b / a - b (sub != 0) / -a (b ignored when neg != 0)
+void ew_add(const Rows &out, const Rows &a, const Rows &b, int n_rows, int sub, int log_n, cudaStream_t s);
+void ew_neg(const Rows &out, const Rows &a, int n_rows, int log_n, cudaStream_t s);
+void ew_copy(const Rows &out, const Rows &a, int n_rows, int log_n, cudaStream_t s);
+// out = a * K (per prime residue of K)
+void ew_mul_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s);
+// out = a + K in every position (NTT form of a constant polynomial)
+void ew_add_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s);
+// out = a (*) b pointwise
+void ew_mul(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s);
+// out = out + a (*) b pointwise
+void ew_mul_acc(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s);
+// out = a0 - a1 (*) b  (decryption / encryption building block)
+void ew_tensor(const Rows &d0, const Rows &d1, const Rows &d2, const Rows &a0, const Rows &a1,
+               const Rows &b0, const Rows &b1, int n_rows, int log_n, cudaStream_t s);
+// automorphism X -> X^g in NTT form (permutation of positions)
+void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log_n, cudaStream_t s);
+
+// Key-switch pieces
+// out row (poly*n_out + t) = sum_a [in_a * qhinv_a] * qhat[a][t], in row (poly*n_in + a)
+void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s);
+// acc0/acc1 rows t < n_rows: sum_j x_j[t] * key_j[t], x_j = (t in digit j) ? d[t] : ext_j[t]
+struct KeyIP {
+    const u64 *d_ntt;     // level limbs of the input polynomial (NTT form)
+    const u64 *ext;       // [beta][n_rows][N] extended digits (rows inside the digit unused)
+    const u64 *key;       // [beta][2][nq+np][N]
+    u64 *acc;             // [2][n_rows][N]
+    int n_rows, l1, nq, np, alpha, beta, key_limbs;
+    int slot;
+};
+void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s);
+// out_i = (acc_i - conv_i) * pinv_i; polynomial p of the batch (row / lpp)
+// also adds add_to's row when bit p of add_mask is set.
+void moddown_finish(const Rows &out, const Rows &acc, const Rows &conv, const ScalarTab &pinv, int n_rows,
+                    const Rows &add_to, int add_mask, int log_n, cudaStream_t s);
+// rescale: from coefficient-form last limbs (2 rows, prime ql) write the
+// centred lift into rows of `lift` (n_rows = 2*l targets)
+void rescale_lift(const Rows &lift, const u64 *last0, const u64 *last1, u64 ql, int l, int log_n, cudaStream_t s);
+void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const ScalarTab &qlinv, int n_rows,
+                    int log_n, cudaStream_t s);
+// mod-raise: from coefficient-form level-0 limbs of c0, c1 (prime q0) write
+// the centred lift into rows 0..l of out (coefficient form)
+void modraise_lift(const Rows &out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n, cudaStream_t s);
+
+// Sampling (Philox4x32-10, counter = (index, limb, object, domain))
+void sample_uniform(const Rows &out, int n_rows, u64 seed, u32 object, u32 domain, int log_n, cudaStream_t s);
+// e_k for every row: rounded Gaussian by CDT, optional plaintext add (integer
+// valued doubles, may be null)
+void sample_error_plus(const Rows &out, int n_rows, u64 seed, u32 object, u32 domain, const double *pt,
+                       int log_n, cudaStream_t s);
+// small signed integers (secret) -> rows
+void load_small(const Rows &out, int n_rows, const int8_t *v, int log_n, cudaStream_t s);
+// integer-valued doubles -> rows
+void load_intd(const Rows &out, int n_rows, const double *v, int log_n, cudaStream_t s);
+
+// Encoding (float64 canonical embedding)
+struct Cplx { double re, im; };
+void encode_slots(double *out_coeff, const double *re, const double *im, int n_slots, double scale,
+                  const int *slot_l, Cplx *work, int log_n, cudaStream_t s);
+void decode_coeffs(double *re, double *im, const double *coeff, double scale, const int *slot_l, Cplx *work,
+                   int log_n, cudaStream_t s);
+// centred CRT of rows 0 (and 1 when two) in coefficient form -> doubles
+void crt_to_double(double *out, const u64 *r0, const u64 *r1, u64 q0, u64 q1, u64 q0inv_mod_q1, int two,
+                   int log_n, cudaStream_t s);
+// pointwise out[k] = a[k]*b[k] + c[k] for decryption (rows 0..n_rows-1)
+void decrypt_rows(const Rows &out, const Rows &c0, const Rows &c1, const Rows &sk, int n_rows, int log_n,
+                  cudaStream_t s);
+
+}  // namespace he

@@ -1,0 +1,330 @@
+"""Thin ctypes binding of libhecutmax.so (the C ABI in include/he_cutmax.h).
+
+Argument marshalling only: every step of every operation runs in the CUDA
+library.  Device memory for the library's arena comes from PyTorch's caching
+allocator, and the library issues its kernels on PyTorch's current stream.
+If the compiled library is missing, loading raises; there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhecutmax.so")
+
+HE_OK, HE_EINVAL, HE_ENOMEM, HE_ELEVEL, HE_ERANGE, HE_ECUDA, HE_ETIMEOUT, HE_ENOKEY = range(8)
+_NAMES = {0: "HE_OK", 1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ELEVEL", 4: "HE_ERANGE", 5: "HE_ECUDA",
+          6: "HE_ETIMEOUT", 7: "HE_ENOKEY"}
+
+
+class HeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("log_n", C.c_uint32), ("n_q", C.c_uint32), ("n_p", C.c_uint32), ("dnum", C.c_uint32),
+                ("q_bits", C.POINTER(C.c_int32)), ("p_bits", C.POINTER(C.c_int32)), ("log_scale", C.c_double),
+                ("sigma", C.c_double), ("secret_hw", C.c_uint32), ("seed", C.c_uint64),
+                ("enable_bootstrap", C.c_int32)]
+
+
+class CPlan(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("packing", C.c_uint32), ("T", C.c_uint32), ("power", C.POINTER(C.c_uint32)),
+                ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_uint32)), ("kappa", C.POINTER(C.c_double)),
+                ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double)]
+
+
+_lib = None
+VP = C.c_void_p
+PP = C.POINTER(C.c_void_p)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_2509_08383_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        u64, u32, i32, i64, dbl, sz = C.c_uint64, C.c_uint32, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+        pd, pu64 = C.POINTER(C.c_double), C.POINTER(C.c_uint64)
+        sig = {
+            "he_ctx_create": [C.POINTER(Params), VP, sz, PP],
+            "he_ctx_destroy": [VP],
+            "he_ctx_set_stream": [VP, VP],
+            "he_ctx_primes": [VP, pu64],
+            "he_ctx_memory": [VP, C.POINTER(sz), C.POINTER(sz)],
+            "he_last_error": [VP],
+            "he_launch_count": [],
+            "he_keygen_relin": [VP],
+            "he_keygen_galois": [VP, u64],
+            "he_keygen_rotations": [VP, C.POINTER(i32), sz],
+            "he_export_secret": [VP, C.POINTER(C.c_int8)],
+            "he_export_key": [VP, u64, u32, i32, pu64],
+            "he_encode": [VP, pd, pd, sz, dbl, pd],
+            "he_encrypt": [VP, pd, pd, sz, dbl, u32, i32, PP],
+            "he_encrypt_poly": [VP, pd, dbl, u32, i32, PP],
+            "he_decrypt": [VP, VP, pd, pd, sz],
+            "he_decrypt_poly": [VP, VP, pd],
+            "he_ct_export": [VP, VP, pu64, sz],
+            "he_ct_import": [VP, pu64, u32, dbl, PP],
+            "he_ct_info": [VP, C.POINTER(u32), pd],
+            "he_ct_device": [VP, C.POINTER(pu64), C.POINTER(sz)],
+            "he_ct_free": [VP],
+            "he_add": [VP, VP, VP, PP],
+            "he_sub": [VP, VP, VP, PP],
+            "he_mul_int": [VP, VP, i64, PP],
+            "he_mul_const": [VP, VP, dbl, dbl, PP],
+            "he_add_const": [VP, VP, dbl, PP],
+            "he_mul": [VP, VP, VP, PP],
+            "he_rescale": [VP, VP, PP],
+            "he_drop": [VP, VP, u32, PP],
+            "he_rotate": [VP, VP, i32, PP],
+            "he_conjugate": [VP, VP, PP],
+            "he_automorphism": [VP, VP, u64, PP],
+            "he_rotsum": [VP, VP, u32, PP],
+            "he_keyswitch_raw": [VP, pu64, u32, u64, pu64, pu64],
+            "he_ntt_device": [VP, VP, u32, u32, i32],
+            "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
+            "cutmax": [VP, VP, C.POINTER(CPlan), PP],
+            "nucleus_sample": [VP, VP, VP, C.POINTER(CPlan), PP],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name in ("he_ctx_destroy", "he_ct_free") else C.c_int
+        L.he_last_error.restype = C.c_char_p
+        L.he_launch_count.restype = C.c_uint64
+        _lib = L
+    return _lib
+
+
+def launch_count():
+    return int(lib().he_launch_count())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _u64ptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint64))
+
+
+class Ciphertext:
+    __slots__ = ("ctx", "ptr")
+
+    def __init__(self, ctx, ptr):
+        self.ctx = ctx
+        self.ptr = ptr
+
+    def __del__(self):
+        if self.ptr and _lib is not None:
+            _lib.he_ct_free(self.ptr)
+            self.ptr = None
+
+    def _info(self):
+        lv, sc = C.c_uint32(), C.c_double()
+        lib().he_ct_info(self.ptr, C.byref(lv), C.byref(sc))
+        return lv.value, sc.value
+
+    @property
+    def level(self):
+        return self._info()[0]
+
+    @property
+    def scale(self):
+        return self._info()[1]
+
+    def export(self):
+        """(2, level+1, N) uint64, coefficient form."""
+        L = self.level
+        out = np.zeros(2 * (L + 1) * self.ctx.n, dtype=np.uint64)
+        self.ctx._chk(lib().he_ct_export(self.ctx.ptr, self.ptr, _u64ptr(out), out.size))
+        return out.reshape(2, L + 1, self.ctx.n)
+
+
+def plan_struct(plan):
+    """Package CutMaxPlan -> (ctypes struct, keep-alive arrays)."""
+    T = plan.T
+    arrs = dict(power=(C.c_uint32 * T)(*plan.p), c=(C.c_double * T)(*plan.c), k=(C.c_uint32 * T)(*plan.k),
+                kappa=(C.c_double * T)(*plan.kappa), y0=(C.c_double * T)(*plan.y0))
+    s = CPlan(n=plan.n, packing=0 if plan.packing == "replicate" else 1, T=T, power=arrs["power"], c=arrs["c"],
+              k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f)
+    return s, arrs
+
+
+class Context:
+    """A CKKS context on the current CUDA device (see he_ctx_create)."""
+
+    def __init__(self, log_n, qbits, pbits, dnum, log_scale=40.0, sigma=3.2, h=0, seed=0, bootstrap=False,
+                 arena_bytes=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.log_n, self.n, self.slots = log_n, 1 << log_n, 1 << (log_n - 1)
+        self.nq, self.np_ = len(qbits), len(pbits)
+        self.delta = 2.0 ** log_scale
+        qb = (C.c_int32 * len(qbits))(*qbits)
+        pb = (C.c_int32 * len(pbits))(*pbits)
+        prm = Params(log_n=log_n, n_q=len(qbits), n_p=len(pbits), dnum=dnum, q_bits=qb, p_bits=pb,
+                     log_scale=log_scale, sigma=sigma, secret_hw=h, seed=seed, enable_bootstrap=int(bootstrap))
+        if arena_bytes is None:
+            alpha = -(-len(qbits) // dnum)
+            beta = -(-len(qbits) // alpha)
+            key = beta * 2 * (len(qbits) + len(pbits)) * self.n * 8
+            ct = 2 * len(qbits) * self.n * 8
+            arena_bytes = 48 * key + 192 * ct + (64 << 20)
+        self._arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        self.ptr = C.c_void_p()
+        rc = lib().he_ctx_create(C.byref(prm), C.c_void_p(self._arena.data_ptr()), int(arena_bytes),
+                                 C.byref(self.ptr))
+        if rc != 0:
+            raise HeError(rc, "context creation failed")
+        self._chk(lib().he_ctx_set_stream(self.ptr, C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        pr = np.zeros(self.nq + self.np_, dtype=np.uint64)
+        lib().he_ctx_primes(self.ptr, _u64ptr(pr))
+        self.primes = [int(p) for p in pr]
+        self.top_level = self.nq - 1
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.he_ctx_destroy(self.ptr)
+            self.ptr = None
+
+    def _chk(self, rc):
+        if rc != 0:
+            raise HeError(rc, lib().he_last_error(self.ptr).decode())
+
+    def _ct(self, fn, *args):
+        out = C.c_void_p()
+        self._chk(fn(self.ptr, *args, C.byref(out)))
+        return Ciphertext(self, out)
+
+    def memory(self):
+        a, b = C.c_size_t(), C.c_size_t()
+        lib().he_ctx_memory(self.ptr, C.byref(a), C.byref(b))
+        return a.value, b.value
+
+    # keys
+    def secret(self):
+        out = np.zeros(self.n, dtype=np.int8)
+        self._chk(lib().he_export_secret(self.ptr, out.ctypes.data_as(C.POINTER(C.c_int8))))
+        return out
+
+    def gen_relin_key(self):
+        self._chk(lib().he_keygen_relin(self.ptr))
+
+    def gen_galois_key(self, g):
+        self._chk(lib().he_keygen_galois(self.ptr, int(g)))
+
+    def gen_rot_keys(self, steps):
+        arr = (C.c_int32 * len(steps))(*steps)
+        self._chk(lib().he_keygen_rotations(self.ptr, arr, len(steps)))
+
+    def key_export(self, g, digit, which):
+        out = np.zeros((self.nq + self.np_) * self.n, dtype=np.uint64)
+        self._chk(lib().he_export_key(self.ptr, int(g), digit, which, _u64ptr(out)))
+        return out.reshape(self.nq + self.np_, self.n)
+
+    # encoding / encryption
+    def encode(self, z, scale):
+        z = np.asarray(z)
+        re = np.ascontiguousarray(z.real, dtype=np.float64)
+        im = np.ascontiguousarray(z.imag, dtype=np.float64) if np.iscomplexobj(z) else None
+        out = np.zeros(self.n)
+        self._chk(lib().he_encode(self.ptr, _dptr(re), _dptr(im) if im is not None else None, len(re), float(scale),
+                                  _dptr(out)))
+        return out
+
+    def encrypt(self, z, scale, ctr, level=-1):
+        z = np.asarray(z)
+        re = np.ascontiguousarray(z.real, dtype=np.float64)
+        im = np.ascontiguousarray(z.imag, dtype=np.float64) if np.iscomplexobj(z) else None
+        return self._ct(lib().he_encrypt, _dptr(re), _dptr(im) if im is not None else None, len(re), float(scale),
+                        int(ctr), int(level))
+
+    def encrypt_poly(self, m, scale, ctr, level=-1):
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        return self._ct(lib().he_encrypt_poly, _dptr(m), float(scale), int(ctr), int(level))
+
+    def decrypt(self, ct, n_slots=None, complex_out=False):
+        n_slots = self.slots if n_slots is None else n_slots
+        re = np.zeros(n_slots)
+        im = np.zeros(n_slots) if complex_out else None
+        self._chk(lib().he_decrypt(self.ptr, ct.ptr, _dptr(re), _dptr(im) if im is not None else None, n_slots))
+        return re + 1j * im if complex_out else re
+
+    def decrypt_poly(self, ct):
+        out = np.zeros(self.n)
+        self._chk(lib().he_decrypt_poly(self.ptr, ct.ptr, _dptr(out)))
+        return out
+
+    def import_ct(self, arr, level, scale):
+        a = np.ascontiguousarray(arr, dtype=np.uint64).reshape(-1)
+        return self._ct(lib().he_ct_import, _u64ptr(a), int(level), float(scale))
+
+    # operations
+    def add(self, a, b):
+        return self._ct(lib().he_add, a.ptr, b.ptr)
+
+    def sub(self, a, b):
+        return self._ct(lib().he_sub, a.ptr, b.ptr)
+
+    def mul_int(self, a, k):
+        return self._ct(lib().he_mul_int, a.ptr, int(k))
+
+    def mul_const(self, a, c, target):
+        return self._ct(lib().he_mul_const, a.ptr, float(c), float(target))
+
+    def add_const(self, a, c):
+        return self._ct(lib().he_add_const, a.ptr, float(c))
+
+    def mul(self, a, b):
+        return self._ct(lib().he_mul, a.ptr, b.ptr)
+
+    def rescale(self, a):
+        return self._ct(lib().he_rescale, a.ptr)
+
+    def drop(self, a, level):
+        return self._ct(lib().he_drop, a.ptr, int(level))
+
+    def rotate(self, a, r):
+        return self._ct(lib().he_rotate, a.ptr, int(r))
+
+    def conj(self, a):
+        return self._ct(lib().he_conjugate, a.ptr)
+
+    def automorphism(self, a, g):
+        return self._ct(lib().he_automorphism, a.ptr, int(g))
+
+    def rotsum(self, a, steps):
+        return self._ct(lib().he_rotsum, a.ptr, int(steps))
+
+    def keyswitch(self, d, level, g):
+        d = np.ascontiguousarray(d, dtype=np.uint64).reshape(-1)
+        o0, o1 = np.zeros_like(d), np.zeros_like(d)
+        self._chk(lib().he_keyswitch_raw(self.ptr, _u64ptr(d), int(level), int(g), _u64ptr(o0), _u64ptr(o1)))
+        return o0.reshape(level + 1, self.n), o1.reshape(level + 1, self.n)
+
+    def ntt_device(self, tensor, prime_idx0, inverse=False):
+        """In-place (I)NTT of a CUDA uint64/int64 tensor of shape (limbs, N)."""
+        assert tensor.is_cuda and tensor.is_contiguous() and tensor.shape[-1] == self.n
+        limbs = tensor.numel() // self.n
+        self._chk(lib().he_ntt_device(self.ptr, C.c_void_p(tensor.data_ptr()), limbs, int(prime_idx0),
+                                      int(bool(inverse))))
+
+    # CutMax / nucleus
+    def cutmax_prepare(self, plan):
+        s, keep = plan_struct(plan)
+        self._chk(lib().he_cutmax_prepare(self.ptr, C.byref(s)))
+
+    def cutmax(self, ct, plan):
+        s, keep = plan_struct(plan)
+        return self._ct(lib().cutmax, ct.ptr, C.byref(s))
+
+    def nucleus_sample(self, ct, rand_ct, plan):
+        s, keep = plan_struct(plan)
+        return self._ct(lib().nucleus_sample, ct.ptr, rand_ct.ptr, C.byref(s))

@@ -1,0 +1,290 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Integer work (NTT, keys, encryption, key switching, rescale, rotations, the
+whole leveled circuit) must match bit for bit given the same integer
+plaintexts and seeds.  Float64 encoding may differ in the last bit of a
+coefficient before rounding, so encodings are compared within +-1.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import ckks as ock                     # noqa: E402
+from oracle import cutmax_fp64 as F                # noqa: E402
+from oracle import encoding as oenc                # noqa: E402
+from oracle.circuit import HE, cutmax_he, nucleus_he, required_rotations  # noqa: E402
+from paper_2509_08383_gb300 import build, he       # noqa: E402
+from paper_2509_08383_gb300 import plan as P       # noqa: E402
+from paper_2509_08383_gb300 import synth           # noqa: E402
+
+build.build_library()
+
+CFG1_Q = [60] + [40] * 21
+CFG1_P = [60, 60]
+
+
+def pair(log_n, qbits, pbits, dnum, h=0, seed=5):
+    g = he.Context(log_n, qbits, pbits, dnum, h=h, seed=seed)
+    o = ock.Context(log_n, qbits, pbits, dnum, h=h, seed=seed)
+    return g, o
+
+
+@pytest.fixture(scope="module")
+def small():
+    g, o = pair(11, CFG1_Q, CFG1_P, dnum=11)
+    for c in (g, o):
+        c.gen_relin_key()
+    return g, o
+
+
+# ------------------------------------------------------------------ NTT
+@pytest.mark.parametrize("log_n", [10, 11, 12, 13, 14, 15, 16])
+def test_ntt_bit_exact(log_n):
+    qbits = [60, 40, 61, 36]
+    g = he.Context(log_n, qbits, [60], dnum=2, arena_bytes=256 << 20)
+    primes = g.primes
+    rng = np.random.default_rng(log_n)
+    data = np.stack([rng.integers(0, q, 1 << log_n, dtype=np.uint64) for q in primes[:4]])
+    t = torch.from_numpy(data.view(np.int64)).cuda()
+    g.ntt_device(t, 0)
+    got = t.cpu().numpy().view(np.uint64)
+    for i in range(4):
+        assert (got[i] == ock.ntt(data[i], log_n, primes[i])).all()
+    g.ntt_device(t, 0, inverse=True)
+    assert (t.cpu().numpy().view(np.uint64) == data).all()
+    # edge values: all zeros and all q-1
+    for fill in ("zero", "max"):
+        d2 = np.stack([np.full(1 << log_n, 0 if fill == "zero" else q - 1, dtype=np.uint64) for q in primes[:4]])
+        t2 = torch.from_numpy(d2.view(np.int64).copy()).cuda()
+        g.ntt_device(t2, 0)
+        got2 = t2.cpu().numpy().view(np.uint64)
+        for i in range(4):
+            assert (got2[i] == ock.ntt(d2[i], log_n, primes[i])).all()
+
+
+# ------------------------------------------------------------------ context, keys, encryption
+def test_primes_secret_keys_match(small):
+    g, o = small
+    assert g.primes == o.primes
+    assert (g.secret() == o.secret()).all()
+    for digit in (0, o.beta - 1):
+        for which in (0, 1):
+            assert (g.key_export(0, digit, which) == o.key_export(0, digit, which)).all()
+    gr = ock.rot_galois(11, 5)
+    g.gen_galois_key(gr)
+    o.gen_galois_key(gr)
+    assert (g.key_export(gr, 3, 0) == o.key_export(gr, 3, 0)).all()
+
+
+def test_sparse_secret_matches():
+    g, o = pair(12, [60, 40, 40], [60], dnum=3, h=64, seed=9)
+    s = g.secret()
+    assert (s == o.secret()).all() and np.abs(s).sum() == 64
+
+
+def test_encrypt_decrypt_bit_exact(small):
+    g, o = small
+    rng = np.random.default_rng(1)
+    m = np.rint(rng.normal(size=g.n) * 2.0 ** 40)
+    for level in (-1, 0, 5):
+        cg = g.encrypt_poly(m, 2.0 ** 40, 77, level)
+        co = o.encrypt(m, 2.0 ** 40, 77, None if level < 0 else level)
+        assert (cg.export() == co.export()).all()
+        assert (g.decrypt_poly(cg) == o.decrypt(co)).all()
+
+
+def test_encode_within_one(small):
+    g, o = small
+    rng = np.random.default_rng(2)
+    z = rng.normal(size=g.slots) + 1j * rng.normal(size=g.slots)
+    mg = g.encode(z, 2.0 ** 40)
+    mo = oenc.encode(z, g.log_n, 2.0 ** 40)
+    assert np.abs(mg - mo).max() <= 1
+    assert (mg != mo).mean() < 0.05
+    ct = g.encrypt(z, 2.0 ** 40, 3)
+    assert np.abs(g.decrypt(ct, complex_out=True) - z).max() < 1e-6
+
+
+# ------------------------------------------------------------------ operations
+def _same_ct(g, o, rng, level=None, scale=2.0 ** 40, ctr=11):
+    m = np.rint(rng.normal(size=g.n) * scale)
+    return g.encrypt_poly(m, scale, ctr, -1 if level is None else level), o.encrypt(m, scale, ctr, level)
+
+
+def test_ops_bit_exact(small):
+    g, o = small
+    rng = np.random.default_rng(3)
+    a_g, a_o = _same_ct(g, o, rng, ctr=1)
+    b_g, b_o = _same_ct(g, o, rng, ctr=2)
+    eq = lambda x, y: (x.export() == y.export()).all() and x.level == y.level
+    assert eq(g.add(a_g, b_g), o.add(a_o, b_o))
+    assert eq(g.sub(a_g, b_g), o.sub(a_o, b_o))
+    assert eq(g.mul_int(a_g, -12345), o.mul_int(a_o, -12345))
+    assert eq(g.add_const(a_g, 0.75), o.add_intd(a_o, float(np.rint(0.75 * a_o.scale))))
+    prod_g, prod_o = g.mul(a_g, b_g), o.mul(a_o, b_o)
+    assert eq(prod_g, prod_o)
+    rs_g, rs_o = g.rescale(prod_g), o.rescale(prod_o)
+    assert eq(rs_g, rs_o) and rs_g.scale == rs_o.scale
+    # constant multiplication with the scale rule
+    c, target = -0.3125, 2.0 ** 40
+    E = (target * float(o.primes[a_o.level])) / a_o.scale
+    ref = o.rescale(o.mul_intd(a_o, float(np.rint(c * E)), a_o.scale * E))
+    got = g.mul_const(a_g, c, target)
+    assert eq(got, ref) and got.scale == ref.scale
+    # mixed levels: product at the lower level
+    low_g, low_o = g.drop(a_g, 7), o.drop(a_o, 7)
+    assert eq(g.mul(low_g, b_g), o.mul(low_o, o.drop(b_o, 7)))
+
+
+@pytest.mark.parametrize("r", [1, 2, 64, 511, -3])
+def test_rotation_bit_exact(small, r):
+    g, o = small
+    rng = np.random.default_rng(4)
+    a_g, a_o = _same_ct(g, o, rng, ctr=5)
+    g.gen_rot_keys([r])
+    o.gen_rot_key(r)
+    assert (g.rotate(a_g, r).export() == o.rotate(a_o, r).export()).all()
+
+
+def test_conjugation_and_low_level_rotation(small):
+    g, o = small
+    rng = np.random.default_rng(5)
+    a_g, a_o = _same_ct(g, o, rng, level=3, ctr=6)
+    cj = 2 * g.n - 1
+    g.gen_galois_key(cj)
+    o.gen_galois_key(cj)
+    assert (g.conj(a_g).export() == o.conj(a_o).export()).all()
+    g.gen_rot_keys([1])
+    o.gen_rot_key(1)
+    a0_g, a0_o = _same_ct(g, o, rng, level=0, ctr=7)
+    assert (g.rotate(a0_g, 1).export() == o.rotate(a0_o, 1).export()).all()
+
+
+@pytest.mark.parametrize("level", [0, 1, 9, 21])
+def test_keyswitch_raw_bit_exact(small, level):
+    g, o = small
+    rng = np.random.default_rng(level)
+    d = np.stack([rng.integers(0, q, g.n, dtype=np.uint64) for q in g.primes[: level + 1]])
+    og = g.keyswitch(d, level, 0)
+    oo = o.keyswitch(d, level, 0)
+    assert (og[0] == oo[0]).all() and (og[1] == oo[1]).all()
+
+
+def test_rescale_chain_to_zero(small):
+    g, o = small
+    rng = np.random.default_rng(6)
+    a_g, a_o = _same_ct(g, o, rng, ctr=8)
+    for _ in range(a_g.level):
+        a_g, a_o = g.rescale(a_g), o.rescale(a_o)
+        assert (a_g.export() == a_o.export()).all()
+    assert a_g.level == 0
+    with pytest.raises(he.HeError) as ei:
+        g.rescale(a_g)
+    assert ei.value.code == he.HE_ELEVEL
+
+
+def test_missing_key_is_an_error(small):
+    g, _ = small
+    rng = np.random.default_rng(7)
+    a = g.encrypt_poly(np.rint(rng.normal(size=g.n) * 2 ** 30), 2.0 ** 30, 9)
+    with pytest.raises(he.HeError) as ei:
+        g.automorphism(a, 2 * 777 + 1)
+    assert ei.value.code == he.HE_ENOKEY
+
+
+# ------------------------------------------------------------------ CutMax circuit
+def _cfg1_plan(slots, n=1024):
+    return P.calibrate(lambda i: synth.logits_gaussian(1000 + i, n=n), 60, n, slots, 2, 3, 5.0, k_fixed=2, d_fixed=2)
+
+
+def _circuit_pair(log_n, seed=3):
+    g, o = pair(log_n, CFG1_Q, CFG1_P, dnum=11, seed=seed)
+    return g, o
+
+
+def _run_cutmax_pair(g, o, pl, x, ctr=1):
+    delta = 2.0 ** 40
+    pt = oenc.encode(P.pack(x, g.slots, pl.packing), g.log_n, delta)
+    g.cutmax_prepare(pl)
+    o.gen_relin_key()
+    for r in required_rotations(pl):
+        o.gen_rot_key(r)
+    zg = g.cutmax(g.encrypt_poly(pt, delta, ctr), pl)
+    zo = cutmax_he(HE(o, delta), o.encrypt(pt, delta, ctr), pl)
+    return zg, zo
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_cutmax_bit_exact_small(seed):
+    """Whole leveled CutMax (Alg. 2), N = 2^11, 21 levels: bit-exact ciphertexts."""
+    g, o = _circuit_pair(11)
+    pl = _cfg1_plan(g.slots)
+    x = synth.logits_gaussian(seed)
+    zg, zo = _run_cutmax_pair(g, o, pl, x)
+    assert zg.level == zo.level == 0 and zg.scale == zo.scale
+    assert (zg.export() == zo.export()).all()
+    dec = g.decrypt(zg, pl.n)
+    assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-3
+    assert np.argmax(dec) == np.argmax(x)
+
+
+def test_cutmax_cfg1_full_size():
+    """Config 1: N = 2^14, 1024 logits replicated 8x, T = 2, p = 3: bit-exact."""
+    g, o = _circuit_pair(14)
+    pl = _cfg1_plan(g.slots)
+    x = synth.logits_gaussian(11)
+    zg, zo = _run_cutmax_pair(g, o, pl, x)
+    assert (zg.export() == zo.export()).all()
+    dec = g.decrypt(zg, pl.n)
+    assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-3
+    assert np.abs(dec - F.cutmax_exact(x, 2, 3, 5.0)).max() < 1e-3
+    assert np.argmax(dec) == np.argmax(x)
+
+
+def test_cutmax_padded_packing():
+    """n = 1000 real logits zero-padded into 1024 slots (mask + variance correction)."""
+    g = he.Context(11, CFG1_Q, CFG1_P, dnum=11, seed=4)
+    pl = _cfg1_plan(g.slots, n=1000)
+    assert pl.packing == "pad"
+    x = synth.logits_gaussian(2, n=1000)
+    g.cutmax_prepare(pl)
+    z = g.cutmax(g.encrypt(P.pack(x, g.slots, pl.packing), g.delta, 1), pl)
+    dec = g.decrypt(z)
+    assert np.abs(dec[:1000] - F.cutmax_circuit(x, pl)).max() < 1e-3
+    assert np.abs(dec[1000:]).max() < 1e-3
+    assert np.argmax(dec[:1000]) == np.argmax(x)
+
+
+def test_nucleus_bit_exact():
+    """Alg. 3 with client-encrypted Beta(alpha,1) cut noise: bit-exact to the oracle."""
+    g, o = _circuit_pair(11, seed=8)
+    pl = _cfg1_plan(g.slots)
+    x = synth.logits_gaussian(3)
+    alpha = F.beta_alpha(0.9)
+    G = F.beta_noise(synth.uniforms(3, pl.n), alpha)
+    delta = 2.0 ** 40
+    ptx = oenc.encode(P.pack(x, g.slots, pl.packing), g.log_n, delta)
+    ptg = oenc.encode(P.pack(G, g.slots, pl.packing), g.log_n, delta)
+    g.cutmax_prepare(pl)
+    o.gen_relin_key()
+    for r in required_rotations(pl):
+        o.gen_rot_key(r)
+    zg = g.nucleus_sample(g.encrypt_poly(ptx, delta, 1), g.encrypt_poly(ptg, delta, 2), pl)
+    zo = nucleus_he(HE(o, delta), o.encrypt(ptx, delta, 1), o.encrypt(ptg, delta, 2), pl)
+    assert (zg.export() == zo.export()).all()
+    assert np.argmax(g.decrypt(zg, pl.n)) == np.argmax(x + G)
+
+
+def test_circuit_too_deep_is_an_error():
+    g = he.Context(11, [60] + [40] * 8, CFG1_P, dnum=3, seed=1)
+    pl = _cfg1_plan(g.slots)
+    g.cutmax_prepare(pl)
+    ct = g.encrypt(np.zeros(g.slots), g.delta, 1)
+    with pytest.raises(he.HeError) as ei:
+        g.cutmax(ct, pl)
+    assert ei.value.code == he.HE_ELEVEL
