@@ -25,6 +25,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "encrypted CutMax decodes/sec (vocab 32k, N=2^16), 1 GB300"
+PROF_NAMES = {0: "ntt_forward (k_ntt_cols+k_ntt_rows)", 1: "ntt_inverse (k_ntt_rows+k_ntt_cols)",
+              2: "keyswitch_inner (k_keyswitch_inner)", 3: "bconv (k_bconv)"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def workload(name):
@@ -134,7 +145,7 @@ def run_reference(args):
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     T = sum(times)
-    cores = len(os.sched_getaffinity(0))
+    cores = ock.get_threads()
     val = args.steps / T
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "decodes/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
@@ -163,7 +174,7 @@ def cpu_baseline(args, desc):
     t0 = time.perf_counter()
     cutmax_he(HE(o, delta), ct, pl)
     dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "decodes/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+    return {"value": 1.0 / dt, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
             "sample": "1 full CutMax decode of the bench workload on the oracle (device-resident equivalent: "
                       "ciphertext already encrypted)"}
 
@@ -196,6 +207,16 @@ def main():
     cts = [g.encrypt(P.pack(gen(10000 * rank + s), slots, pl.packing), g.delta, s) for s in range(nsteps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    # dominant kernel class: one instrumented CutMax per class (untimed)
+    share = {}
+    for cls in PROF_NAMES:
+        he.profile_enable(cls)
+        z = g.cutmax(cts[0], pl)
+        torch.cuda.synchronize()
+        share[cls] = he.profile_read(cls)[1]
+        del z
+    dom = max(share, key=share.get)
+    he.profile_enable(dom)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -209,6 +230,7 @@ def main():
             if s == args.warmup - 1:
                 torch.cuda.synchronize()
                 l0 = he.launch_count()
+                he.profile_enable(dom)
             del z
         torch.cuda.synchronize()
     launches = he.launch_count() - l0
@@ -218,6 +240,16 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
+    n_dom, ms_dom, bytes_dom = he.profile_read(dom)
+    he.profile_enable(-1)
+    peak, peak_kind = measured_peaks()
+    achieved = (bytes_dom / n_dom) / (ms_dom / n_dom * 1e-3) / 1e9 if n_dom else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": PROF_NAMES[dom], "launches": n_dom,
+                "avg_launch_us": 1000.0 * ms_dom / max(n_dom, 1),
+                "algorithmic_bytes_per_launch": bytes_dom / max(n_dom, 1),
+                "share_of_step": (ms_dom / args.steps) / ms if ms else None, "peak_source": peak_kind,
+                "class_ms_per_step": {PROF_NAMES[c]: v for c, v in share.items()}}
     value = ws * 1000.0 / ms
 
     # end to end through the C ABI: pinned host logits -> host outputs
@@ -247,7 +279,7 @@ def main():
            "clocks": clk.summary(),
            "e2e": {"value": e2e, "unit": "decodes/s", "h2d_bytes_per_step": slots * 8,
                    "d2h_bytes_per_step": pl.n * 8},
-           "gpu_launches": int(launches), "roofline": None}
+           "gpu_launches": int(launches), "roofline": roofline}
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
             res["cpu_baseline"] = cpu_baseline(args, desc)

@@ -87,6 +87,16 @@ const char *he_last_error(const he_ctx *ctx);
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all contexts); used to count launches inside a timed region. */
 uint64_t he_launch_count(void);
+/* Time one kernel class with CUDA events around each of its launches (on
+ * the launch stream): 0 forward NTT, 1 inverse NTT, 2 key-switch inner
+ * product, 3 basis conversion; -1 turns timing off.  Enabling resets the
+ * counters.  he_profile_read synchronises the recorded events and returns
+ * the launch count, the summed device time (ms) and the summed algorithmic
+ * bytes of those launches (NTT: 16 bytes per coefficient per limb; inner
+ * product: (3*beta + 2) words per coefficient per row; conversion: one
+ * word per input and output coefficient). */
+int he_profile_enable(int32_t kernel_class);
+int he_profile_read(int32_t kernel_class, uint64_t *launches, double *ms, double *bytes);
 
 /* ---- keys (Sect. 2.1 rotations; hybrid key switching) ---------------- */
 int he_keygen_relin(he_ctx *ctx);

@@ -20,6 +20,8 @@ def lib():
         pdbl = P(np.float64, flags="C")
         sig = {
             "or_powmod": (u64, [u64, u64, u64]),
+            "or_set_threads": (ip, [ip]),
+            "or_get_threads": (ip, []),
             "or_invmod": (u64, [u64, u64]),
             "or_is_prime": (ip, [u64]),
             "or_gen_primes": (ip, [ip, P(np.int32, flags="C"), ip, pu64]),
@@ -73,6 +75,15 @@ def lib():
 
 
 # ----------------------------------------------------------------- helpers
+def set_threads(n):
+    """Threads for the per-limb loops (0 = all cores of this process's affinity)."""
+    return lib().or_set_threads(int(n))
+
+
+def get_threads():
+    return lib().or_get_threads()
+
+
 def gen_primes(log_n, bits):
     b = np.asarray(bits, dtype=np.int32)
     out = np.zeros(len(b), dtype=np.uint64)

@@ -20,15 +20,60 @@
  * The paper (arXiv 2509.08383) assumes an abstract CKKS API with Enc, Dec,
  * add, mult and rotate (Sect. 2.1 "HE Preliminaries"); this file is that API.
  */
+#define _GNU_SOURCE
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
+#include <sched.h>
 
 typedef uint64_t u64;
 typedef int64_t i64;
 typedef uint32_t u32;
 typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------ */
+/* parallel loop over independent limbs (pthreads; the arithmetic of  */
+/* each iteration does not depend on the thread count)               */
+/* ------------------------------------------------------------------ */
+typedef void (*pf_body)(void *arg, int i);
+typedef struct { pf_body fn; void *arg; int n, next; pthread_mutex_t mu; } pf_state;
+static int g_threads = 0;
+
+int or_set_threads(int n) { g_threads = n; return n; }
+int or_get_threads(void) {
+    if (g_threads > 0) return g_threads;
+    const char *e = getenv("OR_THREADS");
+    if (e && atoi(e) > 0) return atoi(e);
+    cpu_set_t cs;
+    if (sched_getaffinity(0, sizeof(cs), &cs) == 0) return CPU_COUNT(&cs);
+    return 1;
+}
+static void *pf_worker(void *p) {
+    pf_state *s = (pf_state *)p;
+    for (;;) {
+        pthread_mutex_lock(&s->mu);
+        int i = s->next++;
+        pthread_mutex_unlock(&s->mu);
+        if (i >= s->n) break;
+        s->fn(s->arg, i);
+    }
+    return NULL;
+}
+static void parallel_for(int n, pf_body fn, void *arg) {
+    int T = or_get_threads();
+    if (T > n) T = n;
+    if (T > 64) T = 64;
+    if (T <= 1) { for (int i = 0; i < n; i++) fn(arg, i); return; }
+    pf_state s; s.fn = fn; s.arg = arg; s.n = n; s.next = 0;
+    pthread_mutex_init(&s.mu, NULL);
+    pthread_t th[64];
+    for (int t = 1; t < T; t++) pthread_create(&th[t], NULL, pf_worker, &s);
+    pf_worker(&s);
+    for (int t = 1; t < T; t++) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&s.mu);
+}
 
 /* ------------------------------------------------------------------ */
 /* modular arithmetic by definition                                    */
@@ -316,6 +361,26 @@ static u64 dmod(double x, u64 q) {
     return mulmod(r, or_powmod(2, (u64)e, q), q);
 }
 
+typedef struct { or_ctx *cx; or_key *k; int j; u32 obj; const i64 *e; const u64 *sp; } bk_args;
+static void bk_body(void *vp, int i) {
+    bk_args *A = (bk_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n; int j = A->j;
+    u64 q = cx->primes[i];
+    u64 *a = A->k->a[j] + (u64)i * n, *b = A->k->b[j] + (u64)i * n;
+    for (u64 c = 0; c < n; c++) a[c] = uniform_mod(cx->seed, (u32)c, (u32)i, A->obj, DOM_KEY_A, q);
+    for (u64 c = 0; c < n; c++) b[c] = smod(A->e[c], q);
+    poly_ntt(cx, b, i);
+    u64 pmod = 1;
+    for (int p = 0; p < cx->np; p++) pmod = mulmod(pmod, cx->primes[cx->nq + p] % q, q);
+    int in_digit = (i < cx->nq) && (i / cx->alpha == j);
+    const u64 *s = cx->sk_ntt + (u64)i * n, *s2 = A->sp + (u64)i * n;
+    for (u64 c = 0; c < n; c++) {
+        u64 v = submod(b[c], mulmod(a[c], s[c], q), q);
+        if (in_digit) v = addmod(v, mulmod(pmod, s2[c], q), q);
+        b[c] = v;
+    }
+}
+
 static void build_key(or_ctx *cx, or_key *k, const u64 *s_prime_ntt /*[(nq+np)*N]*/, u32 key_id) {
     u64 n = cx->n; int tot = cx->nq + cx->np;
     u64 cdt[GAUSS_BOUND]; or_gauss_cdt(cx->sigma, cdt);
@@ -325,25 +390,21 @@ static void build_key(or_ctx *cx, or_key *k, const u64 *s_prime_ntt /*[(nq+np)*N
         k->b[j] = malloc(tot * n * 8); k->a[j] = malloc(tot * n * 8);
         i64 *e = malloc(n * 8);
         for (u64 c = 0; c < n; c++) e[c] = gauss_sample(cx->seed, (u32)c, obj, DOM_KEY_E, cdt);
-        #pragma omp parallel for schedule(dynamic)
-        for (int i = 0; i < tot; i++) {
-            u64 q = cx->primes[i];
-            u64 *a = k->a[j] + (u64)i * n, *b = k->b[j] + (u64)i * n;
-            for (u64 c = 0; c < n; c++) a[c] = uniform_mod(cx->seed, (u32)c, (u32)i, obj, DOM_KEY_A, q);
-            for (u64 c = 0; c < n; c++) b[c] = smod(e[c], q);
-            poly_ntt(cx, b, i);
-            u64 pmod = 1;
-            for (int p = 0; p < cx->np; p++) pmod = mulmod(pmod, cx->primes[cx->nq + p] % q, q);
-            int in_digit = (i < cx->nq) && (i / cx->alpha == j);
-            const u64 *s = cx->sk_ntt + (u64)i * n, *s2 = s_prime_ntt + (u64)i * n;
-            for (u64 c = 0; c < n; c++) {
-                u64 v = submod(b[c], mulmod(a[c], s[c], q), q);
-                if (in_digit) v = addmod(v, mulmod(pmod, s2[c], q), q);
-                b[c] = v;
-            }
-        }
+        bk_args A = {cx, k, j, obj, e, s_prime_ntt};
+        parallel_for(tot, bk_body, &A);
         free(e);
     }
+}
+
+static void tab_body(void *vp, int i) {
+    or_ctx *cx = (or_ctx *)vp;
+    tab_init(&cx->tab[i], cx->primes[i], cx->log_n);
+}
+static void sk_body(void *vp, int i) {
+    or_ctx *cx = (or_ctx *)vp;
+    u64 *p = cx->sk_ntt + (u64)i * cx->n;
+    for (u64 c = 0; c < cx->n; c++) p[c] = smod(cx->sk[c], cx->primes[i]);
+    poly_ntt(cx, p, i);
 }
 
 or_ctx *or_ctx_create(int log_n, int nq, int np, const int *qbits, const int *pbits,
@@ -360,17 +421,11 @@ or_ctx *or_ctx_create(int log_n, int nq, int np, const int *qbits, const int *pb
     if (or_gen_primes(log_n, bits, tot, cx->primes) != 0) { free(bits); free(cx->primes); free(cx); return NULL; }
     free(bits);
     cx->tab = malloc(sizeof(prime_tab) * tot);
-    #pragma omp parallel for
-    for (int i = 0; i < tot; i++) tab_init(&cx->tab[i], cx->primes[i], log_n);
+    parallel_for(tot, tab_body, cx);
     cx->sk = malloc(cx->n);
     or_sample_secret(seed, log_n, h, cx->sk);
     cx->sk_ntt = malloc(tot * cx->n * 8);
-    #pragma omp parallel for
-    for (int i = 0; i < tot; i++) {
-        u64 *p = cx->sk_ntt + (u64)i * cx->n;
-        for (u64 c = 0; c < cx->n; c++) p[c] = smod(cx->sk[c], cx->primes[i]);
-        poly_ntt(cx, p, i);
-    }
+    parallel_for(tot, sk_body, cx);
     return cx;
 }
 
@@ -476,24 +531,28 @@ or_ct *or_ct_import(or_ctx *cx, const u64 *in, int level, double scale) {
 /* Secret-key encryption of an integer plaintext polynomial (coefficients
  * given as integer-valued doubles): c1 = a, c0 = -a*s + e + m, at `level`.
  * a is uniform in the NTT domain; e is the rounded Gaussian. */
+typedef struct { or_ctx *cx; or_ct *ct; u32 ctr; const i64 *e; const double *m; } enc_args;
+static void enc_body(void *vp, int i) {
+    enc_args *A = (enc_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n, q = cx->primes[i];
+    u64 *c0 = A->ct->c[0] + (u64)i * n, *c1 = A->ct->c[1] + (u64)i * n;
+    for (u64 c = 0; c < n; c++) c1[c] = uniform_mod(cx->seed, (u32)c, (u32)i, A->ctr, DOM_UNIFORM, q);
+    for (u64 c = 0; c < n; c++) c0[c] = addmod(smod(A->e[c], q), dmod(A->m[c], q), q);
+    poly_ntt(cx, c0, i);
+    const u64 *s = cx->sk_ntt + (u64)i * n;
+    for (u64 c = 0; c < n; c++) c0[c] = submod(c0[c], mulmod(c1[c], s[c], q), q);
+    poly_intt(cx, c0, i);
+    poly_intt(cx, c1, i);
+}
+
 or_ct *or_encrypt(or_ctx *cx, const double *m, double scale, u32 ctr, int level) {
     u64 n = cx->n;
     or_ct *ct = or_ct_new(cx, level, scale);
     u64 cdt[GAUSS_BOUND]; or_gauss_cdt(cx->sigma, cdt);
     i64 *e = malloc(n * 8);
     for (u64 c = 0; c < n; c++) e[c] = gauss_sample(cx->seed, (u32)c, ctr, DOM_ERROR, cdt);
-    #pragma omp parallel for schedule(dynamic)
-    for (int i = 0; i <= level; i++) {
-        u64 q = cx->primes[i];
-        u64 *c0 = ct->c[0] + (u64)i * n, *c1 = ct->c[1] + (u64)i * n;
-        for (u64 c = 0; c < n; c++) c1[c] = uniform_mod(cx->seed, (u32)c, (u32)i, ctr, DOM_UNIFORM, q);
-        for (u64 c = 0; c < n; c++) c0[c] = addmod(smod(e[c], q), dmod(m[c], q), q);
-        poly_ntt(cx, c0, i);
-        const u64 *s = cx->sk_ntt + (u64)i * n;
-        for (u64 c = 0; c < n; c++) c0[c] = submod(c0[c], mulmod(c1[c], s[c], q), q);
-        poly_intt(cx, c0, i);
-        poly_intt(cx, c1, i);
-    }
+    enc_args A = {cx, ct, ctr, e, m};
+    parallel_for(level + 1, enc_body, &A);
     free(e);
     return ct;
 }
@@ -597,25 +656,106 @@ or_ct *or_add_plain(or_ctx *cx, const or_ct *a, const double *pt) {
 }
 
 /* multiply by an integer plaintext polynomial; scale becomes scale_out */
-or_ct *or_mul_plain(or_ctx *cx, const or_ct *a, const double *pt, double scale_out) {
-    u64 n = cx->n;
-    or_ct *r = or_ct_new(cx, a->level, scale_out);
-    #pragma omp parallel for schedule(dynamic)
-    for (int i = 0; i <= a->level; i++) {
-        u64 q = cx->primes[i];
-        u64 *p = malloc(n * 8), *t = malloc(n * 8);
-        for (u64 c = 0; c < n; c++) p[c] = dmod(pt[c], q);
-        poly_ntt(cx, p, i);
-        for (int j = 0; j < 2; j++) {
-            memcpy(t, a->c[j] + (u64)i * n, n * 8);
-            poly_ntt(cx, t, i);
-            for (u64 c = 0; c < n; c++) t[c] = mulmod(t[c], p[c], q);
-            poly_intt(cx, t, i);
-            memcpy(r->c[j] + (u64)i * n, t, n * 8);
-        }
-        free(p); free(t);
+typedef struct { or_ctx *cx; const or_ct *a; or_ct *r; const double *pt; } mp_args;
+static void mp_body(void *vp, int i) {
+    mp_args *A = (mp_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n, q = cx->primes[i];
+    u64 *p = malloc(n * 8), *t = malloc(n * 8);
+    for (u64 c = 0; c < n; c++) p[c] = dmod(A->pt[c], q);
+    poly_ntt(cx, p, i);
+    for (int j = 0; j < 2; j++) {
+        memcpy(t, A->a->c[j] + (u64)i * n, n * 8);
+        poly_ntt(cx, t, i);
+        for (u64 c = 0; c < n; c++) t[c] = mulmod(t[c], p[c], q);
+        poly_intt(cx, t, i);
+        memcpy(A->r->c[j] + (u64)i * n, t, n * 8);
     }
+    free(p); free(t);
+}
+
+or_ct *or_mul_plain(or_ctx *cx, const or_ct *a, const double *pt, double scale_out) {
+    or_ct *r = or_ct_new(cx, a->level, scale_out);
+    mp_args A = {cx, a, r, pt};
+    parallel_for(a->level + 1, mp_body, &A);
     return r;
+}
+
+/* Hybrid key switching of the coefficient-form polynomial d at level l.
+ * ModUp per digit by the approximate basis conversion
+ *   [x]_t = sum_{i in D_j} [x_i * (Qhat_i)^-1]_{q_i} * Qhat_i  mod t,
+ * inner product with the key over Q_l u P, then ModDown
+ *   out_i = (acc_i - [acc_P]_{q_i}) * P^-1 mod q_i
+ * with the same conversion from P to q_i. */
+typedef struct {
+    or_ctx *cx; const u64 *d; const or_key *key; int j, lo, hi, cnt; const u64 *qhinv; const int *pidx;
+    u64 *acc0, *acc1;
+} mu_args;
+static void mu_body(void *vp, int t) {
+    mu_args *A = (mu_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n;
+    int pt = A->pidx[t], lo = A->lo, hi = A->hi, cnt = A->cnt;
+    u64 qt = cx->primes[pt];
+    u64 *e = malloc(n * 8);
+    if (pt >= lo && pt < hi) {
+        memcpy(e, A->d + (u64)pt * n, n * 8);
+    } else {
+        u64 *qh = malloc(8 * cnt);
+        for (int a = 0; a < cnt; a++) {
+            u64 v = 1;
+            for (int b = 0; b < cnt; b++) if (b != a) v = mulmod(v, cx->primes[lo + b] % qt, qt);
+            qh[a] = v;
+        }
+        for (u64 c = 0; c < n; c++) {
+            u64 s = 0;
+            for (int a = 0; a < cnt; a++) {
+                u64 qa = cx->primes[lo + a];
+                u64 y = mulmod(A->d[(u64)(lo + a) * n + c], A->qhinv[a], qa);
+                s = addmod(s, mulmod(y % qt, qh[a], qt), qt);
+            }
+            e[c] = s;
+        }
+        free(qh);
+    }
+    poly_ntt(cx, e, pt);
+    const u64 *kb = A->key->b[A->j] + (u64)pt * n, *ka = A->key->a[A->j] + (u64)pt * n;
+    u64 *a0 = A->acc0 + (u64)t * n, *a1 = A->acc1 + (u64)t * n;
+    for (u64 c = 0; c < n; c++) {
+        a0[c] = addmod(a0[c], mulmod(e[c], kb[c], qt), qt);
+        a1[c] = addmod(a1[c], mulmod(e[c], ka[c], qt), qt);
+    }
+    free(e);
+}
+typedef struct { or_ctx *cx; u64 *acc0, *acc1; int ext; const int *pidx; } it_args;
+static void it_body(void *vp, int t) {
+    it_args *A = (it_args *)vp;
+    u64 *p = (t < A->ext ? A->acc0 + (u64)t * A->cx->n : A->acc1 + (u64)(t - A->ext) * A->cx->n);
+    poly_intt(A->cx, p, A->pidx[t % A->ext]);
+}
+typedef struct { or_ctx *cx; const u64 *acc0, *acc1; u64 *out0, *out1; int l, K; const u64 *phinv; } md_args;
+static void md_body(void *vp, int i) {
+    md_args *A = (md_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K, l = A->l;
+    u64 qi = cx->primes[i], pinv = 1, *ph = malloc(8 * K);
+    for (int a = 0; a < K; a++) pinv = mulmod(pinv, cx->primes[cx->nq + a] % qi, qi);
+    pinv = or_invmod(pinv, qi);
+    for (int a = 0; a < K; a++) {
+        u64 v = 1;
+        for (int b = 0; b < K; b++) if (b != a) v = mulmod(v, cx->primes[cx->nq + b] % qi, qi);
+        ph[a] = v;
+    }
+    for (int w = 0; w < 2; w++) {
+        const u64 *acc = w ? A->acc1 : A->acc0; u64 *out = w ? A->out1 : A->out0;
+        for (u64 c = 0; c < n; c++) {
+            u64 s = 0;
+            for (int a = 0; a < K; a++) {
+                u64 pa = cx->primes[cx->nq + a];
+                u64 y = mulmod(acc[(u64)(l + 1 + a) * n + c], A->phinv[a], pa);
+                s = addmod(s, mulmod(y % qi, ph[a], qi), qi);
+            }
+            out[(u64)i * n + c] = mulmod(submod(acc[(u64)i * n + c], s, qi), pinv, qi);
+        }
+    }
+    free(ph);
 }
 
 /* Hybrid key switching of the coefficient-form polynomial d at level l.
@@ -627,7 +767,6 @@ or_ct *or_mul_plain(or_ctx *cx, const or_ct *a, const double *pt, double scale_o
 static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *out0, u64 *out1) {
     u64 n = cx->n; int K = cx->np, ext = l + 1 + K;
     int beta = (l + 1 + cx->alpha - 1) / cx->alpha;
-    /* prime index of extended limb t */
     int *pidx = malloc(sizeof(int) * ext);
     for (int t = 0; t <= l; t++) pidx[t] = t;
     for (int t = 0; t < K; t++) pidx[l + 1 + t] = cx->nq + t;
@@ -635,84 +774,26 @@ static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *o
     for (int j = 0; j < beta; j++) {
         int lo = j * cx->alpha, hi = lo + cx->alpha; if (hi > l + 1) hi = l + 1;
         int cnt = hi - lo;
-        /* Qhat_i^-1 mod q_i for i in digit */
         u64 *qhinv = malloc(8 * cnt);
         for (int a = 0; a < cnt; a++) {
             u64 q = cx->primes[lo + a], v = 1;
             for (int b = 0; b < cnt; b++) if (b != a) v = mulmod(v, cx->primes[lo + b] % q, q);
             qhinv[a] = or_invmod(v, q);
         }
-        #pragma omp parallel for schedule(dynamic)
-        for (int t = 0; t < ext; t++) {
-            int pt = pidx[t]; u64 qt = cx->primes[pt];
-            u64 *e = malloc(n * 8);
-            if (pt >= lo && pt < hi) {
-                memcpy(e, d + (u64)pt * n, n * 8);
-            } else {
-                u64 *qh = malloc(8 * cnt);
-                for (int a = 0; a < cnt; a++) {
-                    u64 v = 1;
-                    for (int b = 0; b < cnt; b++) if (b != a) v = mulmod(v, cx->primes[lo + b] % qt, qt);
-                    qh[a] = v;
-                }
-                for (u64 c = 0; c < n; c++) {
-                    u64 s = 0;
-                    for (int a = 0; a < cnt; a++) {
-                        u64 qa = cx->primes[lo + a];
-                        u64 y = mulmod(d[(u64)(lo + a) * n + c], qhinv[a], qa);
-                        s = addmod(s, mulmod(y % qt, qh[a], qt), qt);
-                    }
-                    e[c] = s;
-                }
-                free(qh);
-            }
-            poly_ntt(cx, e, pt);
-            const u64 *kb = key->b[j] + (u64)pt * n, *ka = key->a[j] + (u64)pt * n;
-            u64 *a0 = acc0 + (u64)t * n, *a1 = acc1 + (u64)t * n;
-            for (u64 c = 0; c < n; c++) {
-                a0[c] = addmod(a0[c], mulmod(e[c], kb[c], qt), qt);
-                a1[c] = addmod(a1[c], mulmod(e[c], ka[c], qt), qt);
-            }
-            free(e);
-        }
+        mu_args A = {cx, d, key, j, lo, hi, cnt, qhinv, pidx, acc0, acc1};
+        parallel_for(ext, mu_body, &A);
         free(qhinv);
     }
-    #pragma omp parallel for schedule(dynamic)
-    for (int t = 0; t < 2 * ext; t++) {
-        u64 *p = (t < ext ? acc0 + (u64)t * n : acc1 + (u64)(t - ext) * n);
-        poly_intt(cx, p, pidx[t % ext]);
-    }
-    /* ModDown */
+    it_args B = {cx, acc0, acc1, ext, pidx};
+    parallel_for(2 * ext, it_body, &B);
     u64 *phinv = malloc(8 * K);
     for (int a = 0; a < K; a++) {
         u64 q = cx->primes[cx->nq + a], v = 1;
         for (int b = 0; b < K; b++) if (b != a) v = mulmod(v, cx->primes[cx->nq + b] % q, q);
         phinv[a] = or_invmod(v, q);
     }
-    #pragma omp parallel for schedule(dynamic)
-    for (int i = 0; i <= l; i++) {
-        u64 qi = cx->primes[i], pinv = 1, *ph = malloc(8 * K);
-        for (int a = 0; a < K; a++) pinv = mulmod(pinv, cx->primes[cx->nq + a] % qi, qi);
-        pinv = or_invmod(pinv, qi);
-        for (int a = 0; a < K; a++) {
-            u64 v = 1;
-            for (int b = 0; b < K; b++) if (b != a) v = mulmod(v, cx->primes[cx->nq + b] % qi, qi);
-            ph[a] = v;
-        }
-        for (int w = 0; w < 2; w++) {
-            const u64 *acc = w ? acc1 : acc0; u64 *out = w ? out1 : out0;
-            for (u64 c = 0; c < n; c++) {
-                u64 s = 0;
-                for (int a = 0; a < K; a++) {
-                    u64 pa = cx->primes[cx->nq + a];
-                    u64 y = mulmod(acc[(u64)(l + 1 + a) * n + c], phinv[a], pa);
-                    s = addmod(s, mulmod(y % qi, ph[a], qi), qi);
-                }
-                out[(u64)i * n + c] = mulmod(submod(acc[(u64)i * n + c], s, qi), pinv, qi);
-            }
-        }
-        free(ph);
-    }
+    md_args M = {cx, acc0, acc1, out0, out1, l, K, phinv};
+    parallel_for(l + 1, md_body, &M);
     free(phinv); free(acc0); free(acc1); free(pidx);
 }
 
@@ -724,6 +805,24 @@ int or_keyswitch(or_ctx *cx, const u64 *d, int l, u64 g, u64 *out0, u64 *out1) {
     return 0;
 }
 
+typedef struct { or_ctx *cx; const or_ct *a, *b; or_ct *r; u64 *d2; } tp_args;
+static void tp_body(void *vp, int i) {
+    tp_args *A = (tp_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n, q = cx->primes[i];
+    u64 *a0 = malloc(n * 8), *a1 = malloc(n * 8), *b0 = malloc(n * 8), *b1 = malloc(n * 8);
+    memcpy(a0, A->a->c[0] + (u64)i * n, n * 8); memcpy(a1, A->a->c[1] + (u64)i * n, n * 8);
+    memcpy(b0, A->b->c[0] + (u64)i * n, n * 8); memcpy(b1, A->b->c[1] + (u64)i * n, n * 8);
+    poly_ntt(cx, a0, i); poly_ntt(cx, a1, i); poly_ntt(cx, b0, i); poly_ntt(cx, b1, i);
+    u64 *d0 = A->r->c[0] + (u64)i * n, *d1 = A->r->c[1] + (u64)i * n, *e2 = A->d2 + (u64)i * n;
+    for (u64 c = 0; c < n; c++) {
+        d0[c] = mulmod(a0[c], b0[c], q);
+        d1[c] = addmod(mulmod(a0[c], b1[c], q), mulmod(a1[c], b0[c], q), q);
+        e2[c] = mulmod(a1[c], b1[c], q);
+    }
+    poly_intt(cx, d0, i); poly_intt(cx, d1, i); poly_intt(cx, e2, i);
+    free(a0); free(a1); free(b0); free(b1);
+}
+
 /* tensor product + relinearisation (no rescale); scale = a.scale * b.scale */
 or_ct *or_mul(or_ctx *cx, const or_ct *a, const or_ct *b) {
     or_key *rk = find_key(cx, 0);
@@ -732,22 +831,8 @@ or_ct *or_mul(or_ctx *cx, const or_ct *a, const or_ct *b) {
     u64 n = cx->n;
     or_ct *r = or_ct_new(cx, l, a->scale * b->scale);
     u64 *d2 = malloc((l + 1) * n * 8);
-    #pragma omp parallel for schedule(dynamic)
-    for (int i = 0; i <= l; i++) {
-        u64 q = cx->primes[i];
-        u64 *a0 = malloc(n * 8), *a1 = malloc(n * 8), *b0 = malloc(n * 8), *b1 = malloc(n * 8);
-        memcpy(a0, a->c[0] + (u64)i * n, n * 8); memcpy(a1, a->c[1] + (u64)i * n, n * 8);
-        memcpy(b0, b->c[0] + (u64)i * n, n * 8); memcpy(b1, b->c[1] + (u64)i * n, n * 8);
-        poly_ntt(cx, a0, i); poly_ntt(cx, a1, i); poly_ntt(cx, b0, i); poly_ntt(cx, b1, i);
-        u64 *d0 = r->c[0] + (u64)i * n, *d1 = r->c[1] + (u64)i * n, *e2 = d2 + (u64)i * n;
-        for (u64 c = 0; c < n; c++) {
-            d0[c] = mulmod(a0[c], b0[c], q);
-            d1[c] = addmod(mulmod(a0[c], b1[c], q), mulmod(a1[c], b0[c], q), q);
-            e2[c] = mulmod(a1[c], b1[c], q);
-        }
-        poly_intt(cx, d0, i); poly_intt(cx, d1, i); poly_intt(cx, e2, i);
-        free(a0); free(a1); free(b0); free(b1);
-    }
+    tp_args A = {cx, a, b, r, d2};
+    parallel_for(l + 1, tp_body, &A);
     u64 *o0 = malloc((l + 1) * n * 8), *o1 = malloc((l + 1) * n * 8);
     keyswitch(cx, d2, l, rk, o0, o1);
     for (int i = 0; i <= l; i++) {

@@ -29,6 +29,10 @@ static void need(bool ok, const char *msg) {
     if (!ok) throw Error{HE_EINVAL, msg};
 }
 static void launched(he_ctx *cx, const char *what) { check_cuda(cudaGetLastError(), what); }
+// every ciphertext argument must belong to the context it is used with
+static void own(const he_ctx *cx, const he_ct *ct) {
+    if (ct && ct->ctx != cx) throw Error{HE_EINVAL, "ciphertext does not belong to this context"};
+}
 
 extern "C" {
 
@@ -81,6 +85,20 @@ int he_ctx_memory(const he_ctx *cx, size_t *in_use, size_t *peak) {
 const char *he_last_error(const he_ctx *cx) { return cx ? cx->err.c_str() : "null context"; }
 
 uint64_t he_launch_count(void) { return (uint64_t)launch_count(); }
+
+int he_profile_enable(int32_t kernel_class) {
+    if (kernel_class < -1 || kernel_class > 3) return HE_EINVAL;
+    prof_enable(kernel_class);
+    return HE_OK;
+}
+
+int he_profile_read(int32_t kernel_class, uint64_t *launches, double *ms, double *bytes) {
+    if (!launches || !ms || !bytes) return HE_EINVAL;
+    unsigned long long l = 0;
+    prof_read(kernel_class, &l, ms, bytes);
+    *launches = l;
+    return HE_OK;
+}
 
 int he_keygen_relin(he_ctx *cx) {
     if (!cx) return HE_EINVAL;
@@ -173,6 +191,7 @@ int he_encrypt_poly(he_ctx *cx, const double *m, double scale, uint32_t ctr, int
 int he_decrypt(he_ctx *cx, const he_ct *ct, double *re, double *im, size_t n_slots) {
     if (!cx || !ct || !re) return HE_EINVAL;
     API_TRY
+    own(cx, ct);
     const size_t N = cx->N();
     need(n_slots <= N / 2, "more values than slots");
     double *d_c = cx->d_dbl + N, *d_re = cx->d_dbl, *d_im = cx->d_dbl + N / 2;
@@ -187,6 +206,7 @@ int he_decrypt(he_ctx *cx, const he_ct *ct, double *re, double *im, size_t n_slo
 int he_decrypt_poly(he_ctx *cx, const he_ct *ct, double *out) {
     if (!cx || !ct || !out) return HE_EINVAL;
     API_TRY
+    own(cx, ct);
     double *d_c = cx->d_dbl + cx->N();
     decrypt_dev(cx, ct, d_c);
     check_cuda(cudaMemcpyAsync(out, d_c, cx->N() * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
@@ -197,6 +217,7 @@ int he_decrypt_poly(he_ctx *cx, const he_ct *ct, double *out) {
 int he_ct_export(he_ctx *cx, const he_ct *ct, uint64_t *out, size_t cap) {
     if (!cx || !ct || !out) return HE_EINVAL;
     API_TRY
+    own(cx, ct);
     const size_t N = cx->N(), m = (size_t)(ct->level + 1) * N;
     need(cap >= 2 * m, "export buffer too small");
     u64 *tmp = (u64 *)cx->arena.alloc(2 * m * 8);
@@ -235,7 +256,7 @@ int he_ct_info(const he_ct *ct, uint32_t *level, double *scale) {
 }
 
 int he_ct_device(const he_ct *ct, uint64_t **dev, size_t *poly_stride) {
-    if (!ct) return HE_EINVAL;
+    if (!ct || !ct->ctx) return HE_EINVAL;
     if (dev) *dev = ct->d;
     if (poly_stride) *poly_stride = (size_t)ct->cap * ct->ctx->N();
     return HE_OK;
@@ -247,16 +268,17 @@ void he_ct_free(he_ct *ct) { ct_release(ct); }
     int name {                                                   \
         if (!cx || !a || !out) return HE_EINVAL;                 \
         API_TRY                                                  \
+        own(cx, a);                                              \
         Ct res_ = expr;                                          \
         launched(cx, #name);                                     \
         *out = res_.release();                                   \
         API_CATCH(cx)                                            \
     }
 
-UNARY_OP(he_add(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), op_add(cx, a, b, false)))
-UNARY_OP(he_sub(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), op_add(cx, a, b, true)))
+UNARY_OP(he_add(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), own(cx, b), op_add(cx, a, b, false)))
+UNARY_OP(he_sub(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), own(cx, b), op_add(cx, a, b, true)))
 UNARY_OP(he_mul_int(he_ctx *cx, const he_ct *a, int64_t k, he_ct **out), op_mul_int(cx, a, k))
-UNARY_OP(he_mul(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), op_mul(cx, a, b)))
+UNARY_OP(he_mul(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), own(cx, b), op_mul(cx, a, b)))
 UNARY_OP(he_rescale(he_ctx *cx, const he_ct *a, he_ct **out), op_rescale(cx, a))
 UNARY_OP(he_drop(he_ctx *cx, const he_ct *a, uint32_t level, he_ct **out), op_drop(cx, a, (int)level))
 UNARY_OP(he_rotate(he_ctx *cx, const he_ct *a, int32_t r, he_ct **out), op_automorph(cx, a, rot_galois(cx, r)))
@@ -266,6 +288,7 @@ UNARY_OP(he_automorphism(he_ctx *cx, const he_ct *a, uint64_t g, he_ct **out), o
 int he_mul_const(he_ctx *cx, const he_ct *a, double c, double target, he_ct **out) {
     if (!cx || !a || !out) return HE_EINVAL;
     API_TRY
+    own(cx, a);
     double E = (target * (double)cx->primes[a->level]) / a->scale;
     double K = std::rint(c * E);
     Ct t = op_mul_intd(cx, a, K, a->scale * E);
@@ -278,6 +301,7 @@ int he_mul_const(he_ctx *cx, const he_ct *a, double c, double target, he_ct **ou
 int he_add_const(he_ctx *cx, const he_ct *a, double c, he_ct **out) {
     if (!cx || !a || !out) return HE_EINVAL;
     API_TRY
+    own(cx, a);
     Ct r = op_add_intd(cx, a, std::rint(c * a->scale));
     launched(cx, "add_const");
     *out = r.release();
@@ -287,6 +311,7 @@ int he_add_const(he_ctx *cx, const he_ct *a, double c, he_ct **out) {
 int he_rotsum(he_ctx *cx, const he_ct *a, uint32_t steps, he_ct **out) {
     if (!cx || !a || !out) return HE_EINVAL;
     API_TRY
+    own(cx, a);
     Ct cur = op_copy(cx, a);
     for (uint32_t i = 0; i < steps; i++) {
         Ct r = op_automorph(cx, cur.get(), rot_galois(cx, (i64)1 << i));
@@ -343,6 +368,7 @@ int he_cutmax_prepare(he_ctx *cx, const he_cutmax_plan *plan) {
 int cutmax(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out) {
     if (!cx || !in || !out) return HE_EINVAL;
     API_TRY
+    own(cx, in);
     Plan pl = plan_from(plan);
     Ct r = cutmax_ct(cx, in, pl);
     launched(cx, "cutmax");
@@ -353,6 +379,8 @@ int cutmax(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out)
 int nucleus_sample(he_ctx *cx, const he_ct *logits, const he_ct *rand_ct, const he_cutmax_plan *plan, he_ct **out) {
     if (!cx || !logits || !rand_ct || !out) return HE_EINVAL;
     API_TRY
+    own(cx, logits);
+    own(cx, rand_ct);
     Plan pl = plan_from(plan);
     Ct x = op_add(cx, logits, rand_ct, false);
     Ct r = cutmax_ct(cx, x.get(), pl);

@@ -176,6 +176,7 @@ he_ct *ct_alloc(he_ctx *cx, int level, double scale) {
     ct->bytes = (size_t)2 * ct->cap * cx->N() * 8;
     try {
         ct->d = (u64 *)cx->arena.alloc(ct->bytes);
+        cx->live.insert(ct);
     } catch (...) {
         delete ct;
         throw;
@@ -184,7 +185,10 @@ he_ct *ct_alloc(he_ctx *cx, int level, double scale) {
 }
 void ct_release(he_ct *ct) {
     if (!ct) return;
-    ct->ctx->arena.release(ct->d, ct->bytes);
+    if (ct->ctx) {  // an orphan's memory went away with its context's arena
+        ct->ctx->arena.release(ct->d, ct->bytes);
+        ct->ctx->live.erase(ct);
+    }
     delete ct;
 }
 Rows ct_rows(const he_ct *ct, int level) {
@@ -772,6 +776,7 @@ Ct op_mod_raise(he_ctx *cx, const he_ct *a, int level) {
 }  // namespace he
 
 he_ctx::~he_ctx() {
+    for (he_ct *c : live) c->ctx = nullptr;
     he::release_slot(slot);
     for (auto &k : keys) arena.release(k.data, k.bytes);
     if (arena.owned && arena.base) cudaFree(arena.base);

@@ -3,6 +3,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/he_cutmax.h"
@@ -41,7 +42,7 @@ struct LevelTabs {
 }  // namespace he
 
 struct he_ct {
-    he_ctx *ctx;
+    he_ctx *ctx;    // null once the owning context has been destroyed
     int level;
     double scale;
     u64 *d;     // c0 limbs then c1 limbs
@@ -80,6 +81,7 @@ struct he_ctx {
     u64 *ks_coef = nullptr, *ks_ext = nullptr, *ks_acc = nullptr, *ks_conv = nullptr;
     u64 *sc_a = nullptr, *sc_b = nullptr;  // 2*(nq+np) rows each, general scratch
     std::vector<he::KeyDev> keys;
+    std::unordered_set<he_ct *> live;      // ciphertexts handed out and not yet freed
 
     ~he_ctx();
     size_t N() const { return (size_t)n; }

@@ -6,6 +6,7 @@
 // Philox samplers and the float64 canonical-embedding FFT.
 #include <atomic>
 #include <cstdio>
+#include <vector>
 
 #include "kernels.h"
 
@@ -27,6 +28,62 @@ void upload_constants(int slot, const PrimeConsts &pc_in, const u64 *cdt, int n_
 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long launch_count() { return g_launches.load(); }
+
+// ---------------------------------------------------------------- profiling
+// When a kernel class is enabled, its launchers bracket each launch with a
+// pair of CUDA events on the launch stream; prof_read sums the durations.
+namespace {
+struct ProfState {
+    int cls = -1;
+    std::vector<cudaEvent_t> ev;  // pairs
+    std::vector<double> bytes;
+    size_t used = 0;
+    double total_bytes = 0;
+};
+ProfState g_prof;
+}  // namespace
+
+void prof_enable(int cls) {
+    g_prof.cls = cls;
+    g_prof.used = 0;
+    g_prof.total_bytes = 0;
+    g_prof.bytes.clear();
+}
+bool prof_on(int cls) { return cls == g_prof.cls; }
+void prof_begin(int cls, cudaStream_t s) {
+    if (cls != g_prof.cls) return;
+    if (g_prof.used * 2 + 2 > g_prof.ev.size()) {
+        size_t grow = g_prof.ev.size() ? g_prof.ev.size() : 1024;
+        for (size_t i = 0; i < grow; i++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            g_prof.ev.push_back(e);
+        }
+    }
+    cudaEventRecord(g_prof.ev[2 * g_prof.used], s);
+}
+void prof_end(int cls, cudaStream_t s, double bytes) {
+    if (cls != g_prof.cls) return;
+    cudaEventRecord(g_prof.ev[2 * g_prof.used + 1], s);
+    g_prof.used++;
+    g_prof.total_bytes += bytes;
+}
+void prof_read(int cls, unsigned long long *launches, double *ms, double *bytes) {
+    *launches = 0;
+    *ms = 0;
+    *bytes = 0;
+    if (cls != g_prof.cls) return;
+    double t = 0;
+    for (size_t i = 0; i < g_prof.used; i++) {
+        cudaEventSynchronize(g_prof.ev[2 * i + 1]);
+        float f = 0;
+        cudaEventElapsedTime(&f, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]);
+        t += f;
+    }
+    *launches = g_prof.used;
+    *ms = t;
+    *bytes = g_prof.total_bytes;
+}
 
 static inline unsigned grid_for(size_t total, int per_block) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -168,6 +225,8 @@ static void ntt_launch(const Rows &rows, int n_rows, const NttTables &tw, bool f
 
 static void ntt_dispatch(const Rows &rows, int n_rows, const NttTables &tw, int log_n, bool fwd, cudaStream_t s) {
     if (n_rows <= 0) return;
+    const int cls = fwd ? PROF_NTT_FWD : PROF_NTT_INV;
+    prof_begin(cls, s);
     switch (log_n) {
         case 10: ntt_launch<5, 5>(rows, n_rows, tw, fwd, s); break;
         case 11: ntt_launch<5, 6>(rows, n_rows, tw, fwd, s); break;
@@ -178,6 +237,7 @@ static void ntt_dispatch(const Rows &rows, int n_rows, const NttTables &tw, int 
         case 16: ntt_launch<8, 8>(rows, n_rows, tw, fwd, s); break;
         default: break;
     }
+    prof_end(cls, s, 16.0 * (double)n_rows * (double)(1 << log_n));
 }
 void ntt_forward(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s) {
     ntt_dispatch(rows, n_rows, tw, log_n, true, s);
@@ -344,7 +404,9 @@ __global__ void k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n)
 }
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s) {
     size_t t = (size_t)n_polys << log_n;
+    prof_begin(PROF_BCONV, s);
     k_bconv<<<grid_for(t, 128), 128, 0, s>>>(out, in, tab, n_polys, log_n);
+    prof_end(PROF_BCONV, s, 8.0 * (tab.n_in + tab.n_out) * (double)n_polys * (double)(1 << log_n));
 }
 
 __global__ void k_keyswitch_inner(KeyIP kp, int log_n) {
@@ -372,7 +434,9 @@ __global__ void k_keyswitch_inner(KeyIP kp, int log_n) {
 }
 void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
     size_t t = (size_t)k.n_rows << log_n;
+    prof_begin(PROF_KS_INNER, s);
     k_keyswitch_inner<<<grid_for(t, 256), 256, 0, s>>>(k, log_n);
+    prof_end(PROF_KS_INNER, s, 8.0 * (3.0 * k.beta + 2.0) * (double)k.n_rows * (double)(1 << log_n));
 }
 
 __global__ void k_moddown_finish(Rows out, Rows acc, Rows conv, ScalarTab pinv, int n_rows, Rows add_to,

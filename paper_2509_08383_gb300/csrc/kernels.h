@@ -29,6 +29,13 @@ struct BConvTab {
 // number of kernels launched by this library so far (all contexts)
 unsigned long long launch_count();
 
+// CUDA-event timing of one kernel class at a time (see he_profile_enable)
+enum ProfClass { PROF_NTT_FWD = 0, PROF_NTT_INV = 1, PROF_KS_INNER = 2, PROF_BCONV = 3 };
+void prof_enable(int cls);
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s, double bytes);
+void prof_read(int cls, unsigned long long *launches, double *ms, double *bytes);
+
 void upload_constants(int slot, const PrimeConsts &pc, const u64 *cdt, int n_cdt, cudaStream_t s);
 
 // NTT / INTT of n_rows limb rows in place.

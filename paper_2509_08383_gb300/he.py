@@ -58,6 +58,8 @@ def lib():
             "he_ctx_memory": [VP, C.POINTER(sz), C.POINTER(sz)],
             "he_last_error": [VP],
             "he_launch_count": [],
+            "he_profile_enable": [i32],
+            "he_profile_read": [i32, C.POINTER(u64), pd, pd],
             "he_keygen_relin": [VP],
             "he_keygen_galois": [VP, u64],
             "he_keygen_rotations": [VP, C.POINTER(i32), sz],
@@ -103,6 +105,20 @@ def lib():
 
 def launch_count():
     return int(lib().he_launch_count())
+
+
+PROF_NTT_FWD, PROF_NTT_INV, PROF_KS_INNER, PROF_BCONV = 0, 1, 2, 3
+
+
+def profile_enable(kernel_class):
+    if lib().he_profile_enable(int(kernel_class)) != 0:
+        raise ValueError(kernel_class)
+
+
+def profile_read(kernel_class):
+    n, ms, b = C.c_uint64(), C.c_double(), C.c_double()
+    lib().he_profile_read(int(kernel_class), C.byref(n), C.byref(ms), C.byref(b))
+    return int(n.value), float(ms.value), float(b.value)
 
 
 def _dptr(a):
