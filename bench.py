@@ -38,9 +38,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+CFG2_Q = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+CFG2_P = [61] * 10
+
+
 def workload(name):
+    """(log_n, q bits, p bits, dnum, plan, logits generator, description, bootstrap (h, K, r, d) or None)."""
     from paper_2509_08383_gb300 import plan as P
     from paper_2509_08383_gb300 import synth
+    if name == "cfg2":
+        log_n, n = 16, 32000
+        gaps = [0.05, 0.2, 1.0]
+        gen = lambda s: synth.logits_heavy_tail(s, n=n, gap=gaps[s % 3])
+        pl = P.calibrate(lambda i: gen(100000 + i), 200, n, 1 << (log_n - 1), 4, [16, 4, 4, 6],
+                         [5.0, 3.0, 3.0, 3.0], margin=2.0, tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6,
+                         bootstrap=True)
+        desc = {"workload": "CutMax T=4 p=[16,4,4,6] c=[5,3,3,3], 32000 logits N(0,9) + 50 heavy-tail "
+                            "Exp(1.5), top-1 gap in {0.05,0.2,1.0}, zero-padded in N=2^16 slots, CKKS "
+                            "bootstrapping when levels run out (logQ=1534, dnum=3, h=192)",
+                "log_n": log_n, "n": n, "T": 4, "k": pl.k, "d": pl.d}
+        return log_n, CFG2_Q, CFG2_P, 3, pl, gen, desc, (192, 24, 4, 31)
     if name == "cfg1":
         log_n, qb, pb, dnum = 14, [60] + [40] * 21, [60, 60], 11
         n = 1024
@@ -49,7 +66,7 @@ def workload(name):
         gen = lambda s: synth.logits_gaussian(s, n=n)
         desc = {"workload": "CutMax T=2 p=3 c=5, 1024 logits N(0,4) replicated in N=2^14 slots, leveled "
                             "(L=21, 40-bit scale, dnum=11)", "log_n": log_n, "n": n, "T": 2}
-        return log_n, qb, pb, dnum, pl, gen, desc
+        return log_n, qb, pb, dnum, pl, gen, desc, None
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -120,6 +137,32 @@ def dist_setup(args):
     return None, rank, ws
 
 
+def oracle_ks_model(log_n, qb, pb, dnum, h, levels, reps=1):
+    """Oracle key-switch seconds at the given levels (bounded sample)."""
+    from oracle import ckks as ock
+    o = ock.Context(log_n, qb, pb, dnum, h=h, seed=1)
+    o.gen_relin_key()
+    rng = np.random.default_rng(0)
+    out = {}
+    for l in levels:
+        d = np.stack([rng.integers(0, q, 1 << log_n, dtype=np.uint64) for q in o.primes[: l + 1]])
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            o.keyswitch(d, l, 0)
+        out[l] = (time.perf_counter() - t0) / reps
+    return out
+
+
+def extrapolate(ks_by_level, model):
+    """sum_l count_l * t(l), t linear between the measured levels."""
+    lv = sorted(model)
+    tot = 0.0
+    for l, cnt in ks_by_level.items():
+        t = float(np.interp(l, lv, [model[x] for x in lv]))
+        tot += cnt * t
+    return tot
+
+
 def run_reference(args):
     """The CPU oracle as it stands, on this machine's host cores."""
     dist, rank, ws = dist_setup(args)
@@ -128,42 +171,61 @@ def run_reference(args):
     from oracle import ckks as ock
     from oracle import encoding as oenc
     from oracle.circuit import HE, cutmax_he, required_rotations
+    from paper_2509_08383_gb300 import ledger
     from paper_2509_08383_gb300 import plan as P
-    log_n, qb, pb, dnum, pl, gen, desc = workload(args.workload)
-    o = ock.Context(log_n, qb, pb, dnum, seed=1)
-    o.gen_relin_key()
-    for r in required_rotations(pl):
-        o.gen_rot_key(r)
-    delta = 2.0 ** 40
+    log_n, qb, pb, dnum, pl, gen, desc, boot = workload(args.workload)
     times = []
-    for step in range(args.warmup + args.steps):
-        x = gen(50000 + step)
-        t0 = time.perf_counter()
-        ct = o.encrypt(oenc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, step)
-        z = cutmax_he(HE(o, delta), ct, pl)
-        oenc.decode(o.decrypt(z), log_n, z.scale)
-        if step >= args.warmup:
-            times.append(time.perf_counter() - t0)
+    if boot is None:
+        o = ock.Context(log_n, qb, pb, dnum, seed=1)
+        o.gen_relin_key()
+        for r in required_rotations(pl):
+            o.gen_rot_key(r)
+        delta = 2.0 ** 40
+        for step in range(args.warmup + args.steps):
+            x = gen(50000 + step)
+            t0 = time.perf_counter()
+            ct = o.encrypt(oenc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, step)
+            z = cutmax_he(HE(o, delta), ct, pl)
+            oenc.decode(o.decrypt(z), log_n, z.scale)
+            if step >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        sample = f"{args.steps} full CutMax decodes (encrypt + CutMax + decrypt) on the oracle"
+    else:
+        ks, nb = ledger.cutmax_ledger(pl, len(qb), log_n, boot=boot[1:])
+        levels = [min(ks), (min(ks) + len(qb) - 1) // 2, len(qb) - 1]
+        for step in range(args.warmup + args.steps):
+            model = oracle_ks_model(log_n, qb, pb, dnum, boot[0], levels)
+            if step >= args.warmup:
+                times.append(extrapolate(ks, model))
+        sample = (f"per step, oracle key switches timed at levels {levels} and scaled by the circuit's "
+                  f"{sum(ks.values())} key switches per decode ({nb} bootstraps); a full decode on the oracle "
+                  "is hours")
     T = sum(times)
-    cores = ock.get_threads()
     val = args.steps / T
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "decodes/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": desc,
-           "cpu_baseline": {"value": val, "unit": "decodes/s", "cores": cores, "kind": "oracle",
-                            "sample": f"{args.steps} full CutMax decodes (encrypt+CutMax+decrypt) on the oracle"},
+           "cpu_baseline": {"value": val, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": val, "unit": "decodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def cpu_baseline(args, desc):
-    """Bounded oracle sample: one full CutMax of the same workload on host cores."""
+def cpu_baseline(args, ks_by_level=None):
+    """Bounded oracle sample of the bench workload, in decodes/s."""
     from oracle import ckks as ock
     from oracle import encoding as oenc
     from oracle.circuit import HE, cutmax_he, required_rotations
     from paper_2509_08383_gb300 import plan as P
-    log_n, qb, pb, dnum, pl, gen, _ = workload(args.workload)
+    log_n, qb, pb, dnum, pl, gen, _, boot = workload(args.workload)
+    if boot is not None:
+        levels = [min(ks_by_level), (min(ks_by_level) + len(qb) - 1) // 2, len(qb) - 1]
+        model = oracle_ks_model(log_n, qb, pb, dnum, boot[0], levels)
+        t = extrapolate(ks_by_level, model)
+        return {"value": 1.0 / t, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
+                "sample": f"oracle key switches timed at levels {levels}, scaled by the {sum(ks_by_level.values())} "
+                          "key switches of one decode (the library's ledger); extrapolated, key switching only"}
     o = ock.Context(log_n, qb, pb, dnum, seed=1)
     o.gen_relin_key()
     for r in required_rotations(pl):
@@ -175,8 +237,7 @@ def cpu_baseline(args, desc):
     cutmax_he(HE(o, delta), ct, pl)
     dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
-            "sample": "1 full CutMax decode of the bench workload on the oracle (device-resident equivalent: "
-                      "ciphertext already encrypted)"}
+            "sample": "1 full CutMax decode of the bench workload on the oracle (ciphertext already encrypted)"}
 
 
 def main():
@@ -185,7 +246,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg1")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -198,8 +259,12 @@ def main():
     from paper_2509_08383_gb300 import build, he
     from paper_2509_08383_gb300 import plan as P
     build.build_library()
-    log_n, qb, pb, dnum, pl, gen, desc = workload(args.workload)
-    g = he.Context(log_n, qb, pb, dnum, seed=1 + rank)
+    log_n, qb, pb, dnum, pl, gen, desc, boot = workload(args.workload)
+    if boot is not None:
+        g = he.Context(log_n, qb, pb, dnum, h=boot[0], seed=1 + rank, arena_bytes=64 << 30)
+        g.bootstrap_prepare(*boot[1:])
+    else:
+        g = he.Context(log_n, qb, pb, dnum, seed=1 + rank)
     g.cutmax_prepare(pl)
     slots = 1 << (log_n - 1)
     stream = torch.cuda.current_stream()
@@ -220,6 +285,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    g.ledger(reset=True)
     l0 = he.launch_count()
     with ClockSampler(local) as clk:
         for s in range(nsteps):
@@ -230,10 +296,13 @@ def main():
             if s == args.warmup - 1:
                 torch.cuda.synchronize()
                 l0 = he.launch_count()
+                g.ledger(reset=True)
                 he.profile_enable(dom)
             del z
         torch.cuda.synchronize()
     launches = he.launch_count() - l0
+    ks_led, nboot = g.ledger(reset=True)
+    ks_by_level = {i: int(v) // args.steps for i, v in enumerate(ks_led) if v}
     ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -279,10 +348,12 @@ def main():
            "clocks": clk.summary(),
            "e2e": {"value": e2e, "unit": "decodes/s", "h2d_bytes_per_step": slots * 8,
                    "d2h_bytes_per_step": pl.n * 8},
-           "gpu_launches": int(launches), "roofline": roofline}
+           "gpu_launches": int(launches), "roofline": roofline,
+           "ledger": {"keyswitches_per_decode": int(sum(ks_by_level.values())),
+                      "bootstraps_per_decode": nboot / args.steps}}
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
-            res["cpu_baseline"] = cpu_baseline(args, desc)
+            res["cpu_baseline"] = cpu_baseline(args, ks_by_level)
         print(json.dumps(res))
 
 

@@ -96,6 +96,10 @@ uint64_t he_launch_count(void);
  * product: (3*beta + 2) words per coefficient per row; conversion: one
  * word per input and output coefficient). */
 int he_profile_enable(int32_t kernel_class);
+/* Operation ledger of a context since creation (or the last reset): host
+ * ks_by_level[n_q] = key switches performed at each level, *n_boot = number of
+ * bootstraps.  reset != 0 zeroes the ledger after reading. */
+int he_ledger_read(he_ctx *ctx, uint64_t *ks_by_level, uint64_t *n_boot, int32_t reset);
 int he_profile_read(int32_t kernel_class, uint64_t *launches, double *ms, double *bytes);
 
 /* ---- keys (Sect. 2.1 rotations; hybrid key switching) ---------------- */
@@ -165,6 +169,22 @@ int he_keyswitch_raw(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g,
  * a(psi^(2 brv(i) + 1)), psi the canonical 2N-th root of that prime. */
 int he_ntt_device(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, uint32_t prime_idx0, int32_t inverse);
 
+/* ---- bootstrapping (App. B.1: ciphertexts are refreshed when their
+ * multiplicative depth runs out) ------------------------------------------- */
+/* Build the bootstrapping tables and keys.  K bounds |I| in the ModRaise
+ * plaintext t = m + q0*I (about 6 standard deviations of the secret's
+ * contribution, sqrt(h/12) for Hamming weight h); the modular reduction is
+ * cos(2 pi((K+1)x - 1/4)/2^r) by a Chebyshev series of degree d (d < 64),
+ * followed by r double angles.  Needs n_q >= 18: the transforms take 3 + 3
+ * levels and EvalMod ceil(log2 d) + 1 + r levels, all from the top of the
+ * chain; a bootstrapped ciphertext comes out at level n_q - 1 - that many.
+ * Level-consuming steps use the chain from the top down, so the top
+ * primes should be the large (about 60-bit) ones. */
+int he_bootstrap_prepare(he_ctx *ctx, uint32_t K, uint32_t r, uint32_t d);
+/* Refresh a ciphertext (any level; only limb q0 is used) to a high level,
+ * encrypting the same message up to the bootstrapping error. */
+int he_bootstrap(he_ctx *ctx, const he_ct *in, he_ct **out);
+
 /* ---- CutMax (Alg. 2) and nucleus sampling (Alg. 3) ------------------- */
 /* Circuit plan: the range-scaling constants of Sect. 3.2's obligations.
  * n real entries per ciphertext; packing 0 = replicate (n a power of two
@@ -172,7 +192,12 @@ int he_ntt_device(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, uint32_t prime_
  * Per iteration t < T: power[t] (p), c[t], k[t] Goldschmidt inverse-sqrt
  * iterations, kappa[t] range scale of V_t = sum (n y - S)^2, y0[t] initial
  * guess.  Final normalisation: Goldschmidt inverse of degree d on
- * kappa_f * sum(Y). */
+ * kappa_f * sum(Y).  bootstrap != 0 selects the bootstrapped circuit (needs
+ * he_bootstrap_prepare): the Goldschmidt input is x = kappa V, Y_(t+1) is
+ * scaled by norm[t] (NULL = all 1) and a ciphertext is bootstrapped before
+ * any phase that needs more levels than it has (Y before the statistics: 3;
+ * x: 2; g and h between Goldschmidt steps: 2; D' and h: 1; u before the
+ * power: ceil(log2 p); Y before the final normalisation: d + 3). */
 typedef struct {
     uint32_t n, packing, T;
     const uint32_t *power;
@@ -182,6 +207,8 @@ typedef struct {
     const double *y0;
     uint32_t d;
     double kappa_f;
+    const double *norm;
+    int32_t bootstrap;
 } he_cutmax_plan;
 
 /* Generate every key the plan needs (rotations 2^i, relinearisation and,

@@ -146,6 +146,62 @@ def cutmax_he(he, ct, plan, bootstrap=None):
     return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
 
 
+def cutmax_he_boot(he, ct, plan, boot):
+    """Alg. 2 with bootstrapping when levels run out.
+
+    Same steps as cutmax_he, with two changes that keep every refreshed
+    ciphertext bounded: the Goldschmidt input is x = kappa V (one level) and
+    Y_(t+1) is scaled by plan.norm[t] through u' = norm^(1/p) u.  Before each
+    phase a ciphertext with fewer levels than the phase needs is bootstrapped:
+    Y before the statistics (3), x before the iteration (2), g and h together
+    between Goldschmidt steps (2), D' and h before the product (1), u before the
+    power (ceil log2 p), Y before the final normalisation (d + 3).
+    """
+    ctx = he.ctx
+    n, steps, m = plan.n, plan.rotsum_steps, plan.pad
+
+    def ensure(c, need):
+        return boot.bootstrap(c) if c.level < need else c
+
+    mask = None
+    if m:
+        mask = np.zeros(plan.slots)
+        mask[:n] = 1.0
+    Y = ct
+    for t in range(plan.T):
+        p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
+        rn = plan.norm[t] ** (1.0 / p)
+        Y = ensure(Y, 3)
+        S = he.rotsum(Y, steps)
+        D = ctx.sub(ctx.mul_int(Y, n), S)
+        E = he.mul_rescale(D, D)
+        V = he.rotsum(E, steps)
+        if m:
+            V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
+        x = ensure(he.mcr(V, kap), 2)
+        coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
+        Dp = he.mul_plain_rescale(D, coef * mask) if m else he.mcr(D, coef)
+        a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), 1.5)
+        h = he.mcr(a, y0 / 2.0)
+        g = he.mul_rescale(he.mcr(x, y0), a) if k >= 2 else None
+        for i in range(2, k + 1):
+            if h.level < 2:
+                g, h = boot.bootstrap(g), boot.bootstrap(h)
+            a = he.add_const(he.neg(he.mul_rescale(g, h)), 1.5)
+            if i < k:
+                g = he.mul_rescale(g, a)
+            h = he.mul_rescale(h, a)
+        h, Dp = ensure(h, 1), ensure(Dp, 1)
+        u = he.mul_rescale(Dp, h)
+        u = he.add_plain_vec(u, rn * mask) if m else he.add_const(u, rn)
+        u = ensure(u, (p - 1).bit_length())
+        Y = he.power(u, p)
+    Y = ensure(Y, plan.d + 3)
+    S = he.rotsum(Y, steps)
+    F = inverse_goldschmidt(he, S, plan.kappa_f, plan.d)
+    return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
+
+
 def nucleus_he(he, ct_logits, ct_noise, plan):
     """Alg. 3: X~ = X + G (G = U^(1/alpha) supplied encrypted), then CutMax."""
     return cutmax_he(he, he.ctx.add(ct_logits, ct_noise), plan)

@@ -123,6 +123,7 @@ def cutmax_circuit(x, plan, return_trace=False):
     """
     y = np.asarray(x, dtype=np.float64).copy()
     n = plan.n
+    boot = bool(getattr(plan, "bootstrap", False))
     trace = {"V": [], "S_final": None}
     for t in range(plan.T):
         S = y.sum()
@@ -130,16 +131,23 @@ def cutmax_circuit(x, plan, return_trace=False):
         V = (D * D).sum()
         trace["V"].append(V)
         kap, y0, k = plan.kappa[t], plan.y0[t], plan.k[t]
-        a = 1.5 - (kap * y0 * y0 / 2.0) * V
-        h = (y0 / 2.0) * a
-        g = (kap * y0 * V) * a
+        rn = plan.norm[t] ** (1.0 / plan.p[t]) if boot else 1.0
+        if boot:                      # bootstrapped circuit: x = kappa V first
+            xx = kap * V
+            a = 1.5 - (y0 * y0 / 2.0) * xx
+            h = (y0 / 2.0) * a
+            g = (xx * y0) * a
+        else:
+            a = 1.5 - (kap * y0 * y0 / 2.0) * V
+            h = (y0 / 2.0) * a
+            g = (kap * y0 * V) * a
         for i in range(2, k + 1):
             a = 1.5 - g * h
             if i < k:
                 g = g * a
             h = h * a
-        Dp = D * (2.0 * math.sqrt(kap * n) / plan.c[t])
-        u = Dp * h + 1.0
+        Dp = D * (2.0 * math.sqrt(kap * n) / plan.c[t] * rn)
+        u = Dp * h + rn
         y = power_by_squaring(u, plan.p[t])
     S = y.sum()
     trace["S_final"] = S

@@ -92,6 +92,17 @@ int he_profile_enable(int32_t kernel_class) {
     return HE_OK;
 }
 
+int he_ledger_read(he_ctx *cx, uint64_t *ks_by_level, uint64_t *n_boot, int32_t reset) {
+    if (!cx) return HE_EINVAL;
+    if (ks_by_level) memcpy(ks_by_level, cx->ks_by_level, sizeof(uint64_t) * cx->nq);
+    if (n_boot) *n_boot = cx->n_boot;
+    if (reset) {
+        memset(cx->ks_by_level, 0, sizeof(cx->ks_by_level));
+        cx->n_boot = 0;
+    }
+    return HE_OK;
+}
+
 int he_profile_read(int32_t kernel_class, uint64_t *launches, double *ms, double *bytes) {
     if (!launches || !ms || !bytes) return HE_EINVAL;
     unsigned long long l = 0;
@@ -350,6 +361,24 @@ int he_ntt_device(he_ctx *cx, uint64_t *data, uint32_t n_limbs, uint32_t prime_i
     if (inverse) ntt_inverse(r, (int)n_limbs, cx->tw, cx->log_n, cx->stream);
     else ntt_forward(r, (int)n_limbs, cx->tw, cx->log_n, cx->stream);
     launched(cx, "ntt");
+    API_CATCH(cx)
+}
+
+int he_bootstrap_prepare(he_ctx *cx, uint32_t K, uint32_t r, uint32_t d) {
+    if (!cx) return HE_EINVAL;
+    API_TRY
+    boot_prepare(cx, (int)K, (int)r, (int)d);
+    sync(cx, "bootstrap keys");
+    API_CATCH(cx)
+}
+
+int he_bootstrap(he_ctx *cx, const he_ct *in, he_ct **out) {
+    if (!cx || !in || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, in);
+    Ct r = bootstrap_ct(cx, in);
+    launched(cx, "bootstrap");
+    *out = r.release();
     API_CATCH(cx)
 }
 

@@ -16,6 +16,7 @@
 //   Y = u^p by square-and-multiply
 // Final: S = rotsum(Y); a = 1 - kappa_f S; F = prod_{i<=d}(1 + a^(2^i));
 //   Z = (kappa_f Y) F   (Goldschmidt inverse, App. B.1)
+#include <algorithm>
 #include <cmath>
 
 #include "context.h"
@@ -128,7 +129,11 @@ Plan plan_from(const he_cutmax_plan *p) {
         pl.k.push_back((int)p->k[t]);
         pl.kappa.push_back(p->kappa[t]);
         pl.y0.push_back(p->y0[t]);
+        double nm = p->norm ? p->norm[t] : 1.0;
+        if (!(nm > 0)) throw Error{HE_ERANGE, "plan normalisers must be positive"};
+        pl.norm.push_back(nm);
     }
+    pl.bootstrap = p->bootstrap != 0;
     pl.d = (int)p->d;
     pl.kappa_f = p->kappa_f;
     if (!(pl.kappa_f > 0)) throw Error{HE_ERANGE, "kappa_f must be positive"};
@@ -146,8 +151,11 @@ void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois) {
     for (int i = 0; i < steps; i++) galois.push_back(rot_galois(cx, (i64)1 << i));
 }
 
+static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl);
+
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
     const int slots = cx->n / 2;
+    if (pl.bootstrap) return cutmax_boot(cx, in, pl);
     if (pl.n > slots) throw Error{HE_EINVAL, "plan n exceeds the slot count"};
     if (pl.packing == 0 && (slots % pl.n != 0 || (pl.n & (pl.n - 1))))
         throw Error{HE_EINVAL, "replicated packing needs n a power of two dividing N/2"};
@@ -194,6 +202,468 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
         u = m ? he.add_plain_vec(u.get(), d_mask, slots) : he.add_const(u.get(), 1.0);
         Y = he.power(u.get(), pl.p[t]);
     }
+    Ct S = he.rotsum(Y.get(), steps);
+    Ct F = inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d);
+    return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());
+}
+
+}  // namespace he
+
+// ======================================================================
+// Bootstrapping (full-slot, real messages).  The paper refreshes
+// ciphertexts whose levels run out by bootstrapping (App. B.1); the steps:
+//   ModRaise   level-0 ciphertext -> top modulus; the plaintext becomes
+//              t = m + q0*I.  Its scale is declared q0*(K+1), so its slots
+//              read decode(t)/(q0 (K+1)).
+//   CoeffToSlot  slots <- BR(w(t))/(q0 (K+1)), w_k = t_k + i t_(k+h): the
+//              inverse of the slot-domain special FFT V = S_h ... S_2 BR
+//              (S_len: radix-2 stage of block length len with twiddles
+//              exp(2 pi i (5^j mod 4 len)/(4 len))), its stages grouped into
+//              three levels, each a baby-step giant-step sum of rotations.
+//   split      Re / Im by one conjugation (factor 1/2 in the scale; -i is
+//              X^(3N/2)).
+//   EvalMod    cos(2 pi ((K+1)x - 1/4)/2^r) by its Chebyshev series, then r
+//              double angles: sin(2 pi t/q0).
+//   SlotToCoeff  the stages of V in three levels; the factor q0/(2 pi S)
+//              is taken into the scale, so the result encrypts the message.
+// Bit-reversed slot order between the two transforms is harmless because
+// EvalMod acts slot by slot.
+// ======================================================================
+#include <complex>
+#include <numeric>
+
+namespace he {
+
+using cplx = std::complex<double>;
+using Diag = std::map<int, std::vector<cplx>>;  // offset (mod h) -> diagonal
+
+struct LinLevel {
+    Diag diag;
+    std::vector<int> baby, giant;          // rotation amounts (signed slots)
+    std::vector<std::vector<int>> idx;     // [g][b] -> index into pts, or -1
+    std::vector<int> offs;                 // per plaintext: its diagonal offset
+    std::vector<int> pg;                   // per plaintext: its giant amount
+    u64 *pts = nullptr;                    // [n_pt][level+1][N] NTT form
+    size_t pts_bytes = 0;
+    int level = -1;
+    double scale_in = 0, E = 0, target = 0;
+};
+
+struct Boot {
+    int K = 0, r = 0, d = 0;
+    double s_fix = 0, em_scale = 0;
+    std::vector<double> cheb;
+    LinLevel cts[3], stc[3];
+    std::vector<u64> galois;
+};
+
+static Diag stage_diag(int h, int len, bool inverse) {
+    Diag D;
+    std::vector<cplx> d0(h), dp(h), dm(h);
+    for (int i = 0; i < h; i++) {
+        int j = i % len, half = len / 2;
+        int jj = j < half ? j : j - half;
+        u64 e = powmod_host(5, (u64)jj, 4ull * len);
+        cplx tau = std::polar(1.0, 2.0 * M_PI * (double)e / (4.0 * len));
+        if (!inverse) {
+            if (j < half) { d0[i] = 1.0; dp[i] = tau; }
+            else { dm[i] = 1.0; d0[i] = -tau; }
+        } else {
+            if (j < half) { d0[i] = 0.5; dp[i] = 0.5; }
+            else { d0[i] = -0.5 / tau; dm[i] = 0.5 / tau; }
+        }
+    }
+    auto put = [&](int off, std::vector<cplx> &v) {
+        off = ((off % h) + h) % h;
+        auto it = D.find(off);
+        if (it == D.end()) D[off] = v;
+        else for (int i = 0; i < h; i++) it->second[i] += v[i];
+    };
+    put(0, d0);
+    put(len / 2, dp);
+    put(-len / 2, dm);
+    return D;
+}
+
+// (A B) x = A (B x): diag_{r+s} += dA_r * rot(dB_s, r), rot(v, r)[i] = v[i+r]
+static Diag diag_mul(const Diag &A, const Diag &B, int h) {
+    Diag C;
+    for (auto &a : A)
+        for (auto &b : B) {
+            int off = (a.first + b.first) % h;
+            auto &dst = C[off];
+            if (dst.empty()) dst.assign(h, 0.0);
+            for (int i = 0; i < h; i++) dst[i] += a.second[i] * b.second[(i + a.first) % h];
+        }
+    for (auto it = C.begin(); it != C.end();) {
+        double mx = 0;
+        for (auto &v : it->second) mx = std::max(mx, std::abs(v));
+        if (mx < 1e-300) it = C.erase(it);
+        else ++it;
+    }
+    return C;
+}
+
+static void bsgs_layout(LinLevel &L, int h) {
+    std::vector<int> so;
+    for (auto &d : L.diag) {
+        int r = d.first;
+        if (r > h / 2) r -= h;
+        so.push_back(r);
+    }
+    int u = 0;
+    for (int r : so) u = std::gcd(u, std::abs(r));
+    if (u == 0) u = 1;
+    int mmin = 1 << 30, mmax = -(1 << 30);
+    for (int r : so) { mmin = std::min(mmin, r / u); mmax = std::max(mmax, r / u); }
+    int span = mmax - mmin + 1, bs = 1;
+    while ((long)bs * bs < span) bs <<= 1;
+    int ng = (span + bs - 1) / bs;
+    L.baby.clear();
+    L.giant.clear();
+    for (int b = 0; b < bs; b++) L.baby.push_back(b * u);
+    for (int g = 0; g < ng; g++) L.giant.push_back((mmin + g * bs) * u);
+    L.idx.assign(ng, std::vector<int>(bs, -1));
+    L.offs.clear();
+    L.pg.clear();
+    for (int r : so) {
+        int m = r / u - mmin, g = m / bs, b = m % bs;
+        L.idx[g][b] = (int)L.offs.size();
+        L.offs.push_back(((r % h) + h) % h);
+        L.pg.push_back(L.giant[g]);
+    }
+}
+
+static std::vector<double> chebyshev_coeffs(int K, int r, int d) {
+    std::vector<double> c(d + 1), fx(d + 1), th(d + 1);
+    for (int j = 0; j <= d; j++) {
+        th[j] = M_PI * (j + 0.5) / (d + 1);
+        double x = std::cos(th[j]);
+        fx[j] = std::cos(2.0 * M_PI * ((K + 1) * x - 0.25) / std::ldexp(1.0, r));
+    }
+    for (int k = 0; k <= d; k++) {
+        double s = 0;
+        for (int j = 0; j <= d; j++) s += fx[j] * std::cos(k * th[j]);
+        c[k] = 2.0 / (d + 1) * s;
+    }
+    c[0] /= 2;
+    return c;
+}
+
+// Plaintexts of one transform level for a ciphertext at `level` and `scale`.
+static void build_level(he_ctx *cx, LinLevel &L, int level, double scale_in, double target) {
+    if (L.pts && L.level == level && L.scale_in == scale_in && L.target == target) return;
+    const int h = cx->n / 2;
+    const size_t N = cx->N();
+    if (L.pts) cx->arena.release(L.pts, L.pts_bytes);
+    L.level = level;
+    L.scale_in = scale_in;
+    L.target = target;
+    L.E = (target * (double)cx->primes[level]) / scale_in;
+    const int npt = (int)L.offs.size();
+    L.pts_bytes = (size_t)npt * (level + 1) * N * 8;
+    L.pts = (u64 *)cx->arena.alloc(L.pts_bytes);
+    std::vector<double> re(h), im(h);
+    for (int p = 0; p < npt; p++) {
+        const std::vector<cplx> &dg = L.diag.at(L.offs[p]);
+        int G = ((L.pg[p] % h) + h) % h;
+        for (int i = 0; i < h; i++) {  // v'[i] = diag[i - G]
+            cplx v = dg[((i - G) % h + h) % h];
+            re[i] = v.real();
+            im[i] = v.imag();
+        }
+        double *d_re = cx->d_dbl, *d_im = cx->d_dbl + N / 2, *d_pt = cx->d_dbl + N;
+        check_cuda(cudaMemcpyAsync(d_re, re.data(), h * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+        check_cuda(cudaMemcpyAsync(d_im, im.data(), h * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+        encode_dev(cx, d_re, d_im, h, L.E, d_pt);
+        Rows pr = make_rows(L.pts + (size_t)p * (level + 1) * N, 0, level + 1, level + 1, cx->nq);
+        load_intd(pr, level + 1, d_pt, cx->log_n, cx->stream);
+        ntt_forward(pr, level + 1, cx->tw, cx->log_n, cx->stream);
+        check_cuda(cudaStreamSynchronize(cx->stream), "build transform plaintexts");
+    }
+}
+
+// sum_g rot_G( sum_b pt[g][b] * rot_b(x) ), one rescale
+static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
+    build_level(cx, L, x->level, x->scale, target);
+    const int l = x->level;
+    const size_t N = cx->N();
+    // baby-step rotations share one ModUp of c1 (hoisting): each reads the
+    // extended digits through its own automorphism
+    std::vector<Ct> baby(L.baby.size());
+    const LevelTabs &LT = cx->lv[l];
+    const size_t ext_bytes = (size_t)LT.beta * LT.n_ext * N * 8;
+    u64 *ext = nullptr;
+    for (size_t b = 1; b < L.baby.size(); b++) {
+        bool used = false;
+        for (auto &row : L.idx) used |= row[b] >= 0;
+        if (!used) continue;
+        u64 g = rot_galois(cx, L.baby[b]);
+        const KeyDev *key = find_key(cx, g);
+        if (!key) throw Error{HE_ENOKEY, "bootstrapping rotation key missing"};
+        if (!ext) {
+            ext = (u64 *)cx->arena.alloc(ext_bytes);
+            modup(cx, ct_poly(x, 1), l, ext);
+        }
+        Ct r(ct_alloc(cx, l, x->scale));
+        Rows sa = make_rows(cx->sc_a, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+        ew_automorph_ntt(sa, make_rows(ct_poly(x, 0), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
+        keyswitch_ext(cx, ct_poly(x, 1), ext, l, *key, g, ct_rows(r.get()), sa, 1);
+        baby[b] = std::move(r);
+    }
+    if (ext) cx->arena.release(ext, ext_bytes);
+    Ct acc;
+    for (size_t g = 0; g < L.giant.size(); g++) {
+        Ct inner;
+        for (size_t b = 0; b < L.baby.size(); b++) {
+            int p = L.idx[g][b];
+            if (p < 0) continue;
+            const he_ct *src = b == 0 ? x : baby[b].get();
+            Rows pt = make_rows(L.pts + (size_t)p * (l + 1) * N, 0, l + 1, l + 1, cx->nq);
+            if (!inner) {
+                inner = Ct(ct_alloc(cx, l, x->scale * L.E));
+                for (int k = 0; k < 2; k++)
+                    ew_mul(make_rows(ct_poly(inner.get(), k), 0, l + 1, l + 1, cx->nq),
+                           make_rows(ct_poly(src, k), 0, l + 1, l + 1, cx->nq), pt, l + 1, cx->log_n, cx->stream);
+            } else {
+                for (int k = 0; k < 2; k++)
+                    ew_mul_acc(make_rows(ct_poly(inner.get(), k), 0, l + 1, l + 1, cx->nq),
+                               make_rows(ct_poly(src, k), 0, l + 1, l + 1, cx->nq), pt, l + 1, cx->log_n, cx->stream);
+            }
+        }
+        if (!inner) continue;
+        if (L.giant[g] % (cx->n / 2) != 0) inner = op_automorph(cx, inner.get(), rot_galois(cx, L.giant[g]));
+        acc = acc ? op_add(cx, acc.get(), inner.get(), false) : std::move(inner);
+    }
+    return op_rescale(cx, acc.get());
+}
+
+// Chebyshev series sum_k c_k T_k(x) by baby steps T_1..T_(m-1) and giant
+// steps T_m, T_2m, T_4m, ...: a series of degree >= m is split by the largest
+// giant G <= degree as q T_G + r (T_G T_j = (T_(G+j) + T_(|G-j|))/2 gives
+// q_0 = c_G, q_j = 2 c_(G+j), r_(G-j) = c_(G-j) - c_(G+j)); q is evaluated
+// first, and r is aimed at the exact scale of the rescaled product q T_G.
+struct ChebEval {
+    HE &he;
+    std::vector<Ct> T;   // T_1..T_(m-1) and the giants (index k)
+    int m;
+
+    Ct baby_sum(const std::vector<double> &c, double target) {
+        he_ctx *cx = he.cx;
+        Ct acc;
+        int low = 1 << 30;
+        std::vector<Ct> terms;
+        for (size_t k = 1; k < c.size(); k++) {
+            if (c[k] == 0.0) continue;
+            terms.push_back(he.mcr(T[k].get(), c[k], target));
+            low = std::min(low, terms.back()->level);
+        }
+        for (auto &t : terms) {
+            Ct u = t->level > low ? op_drop(cx, t.get(), low) : std::move(t);
+            acc = acc ? op_add(cx, acc.get(), u.get(), false) : std::move(u);
+        }
+        if (!acc) throw Error{HE_EINVAL, "empty Chebyshev series"};
+        return he.add_const(acc.get(), c[0]);
+    }
+
+    Ct eval(const std::vector<double> &c, double target) {
+        he_ctx *cx = he.cx;
+        int deg = (int)c.size() - 1;
+        if (deg < m) return baby_sum(c, target);
+        int G = m;
+        while (2 * G <= deg) G *= 2;
+        std::vector<double> q(deg - G + 1), r(c.begin(), c.begin() + G);
+        q[0] = c[G];
+        for (int j = 1; j <= deg - G; j++) {
+            q[j] = 2.0 * c[G + j];
+            r[G - j] -= c[G + j];
+        }
+        Ct Q = eval(q, target);
+        Ct P = he.mul_rescale(Q.get(), T[G].get());
+        Ct R = eval(r, P->scale);
+        if (R->level > P->level) R = op_drop(cx, R.get(), P->level);
+        return op_add(cx, P.get(), R.get(), false);
+    }
+};
+
+static Ct evalmod(HE &he, const he_ct *x, const Boot &B) {
+    he_ctx *cx = he.cx;
+    const int d = B.d;
+    int m = 1;
+    while (m * m <= d + 1) m *= 2;  // baby steps T_1..T_(m-1)
+    int top = m;
+    while (2 * top <= d) top *= 2;  // largest giant step
+    ChebEval ce{he, std::vector<Ct>(std::max(m, top) + 1), m};
+    ce.T[1] = op_copy(cx, x);
+    auto make = [&](int k) {  // T_k = 2 T_a T_b - T_(a-b), a = ceil(k/2), b = floor(k/2)
+        int a = (k + 1) / 2, b = k / 2;
+        Ct P2 = op_mul_int(cx, he.mul_rescale(ce.T[a].get(), ce.T[b].get()).get(), 2);
+        if (a == b) {
+            ce.T[k] = he.add_const(P2.get(), -1.0);
+        } else {
+            Ct xm = he.mcr(ce.T[1].get(), 1.0, P2->scale);
+            if (xm->level > P2->level) xm = op_drop(cx, xm.get(), P2->level);
+            ce.T[k] = op_add(cx, P2.get(), xm.get(), true);
+        }
+    };
+    for (int k = 2; k < m; k++) make(k);
+    for (int g = m; g <= top; g *= 2) make(g);
+    Ct c = ce.eval(B.cheb, B.em_scale);
+    for (int i = 0; i < B.r; i++) c = he.add_const(op_mul_int(cx, he.mul_rescale(c.get(), c.get()).get(), 2).get(), -1.0);
+    return c;
+}
+
+void boot_prepare(he_ctx *cx, int K, int r, int d) {
+    if (d < 2 || d > 63 || r < 0 || r > 8 || K < 1) throw Error{HE_EINVAL, "bootstrap parameters out of range"};
+    if (cx->nq < 18) throw Error{HE_ELEVEL, "bootstrapping needs at least 17 levels above q0"};
+    auto B = std::make_shared<Boot>();
+    B->K = K;
+    B->r = r;
+    B->d = d;
+    B->s_fix = cx->delta;
+    B->em_scale = std::ldexp(1.0, 60);
+    B->cheb = chebyshev_coeffs(K, r, d);
+    const int h = cx->n / 2, s = cx->log_n - 1;
+    int g3 = s / 3, g2 = (s - g3) / 2, g1 = s - g3 - g2;  // g1 >= g2 >= g3
+    int sizes[3] = {g1, g2, g3};
+    // SlotToCoeff: stages len = 2, 4, ..., applied in that order, grouped
+    int st = 1;
+    for (int lv = 0; lv < 3; lv++) {
+        Diag M;
+        for (int k = 0; k < sizes[lv]; k++, st++) {
+            Diag S = stage_diag(h, 1 << st, false);
+            M = M.empty() ? S : diag_mul(S, M, h);
+        }
+        B->stc[lv].diag = M;
+        bsgs_layout(B->stc[lv], h);
+    }
+    // CoeffToSlot: inverse stages len = h, h/2, ..., grouped
+    st = s;
+    for (int lv = 0; lv < 3; lv++) {
+        Diag M;
+        for (int k = 0; k < sizes[lv]; k++, st--) {
+            Diag S = stage_diag(h, 1 << st, true);
+            M = M.empty() ? S : diag_mul(S, M, h);
+        }
+        B->cts[lv].diag = M;
+        bsgs_layout(B->cts[lv], h);
+    }
+    std::vector<u64> gs;
+    for (auto *Ls : {B->cts, B->stc})
+        for (int lv = 0; lv < 3; lv++) {
+            for (int b : Ls[lv].baby)
+                if (b % h) gs.push_back(rot_galois(cx, b));
+            for (int g : Ls[lv].giant)
+                if (g % h) gs.push_back(rot_galois(cx, g));
+        }
+    gs.push_back(2 * cx->N() - 1);
+    std::sort(gs.begin(), gs.end());
+    gs.erase(std::unique(gs.begin(), gs.end()), gs.end());
+    B->galois = gs;
+    gen_relin_key(cx);
+    for (u64 g : gs) gen_galois_key(cx, g);
+    cx->boot_state = B;
+}
+
+Ct bootstrap_ct(he_ctx *cx, const he_ct *in) {
+    auto B = cx->boot_state;
+    if (!B) throw Error{HE_EINVAL, "bootstrapping not prepared"};
+    HE he{cx, B->em_scale};
+    cx->n_boot++;
+    const u64 q0 = cx->primes[0];
+    const double ratio = in->scale / B->s_fix;
+    Ct low = in->level ? op_drop(cx, in, 0) : op_copy(cx, in);
+    Ct x = op_mod_raise(cx, low.get(), cx->nq - 1);
+    x->scale = (double)q0 * (double)(B->K + 1);
+    // CoeffToSlot, aimed at half the EvalMod scale (the split doubles it)
+    for (int lv = 0; lv < 3; lv++) x = apply_level(cx, x.get(), B->cts[lv], B->em_scale / 2);
+    Ct xc = op_automorph(cx, x.get(), 2 * cx->N() - 1);
+    Ct re = op_add(cx, x.get(), xc.get(), false);
+    re->scale *= 2;
+    Ct im = op_mul_monomial(cx, op_add(cx, x.get(), xc.get(), true).get(), 3 * cx->N() / 2);
+    im->scale *= 2;
+    re = evalmod(he, re.get(), *B);
+    im = evalmod(he, im.get(), *B);
+    Ct w = op_add(cx, re.get(), op_mul_monomial(cx, im.get(), cx->N() / 2).get(), false);
+    // values sin(2 pi t/q0) ~ 2 pi m/q0: read them as m / s_fix
+    w->scale = w->scale * (2.0 * M_PI * B->s_fix) / (double)q0;
+    const double tg[3] = {std::ldexp(1.0, 50), std::ldexp(1.0, 45), cx->delta};
+    for (int lv = 0; lv < 3; lv++) w = apply_level(cx, w.get(), B->stc[lv], tg[lv]);
+    w->scale = w->scale / ratio;
+    return w;
+}
+
+// Alg. 2 with bootstrapping when levels run out (same steps as cutmax_ct;
+// the Goldschmidt input is x = kappa V and Y_(t+1) is scaled by norm[t]
+// through u' = norm^(1/p) u, so that every refreshed ciphertext is bounded).
+static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
+    if (!cx->boot_state) throw Error{HE_EINVAL, "bootstrapped plan needs he_bootstrap_prepare"};
+    const int slots = cx->n / 2;
+    if (pl.n > slots) throw Error{HE_EINVAL, "plan n exceeds the slot count"};
+    if (pl.packing == 0 && (slots % pl.n != 0 || (pl.n & (pl.n - 1))))
+        throw Error{HE_EINVAL, "replicated packing needs n a power of two dividing N/2"};
+    HE he{cx, cx->delta};
+    const int steps = rotsum_steps(pl, slots);
+    const int m = pl.pad(slots);
+    auto ensure = [&](Ct c, int need) -> Ct { return c->level < need ? bootstrap_ct(cx, c.get()) : std::move(c); };
+    std::vector<double> mask;
+    double *d_mask = cx->d_dbl + 2 * cx->N(), *d_cm = cx->d_dbl + 2 * cx->N() + slots;
+    if (m) {
+        mask.assign(slots, 0.0);
+        for (int i = 0; i < pl.n; i++) mask[i] = 1.0;
+    }
+    Ct Y = op_copy(cx, in);
+    for (int t = 0; t < pl.T; t++) {
+        const int p = pl.p[t], k = pl.k[t];
+        const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
+        Y = ensure(std::move(Y), 3);
+        Ct S = he.rotsum(Y.get(), steps);
+        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), S.get(), true);
+        Ct E = he.mul_rescale(D.get(), D.get());
+        Ct V = he.rotsum(E.get(), steps);
+        if (m) {
+            Ct S2 = he.mul_rescale(S.get(), S.get());
+            V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
+        }
+        Ct x = ensure(he.mcr(V.get(), kap), 2);
+        const double coef = 2.0 * std::sqrt(kap * pl.n) / pl.c[t] * rn;
+        Ct Dp;
+        if (m) {
+            std::vector<double> cm(slots, 0.0);
+            for (int i = 0; i < pl.n; i++) cm[i] = coef;
+            check_cuda(cudaMemcpyAsync(d_cm, cm.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
+            Dp = he.mul_plain_rescale(D.get(), d_cm, slots);
+        } else {
+            Dp = he.mcr(D.get(), coef);
+        }
+        Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), 1.5);
+        Ct h = he.mcr(a.get(), y0 / 2.0);
+        Ct g;
+        if (k >= 2) g = he.mul_rescale(he.mcr(x.get(), y0).get(), a.get());
+        for (int i = 2; i <= k; i++) {
+            if (h->level < 2) {
+                g = bootstrap_ct(cx, g.get());
+                h = bootstrap_ct(cx, h.get());
+            }
+            a = he.add_const(he.neg(he.mul_rescale(g.get(), h.get()).get()).get(), 1.5);
+            if (i < k) g = he.mul_rescale(g.get(), a.get());
+            h = he.mul_rescale(h.get(), a.get());
+        }
+        h = ensure(std::move(h), 1);
+        Dp = ensure(std::move(Dp), 1);
+        Ct u = he.mul_rescale(Dp.get(), h.get());
+        if (m) {
+            std::vector<double> rm(slots, 0.0);
+            for (int i = 0; i < pl.n; i++) rm[i] = rn;
+            check_cuda(cudaMemcpyAsync(d_mask, rm.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
+            u = he.add_plain_vec(u.get(), d_mask, slots);
+        } else {
+            u = he.add_const(u.get(), rn);
+        }
+        u = ensure(std::move(u), power_depth(p));
+        Y = he.power(u.get(), p);
+    }
+    Y = ensure(std::move(Y), pl.d + 3);
     Ct S = he.rotsum(Y.get(), steps);
     Ct F = inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d);
     return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());

@@ -657,28 +657,37 @@ Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt) {
     return out;
 }
 
-void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask) {
+// ModUp of d (NTT form, limbs 0..l) into ext ([beta][n_ext][N] NTT form,
+// rows inside each digit left unused): INTT, basis conversion per digit, NTT.
+void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext) {
+    const int log_n = cx->log_n;
+    const size_t N = cx->N();
+    const LevelTabs &T = cx->lv[l];
+    cudaStream_t s = cx->stream;
+    Rows coef = make_rows(cx->ks_coef, 0, l + 1, l + 1, cx->nq);
+    ew_copy(coef, make_rows((u64 *)d_ntt, 0, l + 1, l + 1, cx->nq), l + 1, log_n, s);
+    ntt_inverse(coef, l + 1, cx->tw, log_n, s);
+    for (int j = 0; j < T.beta; j++) {
+        int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
+        Rows in = make_rows(cx->ks_coef + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
+        Rows o = desc_rows(ext, T.desc + T.digit_off[j]);
+        bconv(o, in, T.modup[j], 1, log_n, s);
+    }
+    ntt_forward(desc_rows(ext, T.desc), T.n_desc, cx->tw, log_n, s);
+}
+
+// Inner product with the key (reading the digits through X -> X^galois when
+// galois != 0) and ModDown: out = (acc - conv(acc_P)) * P^-1 (+ add).
+void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
+                   const Rows &out, const Rows &add, int add_mask) {
     const int K = cx->np, log_n = cx->log_n;
     const size_t N = cx->N();
     const LevelTabs &T = cx->lv[l];
     cudaStream_t s = cx->stream;
-    // 1. coefficient form of d
-    Rows coef = make_rows(cx->ks_coef, 0, l + 1, l + 1, cx->nq);
-    ew_copy(coef, make_rows((u64 *)d_ntt, 0, l + 1, l + 1, cx->nq), l + 1, log_n, s);
-    ntt_inverse(coef, l + 1, cx->tw, log_n, s);
-    // 2. ModUp: approximate basis conversion of every digit
-    for (int j = 0; j < T.beta; j++) {
-        int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
-        Rows in = make_rows(cx->ks_coef + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
-        Rows o = desc_rows(cx->ks_ext, T.desc + T.digit_off[j]);
-        bconv(o, in, T.modup[j], 1, log_n, s);
-    }
-    // 3. NTT of all extension rows
-    ntt_forward(desc_rows(cx->ks_ext, T.desc), T.n_desc, cx->tw, log_n, s);
-    // 4. inner product with the key
+    cx->ks_by_level[l]++;
     KeyIP kp;
     kp.d_ntt = d_ntt;
-    kp.ext = cx->ks_ext;
+    kp.ext = ext;
     kp.key = key.data;
     kp.acc = cx->ks_acc;
     kp.n_rows = T.n_ext;
@@ -689,8 +698,8 @@ void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Row
     kp.beta = T.beta;
     kp.key_limbs = cx->nq + cx->np;
     kp.slot = cx->slot;
+    kp.galois = galois;
     keyswitch_inner(kp, log_n, s);
-    // 5. ModDown: INTT of the P rows, conversion P -> Q_l, NTT, subtract and scale
     Rows accP = make_rows(cx->ks_acc + (size_t)(l + 1) * N, (size_t)T.n_ext * N, K, 0, cx->nq);
     ntt_inverse(accP, 2 * K, cx->tw, log_n, s);
     BConvTab md = cx->moddown;
@@ -700,6 +709,11 @@ void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Row
     ntt_forward(conv, 2 * (l + 1), cx->tw, log_n, s);
     Rows accQ = make_rows(cx->ks_acc, (size_t)T.n_ext * N, l + 1, l + 1, cx->nq);
     moddown_finish(out, accQ, conv, cx->p_inv, 2 * (l + 1), add, add_mask, log_n, s);
+}
+
+void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask) {
+    modup(cx, d_ntt, l, cx->ks_ext);
+    keyswitch_ext(cx, d_ntt, cx->ks_ext, l, key, 0, out, add, add_mask);
 }
 
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
@@ -756,6 +770,12 @@ Ct op_automorph(he_ctx *cx, const he_ct *a, u64 g) {
     ew_automorph_ntt(sa, make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
     ew_automorph_ntt(sb, make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
     keyswitch(cx, cx->sc_b, l, *k, ct_rows(out.get()), sa, 1);
+    return out;
+}
+
+Ct op_mul_monomial(he_ctx *cx, const he_ct *a, u64 e) {
+    Ct out(ct_alloc(cx, a->level, a->scale));
+    ew_monomial(ct_rows(out.get()), ct_rows(a), 2 * (a->level + 1), e % (2 * cx->N()), cx->tw, cx->log_n, cx->stream);
     return out;
 }
 

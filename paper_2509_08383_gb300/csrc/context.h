@@ -10,6 +10,7 @@
 #include "kernels.h"
 
 namespace he {
+struct Boot;
 
 // Sub-allocator over one device buffer; exact-size reuse of freed blocks.
 struct Arena {
@@ -82,6 +83,10 @@ struct he_ctx {
     u64 *sc_a = nullptr, *sc_b = nullptr;  // 2*(nq+np) rows each, general scratch
     std::vector<he::KeyDev> keys;
     std::unordered_set<he_ct *> live;      // ciphertexts handed out and not yet freed
+    std::shared_ptr<he::Boot> boot_state;  // bootstrapping tables, when prepared
+    // operation ledger: key switches by level, bootstraps
+    uint64_t ks_by_level[HE_MAX_PRIMES] = {0};
+    uint64_t n_boot = 0;
 
     ~he_ctx();
     size_t N() const { return (size_t)n; }
@@ -137,19 +142,26 @@ Ct op_copy(he_ctx *cx, const he_ct *a);
 // raw hybrid key switch: d (NTT form, limbs 0..l) -> out (2 polys, NTT form),
 // add_mask bit k: out poly k += add poly k
 void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask);
+// the two halves of a key switch, for rotations that share one ModUp
+void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext);
+void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
+                   const Rows &out, const Rows &add, int add_mask);
 
 // ---- circuits (circuit.cu)
 struct Plan {
     int n, packing, T;
     std::vector<int> p, k;
-    std::vector<double> c, kappa, y0;
+    std::vector<double> c, kappa, y0, norm;
     int d;
     double kappa_f;
+    bool bootstrap;
     int pad(int slots) const;
 };
 Plan plan_from(const he_cutmax_plan *p);
 void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois);
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl);
+void boot_prepare(he_ctx *cx, int K, int r, int d);
+Ct bootstrap_ct(he_ctx *cx, const he_ct *in);
 
 void check_cuda(cudaError_t e, const char *what);
 void release_slot(int slot);

@@ -339,6 +339,28 @@ __global__ void k_automorph(Rows out, Rows a, int n_rows, u64 g, int log_n) {
     }
 }
 
+// out = a * X^e: in NTT form position i is multiplied by psi^((2 brv(i)+1) e),
+// read from the forward table (psi^j = fwd[brv(j)], psi^(j+N) = -psi^j).
+__global__ void k_monomial(Rows out, Rows a, int n_rows, u64 e, NttTables tw, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    const u64 n = 1ull << log_n, two_n_mask = 2 * n - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        u32 i = (u32)(gi & mask);
+        int p = out.prime(r);
+        const ModQ &m = pc.m[p];
+        u64 x = ((2ull * (__brev(i) >> (32 - log_n)) + 1) * e) & two_n_mask;
+        const u64 *fw = tw.fwd + ((size_t)p << log_n);
+        u64 w = x < n ? fw[__brev((u32)x) >> (32 - log_n)] : m.q - fw[__brev((u32)(x - n)) >> (32 - log_n)];
+        out.row(r, log_n)[i] = mul_mod(a.row(r, log_n)[i], w, m);
+    }
+}
+void ew_monomial(const Rows &out, const Rows &a, int n_rows, u64 e, const NttTables &tw, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_monomial<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, e, tw, log_n);
+}
+
 void ew_add(const Rows &out, const Rows &a, const Rows &b, int n_rows, int sub, int log_n, cudaStream_t s) {
     size_t t = (size_t)n_rows << log_n;
     k_add<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, sub, log_n);
@@ -413,16 +435,23 @@ __global__ void k_keyswitch_inner(KeyIP kp, int log_n) {
     const PrimeConsts &pc = c_pcs[kp.slot];
     const size_t n = (size_t)1 << log_n;
     const size_t total = (size_t)kp.n_rows * n;
+    const u64 two_n_mask = 2 * n - 1;
     EW_LOOP(total) {
         int t = (int)(gi >> log_n);
         size_t k = gi & (n - 1);
+        size_t src = k;
+        if (kp.galois) {  // hoisted rotation: position k reads the automorphism's source position
+            u64 e = 2ull * (__brev((u32)k) >> (32 - log_n)) + 1;
+            u64 e2 = (e * kp.galois) & two_n_mask;
+            src = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
+        }
         int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
         const ModQ &m = pc.m[p];
         int jt = t < kp.l1 ? t / kp.alpha : -1;
         u64 a0 = 0, a1 = 0;
         for (int j = 0; j < kp.beta; j++) {
-            u64 x = (j == jt) ? kp.d_ntt[((size_t)t << log_n) + k]
-                              : kp.ext[(((size_t)j * kp.n_rows + t) << log_n) + k];
+            u64 x = (j == jt) ? kp.d_ntt[((size_t)t << log_n) + src]
+                              : kp.ext[(((size_t)j * kp.n_rows + t) << log_n) + src];
             const u64 *kb = kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n);
             const u64 *ka = kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n);
             a0 = add_mod(a0, mul_mod(x, kb[k], m), m.q);

@@ -57,6 +57,8 @@ void ew_mul_acc(const Rows &out, const Rows &a, const Rows &b, int n_rows, int l
 // out = a0 - a1 (*) b  (decryption / encryption building block)
 void ew_tensor(const Rows &d0, const Rows &d1, const Rows &d2, const Rows &a0, const Rows &a1,
                const Rows &b0, const Rows &b1, int n_rows, int log_n, cudaStream_t s);
+// out = a * X^e (e < 2N) in NTT form
+void ew_monomial(const Rows &out, const Rows &a, int n_rows, u64 e, const NttTables &tw, int log_n, cudaStream_t s);
 // automorphism X -> X^g in NTT form (permutation of positions)
 void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log_n, cudaStream_t s);
 
@@ -71,6 +73,7 @@ struct KeyIP {
     u64 *acc;             // [2][n_rows][N]
     int n_rows, l1, nq, np, alpha, beta, key_limbs;
     int slot;
+    u64 galois;           // 0: read x_j at position i; else at the source of i under X -> X^galois
 };
 void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s);
 // out_i = (acc_i - conv_i) * pinv_i; polynomial p of the batch (row / lpp)

@@ -34,7 +34,8 @@ class Params(C.Structure):
 class CPlan(C.Structure):
     _fields_ = [("n", C.c_uint32), ("packing", C.c_uint32), ("T", C.c_uint32), ("power", C.POINTER(C.c_uint32)),
                 ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_uint32)), ("kappa", C.POINTER(C.c_double)),
-                ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double)]
+                ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double),
+                ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32)]
 
 
 _lib = None
@@ -59,6 +60,7 @@ def lib():
             "he_last_error": [VP],
             "he_launch_count": [],
             "he_profile_enable": [i32],
+            "he_ledger_read": [VP, pu64, pu64, i32],
             "he_profile_read": [i32, C.POINTER(u64), pd, pd],
             "he_keygen_relin": [VP],
             "he_keygen_galois": [VP, u64],
@@ -89,6 +91,8 @@ def lib():
             "he_rotsum": [VP, VP, u32, PP],
             "he_keyswitch_raw": [VP, pu64, u32, u64, pu64, pu64],
             "he_ntt_device": [VP, VP, u32, u32, i32],
+            "he_bootstrap_prepare": [VP, u32, u32, u32],
+            "he_bootstrap": [VP, VP, PP],
             "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
             "nucleus_sample": [VP, VP, VP, C.POINTER(CPlan), PP],
@@ -165,10 +169,12 @@ class Ciphertext:
 def plan_struct(plan):
     """Package CutMaxPlan -> (ctypes struct, keep-alive arrays)."""
     T = plan.T
+    norm = list(plan.norm) if getattr(plan, "norm", None) is not None else [1.0] * T
     arrs = dict(power=(C.c_uint32 * T)(*plan.p), c=(C.c_double * T)(*plan.c), k=(C.c_uint32 * T)(*plan.k),
-                kappa=(C.c_double * T)(*plan.kappa), y0=(C.c_double * T)(*plan.y0))
+                kappa=(C.c_double * T)(*plan.kappa), y0=(C.c_double * T)(*plan.y0), norm=(C.c_double * T)(*norm))
     s = CPlan(n=plan.n, packing=0 if plan.packing == "replicate" else 1, T=T, power=arrs["power"], c=arrs["c"],
-              k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f)
+              k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f,
+              norm=arrs["norm"], bootstrap=int(bool(getattr(plan, "bootstrap", False))))
     return s, arrs
 
 
@@ -192,7 +198,7 @@ class Context:
             beta = -(-len(qbits) // alpha)
             key = beta * 2 * (len(qbits) + len(pbits)) * self.n * 8
             ct = 2 * len(qbits) * self.n * 8
-            arena_bytes = 48 * key + 192 * ct + (64 << 20)
+            arena_bytes = 128 * key + 512 * ct + (64 << 20)
         self._arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
         self.ptr = C.c_void_p()
         rc = lib().he_ctx_create(C.byref(prm), C.c_void_p(self._arena.data_ptr()), int(arena_bytes),
@@ -218,6 +224,13 @@ class Context:
         out = C.c_void_p()
         self._chk(fn(self.ptr, *args, C.byref(out)))
         return Ciphertext(self, out)
+
+    def ledger(self, reset=False):
+        """(key switches per level [n_q], bootstraps) since creation / last reset."""
+        ks = np.zeros(self.nq, dtype=np.uint64)
+        nb = np.zeros(1, dtype=np.uint64)
+        self._chk(lib().he_ledger_read(self.ptr, _u64ptr(ks), _u64ptr(nb), int(bool(reset))))
+        return ks.astype(np.int64), int(nb[0])
 
     def memory(self):
         a, b = C.c_size_t(), C.c_size_t()
@@ -331,6 +344,13 @@ class Context:
         limbs = tensor.numel() // self.n
         self._chk(lib().he_ntt_device(self.ptr, C.c_void_p(tensor.data_ptr()), limbs, int(prime_idx0),
                                       int(bool(inverse))))
+
+    # bootstrapping
+    def bootstrap_prepare(self, K, r, d):
+        self._chk(lib().he_bootstrap_prepare(self.ptr, int(K), int(r), int(d)))
+
+    def bootstrap(self, ct):
+        return self._ct(lib().he_bootstrap, ct.ptr)
 
     # CutMax / nucleus
     def cutmax_prepare(self, plan):

@@ -1,0 +1,217 @@
+"""Operation-count model of the encrypted CutMax circuit.
+
+Replays the level bookkeeping of the library's circuits (leveled Alg. 2, the
+bootstrapped variant and bootstrapping itself) without any arithmetic and
+counts the hybrid key switches at each level: one per ciphertext product
+(relinearisation) and one per rotation or conjugation.  The counts say where
+the time goes (key switching dominates every step of Alg. 2) and scale
+per-operation timings to a whole decode.
+"""
+import math
+from collections import Counter
+
+
+def _stage_offsets(h, len_):
+    return {0, (len_ // 2) % h, (-len_ // 2) % h}
+
+
+def _group_offsets(h, lens):
+    offs = {0}
+    for L in lens:
+        offs = {(a + b) % h for a in offs for b in _stage_offsets(h, L)}
+    return offs
+
+
+def _bsgs_counts(h, offs):
+    """(used baby rotations, nonzero giant rotations) of one transform level."""
+    so = [r - h if r > h // 2 else r for r in offs]
+    u = 0
+    for r in so:
+        u = math.gcd(u, abs(r))
+    u = u or 1
+    ms = [r // u for r in so]
+    mmin, mmax = min(ms), max(ms)
+    span = mmax - mmin + 1
+    bs = 1
+    while bs * bs < span:
+        bs <<= 1
+    babies, giants = set(), set()
+    for m in ms:
+        g, b = divmod(m - mmin, bs)
+        if b:
+            babies.add(b)
+        G = (mmin + g * bs) * u
+        if G % h:
+            giants.add(g)
+    return len(babies), len(giants)
+
+
+def transform_rotations(log_n):
+    """Key switches of the three CoeffToSlot and three SlotToCoeff levels."""
+    h = 1 << (log_n - 1)
+    s = log_n - 1
+    g3 = s // 3
+    g2 = (s - g3) // 2
+    g1 = s - g3 - g2
+    sizes = [g1, g2, g3]
+    stc, cts = [], []
+    st = 1
+    for sz in sizes:
+        lens = [1 << (st + k) for k in range(sz)]
+        st += sz
+        stc.append(sum(_bsgs_counts(h, _group_offsets(h, lens))))
+    st = s
+    for sz in sizes:
+        lens = [1 << (st - k) for k in range(sz)]
+        st -= sz
+        cts.append(sum(_bsgs_counts(h, _group_offsets(h, lens))))
+    return cts, stc
+
+
+class Sim:
+    """Level-only stand-in for a ciphertext context."""
+
+    def __init__(self, nq, log_n, boot=None):
+        self.nq, self.log_n, self.boot = nq, log_n, boot
+        self.ks = Counter()
+        self.n_boot = 0
+
+    def mul(self, a, b):
+        l = min(a, b)
+        self.ks[l] += 1
+        return l - 1                      # relinearise + rescale
+
+    def rot(self, a):
+        self.ks[a] += 1
+        return a
+
+    def _evalmod(self, lvl, d, r):
+        """Baby-step giant-step Chebyshev series of degree d, then r double angles."""
+        m = 1
+        while m * m <= d + 1:
+            m *= 2
+        top = m
+        while 2 * top <= d:
+            top *= 2
+        T = {1: lvl}
+
+        def make(k):
+            T[k] = self.mul(T[(k + 1) // 2], T[k // 2])
+
+        for k in range(2, m):
+            make(k)
+        g = m
+        while g <= top:
+            make(g)
+            g *= 2
+
+        def ev(deg):
+            if deg < m:
+                return min(T[k] for k in range(1, deg + 1)) - 1
+            G = m
+            while 2 * G <= deg:
+                G *= 2
+            Q = ev(deg - G)
+            P = self.mul(Q, T[G])
+            ev(G - 1)
+            return P
+
+        c = ev(d)
+        for _ in range(r):
+            c = self.mul(c, c)
+        return c
+
+    def bootstrap(self, a):
+        K, r, d = self.boot
+        self.n_boot += 1
+        L = self.nq - 1
+        cts, stc = transform_rotations(self.log_n)
+        for i in range(3):
+            self.ks[L - i] += cts[i]
+        lvl = L - 3
+        self.ks[lvl] += 1                 # conjugation
+        for _ in range(2):                # EvalMod of the real and imaginary parts
+            c = self._evalmod(lvl, d, r)
+        for i in range(3):
+            self.ks[c - i] += stc[i]
+        return c - 3
+
+
+def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
+    """Key switches per level and bootstraps of one CutMax (library circuit)."""
+    sim = Sim(nq, log_n, boot)
+    steps = plan.rotsum_steps
+    m = plan.pad
+
+    def rotsum(a):
+        for _ in range(steps):
+            sim.rot(a)
+        return a
+
+    def mcr(a):
+        return a - 1
+
+    def power(u, p):
+        sq, acc, pp = u, None, int(p)
+        while True:
+            if pp & 1:
+                acc = sq if acc is None else sim.mul(acc, sq)
+            pp >>= 1
+            if pp == 0:
+                break
+            sq = sim.mul(sq, sq)
+        return acc
+
+    def ensure(a, need):
+        return sim.bootstrap(a) if a < need else a
+
+    Y = nq - 1 if start_level is None else start_level
+    for t in range(plan.T):
+        p, k = plan.p[t], plan.k[t]
+        if plan.bootstrap:
+            Y = ensure(Y, 3)
+        rotsum(Y)
+        D = Y
+        E = sim.mul(D, D)
+        V = rotsum(E)
+        if m:
+            sim.mul(Y, Y)
+        if plan.bootstrap:
+            x = ensure(mcr(V), 2)
+            Dp = mcr(D)
+            a = mcr(x)
+            h = mcr(a)
+            g = sim.mul(mcr(x), a) if k >= 2 else None
+            for i in range(2, k + 1):
+                if h < 2:
+                    g, h = sim.bootstrap(g), sim.bootstrap(h)
+                a = sim.mul(g, h)
+                if i < k:
+                    g = sim.mul(g, a)
+                h = sim.mul(h, a)
+            h, Dp = ensure(h, 1), ensure(Dp, 1)
+            u = sim.mul(Dp, h)
+            u = ensure(u, (p - 1).bit_length())
+        else:
+            a = mcr(V)
+            h = mcr(a)
+            g = sim.mul(mcr(V), a) if k >= 2 else None
+            for i in range(2, k + 1):
+                a = sim.mul(g, h)
+                if i < k:
+                    g = sim.mul(g, a)
+                h = sim.mul(h, a)
+            Dp = mcr(D)
+            u = sim.mul(Dp, h)
+        Y = power(u, p)
+    if plan.bootstrap:
+        Y = ensure(Y, plan.d + 3)
+    S = rotsum(Y)
+    a = mcr(S)
+    F = a
+    sq = a
+    for _ in range(plan.d):
+        sq = sim.mul(sq, sq)
+        F = sim.mul(F, sq)
+    sim.mul(mcr(Y), F)
+    return dict(sim.ks), sim.n_boot

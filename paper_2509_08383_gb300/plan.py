@@ -13,6 +13,13 @@ distribution (client side, never on encrypted data):
   k[t]      Goldschmidt inverse-square-root iterations (2 levels each)
   kappa_f   range scale of the final sum S_T for the Goldschmidt inverse
   d         degree of the Goldschmidt inverse (product of d+1 factors)
+  norm[t]   positive factor applied to Y_(t+1) (folded as norm^(1/p) into the
+            standardisation constants) so that max Y stays near 1 where a
+            ciphertext may be bootstrapped; 1 for leveled plans
+
+The statistics are those of the polynomial circuit itself (its Goldschmidt
+iterates, not the exact Alg. 1), taken iteration by iteration, since an
+approximate inverse square root changes every later statistic.
 
 S_c is scale invariant (Def. of c-semi-standardisation, App. E.1) and so is
 the final normalisation, so only the spread of V_t and S_T across inputs
@@ -39,7 +46,12 @@ class CutMaxPlan:
     d: int
     kappa_f: float
     bootstrap: bool = False
+    norm: List[float] = None
     extra: dict = field(default_factory=dict)
+
+    def __post_init__(self):
+        if self.norm is None:
+            self.norm = [1.0] * self.T
 
     @property
     def rotsum_steps(self) -> int:
@@ -104,7 +116,8 @@ def _exact_stats(x, T, p, c):
     return Vs, float(y.sum())
 
 
-def _invsqrt_err(x, k, y0):
+def _invsqrt_half(x, k, y0):
+    """The circuit's Goldschmidt output h ~ 1/(2 sqrt(x)) (k iterations)."""
     a = 1.5 - (y0 * y0 / 2.0) * x
     h = (y0 / 2.0) * a
     g = (x * y0) * a
@@ -113,7 +126,11 @@ def _invsqrt_err(x, k, y0):
         if i < k:
             g = g * a
         h = h * a
-    return np.abs(2.0 * h * np.sqrt(x) - 1.0).max()
+    return h
+
+
+def _invsqrt_err(x, k, y0):
+    return np.abs(2.0 * _invsqrt_half(x, k, y0) * np.sqrt(x) - 1.0).max()
 
 
 def _inv_err(x, d):
@@ -126,21 +143,37 @@ def _inv_err(x, d):
     return np.abs(x * f - 1.0).max()
 
 
+def _power(u, p):
+    sq, acc, pp = u, None, int(p)
+    while True:
+        if pp & 1:
+            acc = sq if acc is None else acc * sq
+        pp >>= 1
+        if pp == 0:
+            break
+        sq = sq * sq
+    return acc
+
+
 def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1e-7,
-              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False):
-    """Pick kappa/y0/k and kappa_f/d from `n_cal` draws of ``sample(i)``."""
+              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False, norm_margin=1.25):
+    """Pick kappa/y0/k per iteration and kappa_f/d from `n_cal` draws of ``sample(i)``,
+    following the circuit's own iterates; with bootstrap=True also the
+    normalisers norm[t] that keep max Y_(t+1) at about 1/norm_margin."""
     p = [int(v) for v in (p if not np.isscalar(p) else [p] * T)]
     c = [float(v) for v in (c if not np.isscalar(c) else [c] * T)]
-    Vs, Ss = [], []
-    for i in range(n_cal):
-        v, s = _exact_stats(sample(i), T, p, c)
-        Vs.append(v)
-        Ss.append(s)
-    Vs = np.asarray(Vs)
-    Ss = np.asarray(Ss)
-    kappa, y0s, ks = [], [], []
+    ys = [np.asarray(sample(i), dtype=np.float64).copy() for i in range(n_cal)]
+    kappa, y0s, ks, norms, vr = [], [], [], [], []
     for t in range(T):
-        a, b = Vs[:, t].min() / margin, Vs[:, t].max() * margin
+        Vs, Ds = [], []
+        for y in ys:
+            S = y.sum()
+            D = n * y - S
+            Ds.append(D)
+            Vs.append(float((D * D).sum()))
+        Vs = np.asarray(Vs)
+        vr.append([float(Vs.min()), float(Vs.max())])
+        a, b = Vs.min() / margin, Vs.max() * margin
         kap = 1.0 / math.sqrt(a * b)
         xs = np.geomspace(a * kap, b * kap, 2001)
         y0 = 1.0 if xs[-1] < 2.5 else math.sqrt(2.5 / xs[-1])
@@ -152,9 +185,20 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
                 if _invsqrt_err(xs, kk, y0) < tol_k:
                     k = kk
                     break
+        new = []
+        for D, V in zip(Ds, Vs):
+            h = _invsqrt_half(kap * V, k, y0)
+            u = D * (2.0 * math.sqrt(kap * n) / c[t]) * h + 1.0
+            new.append(_power(u, p[t]))
+        nm = 1.0
+        if bootstrap:
+            nm = 1.0 / (norm_margin * max(float(np.abs(v).max()) for v in new))
+        ys = [v * nm for v in new]
         kappa.append(kap)
         y0s.append(y0)
         ks.append(k)
+        norms.append(nm)
+    Ss = np.asarray([float(y.sum()) for y in ys])
     af, bf = Ss.min() / margin, Ss.max() * margin
     kf = 2.0 / (af + bf)
     xs = np.linspace(af * kf, bf * kf, 2001)
@@ -167,7 +211,6 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
                 d = dd
                 break
     return CutMaxPlan(n=n, slots=slots, packing=packing_for(n, slots), T=T, p=p, c=c, k=ks,
-                      kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap,
-                      extra={"V_range": [[float(Vs[:, t].min()), float(Vs[:, t].max())] for t in range(T)],
-                             "S_range": [float(Ss.min()), float(Ss.max())], "margin": margin,
+                      kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap, norm=norms,
+                      extra={"V_range": vr, "S_range": [float(Ss.min()), float(Ss.max())], "margin": margin,
                              "n_cal": n_cal})

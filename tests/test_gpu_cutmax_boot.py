@@ -1,0 +1,92 @@
+"""Bootstrapped CutMax (Alg. 2 with refreshes) on the GPU.
+
+Config-2 shape at a reduced ring: heavy-tailed logits, T = 4,
+p = [16, 4, 4, 6], c = [5, 3, 3, 3] (the paper's HE setting, Sect. 4.2),
+zero-padded packing, bootstrapping whenever a phase runs out of levels.
+Checked against the FP64 mirror of the same circuit (max-abs 1e-3), the exact
+Alg. 1 argmax, and, on one input, the oracle's own bootstrapped circuit.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import cutmax_fp64 as F                 # noqa: E402
+from paper_2509_08383_gb300 import build, he        # noqa: E402
+from paper_2509_08383_gb300 import plan as P        # noqa: E402
+from paper_2509_08383_gb300 import synth            # noqa: E402
+
+build.build_library()
+
+LOG_N = 11
+QB = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+PB = [61] * 10
+H, K, R, D = 64, 14, 4, 27
+NV = 1000
+T, PW, CC = 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0]
+
+
+def gen(i):
+    return synth.logits_heavy_tail(i, n=NV, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+
+
+@pytest.fixture(scope="module")
+def setup():
+    pl = P.calibrate(lambda i: gen(1000 + i), 200, NV, 1 << (LOG_N - 1), T, PW, CC, margin=2.0, tol_k=1e-6,
+                     k_max=20, d_max=14, tol_d=1e-6, bootstrap=True)
+    g = he.Context(LOG_N, QB, PB, dnum=3, h=H, seed=21)
+    g.bootstrap_prepare(K, R, D)
+    g.cutmax_prepare(pl)
+    return g, pl
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bootstrapped_cutmax_matches_mirror(setup, seed):
+    g, pl = setup
+    x = gen(seed)
+    z = g.cutmax(g.encrypt(P.pack(x, g.slots, pl.packing), g.delta, 1 + seed), pl)
+    dec = g.decrypt(z)
+    ref = F.cutmax_circuit(x, pl)
+    assert np.abs(dec[:NV] - ref).max() < 1e-3
+    assert np.abs(dec[NV:]).max() < 1e-3
+    assert int(np.argmax(dec[:NV])) == int(np.argmax(x)) == int(np.argmax(F.cutmax_exact(x, T, PW, CC)))
+
+
+def test_bootstrapped_cutmax_matches_oracle_circuit(setup):
+    from oracle import ckks as ock
+    from oracle import encoding as oenc
+    from oracle.bootstrap import Bootstrapper
+    from oracle.circuit import HE, cutmax_he_boot, required_rotations
+    g, pl = setup
+    o = ock.Context(LOG_N, QB, PB, dnum=3, h=H, seed=21)
+    ob = Bootstrapper(o, K=K, r=R, d=D)
+    ob.gen_keys()
+    for r in required_rotations(pl):
+        o.gen_rot_key(r)
+    x = gen(7)
+    pt = oenc.encode(P.pack(x, g.slots, pl.packing), LOG_N, g.delta)
+    zg = g.cutmax(g.encrypt_poly(pt, g.delta, 3), pl)
+    zo = cutmax_he_boot(HE(o, g.delta), o.encrypt(pt, g.delta, 3), pl, ob)
+    assert zg.level == zo.level
+    dg = g.decrypt(zg)[:NV]
+    do = oenc.decode(o.decrypt(zo), LOG_N, zo.scale).real[:NV]
+    assert np.abs(dg - do).max() < 1e-3
+    assert int(np.argmax(dg)) == int(np.argmax(do)) == int(np.argmax(x))
+
+
+def test_ledger_model_matches_library(setup):
+    """The operation-count model replays the library's circuit exactly."""
+    from paper_2509_08383_gb300 import ledger
+    g, pl = setup
+    x = gen(11)
+    ct = g.encrypt(P.pack(x, g.slots, pl.packing), g.delta, 4)
+    g.ledger(reset=True)
+    g.cutmax(ct, pl)
+    ks, nb = g.ledger(reset=True)
+    model, nb_model = ledger.cutmax_ledger(pl, len(QB), LOG_N, boot=(K, R, D))
+    assert nb == nb_model
+    assert {i: int(v) for i, v in enumerate(ks) if v} == model

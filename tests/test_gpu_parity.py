@@ -288,3 +288,17 @@ def test_circuit_too_deep_is_an_error():
     with pytest.raises(he.HeError) as ei:
         g.cutmax(ct, pl)
     assert ei.value.code == he.HE_ELEVEL
+
+
+def test_ledger_model_matches_leveled_circuit():
+    from paper_2509_08383_gb300 import ledger
+    g = he.Context(11, CFG1_Q, CFG1_P, dnum=11, seed=6)
+    pl = _cfg1_plan(g.slots)
+    g.cutmax_prepare(pl)
+    ct = g.encrypt(P.pack(synth.logits_gaussian(4), g.slots, pl.packing), g.delta, 1)
+    g.ledger(reset=True)
+    g.cutmax(ct, pl)
+    ks, nb = g.ledger(reset=True)
+    model, nb_model = ledger.cutmax_ledger(pl, len(CFG1_Q), 11)
+    assert nb == nb_model == 0
+    assert {i: int(v) for i, v in enumerate(ks) if v} == model
