@@ -290,9 +290,13 @@ def main():
     with ClockSampler(local) as clk:
         for s in range(nsteps):
             flush.zero_()
+            if s >= args.warmup:
+                torch.cuda.nvtx.range_push("timed_step")
             ev[s][0].record(stream)
             z = g.cutmax(cts[s], pl)
             ev[s][1].record(stream)
+            if s >= args.warmup:
+                torch.cuda.nvtx.range_pop()
             if s == args.warmup - 1:
                 torch.cuda.synchronize()
                 l0 = he.launch_count()

@@ -74,6 +74,10 @@ class Bootstrapper:
         self.cheb = chebyshev_coeffs(evalmod_function(K, r), d)
         self.bs = 1 << int(math.ceil(math.log2(math.sqrt(self.h))))
 
+    def out_level(self):
+        """Level of a bootstrapped ciphertext: 3 + ceil(log2(d+1)) + 1 + r + 3 below the top."""
+        return self.ctx.nq - 1 - 6 - (math.ceil(math.log2(self.d + 1)) + 1 + self.r)
+
     def rotations(self):
         h, bs = self.h, self.bs
         rots = set(range(1, bs)) | set(range(bs, h, bs))

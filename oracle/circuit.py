@@ -151,11 +151,13 @@ def cutmax_he_boot(he, ct, plan, boot):
 
     Same steps as cutmax_he, with two changes that keep every refreshed
     ciphertext bounded: the Goldschmidt input is x = kappa V (one level) and
-    Y_(t+1) is scaled by plan.norm[t] through u' = norm^(1/p) u.  Before each
+    Y_(t+1) is scaled by plan.norm[t] through u' = norm^(1/p) u.
+    The input is first dropped to the bootstrap's output level.  Before each
     phase a ciphertext with fewer levels than the phase needs is bootstrapped:
-    Y before the statistics (3), x before the iteration (2), g and h together
-    between Goldschmidt steps (2), D' and h before the product (1), u before the
-    power (ceil log2 p), Y before the final normalisation (d + 3).
+    Y before the statistics (3), x before the iteration (2), the packed
+    Goldschmidt pair [g | h] between steps (2) and before h is extracted (1),
+    D' and h before the product (1), u before the power (ceil log2 p), Y before
+    the final normalisation (d + 3).
     """
     ctx = he.ctx
     n, steps, m = plan.n, plan.rotsum_steps, plan.pad
@@ -167,7 +169,10 @@ def cutmax_he_boot(he, ct, plan, boot):
     if m:
         mask = np.zeros(plan.slots)
         mask[:n] = 1.0
-    Y = ct
+    # compute only on the levels a bootstrap hands back (the primes above are
+    # the bootstrapping primes, where products of Delta-scale ciphertexts
+    # would shrink the scale)
+    Y = ctx.drop(ct, boot.out_level()) if ct.level > boot.out_level() else ct
     for t in range(plan.T):
         p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
         rn = plan.norm[t] ** (1.0 / p)
@@ -181,16 +186,23 @@ def cutmax_he_boot(he, ct, plan, boot):
         x = ensure(he.mcr(V, kap), 2)
         coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
         Dp = he.mul_plain_rescale(D, coef * mask) if m else he.mcr(D, coef)
+        # Goldschmidt pair packed in one ciphertext: slots [0, s/2) hold g,
+        # slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
+        half = plan.slots // 2
+        lo = np.zeros(plan.slots)
+        lo[:half] = 1.0
+        hi = 1.0 - lo
         a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), 1.5)
-        h = he.mcr(a, y0 / 2.0)
-        g = he.mul_rescale(he.mcr(x, y0), a) if k >= 2 else None
+        P = he.add_plain_vec(he.mul_plain_rescale(x, y0 * lo), (y0 / 2.0) * hi)
+        P = he.mul_rescale(P, a)
         for i in range(2, k + 1):
-            if h.level < 2:
-                g, h = boot.bootstrap(g), boot.bootstrap(h)
-            a = he.add_const(he.neg(he.mul_rescale(g, h)), 1.5)
-            if i < k:
-                g = he.mul_rescale(g, a)
-            h = he.mul_rescale(h, a)
+            if P.level < 2:
+                P = boot.bootstrap(P)
+            Q = he.mul_rescale(P, ctx.rotate(P, half))
+            P = he.mul_rescale(P, he.add_const(he.neg(Q), 1.5))
+        P = ensure(P, 1)
+        hm = he.mul_plain_rescale(P, hi)
+        h = ctx.add(hm, ctx.rotate(hm, half))
         h, Dp = ensure(h, 1), ensure(Dp, 1)
         u = he.mul_rescale(Dp, h)
         u = he.add_plain_vec(u, rn * mask) if m else he.add_const(u, rn)

@@ -149,9 +149,11 @@ static int power_depth(int p) {
 void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois) {
     int steps = rotsum_steps(pl, cx->n / 2);
     for (int i = 0; i < steps; i++) galois.push_back(rot_galois(cx, (i64)1 << i));
+    if (pl.bootstrap) galois.push_back(rot_galois(cx, cx->n / 4));  // packed Goldschmidt pair
 }
 
 static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl);
+int boot_out_level(he_ctx *cx);
 
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
     const int slots = cx->n / 2;
@@ -513,6 +515,14 @@ static Ct evalmod(HE &he, const he_ct *x, const Boot &B) {
     return c;
 }
 
+// level of a bootstrapped ciphertext: 3 (CoeffToSlot) + EvalMod depth + 3 below the top
+int boot_out_level(he_ctx *cx) {
+    const Boot &B = *cx->boot_state;
+    int lg = 0;
+    while ((1 << lg) < B.d + 1) lg++;
+    return cx->nq - 1 - 6 - (lg + 1 + B.r);
+}
+
 void boot_prepare(he_ctx *cx, int K, int r, int d) {
     if (d < 2 || d > 63 || r < 0 || r > 8 || K < 1) throw Error{HE_EINVAL, "bootstrap parameters out of range"};
     if (cx->nq < 18) throw Error{HE_ELEVEL, "bootstrapping needs at least 17 levels above q0"};
@@ -612,7 +622,11 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         mask.assign(slots, 0.0);
         for (int i = 0; i < pl.n; i++) mask[i] = 1.0;
     }
-    Ct Y = op_copy(cx, in);
+    // compute only on the levels a bootstrap hands back: the primes above are
+    // the bootstrapping primes, where products of Delta-scale ciphertexts
+    // would shrink the scale
+    const int out_level = boot_out_level(cx);
+    Ct Y = in->level > out_level ? op_drop(cx, in, out_level) : op_copy(cx, in);
     for (int t = 0; t < pl.T; t++) {
         const int p = pl.p[t], k = pl.k[t];
         const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
@@ -636,19 +650,30 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         } else {
             Dp = he.mcr(D.get(), coef);
         }
+        // Goldschmidt pair packed in one ciphertext: slots [0, s/2) hold g,
+        // slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
+        const int half = slots / 2;
+        std::vector<double> vlo(slots, 0.0), vhi(slots, 0.0);
+        for (int i = 0; i < half; i++) vlo[i] = y0;
+        for (int i = half; i < slots; i++) vhi[i] = y0 / 2.0;
+        double *d_v = cx->d_dbl + 2 * cx->N();
         Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), 1.5);
-        Ct h = he.mcr(a.get(), y0 / 2.0);
-        Ct g;
-        if (k >= 2) g = he.mul_rescale(he.mcr(x.get(), y0).get(), a.get());
+        check_cuda(cudaMemcpyAsync(d_v, vlo.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
+        Ct P = he.mul_plain_rescale(x.get(), d_v, slots);
+        check_cuda(cudaMemcpyAsync(d_v, vhi.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
+        P = he.add_plain_vec(P.get(), d_v, slots);
+        P = he.mul_rescale(P.get(), a.get());
+        const u64 g_half = rot_galois(cx, half);
         for (int i = 2; i <= k; i++) {
-            if (h->level < 2) {
-                g = bootstrap_ct(cx, g.get());
-                h = bootstrap_ct(cx, h.get());
-            }
-            a = he.add_const(he.neg(he.mul_rescale(g.get(), h.get()).get()).get(), 1.5);
-            if (i < k) g = he.mul_rescale(g.get(), a.get());
-            h = he.mul_rescale(h.get(), a.get());
+            if (P->level < 2) P = bootstrap_ct(cx, P.get());
+            Ct Q = he.mul_rescale(P.get(), op_automorph(cx, P.get(), g_half).get());
+            P = he.mul_rescale(P.get(), he.add_const(he.neg(Q.get()).get(), 1.5).get());
         }
+        P = ensure(std::move(P), 1);
+        for (int i = 0; i < slots; i++) vhi[i] = i < half ? 0.0 : 1.0;
+        check_cuda(cudaMemcpyAsync(d_v, vhi.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
+        Ct hm = he.mul_plain_rescale(P.get(), d_v, slots);
+        Ct h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
         h = ensure(std::move(h), 1);
         Dp = ensure(std::move(Dp), 1);
         Ct u = he.mul_rescale(Dp.get(), h.get());

@@ -402,33 +402,43 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // ------------------------------------------------------------------ key switching
 // Approximate basis conversion: for every coefficient, y_a = [x_a*qhinv_a]_{q_a},
 // out_t = sum_a y_a * qhat[a][t] mod p_t.
-__global__ void k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
+// One thread per (coefficient, chunk of BCONV_CHUNK output rows): the n_in
+// products y_a = [x_a * qhinv_a]_{q_a} stay in registers (n_in <= 16).
+constexpr int BCONV_CHUNK = 4;
+__global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
-    const size_t total = (size_t)n_polys * n;
-    EW_LOOP(total) {
-        int poly = (int)(gi >> log_n);
-        size_t k = gi & (n - 1);
-        u64 y[16];
-        for (int a = 0; a < tab.n_in; a++) {
+    const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y % n_chunks, poly = blockIdx.y / n_chunks;
+    if (k >= n || poly >= n_polys) return;
+    u64 y[16];
+#pragma unroll
+    for (int a = 0; a < 16; a++) {
+        if (a < tab.n_in) {
             int r = poly * tab.n_in + a;
-            u64 x = in.row(r, log_n)[k];
-            y[a] = shoup_mul(x, tab.qhinv[a], tab.qhinv_sh[a], pc.m[in.prime(r)].q);
+            y[a] = shoup_mul(in.row(r, log_n)[k], tab.qhinv[a], tab.qhinv_sh[a], pc.m[in.prime(r)].q);
         }
-        for (int t = 0; t < tab.n_out; t++) {
-            int r = poly * tab.n_out + t;
-            u64 qt = pc.m[out.prime(r)].q, s = 0;
-            for (int a = 0; a < tab.n_in; a++)
+    }
+    const int t0 = chunk * BCONV_CHUNK, t1 = min(t0 + BCONV_CHUNK, tab.n_out);
+    for (int t = t0; t < t1; t++) {
+        int r = poly * tab.n_out + t;
+        u64 qt = pc.m[out.prime(r)].q, s = 0;
+#pragma unroll
+        for (int a = 0; a < 16; a++)
+            if (a < tab.n_in)
                 s = add_mod(s, shoup_mul(y[a], tab.qhat[a * tab.stride + t], tab.qhat_sh[a * tab.stride + t], qt), qt);
-            out.row(r, log_n)[k] = s;
-        }
+        out.row(r, log_n)[k] = s;
     }
 }
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_polys << log_n;
+    const size_t n = (size_t)1 << log_n;
+    const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
+    dim3 grid((unsigned)((n + 127) / 128), (unsigned)(n_chunks * n_polys));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     prof_begin(PROF_BCONV, s);
-    k_bconv<<<grid_for(t, 128), 128, 0, s>>>(out, in, tab, n_polys, log_n);
-    prof_end(PROF_BCONV, s, 8.0 * (tab.n_in + tab.n_out) * (double)n_polys * (double)(1 << log_n));
+    k_bconv<<<grid, 128, 0, s>>>(out, in, tab, n_polys, log_n);
+    prof_end(PROF_BCONV, s, 8.0 * (tab.n_in + tab.n_out) * (double)n_polys * (double)n);
 }
 
 __global__ void k_keyswitch_inner(KeyIP kp, int log_n) {

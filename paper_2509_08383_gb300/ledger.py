@@ -166,6 +166,9 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
         return sim.bootstrap(a) if a < need else a
 
     Y = nq - 1 if start_level is None else start_level
+    if plan.bootstrap:                    # the circuit computes on the bootstrap's output levels
+        K, r, d = boot
+        Y = min(Y, nq - 1 - 6 - (math.ceil(math.log2(d + 1)) + 1 + r))
     for t in range(plan.T):
         p, k = plan.p[t], plan.k[t]
         if plan.bootstrap:
@@ -180,15 +183,15 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
             x = ensure(mcr(V), 2)
             Dp = mcr(D)
             a = mcr(x)
-            h = mcr(a)
-            g = sim.mul(mcr(x), a) if k >= 2 else None
+            P = sim.mul(mcr(x), a)            # packed [g | h]
             for i in range(2, k + 1):
-                if h < 2:
-                    g, h = sim.bootstrap(g), sim.bootstrap(h)
-                a = sim.mul(g, h)
-                if i < k:
-                    g = sim.mul(g, a)
-                h = sim.mul(h, a)
+                if P < 2:
+                    P = sim.bootstrap(P)
+                Q = sim.mul(P, sim.rot(P))
+                P = sim.mul(P, Q)
+            P = ensure(P, 1)
+            hm = mcr(P)
+            h = sim.rot(hm)
             h, Dp = ensure(h, 1), ensure(Dp, 1)
             u = sim.mul(Dp, h)
             u = ensure(u, (p - 1).bit_length())
