@@ -98,114 +98,150 @@ static inline unsigned grid_for(size_t total, int per_block) {
 // (row pass).  Stage with m groups uses twiddle psi^brv(m + j/(2t)).
 // Inverse (Gentleman-Sande, [0,2q)) runs the same stages in reverse, then
 // multiplies by N^-1.
+// Each CTA transforms a tile of 16 independent sub-transforms of size
+// M = 2^LOGM (16 columns of R rows in the column pass, 16 rows of C entries in
+// the row pass) with M threads; every thread holds 16 entries in registers.
+// Round A covers the sub-transform's first four stages (distances M/2 ..
+// M/16): thread j owns entries j + (M/16) i.  Round B covers the remaining
+// LOGM - 4 stages (distances < 16): thread j owns entries 16 j + i.  The tile
+// passes through shared memory between rounds (row pass: one pad word per 16
+// entries to spread the banks).  Local stage s of a sub-transform is global
+// stage s (column pass) or LOGR + s (row pass); its twiddle index is
+// 2^s + r/(2t) (column) or R 2^s + row 2^s + c/(2t) (row), t = M >> (s+1).
 constexpr int NTT_TILE = 16;
-constexpr int NTT_THREADS = 256;
 
-template <int LOGR, int LOGC, bool FWD>
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_cols(Rows rows, NttTables tw) {
+template <bool FWD>
+__device__ __forceinline__ void bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q2) {
+    if (FWD) {  // Harvey CT, values in [0, 4q)
+        if (X >= q2) X -= q2;
+        u64 T = shoup_mul_lazy(Y, w, ws, q);
+        Y = X - T + q2;
+        X = X + T;
+    } else {    // Harvey GS, values in [0, 2q)
+        u64 S = X + Y;
+        if (S >= q2) S -= q2;
+        Y = shoup_mul_lazy(X - Y + q2, w, ws, q);
+        X = S;
+    }
+}
+
+template <int LOGR, int LOGC, bool FWD, bool COLS>
+__global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, NttTables tw) {
+    constexpr int LOGN = LOGR + LOGC, R = 1 << LOGR, C = 1 << LOGC;
+    constexpr int LOGM = COLS ? LOGR : LOGC, M = 1 << LOGM, TPS = M / 16;
+    constexpr int SMEM = COLS ? 16 * M : 16 * M + 16 * M / 16;  // row pass padded
+    __shared__ u64 sm[SMEM];
     const PrimeConsts &pc = c_pcs[rows.slot];
-    constexpr int R = 1 << LOGR, C = 1 << LOGC, LOGN = LOGR + LOGC, TC = NTT_TILE;
-    __shared__ u64 sm[R * TC];
     const int rb = blockIdx.y;
     u64 *x = rows.row(rb, LOGN);
     const int p = rows.prime(rb);
     const u64 q = pc.m[p].q, q2 = 2 * q;
-    const int c0 = blockIdx.x * TC;
-    for (int idx = threadIdx.x; idx < R * TC; idx += NTT_THREADS) {
-        int r = idx / TC, cc = idx % TC;
-        sm[idx] = x[(size_t)r * C + c0 + cc];
-    }
-    __syncthreads();
     const u64 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
     const u64 *Ws = (FWD ? tw.fwd_sh : tw.inv_sh) + ((size_t)p << LOGN);
-#pragma unroll 1
-    for (int st = 0; st < LOGR; st++) {
-        const int s = FWD ? st : LOGR - 1 - st;
-        const int m = 1 << s, tr = R >> (s + 1);
-        for (int b = threadIdx.x; b < (R / 2) * TC; b += NTT_THREADS) {
-            int cc = b % TC, bi = b / TC;
-            int grp = bi / tr, pos = bi % tr;
-            int r0 = grp * 2 * tr + pos;
-            u64 w = W[m + grp], ws = Ws[m + grp];
-            u64 X = sm[r0 * TC + cc], Y = sm[(r0 + tr) * TC + cc];
-            if (FWD) {
-                if (X >= q2) X -= q2;
-                u64 T = shoup_mul_lazy(Y, w, ws, q);
-                sm[r0 * TC + cc] = X + T;
-                sm[(r0 + tr) * TC + cc] = X - T + q2;
-            } else {
-                u64 S = X + Y;
-                if (S >= q2) S -= q2;
-                sm[r0 * TC + cc] = S;
-                sm[(r0 + tr) * TC + cc] = shoup_mul_lazy(X - Y + q2, w, ws, q);
-            }
-        }
-        __syncthreads();
-    }
-    if (FWD) {
-        for (int idx = threadIdx.x; idx < R * TC; idx += NTT_THREADS) {
-            int r = idx / TC, cc = idx % TC;
-            x[(size_t)r * C + c0 + cc] = sm[idx];  // lazy, finished by the row pass
+    const int tid = threadIdx.x;
+    // smem index of entry e of sub-transform `sub`
+    auto sidx = [&](int sub, int e) -> int {
+        if (COLS) return e * 16 + sub;
+        int a = sub * M + e;
+        return a + (a >> 4);
+    };
+    // global load of the tile (coalesced)
+    if (COLS) {
+        const int c0 = blockIdx.x * 16;
+        for (int idx = tid; idx < 16 * M; idx += M) {
+            int r = idx >> 4, cc = idx & 15;
+            sm[sidx(cc, r)] = x[(size_t)r * C + c0 + cc];
         }
     } else {
-        const u64 ni = pc.n_inv[p], nis = pc.n_inv_shoup[p];
-        for (int idx = threadIdx.x; idx < R * TC; idx += NTT_THREADS) {
-            int r = idx / TC, cc = idx % TC;
-            x[(size_t)r * C + c0 + cc] = shoup_mul(sm[idx], ni, nis, q);
-        }
+        const u64 *xr = x + (size_t)blockIdx.x * 16 * C;
+        for (int idx = tid; idx < 16 * M; idx += M) sm[sidx(idx / M, idx % M)] = xr[idx];
     }
-}
-
-template <int LOGR, int LOGC, bool FWD>
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_rows(Rows rows, NttTables tw) {
-    const PrimeConsts &pc = c_pcs[rows.slot];
-    constexpr int C = 1 << LOGC, LOGN = LOGR + LOGC, TR = NTT_TILE;
-    __shared__ u64 sm[TR * C];
-    const int rb = blockIdx.y;
-    u64 *x = rows.row(rb, LOGN) + (size_t)blockIdx.x * TR * C;
-    const int p = rows.prime(rb);
-    const u64 q = pc.m[p].q, q2 = 2 * q;
-    for (int idx = threadIdx.x; idx < TR * C; idx += NTT_THREADS) sm[idx] = x[idx];
     __syncthreads();
-    const u64 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
-    const u64 *Ws = (FWD ? tw.fwd_sh : tw.inv_sh) + ((size_t)p << LOGN);
-    const int rbase = blockIdx.x * TR;
-#pragma unroll 1
-    for (int st = 0; st < LOGC; st++) {
-        const int s = FWD ? st : LOGC - 1 - st;  // stage inside the row
-        const int t = C >> (s + 1);
-        const int m = (1 << LOGR) << s;
-        for (int b = threadIdx.x; b < TR * (C / 2); b += NTT_THREADS) {
-            int rr = b / (C / 2), bi = b % (C / 2);
-            int grp = bi / t, pos = bi % t;
-            int c0 = grp * 2 * t + pos;
-            int ti = m + ((rbase + rr) << s) + grp;
-            u64 w = W[ti], ws = Ws[ti];
-            u64 *pa = &sm[rr * C + c0];
-            u64 X = pa[0], Y = pa[t];
-            if (FWD) {
-                if (X >= q2) X -= q2;
-                u64 T = shoup_mul_lazy(Y, w, ws, q);
-                pa[0] = X + T;
-                pa[t] = X - T + q2;
-            } else {
-                u64 S = X + Y;
-                if (S >= q2) S -= q2;
-                pa[0] = S;
-                pa[t] = shoup_mul_lazy(X - Y + q2, w, ws, q);
+    // thread -> (sub-transform, position)
+    const int sub = COLS ? (tid & 15) : (tid / TPS);
+    const int j = COLS ? (tid >> 4) : (tid % TPS);
+    const int rowg = COLS ? 0 : blockIdx.x * 16 + sub;  // global row (row pass)
+    u64 v[16];
+    auto twid = [&](int s, int grp) -> int {  // twiddle index for local stage s, group grp
+        return COLS ? (1 << s) + grp : (R << s) + (rowg << s) + grp;
+    };
+    auto round_a = [&]() {  // stages 0..3, entries j + TPS i
+#pragma unroll
+        for (int st = 0; st < 4; st++) {
+            const int s = FWD ? st : 3 - st;
+            const int d = 8 >> s;  // distance in i
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                if ((i & d) == 0) {
+                    int ti = twid(s, i >> (4 - s));
+                    bfly<FWD>(v[i], v[i + d], W[ti], Ws[ti], q, q2);
+                }
             }
         }
-        __syncthreads();
-    }
+    };
+    auto round_b = [&]() {  // stages 4..LOGM-1, entries 16 j + i
+#pragma unroll
+        for (int st = 0; st < LOGM - 4; st++) {
+            const int s = FWD ? 4 + st : LOGM - 1 - st;
+            const int t = M >> (s + 1);  // distance (< 16)
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                if ((i & t) == 0) {
+                    int ti = twid(s, j * (8 / t) + i / (2 * t));
+                    bfly<FWD>(v[i], v[i + t], W[ti], Ws[ti], q, q2);
+                }
+            }
+        }
+    };
     if (FWD) {
-        for (int idx = threadIdx.x; idx < TR * C; idx += NTT_THREADS) {
-            u64 v = sm[idx];
-            if (v >= q2) v -= q2;
-            if (v >= q) v -= q;
-            x[idx] = v;
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, j + TPS * i)];
+        round_a();
+#pragma unroll
+        for (int i = 0; i < 16; i++) sm[sidx(sub, j + TPS * i)] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, 16 * j + i)];
+        round_b();
+        if (!COLS) {  // last stage of the forward transform: reduce to [0, q)
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                u64 t = v[i];
+                if (t >= q2) t -= q2;
+                if (t >= q) t -= q;
+                v[i] = t;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++) sm[sidx(sub, 16 * j + i)] = v[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, 16 * j + i)];
+        round_b();
+#pragma unroll
+        for (int i = 0; i < 16; i++) sm[sidx(sub, 16 * j + i)] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, j + TPS * i)];
+        round_a();
+        if (COLS) {  // end of the inverse transform: times N^-1, reduce to [0, q)
+            const u64 ni = pc.n_inv[p], nis = pc.n_inv_shoup[p];
+#pragma unroll
+            for (int i = 0; i < 16; i++) v[i] = shoup_mul(v[i], ni, nis, q);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++) sm[sidx(sub, j + TPS * i)] = v[i];
+    }
+    __syncthreads();
+    if (COLS) {
+        const int c0 = blockIdx.x * 16;
+        for (int idx = tid; idx < 16 * M; idx += M) {
+            int r = idx >> 4, cc = idx & 15;
+            x[(size_t)r * C + c0 + cc] = sm[sidx(cc, r)];
         }
     } else {
-        for (int idx = threadIdx.x; idx < TR * C; idx += NTT_THREADS) x[idx] = sm[idx];  // [0,2q), column pass ends it
+        u64 *xr = x + (size_t)blockIdx.x * 16 * C;
+        for (int idx = tid; idx < 16 * M; idx += M) xr[idx] = sm[sidx(idx / M, idx % M)];
     }
 }
 
@@ -215,11 +251,11 @@ static void ntt_launch(const Rows &rows, int n_rows, const NttTables &tw, bool f
     dim3 gc(C / NTT_TILE, n_rows), gr(R / NTT_TILE, n_rows);
     g_launches.fetch_add(2, std::memory_order_relaxed);
     if (fwd) {
-        k_ntt_cols<LOGR, LOGC, true><<<gc, NTT_THREADS, 0, s>>>(rows, tw);
-        k_ntt_rows<LOGR, LOGC, true><<<gr, NTT_THREADS, 0, s>>>(rows, tw);
+        k_ntt<LOGR, LOGC, true, true><<<gc, R, 0, s>>>(rows, tw);
+        k_ntt<LOGR, LOGC, true, false><<<gr, C, 0, s>>>(rows, tw);
     } else {
-        k_ntt_rows<LOGR, LOGC, false><<<gr, NTT_THREADS, 0, s>>>(rows, tw);
-        k_ntt_cols<LOGR, LOGC, false><<<gc, NTT_THREADS, 0, s>>>(rows, tw);
+        k_ntt<LOGR, LOGC, false, false><<<gr, C, 0, s>>>(rows, tw);
+        k_ntt<LOGR, LOGC, false, true><<<gc, R, 0, s>>>(rows, tw);
     }
 }
 
