@@ -258,6 +258,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2509_08383_gb300 import build, he
     from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import replicas
     build.build_library()
     log_n, qb, pb, dnum, pl, gen, desc, boot = workload(args.workload)
     if boot is not None:
@@ -308,10 +309,8 @@ def main():
     ks_led, nboot = g.ledger(reset=True)
     ks_by_level = {i: int(v) // args.steps for i, v in enumerate(ks_led) if v}
     ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
+    ms = replicas.max_over_ranks(ms, dist, device="cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     n_dom, ms_dom, bytes_dom = he.profile_read(dom)
     he.profile_enable(-1)
@@ -339,11 +338,7 @@ def main():
         t1 = time.perf_counter()
         if s >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e = ws * args.steps / sum(e2e_times)
-    if dist:
-        t = torch.tensor([sum(e2e_times)], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = ws * args.steps / float(t.item())
+    e2e = ws * args.steps / replicas.max_over_ranks(sum(e2e_times), dist, device="cuda")
 
     res = {"metric": METRIC, "value": value, "unit": "decodes/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -232,6 +232,7 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
 // EvalMod acts slot by slot.
 // ======================================================================
 #include <complex>
+#include <functional>
 #include <numeric>
 
 namespace he {
@@ -480,8 +481,13 @@ struct ChebEval {
             q[j] = 2.0 * c[G + j];
             r[G - j] -= c[G + j];
         }
-        Ct Q = eval(q, target);
-        Ct P = he.mul_rescale(Q.get(), T[G].get());
+        Ct P;
+        if (deg == G) {  // constant quotient: one constant multiplication of T_G
+            P = he.mcr(T[G].get(), q[0], target);
+        } else {
+            Ct Q = eval(q, target);
+            P = he.mul_rescale(Q.get(), T[G].get());
+        }
         Ct R = eval(r, P->scale);
         if (R->level > P->level) R = op_drop(cx, R.get(), P->level);
         return op_add(cx, P.get(), R.get(), false);
@@ -515,12 +521,38 @@ static Ct evalmod(HE &he, const he_ct *x, const Boot &B) {
     return c;
 }
 
-// level of a bootstrapped ciphertext: 3 (CoeffToSlot) + EvalMod depth + 3 below the top
+// Level bookkeeping of evalmod(): the baby-step giant-step series can use
+// one level less than ceil(log2(d+1)) + 1 for some degrees, so the output
+// level is found by replaying it.
+static int evalmod_out_level(int l0, int d, int r) {
+    int m = 1;
+    while (m * m <= d + 1) m *= 2;
+    int top = m;
+    while (2 * top <= d) top *= 2;
+    std::vector<int> T(std::max(m, top) + 1, 0);
+    T[1] = l0;
+    auto make = [&](int k) { T[k] = std::min(T[(k + 1) / 2], T[k / 2]) - 1; };
+    for (int k = 2; k < m; k++) make(k);
+    for (int g = m; g <= top; g *= 2) make(g);
+    std::function<int(int)> ev = [&](int deg) -> int {
+        if (deg < m) {
+            int lo = 1 << 30;
+            for (int k = 1; k <= deg; k++) lo = std::min(lo, T[k]);
+            return lo - 1;
+        }
+        int G = m;
+        while (2 * G <= deg) G *= 2;
+        if (deg == G) return T[G] - 1;
+        int Q = ev(deg - G);
+        return std::min(Q, T[G]) - 1;
+    };
+    return ev(d) - r;
+}
+
+// level of a bootstrapped ciphertext: 3 (CoeffToSlot) + EvalMod + 3 (SlotToCoeff) below the top
 int boot_out_level(he_ctx *cx) {
     const Boot &B = *cx->boot_state;
-    int lg = 0;
-    while ((1 << lg) < B.d + 1) lg++;
-    return cx->nq - 1 - 6 - (lg + 1 + B.r);
+    return evalmod_out_level(cx->nq - 1 - 3, B.d, B.r) - 3;
 }
 
 void boot_prepare(he_ctx *cx, int K, int r, int d) {

@@ -665,8 +665,7 @@ void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext) {
     const LevelTabs &T = cx->lv[l];
     cudaStream_t s = cx->stream;
     Rows coef = make_rows(cx->ks_coef, 0, l + 1, l + 1, cx->nq);
-    ew_copy(coef, make_rows((u64 *)d_ntt, 0, l + 1, l + 1, cx->nq), l + 1, log_n, s);
-    ntt_inverse(coef, l + 1, cx->tw, log_n, s);
+    ntt_inverse_from(coef, make_rows((u64 *)d_ntt, 0, l + 1, l + 1, cx->nq), l + 1, cx->tw, log_n, s);
     for (int j = 0; j < T.beta; j++) {
         int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
         Rows in = make_rows(cx->ks_coef + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
@@ -742,8 +741,7 @@ Ct op_rescale(he_ctx *cx, const he_ct *a) {
     // last limbs of c0, c1 -> coefficient form (scratch rows 0, 1)
     Rows last = make_rows(cx->sc_a, N, 1, 1, cx->nq, l);
     Rows src = make_rows(ct_poly(a, 0) + (size_t)l * N, (size_t)a->cap * N, 1, 1, cx->nq, l);
-    ew_copy(last, src, 2, cx->log_n, s);
-    ntt_inverse(last, 2, cx->tw, cx->log_n, s);
+    ntt_inverse_from(last, src, 2, cx->tw, cx->log_n, s);
     Rows lift = make_rows(cx->sc_b, (size_t)l * N, l, l, cx->nq);
     rescale_lift(lift, cx->sc_a, cx->sc_a + N, ql, l, cx->log_n, s);
     ntt_forward(lift, 2 * l, cx->tw, cx->log_n, s);

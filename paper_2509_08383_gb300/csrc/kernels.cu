@@ -126,7 +126,7 @@ __device__ __forceinline__ void bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q
 }
 
 template <int LOGR, int LOGC, bool FWD, bool COLS>
-__global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, NttTables tw) {
+__global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Rows src, NttTables tw) {
     constexpr int LOGN = LOGR + LOGC, R = 1 << LOGR, C = 1 << LOGC;
     constexpr int LOGM = COLS ? LOGR : LOGC, M = 1 << LOGM, TPS = M / 16;
     constexpr int SMEM = COLS ? 16 * M : 16 * M + 16 * M / 16;  // row pass padded
@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Nt
     const PrimeConsts &pc = c_pcs[rows.slot];
     const int rb = blockIdx.y;
     u64 *x = rows.row(rb, LOGN);
+    const u64 *xin = src.base ? src.row(rb, LOGN) : x;  // out-of-place first pass
     const int p = rows.prime(rb);
     const u64 q = pc.m[p].q, q2 = 2 * q;
     const u64 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
@@ -150,10 +151,10 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Nt
         const int c0 = blockIdx.x * 16;
         for (int idx = tid; idx < 16 * M; idx += M) {
             int r = idx >> 4, cc = idx & 15;
-            sm[sidx(cc, r)] = x[(size_t)r * C + c0 + cc];
+            sm[sidx(cc, r)] = xin[(size_t)r * C + c0 + cc];
         }
     } else {
-        const u64 *xr = x + (size_t)blockIdx.x * 16 * C;
+        const u64 *xr = xin + (size_t)blockIdx.x * 16 * C;
         for (int idx = tid; idx < 16 * M; idx += M) sm[sidx(idx / M, idx % M)] = xr[idx];
     }
     __syncthreads();
@@ -246,40 +247,51 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Nt
 }
 
 template <int LOGR, int LOGC>
-static void ntt_launch(const Rows &rows, int n_rows, const NttTables &tw, bool fwd, cudaStream_t s) {
+static void ntt_launch(const Rows &rows, const Rows &src, int n_rows, const NttTables &tw, bool fwd, cudaStream_t s) {
     constexpr int R = 1 << LOGR, C = 1 << LOGC;
     dim3 gc(C / NTT_TILE, n_rows), gr(R / NTT_TILE, n_rows);
+    Rows none = rows;
+    none.base = nullptr;
     g_launches.fetch_add(2, std::memory_order_relaxed);
     if (fwd) {
-        k_ntt<LOGR, LOGC, true, true><<<gc, R, 0, s>>>(rows, tw);
-        k_ntt<LOGR, LOGC, true, false><<<gr, C, 0, s>>>(rows, tw);
+        k_ntt<LOGR, LOGC, true, true><<<gc, R, 0, s>>>(rows, src, tw);
+        k_ntt<LOGR, LOGC, true, false><<<gr, C, 0, s>>>(rows, none, tw);
     } else {
-        k_ntt<LOGR, LOGC, false, false><<<gr, C, 0, s>>>(rows, tw);
-        k_ntt<LOGR, LOGC, false, true><<<gc, R, 0, s>>>(rows, tw);
+        k_ntt<LOGR, LOGC, false, false><<<gr, C, 0, s>>>(rows, src, tw);
+        k_ntt<LOGR, LOGC, false, true><<<gc, R, 0, s>>>(rows, none, tw);
     }
 }
 
-static void ntt_dispatch(const Rows &rows, int n_rows, const NttTables &tw, int log_n, bool fwd, cudaStream_t s) {
+static void ntt_dispatch(const Rows &rows, const Rows &src, int n_rows, const NttTables &tw, int log_n, bool fwd,
+                         cudaStream_t s) {
     if (n_rows <= 0) return;
     const int cls = fwd ? PROF_NTT_FWD : PROF_NTT_INV;
     prof_begin(cls, s);
     switch (log_n) {
-        case 10: ntt_launch<5, 5>(rows, n_rows, tw, fwd, s); break;
-        case 11: ntt_launch<5, 6>(rows, n_rows, tw, fwd, s); break;
-        case 12: ntt_launch<6, 6>(rows, n_rows, tw, fwd, s); break;
-        case 13: ntt_launch<6, 7>(rows, n_rows, tw, fwd, s); break;
-        case 14: ntt_launch<7, 7>(rows, n_rows, tw, fwd, s); break;
-        case 15: ntt_launch<7, 8>(rows, n_rows, tw, fwd, s); break;
-        case 16: ntt_launch<8, 8>(rows, n_rows, tw, fwd, s); break;
+        case 10: ntt_launch<5, 5>(rows, src, n_rows, tw, fwd, s); break;
+        case 11: ntt_launch<5, 6>(rows, src, n_rows, tw, fwd, s); break;
+        case 12: ntt_launch<6, 6>(rows, src, n_rows, tw, fwd, s); break;
+        case 13: ntt_launch<6, 7>(rows, src, n_rows, tw, fwd, s); break;
+        case 14: ntt_launch<7, 7>(rows, src, n_rows, tw, fwd, s); break;
+        case 15: ntt_launch<7, 8>(rows, src, n_rows, tw, fwd, s); break;
+        case 16: ntt_launch<8, 8>(rows, src, n_rows, tw, fwd, s); break;
         default: break;
     }
     prof_end(cls, s, 16.0 * (double)n_rows * (double)(1 << log_n));
 }
+static Rows no_src(const Rows &r) {
+    Rows n = r;
+    n.base = nullptr;
+    return n;
+}
 void ntt_forward(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s) {
-    ntt_dispatch(rows, n_rows, tw, log_n, true, s);
+    ntt_dispatch(rows, no_src(rows), n_rows, tw, log_n, true, s);
 }
 void ntt_inverse(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s) {
-    ntt_dispatch(rows, n_rows, tw, log_n, false, s);
+    ntt_dispatch(rows, no_src(rows), n_rows, tw, log_n, false, s);
+}
+void ntt_inverse_from(const Rows &dst, const Rows &src, int n_rows, const NttTables &tw, int log_n, cudaStream_t s) {
+    ntt_dispatch(dst, src, n_rows, tw, log_n, false, s);
 }
 
 // ------------------------------------------------------------------ elementwise

@@ -41,6 +41,8 @@ void upload_constants(int slot, const PrimeConsts &pc, const u64 *cdt, int n_cdt
 // NTT / INTT of n_rows limb rows in place.
 void ntt_forward(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s);
 void ntt_inverse(const Rows &rows, int n_rows, const NttTables &tw, int log_n, cudaStream_t s);
+// out-of-place INTT: dst <- INTT(src) (src rows read once, by the first pass)
+void ntt_inverse_from(const Rows &dst, const Rows &src, int n_rows, const NttTables &tw, int log_n, cudaStream_t s);
 
 // out = a + b / a - b (sub != 0) / -a (b ignored when neg != 0)
 void ew_add(const Rows &out, const Rows &a, const Rows &b, int n_rows, int sub, int log_n, cudaStream_t s);

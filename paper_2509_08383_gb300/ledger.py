@@ -111,8 +111,10 @@ class Sim:
             G = m
             while 2 * G <= deg:
                 G *= 2
-            Q = ev(deg - G)
-            P = self.mul(Q, T[G])
+            if deg == G:                  # constant quotient: a constant multiplication
+                P = T[G] - 1
+            else:
+                P = self.mul(ev(deg - G), T[G])
             ev(G - 1)
             return P
 
@@ -167,8 +169,7 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
 
     Y = nq - 1 if start_level is None else start_level
     if plan.bootstrap:                    # the circuit computes on the bootstrap's output levels
-        K, r, d = boot
-        Y = min(Y, nq - 1 - 6 - (math.ceil(math.log2(d + 1)) + 1 + r))
+        Y = min(Y, Sim(nq, log_n, boot).bootstrap(0))
     for t in range(plan.T):
         p, k = plan.p[t], plan.k[t]
         if plan.bootstrap:

@@ -24,7 +24,7 @@ build.build_library()
 LOG_N = 11
 QB = [55] + [40] * 3 + [60] * 3 + [60] * 10 + [58] * 3
 PB = [61] * 7
-H, K, R, D = 64, 14, 4, 27
+H, K, R, D = 64, 14, 4, 31
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def test_bootstrap_matches_message_and_oracle(boot_pair):
     assert (cg.export() == co.export()).all()
     bg = g.bootstrap(cg)
     bo = ob.bootstrap(co)
-    assert bg.level == bo.level == len(QB) - 1 - 16
+    assert bg.level == bo.level == len(QB) - 1 - 16   # d = 31: both evaluations take 6 + r levels
     dg = g.decrypt(bg, complex_out=True)
     do = oenc.decode(o.decrypt(bo), LOG_N, bo.scale)
     assert np.abs(dg - z).max() < 1e-6

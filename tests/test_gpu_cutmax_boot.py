@@ -25,7 +25,7 @@ build.build_library()
 LOG_N = 11
 QB = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
 PB = [61] * 10
-H, K, R, D = 64, 14, 4, 27
+H, K, R, D = 64, 14, 4, 31
 NV = 1000
 T, PW, CC = 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0]
 
