@@ -184,6 +184,11 @@ int he_bootstrap_prepare(he_ctx *ctx, uint32_t K, uint32_t r, uint32_t d);
 /* Refresh a ciphertext (any level; only limb q0 is used) to a high level,
  * encrypting the same message up to the bootstrapping error. */
 int he_bootstrap(he_ctx *ctx, const he_ct *in, he_ct **out);
+/* The ciphertext after one stage of he_bootstrap, for inspection: 0 ModRaise
+ * (scale declared q0 (K+1)), 1..3 after each CoeffToSlot level, 4 / 5 the
+ * real / imaginary part, 6 / 7 those after EvalMod, 8 recombined, 9 / 10 after
+ * the first two SlotToCoeff levels, 11 the result. */
+int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out);
 
 /* ---- CutMax (Alg. 2) and nucleus sampling (Alg. 3) ------------------- */
 /* Circuit plan: the range-scaling constants of Sect. 3.2's obligations.

@@ -152,6 +152,7 @@ int he_export_key(he_ctx *cx, uint64_t g, uint32_t digit, int32_t which, uint64_
     Rows tmp = make_rows(cx->ks_acc, 0, tot, cx->nq, cx->nq);
     Rows src = make_rows(k->data + (size_t)(2 * digit + which) * tot * N, 0, tot, cx->nq, cx->nq);
     ew_copy(tmp, src, tot, cx->log_n, cx->stream);
+    ew_mont(tmp, tot, 1, cx->log_n, cx->stream);  // keys are stored in Montgomery form
     ntt_inverse(tmp, tot, cx->tw, cx->log_n, cx->stream);
     check_cuda(cudaMemcpyAsync(out, cx->ks_acc, (size_t)tot * N * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
     sync(cx, "export key");
@@ -378,6 +379,16 @@ int he_bootstrap(he_ctx *cx, const he_ct *in, he_ct **out) {
     own(cx, in);
     Ct r = bootstrap_ct(cx, in);
     launched(cx, "bootstrap");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_bootstrap_stage(he_ctx *cx, const he_ct *in, int32_t stage, he_ct **out) {
+    if (!cx || !in || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, in);
+    Ct r = bootstrap_stage(cx, in, stage);
+    launched(cx, "bootstrap stage");
     *out = r.release();
     API_CATCH(cx)
 }

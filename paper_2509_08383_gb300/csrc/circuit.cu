@@ -154,6 +154,7 @@ void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois) {
 
 static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl);
 int boot_out_level(he_ctx *cx);
+Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage);
 
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
     const int slots = cx->n / 2;
@@ -444,12 +445,35 @@ static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
 // Chebyshev series sum_k c_k T_k(x) by baby steps T_1..T_(m-1) and giant
 // steps T_m, T_2m, T_4m, ...: a series of degree >= m is split by the largest
 // giant G <= degree as q T_G + r (T_G T_j = (T_(G+j) + T_(|G-j|))/2 gives
-// q_0 = c_G, q_j = 2 c_(G+j), r_(G-j) = c_(G-j) - c_(G+j)); q is evaluated
-// first, and r is aimed at the exact scale of the rescaled product q T_G.
+// q_0 = c_G, q_j = 2 c_(G+j), r_(G-j) = c_(G-j) - c_(G+j)).  Every call
+// lands on the scale it is asked for: q is aimed at target q_lp / scale(T_G),
+// q_lp the prime that rescales the product q T_G, so that the product comes
+// out at the target, and r is aimed at the product's scale.  (Two summands
+// whose declared scales differ by a relative e add with an error e |value|,
+// which the double-angle steps and the 1/(2 pi) read-out of bootstrapping
+// amplify by several orders of magnitude.)
 struct ChebEval {
     HE &he;
     std::vector<Ct> T;   // T_1..T_(m-1) and the giants (index k)
     int m;
+
+    int giant(int deg) const {
+        int G = m;
+        while (2 * G <= deg) G *= 2;
+        return G;
+    }
+
+    // level of eval()'s result for a series of degree deg
+    int out_level(int deg) const {
+        if (deg < m) {
+            int lo = 1 << 30;
+            for (int k = 1; k <= deg; k++) lo = std::min(lo, T[k]->level);
+            return lo - 1;
+        }
+        int G = giant(deg);
+        if (deg == G) return T[G]->level - 1;
+        return std::min(out_level(deg - G), T[G]->level) - 1;
+    }
 
     Ct baby_sum(const std::vector<double> &c, double target) {
         he_ctx *cx = he.cx;
@@ -473,8 +497,7 @@ struct ChebEval {
         he_ctx *cx = he.cx;
         int deg = (int)c.size() - 1;
         if (deg < m) return baby_sum(c, target);
-        int G = m;
-        while (2 * G <= deg) G *= 2;
+        int G = giant(deg);
         std::vector<double> q(deg - G + 1), r(c.begin(), c.begin() + G);
         q[0] = c[G];
         for (int j = 1; j <= deg - G; j++) {
@@ -485,7 +508,8 @@ struct ChebEval {
         if (deg == G) {  // constant quotient: one constant multiplication of T_G
             P = he.mcr(T[G].get(), q[0], target);
         } else {
-            Ct Q = eval(q, target);
+            const int lp = std::min(out_level(deg - G), T[G]->level);
+            Ct Q = eval(q, target * (double)cx->primes[lp] / T[G]->scale);
             P = he.mul_rescale(Q.get(), T[G].get());
         }
         Ct R = eval(r, P->scale);
@@ -607,7 +631,12 @@ void boot_prepare(he_ctx *cx, int K, int r, int d) {
     cx->boot_state = B;
 }
 
-Ct bootstrap_ct(he_ctx *cx, const he_ct *in) {
+Ct bootstrap_ct(he_ctx *cx, const he_ct *in) { return bootstrap_stage(cx, in, 100); }
+
+// stage: 0 ModRaise, 1..3 after CoeffToSlot level, 4 real part, 5 imaginary
+// part, 6 real part after EvalMod, 7 imaginary part after EvalMod, 8 combined,
+// 9..11 after SlotToCoeff level (11 = the bootstrapped result)
+Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
     auto B = cx->boot_state;
     if (!B) throw Error{HE_EINVAL, "bootstrapping not prepared"};
     HE he{cx, B->em_scale};
@@ -617,20 +646,32 @@ Ct bootstrap_ct(he_ctx *cx, const he_ct *in) {
     Ct low = in->level ? op_drop(cx, in, 0) : op_copy(cx, in);
     Ct x = op_mod_raise(cx, low.get(), cx->nq - 1);
     x->scale = (double)q0 * (double)(B->K + 1);
+    if (stage == 0) return x;
     // CoeffToSlot, aimed at half the EvalMod scale (the split doubles it)
-    for (int lv = 0; lv < 3; lv++) x = apply_level(cx, x.get(), B->cts[lv], B->em_scale / 2);
+    for (int lv = 0; lv < 3; lv++) {
+        x = apply_level(cx, x.get(), B->cts[lv], B->em_scale / 2);
+        if (stage == 1 + lv) return x;
+    }
     Ct xc = op_automorph(cx, x.get(), 2 * cx->N() - 1);
     Ct re = op_add(cx, x.get(), xc.get(), false);
     re->scale *= 2;
+    if (stage == 4) return re;
     Ct im = op_mul_monomial(cx, op_add(cx, x.get(), xc.get(), true).get(), 3 * cx->N() / 2);
     im->scale *= 2;
+    if (stage == 5) return im;
     re = evalmod(he, re.get(), *B);
+    if (stage == 6) return re;
     im = evalmod(he, im.get(), *B);
+    if (stage == 7) return im;
     Ct w = op_add(cx, re.get(), op_mul_monomial(cx, im.get(), cx->N() / 2).get(), false);
     // values sin(2 pi t/q0) ~ 2 pi m/q0: read them as m / s_fix
     w->scale = w->scale * (2.0 * M_PI * B->s_fix) / (double)q0;
+    if (stage == 8) return w;
     const double tg[3] = {std::ldexp(1.0, 50), std::ldexp(1.0, 45), cx->delta};
-    for (int lv = 0; lv < 3; lv++) w = apply_level(cx, w.get(), B->stc[lv], tg[lv]);
+    for (int lv = 0; lv < 3; lv++) {
+        w = apply_level(cx, w.get(), B->stc[lv], tg[lv]);
+        if (stage == 9 + lv && lv < 2) return w;
+    }
     w->scale = w->scale / ratio;
     return w;
 }

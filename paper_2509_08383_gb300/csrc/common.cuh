@@ -33,6 +33,7 @@ struct PrimeConsts {
     u64 n_inv[HE_MAX_PRIMES];
     u64 n_inv_shoup[HE_MAX_PRIMES];
     u64 r64[HE_MAX_PRIMES];  // 2^64 mod q
+    u64 mont_qinv[HE_MAX_PRIMES];  // -q^-1 mod 2^64 (Montgomery reduction)
     u64 cdt[24];             // rounded-Gaussian CDT thresholds
     int ncdt;
     int pad;
@@ -72,6 +73,13 @@ __device__ __forceinline__ u64 mul_add_mod(u64 a, u64 b, u64 c, u64 d, const Mod
     u64 hi = hi1 + hi2 + (lo < lo1 ? 1ull : 0ull);
     return barrett_reduce(lo, hi, m);
 }
+// Montgomery reduction of T = hi*2^64 + lo < q 2^64: T / 2^64 mod q in [0, q)
+__device__ __forceinline__ u64 mont_reduce(u64 lo, u64 hi, u64 q, u64 qinv_neg) {
+    u64 m = lo * qinv_neg;
+    u64 t = hi + __umul64hi(m, q) + (lo != 0 ? 1ull : 0ull);
+    return t >= q ? t - q : t;
+}
+
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
     u64 s = a + b;
     return s >= q ? s - q : s;

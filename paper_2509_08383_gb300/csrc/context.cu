@@ -269,6 +269,9 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     for (uint32_t i = 0; i < p->n_p; i++) bits.push_back(p->p_bits[i]);
     cx->primes = make_primes(cx->log_n, bits);
     const int tot = cx->nq + cx->np;
+    for (u64 q : cx->primes)  // the key-switch inner product sums beta products below q 2^64
+        if ((unsigned __int128)cx->beta * q >= ((unsigned __int128)1 << 64))
+            throw Error{HE_EINVAL, "dnum too large for the prime sizes (beta * q must stay below 2^64)"};
     const size_t N = cx->N();
 
     // arena
@@ -519,6 +522,8 @@ static void build_key(he_ctx *cx, u64 g, const u64 *d_sp /*[(nq+np)][N] NTT*/) {
         ew_mul_scalar(t2, sp, cx->p_mod, cnt, cx->log_n, s);
         ew_add(dig, dig, t2, cnt, 0, cx->log_n, s);
     }
+    // stored in Montgomery form for the key-switch inner product
+    ew_mont(make_rows(k.data, (size_t)tot * N, tot, cx->nq, cx->nq), 2 * cx->beta * tot, 0, cx->log_n, s);
     check_cuda(cudaGetLastError(), "key generation");
     cx->keys.push_back(k);
 }

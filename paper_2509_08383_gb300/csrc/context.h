@@ -162,6 +162,7 @@ void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois);
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl);
 void boot_prepare(he_ctx *cx, int K, int r, int d);
 Ct bootstrap_ct(he_ctx *cx, const he_ct *in);
+Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage);
 
 void check_cuda(cudaError_t e, const char *what);
 void release_slot(int slot);

@@ -20,6 +20,9 @@ void upload_constants(int slot, const PrimeConsts &pc_in, const u64 *cdt, int n_
     for (int i = 0; i < HE_MAX_PRIMES; i++) {
         u64 q = pc.m[i].q;
         pc.r64[i] = q ? (u64)(((unsigned __int128)1 << 64) % q) : 0;
+        u64 inv = 1;  // q^-1 mod 2^64 by Newton iteration (q odd)
+        for (int it = 0; it < 6; it++) inv *= 2 - q * inv;
+        pc.mont_qinv[i] = q ? (u64)0 - inv : 0;
     }
     for (int i = 0; i < n_cdt && i < 24; i++) pc.cdt[i] = cdt[i];
     pc.ncdt = n_cdt;
@@ -404,6 +407,24 @@ __global__ void k_monomial(Rows out, Rows a, int n_rows, u64 e, NttTables tw, in
         out.row(r, log_n)[i] = mul_mod(a.row(r, log_n)[i], w, m);
     }
 }
+// x -> x * 2^64 mod q (to Montgomery form) or x * 2^-64 mod q (back)
+__global__ void k_to_mont(Rows out, int n_rows, int back, int log_n) {
+    const PrimeConsts &pc = c_pcs[out.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        int r = (int)(gi >> log_n);
+        size_t k = gi & mask;
+        int p = out.prime(r);
+        const ModQ &m = pc.m[p];
+        u64 *x = out.row(r, log_n) + k;
+        *x = back ? mont_reduce(*x, 0, m.q, pc.mont_qinv[p]) : mul_mod(*x, pc.r64[p], m);
+    }
+}
+void ew_mont(const Rows &rows, int n_rows, int back, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_to_mont<<<grid_for(t, 256), 256, 0, s>>>(rows, n_rows, back, log_n);
+}
+
 void ew_monomial(const Rows &out, const Rows &a, int n_rows, u64 e, const NttTables &tw, int log_n, cudaStream_t s) {
     size_t t = (size_t)n_rows << log_n;
     k_monomial<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, e, tw, log_n);
@@ -504,17 +525,26 @@ __global__ void k_keyswitch_inner(KeyIP kp, int log_n) {
             src = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
         }
         int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
-        const ModQ &m = pc.m[p];
+        const u64 q = pc.m[p].q, qn = pc.mont_qinv[p];
         int jt = t < kp.l1 ? t / kp.alpha : -1;
-        u64 a0 = 0, a1 = 0;
+        // keys are in Montgomery form (times 2^64): the beta products are summed
+        // in 128 bits (< beta q^2 < q 2^64) and reduced once
+        u64 l0 = 0, h0 = 0, l1 = 0, h1 = 0;
         for (int j = 0; j < kp.beta; j++) {
             u64 x = (j == jt) ? kp.d_ntt[((size_t)t << log_n) + src]
                               : kp.ext[(((size_t)j * kp.n_rows + t) << log_n) + src];
             const u64 *kb = kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n);
             const u64 *ka = kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n);
-            a0 = add_mod(a0, mul_mod(x, kb[k], m), m.q);
-            a1 = add_mod(a1, mul_mod(x, ka[k], m), m.q);
+            u64 b = kb[k], a = ka[k];
+            u64 pl = x * b, ph = __umul64hi(x, b);
+            l0 += pl;
+            h0 += ph + (l0 < pl);
+            pl = x * a;
+            ph = __umul64hi(x, a);
+            l1 += pl;
+            h1 += ph + (l1 < pl);
         }
+        u64 a0 = mont_reduce(l0, h0, q, qn), a1 = mont_reduce(l1, h1, q, qn);
         kp.acc[((size_t)t << log_n) + k] = a0;
         kp.acc[(((size_t)kp.n_rows + t) << log_n) + k] = a1;
     }

@@ -59,6 +59,8 @@ void ew_mul_acc(const Rows &out, const Rows &a, const Rows &b, int n_rows, int l
 // out = a0 - a1 (*) b  (decryption / encryption building block)
 void ew_tensor(const Rows &d0, const Rows &d1, const Rows &d2, const Rows &a0, const Rows &a1,
                const Rows &b0, const Rows &b1, int n_rows, int log_n, cudaStream_t s);
+// in place: x -> x 2^64 mod q (back = 0) or x 2^-64 mod q (back = 1)
+void ew_mont(const Rows &rows, int n_rows, int back, int log_n, cudaStream_t s);
 // out = a * X^e (e < 2N) in NTT form
 void ew_monomial(const Rows &out, const Rows &a, int n_rows, u64 e, const NttTables &tw, int log_n, cudaStream_t s);
 // automorphism X -> X^g in NTT form (permutation of positions)

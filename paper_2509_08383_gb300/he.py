@@ -93,6 +93,7 @@ def lib():
             "he_ntt_device": [VP, VP, u32, u32, i32],
             "he_bootstrap_prepare": [VP, u32, u32, u32],
             "he_bootstrap": [VP, VP, PP],
+            "he_bootstrap_stage": [VP, VP, i32, PP],
             "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
             "nucleus_sample": [VP, VP, VP, C.POINTER(CPlan), PP],
@@ -351,6 +352,9 @@ class Context:
 
     def bootstrap(self, ct):
         return self._ct(lib().he_bootstrap, ct.ptr)
+
+    def bootstrap_stage(self, ct, stage):
+        return self._ct(lib().he_bootstrap_stage, ct.ptr, int(stage))
 
     # CutMax / nucleus
     def cutmax_prepare(self, plan):

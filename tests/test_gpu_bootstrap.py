@@ -65,3 +65,46 @@ def test_bootstrap_twice_and_from_higher_level(boot_pair):
     sq = g.rescale(g.mul(b1, b1))            # use a level, then refresh again
     b2 = g.bootstrap(sq)
     assert np.abs(g.decrypt(b2) - z * z).max() < 1e-5
+
+
+def _bitrev(n):
+    b = n.bit_length() - 1
+    return np.array([int(format(i, f"0{b}b")[::-1], 2) for i in range(n)])
+
+
+def test_bootstrap_stages(boot_pair):
+    """Each stage of the GPU bootstrapping against its closed form.
+
+    ModRaise gives t = m + q0 I; CoeffToSlot puts (t_j + i t_(j+h)) / (q0 (K+1))
+    in bit-reversed slot order; EvalMod gives sin(2 pi (K+1) x) of its input
+    slots (the Chebyshev series must not add more than ~1e-11, since the
+    read-out multiplies its error by q0 / (2 pi s_fix)); the recombined
+    ciphertext holds the message coefficients m / s_fix.
+    """
+    g, _, _ = boot_pair
+    h = g.slots
+    rng = np.random.default_rng(3)
+    z = rng.uniform(-1, 1, h)
+    delta = 2.0 ** 40
+    pt = oenc.encode(z, LOG_N, delta)
+    ct = g.encrypt_poly(pt, delta, 11, level=0)
+    br = _bitrev(h)
+    s0 = g.bootstrap_stage(ct, 0)
+    t = g.decrypt_poly(s0)
+    I = np.round((t - pt) / g.primes[0])
+    assert np.abs(t - pt - I * g.primes[0]).max() < 2 ** 12     # t = m + q0 I (+ encryption noise)
+    assert np.abs(I).max() <= K
+    cvec = ((t[:h] + 1j * t[h:]) / s0.scale)[br]
+    d3 = g.decrypt(g.bootstrap_stage(ct, 3), complex_out=True)
+    assert np.abs(d3 - cvec).max() < 1e-12
+    d4 = g.decrypt(g.bootstrap_stage(ct, 4), complex_out=True)
+    d5 = g.decrypt(g.bootstrap_stage(ct, 5), complex_out=True)
+    assert np.abs(d4 - cvec.real).max() < 1e-12
+    assert np.abs(d5 - cvec.imag).max() < 1e-12
+    d6 = g.decrypt(g.bootstrap_stage(ct, 6), complex_out=True)
+    d7 = g.decrypt(g.bootstrap_stage(ct, 7), complex_out=True)
+    assert np.abs(d6 - np.sin(2 * np.pi * (K + 1) * d4.real)).max() < 1e-11
+    assert np.abs(d7 - np.sin(2 * np.pi * (K + 1) * d5.real)).max() < 1e-11
+    d8 = g.decrypt(g.bootstrap_stage(ct, 8), complex_out=True)
+    mvec = ((pt[:h] + 1j * pt[h:]) / delta)[br]
+    assert np.abs(d8 - mvec).max() < 1e-7
