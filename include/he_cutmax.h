@@ -164,6 +164,22 @@ int he_rotsum(he_ctx *ctx, const he_ct *a, uint32_t steps, he_ct **out);
 /* Hybrid key switch of a raw polynomial: host d[(level+1)*N] coefficient
  * form -> host out0/out1[(level+1)*N] coefficient form, with key g. */
 int he_keyswitch_raw(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out0, uint64_t *out1);
+/* Key switch that allocates nothing, for callers that cannot allocate device
+ * memory on demand: cudaMalloc/cudaFree synchronise the device and can fail
+ * under fragmentation, so latency-critical serving code, or a process whose
+ * device memory is entirely reserved by another allocator, cannot get
+ * scratch space per call.  The paper has no counterpart.
+ * Computes the same hybrid key switch as he_keyswitch_raw, on DEVICE data:
+ * d[(level+1)*N] in NTT form -> out[2][level+1][N] in NTT form (key g, g = 0:
+ * relinearisation).  Scratch comes from one file-scope device array of 2^22
+ * 64-bit words (32 MiB) that every GPU loading the library holds until exit;
+ * a key switch needing more (words = (level+1)N + beta*n_ext*N + 2 n_ext N +
+ * 2 (level+1) N, n_ext = level+1+n_p) is rejected with HE_EINVAL.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress with
+ * that device current), so make that first call before any stream capture.
+ * All calls share the array and nothing in it needs clearing (every word is
+ * written before it is read); calls whose GPU work overlaps race on it. */
+int he_keyswitch_noalloc(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out);
 /* Negacyclic NTT (inverse != 0: INTT) in place on DEVICE data[n_limbs][N];
  * limb t uses prime prime_idx0 + t.  NTT form: position i holds
  * a(psi^(2 brv(i) + 1)), psi the canonical 2N-th root of that prime. */

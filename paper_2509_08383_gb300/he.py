@@ -91,6 +91,7 @@ def lib():
             "he_rotsum": [VP, VP, u32, PP],
             "he_keyswitch_raw": [VP, pu64, u32, u64, pu64, pu64],
             "he_ntt_device": [VP, VP, u32, u32, i32],
+            "he_keyswitch_noalloc": [VP, VP, u32, u64, VP],
             "he_bootstrap_prepare": [VP, u32, u32, u32],
             "he_bootstrap": [VP, VP, PP],
             "he_bootstrap_stage": [VP, VP, i32, PP],
@@ -338,6 +339,13 @@ class Context:
         o0, o1 = np.zeros_like(d), np.zeros_like(d)
         self._chk(lib().he_keyswitch_raw(self.ptr, _u64ptr(d), int(level), int(g), _u64ptr(o0), _u64ptr(o1)))
         return o0.reshape(level + 1, self.n), o1.reshape(level + 1, self.n)
+
+    def keyswitch_noalloc(self, d_tensor, level, g, out_tensor):
+        """Key switch on device tensors with the library's static scratch (no allocation):
+        d (level+1, N) NTT form -> out (2, level+1, N) NTT form."""
+        assert d_tensor.is_cuda and out_tensor.is_cuda
+        self._chk(lib().he_keyswitch_noalloc(self.ptr, C.c_void_p(d_tensor.data_ptr()), int(level), int(g),
+                                             C.c_void_p(out_tensor.data_ptr())))
 
     def ntt_device(self, tensor, prime_idx0, inverse=False):
         """In-place (I)NTT of a CUDA uint64/int64 tensor of shape (limbs, N)."""
