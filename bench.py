@@ -1,6 +1,6 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|mul16]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|mul16|boot16]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
@@ -240,19 +240,31 @@ def cpu_baseline(args, ks_by_level=None):
             "sample": "1 full CutMax decode of the bench workload on the oracle (ciphertext already encrypted)"}
 
 
-def run_mul16(args):
-    """Micro workload for kernel profiles: one homomorphic multiplication
-    (tensor product, hybrid key switch, rescale) at the top level of the
-    N=2^16 parameter set; the same kernels as a CutMax step at full size."""
+def run_micro(args):
+    """Micro workloads for kernel profiles at the N=2^16 parameter set (the
+    same kernels as a CutMax step at full size): mul16 = one homomorphic
+    multiplication (tensor product, hybrid key switch, rescale) at the top
+    level; boot16 = one bootstrapping of a level-0 ciphertext."""
     import torch
     from paper_2509_08383_gb300 import build, he
     build.build_library()
     torch.cuda.set_device(0)
-    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=4 << 30)
-    g.gen_relin_key()
+    boot = args.workload == "boot16"
+    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=(24 << 30) if boot else (4 << 30))
     rng = np.random.default_rng(0)
     slots = 1 << 15
-    cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, s) for s in range(2)]
+    if boot:
+        g.bootstrap_prepare(24, 4, 31)
+        cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, 0, level=0)]
+        op = lambda: g.bootstrap(cts[0])
+        metric, unit = "bootstraps/s (N=2^16, K=24, r=4, d=31, dnum=3)", "boot/s"
+        wl = "CKKS bootstrapping of a level-0 ciphertext, N=2^16, 31 primes + 10 special primes, h=192"
+    else:
+        g.gen_relin_key()
+        cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, s) for s in range(2)]
+        op = lambda: g.rescale(g.mul(cts[0], cts[1]))
+        metric, unit = "homomorphic multiplications/s (N=2^16, level 30, dnum=3)", "mul/s"
+        wl = "ciphertext product + relinearisation + rescale, N=2^16, 31 primes + 10 special primes"
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     nsteps = args.warmup + args.steps
@@ -261,17 +273,15 @@ def run_mul16(args):
         for s in range(nsteps):
             flush.zero_()
             ev[s][0].record(stream)
-            z = g.rescale(g.mul(cts[0], cts[1]))
+            z = op()
             ev[s][1].record(stream)
             del z
         torch.cuda.synchronize()
     ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
-    print(json.dumps({"metric": "homomorphic multiplications/s (N=2^16, level 30, dnum=3)",
-                      "value": 1000.0 / ms, "unit": "mul/s", "n_gpus": 1, "steps": args.steps,
+    print(json.dumps({"metric": metric, "value": 1000.0 / ms, "unit": unit, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                       "dtype": "u64", "data": "synthetic", "clocks": clk.summary(),
-                      "config": {"workload": "ciphertext product + relinearisation + rescale, N=2^16, "
-                                             "31 primes + 10 special primes", "l2": "flushed between steps"}}))
+                      "config": {"workload": wl, "l2": "flushed between steps"}}))
 
 
 def main():
@@ -280,13 +290,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "mul16"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "mul16", "boot16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "mul16":
-        return run_mul16(args)
+    if args.workload in ("mul16", "boot16"):
+        return run_micro(args)
 
     import torch
     dist, rank, ws = dist_setup(args)

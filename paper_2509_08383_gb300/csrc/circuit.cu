@@ -383,6 +383,7 @@ static void build_level(he_ctx *cx, LinLevel &L, int level, double scale_in, dou
         Rows pr = make_rows(L.pts + (size_t)p * (level + 1) * N, 0, level + 1, level + 1, cx->nq);
         load_intd(pr, level + 1, d_pt, cx->log_n, cx->stream);
         ntt_forward(pr, level + 1, cx->tw, cx->log_n, cx->stream);
+        ew_mont(pr, level + 1, 0, cx->log_n, cx->stream);  // Montgomery form for ew_diag_mac
         check_cuda(cudaStreamSynchronize(cx->stream), "build transform plaintexts");
     }
 }
@@ -418,24 +419,24 @@ static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
     if (ext) cx->arena.release(ext, ext_bytes);
     Ct acc;
     for (size_t g = 0; g < L.giant.size(); g++) {
-        Ct inner;
+        DiagMac dm;
+        dm.n = 0;
+        dm.slot = cx->slot;
         for (size_t b = 0; b < L.baby.size(); b++) {
             int p = L.idx[g][b];
             if (p < 0) continue;
+            if (dm.n == DIAG_MAC_MAX) throw Error{HE_EINVAL, "too many diagonals in one giant step"};
             const he_ct *src = b == 0 ? x : baby[b].get();
-            Rows pt = make_rows(L.pts + (size_t)p * (l + 1) * N, 0, l + 1, l + 1, cx->nq);
-            if (!inner) {
-                inner = Ct(ct_alloc(cx, l, x->scale * L.E));
-                for (int k = 0; k < 2; k++)
-                    ew_mul(make_rows(ct_poly(inner.get(), k), 0, l + 1, l + 1, cx->nq),
-                           make_rows(ct_poly(src, k), 0, l + 1, l + 1, cx->nq), pt, l + 1, cx->log_n, cx->stream);
-            } else {
-                for (int k = 0; k < 2; k++)
-                    ew_mul_acc(make_rows(ct_poly(inner.get(), k), 0, l + 1, l + 1, cx->nq),
-                               make_rows(ct_poly(src, k), 0, l + 1, l + 1, cx->nq), pt, l + 1, cx->log_n, cx->stream);
-            }
+            dm.c0[dm.n] = ct_poly(src, 0);
+            dm.c1[dm.n] = ct_poly(src, 1);
+            dm.pt[dm.n] = L.pts + (size_t)p * (l + 1) * N;
+            dm.n++;
         }
-        if (!inner) continue;
+        if (!dm.n) continue;
+        Ct inner(ct_alloc(cx, l, x->scale * L.E));
+        dm.out0 = ct_poly(inner.get(), 0);
+        dm.out1 = ct_poly(inner.get(), 1);
+        ew_diag_mac(dm, l + 1, cx->log_n, cx->stream);
         if (L.giant[g] % (cx->n / 2) != 0) inner = op_automorph(cx, inner.get(), rot_galois(cx, L.giant[g]));
         acc = acc ? op_add(cx, acc.get(), inner.get(), false) : std::move(inner);
     }

@@ -62,6 +62,13 @@ __device__ __forceinline__ u64 barrett_reduce(u64 lo, u64 hi, const ModQ &m) {
     if (r >= m.q) r -= m.q;
     return r;
 }
+// (hi 2^64 + lo) 2^-64 mod q, fully reduced, for any hi < 2^63 - q (the
+// Montgomery quotient step leaves a value < hi + q, which Barrett reduces)
+__device__ __forceinline__ u64 mont_reduce_wide(u64 lo, u64 hi, const ModQ &m, u64 qinv_neg) {
+    u64 mm = lo * qinv_neg;
+    u64 t = hi + __umul64hi(mm, m.q) + (lo != 0 ? 1ull : 0ull);
+    return barrett_reduce(t, 0, m);
+}
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const ModQ &m) {
     return barrett_reduce(a * b, __umul64hi(a, b), m);
 }

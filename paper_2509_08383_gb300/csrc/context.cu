@@ -319,21 +319,18 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
                 pw[k] = mulmod_host(pw[k - 1], psi, q);
                 ipw[k] = mulmod_host(ipw[k - 1], ipsi, q);
             }
-            u64 *f = &h[(size_t)i * N], *fs = &h[((size_t)tot + i) * N];
-            u64 *v = &h[((size_t)2 * tot + i) * N], *vs = &h[((size_t)3 * tot + i) * N];
+            u64 *f = &h[(size_t)2 * i * N], *v = &h[(size_t)2 * (tot + i) * N];  // (value, Shoup) pairs
             for (size_t k = 0; k < N; k++) {
                 u32 b = brv_host((u32)k, cx->log_n);
-                f[k] = pw[b];
-                fs[k] = shoup_host(f[k], q);
-                v[k] = ipw[b];
-                vs[k] = shoup_host(v[k], q);
+                f[2 * k] = pw[b];
+                f[2 * k + 1] = shoup_host(pw[b], q);
+                v[2 * k] = ipw[b];
+                v[2 * k + 1] = shoup_host(ipw[b], q);
             }
         }
         check_cuda(cudaMemcpy(cx->d_tw, h.data(), h.size() * 8, cudaMemcpyHostToDevice), "upload twiddles");
-        cx->tw.fwd = cx->d_tw;
-        cx->tw.fwd_sh = cx->d_tw + (size_t)tot * N;
-        cx->tw.inv = cx->d_tw + (size_t)2 * tot * N;
-        cx->tw.inv_sh = cx->d_tw + (size_t)3 * tot * N;
+        cx->tw.fwd = reinterpret_cast<const ulonglong2 *>(cx->d_tw);
+        cx->tw.inv = reinterpret_cast<const ulonglong2 *>(cx->d_tw + (size_t)2 * tot * N);
     }
 
     // scratch
@@ -407,7 +404,7 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
                 for (size_t u = 0; u < targets.size(); u++) {
                     int t = targets[u];
                     u64 pt = cx->primes[t <= l ? t : cx->nq + (t - l - 1)];
-                    tab.push_back(shoup_host(qh[(size_t)a * targets.size() + u], pt));
+                    tab.push_back((u64)(((u128)qh[(size_t)a * targets.size() + u] << 64) % pt));  // Montgomery form
                 }
             pend.push_back(pd);
         }
@@ -440,7 +437,8 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
             tab.push_back(v);
         }
     for (int a = 0; a < K; a++)
-        for (int i = 0; i < cx->nq; i++) tab.push_back(shoup_host(tab[md_qhat + (size_t)a * cx->nq + i], cx->primes[i]));
+        for (int i = 0; i < cx->nq; i++)  // Montgomery form
+            tab.push_back((u64)(((u128)tab[md_qhat + (size_t)a * cx->nq + i] << 64) % cx->primes[i]));
     memset(&cx->p_inv, 0, sizeof(cx->p_inv));
     memset(&cx->p_mod, 0, sizeof(cx->p_mod));
     for (int i = 0; i < cx->nq; i++) {
@@ -462,7 +460,7 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
         bt.qhinv = cx->d_tabs + pd.qhinv;
         bt.qhinv_sh = cx->d_tabs + pd.qhinv + pd.n_in;
         bt.qhat = cx->d_tabs + pd.qhat;
-        bt.qhat_sh = cx->d_tabs + pd.qhat + (size_t)pd.n_in * pd.n_out;
+        bt.qhat_mont = cx->d_tabs + pd.qhat + (size_t)pd.n_in * pd.n_out;
         bt.n_in = pd.n_in;
         bt.n_out = pd.n_out;
         bt.stride = pd.n_out;
@@ -472,7 +470,7 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     cx->moddown.qhinv = cx->d_tabs + md_off;
     cx->moddown.qhinv_sh = cx->d_tabs + md_off + K;
     cx->moddown.qhat = cx->d_tabs + md_qhat;
-    cx->moddown.qhat_sh = cx->d_tabs + md_qhat + (size_t)K * cx->nq;
+    cx->moddown.qhat_mont = cx->d_tabs + md_qhat + (size_t)K * cx->nq;
     cx->moddown.n_in = K;
     cx->moddown.n_out = cx->nq;
     cx->moddown.stride = cx->nq;

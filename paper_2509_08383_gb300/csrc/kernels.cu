@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "context.h"
 #include "kernels.h"
 
 namespace he {
@@ -106,81 +107,125 @@ static inline unsigned grid_for(size_t total, int per_block) {
 // the row pass) with M threads; every thread holds 16 entries in registers.
 // Round A covers the sub-transform's first four stages (distances M/2 ..
 // M/16): thread j owns entries j + (M/16) i.  Round B covers the remaining
-// LOGM - 4 stages (distances < 16): thread j owns entries 16 j + i.  The tile
-// passes through shared memory between rounds (row pass: one pad word per 16
-// entries to spread the banks).  Local stage s of a sub-transform is global
-// stage s (column pass) or LOGR + s (row pass); its twiddle index is
-// 2^s + r/(2t) (column) or R 2^s + row 2^s + c/(2t) (row), t = M >> (s+1).
+// LOGM - 4 stages (distances < 16): thread j owns entries 16 j + i.
+// Local stage s of a sub-transform is global stage s (column pass) or
+// LOGR + s (row pass); its twiddle index is 2^s + grp (column) or
+// 2^s (R + row) + grp (row), grp < 2^s.
+// The CTA first stages its tile and every twiddle pair (value, Shoup
+// companion) it will use in shared memory with asynchronous 16-byte copies:
+// the column pass shares the R - 1 twiddles of its stages among all columns;
+// the row pass needs, for stage s, the 16 * 2^s consecutive table entries
+// starting at 2^s (R + first row).  The butterflies then read only shared
+// memory.  Row-pass tiles carry two pad words per 16 entries, which keeps
+// 16-byte alignment and spreads round B's 16-byte reads over the banks.
 constexpr int NTT_TILE = 16;
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int LOGR, int LOGC, bool COLS>
+struct NttShape {
+    static constexpr int LOGM = COLS ? LOGR : LOGC, M = 1 << LOGM;
+    static constexpr int DATA = COLS ? 16 * M : 18 * M;       // u64 words
+    static constexpr int TW = COLS ? M : 16 * (M - 1);         // twiddle pairs
+    static constexpr size_t SMEM = (size_t)DATA * 8 + (size_t)TW * 16;
+};
+
 template <bool FWD>
-__device__ __forceinline__ void bfly(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q2) {
+__device__ __forceinline__ void bfly(u64 &X, u64 &Y, ulonglong2 w, u64 q, u64 q2) {
     if (FWD) {  // Harvey CT, values in [0, 4q)
         if (X >= q2) X -= q2;
-        u64 T = shoup_mul_lazy(Y, w, ws, q);
+        u64 T = shoup_mul_lazy(Y, w.x, w.y, q);
         Y = X - T + q2;
         X = X + T;
     } else {    // Harvey GS, values in [0, 2q)
         u64 S = X + Y;
         if (S >= q2) S -= q2;
-        Y = shoup_mul_lazy(X - Y + q2, w, ws, q);
+        Y = shoup_mul_lazy(X - Y + q2, w.x, w.y, q);
         X = S;
     }
 }
 
 template <int LOGR, int LOGC, bool FWD, bool COLS>
 __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Rows src, NttTables tw) {
+    using S = NttShape<LOGR, LOGC, COLS>;
     constexpr int LOGN = LOGR + LOGC, R = 1 << LOGR, C = 1 << LOGC;
-    constexpr int LOGM = COLS ? LOGR : LOGC, M = 1 << LOGM, TPS = M / 16;
-    constexpr int SMEM = COLS ? 16 * M : 16 * M + 16 * M / 16;  // row pass padded
-    __shared__ u64 sm[SMEM];
+    constexpr int LOGM = S::LOGM, M = S::M, TPS = M / 16;
+    extern __shared__ __align__(16) unsigned char ntt_smem[];
+    u64 *sm = reinterpret_cast<u64 *>(ntt_smem);
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(ntt_smem + (size_t)S::DATA * 8);
     const PrimeConsts &pc = c_pcs[rows.slot];
     const int rb = blockIdx.y;
     u64 *x = rows.row(rb, LOGN);
     const u64 *xin = src.base ? src.row(rb, LOGN) : x;  // out-of-place first pass
     const int p = rows.prime(rb);
     const u64 q = pc.m[p].q, q2 = 2 * q;
-    const u64 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
-    const u64 *Ws = (FWD ? tw.fwd_sh : tw.inv_sh) + ((size_t)p << LOGN);
+    const ulonglong2 *W = (FWD ? tw.fwd : tw.inv) + ((size_t)p << LOGN);
     const int tid = threadIdx.x;
-    // smem index of entry e of sub-transform `sub`
+    // smem word of entry e of sub-transform `sub`
     auto sidx = [&](int sub, int e) -> int {
         if (COLS) return e * 16 + sub;
         int a = sub * M + e;
-        return a + (a >> 4);
+        return a + 2 * (a >> 4);
     };
-    // global load of the tile (coalesced)
     if (COLS) {
         const int c0 = blockIdx.x * 16;
-        for (int idx = tid; idx < 16 * M; idx += M) {
-            int r = idx >> 4, cc = idx & 15;
-            sm[sidx(cc, r)] = xin[(size_t)r * C + c0 + cc];
+#pragma unroll 4
+        for (int idx = tid; idx < 8 * M; idx += M) {  // row r of the tile: 16 words at xin[r C + c0]
+            int r = idx >> 3, h = idx & 7;
+            cp_async16(sm + r * 16 + 2 * h, xin + (size_t)r * C + c0 + 2 * h);
         }
+        if (tid + 1 < M) cp_async16(stw + tid, W + tid + 1);
     } else {
         const u64 *xr = xin + (size_t)blockIdx.x * 16 * C;
-        for (int idx = tid; idx < 16 * M; idx += M) sm[sidx(idx / M, idx % M)] = xr[idx];
+#pragma unroll 4
+        for (int idx = tid; idx < 8 * M; idx += M) {
+            int a = 2 * idx;
+            cp_async16(sm + a + 2 * (a >> 4), xr + a);
+        }
+        const size_t r0 = (size_t)blockIdx.x * 16;
+#pragma unroll
+        for (int s = 0; s < LOGM; s++) {
+            const ulonglong2 *ws = W + ((R + r0) << s);
+            ulonglong2 *ds = stw + 16 * ((1 << s) - 1);
+            if (s < 4) {  // round A: one group per thread group of a row (broadcast reads)
+                for (int k = tid; k < (16 << s); k += M) cp_async16(ds + k, ws + k);
+            } else {      // round B: group j G + g of row `sub` stored at g TPS + j
+                constexpr int LT = LOGM - 4;  // log2 TPS
+                for (int k = tid; k < (16 << s); k += M) {
+                    const int sub_k = k >> s, grp = k & ((1 << s) - 1);
+                    const int jj = grp >> (s - LT), g = grp & ((1 << (s - LT)) - 1);
+                    cp_async16(ds + (sub_k << s) + (g << LT) + jj, ws + k);
+                }
+            }
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
     // thread -> (sub-transform, position)
     const int sub = COLS ? (tid & 15) : (tid / TPS);
     const int j = COLS ? (tid >> 4) : (tid % TPS);
-    const int rowg = COLS ? 0 : blockIdx.x * 16 + sub;  // global row (row pass)
-    u64 v[16];
-    auto twid = [&](int s, int grp) -> int {  // twiddle index for local stage s, group grp
-        return COLS ? (1 << s) + grp : (R << s) + (rowg << s) + grp;
+    auto twl = [&](int s, int grp) -> ulonglong2 {  // local stage s, group grp
+        if (COLS) return stw[(1 << s) - 1 + grp];
+        return stw[16 * ((1 << s) - 1) + (sub << s) + grp];
     };
+    // row pass, round B: group j G + g (G = 2^s / TPS), stored transposed
+    auto twl_b = [&](int s, int g) -> ulonglong2 {
+        if (COLS) return stw[(1 << s) - 1 + j * ((1 << s) / TPS) + g];
+        return stw[16 * ((1 << s) - 1) + (sub << s) + g * TPS + j];
+    };
+    u64 v[16];
     auto round_a = [&]() {  // stages 0..3, entries j + TPS i
 #pragma unroll
         for (int st = 0; st < 4; st++) {
             const int s = FWD ? st : 3 - st;
             const int d = 8 >> s;  // distance in i
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                if ((i & d) == 0) {
-                    int ti = twid(s, i >> (4 - s));
-                    bfly<FWD>(v[i], v[i + d], W[ti], Ws[ti], q, q2);
-                }
-            }
+            for (int i = 0; i < 16; i++)
+                if ((i & d) == 0) bfly<FWD>(v[i], v[i + d], twl(s, i >> (4 - s)), q, q2);
         }
     };
     auto round_b = [&]() {  // stages 4..LOGM-1, entries 16 j + i
@@ -189,23 +234,48 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Ro
             const int s = FWD ? 4 + st : LOGM - 1 - st;
             const int t = M >> (s + 1);  // distance (< 16)
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                if ((i & t) == 0) {
-                    int ti = twid(s, j * (8 / t) + i / (2 * t));
-                    bfly<FWD>(v[i], v[i + t], W[ti], Ws[ti], q, q2);
-                }
+            for (int i = 0; i < 16; i++)
+                if ((i & t) == 0) bfly<FWD>(v[i], v[i + t], twl_b(s, i / (2 * t)), q, q2);
+        }
+    };
+    auto load_a = [&]() {
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, j + TPS * i)];
+    };
+    auto store_a = [&]() {
+#pragma unroll
+        for (int i = 0; i < 16; i++) sm[sidx(sub, j + TPS * i)] = v[i];
+    };
+    auto load_b = [&]() {
+        if (COLS) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, 16 * j + i)];
+        } else {
+            const ulonglong2 *p2 = reinterpret_cast<const ulonglong2 *>(sm + sidx(sub, 16 * j));
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                ulonglong2 t2 = p2[i];
+                v[2 * i] = t2.x;
+                v[2 * i + 1] = t2.y;
             }
         }
     };
+    auto store_b = [&]() {
+        if (COLS) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) sm[sidx(sub, 16 * j + i)] = v[i];
+        } else {
+            ulonglong2 *p2 = reinterpret_cast<ulonglong2 *>(sm + sidx(sub, 16 * j));
+#pragma unroll
+            for (int i = 0; i < 8; i++) p2[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
+        }
+    };
     if (FWD) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, j + TPS * i)];
+        load_a();
         round_a();
-#pragma unroll
-        for (int i = 0; i < 16; i++) sm[sidx(sub, j + TPS * i)] = v[i];
+        store_a();
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, 16 * j + i)];
+        load_b();
         round_b();
         if (!COLS) {  // last stage of the forward transform: reduce to [0, q)
 #pragma unroll
@@ -216,58 +286,80 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Ro
                 v[i] = t;
             }
         }
-#pragma unroll
-        for (int i = 0; i < 16; i++) sm[sidx(sub, 16 * j + i)] = v[i];
+        store_b();
     } else {
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, 16 * j + i)];
+        load_b();
         round_b();
-#pragma unroll
-        for (int i = 0; i < 16; i++) sm[sidx(sub, 16 * j + i)] = v[i];
+        store_b();
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = sm[sidx(sub, j + TPS * i)];
+        load_a();
         round_a();
         if (COLS) {  // end of the inverse transform: times N^-1, reduce to [0, q)
             const u64 ni = pc.n_inv[p], nis = pc.n_inv_shoup[p];
 #pragma unroll
             for (int i = 0; i < 16; i++) v[i] = shoup_mul(v[i], ni, nis, q);
         }
-#pragma unroll
-        for (int i = 0; i < 16; i++) sm[sidx(sub, j + TPS * i)] = v[i];
+        store_a();
     }
     __syncthreads();
     if (COLS) {
         const int c0 = blockIdx.x * 16;
-        for (int idx = tid; idx < 16 * M; idx += M) {
-            int r = idx >> 4, cc = idx & 15;
-            x[(size_t)r * C + c0 + cc] = sm[sidx(cc, r)];
+#pragma unroll 4
+        for (int idx = tid; idx < 8 * M; idx += M) {
+            int r = idx >> 3, h = idx & 7;
+            *reinterpret_cast<ulonglong2 *>(x + (size_t)r * C + c0 + 2 * h) =
+                *reinterpret_cast<const ulonglong2 *>(sm + r * 16 + 2 * h);
         }
     } else {
         u64 *xr = x + (size_t)blockIdx.x * 16 * C;
-        for (int idx = tid; idx < 16 * M; idx += M) xr[idx] = sm[sidx(idx / M, idx % M)];
+#pragma unroll 4
+        for (int idx = tid; idx < 8 * M; idx += M) {
+            int a = 2 * idx;
+            *reinterpret_cast<ulonglong2 *>(xr + a) = *reinterpret_cast<const ulonglong2 *>(sm + a + 2 * (a >> 4));
+        }
     }
+}
+
+// dynamic shared memory above 48 KB is an opt-in attribute, set once per device
+template <typename K>
+static void ntt_smem_attr(K kern, size_t bytes, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+               "NTT shared memory attribute");
+    done.fetch_or(bit, std::memory_order_release);
 }
 
 template <int LOGR, int LOGC>
 static void ntt_launch(const Rows &rows, const Rows &src, int n_rows, const NttTables &tw, bool fwd, cudaStream_t s) {
     constexpr int R = 1 << LOGR, C = 1 << LOGC;
+    using SC = NttShape<LOGR, LOGC, true>;
+    using SR = NttShape<LOGR, LOGC, false>;
+    static std::atomic<unsigned long long> done[4];
     dim3 gc(C / NTT_TILE, n_rows), gr(R / NTT_TILE, n_rows);
     Rows none = rows;
     none.base = nullptr;
     g_launches.fetch_add(2, std::memory_order_relaxed);
     if (fwd) {
-        k_ntt<LOGR, LOGC, true, true><<<gc, R, 0, s>>>(rows, src, tw);
-        k_ntt<LOGR, LOGC, true, false><<<gr, C, 0, s>>>(rows, none, tw);
+        ntt_smem_attr(k_ntt<LOGR, LOGC, true, true>, SC::SMEM, done[0]);
+        ntt_smem_attr(k_ntt<LOGR, LOGC, true, false>, SR::SMEM, done[1]);
+        k_ntt<LOGR, LOGC, true, true><<<gc, R, SC::SMEM, s>>>(rows, src, tw);
+        k_ntt<LOGR, LOGC, true, false><<<gr, C, SR::SMEM, s>>>(rows, none, tw);
     } else {
-        k_ntt<LOGR, LOGC, false, false><<<gr, C, 0, s>>>(rows, src, tw);
-        k_ntt<LOGR, LOGC, false, true><<<gc, R, 0, s>>>(rows, none, tw);
+        ntt_smem_attr(k_ntt<LOGR, LOGC, false, false>, SR::SMEM, done[2]);
+        ntt_smem_attr(k_ntt<LOGR, LOGC, false, true>, SC::SMEM, done[3]);
+        k_ntt<LOGR, LOGC, false, false><<<gr, C, SR::SMEM, s>>>(rows, src, tw);
+        k_ntt<LOGR, LOGC, false, true><<<gc, R, SC::SMEM, s>>>(rows, none, tw);
     }
 }
 
 static void ntt_dispatch(const Rows &rows, const Rows &src, int n_rows, const NttTables &tw, int log_n, bool fwd,
                          cudaStream_t s) {
     if (n_rows <= 0) return;
+    if ((reinterpret_cast<uintptr_t>(rows.base) & 15) || (reinterpret_cast<uintptr_t>(src.base) & 15))
+        throw Error{HE_EINVAL, "NTT data must start on a 16-byte boundary"};
     const int cls = fwd ? PROF_NTT_FWD : PROF_NTT_INV;
     prof_begin(cls, s);
     switch (log_n) {
@@ -363,6 +455,43 @@ __global__ void k_mul(Rows out, Rows a, Rows b, int n_rows, int acc, int log_n) 
         *o = acc ? add_mod(*o, v, m.q) : v;
     }
 }
+// out_k = sum_b src_b,k * pt_b (k = 0, 1: both polynomials of a ciphertext),
+// plaintexts in Montgomery form: the products are summed in 128 bits and each
+// output is reduced once.
+__global__ void k_diag_mac(DiagMac dm, int n_rows, int log_n) {
+    const PrimeConsts &pc = c_pcs[dm.slot];
+    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+    EW_LOOP(total) {
+        const int r = (int)(gi >> log_n);
+        const size_t k = gi & mask, off = ((size_t)r << log_n) + k;
+        const ModQ &m = pc.m[r];
+        u64 s0 = 0, s1 = 0;
+        for (int b0 = 0; b0 < dm.n; b0 += 16) {  // at most 16 products (< 2^126) per 128-bit sum
+            u64 l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+            const int b1 = min(dm.n, b0 + 16);
+            for (int b = b0; b < b1; b++) {
+                const u64 w = dm.pt[b][off];
+                const u64 x0 = dm.c0[b][off], x1 = dm.c1[b][off];
+                u64 pl = x0 * w, ph = __umul64hi(x0, w);
+                l0 += pl;
+                h0 += ph + (l0 < pl ? 1ull : 0ull);
+                pl = x1 * w;
+                ph = __umul64hi(x1, w);
+                l1 += pl;
+                h1 += ph + (l1 < pl ? 1ull : 0ull);
+            }
+            s0 = add_mod(s0, mont_reduce_wide(l0, h0, m, pc.mont_qinv[r]), m.q);
+            s1 = add_mod(s1, mont_reduce_wide(l1, h1, m, pc.mont_qinv[r]), m.q);
+        }
+        dm.out0[off] = s0;
+        dm.out1[off] = s1;
+    }
+}
+void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s) {
+    size_t t = (size_t)n_rows << log_n;
+    k_diag_mac<<<grid_for(t, 256), 256, 0, s>>>(dm, n_rows, log_n);
+}
+
 __global__ void k_tensor(Rows d0, Rows d1, Rows d2, Rows a0, Rows a1, Rows b0, Rows b1, int n_rows, int log_n) {
     const PrimeConsts &pc = c_pcs[d0.slot];
     const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
@@ -402,8 +531,8 @@ __global__ void k_monomial(Rows out, Rows a, int n_rows, u64 e, NttTables tw, in
         int p = out.prime(r);
         const ModQ &m = pc.m[p];
         u64 x = ((2ull * (__brev(i) >> (32 - log_n)) + 1) * e) & two_n_mask;
-        const u64 *fw = tw.fwd + ((size_t)p << log_n);
-        u64 w = x < n ? fw[__brev((u32)x) >> (32 - log_n)] : m.q - fw[__brev((u32)(x - n)) >> (32 - log_n)];
+        const ulonglong2 *fw = tw.fwd + ((size_t)p << log_n);
+        u64 w = x < n ? fw[__brev((u32)x) >> (32 - log_n)].x : m.q - fw[__brev((u32)(x - n)) >> (32 - log_n)].x;
         out.row(r, log_n)[i] = mul_mod(a.row(r, log_n)[i], w, m);
     }
 }
@@ -471,33 +600,55 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // ------------------------------------------------------------------ key switching
 // Approximate basis conversion: for every coefficient, y_a = [x_a*qhinv_a]_{q_a},
 // out_t = sum_a y_a * qhat[a][t] mod p_t.
-// One thread per (coefficient, chunk of BCONV_CHUNK output rows): the n_in
-// products y_a = [x_a * qhinv_a]_{q_a} stay in registers (n_in <= 16).
-constexpr int BCONV_CHUNK = 4;
+// One thread per (coefficient, chunk of BCONV_CHUNK output rows).  The
+// products y_a * (qhat[a][t] 2^64 mod p_t) are summed in 128 bits (n_in <= 16
+// terms below 2^122 each) and each output is reduced once, by a Montgomery
+// step and a Barrett correction.  The chunk's constants sit in shared memory
+// (every thread reads the same word: broadcasts).
+constexpr int BCONV_CHUNK = 8;
 __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
+    __shared__ u64 s_qh[16 * BCONV_CHUNK];
+    __shared__ u64 s_qi[16], s_qis[16], s_q[16];
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
-    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y % n_chunks, poly = blockIdx.y / n_chunks;
+    const int t0 = chunk * BCONV_CHUNK, nt = min(BCONV_CHUNK, tab.n_out - t0);
+    for (int i = threadIdx.x; i < 16 * BCONV_CHUNK; i += blockDim.x) {
+        int a = i / BCONV_CHUNK, c = i % BCONV_CHUNK;
+        s_qh[i] = (a < tab.n_in && c < nt) ? tab.qhat_mont[a * tab.stride + t0 + c] : 0;
+    }
+    if (threadIdx.x < 16) {
+        int a = threadIdx.x;
+        bool ok = a < tab.n_in && poly < n_polys;
+        s_qi[a] = ok ? tab.qhinv[a] : 0;
+        s_qis[a] = ok ? tab.qhinv_sh[a] : 0;
+        s_q[a] = ok ? pc.m[in.prime(poly * tab.n_in + a)].q : 1;
+    }
+    __syncthreads();
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || poly >= n_polys) return;
-    u64 y[16];
+    u64 lo[BCONV_CHUNK], hi[BCONV_CHUNK];
 #pragma unroll
-    for (int a = 0; a < 16; a++) {
-        if (a < tab.n_in) {
-            int r = poly * tab.n_in + a;
-            y[a] = shoup_mul(in.row(r, log_n)[k], tab.qhinv[a], tab.qhinv_sh[a], pc.m[in.prime(r)].q);
+    for (int c = 0; c < BCONV_CHUNK; c++) lo[c] = hi[c] = 0;
+#pragma unroll 2
+    for (int a = 0; a < tab.n_in; a++) {
+        const u64 y = shoup_mul(in.row(poly * tab.n_in + a, log_n)[k], s_qi[a], s_qis[a], s_q[a]);
+#pragma unroll
+        for (int c = 0; c < BCONV_CHUNK; c++) {
+            const u64 w = s_qh[a * BCONV_CHUNK + c];
+            const u64 pl = y * w, ph = __umul64hi(y, w);
+            lo[c] += pl;
+            hi[c] += ph + (lo[c] < pl ? 1ull : 0ull);
         }
     }
-    const int t0 = chunk * BCONV_CHUNK, t1 = min(t0 + BCONV_CHUNK, tab.n_out);
-    for (int t = t0; t < t1; t++) {
-        int r = poly * tab.n_out + t;
-        u64 qt = pc.m[out.prime(r)].q, s = 0;
 #pragma unroll
-        for (int a = 0; a < 16; a++)
-            if (a < tab.n_in)
-                s = add_mod(s, shoup_mul(y[a], tab.qhat[a * tab.stride + t], tab.qhat_sh[a * tab.stride + t], qt), qt);
-        out.row(r, log_n)[k] = s;
+    for (int c = 0; c < BCONV_CHUNK; c++) {
+        if (c < nt) {
+            const int r = poly * tab.n_out + t0 + c;
+            const int p = out.prime(r);
+            out.row(r, log_n)[k] = mont_reduce_wide(lo[c], hi[c], pc.m[p], pc.mont_qinv[p]);
+        }
     }
 }
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s) {

@@ -9,7 +9,7 @@
 namespace he {
 
 struct NttTables {
-    const u64 *fwd, *fwd_sh, *inv, *inv_sh;  // [prime][N]
+    const ulonglong2 *fwd, *inv;  // [prime][N] pairs (twiddle, Shoup companion)
 };
 
 // Residues of one constant for every prime (value and Shoup companion).
@@ -19,10 +19,11 @@ struct ScalarTab {
 };
 
 // Basis-conversion table: for input a < n_in and output row t < n_out,
-// qhat[a*stride + t] (+ Shoup) and qhinv[a] (+ Shoup), device memory.
+// qhat[a*stride + t] and its Montgomery form qhat * 2^64 mod p_t, and
+// qhinv[a] (+ Shoup), device memory.
 struct BConvTab {
-    const u64 *qhinv, *qhinv_sh;  // [n_in]
-    const u64 *qhat, *qhat_sh;    // [n_in][stride]
+    const u64 *qhinv, *qhinv_sh;    // [n_in]
+    const u64 *qhat, *qhat_mont;    // [n_in][stride]
     int n_in, n_out, stride;
 };
 
@@ -53,6 +54,16 @@ void ew_mul_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_row
 // out = a + K in every position (NTT form of a constant polynomial)
 void ew_add_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s);
 // out = a (*) b pointwise
+// Plaintext-diagonal multiply-accumulate of one baby-step giant-step group:
+// out0/out1 = sum_{b < n} c0[b]/c1[b] * pt[b], limb-major rows 0..n_rows-1 on
+// the Q chain (row r uses prime r), plaintexts in Montgomery form (x 2^64).
+constexpr int DIAG_MAC_MAX = 64;
+struct DiagMac {
+    const u64 *c0[DIAG_MAC_MAX], *c1[DIAG_MAC_MAX], *pt[DIAG_MAC_MAX];
+    u64 *out0, *out1;
+    int n, slot;
+};
+void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s);
 void ew_mul(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s);
 // out = out + a (*) b pointwise
 void ew_mul_acc(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s);
