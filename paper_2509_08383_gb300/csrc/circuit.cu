@@ -320,8 +320,10 @@ static void bsgs_layout(LinLevel &L, int h) {
     if (u == 0) u = 1;
     int mmin = 1 << 30, mmax = -(1 << 30);
     for (int r : so) { mmin = std::min(mmin, r / u); mmax = std::max(mmax, r / u); }
+    // baby steps only cost an inner product (their ModDown is hoisted), giant
+    // steps a full key switch: take bs^2 >= 4 span (more babies, fewer giants)
     int span = mmax - mmin + 1, bs = 1;
-    while ((long)bs * bs < span) bs <<= 1;
+    while ((long)bs * bs < 4L * span) bs <<= 1;
     int ng = (span + bs - 1) / bs;
     L.baby.clear();
     L.giant.clear();
@@ -365,7 +367,8 @@ static void build_level(he_ctx *cx, LinLevel &L, int level, double scale_in, dou
     L.target = target;
     L.E = (target * (double)cx->primes[level]) / scale_in;
     const int npt = (int)L.offs.size();
-    L.pts_bytes = (size_t)npt * (level + 1) * N * 8;
+    const int ne = cx->lv[level].n_ext;  // plaintexts live in the QP basis
+    L.pts_bytes = (size_t)npt * ne * N * 8;
     L.pts = (u64 *)cx->arena.alloc(L.pts_bytes);
     std::vector<double> re(h), im(h);
     for (int p = 0; p < npt; p++) {
@@ -380,67 +383,110 @@ static void build_level(he_ctx *cx, LinLevel &L, int level, double scale_in, dou
         check_cuda(cudaMemcpyAsync(d_re, re.data(), h * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
         check_cuda(cudaMemcpyAsync(d_im, im.data(), h * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
         encode_dev(cx, d_re, d_im, h, L.E, d_pt);
-        Rows pr = make_rows(L.pts + (size_t)p * (level + 1) * N, 0, level + 1, level + 1, cx->nq);
-        load_intd(pr, level + 1, d_pt, cx->log_n, cx->stream);
-        ntt_forward(pr, level + 1, cx->tw, cx->log_n, cx->stream);
-        ew_mont(pr, level + 1, 0, cx->log_n, cx->stream);  // Montgomery form for ew_diag_mac
+        Rows pr = make_rows(L.pts + (size_t)p * ne * N, 0, ne, level + 1, cx->nq);
+        load_intd(pr, ne, d_pt, cx->log_n, cx->stream);
+        ntt_forward(pr, ne, cx->tw, cx->log_n, cx->stream);
+        ew_mont(pr, ne, 0, cx->log_n, cx->stream);  // Montgomery form for ew_diag_mac
         check_cuda(cudaStreamSynchronize(cx->stream), "build transform plaintexts");
     }
 }
 
-// sum_g rot_G( sum_b pt[g][b] * rot_b(x) ), one rescale
+// sum_g rot_G( sum_b pt[g][b] * rot_b(x) ), one rescale, with both key-switch
+// halves hoisted: one ModUp of c1 serves every baby step; the baby-step
+// rotations stay in the QP basis as P rot_b(x) (inner product with the key
+// plus P sigma_b(c0), no ModDown), the plaintext diagonals are applied there,
+// and each giant group pays one ModDown before its giant rotation, whose own
+// result is again accumulated in QP; one ModDown at the end.
 static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
     build_level(cx, L, x->level, x->scale, target);
-    const int l = x->level;
+    const int l = x->level, h = cx->n / 2;
     const size_t N = cx->N();
-    // baby-step rotations share one ModUp of c1 (hoisting): each reads the
-    // extended digits through its own automorphism
-    std::vector<Ct> baby(L.baby.size());
     const LevelTabs &LT = cx->lv[l];
-    const size_t ext_bytes = (size_t)LT.beta * LT.n_ext * N * 8;
+    const int ne = LT.n_ext;
+    const size_t qp_bytes = (size_t)2 * ne * N * 8, ext_bytes = (size_t)LT.beta * ne * N * 8;
+    cudaStream_t s = cx->stream;
+    struct Bufs {  // arena buffers, released on every exit path
+        he_ctx *cx;
+        std::vector<std::pair<u64 *, size_t>> v;
+        u64 *get(size_t b) {
+            u64 *p = (u64 *)cx->arena.alloc(b);
+            v.emplace_back(p, b);
+            return p;
+        }
+        ~Bufs() {
+            for (auto &pb : v) cx->arena.release(pb.first, pb.second);
+        }
+    } bufs{cx, {}};
+    auto qp = [&](u64 *base) { return make_rows(base, (size_t)ne * N, ne, l + 1, cx->nq); };
+    // baby steps in QP
+    std::vector<u64 *> baby(L.baby.size(), nullptr);
     u64 *ext = nullptr;
-    for (size_t b = 1; b < L.baby.size(); b++) {
+    for (size_t b = 0; b < L.baby.size(); b++) {
         bool used = false;
         for (auto &row : L.idx) used |= row[b] >= 0;
         if (!used) continue;
+        baby[b] = bufs.get(qp_bytes);
+        if (b == 0) {
+            ew_qp_lift(baby[b], ct_poly(x, 0), l + 1, ne, 0, 0, cx->p_mod, cx->slot, cx->log_n, s);
+            ew_qp_lift(baby[b] + (size_t)ne * N, ct_poly(x, 1), l + 1, ne, 0, 0, cx->p_mod, cx->slot, cx->log_n, s);
+            continue;
+        }
         u64 g = rot_galois(cx, L.baby[b]);
         const KeyDev *key = find_key(cx, g);
         if (!key) throw Error{HE_ENOKEY, "bootstrapping rotation key missing"};
         if (!ext) {
-            ext = (u64 *)cx->arena.alloc(ext_bytes);
+            ext = bufs.get(ext_bytes);
             modup(cx, ct_poly(x, 1), l, ext);
         }
-        Ct r(ct_alloc(cx, l, x->scale));
-        Rows sa = make_rows(cx->sc_a, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
-        ew_automorph_ntt(sa, make_rows(ct_poly(x, 0), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
-        keyswitch_ext(cx, ct_poly(x, 1), ext, l, *key, g, ct_rows(r.get()), sa, 1);
-        baby[b] = std::move(r);
+        ks_inner(cx, ct_poly(x, 1), ext, l, *key, g, baby[b]);
+        ew_qp_lift(baby[b], ct_poly(x, 0), l + 1, ne, g, 1, cx->p_mod, cx->slot, cx->log_n, s);
     }
-    if (ext) cx->arena.release(ext, ext_bytes);
-    Ct acc;
+    // giant groups
+    u64 *tot = bufs.get(qp_bytes), *inner = bufs.get(qp_bytes);
+    bool have = false;
     for (size_t g = 0; g < L.giant.size(); g++) {
         DiagMac dm;
         dm.n = 0;
         dm.slot = cx->slot;
+        dm.l1 = l + 1;
+        dm.nq = cx->nq;
         for (size_t b = 0; b < L.baby.size(); b++) {
             int p = L.idx[g][b];
             if (p < 0) continue;
             if (dm.n == DIAG_MAC_MAX) throw Error{HE_EINVAL, "too many diagonals in one giant step"};
-            const he_ct *src = b == 0 ? x : baby[b].get();
-            dm.c0[dm.n] = ct_poly(src, 0);
-            dm.c1[dm.n] = ct_poly(src, 1);
-            dm.pt[dm.n] = L.pts + (size_t)p * (l + 1) * N;
+            dm.c0[dm.n] = baby[b];
+            dm.c1[dm.n] = baby[b] + (size_t)ne * N;
+            dm.pt[dm.n] = L.pts + (size_t)p * ne * N;
             dm.n++;
         }
         if (!dm.n) continue;
-        Ct inner(ct_alloc(cx, l, x->scale * L.E));
-        dm.out0 = ct_poly(inner.get(), 0);
-        dm.out1 = ct_poly(inner.get(), 1);
-        ew_diag_mac(dm, l + 1, cx->log_n, cx->stream);
-        if (L.giant[g] % (cx->n / 2) != 0) inner = op_automorph(cx, inner.get(), rot_galois(cx, L.giant[g]));
-        acc = acc ? op_add(cx, acc.get(), inner.get(), false) : std::move(inner);
+        const bool rot = L.giant[g] % h != 0;
+        u64 *dst = (!rot && !have) ? tot : inner;
+        dm.out0 = dst;
+        dm.out1 = dst + (size_t)ne * N;
+        ew_diag_mac(dm, ne, cx->log_n, s);
+        if (!rot) {
+            if (have) ew_add(qp(tot), qp(tot), qp(inner), 2 * ne, 0, cx->log_n, s);
+            have = true;
+            continue;
+        }
+        // ModDown of the group, then its giant rotation, accumulated in QP
+        Ct y(ct_alloc(cx, l, x->scale * L.E));
+        moddown(cx, inner, l, ct_rows(y.get()), ct_rows(y.get()), 0);
+        u64 gg = rot_galois(cx, L.giant[g]);
+        const KeyDev *key = find_key(cx, gg);
+        if (!key) throw Error{HE_ENOKEY, "bootstrapping rotation key missing"};
+        modup(cx, ct_poly(y.get(), 1), l, cx->ks_ext);
+        u64 *acc = have ? cx->ks_acc : tot;
+        ks_inner(cx, ct_poly(y.get(), 1), cx->ks_ext, l, *key, gg, acc);
+        ew_qp_lift(acc, ct_poly(y.get(), 0), l + 1, ne, gg, 1, cx->p_mod, cx->slot, cx->log_n, s);
+        if (have) ew_add(qp(tot), qp(tot), qp(acc), 2 * ne, 0, cx->log_n, s);
+        have = true;
     }
-    return op_rescale(cx, acc.get());
+    if (!have) throw Error{HE_EINVAL, "empty linear transform level"};
+    Ct out(ct_alloc(cx, l, x->scale * L.E));
+    moddown(cx, tot, l, ct_rows(out.get()), ct_rows(out.get()), 0);
+    return op_rescale(cx, out.get());
 }
 
 // Chebyshev series sum_k c_k T_k(x) by baby steps T_1..T_(m-1) and giant

@@ -678,39 +678,52 @@ void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext) {
     ntt_forward(desc_rows(ext, T.desc), T.n_desc, cx->tw, log_n, s);
 }
 
-// Inner product with the key (reading the digits through X -> X^galois when
-// galois != 0) and ModDown: out = (acc - conv(acc_P)) * P^-1 (+ add).
-void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
-                   const Rows &out, const Rows &add, int add_mask) {
-    const int K = cx->np, log_n = cx->log_n;
-    const size_t N = cx->N();
+// Inner product with the key, reading the digits through X -> X^galois when
+// galois != 0: acc = (sum_j ext_j * b_j, sum_j ext_j * a_j) over QP, two
+// polynomials of n_ext rows each (Q limbs 0..l, then the special primes).
+void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc) {
     const LevelTabs &T = cx->lv[l];
-    cudaStream_t s = cx->stream;
     cx->ks_by_level[l]++;
     KeyIP kp;
     kp.d_ntt = d_ntt;
     kp.ext = ext;
     kp.key = key.data;
-    kp.acc = cx->ks_acc;
+    kp.acc = acc;
     kp.n_rows = T.n_ext;
     kp.l1 = l + 1;
     kp.nq = cx->nq;
-    kp.np = K;
+    kp.np = cx->np;
     kp.alpha = cx->alpha;
     kp.beta = T.beta;
     kp.key_limbs = cx->nq + cx->np;
     kp.slot = cx->slot;
     kp.galois = galois;
-    keyswitch_inner(kp, log_n, s);
-    Rows accP = make_rows(cx->ks_acc + (size_t)(l + 1) * N, (size_t)T.n_ext * N, K, 0, cx->nq);
+    keyswitch_inner(kp, cx->log_n, cx->stream);
+}
+
+// ModDown of a two-polynomial QP accumulator (destroys its special-prime
+// rows): out = (acc_Q - conv(acc_P)) * P^-1 (+ add where add_mask selects).
+void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask) {
+    const int K = cx->np, log_n = cx->log_n;
+    const size_t N = cx->N();
+    const LevelTabs &T = cx->lv[l];
+    cudaStream_t s = cx->stream;
+    Rows accP = make_rows(acc + (size_t)(l + 1) * N, (size_t)T.n_ext * N, K, 0, cx->nq);
     ntt_inverse(accP, 2 * K, cx->tw, log_n, s);
     BConvTab md = cx->moddown;
     md.n_out = l + 1;
     Rows conv = make_rows(cx->ks_conv, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
     bconv(conv, accP, md, 2, log_n, s);
     ntt_forward(conv, 2 * (l + 1), cx->tw, log_n, s);
-    Rows accQ = make_rows(cx->ks_acc, (size_t)T.n_ext * N, l + 1, l + 1, cx->nq);
+    Rows accQ = make_rows(acc, (size_t)T.n_ext * N, l + 1, l + 1, cx->nq);
     moddown_finish(out, accQ, conv, cx->p_inv, 2 * (l + 1), add, add_mask, log_n, s);
+}
+
+// Inner product with the key and ModDown: out = ModDown(acc) (+ add).
+void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
+                   const Rows &out, const Rows &add, int add_mask) {
+    ks_inner(cx, d_ntt, ext, l, key, galois, cx->ks_acc);
+    moddown(cx, cx->ks_acc, l, out, add, add_mask);
 }
 
 void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask) {

@@ -144,6 +144,8 @@ Ct op_copy(he_ctx *cx, const he_ct *a);
 void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask);
 // the two halves of a key switch, for rotations that share one ModUp
 void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext);
+void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc);
+void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask);
 void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
                    const Rows &out, const Rows &add, int add_mask);
 

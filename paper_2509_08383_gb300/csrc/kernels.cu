@@ -464,7 +464,8 @@ __global__ void k_diag_mac(DiagMac dm, int n_rows, int log_n) {
     EW_LOOP(total) {
         const int r = (int)(gi >> log_n);
         const size_t k = gi & mask, off = ((size_t)r << log_n) + k;
-        const ModQ &m = pc.m[r];
+        const int pr = r < dm.l1 ? r : dm.nq + (r - dm.l1);
+        const ModQ &m = pc.m[pr];
         u64 s0 = 0, s1 = 0;
         for (int b0 = 0; b0 < dm.n; b0 += 16) {  // at most 16 products (< 2^126) per 128-bit sum
             u64 l0 = 0, h0 = 0, l1 = 0, h1 = 0;
@@ -480,8 +481,8 @@ __global__ void k_diag_mac(DiagMac dm, int n_rows, int log_n) {
                 l1 += pl;
                 h1 += ph + (l1 < pl ? 1ull : 0ull);
             }
-            s0 = add_mod(s0, mont_reduce_wide(l0, h0, m, pc.mont_qinv[r]), m.q);
-            s1 = add_mod(s1, mont_reduce_wide(l1, h1, m, pc.mont_qinv[r]), m.q);
+            s0 = add_mod(s0, mont_reduce_wide(l0, h0, m, pc.mont_qinv[pr]), m.q);
+            s1 = add_mod(s1, mont_reduce_wide(l1, h1, m, pc.mont_qinv[pr]), m.q);
         }
         dm.out0[off] = s0;
         dm.out1[off] = s1;
@@ -490,6 +491,38 @@ __global__ void k_diag_mac(DiagMac dm, int n_rows, int log_n) {
 void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s) {
     size_t t = (size_t)n_rows << log_n;
     k_diag_mac<<<grid_for(t, 256), 256, 0, s>>>(dm, n_rows, log_n);
+}
+
+// One polynomial in the QP basis, times P: out_r = (add ? out_r : 0) +
+// (P mod q_r) * src_r read through X -> X^g (g = 0: identity) for the Q rows
+// r < l1 of an n_rows-row block; the special-prime rows are 0 (P = 0 mod p_i)
+// and are left unchanged when adding.
+__global__ void k_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, ScalarTab pm, int slot,
+                          int log_n) {
+    const PrimeConsts &pc = c_pcs[slot];
+    const size_t total = (size_t)(add ? l1 : n_rows) << log_n, mask = ((size_t)1 << log_n) - 1;
+    const u64 two_n_mask = (2ull << log_n) - 1;
+    EW_LOOP(total) {
+        const int r = (int)(gi >> log_n);
+        if (r >= l1) {
+            out[gi] = 0;
+            continue;
+        }
+        u32 i = (u32)(gi & mask), si = i;
+        if (g) {
+            u64 e = 2ull * (__brev(i) >> (32 - log_n)) + 1;
+            u64 e2 = (e * g) & two_n_mask;
+            si = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
+        }
+        const u64 q = pc.m[r].q;
+        const u64 v = shoup_mul(src[((size_t)r << log_n) + si], pm.v[r], pm.s[r], q);
+        out[gi] = add ? add_mod(out[gi], v, q) : v;
+    }
+}
+void ew_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, const ScalarTab &pm, int slot,
+                int log_n, cudaStream_t s) {
+    size_t t = (size_t)(add ? l1 : n_rows) << log_n;
+    k_qp_lift<<<grid_for(t, 256), 256, 0, s>>>(out, src, l1, n_rows, g, add, pm, slot, log_n);
 }
 
 __global__ void k_tensor(Rows d0, Rows d1, Rows d2, Rows a0, Rows a1, Rows b0, Rows b1, int n_rows, int log_n) {

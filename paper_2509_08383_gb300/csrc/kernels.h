@@ -55,14 +55,17 @@ void ew_mul_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_row
 void ew_add_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s);
 // out = a (*) b pointwise
 // Plaintext-diagonal multiply-accumulate of one baby-step giant-step group:
-// out0/out1 = sum_{b < n} c0[b]/c1[b] * pt[b], limb-major rows 0..n_rows-1 on
-// the Q chain (row r uses prime r), plaintexts in Montgomery form (x 2^64).
+// out0/out1 = sum_{b < n} c0[b]/c1[b] * pt[b], limb-major rows 0..n_rows-1
+// (row r uses prime r for r < l1, special prime nq + r - l1 after), plaintexts
+// in Montgomery form (x 2^64).
 constexpr int DIAG_MAC_MAX = 64;
 struct DiagMac {
     const u64 *c0[DIAG_MAC_MAX], *c1[DIAG_MAC_MAX], *pt[DIAG_MAC_MAX];
     u64 *out0, *out1;
-    int n, slot;
+    int n, slot, l1, nq;
 };
+void ew_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, const ScalarTab &pm, int slot,
+                int log_n, cudaStream_t s);
 void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s);
 void ew_mul(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s);
 // out = out + a (*) b pointwise

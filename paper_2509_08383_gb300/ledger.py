@@ -33,7 +33,7 @@ def _bsgs_counts(h, offs):
     mmin, mmax = min(ms), max(ms)
     span = mmax - mmin + 1
     bs = 1
-    while bs * bs < span:
+    while bs * bs < 4 * span:              # babies are cheap (hoisted ModUp and ModDown)
         bs <<= 1
     babies, giants = set(), set()
     for m in ms:
