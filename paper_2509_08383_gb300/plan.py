@@ -133,6 +133,22 @@ def _invsqrt_err(x, k, y0):
     return np.abs(2.0 * _invsqrt_half(x, k, y0) * np.sqrt(x) - 1.0).max()
 
 
+def _fewest_iterations(xs, k_max, tol, y0_default):
+    """Smallest k (and a constant start y0 reaching it) with the circuit's
+    Goldschmidt error below tol on xs.  The iteration needs 0 < x y0^2 < 3;
+    candidates put x_max y0^2 between 0.5 and 2.5 (headroom below 3 for inputs
+    beyond the calibrated range)."""
+    cands = [y0_default] + [math.sqrt(u / xs[-1]) for u in np.linspace(0.5, 2.5, 50)]
+    best_k, best_y0 = k_max, y0_default
+    for kk in range(1, k_max + 1):
+        ok = [y for y in cands if _invsqrt_err(xs, kk, y) < tol]
+        if ok:
+            # among the starts that reach tol in kk steps, the one with the least error
+            errs = [_invsqrt_err(xs, kk, y) for y in ok]
+            return kk, ok[int(np.argmin(errs))]
+    return best_k, best_y0
+
+
 def _inv_err(x, d):
     a = 1.0 - x
     f = 1.0 + a
@@ -180,11 +196,7 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
         if k_fixed is not None:
             k = int(k_fixed if np.isscalar(k_fixed) else k_fixed[t])
         else:
-            k = k_max
-            for kk in range(1, k_max + 1):
-                if _invsqrt_err(xs, kk, y0) < tol_k:
-                    k = kk
-                    break
+            k, y0 = _fewest_iterations(xs, k_max, tol_k, y0)
         new = []
         for D, V in zip(Ds, Vs):
             h = _invsqrt_half(kap * V, k, y0)
