@@ -1,6 +1,6 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|mul16|boot16]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|mul16|rot16|ntt16|boot16]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
@@ -247,7 +247,10 @@ def run_micro(args):
     """Micro workloads for kernel profiles at the N=2^16 parameter set (the
     same kernels as a CutMax step at full size): mul16 = one homomorphic
     multiplication (tensor product, hybrid key switch, rescale) at the top
-    level; boot16 = one bootstrapping of a level-0 ciphertext."""
+    level; rot16 = one rotation (automorphism + hybrid key switch) at the top
+    level; ntt16 = a forward and an inverse NTT of one 41-limb block (every
+    prime of the chain, 21 MB); boot16 = one bootstrapping of a level-0
+    ciphertext."""
     import torch
     from paper_2509_08383_gb300 import build, he
     build.build_library()
@@ -256,12 +259,30 @@ def run_micro(args):
     g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=(24 << 30) if boot else (4 << 30))
     rng = np.random.default_rng(0)
     slots = 1 << 15
+    roof = None
     if boot:
         g.bootstrap_prepare(24, 4, 31)
         cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, 0, level=0)]
         op = lambda: g.bootstrap(cts[0])
         metric, unit = "bootstraps/s (N=2^16, K=24, r=4, d=31, dnum=3)", "boot/s"
         wl = "CKKS bootstrapping of a level-0 ciphertext, N=2^16, 31 primes + 10 special primes, h=192"
+    elif args.workload == "ntt16":
+        limbs = len(CFG2_Q) + len(CFG2_P)
+        blk = torch.randint(0, 1 << 39, (limbs, 1 << 16), dtype=torch.int64, device="cuda")
+        op = lambda: (g.ntt_device(blk, 0), g.ntt_device(blk, 0, inverse=True))
+        metric, unit = "NTT forward + inverse, 41 limbs (N=2^16)", "pairs/s"
+        wl = "negacyclic NTT then INTT of a 41-limb block (every prime of the N=2^16 chain), in place"
+        roof = 2 * 16.0 * limbs * (1 << 16)  # algorithmic bytes per step: read + write each limb, twice
+    elif args.workload == "rot16":
+        g.gen_rot_keys([1])
+        cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, 0)]
+        op = lambda: g.rotate(cts[0], 1)
+        metric, unit = "homomorphic rotations/s (N=2^16, level 30, dnum=3)", "rot/s"
+        wl = "slot rotation by 1 (automorphism + hybrid key switch), N=2^16, 31 primes + 10 special primes"
+        l1, K, beta = len(CFG2_Q), len(CFG2_P), 3
+        # automorphism (read + write both polynomials) + key switch: d in, beta key digits
+        # (b and a over l+1+K primes), two output polynomials
+        roof = 8.0 * (1 << 16) * (4 * l1 + l1 + 2 * beta * (l1 + K) + 2 * l1)
     else:
         g.gen_relin_key()
         cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, s) for s in range(2)]
@@ -281,10 +302,15 @@ def run_micro(args):
             del z
         torch.cuda.synchronize()
     ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
-    print(json.dumps({"metric": metric, "value": 1000.0 / ms, "unit": unit, "n_gpus": 1, "steps": args.steps,
-                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                      "dtype": "u64", "data": "synthetic", "clocks": clk.summary(),
-                      "config": {"workload": wl, "l2": "flushed between steps"}}))
+    out = {"metric": metric, "value": 1000.0 / ms, "unit": unit, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "dtype": "u64", "data": "synthetic", "clocks": clk.summary(),
+           "config": {"workload": wl, "l2": "flushed between steps"}}
+    if roof:
+        peak, kind = measured_peaks()
+        out["roofline"] = {"bound": "hbm", "achieved": roof / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": roof / (ms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": kind}
+    print(json.dumps(out))
 
 
 def main():
@@ -293,12 +319,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "mul16", "boot16"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "mul16", "rot16", "ntt16", "boot16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("mul16", "boot16"):
+    if args.workload in ("mul16", "rot16", "ntt16", "boot16"):
         return run_micro(args)
 
     import torch

@@ -390,289 +390,371 @@ void ntt_inverse_from(const Rows &dst, const Rows &src, int n_rows, const NttTab
 }
 
 // ------------------------------------------------------------------ elementwise
-#define EW_LOOP(total)                                                                 \
-    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (total);      \
-         gi += (size_t)gridDim.x * blockDim.x)
+// Row-parallel layout: blockIdx.y selects the limb row and every thread of
+// an EW_T-thread block handles EW_PAIRS pairs of consecutive coefficients
+// (one 16-byte access per operand and pair; pairs EW_T apart, so each warp
+// access is one contiguous 512-byte span).  A row's addresses and prime are
+// resolved once per thread.  Every row must start on a 16-byte boundary
+// (the launchers check the base pointers; rows are N >= 2 words apart).
+constexpr int EW_T = 256, EW_PAIRS = 4;
 
-__global__ void k_add(Rows out, Rows a, Rows b, int n_rows, int sub, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        u64 q = pc.m[out.prime(r)].q;
-        u64 x = a.row(r, log_n)[k], y = b.row(r, log_n)[k];
-        out.row(r, log_n)[k] = sub ? sub_mod(x, y, q) : add_mod(x, y, q);
+static inline dim3 ew_grid(int n_rows, int log_n) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (n_rows > 65535) throw Error{HE_EINVAL, "too many rows for one elementwise launch"};
+    const size_t per_block = (size_t)EW_T * 2 * EW_PAIRS;
+    return dim3((unsigned)((((size_t)1 << log_n) + per_block - 1) / per_block), (unsigned)n_rows);
+}
+static inline void need16(const void *p) {
+    if (reinterpret_cast<uintptr_t>(p) & 15) throw Error{HE_EINVAL, "device rows must start on a 16-byte boundary"};
+}
+static inline void need16(const Rows &r) { need16(r.base); }
+
+// k runs over the first coefficient of each pair this thread owns in its row
+#define EW_PAIRS_FOR(k, log_n)                                                                 \
+    _Pragma("unroll") for (int ew_i = 0; ew_i < EW_PAIRS; ew_i++)                              \
+        if (const size_t k = 2 * (((size_t)blockIdx.x * EW_PAIRS + ew_i) * EW_T + threadIdx.x); \
+            k < ((size_t)1 << (log_n)))
+
+__device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
+__device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) {
+    *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b);
+}
+
+__global__ void __launch_bounds__(EW_T) k_add(Rows out, Rows a, Rows b, int sub, int log_n) {
+    const int r = blockIdx.y;
+    const u64 q = c_pcs[out.slot].m[out.prime(r)].q;
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n), *y = b.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        ulonglong2 u = ld2(x + k), v = ld2(y + k);
+        if (sub) st2(o + k, sub_mod(u.x, v.x, q), sub_mod(u.y, v.y, q));
+        else st2(o + k, add_mod(u.x, v.x, q), add_mod(u.y, v.y, q));
     }
 }
-__global__ void k_neg(Rows out, Rows a, int n_rows, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        u64 q = pc.m[out.prime(r)].q, x = a.row(r, log_n)[k];
-        out.row(r, log_n)[k] = x ? q - x : 0;
+__global__ void __launch_bounds__(EW_T) k_neg(Rows out, Rows a, int log_n) {
+    const int r = blockIdx.y;
+    const u64 q = c_pcs[out.slot].m[out.prime(r)].q;
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        ulonglong2 u = ld2(x + k);
+        st2(o + k, u.x ? q - u.x : 0, u.y ? q - u.y : 0);
     }
 }
-__global__ void k_copy(Rows out, Rows a, int n_rows, int log_n) {
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        out.row(r, log_n)[k] = a.row(r, log_n)[k];
+__global__ void __launch_bounds__(EW_T) k_copy(Rows out, Rows a, int log_n) {
+    const int r = blockIdx.y;
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        ulonglong2 u = ld2(x + k);
+        st2(o + k, u.x, u.y);
     }
 }
-__global__ void k_mul_scalar(Rows out, Rows a, ScalarTab kt, int n_rows, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        int p = out.prime(r);
-        out.row(r, log_n)[k] = shoup_mul(a.row(r, log_n)[k], kt.v[p], kt.s[p], pc.m[p].q);
+__global__ void __launch_bounds__(EW_T) k_mul_scalar(Rows out, Rows a, ScalarTab kt, int log_n) {
+    const int r = blockIdx.y, p = out.prime(r);
+    const u64 q = c_pcs[out.slot].m[p].q, w = kt.v[p], ws = kt.s[p];
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        ulonglong2 u = ld2(x + k);
+        st2(o + k, shoup_mul(u.x, w, ws, q), shoup_mul(u.y, w, ws, q));
     }
 }
-__global__ void k_add_scalar(Rows out, Rows a, ScalarTab kt, int n_rows, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        int p = out.prime(r);
-        out.row(r, log_n)[k] = add_mod(a.row(r, log_n)[k], kt.v[p], pc.m[p].q);
+__global__ void __launch_bounds__(EW_T) k_add_scalar(Rows out, Rows a, ScalarTab kt, int log_n) {
+    const int r = blockIdx.y, p = out.prime(r);
+    const u64 q = c_pcs[out.slot].m[p].q, w = kt.v[p];
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        ulonglong2 u = ld2(x + k);
+        st2(o + k, add_mod(u.x, w, q), add_mod(u.y, w, q));
     }
 }
-__global__ void k_mul(Rows out, Rows a, Rows b, int n_rows, int acc, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        const ModQ &m = pc.m[out.prime(r)];
-        u64 v = mul_mod(a.row(r, log_n)[k], b.row(r, log_n)[k], m);
-        u64 *o = out.row(r, log_n) + k;
-        *o = acc ? add_mod(*o, v, m.q) : v;
+__global__ void __launch_bounds__(EW_T) k_mul(Rows out, Rows a, Rows b, int acc, int log_n) {
+    const int r = blockIdx.y;
+    const ModQ m = c_pcs[out.slot].m[out.prime(r)];
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n), *y = b.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        ulonglong2 u = ld2(x + k), v = ld2(y + k);
+        u64 p0 = mul_mod(u.x, v.x, m), p1 = mul_mod(u.y, v.y, m);
+        if (acc) {
+            ulonglong2 c = ld2(o + k);
+            p0 = add_mod(c.x, p0, m.q);
+            p1 = add_mod(c.y, p1, m.q);
+        }
+        st2(o + k, p0, p1);
     }
 }
 // out_k = sum_b src_b,k * pt_b (k = 0, 1: both polynomials of a ciphertext),
 // plaintexts in Montgomery form: the products are summed in 128 bits and each
 // output is reduced once.
-__global__ void k_diag_mac(DiagMac dm, int n_rows, int log_n) {
+__device__ __forceinline__ void mac128(u64 &lo, u64 &hi, u64 x, u64 w) {
+    const u64 pl = x * w, ph = __umul64hi(x, w);
+    lo += pl;
+    hi += ph + (lo < pl ? 1ull : 0ull);
+}
+__global__ void __launch_bounds__(EW_T) k_diag_mac(DiagMac dm, int log_n) {
     const PrimeConsts &pc = c_pcs[dm.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        const int r = (int)(gi >> log_n);
-        const size_t k = gi & mask, off = ((size_t)r << log_n) + k;
-        const int pr = r < dm.l1 ? r : dm.nq + (r - dm.l1);
-        const ModQ &m = pc.m[pr];
-        u64 s0 = 0, s1 = 0;
+    const int r = blockIdx.y;
+    const int pr = r < dm.l1 ? r : dm.nq + (r - dm.l1);
+    const ModQ m = pc.m[pr];
+    const u64 qn = pc.mont_qinv[pr];
+    const size_t row = (size_t)r << log_n;
+    EW_PAIRS_FOR(k, log_n) {
+        const size_t off = row + k;
+        u64 s00 = 0, s01 = 0, s10 = 0, s11 = 0;
         for (int b0 = 0; b0 < dm.n; b0 += 16) {  // at most 16 products (< 2^126) per 128-bit sum
-            u64 l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+            u64 l00 = 0, h00 = 0, l01 = 0, h01 = 0, l10 = 0, h10 = 0, l11 = 0, h11 = 0;
             const int b1 = min(dm.n, b0 + 16);
             for (int b = b0; b < b1; b++) {
-                const u64 w = dm.pt[b][off];
-                const u64 x0 = dm.c0[b][off], x1 = dm.c1[b][off];
-                u64 pl = x0 * w, ph = __umul64hi(x0, w);
-                l0 += pl;
-                h0 += ph + (l0 < pl ? 1ull : 0ull);
-                pl = x1 * w;
-                ph = __umul64hi(x1, w);
-                l1 += pl;
-                h1 += ph + (l1 < pl ? 1ull : 0ull);
+                const ulonglong2 w = ld2(dm.pt[b] + off);
+                const ulonglong2 x0 = ld2(dm.c0[b] + off), x1 = ld2(dm.c1[b] + off);
+                mac128(l00, h00, x0.x, w.x);
+                mac128(l01, h01, x0.y, w.y);
+                mac128(l10, h10, x1.x, w.x);
+                mac128(l11, h11, x1.y, w.y);
             }
-            s0 = add_mod(s0, mont_reduce_wide(l0, h0, m, pc.mont_qinv[pr]), m.q);
-            s1 = add_mod(s1, mont_reduce_wide(l1, h1, m, pc.mont_qinv[pr]), m.q);
+            s00 = add_mod(s00, mont_reduce_wide(l00, h00, m, qn), m.q);
+            s01 = add_mod(s01, mont_reduce_wide(l01, h01, m, qn), m.q);
+            s10 = add_mod(s10, mont_reduce_wide(l10, h10, m, qn), m.q);
+            s11 = add_mod(s11, mont_reduce_wide(l11, h11, m, qn), m.q);
         }
-        dm.out0[off] = s0;
-        dm.out1[off] = s1;
+        st2(dm.out0 + off, s00, s01);
+        st2(dm.out1 + off, s10, s11);
     }
 }
 void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_diag_mac<<<grid_for(t, 256), 256, 0, s>>>(dm, n_rows, log_n);
+    need16(dm.out0);
+    need16(dm.out1);
+    for (int b = 0; b < dm.n; b++) {
+        need16(dm.c0[b]);
+        need16(dm.c1[b]);
+        need16(dm.pt[b]);
+    }
+    k_diag_mac<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(dm, log_n);
+}
+
+// source position of NTT-form position i under X -> X^g (g odd < 2N)
+__device__ __forceinline__ u32 automorph_src(u32 i, u64 g, int log_n) {
+    const u64 two_n_mask = (2ull << log_n) - 1;
+    const u64 e = 2ull * (__brev(i) >> (32 - log_n)) + 1;
+    const u64 e2 = (e * g) & two_n_mask;
+    return __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
 }
 
 // One polynomial in the QP basis, times P: out_r = (add ? out_r : 0) +
 // (P mod q_r) * src_r read through X -> X^g (g = 0: identity) for the Q rows
 // r < l1 of an n_rows-row block; the special-prime rows are 0 (P = 0 mod p_i)
 // and are left unchanged when adding.
-__global__ void k_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, ScalarTab pm, int slot,
-                          int log_n) {
-    const PrimeConsts &pc = c_pcs[slot];
-    const size_t total = (size_t)(add ? l1 : n_rows) << log_n, mask = ((size_t)1 << log_n) - 1;
-    const u64 two_n_mask = (2ull << log_n) - 1;
-    EW_LOOP(total) {
-        const int r = (int)(gi >> log_n);
-        if (r >= l1) {
-            out[gi] = 0;
-            continue;
-        }
-        u32 i = (u32)(gi & mask), si = i;
+__global__ void __launch_bounds__(EW_T) k_qp_lift(u64 *out, const u64 *src, int l1, u64 g, int add, ScalarTab pm,
+                                                  int slot, int log_n) {
+    const int r = blockIdx.y;
+    u64 *o = out + ((size_t)r << log_n);
+    if (r >= l1) {
+        EW_PAIRS_FOR(k, log_n) st2(o + k, 0, 0);
+        return;
+    }
+    const u64 q = c_pcs[slot].m[r].q, w = pm.v[r], ws = pm.s[r];
+    const u64 *x = src + ((size_t)r << log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        u64 a, b;
         if (g) {
-            u64 e = 2ull * (__brev(i) >> (32 - log_n)) + 1;
-            u64 e2 = (e * g) & two_n_mask;
-            si = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
+            a = x[automorph_src((u32)k, g, log_n)];
+            b = x[automorph_src((u32)k + 1, g, log_n)];
+        } else {
+            ulonglong2 u = ld2(x + k);
+            a = u.x;
+            b = u.y;
         }
-        const u64 q = pc.m[r].q;
-        const u64 v = shoup_mul(src[((size_t)r << log_n) + si], pm.v[r], pm.s[r], q);
-        out[gi] = add ? add_mod(out[gi], v, q) : v;
+        a = shoup_mul(a, w, ws, q);
+        b = shoup_mul(b, w, ws, q);
+        if (add) {
+            ulonglong2 c = ld2(o + k);
+            a = add_mod(c.x, a, q);
+            b = add_mod(c.y, b, q);
+        }
+        st2(o + k, a, b);
     }
 }
 void ew_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, const ScalarTab &pm, int slot,
                 int log_n, cudaStream_t s) {
-    size_t t = (size_t)(add ? l1 : n_rows) << log_n;
-    k_qp_lift<<<grid_for(t, 256), 256, 0, s>>>(out, src, l1, n_rows, g, add, pm, slot, log_n);
+    need16(out);
+    need16(src);
+    k_qp_lift<<<ew_grid(add ? l1 : n_rows, log_n), EW_T, 0, s>>>(out, src, l1, g, add, pm, slot, log_n);
 }
 
-__global__ void k_tensor(Rows d0, Rows d1, Rows d2, Rows a0, Rows a1, Rows b0, Rows b1, int n_rows, int log_n) {
-    const PrimeConsts &pc = c_pcs[d0.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        const ModQ &m = pc.m[d0.prime(r)];
-        u64 x0 = a0.row(r, log_n)[k], x1 = a1.row(r, log_n)[k];
-        u64 y0 = b0.row(r, log_n)[k], y1 = b1.row(r, log_n)[k];
-        d0.row(r, log_n)[k] = mul_mod(x0, y0, m);
-        d1.row(r, log_n)[k] = mul_add_mod(x0, y1, x1, y0, m);
-        d2.row(r, log_n)[k] = mul_mod(x1, y1, m);
+__global__ void __launch_bounds__(EW_T) k_tensor(Rows d0, Rows d1, Rows d2, Rows a0, Rows a1, Rows b0, Rows b1,
+                                                 int log_n) {
+    const int r = blockIdx.y;
+    const ModQ m = c_pcs[d0.slot].m[d0.prime(r)];
+    u64 *o0 = d0.row(r, log_n), *o1 = d1.row(r, log_n), *o2 = d2.row(r, log_n);
+    const u64 *pa0 = a0.row(r, log_n), *pa1 = a1.row(r, log_n), *pb0 = b0.row(r, log_n), *pb1 = b1.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 x0 = ld2(pa0 + k), x1 = ld2(pa1 + k), y0 = ld2(pb0 + k), y1 = ld2(pb1 + k);
+        st2(o0 + k, mul_mod(x0.x, y0.x, m), mul_mod(x0.y, y0.y, m));
+        st2(o1 + k, mul_add_mod(x0.x, y1.x, x1.x, y0.x, m), mul_add_mod(x0.y, y1.y, x1.y, y0.y, m));
+        st2(o2 + k, mul_mod(x1.x, y1.x, m), mul_mod(x1.y, y1.y, m));
     }
 }
-__global__ void k_automorph(Rows out, Rows a, int n_rows, u64 g, int log_n) {
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    const u64 two_n_mask = (2ull << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        u32 i = (u32)(gi & mask);
-        u64 e = 2ull * (__brev(i) >> (32 - log_n)) + 1;
-        u64 e2 = (e * g) & two_n_mask;
-        u32 src = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
-        out.row(r, log_n)[i] = a.row(r, log_n)[src];
-    }
+__global__ void __launch_bounds__(EW_T) k_automorph(Rows out, Rows a, u64 g, int log_n) {
+    const int r = blockIdx.y;
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) st2(o + k, x[automorph_src((u32)k, g, log_n)], x[automorph_src((u32)k + 1, g, log_n)]);
 }
 
 // out = a * X^e: in NTT form position i is multiplied by psi^((2 brv(i)+1) e),
 // read from the forward table (psi^j = fwd[brv(j)], psi^(j+N) = -psi^j).
-__global__ void k_monomial(Rows out, Rows a, int n_rows, u64 e, NttTables tw, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
+__global__ void __launch_bounds__(EW_T) k_monomial(Rows out, Rows a, u64 e, NttTables tw, int log_n) {
+    const int r = blockIdx.y, p = out.prime(r);
+    const ModQ m = c_pcs[out.slot].m[p];
     const u64 n = 1ull << log_n, two_n_mask = 2 * n - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        u32 i = (u32)(gi & mask);
-        int p = out.prime(r);
-        const ModQ &m = pc.m[p];
-        u64 x = ((2ull * (__brev(i) >> (32 - log_n)) + 1) * e) & two_n_mask;
-        const ulonglong2 *fw = tw.fwd + ((size_t)p << log_n);
-        u64 w = x < n ? fw[__brev((u32)x) >> (32 - log_n)].x : m.q - fw[__brev((u32)(x - n)) >> (32 - log_n)].x;
-        out.row(r, log_n)[i] = mul_mod(a.row(r, log_n)[i], w, m);
+    const ulonglong2 *fw = tw.fwd + ((size_t)p << log_n);
+    u64 *o = out.row(r, log_n);
+    const u64 *x = a.row(r, log_n);
+    auto factor = [&](u32 i) -> u64 {
+        const u64 t = ((2ull * (__brev(i) >> (32 - log_n)) + 1) * e) & two_n_mask;
+        return t < n ? fw[__brev((u32)t) >> (32 - log_n)].x : m.q - fw[__brev((u32)(t - n)) >> (32 - log_n)].x;
+    };
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 u = ld2(x + k);
+        st2(o + k, mul_mod(u.x, factor((u32)k), m), mul_mod(u.y, factor((u32)k + 1), m));
     }
 }
 // x -> x * 2^64 mod q (to Montgomery form) or x * 2^-64 mod q (back)
-__global__ void k_to_mont(Rows out, int n_rows, int back, int log_n) {
+__global__ void __launch_bounds__(EW_T) k_to_mont(Rows out, int back, int log_n) {
+    const int r = blockIdx.y, p = out.prime(r);
     const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        int p = out.prime(r);
-        const ModQ &m = pc.m[p];
-        u64 *x = out.row(r, log_n) + k;
-        *x = back ? mont_reduce(*x, 0, m.q, pc.mont_qinv[p]) : mul_mod(*x, pc.r64[p], m);
+    const ModQ m = pc.m[p];
+    const u64 qn = pc.mont_qinv[p], r64 = pc.r64[p];
+    u64 *o = out.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 u = ld2(o + k);
+        if (back) st2(o + k, mont_reduce(u.x, 0, m.q, qn), mont_reduce(u.y, 0, m.q, qn));
+        else st2(o + k, mul_mod(u.x, r64, m), mul_mod(u.y, r64, m));
     }
 }
 void ew_mont(const Rows &rows, int n_rows, int back, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_to_mont<<<grid_for(t, 256), 256, 0, s>>>(rows, n_rows, back, log_n);
+    need16(rows);
+    k_to_mont<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(rows, back, log_n);
 }
-
 void ew_monomial(const Rows &out, const Rows &a, int n_rows, u64 e, const NttTables &tw, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_monomial<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, e, tw, log_n);
+    need16(out);
+    need16(a);
+    k_monomial<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, e, tw, log_n);
 }
-
 void ew_add(const Rows &out, const Rows &a, const Rows &b, int n_rows, int sub, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_add<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, sub, log_n);
+    need16(out);
+    need16(a);
+    need16(b);
+    k_add<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, b, sub, log_n);
 }
 void ew_neg(const Rows &out, const Rows &a, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_neg<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, log_n);
+    need16(out);
+    need16(a);
+    k_neg<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, log_n);
 }
 void ew_copy(const Rows &out, const Rows &a, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_copy<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, log_n);
+    need16(out);
+    need16(a);
+    k_copy<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, log_n);
 }
 void ew_mul_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_mul_scalar<<<grid_for(t, 256), 256, 0, s>>>(out, a, k, n_rows, log_n);
+    need16(out);
+    need16(a);
+    k_mul_scalar<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, k, log_n);
 }
 void ew_add_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_add_scalar<<<grid_for(t, 256), 256, 0, s>>>(out, a, k, n_rows, log_n);
+    need16(out);
+    need16(a);
+    k_add_scalar<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, k, log_n);
 }
 void ew_mul(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_mul<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, 0, log_n);
+    need16(out);
+    need16(a);
+    need16(b);
+    k_mul<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, b, 0, log_n);
 }
 void ew_mul_acc(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_mul<<<grid_for(t, 256), 256, 0, s>>>(out, a, b, n_rows, 1, log_n);
+    need16(out);
+    need16(a);
+    need16(b);
+    k_mul<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, b, 1, log_n);
 }
 void ew_tensor(const Rows &d0, const Rows &d1, const Rows &d2, const Rows &a0, const Rows &a1, const Rows &b0,
                const Rows &b1, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_tensor<<<grid_for(t, 256), 256, 0, s>>>(d0, d1, d2, a0, a1, b0, b1, n_rows, log_n);
+    for (const Rows *r : {&d0, &d1, &d2, &a0, &a1, &b0, &b1}) need16(*r);
+    k_tensor<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(d0, d1, d2, a0, a1, b0, b1, log_n);
 }
 void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_automorph<<<grid_for(t, 256), 256, 0, s>>>(out, a, n_rows, g, log_n);
+    need16(out);
+    need16(a);
+    k_automorph<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, a, g, log_n);
 }
 
 // ------------------------------------------------------------------ key switching
 // Approximate basis conversion: for every coefficient, y_a = [x_a*qhinv_a]_{q_a},
 // out_t = sum_a y_a * qhat[a][t] mod p_t.
 // One thread per (coefficient, chunk of BCONV_CHUNK output rows).  The
-// products y_a * (qhat[a][t] 2^64 mod p_t) are summed in 128 bits (n_in <= 16
-// terms below 2^122 each) and each output is reduced once, by a Montgomery
+// products y_a * w_a,t with w = qhat[a][t] 2^64 mod p_t are summed exactly in
+// a 128-bit accumulator of four 32-bit words (n_in <= 16 terms below 2^122
+// each), one schoolbook 64x64-bit product per term folded in by a PTX carry
+// chain of 32-bit multiply-adds; each output is reduced once, by a Montgomery
 // step and a Barrett correction.  The chunk's constants sit in shared memory
 // (every thread reads the same word: broadcasts).
-constexpr int BCONV_CHUNK = 8;
+constexpr int BCONV_CHUNK = 8, BCONV_MAX_IN = 16;
+// (a3:a2:a1:a0) += (y1:y0) * (w1:w0)  (no carry out of a3: the caller's sums stay below 2^128)
+__device__ __forceinline__ void mac128_words(u32 &a0, u32 &a1, u32 &a2, u32 &a3, u32 y0, u32 y1, u32 w0, u32 w1) {
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
+        : "r"(y0), "r"(y1), "r"(w0), "r"(w1));
+}
 __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
-    __shared__ u64 s_qh[16 * BCONV_CHUNK];
-    __shared__ u64 s_qi[16], s_qis[16], s_q[16];
+    __shared__ uint2 s_w[BCONV_MAX_IN * BCONV_CHUNK];
+    __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
+    __shared__ const u64 *s_in[BCONV_MAX_IN];
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
     const int chunk = blockIdx.y % n_chunks, poly = blockIdx.y / n_chunks;
     const int t0 = chunk * BCONV_CHUNK, nt = min(BCONV_CHUNK, tab.n_out - t0);
-    for (int i = threadIdx.x; i < 16 * BCONV_CHUNK; i += blockDim.x) {
-        int a = i / BCONV_CHUNK, c = i % BCONV_CHUNK;
-        s_qh[i] = (a < tab.n_in && c < nt) ? tab.qhat_mont[a * tab.stride + t0 + c] : 0;
+    for (int i = threadIdx.x; i < BCONV_MAX_IN * BCONV_CHUNK; i += blockDim.x) {
+        const int a = i / BCONV_CHUNK, c = i % BCONV_CHUNK;
+        const u64 w = (a < tab.n_in && c < nt) ? tab.qhat_mont[a * tab.stride + t0 + c] : 0;
+        s_w[i] = make_uint2((u32)w, (u32)(w >> 32));
     }
-    if (threadIdx.x < 16) {
-        int a = threadIdx.x;
-        bool ok = a < tab.n_in && poly < n_polys;
+    if (threadIdx.x < BCONV_MAX_IN) {
+        const int a = threadIdx.x;
+        const bool ok = a < tab.n_in && poly < n_polys;
         s_qi[a] = ok ? tab.qhinv[a] : 0;
         s_qis[a] = ok ? tab.qhinv_sh[a] : 0;
         s_q[a] = ok ? pc.m[in.prime(poly * tab.n_in + a)].q : 1;
+        s_in[a] = ok ? in.row(poly * tab.n_in + a, log_n) : nullptr;
     }
     __syncthreads();
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || poly >= n_polys) return;
-    u64 lo[BCONV_CHUNK], hi[BCONV_CHUNK];
+    u32 acc[BCONV_CHUNK][4];
 #pragma unroll
-    for (int c = 0; c < BCONV_CHUNK; c++) lo[c] = hi[c] = 0;
+    for (int c = 0; c < BCONV_CHUNK; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
 #pragma unroll 2
     for (int a = 0; a < tab.n_in; a++) {
-        const u64 y = shoup_mul(in.row(poly * tab.n_in + a, log_n)[k], s_qi[a], s_qis[a], s_q[a]);
+        const u64 y = shoup_mul(s_in[a][k], s_qi[a], s_qis[a], s_q[a]);
+        const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++) {
-            const u64 w = s_qh[a * BCONV_CHUNK + c];
-            const u64 pl = y * w, ph = __umul64hi(y, w);
-            lo[c] += pl;
-            hi[c] += ph + (lo[c] < pl ? 1ull : 0ull);
+            const uint2 w = s_w[a * BCONV_CHUNK + c];
+            mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], y0, y1, w.x, w.y);
         }
     }
 #pragma unroll
@@ -680,11 +762,13 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         if (c < nt) {
             const int r = poly * tab.n_out + t0 + c;
             const int p = out.prime(r);
-            out.row(r, log_n)[k] = mont_reduce_wide(lo[c], hi[c], pc.m[p], pc.mont_qinv[p]);
+            const u64 lo = ((u64)acc[c][1] << 32) | acc[c][0], hi = ((u64)acc[c][3] << 32) | acc[c][2];
+            out.row(r, log_n)[k] = mont_reduce_wide(lo, hi, pc.m[p], pc.mont_qinv[p]);
         }
     }
 }
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s) {
+    if (tab.n_in > BCONV_MAX_IN) throw Error{HE_EINVAL, "basis conversion from more than 16 primes"};
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
     dim3 grid((unsigned)((n + 127) / 128), (unsigned)(n_chunks * n_polys));
@@ -694,131 +778,151 @@ void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, in
     prof_end(PROF_BCONV, s, 8.0 * (tab.n_in + tab.n_out) * (double)n_polys * (double)n);
 }
 
-__global__ void k_keyswitch_inner(KeyIP kp, int log_n) {
+__global__ void __launch_bounds__(EW_T) k_keyswitch_inner(KeyIP kp, int log_n) {
     const PrimeConsts &pc = c_pcs[kp.slot];
-    const size_t n = (size_t)1 << log_n;
-    const size_t total = (size_t)kp.n_rows * n;
-    const u64 two_n_mask = 2 * n - 1;
-    EW_LOOP(total) {
-        int t = (int)(gi >> log_n);
-        size_t k = gi & (n - 1);
-        size_t src = k;
+    const int t = blockIdx.y;
+    const int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
+    const u64 q = pc.m[p].q, qn = pc.mont_qinv[p];
+    const int jt = t < kp.l1 ? t / kp.alpha : -1;
+    const size_t row = (size_t)t << log_n;
+    EW_PAIRS_FOR(k, log_n) {
+        size_t s0 = k, s1 = k + 1;
         if (kp.galois) {  // hoisted rotation: position k reads the automorphism's source position
-            u64 e = 2ull * (__brev((u32)k) >> (32 - log_n)) + 1;
-            u64 e2 = (e * kp.galois) & two_n_mask;
-            src = __brev((u32)((e2 - 1) >> 1)) >> (32 - log_n);
+            s0 = automorph_src((u32)k, kp.galois, log_n);
+            s1 = automorph_src((u32)k + 1, kp.galois, log_n);
         }
-        int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
-        const u64 q = pc.m[p].q, qn = pc.mont_qinv[p];
-        int jt = t < kp.l1 ? t / kp.alpha : -1;
         // keys are in Montgomery form (times 2^64): the beta products are summed
         // in 128 bits (< beta q^2 < q 2^64) and reduced once
-        u64 l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+        u64 l00 = 0, h00 = 0, l01 = 0, h01 = 0, l10 = 0, h10 = 0, l11 = 0, h11 = 0;
         for (int j = 0; j < kp.beta; j++) {
-            u64 x = (j == jt) ? kp.d_ntt[((size_t)t << log_n) + src]
-                              : kp.ext[(((size_t)j * kp.n_rows + t) << log_n) + src];
-            const u64 *kb = kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n);
-            const u64 *ka = kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n);
-            u64 b = kb[k], a = ka[k];
-            u64 pl = x * b, ph = __umul64hi(x, b);
-            l0 += pl;
-            h0 += ph + (l0 < pl);
-            pl = x * a;
-            ph = __umul64hi(x, a);
-            l1 += pl;
-            h1 += ph + (l1 < pl);
+            const u64 *xs = (j == jt) ? kp.d_ntt + row : kp.ext + (((size_t)j * kp.n_rows + t) << log_n);
+            u64 x0, x1;
+            if (kp.galois) {
+                x0 = xs[s0];
+                x1 = xs[s1];
+            } else {
+                const ulonglong2 xv = ld2(xs + k);
+                x0 = xv.x;
+                x1 = xv.y;
+            }
+            const ulonglong2 b = ld2(kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n) + k);
+            const ulonglong2 a = ld2(kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n) + k);
+            mac128(l00, h00, x0, b.x);
+            mac128(l01, h01, x1, b.y);
+            mac128(l10, h10, x0, a.x);
+            mac128(l11, h11, x1, a.y);
         }
-        u64 a0 = mont_reduce(l0, h0, q, qn), a1 = mont_reduce(l1, h1, q, qn);
-        kp.acc[((size_t)t << log_n) + k] = a0;
-        kp.acc[(((size_t)kp.n_rows + t) << log_n) + k] = a1;
+        st2(kp.acc + row + k, mont_reduce(l00, h00, q, qn), mont_reduce(l01, h01, q, qn));
+        st2(kp.acc + (((size_t)kp.n_rows + t) << log_n) + k, mont_reduce(l10, h10, q, qn),
+            mont_reduce(l11, h11, q, qn));
     }
 }
 void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
-    size_t t = (size_t)k.n_rows << log_n;
+    need16(k.d_ntt);
+    need16(k.ext);
+    need16(k.key);
+    need16(k.acc);
     prof_begin(PROF_KS_INNER, s);
-    k_keyswitch_inner<<<grid_for(t, 256), 256, 0, s>>>(k, log_n);
+    k_keyswitch_inner<<<ew_grid(k.n_rows, log_n), EW_T, 0, s>>>(k, log_n);
     prof_end(PROF_KS_INNER, s, 8.0 * (3.0 * k.beta + 2.0) * (double)k.n_rows * (double)(1 << log_n));
 }
 
-__global__ void k_moddown_finish(Rows out, Rows acc, Rows conv, ScalarTab pinv, int n_rows, Rows add_to,
-                                 int add_mask, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        int p = out.prime(r);
-        u64 q = pc.m[p].q;
-        u64 v = shoup_mul(sub_mod(acc.row(r, log_n)[k], conv.row(r, log_n)[k], q), pinv.v[p], pinv.s[p], q);
-        int poly = r / out.lpp;
-        if ((add_mask >> poly) & 1) v = add_mod(v, add_to.row(r, log_n)[k], q);
-        out.row(r, log_n)[k] = v;
+__global__ void __launch_bounds__(EW_T) k_moddown_finish(Rows out, Rows acc, Rows conv, ScalarTab pinv,
+                                                         Rows add_to, int add_mask, int log_n) {
+    const int r = blockIdx.y, p = out.prime(r);
+    const u64 q = c_pcs[out.slot].m[p].q, w = pinv.v[p], ws = pinv.s[p];
+    const bool add = (add_mask >> (r / out.lpp)) & 1;
+    u64 *o = out.row(r, log_n);
+    const u64 *pa = acc.row(r, log_n), *pc = conv.row(r, log_n);
+    const u64 *pd = add ? add_to.row(r, log_n) : nullptr;
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 a = ld2(pa + k), c = ld2(pc + k);
+        u64 v0 = shoup_mul(sub_mod(a.x, c.x, q), w, ws, q), v1 = shoup_mul(sub_mod(a.y, c.y, q), w, ws, q);
+        if (add) {
+            const ulonglong2 d = ld2(pd + k);
+            v0 = add_mod(v0, d.x, q);
+            v1 = add_mod(v1, d.y, q);
+        }
+        st2(o + k, v0, v1);
     }
 }
 void moddown_finish(const Rows &out, const Rows &acc, const Rows &conv, const ScalarTab &pinv, int n_rows,
                     const Rows &add_to, int add_mask, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_moddown_finish<<<grid_for(t, 256), 256, 0, s>>>(out, acc, conv, pinv, n_rows, add_to, add_mask, log_n);
+    need16(out);
+    need16(acc);
+    need16(conv);
+    if (add_mask) need16(add_to);
+    k_moddown_finish<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, acc, conv, pinv, add_to, add_mask, log_n);
 }
 
 // ------------------------------------------------------------------ rescale / mod raise
-__global__ void k_rescale_lift(Rows lift, const u64 *l0, const u64 *l1, u64 ql, int l, int log_n) {
-    const PrimeConsts &pc = c_pcs[lift.slot];
-    const size_t n = (size_t)1 << log_n;
-    const size_t total = (size_t)2 * l * n;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);  // 0..2l-1: poly r / l, target prime r % l
-        size_t k = gi & (n - 1);
-        int poly = r / l, i = r % l;
-        const ModQ &m = pc.m[i];
-        u64 v = (poly ? l1 : l0)[k];
-        u64 vm = barrett_reduce(v, 0, m);
-        if (v > (ql - 1) / 2) vm = sub_mod(vm, barrett_reduce(ql, 0, m), m.q);
-        lift.row(r, log_n)[k] = vm;
+// centred representative of v mod q_src (v in [0, q_src)) reduced mod m
+__device__ __forceinline__ u64 centred_mod(u64 v, u64 q_src, u64 q_src_mod_m, const ModQ &m) {
+    u64 vm = barrett_reduce(v, 0, m);
+    if (v > (q_src - 1) / 2) vm = sub_mod(vm, q_src_mod_m, m.q);
+    return vm;
+}
+__global__ void __launch_bounds__(EW_T) k_rescale_lift(Rows lift, const u64 *l0, const u64 *l1, u64 ql, int l,
+                                                       int log_n) {
+    const int r = blockIdx.y;  // 0..2l-1: polynomial r / l, target prime r % l
+    const int poly = r / l, i = r % l;
+    const ModQ m = c_pcs[lift.slot].m[i];
+    const u64 qlm = barrett_reduce(ql, 0, m);
+    const u64 *src = poly ? l1 : l0;
+    u64 *o = lift.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 v = ld2(src + k);
+        st2(o + k, centred_mod(v.x, ql, qlm, m), centred_mod(v.y, ql, qlm, m));
     }
 }
 void rescale_lift(const Rows &lift, const u64 *last0, const u64 *last1, u64 ql, int l, int log_n, cudaStream_t s) {
-    size_t t = (size_t)2 * l << log_n;
-    k_rescale_lift<<<grid_for(t, 256), 256, 0, s>>>(lift, last0, last1, ql, l, log_n);
+    need16(lift);
+    need16(last0);
+    need16(last1);
+    k_rescale_lift<<<ew_grid(2 * l, log_n), EW_T, 0, s>>>(lift, last0, last1, ql, l, log_n);
 }
-__global__ void k_rescale_finish(Rows out, Rows in, Rows lift, ScalarTab qlinv, int n_rows, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t total = (size_t)n_rows << log_n, mask = ((size_t)1 << log_n) - 1;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & mask;
-        int p = out.prime(r);
-        u64 q = pc.m[p].q;
-        out.row(r, log_n)[k] =
-            shoup_mul(sub_mod(in.row(r, log_n)[k], lift.row(r, log_n)[k], q), qlinv.v[p], qlinv.s[p], q);
+__global__ void __launch_bounds__(EW_T) k_rescale_finish(Rows out, Rows in, Rows lift, ScalarTab qlinv, int log_n) {
+    const int r = blockIdx.y, p = out.prime(r);
+    const u64 q = c_pcs[out.slot].m[p].q, w = qlinv.v[p], ws = qlinv.s[p];
+    u64 *o = out.row(r, log_n);
+    const u64 *x = in.row(r, log_n), *y = lift.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 a = ld2(x + k), b = ld2(y + k);
+        st2(o + k, shoup_mul(sub_mod(a.x, b.x, q), w, ws, q), shoup_mul(sub_mod(a.y, b.y, q), w, ws, q));
     }
 }
 void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const ScalarTab &qlinv, int n_rows,
                     int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_rescale_finish<<<grid_for(t, 256), 256, 0, s>>>(out, in, lift, qlinv, n_rows, log_n);
+    need16(out);
+    need16(in);
+    need16(lift);
+    k_rescale_finish<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, in, lift, qlinv, log_n);
 }
-__global__ void k_modraise_lift(Rows out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n) {
-    const PrimeConsts &pc = c_pcs[out.slot];
-    const size_t n = (size_t)1 << log_n;
-    const size_t total = (size_t)n_rows * n;
-    EW_LOOP(total) {
-        int r = (int)(gi >> log_n);
-        size_t k = gi & (n - 1);
-        int poly = r / out.lpp;
-        const ModQ &m = pc.m[out.prime(r)];
-        u64 v = (poly ? c1 : c0)[k];
-        u64 vm = barrett_reduce(v, 0, m);
-        if (v > (q0 - 1) / 2) vm = sub_mod(vm, barrett_reduce(q0, 0, m), m.q);
-        out.row(r, log_n)[k] = vm;
+__global__ void __launch_bounds__(EW_T) k_modraise_lift(Rows out, const u64 *c0, const u64 *c1, u64 q0, int log_n) {
+    const int r = blockIdx.y;
+    const ModQ m = c_pcs[out.slot].m[out.prime(r)];
+    const u64 q0m = barrett_reduce(q0, 0, m);
+    const u64 *src = (r / out.lpp) ? c1 : c0;
+    u64 *o = out.row(r, log_n);
+    EW_PAIRS_FOR(k, log_n) {
+        const ulonglong2 v = ld2(src + k);
+        st2(o + k, centred_mod(v.x, q0, q0m, m), centred_mod(v.y, q0, q0m, m));
     }
 }
 void modraise_lift(const Rows &out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n, cudaStream_t s) {
-    size_t t = (size_t)n_rows << log_n;
-    k_modraise_lift<<<grid_for(t, 256), 256, 0, s>>>(out, c0, c1, q0, n_rows, log_n);
+    need16(out);
+    need16(c0);
+    need16(c1);
+    k_modraise_lift<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, c0, c1, q0, log_n);
 }
 
 // ------------------------------------------------------------------ sampling
+// (grid-stride loops over flat element indices: these kernels run once per
+// encryption, decryption or key generation)
+#define EW_LOOP(total)                                                                 \
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (total);      \
+         gi += (size_t)gridDim.x * blockDim.x)
+
 __device__ __forceinline__ void philox4x32_10(u32 c[4], u32 k0, u32 k1) {
     const u32 M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
