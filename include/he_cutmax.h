@@ -140,6 +140,16 @@ int he_ct_info(const he_ct *ct, uint32_t *level, double *scale);
  * c0 and c1, for zero-copy inspection. */
 int he_ct_device(const he_ct *ct, uint64_t **dev, size_t *poly_stride);
 void he_ct_free(he_ct *ct);
+/* ---- batches (engineering: the paper evaluates one ciphertext at a time) -
+ * A batch holds several ciphertexts of one level and scale back to back; every
+ * operation on a batch acts on all members with one kernel launch per step.
+ * he_batch_pack copies n ciphertexts (batches allowed: their members are
+ * concatenated) at the lowest of their levels into a new batch; members must
+ * share the scale (HE_EINVAL otherwise).  he_batch_member copies member i
+ * into a new single ciphertext.  he_batch_size reports the member count. */
+int he_batch_pack(he_ctx *ctx, const he_ct *const *cts, size_t n, he_ct **out);
+int he_batch_member(he_ctx *ctx, const he_ct *batch, uint32_t i, he_ct **out);
+int he_batch_size(const he_ct *ct, uint32_t *n);
 
 /* ---- homomorphic operations ------------------------------------------ */
 int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
@@ -208,8 +218,10 @@ int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out)
 
 /* ---- CutMax (Alg. 2) and nucleus sampling (Alg. 3) ------------------- */
 /* Circuit plan: the range-scaling constants of Sect. 3.2's obligations.
- * n real entries per ciphertext; packing 0 = replicate (n a power of two
- * dividing N/2, slot j = x[j mod n]), 1 = zero-pad (slots n.. are zero).
+ * n real entries (the vocabulary) per stream, spread over cts ciphertexts
+ * (0 is read as 1): ciphertext c of a stream holds entries c*N/2 .. in its
+ * slots, the last one zero-padded.  packing 0 = replicate (one ciphertext, n
+ * a power of two dividing N/2, slot j = x[j mod n]), 1 = zero-pad.
  * Per iteration t < T: power[t] (p), c[t], k[t] Goldschmidt inverse-sqrt
  * iterations, kappa[t] range scale of V_t = sum (n y - S)^2, y0[t] initial
  * guess.  Final normalisation: Goldschmidt inverse of degree d on
@@ -230,12 +242,16 @@ typedef struct {
     double kappa_f;
     const double *norm;
     int32_t bootstrap;
+    uint32_t cts;
 } he_cutmax_plan;
 
 /* Generate every key the plan needs (rotations 2^i, relinearisation and,
  * with bootstrapping, its rotations and conjugation). */
 int he_cutmax_prepare(he_ctx *ctx, const he_cutmax_plan *plan);
-/* CutMax_HE (Alg. 2): out = encrypted near-one-hot of argmax(in). */
+/* CutMax_HE (Alg. 2): out = encrypted near-one-hot of argmax(in).  `in` may
+ * be a batch (he_batch_pack) of S streams of plan->cts ciphertexts each,
+ * stream-major; every step then runs once for the whole batch, and the
+ * output is the batch of the streams' results in the same order. */
 int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out);
 /* Nucleus one-shot sampling (Alg. 3): out = CutMax(logits + rand_ct), where
  * rand_ct encrypts the cut noise G_i = U_i^(1/alpha), alpha = ln(1-q)/ln(p)

@@ -21,6 +21,11 @@ Circuit (iteration t; Y at level l):
   Y  = u^p                             square and multiply
 Final (Alg. 2 last step): S = rotsum(Y); a = 1 - kappa_f S;
   F = prod_{i<=d} (1 + a^(2^i)); Z = (kappa_f Y) * F.
+
+A vocabulary longer than the slot count spreads over plan.cts ciphertexts
+(entries c*slots .. in ciphertext c, the last zero-padded): every sum over
+the vocabulary adds the ciphertexts before the rotate-and-sum, and S, h and F
+then serve every ciphertext of the stream.
 """
 import math
 
@@ -119,31 +124,52 @@ def inverse_goldschmidt(he, S, kappa_f, d):
     return F
 
 
+def _masks(plan):
+    """Per-ciphertext 0/1 slot masks of a zero-padded stream (None if unpadded)."""
+    if not plan.pad:
+        return None
+    k = getattr(plan, "cts", 1)
+    flat = np.zeros(k * plan.slots)
+    flat[:plan.n] = 1.0
+    return [flat[c * plan.slots:(c + 1) * plan.slots] for c in range(k)]
+
+
+def _vsum(ctx, cts):
+    """Sum of the stream's ciphertexts (Y_0 + Y_1 + ...)."""
+    acc = cts[0]
+    for c in cts[1:]:
+        acc = ctx.add(acc, c)
+    return acc
+
+
 def cutmax_he(he, ct, plan, bootstrap=None):
-    """Alg. 2 over one ciphertext packed by ``plan.packing``."""
+    """Alg. 2 over one stream: one ciphertext packed by ``plan.packing``, or a
+    list of plan.cts zero-padded ciphertexts (the result is then a list)."""
     ctx = he.ctx
+    many = isinstance(ct, (list, tuple))
+    Ys = list(ct) if many else [ct]
     n, steps, m = plan.n, plan.rotsum_steps, plan.pad
-    mask = None
-    if m:
-        mask = np.zeros(plan.slots)
-        mask[:n] = 1.0
-    Y = ct
+    masks = _masks(plan)
     for t in range(plan.T):
-        S = he.rotsum(Y, steps)
-        D = ctx.sub(ctx.mul_int(Y, n), S)
-        E = he.mul_rescale(D, D)
-        V = he.rotsum(E, steps)
+        S = he.rotsum(_vsum(ctx, Ys), steps)
+        Ds = [ctx.sub(ctx.mul_int(Y, n), S) for Y in Ys]
+        Es = [he.mul_rescale(D, D) for D in Ds]
+        V = he.rotsum(_vsum(ctx, Es), steps)
         if m:
             V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
         h = invsqrt_goldschmidt(he, V, plan.kappa[t], plan.y0[t], plan.k[t])
         coef = 2.0 * math.sqrt(plan.kappa[t] * n) / plan.c[t]
-        Dp = he.mul_plain_rescale(D, coef * mask) if m else he.mcr(D, coef)
-        u = he.mul_rescale(Dp, h)
-        u = he.add_plain_vec(u, mask) if m else he.add_const(u, 1.0)
-        Y = he.power(u, plan.p[t])
-    S = he.rotsum(Y, steps)
+        new = []
+        for c, D in enumerate(Ds):
+            Dp = he.mul_plain_rescale(D, coef * masks[c]) if m else he.mcr(D, coef)
+            u = he.mul_rescale(Dp, h)
+            u = he.add_plain_vec(u, masks[c]) if m else he.add_const(u, 1.0)
+            new.append(he.power(u, plan.p[t]))
+        Ys = new
+    S = he.rotsum(_vsum(ctx, Ys), steps)
     F = inverse_goldschmidt(he, S, plan.kappa_f, plan.d)
-    return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
+    Z = [he.mul_rescale(he.mcr(Y, plan.kappa_f), F) for Y in Ys]
+    return Z if many else Z[0]
 
 
 def cutmax_he_boot(he, ct, plan, boot):

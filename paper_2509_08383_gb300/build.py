@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhecutmax.so")
 SOURCES = ["kernels.cu", "context.cu", "circuit.cu", "capi.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "kernels.h", "context.h"]
+HEADERS = ["common.cuh", "kernels.h", "context.h", "arena.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

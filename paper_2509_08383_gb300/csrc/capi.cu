@@ -33,6 +33,10 @@ static void launched(he_ctx *cx, const char *what) { check_cuda(cudaGetLastError
 static void own(const he_ctx *cx, const he_ct *ct) {
     if (ct && ct->ctx != cx) throw Error{HE_EINVAL, "ciphertext does not belong to this context"};
 }
+// entry points that read or write one ciphertext's data refuse batches
+static void single(const he_ct *ct) {
+    if (ct && ct->batch != 1) throw Error{HE_EINVAL, "a batch here: take its members with he_batch_member"};
+}
 
 extern "C" {
 
@@ -204,6 +208,7 @@ int he_decrypt(he_ctx *cx, const he_ct *ct, double *re, double *im, size_t n_slo
     if (!cx || !ct || !re) return HE_EINVAL;
     API_TRY
     own(cx, ct);
+    single(ct);
     const size_t N = cx->N();
     need(n_slots <= N / 2, "more values than slots");
     double *d_c = cx->d_dbl + N, *d_re = cx->d_dbl, *d_im = cx->d_dbl + N / 2;
@@ -219,6 +224,7 @@ int he_decrypt_poly(he_ctx *cx, const he_ct *ct, double *out) {
     if (!cx || !ct || !out) return HE_EINVAL;
     API_TRY
     own(cx, ct);
+    single(ct);
     double *d_c = cx->d_dbl + cx->N();
     decrypt_dev(cx, ct, d_c);
     check_cuda(cudaMemcpyAsync(out, d_c, cx->N() * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
@@ -230,6 +236,7 @@ int he_ct_export(he_ctx *cx, const he_ct *ct, uint64_t *out, size_t cap) {
     if (!cx || !ct || !out) return HE_EINVAL;
     API_TRY
     own(cx, ct);
+    single(ct);
     const size_t N = cx->N(), m = (size_t)(ct->level + 1) * N;
     need(cap >= 2 * m, "export buffer too small");
     u64 *tmp = (u64 *)cx->arena.alloc(2 * m * 8);
@@ -275,6 +282,36 @@ int he_ct_device(const he_ct *ct, uint64_t **dev, size_t *poly_stride) {
 }
 
 void he_ct_free(he_ct *ct) { ct_release(ct); }
+
+int he_batch_pack(he_ctx *cx, const he_ct *const *cts, size_t n, he_ct **out) {
+    if (!cx || !cts || !out || n == 0) return HE_EINVAL;
+    API_TRY
+    for (size_t i = 0; i < n; i++) {
+        need(cts[i] != nullptr, "null ciphertext");
+        own(cx, cts[i]);
+    }
+    need(n <= 65536, "too many ciphertexts");
+    Ct r = op_batch_pack(cx, cts, (int)n);
+    launched(cx, "batch pack");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_batch_member(he_ctx *cx, const he_ct *batch, uint32_t i, he_ct **out) {
+    if (!cx || !batch || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, batch);
+    Ct r = op_batch_member(cx, batch, (int)i);
+    launched(cx, "batch member");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_batch_size(const he_ct *ct, uint32_t *n) {
+    if (!ct || !n) return HE_EINVAL;
+    *n = (uint32_t)ct->batch;
+    return HE_OK;
+}
 
 #define UNARY_OP(name, expr)                                     \
     int name {                                                   \

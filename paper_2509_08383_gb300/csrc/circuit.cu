@@ -44,19 +44,23 @@ struct HE {
         Ct t = op_mul(cx, a, b);
         return op_rescale(cx, t.get());
     }
-    // device slot vector (n_slots doubles) encoded at scale E, multiply, rescale
-    Ct mul_plain_rescale(const he_ct *ct, const double *d_vec, int n_slots, double target = -1) {
+    // n_pt device slot vectors (n_pt x n_slots doubles; member m of a batch
+    // uses vector m % n_pt) encoded at scale E, multiply, rescale
+    Ct mul_plain_rescale(const he_ct *ct, const double *d_vec, int n_slots, double target = -1, int n_pt = 1) {
         if (target < 0) target = delta;
         double E = (target * (double)q(ct->level)) / ct->scale;
-        double *d_pt = cx->d_dbl + cx->N();
-        encode_dev(cx, d_vec, nullptr, n_slots, E, d_pt);
-        Ct t = op_mul_plain(cx, ct, d_pt, ct->scale * E);
+        Scratch sc{cx, {}};
+        double *d_pt = n_pt == 1 ? cx->d_dbl + cx->N() : (double *)sc.get((size_t)n_pt * cx->N());
+        for (int i = 0; i < n_pt; i++) encode_dev(cx, d_vec + (size_t)i * n_slots, nullptr, n_slots, E, d_pt + i * cx->N());
+        Ct t = op_mul_plain(cx, ct, d_pt, ct->scale * E, n_pt);
         return op_rescale(cx, t.get());
     }
-    Ct add_plain_vec(const he_ct *ct, const double *d_vec, int n_slots) {
-        double *d_pt = cx->d_dbl + cx->N();
-        encode_dev(cx, d_vec, nullptr, n_slots, ct->scale, d_pt);
-        return op_add_plain(cx, ct, d_pt);
+    Ct add_plain_vec(const he_ct *ct, const double *d_vec, int n_slots, int n_pt = 1) {
+        Scratch sc{cx, {}};
+        double *d_pt = n_pt == 1 ? cx->d_dbl + cx->N() : (double *)sc.get((size_t)n_pt * cx->N());
+        for (int i = 0; i < n_pt; i++)
+            encode_dev(cx, d_vec + (size_t)i * n_slots, nullptr, n_slots, ct->scale, d_pt + i * cx->N());
+        return op_add_plain(cx, ct, d_pt, n_pt);
     }
     Ct rotsum(const he_ct *ct, int steps) {
         Ct cur = op_copy(cx, ct);
@@ -112,7 +116,7 @@ int rotsum_steps(const Plan &pl, int slots) {
 
 }  // namespace
 
-int Plan::pad(int slots) const { return packing == 0 ? 0 : slots - n; }
+int Plan::pad(int slots) const { return packing == 0 ? 0 : cps * slots - n; }
 
 Plan plan_from(const he_cutmax_plan *p) {
     if (!p || p->T < 1 || p->T > 64 || !p->power || !p->c || !p->k || !p->kappa || !p->y0 || p->n < 2)
@@ -134,6 +138,8 @@ Plan plan_from(const he_cutmax_plan *p) {
         pl.norm.push_back(nm);
     }
     pl.bootstrap = p->bootstrap != 0;
+    pl.cps = p->cts ? (int)p->cts : 1;
+    if (pl.cps > 64) throw Error{HE_EINVAL, "more than 64 ciphertexts per stream"};
     pl.d = (int)p->d;
     pl.kappa_f = p->kappa_f;
     if (!(pl.kappa_f > 0)) throw Error{HE_ERANGE, "kappa_f must be positive"};
@@ -156,57 +162,86 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl);
 int boot_out_level(he_ctx *cx);
 Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage);
 
+// Streams of pl.cps ciphertexts each, stream-major in the batch.  Checks the
+// shape and builds the per-position slot masks (1 on real entries) that the
+// zero-padded packing needs.
+struct StreamShape {
+    int cps, S, slots, steps, m;
+    std::vector<double> mask;  // [cps][slots]
+};
+static StreamShape stream_shape(he_ctx *cx, const he_ct *in, const Plan &pl) {
+    StreamShape sh;
+    sh.slots = cx->n / 2;
+    sh.cps = pl.cps;
+    if (in->batch % sh.cps) throw Error{HE_EINVAL, "batch is not a whole number of streams"};
+    sh.S = in->batch / sh.cps;
+    if (pl.n > sh.cps * sh.slots) throw Error{HE_EINVAL, "plan n exceeds the slots of its ciphertexts"};
+    if (sh.cps > 1 && pl.n <= (sh.cps - 1) * sh.slots) throw Error{HE_EINVAL, "plan uses more ciphertexts than n needs"};
+    if (pl.packing == 0 && (sh.cps != 1 || sh.slots % pl.n != 0 || (pl.n & (pl.n - 1))))
+        throw Error{HE_EINVAL, "replicated packing needs one ciphertext and n a power of two dividing N/2"};
+    sh.steps = rotsum_steps(pl, sh.slots);
+    sh.m = pl.pad(sh.slots);
+    if (sh.m) {
+        sh.mask.assign((size_t)sh.cps * sh.slots, 0.0);
+        for (int i = 0; i < pl.n; i++) sh.mask[i] = 1.0;
+    }
+    return sh;
+}
+// per-stream sum of a batch (a copy when streams hold one ciphertext) and the
+// broadcast of a per-stream batch back to the streams' ciphertexts
+static Ct stream_sum(he_ctx *cx, const he_ct *a, int cps) {
+    return cps > 1 ? op_group(cx, a, cps, true) : op_copy(cx, a);
+}
+static Ct stream_bcast(he_ctx *cx, const he_ct *a, int cps) {
+    return cps > 1 ? op_group(cx, a, cps, false) : op_copy(cx, a);
+}
+// device copy of `vals` scaled by c, in scratch
+static double *upload_scaled(he_ctx *cx, Scratch &sc, const std::vector<double> &vals, double c) {
+    std::vector<double> v(vals);
+    for (double &x : v) x *= c;
+    double *d = (double *)sc.get(v.size());
+    // a pageable source is staged before the call returns, so v may go
+    check_cuda(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, cx->stream),
+               "upload mask");
+    return d;
+}
+
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
-    const int slots = cx->n / 2;
     if (pl.bootstrap) return cutmax_boot(cx, in, pl);
-    if (pl.n > slots) throw Error{HE_EINVAL, "plan n exceeds the slot count"};
-    if (pl.packing == 0 && (slots % pl.n != 0 || (pl.n & (pl.n - 1))))
-        throw Error{HE_EINVAL, "replicated packing needs n a power of two dividing N/2"};
+    StreamShape sh = stream_shape(cx, in, pl);
     int depth = pl.d + 3;
     for (int t = 0; t < pl.T; t++) depth += 2 + 2 * pl.k[t] + power_depth(pl.p[t]);
     if (depth > in->level) throw Error{HE_ELEVEL, "circuit depth " + std::to_string(depth) + " exceeds level " +
                                                    std::to_string(in->level)};
     HE he{cx, cx->delta};
-    const int steps = rotsum_steps(pl, slots);
-    const int m = pl.pad(slots);
-    double *d_mask = nullptr;
-    std::vector<double> mask;
-    if (m) {
-        // slot masks live in the third N-double scratch block: [mask | coef*mask]
-        mask.assign(slots, 0.0);
-        for (int i = 0; i < pl.n; i++) mask[i] = 1.0;
-        d_mask = cx->d_dbl + 2 * cx->N();
-        check_cuda(cudaMemcpyAsync(d_mask, mask.data(), slots * sizeof(double), cudaMemcpyHostToDevice, cx->stream),
-                   "upload mask");
-    }
+    const int cps = sh.cps, m = sh.m;
+    Scratch sc{cx, {}};
+    double *d_mask = m ? upload_scaled(cx, sc, sh.mask, 1.0) : nullptr;
     Ct Y = op_copy(cx, in);
     for (int t = 0; t < pl.T; t++) {
-        Ct S = he.rotsum(Y.get(), steps);
-        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), S.get(), true);
+        Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).get(), true);
         Ct E = he.mul_rescale(D.get(), D.get());
-        Ct V = he.rotsum(E.get(), steps);
+        Ct V = he.rotsum(stream_sum(cx, E.get(), cps).get(), sh.steps);
         if (m) {
             Ct S2 = he.mul_rescale(S.get(), S.get());
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
         }
-        Ct h = invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t]);
+        Ct h = stream_bcast(cx, invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t]).get(), cps);
         double coef = 2.0 * std::sqrt(pl.kappa[t] * pl.n) / pl.c[t];
         Ct Dp;
         if (m) {
-            for (int i = 0; i < pl.n; i++) mask[i] = coef;
-            double *d_cm = cx->d_dbl + 2 * cx->N() + slots;
-            check_cuda(cudaMemcpyAsync(d_cm, mask.data(), slots * sizeof(double), cudaMemcpyHostToDevice, cx->stream),
-                       "upload scaled mask");
-            Dp = he.mul_plain_rescale(D.get(), d_cm, slots);
+            Scratch s2{cx, {}};
+            Dp = he.mul_plain_rescale(D.get(), upload_scaled(cx, s2, sh.mask, coef), sh.slots, -1, cps);
         } else {
             Dp = he.mcr(D.get(), coef);
         }
         Ct u = he.mul_rescale(Dp.get(), h.get());
-        u = m ? he.add_plain_vec(u.get(), d_mask, slots) : he.add_const(u.get(), 1.0);
+        u = m ? he.add_plain_vec(u.get(), d_mask, sh.slots, cps) : he.add_const(u.get(), 1.0);
         Y = he.power(u.get(), pl.p[t]);
     }
-    Ct S = he.rotsum(Y.get(), steps);
-    Ct F = inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d);
+    Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+    Ct F = stream_bcast(cx, inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d).get(), cps);
     return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());
 }
 
@@ -399,24 +434,14 @@ static void build_level(he_ctx *cx, LinLevel &L, int level, double scale_in, dou
 // result is again accumulated in QP; one ModDown at the end.
 static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
     build_level(cx, L, x->level, x->scale, target);
-    const int l = x->level, h = cx->n / 2;
+    const int l = x->level, h = cx->n / 2, B = x->batch;
     const size_t N = cx->N();
     const LevelTabs &LT = cx->lv[l];
     const int ne = LT.n_ext;
-    const size_t qp_bytes = (size_t)2 * ne * N * 8, ext_bytes = (size_t)LT.beta * ne * N * 8;
+    // per member: a QP-basis ciphertext of 2 ne rows; members back to back
+    const size_t qp_w = (size_t)2 * ne * N, xs = ct_member_stride(x);
     cudaStream_t s = cx->stream;
-    struct Bufs {  // arena buffers, released on every exit path
-        he_ctx *cx;
-        std::vector<std::pair<u64 *, size_t>> v;
-        u64 *get(size_t b) {
-            u64 *p = (u64 *)cx->arena.alloc(b);
-            v.emplace_back(p, b);
-            return p;
-        }
-        ~Bufs() {
-            for (auto &pb : v) cx->arena.release(pb.first, pb.second);
-        }
-    } bufs{cx, {}};
+    Scratch bufs{cx, {}};
     auto qp = [&](u64 *base) { return make_rows(base, (size_t)ne * N, ne, l + 1, cx->nq); };
     // baby steps in QP
     std::vector<u64 *> baby(L.baby.size(), nullptr);
@@ -425,24 +450,26 @@ static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
         bool used = false;
         for (auto &row : L.idx) used |= row[b] >= 0;
         if (!used) continue;
-        baby[b] = bufs.get(qp_bytes);
+        baby[b] = bufs.get((size_t)B * qp_w);
         if (b == 0) {
-            ew_qp_lift(baby[b], ct_poly(x, 0), l + 1, ne, 0, 0, cx->p_mod, cx->slot, cx->log_n, s);
-            ew_qp_lift(baby[b] + (size_t)ne * N, ct_poly(x, 1), l + 1, ne, 0, 0, cx->p_mod, cx->slot, cx->log_n, s);
+            ew_qp_lift(baby[b], ct_poly(x, 0), l + 1, ne, 0, 0, cx->p_mod, cx->slot, cx->log_n, s, B, qp_w, xs);
+            ew_qp_lift(baby[b] + (size_t)ne * N, ct_poly(x, 1), l + 1, ne, 0, 0, cx->p_mod, cx->slot, cx->log_n, s, B,
+                       qp_w, xs);
             continue;
         }
         u64 g = rot_galois(cx, L.baby[b]);
         const KeyDev *key = find_key(cx, g);
         if (!key) throw Error{HE_ENOKEY, "bootstrapping rotation key missing"};
         if (!ext) {
-            ext = bufs.get(ext_bytes);
-            modup(cx, ct_poly(x, 1), l, ext);
+            ext = bufs.get((size_t)B * ks_ext_words(cx, l));
+            modup(cx, ct_poly(x, 1), l, ext, B, xs);
         }
-        ks_inner(cx, ct_poly(x, 1), ext, l, *key, g, baby[b]);
-        ew_qp_lift(baby[b], ct_poly(x, 0), l + 1, ne, g, 1, cx->p_mod, cx->slot, cx->log_n, s);
+        ks_inner(cx, ct_poly(x, 1), ext, l, *key, g, baby[b], B, xs);
+        ew_qp_lift(baby[b], ct_poly(x, 0), l + 1, ne, g, 1, cx->p_mod, cx->slot, cx->log_n, s, B, qp_w, xs);
     }
     // giant groups
-    u64 *tot = bufs.get(qp_bytes), *inner = bufs.get(qp_bytes);
+    u64 *tot = bufs.get((size_t)B * qp_w), *inner = bufs.get((size_t)B * qp_w);
+    u64 *gext = nullptr, *gacc = nullptr;
     bool have = false;
     for (size_t g = 0; g < L.giant.size(); g++) {
         DiagMac dm;
@@ -450,6 +477,9 @@ static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
         dm.slot = cx->slot;
         dm.l1 = l + 1;
         dm.nq = cx->nq;
+        dm.batch = B;
+        dm.c_stride = qp_w;
+        dm.out_stride = qp_w;
         for (size_t b = 0; b < L.baby.size(); b++) {
             int p = L.idx[g][b];
             if (p < 0) continue;
@@ -466,26 +496,32 @@ static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
         dm.out1 = dst + (size_t)ne * N;
         ew_diag_mac(dm, ne, cx->log_n, s);
         if (!rot) {
-            if (have) ew_add(qp(tot), qp(tot), qp(inner), 2 * ne, 0, cx->log_n, s);
+            if (have) ew_add(qp(tot), qp(tot), qp(inner), 2 * B * ne, 0, cx->log_n, s);
             have = true;
             continue;
         }
         // ModDown of the group, then its giant rotation, accumulated in QP
-        Ct y(ct_alloc(cx, l, x->scale * L.E));
-        moddown(cx, inner, l, ct_rows(y.get()), ct_rows(y.get()), 0);
+        Ct y(ct_alloc(cx, l, x->scale * L.E, B));
+        moddown(cx, inner, l, ct_rows(y.get()), ct_rows(y.get()), 0, B);
         u64 gg = rot_galois(cx, L.giant[g]);
         const KeyDev *key = find_key(cx, gg);
         if (!key) throw Error{HE_ENOKEY, "bootstrapping rotation key missing"};
-        modup(cx, ct_poly(y.get(), 1), l, cx->ks_ext);
-        u64 *acc = have ? cx->ks_acc : tot;
-        ks_inner(cx, ct_poly(y.get(), 1), cx->ks_ext, l, *key, gg, acc);
-        ew_qp_lift(acc, ct_poly(y.get(), 0), l + 1, ne, gg, 1, cx->p_mod, cx->slot, cx->log_n, s);
-        if (have) ew_add(qp(tot), qp(tot), qp(acc), 2 * ne, 0, cx->log_n, s);
+        if (!gext) gext = B == 1 ? cx->ks_ext : bufs.get((size_t)B * ks_ext_words(cx, l));
+        const size_t ys = ct_member_stride(y.get());
+        modup(cx, ct_poly(y.get(), 1), l, gext, B, ys);
+        u64 *acc = tot;
+        if (have) {
+            if (!gacc) gacc = B == 1 ? cx->ks_acc : bufs.get((size_t)B * qp_w);
+            acc = gacc;
+        }
+        ks_inner(cx, ct_poly(y.get(), 1), gext, l, *key, gg, acc, B, ys);
+        ew_qp_lift(acc, ct_poly(y.get(), 0), l + 1, ne, gg, 1, cx->p_mod, cx->slot, cx->log_n, s, B, qp_w, ys);
+        if (have) ew_add(qp(tot), qp(tot), qp(acc), 2 * B * ne, 0, cx->log_n, s);
         have = true;
     }
     if (!have) throw Error{HE_EINVAL, "empty linear transform level"};
-    Ct out(ct_alloc(cx, l, x->scale * L.E));
-    moddown(cx, tot, l, ct_rows(out.get()), ct_rows(out.get()), 0);
+    Ct out(ct_alloc(cx, l, x->scale * L.E, B));
+    moddown(cx, tot, l, ct_rows(out.get()), ct_rows(out.get()), 0, B);
     return op_rescale(cx, out.get());
 }
 
@@ -728,33 +764,27 @@ Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
 // through u' = norm^(1/p) u, so that every refreshed ciphertext is bounded).
 static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     if (!cx->boot_state) throw Error{HE_EINVAL, "bootstrapped plan needs he_bootstrap_prepare"};
-    const int slots = cx->n / 2;
-    if (pl.n > slots) throw Error{HE_EINVAL, "plan n exceeds the slot count"};
-    if (pl.packing == 0 && (slots % pl.n != 0 || (pl.n & (pl.n - 1))))
-        throw Error{HE_EINVAL, "replicated packing needs n a power of two dividing N/2"};
+    StreamShape sh = stream_shape(cx, in, pl);
+    const int slots = sh.slots, cps = sh.cps, m = sh.m;
     HE he{cx, cx->delta};
-    const int steps = rotsum_steps(pl, slots);
-    const int m = pl.pad(slots);
     auto ensure = [&](Ct c, int need) -> Ct { return c->level < need ? bootstrap_ct(cx, c.get()) : std::move(c); };
-    std::vector<double> mask;
-    double *d_mask = cx->d_dbl + 2 * cx->N(), *d_cm = cx->d_dbl + 2 * cx->N() + slots;
-    if (m) {
-        mask.assign(slots, 0.0);
-        for (int i = 0; i < pl.n; i++) mask[i] = 1.0;
-    }
     // compute only on the levels a bootstrap hands back: the primes above are
     // the bootstrapping primes, where products of Delta-scale ciphertexts
     // would shrink the scale
     const int out_level = boot_out_level(cx);
     Ct Y = in->level > out_level ? op_drop(cx, in, out_level) : op_copy(cx, in);
+    // Goldschmidt pair packed in one ciphertext per stream: slots [0, s/2) hold
+    // g, slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
+    const int half = slots / 2;
+    const u64 g_half = rot_galois(cx, half);
     for (int t = 0; t < pl.T; t++) {
         const int p = pl.p[t], k = pl.k[t];
         const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
         Y = ensure(std::move(Y), 3);
-        Ct S = he.rotsum(Y.get(), steps);
-        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), S.get(), true);
+        Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).get(), true);
         Ct E = he.mul_rescale(D.get(), D.get());
-        Ct V = he.rotsum(E.get(), steps);
+        Ct V = he.rotsum(stream_sum(cx, E.get(), cps).get(), sh.steps);
         if (m) {
             Ct S2 = he.mul_rescale(S.get(), S.get());
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
@@ -763,27 +793,20 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         const double coef = 2.0 * std::sqrt(kap * pl.n) / pl.c[t] * rn;
         Ct Dp;
         if (m) {
-            std::vector<double> cm(slots, 0.0);
-            for (int i = 0; i < pl.n; i++) cm[i] = coef;
-            check_cuda(cudaMemcpyAsync(d_cm, cm.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
-            Dp = he.mul_plain_rescale(D.get(), d_cm, slots);
+            Scratch s2{cx, {}};
+            Dp = he.mul_plain_rescale(D.get(), upload_scaled(cx, s2, sh.mask, coef), slots, -1, cps);
         } else {
             Dp = he.mcr(D.get(), coef);
         }
-        // Goldschmidt pair packed in one ciphertext: slots [0, s/2) hold g,
-        // slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
-        const int half = slots / 2;
         std::vector<double> vlo(slots, 0.0), vhi(slots, 0.0);
         for (int i = 0; i < half; i++) vlo[i] = y0;
         for (int i = half; i < slots; i++) vhi[i] = y0 / 2.0;
-        double *d_v = cx->d_dbl + 2 * cx->N();
+        Scratch sv{cx, {}};
+        const double *d_vlo = upload_scaled(cx, sv, vlo, 1.0), *d_vhi = upload_scaled(cx, sv, vhi, 1.0);
         Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), 1.5);
-        check_cuda(cudaMemcpyAsync(d_v, vlo.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
-        Ct P = he.mul_plain_rescale(x.get(), d_v, slots);
-        check_cuda(cudaMemcpyAsync(d_v, vhi.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
-        P = he.add_plain_vec(P.get(), d_v, slots);
+        Ct P = he.mul_plain_rescale(x.get(), d_vlo, slots);
+        P = he.add_plain_vec(P.get(), d_vhi, slots);
         P = he.mul_rescale(P.get(), a.get());
-        const u64 g_half = rot_galois(cx, half);
         for (int i = 2; i <= k; i++) {
             if (P->level < 2) P = bootstrap_ct(cx, P.get());
             Ct Q = he.mul_rescale(P.get(), op_automorph(cx, P.get(), g_half).get());
@@ -791,17 +814,14 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         }
         P = ensure(std::move(P), 1);
         for (int i = 0; i < slots; i++) vhi[i] = i < half ? 0.0 : 1.0;
-        check_cuda(cudaMemcpyAsync(d_v, vhi.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
-        Ct hm = he.mul_plain_rescale(P.get(), d_v, slots);
+        Ct hm = he.mul_plain_rescale(P.get(), upload_scaled(cx, sv, vhi, 1.0), slots);
         Ct h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
         h = ensure(std::move(h), 1);
         Dp = ensure(std::move(Dp), 1);
-        Ct u = he.mul_rescale(Dp.get(), h.get());
+        Ct u = he.mul_rescale(Dp.get(), stream_bcast(cx, h.get(), cps).get());
         if (m) {
-            std::vector<double> rm(slots, 0.0);
-            for (int i = 0; i < pl.n; i++) rm[i] = rn;
-            check_cuda(cudaMemcpyAsync(d_mask, rm.data(), slots * 8, cudaMemcpyHostToDevice, cx->stream), "mask");
-            u = he.add_plain_vec(u.get(), d_mask, slots);
+            Scratch s3{cx, {}};
+            u = he.add_plain_vec(u.get(), upload_scaled(cx, s3, sh.mask, rn), slots, cps);
         } else {
             u = he.add_const(u.get(), rn);
         }
@@ -809,8 +829,8 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         Y = he.power(u.get(), p);
     }
     Y = ensure(std::move(Y), pl.d + 3);
-    Ct S = he.rotsum(Y.get(), steps);
-    Ct F = inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d);
+    Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+    Ct F = stream_bcast(cx, inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d).get(), cps);
     return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());
 }
 

@@ -95,11 +95,13 @@ __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) {
     return a >= b ? a - b : a + q - b;
 }
 
-// A batch of limb rows.  Default addressing: row r belongs to polynomial
-// r / lpp, limb t = r % lpp; limb t uses prime prime0 + t when t < l1, else
-// prime nq + (t - l1) (the special primes of the key-switching basis).
-// Descriptor addressing (desc != nullptr): row r lives at base + desc[r].x*N
-// and uses prime desc[r].y.
+// A batch of limb rows.  Row r belongs to polynomial r / lpp, limb t = r % lpp.
+// Default addressing: the limb sits at base + poly*poly_stride + t*N and uses
+// prime prime0 + t when t < l1, else prime nq + (t - l1) (the special primes
+// of the key-switching basis).  Descriptor addressing (desc != nullptr): limb
+// t of every polynomial sits at base + poly*poly_stride + desc[t].x*N and uses
+// prime desc[t].y.  pmod > 0 takes the polynomial index modulo pmod, so that
+// one operand (a plaintext, say) serves every member of a batch.
 struct Rows {
     u64 *base;
     size_t poly_stride;  // elements between consecutive polynomials
@@ -108,14 +110,17 @@ struct Rows {
     int nq;              // index of the first special prime
     int prime0;          // offset added to Q-chain limb indices
     int slot;            // constant-memory slot of the owning context
+    int pmod;            // > 0: polynomial index modulo pmod
     const int2 *desc;
     __host__ __device__ __forceinline__ u64 *row(int r, int log_n) const {
-        if (desc) return base + ((size_t)desc[r].x << log_n);
-        return base + (size_t)(r / lpp) * poly_stride + ((size_t)(r % lpp) << log_n);
+        int poly = r / lpp, t = r - poly * lpp;
+        if (pmod) poly %= pmod;
+        const size_t off = desc ? (size_t)desc[t].x : (size_t)t;
+        return base + (size_t)poly * poly_stride + (off << log_n);
     }
     __host__ __device__ __forceinline__ int prime(int r) const {
-        if (desc) return desc[r].y;
         int t = r % lpp;
+        if (desc) return desc[t].y;
         return t < l1 ? prime0 + t : nq + (t - l1);
     }
 };
@@ -124,11 +129,17 @@ static inline Rows make_rows(u64 *base, size_t poly_stride, int lpp, int l1, int
     Rows r;
     r.base = base; r.poly_stride = poly_stride; r.lpp = lpp; r.l1 = l1; r.nq = nq; r.prime0 = prime0;
     r.slot = he::t_slot;
+    r.pmod = 0;
     r.desc = nullptr;
     return r;
 }
-static inline Rows desc_rows(u64 *base, const int2 *desc) {
-    Rows r = make_rows(base, 0, 1, 1, 0, 0);
+// n_desc descriptor rows per polynomial, polynomials poly_stride apart
+static inline Rows desc_rows(u64 *base, const int2 *desc, int n_desc, size_t poly_stride = 0) {
+    Rows r = make_rows(base, poly_stride, n_desc, n_desc, 0, 0);
     r.desc = desc;
+    return r;
+}
+static inline Rows shared_rows(Rows r, int pmod) {
+    r.pmod = pmod;
     return r;
 }

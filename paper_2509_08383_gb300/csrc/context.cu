@@ -32,30 +32,6 @@ void check_cuda(cudaError_t e, const char *what) {
 }
 
 // ---------------------------------------------------------------- arena
-void *Arena::alloc(size_t bytes) {
-    bytes = (bytes + 255) & ~(size_t)255;
-    auto it = free_blocks.find(bytes);
-    size_t off;
-    if (it != free_blocks.end()) {
-        off = it->second;
-        free_blocks.erase(it);
-    } else {
-        if (top + bytes > cap) throw Error{HE_ENOMEM, "device arena exhausted"};
-        off = top;
-        top += bytes;
-    }
-    in_use += bytes;
-    peak = std::max(peak, in_use);
-    return base + off;
-}
-void Arena::release(void *p, size_t bytes) {
-    if (!p) return;
-    bytes = (bytes + 255) & ~(size_t)255;
-    free_blocks.emplace(bytes, (size_t)((char *)p - base));
-    in_use -= bytes;
-}
-
-// ---------------------------------------------------------------- host arithmetic
 u64 mulmod_host(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
 u64 powmod_host(u64 a, u64 e, u64 q) {
     u64 r = 1 % q;
@@ -167,13 +143,15 @@ ScalarTab scalar_intd(he_ctx *cx, double K, int n_limbs) {
 // ---------------------------------------------------------------- ciphertexts
 void CtDel::operator()(he_ct *c) const { ct_release(c); }
 
-he_ct *ct_alloc(he_ctx *cx, int level, double scale) {
+he_ct *ct_alloc(he_ctx *cx, int level, double scale, int batch) {
+    if (batch < 1) throw Error{HE_EINVAL, "batch size must be positive"};
     he_ct *ct = new he_ct;
     ct->ctx = cx;
     ct->level = level;
     ct->scale = scale;
     ct->cap = level + 1;
-    ct->bytes = (size_t)2 * ct->cap * cx->N() * 8;
+    ct->batch = batch;
+    ct->bytes = (size_t)2 * batch * ct->cap * cx->N() * 8;
     try {
         ct->d = (u64 *)cx->arena.alloc(ct->bytes);
         cx->live.insert(ct);
@@ -196,6 +174,20 @@ Rows ct_rows(const he_ct *ct, int level) {
     return make_rows(ct->d, (size_t)ct->cap * ct->ctx->N(), l + 1, l + 1, ct->ctx->nq);
 }
 u64 *ct_poly(const he_ct *ct, int k) { return ct->d + (size_t)k * ct->cap * ct->ctx->N(); }
+Rows ct_polys(const he_ct *ct, int k, int level) {
+    int l = level < 0 ? ct->level : level;
+    return make_rows(ct_poly(ct, k), (size_t)2 * ct->cap * ct->ctx->N(), l + 1, l + 1, ct->ctx->nq);
+}
+size_t ct_member_stride(const he_ct *ct) { return (size_t)2 * ct->cap * ct->ctx->N(); }
+
+u64 *Scratch::get(size_t words) {
+    u64 *p = (u64 *)cx->arena.alloc(words * 8);
+    v.emplace_back(p, words * 8);
+    return p;
+}
+Scratch::~Scratch() {
+    for (auto &pb : v) cx->arena.release(pb.first, pb.second);
+}
 
 
 // ---------------------------------------------------------------- setup
@@ -592,98 +584,114 @@ void decode_dev(he_ctx *cx, const double *d_coeff, double scale, double *d_re, d
 }
 
 // ---------------------------------------------------------------- evaluator
+// Every operation acts on all `batch` members of its operands (member m's
+// polynomial k at d + (2m + k) cap N): one launch per kernel for the batch.
+static inline int nrows(const he_ct *ct, int l) { return 2 * ct->batch * (l + 1); }
+static void same_batch(const he_ct *a, const he_ct *b) {
+    if (a->batch != b->batch) throw Error{HE_EINVAL, "operands hold different numbers of ciphertexts"};
+}
+
 Ct op_copy(he_ctx *cx, const he_ct *a) {
-    Ct out(ct_alloc(cx, a->level, a->scale));
-    ew_copy(ct_rows(out.get()), ct_rows(a), 2 * (a->level + 1), cx->log_n, cx->stream);
+    Ct out(ct_alloc(cx, a->level, a->scale, a->batch));
+    ew_copy(ct_rows(out.get()), ct_rows(a), nrows(a, a->level), cx->log_n, cx->stream);
     return out;
 }
 
 Ct op_add(he_ctx *cx, const he_ct *a, const he_ct *b, bool sub) {
+    same_batch(a, b);
     int l = std::min(a->level, b->level);
-    Ct out(ct_alloc(cx, l, a->scale));
-    ew_add(ct_rows(out.get()), ct_rows(a, l), ct_rows(b, l), 2 * (l + 1), sub ? 1 : 0, cx->log_n, cx->stream);
+    Ct out(ct_alloc(cx, l, a->scale, a->batch));
+    ew_add(ct_rows(out.get()), ct_rows(a, l), ct_rows(b, l), nrows(a, l), sub ? 1 : 0, cx->log_n, cx->stream);
     return out;
 }
 
 Ct op_mul_int(he_ctx *cx, const he_ct *a, i64 k) {
-    Ct out(ct_alloc(cx, a->level, a->scale));
-    ew_mul_scalar(ct_rows(out.get()), ct_rows(a), scalar_int(cx, k, a->level + 1), 2 * (a->level + 1), cx->log_n,
+    Ct out(ct_alloc(cx, a->level, a->scale, a->batch));
+    ew_mul_scalar(ct_rows(out.get()), ct_rows(a), scalar_int(cx, k, a->level + 1), nrows(a, a->level), cx->log_n,
                   cx->stream);
     return out;
 }
 
 Ct op_mul_intd(he_ctx *cx, const he_ct *a, double K, double scale_out) {
-    Ct out(ct_alloc(cx, a->level, scale_out));
-    ew_mul_scalar(ct_rows(out.get()), ct_rows(a), scalar_intd(cx, K, a->level + 1), 2 * (a->level + 1), cx->log_n,
+    Ct out(ct_alloc(cx, a->level, scale_out, a->batch));
+    ew_mul_scalar(ct_rows(out.get()), ct_rows(a), scalar_intd(cx, K, a->level + 1), nrows(a, a->level), cx->log_n,
                   cx->stream);
     return out;
 }
 
 Ct op_add_intd(he_ctx *cx, const he_ct *a, double K) {
-    Ct out(ct_alloc(cx, a->level, a->scale));
-    int l = a->level;
-    Rows o0 = make_rows(ct_poly(out.get(), 0), 0, l + 1, l + 1, cx->nq);
-    Rows a0 = make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq);
-    Rows o1 = make_rows(ct_poly(out.get(), 1), 0, l + 1, l + 1, cx->nq);
-    Rows a1 = make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq);
-    ew_add_scalar(o0, a0, scalar_intd(cx, K, l + 1), l + 1, cx->log_n, cx->stream);
-    ew_copy(o1, a1, l + 1, cx->log_n, cx->stream);
+    Ct out(ct_alloc(cx, a->level, a->scale, a->batch));
+    const int l = a->level, nr = a->batch * (l + 1);
+    ew_add_scalar(ct_polys(out.get(), 0), ct_polys(a, 0), scalar_intd(cx, K, l + 1), nr, cx->log_n, cx->stream);
+    ew_copy(ct_polys(out.get(), 1), ct_polys(a, 1), nr, cx->log_n, cx->stream);
     return out;
 }
 
-// integer plaintext (device doubles, N) -> NTT rows in scratch sc_b
-static Rows plain_rows(he_ctx *cx, const double *d_pt, int l) {
-    Rows pt = make_rows(cx->sc_b, 0, l + 1, l + 1, cx->nq);
-    load_intd(pt, l + 1, d_pt, cx->log_n, cx->stream);
-    ntt_forward(pt, l + 1, cx->tw, cx->log_n, cx->stream);
-    return pt;
-}
-
-Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out) {
-    int l = a->level;
-    Rows pt = plain_rows(cx, d_pt, l);
-    Ct out(ct_alloc(cx, l, scale_out));
-    for (int k = 0; k < 2; k++) {
-        Rows o = make_rows(ct_poly(out.get(), k), 0, l + 1, l + 1, cx->nq);
-        Rows x = make_rows(ct_poly(a, k), 0, l + 1, l + 1, cx->nq);
-        ew_mul(o, x, pt, l + 1, cx->log_n, cx->stream);
+// n_pt integer plaintexts (device doubles, n_pt x N) -> NTT rows; member m of
+// a batch uses plaintext m % n_pt
+static Rows plain_rows(he_ctx *cx, Scratch &sc, const double *d_pt, int n_pt, int l) {
+    const size_t N = cx->N();
+    u64 *buf = n_pt == 1 ? cx->sc_b : sc.get((size_t)n_pt * (l + 1) * N);
+    for (int i = 0; i < n_pt; i++) {
+        Rows pt = make_rows(buf + (size_t)i * (l + 1) * N, 0, l + 1, l + 1, cx->nq);
+        load_intd(pt, l + 1, d_pt + (size_t)i * N, cx->log_n, cx->stream);
     }
-    return out;
+    Rows all = make_rows(buf, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    ntt_forward(all, n_pt * (l + 1), cx->tw, cx->log_n, cx->stream);
+    return shared_rows(all, n_pt);
 }
 
-Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt) {
+Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt) {
     int l = a->level;
-    Rows pt = plain_rows(cx, d_pt, l);
-    Ct out = op_copy(cx, a);
-    Rows o = make_rows(ct_poly(out.get(), 0), 0, l + 1, l + 1, cx->nq);
-    ew_add(o, o, pt, l + 1, 0, cx->log_n, cx->stream);
+    Scratch sc{cx, {}};
+    Rows pt = plain_rows(cx, sc, d_pt, n_pt, l);
+    Ct out(ct_alloc(cx, l, scale_out, a->batch));
+    for (int k = 0; k < 2; k++) ew_mul(ct_polys(out.get(), k), ct_polys(a, k), pt, a->batch * (l + 1), cx->log_n, cx->stream);
     return out;
 }
 
-// ModUp of d (NTT form, limbs 0..l) into ext ([beta][n_ext][N] NTT form,
-// rows inside each digit left unused): INTT, basis conversion per digit, NTT.
-void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext) {
+Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt, int n_pt) {
+    int l = a->level;
+    Scratch sc{cx, {}};
+    Rows pt = plain_rows(cx, sc, d_pt, n_pt, l);
+    Ct out = op_copy(cx, a);
+    Rows o = ct_polys(out.get(), 0);
+    ew_add(o, o, pt, a->batch * (l + 1), 0, cx->log_n, cx->stream);
+    return out;
+}
+
+// ModUp of B members (member m's limbs 0..l at d_ntt + m*d_stride, NTT form)
+// into ext (member m at ext + m*beta*n_ext*N, [beta][n_ext][N] NTT form, rows
+// inside each digit left unused): INTT, basis conversion per digit, NTT.
+void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext, int B, size_t d_stride) {
     const int log_n = cx->log_n;
     const size_t N = cx->N();
     const LevelTabs &T = cx->lv[l];
+    const size_t ext_w = (size_t)T.beta * T.n_ext * N;
     cudaStream_t s = cx->stream;
-    Rows coef = make_rows(cx->ks_coef, 0, l + 1, l + 1, cx->nq);
-    ntt_inverse_from(coef, make_rows((u64 *)d_ntt, 0, l + 1, l + 1, cx->nq), l + 1, cx->tw, log_n, s);
+    Scratch sc{cx, {}};
+    u64 *coef = B == 1 ? cx->ks_coef : sc.get((size_t)B * (l + 1) * N);
+    if (B == 1) d_stride = 0;
+    Rows crow = make_rows(coef, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    ntt_inverse_from(crow, make_rows((u64 *)d_ntt, d_stride, l + 1, l + 1, cx->nq), B * (l + 1), cx->tw, log_n, s);
     for (int j = 0; j < T.beta; j++) {
         int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
-        Rows in = make_rows(cx->ks_coef + (size_t)lo * N, 0, cnt, cnt, cx->nq, lo);
-        Rows o = desc_rows(ext, T.desc + T.digit_off[j]);
-        bconv(o, in, T.modup[j], 1, log_n, s);
+        Rows in = make_rows(coef + (size_t)lo * N, (size_t)(l + 1) * N, cnt, cnt, cx->nq, lo);
+        Rows o = desc_rows(ext, T.desc + T.digit_off[j], T.digit_nout[j], ext_w);
+        bconv(o, in, T.modup[j], B, log_n, s);
     }
-    ntt_forward(desc_rows(ext, T.desc), T.n_desc, cx->tw, log_n, s);
+    ntt_forward(desc_rows(ext, T.desc, T.n_desc, ext_w), B * T.n_desc, cx->tw, log_n, s);
 }
 
 // Inner product with the key, reading the digits through X -> X^galois when
 // galois != 0: acc = (sum_j ext_j * b_j, sum_j ext_j * a_j) over QP, two
-// polynomials of n_ext rows each (Q limbs 0..l, then the special primes).
-void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc) {
+// polynomials of n_ext rows each (Q limbs 0..l, then the special primes), for
+// B members (member m's acc at + m*2*n_ext*N).
+void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc, int B,
+              size_t d_stride) {
     const LevelTabs &T = cx->lv[l];
-    cx->ks_by_level[l]++;
+    const size_t N = cx->N();
+    cx->ks_by_level[l] += (uint64_t)B;
     KeyIP kp;
     kp.d_ntt = d_ntt;
     kp.ext = ext;
@@ -698,52 +706,68 @@ void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev 
     kp.key_limbs = cx->nq + cx->np;
     kp.slot = cx->slot;
     kp.galois = galois;
+    kp.batch = B;
+    kp.d_stride = B == 1 ? 0 : d_stride;
+    kp.ext_stride = (size_t)T.beta * T.n_ext * N;
+    kp.acc_stride = (size_t)2 * T.n_ext * N;
     keyswitch_inner(kp, cx->log_n, cx->stream);
 }
 
-// ModDown of a two-polynomial QP accumulator (destroys its special-prime
-// rows): out = (acc_Q - conv(acc_P)) * P^-1 (+ add where add_mask selects).
-void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask) {
+// ModDown of B two-polynomial QP accumulators (destroys their special-prime
+// rows): out = (acc_Q - conv(acc_P)) * P^-1 (+ add where add_mask bit k
+// selects polynomial k); out and add cover the 2B polynomials.
+void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask, int B) {
     const int K = cx->np, log_n = cx->log_n;
     const size_t N = cx->N();
     const LevelTabs &T = cx->lv[l];
     cudaStream_t s = cx->stream;
+    Scratch sc{cx, {}};
     Rows accP = make_rows(acc + (size_t)(l + 1) * N, (size_t)T.n_ext * N, K, 0, cx->nq);
-    ntt_inverse(accP, 2 * K, cx->tw, log_n, s);
+    ntt_inverse(accP, 2 * B * K, cx->tw, log_n, s);
     BConvTab md = cx->moddown;
     md.n_out = l + 1;
-    Rows conv = make_rows(cx->ks_conv, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
-    bconv(conv, accP, md, 2, log_n, s);
-    ntt_forward(conv, 2 * (l + 1), cx->tw, log_n, s);
+    u64 *cv = B == 1 ? cx->ks_conv : sc.get((size_t)2 * B * (l + 1) * N);
+    Rows conv = make_rows(cv, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    bconv(conv, accP, md, 2 * B, log_n, s);
+    ntt_forward(conv, 2 * B * (l + 1), cx->tw, log_n, s);
     Rows accQ = make_rows(acc, (size_t)T.n_ext * N, l + 1, l + 1, cx->nq);
-    moddown_finish(out, accQ, conv, cx->p_inv, 2 * (l + 1), add, add_mask, log_n, s);
+    moddown_finish(out, accQ, conv, cx->p_inv, 2 * B * (l + 1), add, add_mask, log_n, s);
 }
+
+size_t ks_ext_words(he_ctx *cx, int l) { return (size_t)cx->lv[l].beta * cx->lv[l].n_ext * cx->N(); }
+size_t ks_acc_words(he_ctx *cx, int l) { return (size_t)2 * cx->lv[l].n_ext * cx->N(); }
 
 // Inner product with the key and ModDown: out = ModDown(acc) (+ add).
 void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
-                   const Rows &out, const Rows &add, int add_mask) {
-    ks_inner(cx, d_ntt, ext, l, key, galois, cx->ks_acc);
-    moddown(cx, cx->ks_acc, l, out, add, add_mask);
+                   const Rows &out, const Rows &add, int add_mask, int B, size_t d_stride) {
+    Scratch sc{cx, {}};
+    u64 *acc = B == 1 ? cx->ks_acc : sc.get((size_t)B * ks_acc_words(cx, l));
+    ks_inner(cx, d_ntt, ext, l, key, galois, acc, B, d_stride);
+    moddown(cx, acc, l, out, add, add_mask, B);
 }
 
-void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask) {
-    modup(cx, d_ntt, l, cx->ks_ext);
-    keyswitch_ext(cx, d_ntt, cx->ks_ext, l, key, 0, out, add, add_mask);
+void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask,
+               int B, size_t d_stride) {
+    Scratch sc{cx, {}};
+    u64 *ext = B == 1 ? cx->ks_ext : sc.get((size_t)B * ks_ext_words(cx, l));
+    modup(cx, d_ntt, l, ext, B, d_stride);
+    keyswitch_ext(cx, d_ntt, ext, l, key, 0, out, add, add_mask, B, d_stride);
 }
 
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
+    same_batch(a, b);
     const KeyDev *rk = find_key(cx, 0);
     if (!rk) throw Error{HE_ENOKEY, "relinearisation key not generated"};
-    int l = std::min(a->level, b->level);
-    Ct out(ct_alloc(cx, l, a->scale * b->scale));
-    Rows d0 = make_rows(ct_poly(out.get(), 0), 0, l + 1, l + 1, cx->nq);
-    Rows d1 = make_rows(ct_poly(out.get(), 1), 0, l + 1, l + 1, cx->nq);
-    Rows d2 = make_rows(cx->sc_a, 0, l + 1, l + 1, cx->nq);
-    Rows a0 = make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq), a1 = make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq);
-    Rows b0 = make_rows(ct_poly(b, 0), 0, l + 1, l + 1, cx->nq), b1 = make_rows(ct_poly(b, 1), 0, l + 1, l + 1, cx->nq);
-    ew_tensor(d0, d1, d2, a0, a1, b0, b1, l + 1, cx->log_n, cx->stream);
+    const int l = std::min(a->level, b->level), B = a->batch;
+    const size_t N = cx->N();
+    Ct out(ct_alloc(cx, l, a->scale * b->scale, B));
+    Scratch sc{cx, {}};
+    u64 *d2 = B == 1 ? cx->sc_a : sc.get((size_t)B * (l + 1) * N);
+    Rows r2 = make_rows(d2, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    ew_tensor(ct_polys(out.get(), 0), ct_polys(out.get(), 1), r2, ct_polys(a, 0, l), ct_polys(a, 1, l),
+              ct_polys(b, 0, l), ct_polys(b, 1, l), B * (l + 1), cx->log_n, cx->stream);
     Rows o = ct_rows(out.get());
-    keyswitch(cx, cx->sc_a, l, *rk, o, o, 3);
+    keyswitch(cx, d2, l, *rk, o, o, 3, B, (size_t)(l + 1) * N);
     return out;
 }
 
@@ -751,59 +775,112 @@ Ct op_rescale(he_ctx *cx, const he_ct *a) {
     int l = a->level;
     if (l < 1) throw Error{HE_ELEVEL, "cannot rescale a level-0 ciphertext"};
     const size_t N = cx->N();
+    const int np2 = 2 * a->batch;
     cudaStream_t s = cx->stream;
     u64 ql = cx->primes[l];
-    Ct out(ct_alloc(cx, l - 1, a->scale / (double)ql));
-    // last limbs of c0, c1 -> coefficient form (scratch rows 0, 1)
-    Rows last = make_rows(cx->sc_a, N, 1, 1, cx->nq, l);
+    Ct out(ct_alloc(cx, l - 1, a->scale / (double)ql, a->batch));
+    Scratch sc{cx, {}};
+    u64 *lastb = a->batch == 1 ? cx->sc_a : sc.get((size_t)np2 * N);
+    u64 *liftb = a->batch == 1 ? cx->sc_b : sc.get((size_t)np2 * l * N);
+    // last limbs of every polynomial -> coefficient form
+    Rows last = make_rows(lastb, N, 1, 1, cx->nq, l);
     Rows src = make_rows(ct_poly(a, 0) + (size_t)l * N, (size_t)a->cap * N, 1, 1, cx->nq, l);
-    ntt_inverse_from(last, src, 2, cx->tw, cx->log_n, s);
-    Rows lift = make_rows(cx->sc_b, (size_t)l * N, l, l, cx->nq);
-    rescale_lift(lift, cx->sc_a, cx->sc_a + N, ql, l, cx->log_n, s);
-    ntt_forward(lift, 2 * l, cx->tw, cx->log_n, s);
-    rescale_finish(ct_rows(out.get()), ct_rows(a, l - 1), lift, cx->lv[l].ql_inv, 2 * l, cx->log_n, s);
+    ntt_inverse_from(last, src, np2, cx->tw, cx->log_n, s);
+    Rows lift = make_rows(liftb, (size_t)l * N, l, l, cx->nq);
+    rescale_lift(lift, lastb, np2, ql, l, cx->log_n, s);
+    ntt_forward(lift, np2 * l, cx->tw, cx->log_n, s);
+    rescale_finish(ct_rows(out.get()), ct_rows(a, l - 1), lift, cx->lv[l].ql_inv, np2 * l, cx->log_n, s);
     return out;
 }
 
 Ct op_drop(he_ctx *cx, const he_ct *a, int level) {
     if (level > a->level || level < 0) throw Error{HE_EINVAL, "drop to an invalid level"};
-    Ct out(ct_alloc(cx, level, a->scale));
-    ew_copy(ct_rows(out.get()), ct_rows(a, level), 2 * (level + 1), cx->log_n, cx->stream);
+    Ct out(ct_alloc(cx, level, a->scale, a->batch));
+    ew_copy(ct_rows(out.get()), ct_rows(a, level), nrows(a, level), cx->log_n, cx->stream);
     return out;
 }
 
 Ct op_automorph(he_ctx *cx, const he_ct *a, u64 g) {
     const KeyDev *k = find_key(cx, g);
     if (!k) throw Error{HE_ENOKEY, "Galois key not generated for element " + std::to_string(g)};
-    int l = a->level;
+    const int l = a->level, B = a->batch;
     const size_t N = cx->N();
-    Ct out(ct_alloc(cx, l, a->scale));
-    // sigma(c0) -> scratch a, sigma(c1) -> scratch b
-    Rows sa = make_rows(cx->sc_a, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
-    Rows sb = make_rows(cx->sc_b, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
-    ew_automorph_ntt(sa, make_rows(ct_poly(a, 0), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
-    ew_automorph_ntt(sb, make_rows(ct_poly(a, 1), 0, l + 1, l + 1, cx->nq), l + 1, g, cx->log_n, cx->stream);
-    keyswitch(cx, cx->sc_b, l, *k, ct_rows(out.get()), sa, 1);
+    Ct out(ct_alloc(cx, l, a->scale, B));
+    // sigma(c0) -> out polynomial 0 (added in place by the ModDown), sigma(c1) -> scratch
+    Scratch sc{cx, {}};
+    u64 *sb = B == 1 ? cx->sc_b : sc.get((size_t)B * (l + 1) * N);
+    ew_automorph_ntt(ct_polys(out.get(), 0), ct_polys(a, 0), B * (l + 1), g, cx->log_n, cx->stream);
+    ew_automorph_ntt(make_rows(sb, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq), ct_polys(a, 1), B * (l + 1), g,
+                     cx->log_n, cx->stream);
+    Rows o = ct_rows(out.get());
+    keyswitch(cx, sb, l, *k, o, o, 1, B, (size_t)(l + 1) * N);
     return out;
 }
 
 Ct op_mul_monomial(he_ctx *cx, const he_ct *a, u64 e) {
-    Ct out(ct_alloc(cx, a->level, a->scale));
-    ew_monomial(ct_rows(out.get()), ct_rows(a), 2 * (a->level + 1), e % (2 * cx->N()), cx->tw, cx->log_n, cx->stream);
+    Ct out(ct_alloc(cx, a->level, a->scale, a->batch));
+    ew_monomial(ct_rows(out.get()), ct_rows(a), nrows(a, a->level), e % (2 * cx->N()), cx->tw, cx->log_n, cx->stream);
     return out;
 }
 
 Ct op_mod_raise(he_ctx *cx, const he_ct *a, int level) {
     if (a->level != 0) throw Error{HE_EINVAL, "mod raise expects a level-0 ciphertext"};
     const size_t N = cx->N();
+    const int np2 = 2 * a->batch;
     cudaStream_t s = cx->stream;
-    Rows last = make_rows(cx->sc_a, N, 1, 1, cx->nq, 0);
-    ew_copy(last, make_rows(ct_poly(a, 0), (size_t)a->cap * N, 1, 1, cx->nq, 0), 2, cx->log_n, s);
-    ntt_inverse(last, 2, cx->tw, cx->log_n, s);
-    Ct out(ct_alloc(cx, level, a->scale));
+    Scratch sc{cx, {}};
+    u64 *lastb = a->batch == 1 ? cx->sc_a : sc.get((size_t)np2 * N);
+    Rows last = make_rows(lastb, N, 1, 1, cx->nq, 0);
+    ew_copy(last, make_rows(ct_poly(a, 0), (size_t)a->cap * N, 1, 1, cx->nq, 0), np2, cx->log_n, s);
+    ntt_inverse(last, np2, cx->tw, cx->log_n, s);
+    Ct out(ct_alloc(cx, level, a->scale, a->batch));
     Rows o = ct_rows(out.get());
-    modraise_lift(o, cx->sc_a, cx->sc_a + N, cx->primes[0], 2 * (level + 1), cx->log_n, s);
-    ntt_forward(o, 2 * (level + 1), cx->tw, cx->log_n, s);
+    modraise_lift(o, lastb, cx->primes[0], np2 * (level + 1), cx->log_n, s);
+    ntt_forward(o, np2 * (level + 1), cx->tw, cx->log_n, s);
+    return out;
+}
+
+// ---- batches
+Ct op_batch_pack(he_ctx *cx, const he_ct *const *cts, int n) {
+    if (n < 1) throw Error{HE_EINVAL, "empty batch"};
+    int l = cts[0]->level;
+    for (int i = 0; i < n; i++) {
+        if (cts[i]->ctx != cx) throw Error{HE_EINVAL, "ciphertext from another context"};
+        if (std::fabs(cts[i]->scale - cts[0]->scale) > 1e-9 * cts[0]->scale)
+            throw Error{HE_EINVAL, "batch members must share one scale"};
+        l = std::min(l, cts[i]->level);
+    }
+    int total = 0;
+    for (int i = 0; i < n; i++) total += cts[i]->batch;
+    Ct out(ct_alloc(cx, l, cts[0]->scale, total));
+    const size_t ms = ct_member_stride(out.get());
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        Rows dst = make_rows(out->d + (size_t)m * ms, (size_t)out->cap * cx->N(), l + 1, l + 1, cx->nq);
+        ew_copy(dst, ct_rows(cts[i], l), nrows(cts[i], l), cx->log_n, cx->stream);
+        m += cts[i]->batch;
+    }
+    return out;
+}
+
+Ct op_batch_member(he_ctx *cx, const he_ct *a, int i, int count) {
+    if (i < 0 || count < 1 || i + count > a->batch) throw Error{HE_EINVAL, "batch member out of range"};
+    Ct out(ct_alloc(cx, a->level, a->scale, count));
+    Rows src = make_rows(a->d + (size_t)i * ct_member_stride(a), (size_t)a->cap * cx->N(), a->level + 1,
+                         a->level + 1, cx->nq);
+    ew_copy(ct_rows(out.get()), src, nrows(out.get(), a->level), cx->log_n, cx->stream);
+    return out;
+}
+
+// groups of g consecutive members: summed (sum) into one member each, or each
+// member repeated g times (broadcast)
+Ct op_group(he_ctx *cx, const he_ct *a, int g, bool sum) {
+    if (g < 1 || (sum && a->batch % g)) throw Error{HE_EINVAL, "batch is not a whole number of groups"};
+    const int l = a->level, nb = sum ? a->batch / g : a->batch * g;
+    Ct out(ct_alloc(cx, l, a->scale, nb));
+    const size_t N = cx->N();
+    ew_group(out->d, a->d, nb, g, sum ? 1 : 0, l + 1, ct_member_stride(out.get()), ct_member_stride(a),
+             (size_t)a->cap * N, (size_t)out->cap * N, cx->slot, cx->log_n, cx->stream);
     return out;
 }
 

@@ -7,20 +7,11 @@
 #include <vector>
 
 #include "../../include/he_cutmax.h"
+#include "arena.h"
 #include "kernels.h"
 
 namespace he {
 struct Boot;
-
-// Sub-allocator over one device buffer; exact-size reuse of freed blocks.
-struct Arena {
-    char *base = nullptr;
-    size_t cap = 0, top = 0, in_use = 0, peak = 0;
-    bool owned = false;
-    std::multimap<size_t, size_t> free_blocks;  // size -> offset
-    void *alloc(size_t bytes);
-    void release(void *p, size_t bytes);
-};
 
 struct KeyDev {
     u64 g;       // Galois element, 0 = relinearisation
@@ -42,12 +33,15 @@ struct LevelTabs {
 
 }  // namespace he
 
+// `batch` ciphertexts of one level and scale stored back to back: member m's
+// polynomial k (c0, c1) holds its limbs at d + (2m + k) cap N.
 struct he_ct {
     he_ctx *ctx;    // null once the owning context has been destroyed
     int level;
     double scale;
-    u64 *d;     // c0 limbs then c1 limbs
+    u64 *d;
     int cap;        // limbs allocated per polynomial
+    int batch = 1;  // ciphertexts held
     size_t bytes;
 };
 
@@ -98,14 +92,22 @@ namespace he {
 struct CtDel { void operator()(he_ct *c) const; };
 using Ct = std::unique_ptr<he_ct, CtDel>;
 
-struct Error { int code; std::string msg; };
+// arena buffers released on every exit path
+struct Scratch {
+    he_ctx *cx;
+    std::vector<std::pair<u64 *, size_t>> v;
+    u64 *get(size_t words);
+    ~Scratch();
+};
 
 // ---- context / memory
 void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes);  // throws Error
-he_ct *ct_alloc(he_ctx *cx, int level, double scale);
+he_ct *ct_alloc(he_ctx *cx, int level, double scale, int batch = 1);
 void ct_release(he_ct *ct);
-Rows ct_rows(const he_ct *ct, int level = -1);  // both polynomials, limbs 0..level
-u64 *ct_poly(const he_ct *ct, int k);
+Rows ct_rows(const he_ct *ct, int level = -1);  // every polynomial of every member, limbs 0..level
+u64 *ct_poly(const he_ct *ct, int k);           // member 0's polynomial k
+Rows ct_polys(const he_ct *ct, int k, int level = -1);  // polynomial k of every member
+size_t ct_member_stride(const he_ct *ct);
 ScalarTab scalar_int(he_ctx *cx, i64 k, int n_limbs);
 ScalarTab scalar_intd(he_ctx *cx, double K, int n_limbs);
 u64 intd_mod_host(double x, u64 q);
@@ -130,8 +132,9 @@ Ct op_add(he_ctx *cx, const he_ct *a, const he_ct *b, bool sub);
 Ct op_mul_int(he_ctx *cx, const he_ct *a, i64 k);
 Ct op_mul_intd(he_ctx *cx, const he_ct *a, double K, double scale_out);
 Ct op_add_intd(he_ctx *cx, const he_ct *a, double K);
-Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out);
-Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt);
+// n_pt plaintexts (n_pt x N integer-valued doubles); member m uses plaintext m % n_pt
+Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt = 1);
+Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt, int n_pt = 1);
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b);
 Ct op_rescale(he_ctx *cx, const he_ct *a);
 Ct op_drop(he_ctx *cx, const he_ct *a, int level);
@@ -139,15 +142,27 @@ Ct op_automorph(he_ctx *cx, const he_ct *a, u64 g);
 Ct op_mod_raise(he_ctx *cx, const he_ct *a, int level);
 Ct op_mul_monomial(he_ctx *cx, const he_ct *a, u64 e);
 Ct op_copy(he_ctx *cx, const he_ct *a);
-// raw hybrid key switch: d (NTT form, limbs 0..l) -> out (2 polys, NTT form),
-// add_mask bit k: out poly k += add poly k
-void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask);
-// the two halves of a key switch, for rotations that share one ModUp
-void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext);
-void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc);
-void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask);
+// batches: members of several ciphertexts packed back to back; members
+// [i, i+count) of a batch; groups of g consecutive members summed, or every
+// member repeated g times
+Ct op_batch_pack(he_ctx *cx, const he_ct *const *cts, int n);
+Ct op_batch_member(he_ctx *cx, const he_ct *a, int i, int count = 1);
+Ct op_group(he_ctx *cx, const he_ct *a, int g, bool sum);
+// raw hybrid key switch of B polynomials (member m's limbs 0..l at d_ntt +
+// m*d_stride, NTT form) -> out (2B polys, NTT form); add_mask bit k: out
+// polynomial k of every member += the matching add polynomial
+void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Rows &out, const Rows &add, int add_mask,
+               int B = 1, size_t d_stride = 0);
+// the pieces of a key switch, for rotations that share one ModUp; ext holds
+// ks_ext_words(l) and acc ks_acc_words(l) words per member
+size_t ks_ext_words(he_ctx *cx, int l);
+size_t ks_acc_words(he_ctx *cx, int l);
+void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext, int B = 1, size_t d_stride = 0);
+void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc,
+              int B = 1, size_t d_stride = 0);
+void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask, int B = 1);
 void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
-                   const Rows &out, const Rows &add, int add_mask);
+                   const Rows &out, const Rows &add, int add_mask, int B = 1, size_t d_stride = 0);
 
 // ---- circuits (circuit.cu)
 struct Plan {
@@ -157,6 +172,7 @@ struct Plan {
     int d;
     double kappa_f;
     bool bootstrap;
+    int cps = 1;  // ciphertexts per stream
     int pad(int slots) const;
 };
 Plan plan_from(const he_cutmax_plan *p);

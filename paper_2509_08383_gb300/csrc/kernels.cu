@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(EW_T) k_diag_mac(DiagMac dm, int log_n) {
     const int pr = r < dm.l1 ? r : dm.nq + (r - dm.l1);
     const ModQ m = pc.m[pr];
     const u64 qn = pc.mont_qinv[pr];
-    const size_t row = (size_t)r << log_n;
+    const size_t row = (size_t)r << log_n, mo = (size_t)blockIdx.z * dm.c_stride, oo = (size_t)blockIdx.z * dm.out_stride;
     EW_PAIRS_FOR(k, log_n) {
         const size_t off = row + k;
         u64 s00 = 0, s01 = 0, s10 = 0, s11 = 0;
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(EW_T) k_diag_mac(DiagMac dm, int log_n) {
             const int b1 = min(dm.n, b0 + 16);
             for (int b = b0; b < b1; b++) {
                 const ulonglong2 w = ld2(dm.pt[b] + off);
-                const ulonglong2 x0 = ld2(dm.c0[b] + off), x1 = ld2(dm.c1[b] + off);
+                const ulonglong2 x0 = ld2(dm.c0[b] + mo + off), x1 = ld2(dm.c1[b] + mo + off);
                 mac128(l00, h00, x0.x, w.x);
                 mac128(l01, h01, x0.y, w.y);
                 mac128(l10, h10, x1.x, w.x);
@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(EW_T) k_diag_mac(DiagMac dm, int log_n) {
             s10 = add_mod(s10, mont_reduce_wide(l10, h10, m, qn), m.q);
             s11 = add_mod(s11, mont_reduce_wide(l11, h11, m, qn), m.q);
         }
-        st2(dm.out0 + off, s00, s01);
-        st2(dm.out1 + off, s10, s11);
+        st2(dm.out0 + oo + off, s00, s01);
+        st2(dm.out1 + oo + off, s10, s11);
     }
 }
 void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s) {
@@ -532,7 +532,50 @@ void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s) {
         need16(dm.c1[b]);
         need16(dm.pt[b]);
     }
-    k_diag_mac<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(dm, log_n);
+    if (dm.batch < 1 || (dm.batch > 1 && ((dm.c_stride | dm.out_stride) & 1)))
+        throw Error{HE_EINVAL, "diagonal multiply-accumulate: bad batch layout"};
+    dim3 grid = ew_grid(n_rows, log_n);
+    grid.z = (unsigned)dm.batch;
+    k_diag_mac<<<grid, EW_T, 0, s>>>(dm, log_n);
+}
+
+// Members of a batch of ciphertexts (both polynomials, limbs 0..l, member m
+// at base + m*stride): out member s = sum of in members s*g .. s*g+g-1
+// (group sum), or out member b = in member b / g (broadcast).
+__global__ void __launch_bounds__(EW_T) k_group(u64 *out, const u64 *in, int g, int sum, int l1, size_t out_stride,
+                                                size_t in_stride, size_t in_poly, size_t out_poly, int slot,
+                                                int log_n) {
+    const int r = blockIdx.y, poly = r / l1, t = r % l1;
+    const u64 q = c_pcs[slot].m[t].q;
+    const size_t m = blockIdx.z;
+    u64 *o = out + m * out_stride + poly * out_poly + ((size_t)t << log_n);
+    if (sum) {
+        const u64 *x = in + m * g * in_stride + poly * in_poly + ((size_t)t << log_n);
+        EW_PAIRS_FOR(k, log_n) {
+            ulonglong2 a = ld2(x + k);
+            for (int c = 1; c < g; c++) {
+                const ulonglong2 b = ld2(x + c * in_stride + k);
+                a.x = add_mod(a.x, b.x, q);
+                a.y = add_mod(a.y, b.y, q);
+            }
+            st2(o + k, a.x, a.y);
+        }
+    } else {
+        const u64 *x = in + (m / g) * in_stride + poly * in_poly + ((size_t)t << log_n);
+        EW_PAIRS_FOR(k, log_n) {
+            const ulonglong2 a = ld2(x + k);
+            st2(o + k, a.x, a.y);
+        }
+    }
+}
+void ew_group(u64 *out, const u64 *in, int n_out_members, int g, int sum, int l1, size_t out_stride, size_t in_stride,
+              size_t in_poly, size_t out_poly, int slot, int log_n, cudaStream_t s) {
+    need16(out);
+    need16(in);
+    if (((out_stride | in_stride | in_poly | out_poly) & 1) || g < 1) throw Error{HE_EINVAL, "group op: bad layout"};
+    dim3 grid = ew_grid(2 * l1, log_n);
+    grid.z = (unsigned)n_out_members;
+    k_group<<<grid, EW_T, 0, s>>>(out, in, g, sum, l1, out_stride, in_stride, in_poly, out_poly, slot, log_n);
 }
 
 // source position of NTT-form position i under X -> X^g (g odd < 2N)
@@ -548,8 +591,10 @@ __device__ __forceinline__ u32 automorph_src(u32 i, u64 g, int log_n) {
 // r < l1 of an n_rows-row block; the special-prime rows are 0 (P = 0 mod p_i)
 // and are left unchanged when adding.
 __global__ void __launch_bounds__(EW_T) k_qp_lift(u64 *out, const u64 *src, int l1, u64 g, int add, ScalarTab pm,
-                                                  int slot, int log_n) {
+                                                  int slot, size_t out_stride, size_t src_stride, int log_n) {
     const int r = blockIdx.y;
+    out += blockIdx.z * out_stride;
+    src += blockIdx.z * src_stride;
     u64 *o = out + ((size_t)r << log_n);
     if (r >= l1) {
         EW_PAIRS_FOR(k, log_n) st2(o + k, 0, 0);
@@ -578,10 +623,13 @@ __global__ void __launch_bounds__(EW_T) k_qp_lift(u64 *out, const u64 *src, int 
     }
 }
 void ew_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, const ScalarTab &pm, int slot,
-                int log_n, cudaStream_t s) {
+                int log_n, cudaStream_t s, int batch, size_t out_stride, size_t src_stride) {
     need16(out);
     need16(src);
-    k_qp_lift<<<ew_grid(add ? l1 : n_rows, log_n), EW_T, 0, s>>>(out, src, l1, g, add, pm, slot, log_n);
+    if (batch > 1 && ((out_stride | src_stride) & 1)) throw Error{HE_EINVAL, "QP lift: bad batch layout"};
+    dim3 grid = ew_grid(add ? l1 : n_rows, log_n);
+    grid.z = (unsigned)batch;
+    k_qp_lift<<<grid, EW_T, 0, s>>>(out, src, l1, g, add, pm, slot, out_stride, src_stride, log_n);
 }
 
 __global__ void __launch_bounds__(EW_T) k_tensor(Rows d0, Rows d1, Rows d2, Rows a0, Rows a1, Rows b0, Rows b1,
@@ -723,6 +771,8 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     __shared__ uint2 s_w[BCONV_MAX_IN * BCONV_CHUNK];
     __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
     __shared__ const u64 *s_in[BCONV_MAX_IN];
+    __shared__ u64 *s_out[BCONV_CHUNK];
+    __shared__ int s_p[BCONV_CHUNK];
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
@@ -740,6 +790,12 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         s_qis[a] = ok ? tab.qhinv_sh[a] : 0;
         s_q[a] = ok ? pc.m[in.prime(poly * tab.n_in + a)].q : 1;
         s_in[a] = ok ? in.row(poly * tab.n_in + a, log_n) : nullptr;
+    }
+    if (threadIdx.x < BCONV_CHUNK) {
+        const int c = threadIdx.x, r = poly * tab.n_out + t0 + c;
+        const bool ok = c < nt && poly < n_polys;
+        s_out[c] = ok ? out.row(r, log_n) : nullptr;
+        s_p[c] = ok ? out.prime(r) : 0;
     }
     __syncthreads();
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -760,10 +816,9 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
 #pragma unroll
     for (int c = 0; c < BCONV_CHUNK; c++) {
         if (c < nt) {
-            const int r = poly * tab.n_out + t0 + c;
-            const int p = out.prime(r);
+            const int p = s_p[c];
             const u64 lo = ((u64)acc[c][1] << 32) | acc[c][0], hi = ((u64)acc[c][3] << 32) | acc[c][2];
-            out.row(r, log_n)[k] = mont_reduce_wide(lo, hi, pc.m[p], pc.mont_qinv[p]);
+            s_out[c][k] = mont_reduce_wide(lo, hi, pc.m[p], pc.mont_qinv[p]);
         }
     }
 }
@@ -778,9 +833,12 @@ void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, in
     prof_end(PROF_BCONV, s, 8.0 * (tab.n_in + tab.n_out) * (double)n_polys * (double)n);
 }
 
+// Batch members are processed KS_MB at a time per thread, so that every key
+// word loaded serves KS_MB members from registers (KS_MB = 1 for one member).
+template <int KS_MB>
 __global__ void __launch_bounds__(EW_T) k_keyswitch_inner(KeyIP kp, int log_n) {
     const PrimeConsts &pc = c_pcs[kp.slot];
-    const int t = blockIdx.y;
+    const int t = blockIdx.y, b0 = blockIdx.z * KS_MB, nb = min(KS_MB, kp.batch - b0);
     const int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
     const u64 q = pc.m[p].q, qn = pc.mont_qinv[p];
     const int jt = t < kp.l1 ? t / kp.alpha : -1;
@@ -793,28 +851,43 @@ __global__ void __launch_bounds__(EW_T) k_keyswitch_inner(KeyIP kp, int log_n) {
         }
         // keys are in Montgomery form (times 2^64): the beta products are summed
         // in 128 bits (< beta q^2 < q 2^64) and reduced once
-        u64 l00 = 0, h00 = 0, l01 = 0, h01 = 0, l10 = 0, h10 = 0, l11 = 0, h11 = 0;
+        u64 acc[KS_MB][8];
+#pragma unroll
+        for (int m = 0; m < KS_MB; m++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) acc[m][i] = 0;
         for (int j = 0; j < kp.beta; j++) {
-            const u64 *xs = (j == jt) ? kp.d_ntt + row : kp.ext + (((size_t)j * kp.n_rows + t) << log_n);
-            u64 x0, x1;
-            if (kp.galois) {
-                x0 = xs[s0];
-                x1 = xs[s1];
-            } else {
-                const ulonglong2 xv = ld2(xs + k);
-                x0 = xv.x;
-                x1 = xv.y;
+            const ulonglong2 kb = ld2(kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n) + k);
+            const ulonglong2 ka = ld2(kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n) + k);
+#pragma unroll
+            for (int m = 0; m < KS_MB; m++) {
+                if (m >= nb) break;
+                const size_t mb = (size_t)(b0 + m);
+                const u64 *xs = (j == jt) ? kp.d_ntt + mb * kp.d_stride + row
+                                          : kp.ext + mb * kp.ext_stride + (((size_t)j * kp.n_rows + t) << log_n);
+                u64 x0, x1;
+                if (kp.galois) {
+                    x0 = xs[s0];
+                    x1 = xs[s1];
+                } else {
+                    const ulonglong2 xv = ld2(xs + k);
+                    x0 = xv.x;
+                    x1 = xv.y;
+                }
+                mac128(acc[m][0], acc[m][1], x0, kb.x);
+                mac128(acc[m][2], acc[m][3], x1, kb.y);
+                mac128(acc[m][4], acc[m][5], x0, ka.x);
+                mac128(acc[m][6], acc[m][7], x1, ka.y);
             }
-            const ulonglong2 b = ld2(kp.key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n) + k);
-            const ulonglong2 a = ld2(kp.key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n) + k);
-            mac128(l00, h00, x0, b.x);
-            mac128(l01, h01, x1, b.y);
-            mac128(l10, h10, x0, a.x);
-            mac128(l11, h11, x1, a.y);
         }
-        st2(kp.acc + row + k, mont_reduce(l00, h00, q, qn), mont_reduce(l01, h01, q, qn));
-        st2(kp.acc + (((size_t)kp.n_rows + t) << log_n) + k, mont_reduce(l10, h10, q, qn),
-            mont_reduce(l11, h11, q, qn));
+#pragma unroll
+        for (int m = 0; m < KS_MB; m++) {
+            if (m >= nb) break;
+            u64 *acc_m = kp.acc + (size_t)(b0 + m) * kp.acc_stride;
+            st2(acc_m + row + k, mont_reduce(acc[m][0], acc[m][1], q, qn), mont_reduce(acc[m][2], acc[m][3], q, qn));
+            st2(acc_m + (((size_t)kp.n_rows + t) << log_n) + k, mont_reduce(acc[m][4], acc[m][5], q, qn),
+                mont_reduce(acc[m][6], acc[m][7], q, qn));
+        }
     }
 }
 void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
@@ -822,16 +895,25 @@ void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
     need16(k.ext);
     need16(k.key);
     need16(k.acc);
+    if (k.batch < 1 || (k.batch > 1 && ((k.d_stride | k.ext_stride | k.acc_stride) & 1)))
+        throw Error{HE_EINVAL, "key inner product: bad batch layout"};
+    constexpr int MB = 4;
+    dim3 grid = ew_grid(k.n_rows, log_n);
+    grid.z = (unsigned)(k.batch == 1 ? 1 : (k.batch + MB - 1) / MB);
     prof_begin(PROF_KS_INNER, s);
-    k_keyswitch_inner<<<ew_grid(k.n_rows, log_n), EW_T, 0, s>>>(k, log_n);
-    prof_end(PROF_KS_INNER, s, 8.0 * (3.0 * k.beta + 2.0) * (double)k.n_rows * (double)(1 << log_n));
+    if (k.batch == 1) k_keyswitch_inner<1><<<grid, EW_T, 0, s>>>(k, log_n);
+    else k_keyswitch_inner<MB><<<grid, EW_T, 0, s>>>(k, log_n);
+    // algorithmic bytes: the beta key digits (b and a) once, then per member the
+    // beta input digits and the two outputs
+    prof_end(PROF_KS_INNER, s,
+             8.0 * (2.0 * k.beta + (k.beta + 2.0) * k.batch) * (double)k.n_rows * (double)(1 << log_n));
 }
 
 __global__ void __launch_bounds__(EW_T) k_moddown_finish(Rows out, Rows acc, Rows conv, ScalarTab pinv,
                                                          Rows add_to, int add_mask, int log_n) {
     const int r = blockIdx.y, p = out.prime(r);
     const u64 q = c_pcs[out.slot].m[p].q, w = pinv.v[p], ws = pinv.s[p];
-    const bool add = (add_mask >> (r / out.lpp)) & 1;
+    const bool add = (add_mask >> ((r / out.lpp) & 1)) & 1;  // bit k: polynomial k of every member
     u64 *o = out.row(r, log_n);
     const u64 *pa = acc.row(r, log_n), *pc = conv.row(r, log_n);
     const u64 *pd = add ? add_to.row(r, log_n) : nullptr;
@@ -862,24 +944,22 @@ __device__ __forceinline__ u64 centred_mod(u64 v, u64 q_src, u64 q_src_mod_m, co
     if (v > (q_src - 1) / 2) vm = sub_mod(vm, q_src_mod_m, m.q);
     return vm;
 }
-__global__ void __launch_bounds__(EW_T) k_rescale_lift(Rows lift, const u64 *l0, const u64 *l1, u64 ql, int l,
-                                                       int log_n) {
-    const int r = blockIdx.y;  // 0..2l-1: polynomial r / l, target prime r % l
+__global__ void __launch_bounds__(EW_T) k_rescale_lift(Rows lift, const u64 *last, u64 ql, int l, int log_n) {
+    const int r = blockIdx.y;  // polynomial r / l, target prime r % l
     const int poly = r / l, i = r % l;
     const ModQ m = c_pcs[lift.slot].m[i];
     const u64 qlm = barrett_reduce(ql, 0, m);
-    const u64 *src = poly ? l1 : l0;
+    const u64 *src = last + ((size_t)poly << log_n);
     u64 *o = lift.row(r, log_n);
     EW_PAIRS_FOR(k, log_n) {
         const ulonglong2 v = ld2(src + k);
         st2(o + k, centred_mod(v.x, ql, qlm, m), centred_mod(v.y, ql, qlm, m));
     }
 }
-void rescale_lift(const Rows &lift, const u64 *last0, const u64 *last1, u64 ql, int l, int log_n, cudaStream_t s) {
+void rescale_lift(const Rows &lift, const u64 *last, int n_polys, u64 ql, int l, int log_n, cudaStream_t s) {
     need16(lift);
-    need16(last0);
-    need16(last1);
-    k_rescale_lift<<<ew_grid(2 * l, log_n), EW_T, 0, s>>>(lift, last0, last1, ql, l, log_n);
+    need16(last);
+    k_rescale_lift<<<ew_grid(n_polys * l, log_n), EW_T, 0, s>>>(lift, last, ql, l, log_n);
 }
 __global__ void __launch_bounds__(EW_T) k_rescale_finish(Rows out, Rows in, Rows lift, ScalarTab qlinv, int log_n) {
     const int r = blockIdx.y, p = out.prime(r);
@@ -898,22 +978,21 @@ void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const Sca
     need16(lift);
     k_rescale_finish<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, in, lift, qlinv, log_n);
 }
-__global__ void __launch_bounds__(EW_T) k_modraise_lift(Rows out, const u64 *c0, const u64 *c1, u64 q0, int log_n) {
+__global__ void __launch_bounds__(EW_T) k_modraise_lift(Rows out, const u64 *src0, u64 q0, int log_n) {
     const int r = blockIdx.y;
     const ModQ m = c_pcs[out.slot].m[out.prime(r)];
     const u64 q0m = barrett_reduce(q0, 0, m);
-    const u64 *src = (r / out.lpp) ? c1 : c0;
+    const u64 *src = src0 + ((size_t)(r / out.lpp) << log_n);
     u64 *o = out.row(r, log_n);
     EW_PAIRS_FOR(k, log_n) {
         const ulonglong2 v = ld2(src + k);
         st2(o + k, centred_mod(v.x, q0, q0m, m), centred_mod(v.y, q0, q0m, m));
     }
 }
-void modraise_lift(const Rows &out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n, cudaStream_t s) {
+void modraise_lift(const Rows &out, const u64 *src, u64 q0, int n_rows, int log_n, cudaStream_t s) {
     need16(out);
-    need16(c0);
-    need16(c1);
-    k_modraise_lift<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, c0, c1, q0, log_n);
+    need16(src);
+    k_modraise_lift<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, src, q0, log_n);
 }
 
 // ------------------------------------------------------------------ sampling

@@ -59,13 +59,23 @@ void ew_add_scalar(const Rows &out, const Rows &a, const ScalarTab &k, int n_row
 // (row r uses prime r for r < l1, special prime nq + r - l1 after), plaintexts
 // in Montgomery form (x 2^64).
 constexpr int DIAG_MAC_MAX = 64;
+// Batch members (grid z) read c0/c1 at + member * c_stride and write out at +
+// member * out_stride; the plaintexts are shared.
 struct DiagMac {
     const u64 *c0[DIAG_MAC_MAX], *c1[DIAG_MAC_MAX], *pt[DIAG_MAC_MAX];
     u64 *out0, *out1;
     int n, slot, l1, nq;
+    int batch = 1;
+    size_t c_stride = 0, out_stride = 0;
 };
+// QP lift of `batch` members (member m at out + m*out_stride, src + m*src_stride)
 void ew_qp_lift(u64 *out, const u64 *src, int l1, int n_rows, u64 g, int add, const ScalarTab &pm, int slot,
-                int log_n, cudaStream_t s);
+                int log_n, cudaStream_t s, int batch = 1, size_t out_stride = 0, size_t src_stride = 0);
+// Batch-member group sum (sum != 0: out member s = sum_{c<g} in member s*g+c)
+// or broadcast (out member b = in member b/g), both polynomials, limbs 0..l1-1
+// (limb t on prime t); member m at + m*stride, polynomial k at + k*poly.
+void ew_group(u64 *out, const u64 *in, int n_out_members, int g, int sum, int l1, size_t out_stride, size_t in_stride,
+              size_t in_poly, size_t out_poly, int slot, int log_n, cudaStream_t s);
 void ew_diag_mac(const DiagMac &dm, int n_rows, int log_n, cudaStream_t s);
 void ew_mul(const Rows &out, const Rows &a, const Rows &b, int n_rows, int log_n, cudaStream_t s);
 // out = out + a (*) b pointwise
@@ -83,7 +93,8 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // Key-switch pieces
 // out row (poly*n_out + t) = sum_a [in_a * qhinv_a] * qhat[a][t], in row (poly*n_in + a)
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s);
-// acc0/acc1 rows t < n_rows: sum_j x_j[t] * key_j[t], x_j = (t in digit j) ? d[t] : ext_j[t]
+// acc0/acc1 rows t < n_rows: sum_j x_j[t] * key_j[t], x_j = (t in digit j) ? d[t] : ext_j[t],
+// for `batch` members (member m's d, ext and acc at + m * the stride)
 struct KeyIP {
     const u64 *d_ntt;     // level limbs of the input polynomial (NTT form)
     const u64 *ext;       // [beta][n_rows][N] extended digits (rows inside the digit unused)
@@ -92,20 +103,23 @@ struct KeyIP {
     int n_rows, l1, nq, np, alpha, beta, key_limbs;
     int slot;
     u64 galois;           // 0: read x_j at position i; else at the source of i under X -> X^galois
+    int batch = 1;
+    size_t d_stride = 0, ext_stride = 0, acc_stride = 0;
 };
 void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s);
 // out_i = (acc_i - conv_i) * pinv_i; polynomial p of the batch (row / lpp)
 // also adds add_to's row when bit p of add_mask is set.
 void moddown_finish(const Rows &out, const Rows &acc, const Rows &conv, const ScalarTab &pinv, int n_rows,
                     const Rows &add_to, int add_mask, int log_n, cudaStream_t s);
-// rescale: from coefficient-form last limbs (2 rows, prime ql) write the
-// centred lift into rows of `lift` (n_rows = 2*l targets)
-void rescale_lift(const Rows &lift, const u64 *last0, const u64 *last1, u64 ql, int l, int log_n, cudaStream_t s);
+// rescale: from coefficient-form last limbs (n_polys rows at last + poly*N,
+// prime ql) write the centred lift into rows of `lift` (n_polys*l targets,
+// row r: polynomial r / l, prime r % l)
+void rescale_lift(const Rows &lift, const u64 *last, int n_polys, u64 ql, int l, int log_n, cudaStream_t s);
 void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const ScalarTab &qlinv, int n_rows,
                     int log_n, cudaStream_t s);
-// mod-raise: from coefficient-form level-0 limbs of c0, c1 (prime q0) write
-// the centred lift into rows 0..l of out (coefficient form)
-void modraise_lift(const Rows &out, const u64 *c0, const u64 *c1, u64 q0, int n_rows, int log_n, cudaStream_t s);
+// mod-raise: from coefficient-form level-0 limbs (prime q0; polynomial p's at
+// src + p*N) write the centred lift into the rows of out (coefficient form)
+void modraise_lift(const Rows &out, const u64 *src, u64 q0, int n_rows, int log_n, cudaStream_t s);
 
 // Sampling (Philox4x32-10, counter = (index, limb, object, domain))
 void sample_uniform(const Rows &out, int n_rows, u64 seed, u32 object, u32 domain, int log_n, cudaStream_t s);

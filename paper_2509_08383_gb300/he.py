@@ -35,7 +35,7 @@ class CPlan(C.Structure):
     _fields_ = [("n", C.c_uint32), ("packing", C.c_uint32), ("T", C.c_uint32), ("power", C.POINTER(C.c_uint32)),
                 ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_uint32)), ("kappa", C.POINTER(C.c_double)),
                 ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double),
-                ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32)]
+                ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32), ("cts", C.c_uint32)]
 
 
 _lib = None
@@ -77,6 +77,9 @@ def lib():
             "he_ct_info": [VP, C.POINTER(u32), pd],
             "he_ct_device": [VP, C.POINTER(pu64), C.POINTER(sz)],
             "he_ct_free": [VP],
+            "he_batch_pack": [VP, PP, sz, PP],
+            "he_batch_member": [VP, VP, u32, PP],
+            "he_batch_size": [VP, C.POINTER(u32)],
             "he_add": [VP, VP, VP, PP],
             "he_sub": [VP, VP, VP, PP],
             "he_mul_int": [VP, VP, i64, PP],
@@ -160,6 +163,12 @@ class Ciphertext:
     def scale(self):
         return self._info()[1]
 
+    @property
+    def batch(self):
+        n = C.c_uint32()
+        lib().he_batch_size(self.ptr, C.byref(n))
+        return n.value
+
     def export(self):
         """(2, level+1, N) uint64, coefficient form."""
         L = self.level
@@ -176,7 +185,8 @@ def plan_struct(plan):
                 kappa=(C.c_double * T)(*plan.kappa), y0=(C.c_double * T)(*plan.y0), norm=(C.c_double * T)(*norm))
     s = CPlan(n=plan.n, packing=0 if plan.packing == "replicate" else 1, T=T, power=arrs["power"], c=arrs["c"],
               k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f,
-              norm=arrs["norm"], bootstrap=int(bool(getattr(plan, "bootstrap", False))))
+              norm=arrs["norm"], bootstrap=int(bool(getattr(plan, "bootstrap", False))),
+              cts=int(getattr(plan, "cts", 1)))
     return s, arrs
 
 
@@ -292,6 +302,15 @@ class Context:
         out = np.zeros(self.n)
         self._chk(lib().he_decrypt_poly(self.ptr, ct.ptr, _dptr(out)))
         return out
+
+    # batches
+    def batch_pack(self, cts):
+        """One batch holding the members of `cts` (ciphertexts or batches), in order."""
+        arr = (C.c_void_p * len(cts))(*[c.ptr for c in cts])
+        return self._ct(lib().he_batch_pack, arr, len(cts))
+
+    def batch_member(self, batch, i):
+        return self._ct(lib().he_batch_member, batch.ptr, int(i))
 
     def import_ct(self, arr, level, scale):
         a = np.ascontiguousarray(arr, dtype=np.uint64).reshape(-1)

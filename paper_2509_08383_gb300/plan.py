@@ -34,7 +34,7 @@ import numpy as np
 
 @dataclass
 class CutMaxPlan:
-    n: int                      # real entries (vocabulary size) per ciphertext
+    n: int                      # real entries (vocabulary size) per stream
     slots: int                  # N/2
     packing: str                # "replicate" (n | slots, n power of two) or "pad"
     T: int
@@ -48,6 +48,7 @@ class CutMaxPlan:
     bootstrap: bool = False
     norm: List[float] = None
     extra: dict = field(default_factory=dict)
+    cts: int = 1                # ciphertexts per stream (n > slots spreads over several)
 
     def __post_init__(self):
         if self.norm is None:
@@ -60,7 +61,7 @@ class CutMaxPlan:
 
     @property
     def pad(self) -> int:
-        return 0 if self.packing == "replicate" else self.slots - self.n
+        return 0 if self.packing == "replicate" else self.cts * self.slots - self.n
 
     def depth(self) -> int:
         """Levels consumed without bootstrapping (see the circuit description)."""
@@ -81,23 +82,38 @@ def power_depth(p: int) -> int:
     return (p - 1).bit_length()
 
 
+def cts_for(n: int, slots: int) -> int:
+    """Ciphertexts a stream of n entries fills."""
+    return -(-int(n) // int(slots))
+
+
 def packing_for(n: int, slots: int) -> str:
-    if n > slots:
-        raise ValueError("n > slots needs several ciphertexts")
-    if slots % n == 0 and (n & (n - 1)) == 0:
+    if n <= slots and slots % n == 0 and (n & (n - 1)) == 0:
         return "replicate"
     return "pad"
 
 
 def pack(x, slots: int, packing: str) -> np.ndarray:
-    """Slot vector for one ciphertext."""
+    """Slot vector for one ciphertext (n <= slots)."""
     x = np.asarray(x, dtype=np.float64)
+    if len(x) > slots:
+        raise ValueError("n > slots: use pack_cts")
     out = np.zeros(slots)
     if packing == "replicate":
         out[:] = np.tile(x, slots // len(x))
     else:
         out[: len(x)] = x
     return out
+
+
+def pack_cts(x, slots: int) -> List[np.ndarray]:
+    """Slot vectors of the ciphertexts of one zero-padded stream: ciphertext c
+    holds entries c*slots .. (c+1)*slots - 1, the last one zero-padded."""
+    x = np.asarray(x, dtype=np.float64)
+    k = cts_for(len(x), slots)
+    out = np.zeros(k * slots)
+    out[: len(x)] = x
+    return [out[c * slots:(c + 1) * slots].copy() for c in range(k)]
 
 
 def _exact_stats(x, T, p, c):
@@ -223,6 +239,6 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
                 d = dd
                 break
     return CutMaxPlan(n=n, slots=slots, packing=packing_for(n, slots), T=T, p=p, c=c, k=ks,
-                      kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap, norm=norms,
+                      kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap, norm=norms, cts=cts_for(n, slots),
                       extra={"V_range": vr, "S_range": [float(Ss.min()), float(Ss.max())], "margin": margin,
                              "n_cal": n_cal})
