@@ -1,6 +1,6 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|mul16|rot16|ntt16|boot16]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|mul16|rot16|ntt16|boot16]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
@@ -38,7 +38,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-CFG2_Q = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+# base prime 47 bits: a bootstrap refreshes with error ~(q0 / Delta) x the EvalMod
+# approximation error, so q0 = 2^47 against Delta = 2^40 keeps it near 1e-7 for
+# messages up to 2 (about 1.5e-5 with a 55-bit q0)
+CFG2_Q = [47] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
 # relative error of the invsqrt and inverse approximations: 10 bits, inside
 # the 7..13-bit range of the invsqrt benchmarks the paper reprints (App. B)
 INVSQRT_TOL = 2.0 ** -10
@@ -194,7 +197,7 @@ def run_reference(args):
                 times.append(time.perf_counter() - t0)
         sample = f"{args.steps} full CutMax decodes (encrypt + CutMax + decrypt) on the oracle"
     else:
-        ks, nb = ledger.cutmax_ledger(pl, len(qb), log_n, boot=boot[1:])
+        ks, nb = ledger.cutmax_ledger(pl, len(qb), log_n, boot=boot[1:], qbits=qb)
         levels = [min(ks), (min(ks) + len(qb) - 1) // 2, len(qb) - 1]
         for step in range(args.warmup + args.steps):
             model = oracle_ks_model(log_n, qb, pb, dnum, boot[0], levels)
@@ -241,6 +244,98 @@ def cpu_baseline(args, ks_by_level=None):
     dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
             "sample": "1 full CutMax decode of the bench workload on the oracle (ciphertext already encrypted)"}
+
+
+CFG3_VOCABS = [8192, 32000, 50257, 128256]
+
+
+def run_cfg3(args):
+    """64 concurrent decode streams, 16 per vocabulary size in CFG3_VOCABS
+    (1/1/2/4 ciphertexts each at N=2^16), logits N(0, 2^2) with the top
+    entry 0.5 above the second, the paper's HE circuit (T=4, p=[16,4,4,6],
+    c=[5,3,3,3]) with bootstrapping.  Batched: one batch per vocabulary size,
+    every homomorphic step one launch for all its streams, the streams' scalar
+    chains shared.  Sequential: one stream at a time; every stream of a
+    vocabulary costs the same, so one stream per vocabulary is timed and
+    counted 16 times."""
+    import torch
+    from paper_2509_08383_gb300 import build, he
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    build.build_library()
+    torch.cuda.set_device(0)
+    per = 16
+    slots = 1 << 15
+    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=200 << 30)
+    g.bootstrap_prepare(24, 4, 31)
+    groups = []
+    for v in CFG3_VOCABS:
+        gen = (lambda s, v=v: synth.logits_gaussian(s, n=v, sd=2.0, gap=0.5))
+        pl = P.calibrate(lambda i: gen(100000 + i), 60, v, slots, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
+                         tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True)
+        pl.shared = True
+        g.cutmax_prepare(pl)
+        xs = [gen(s) for s in range(per)]
+        cts = []
+        for s, x in enumerate(xs):
+            vecs = P.pack_cts(x, slots) if pl.cts > 1 else [P.pack(x, slots, pl.packing)]
+            cts += [g.encrypt(vv, g.delta, 1000 * v + 10 * s + c) for c, vv in enumerate(vecs)]
+        groups.append((v, pl, xs, g.batch_pack(cts), cts[:pl.cts]))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    with ClockSampler(0) as clk:
+        t_batch, t_seq, acc = 0.0, 0.0, []
+        for v, pl, xs, batch, one in groups:
+            for it in range(args.warmup + args.steps):
+                flush.zero_()
+                g.ledger(reset=True)
+                ms, Z = timed(lambda: g.cutmax(batch, pl))
+                _, nb = g.ledger(reset=True)
+                if it >= args.warmup:
+                    t_batch += ms / args.steps
+            # argmax of every stream of the batch
+            ok = 0
+            for s, x in enumerate(xs):
+                dec = np.concatenate([g.decrypt(g.batch_member(Z, s * pl.cts + c)) for c in range(pl.cts)])[:v]
+                ok += int(np.argmax(dec)) == int(np.argmax(x))
+            acc.append(ok)
+            pl1 = P.CutMaxPlan(**{**pl.to_dict(), "shared": False})
+            b1 = g.batch_pack(one)
+            for it in range(args.warmup + args.steps):
+                flush.zero_()
+                g.ledger(reset=True)
+                ms1, _ = timed(lambda: g.cutmax(b1, pl1))
+                _, nb1 = g.ledger(reset=True)
+                if it >= args.warmup:
+                    t_seq += per * ms1 / args.steps
+            res[str(v)] = {"cts_per_stream": pl.cts, "batched_ms": ms, "batched_bootstraps": nb,
+                           "single_stream_ms": ms1, "single_stream_bootstraps": nb1, "argmax_ok": ok, "k": pl.k,
+                           "d": pl.d}
+            del Z
+    n_streams = per * len(CFG3_VOCABS)
+    out = {"metric": "batched encrypted CutMax decodes/sec, 64 streams of vocabularies 8192/32000/50257/128256 "
+                     "(N=2^16), 1 GB300", "value": 1000.0 * n_streams / t_batch, "unit": "decodes/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "64 decode streams, 16 per vocabulary 8192/32000/50257/128256 (1/1/2/4 "
+                                  "ciphertexts), N(0,4) logits with top gap 0.5, T=4 p=[16,4,4,6] c=[5,3,3,3], "
+                                  "bootstrapping, one batch per vocabulary with shared scalar chains",
+                      "l2": "flushed between steps (256 MiB write)"},
+           "sequential": {"value": 1000.0 * n_streams / t_seq, "unit": "decodes/s", "ms_per_step": t_seq,
+                          "how": "one stream per vocabulary timed alone, times 16"},
+           "speedup_vs_sequential": t_seq / t_batch, "argmax_correct": sum(acc), "streams": n_streams,
+           "per_vocabulary": res, "clocks": clk.summary()}
+    print(json.dumps(out))
 
 
 def run_micro(args):
@@ -319,13 +414,16 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "mul16", "rot16", "ntt16", "boot16"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "mul16", "rot16", "ntt16",
+                                                           "boot16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in ("mul16", "rot16", "ntt16", "boot16"):
         return run_micro(args)
+    if args.workload == "cfg3":
+        return run_cfg3(args)
 
     import torch
     dist, rank, ws = dist_setup(args)
@@ -403,14 +501,18 @@ def main():
     pin = torch.empty(slots, dtype=torch.float64).pin_memory()
     out = np.zeros(pl.n)
     e2e_times = []
+    argmax_ok, top_z = 0, []
     for s in range(nsteps):
-        pin.numpy()[:] = P.pack(gen(20000 + s), slots, pl.packing)
+        x_s = gen(20000 + s)
+        pin.numpy()[:] = P.pack(x_s, slots, pl.packing)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ct = g.encrypt(pin.numpy(), g.delta, 100000 + s)
         z = g.cutmax(ct, pl)
         out[:] = g.decrypt(z, pl.n)
         t1 = time.perf_counter()
+        argmax_ok += int(np.argmax(out)) == int(np.argmax(x_s))
+        top_z.append(float(out.max()))
         if s >= args.warmup:
             e2e_times.append(t1 - t0)
     e2e = ws * args.steps / replicas.max_over_ranks(sum(e2e_times), dist, device="cuda")
@@ -423,6 +525,8 @@ def main():
            "e2e": {"value": e2e, "unit": "decodes/s", "h2d_bytes_per_step": slots * 8,
                    "d2h_bytes_per_step": pl.n * 8},
            "gpu_launches": int(launches), "roofline": roofline,
+           "check": {"argmax_correct": argmax_ok, "decodes": nsteps, "mean_max_z": float(np.mean(top_z)),
+                     "what": "decrypted end-to-end outputs: argmax vs the plaintext logits, mean of max Z"},
            "ledger": {"keyswitches_per_decode": int(sum(ks_by_level.values())),
                       "bootstraps_per_decode": nboot / args.steps}}
     if rank == 0:

@@ -228,9 +228,18 @@ int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out)
  * kappa_f * sum(Y).  bootstrap != 0 selects the bootstrapped circuit (needs
  * he_bootstrap_prepare): the Goldschmidt input is x = kappa V, Y_(t+1) is
  * scaled by norm[t] (NULL = all 1) and a ciphertext is bootstrapped before
- * any phase that needs more levels than it has (Y before the statistics: 3;
+ * any phase that needs more levels than it has (Y before the statistics: 5,
+ * since V = sum (n y - S)^2 is scaled to x = kappa V by up to 3 rescales that
+ * keep a 30-bit multiplier, and V itself is too large to refresh;
  * x: 2; g and h between Goldschmidt steps: 2; D' and h: 1; u before the
- * power: ceil(log2 p); Y before the final normalisation: d + 3). */
+ * power: ceil(log2 p); Y before the final normalisation: d + 3).
+ * shared != 0 (bootstrapped plans, batches of S > 1 streams): the per-stream
+ * scalar chains (the Goldschmidt inverse square root and the final inverse,
+ * whose inputs are replicated in every slot) run once for the batch, packed
+ * into one ciphertext (slot i carries stream i mod S', S' = S rounded up to a
+ * power of two, S' <= N/4), and are handed back to the streams by a slot mask
+ * and a log2(S')-step rotate-and-sum; engineering beyond the paper, which
+ * evaluates one stream at a time. */
 typedef struct {
     uint32_t n, packing, T;
     const uint32_t *power;
@@ -243,6 +252,7 @@ typedef struct {
     const double *norm;
     int32_t bootstrap;
     uint32_t cts;
+    uint32_t shared;
 } he_cutmax_plan;
 
 /* Generate every key the plan needs (rotations 2^i, relinearisation and,

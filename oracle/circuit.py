@@ -52,6 +52,21 @@ class HE:
         t = self.ctx.mul_intd(ct, K, ct.scale * E)
         return self.ctx.rescale(t)
 
+    def mcr_bits(self, ct, c, target, min_bits):
+        """c * ct with K = rint(c E) of at least min_bits bits: E spans as many
+        primes r <= 3 (rescales) as that takes, E = target q_l..q_(l-r+1)/scale."""
+        target = self.delta if target is None else target
+        r = 1
+        E = (target * float(self.q(ct.level))) / ct.scale
+        while abs(c * E) < 2.0 ** min_bits and r < 3 and ct.level - r >= 1:
+            E *= float(self.q(ct.level - r))
+            r += 1
+        K = float(np.rint(c * E))
+        t = self.ctx.mul_intd(ct, K, ct.scale * E)
+        for _ in range(r):
+            t = self.ctx.rescale(t)
+        return t
+
     def add_const(self, ct, c):
         return self.ctx.add_intd(ct, float(np.rint(c * ct.scale)))
 
@@ -161,7 +176,9 @@ def cutmax_he(he, ct, plan, bootstrap=None):
         coef = 2.0 * math.sqrt(plan.kappa[t] * n) / plan.c[t]
         new = []
         for c, D in enumerate(Ds):
-            Dp = he.mul_plain_rescale(D, coef * masks[c]) if m else he.mcr(D, coef)
+            # the 0/1 mask as a plaintext, coef as an integer multiplier (a
+            # plaintext of coef-sized values would round to ~1e-5 relative)
+            Dp = he.mcr(he.mul_plain_rescale(D, masks[c]) if m else D, coef)
             u = he.mul_rescale(Dp, h)
             u = he.add_plain_vec(u, masks[c]) if m else he.add_const(u, 1.0)
             new.append(he.power(u, plan.p[t]))
@@ -180,7 +197,9 @@ def cutmax_he_boot(he, ct, plan, boot):
     Y_(t+1) is scaled by plan.norm[t] through u' = norm^(1/p) u.
     The input is first dropped to the bootstrap's output level.  Before each
     phase a ciphertext with fewer levels than the phase needs is bootstrapped:
-    Y before the statistics (3), x before the iteration (2), the packed
+    Y before the statistics (5: the variance sum V, far too large to refresh,
+    needs up to 3 rescales to reach x = kappa V ~ 1 with a 30-bit multiplier),
+    x before the iteration (2), the packed
     Goldschmidt pair [g | h] between steps (2) and before h is extracted (1),
     D' and h before the product (1), u before the power (ceil log2 p), Y before
     the final normalisation (d + 3).
@@ -202,16 +221,16 @@ def cutmax_he_boot(he, ct, plan, boot):
     for t in range(plan.T):
         p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
         rn = plan.norm[t] ** (1.0 / p)
-        Y = ensure(Y, 3)
+        Y = ensure(Y, 5)
         S = he.rotsum(Y, steps)
         D = ctx.sub(ctx.mul_int(Y, n), S)
         E = he.mul_rescale(D, D)
         V = he.rotsum(E, steps)
         if m:
             V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
-        x = ensure(he.mcr(V, kap), 2)
+        x = ensure(he.mcr_bits(V, kap, None, 30), 2)
         coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
-        Dp = he.mul_plain_rescale(D, coef * mask) if m else he.mcr(D, coef)
+        Dp = he.mcr(he.mul_plain_rescale(D, mask), coef) if m else he.mcr(D, coef)
         # Goldschmidt pair packed in one ciphertext: slots [0, s/2) hold g,
         # slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
         half = plan.slots // 2
@@ -223,7 +242,9 @@ def cutmax_he_boot(he, ct, plan, boot):
         P = he.mul_rescale(P, a)
         for i in range(2, k + 1):
             if P.level < 2:
-                P = boot.bootstrap(P)
+                # a step maps the pair's scale s to s^3/(q q'): the refresh is
+                # followed by a multiplication by 1 landing exactly on Delta
+                P = he.mcr(boot.bootstrap(P), 1.0)
             Q = he.mul_rescale(P, ctx.rotate(P, half))
             P = he.mul_rescale(P, he.add_const(he.neg(Q), 1.5))
         P = ensure(P, 1)

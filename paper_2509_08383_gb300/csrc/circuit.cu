@@ -38,6 +38,23 @@ struct HE {
         Ct t = op_mul_intd(cx, ct, K, ct->scale * E);
         return op_rescale(cx, t.get());
     }
+    // c * ct with the integer multiplier K = rint(c E) carrying at least
+    // min_bits bits: a tiny c against a large scale (the range scale kappa of
+    // a variance sum of tens of thousands of terms) is spread over as many
+    // rescales r <= 3 as that takes, E = target q_l ... q_(l-r+1) / scale.
+    Ct mcr_bits(const he_ct *ct, double c, double target, int min_bits) {
+        if (target < 0) target = delta;
+        int r = 1;
+        double E = (target * (double)q(ct->level)) / ct->scale;
+        while (std::fabs(c * E) < std::ldexp(1.0, min_bits) && r < 3 && ct->level - r >= 1) {
+            E *= (double)q(ct->level - r);
+            r++;
+        }
+        double K = std::rint(c * E);
+        Ct t = op_mul_intd(cx, ct, K, ct->scale * E);
+        for (int i = 0; i < r; i++) t = op_rescale(cx, t.get());
+        return t;
+    }
     Ct add_const(const he_ct *ct, double c) { return op_add_intd(cx, ct, std::rint(c * ct->scale)); }
     Ct neg(const he_ct *ct) { return op_mul_int(cx, ct, -1); }
     Ct mul_rescale(const he_ct *a, const he_ct *b) {
@@ -139,6 +156,7 @@ Plan plan_from(const he_cutmax_plan *p) {
     }
     pl.bootstrap = p->bootstrap != 0;
     pl.cps = p->cts ? (int)p->cts : 1;
+    pl.shared = p->shared != 0;
     if (pl.cps > 64) throw Error{HE_EINVAL, "more than 64 ciphertexts per stream"};
     pl.d = (int)p->d;
     pl.kappa_f = p->kappa_f;
@@ -229,13 +247,13 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
         }
         Ct h = stream_bcast(cx, invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t]).get(), cps);
         double coef = 2.0 * std::sqrt(pl.kappa[t] * pl.n) / pl.c[t];
-        Ct Dp;
-        if (m) {
-            Scratch s2{cx, {}};
-            Dp = he.mul_plain_rescale(D.get(), upload_scaled(cx, s2, sh.mask, coef), sh.slots, -1, cps);
-        } else {
-            Dp = he.mcr(D.get(), coef);
-        }
+        // D' = D * coef (times the 0/1 slot mask when padded): the mask is a
+        // plaintext of O(1) slot values and coef (~1e-5 for tens of thousands of
+        // logits) an integer multiplier, each exact to ~1e-7 or better; one
+        // plaintext of coef-sized slot values would round to ~1e-5 relative.
+        // D' has spare levels (h's path is longer), so the split costs no depth.
+        Ct Dp = m ? he.mul_plain_rescale(D.get(), d_mask, sh.slots, -1, cps) : op_copy(cx, D.get());
+        Dp = he.mcr(Dp.get(), coef);
         Ct u = he.mul_rescale(Dp.get(), h.get());
         u = m ? he.add_plain_vec(u.get(), d_mask, sh.slots, cps) : he.add_const(u.get(), 1.0);
         Y = he.power(u.get(), pl.p[t]);
@@ -723,7 +741,7 @@ Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
     auto B = cx->boot_state;
     if (!B) throw Error{HE_EINVAL, "bootstrapping not prepared"};
     HE he{cx, B->em_scale};
-    cx->n_boot++;
+    cx->n_boot += (uint64_t)in->batch;
     const u64 q0 = cx->primes[0];
     const double ratio = in->scale / B->s_fix;
     Ct low = in->level ? op_drop(cx, in, 0) : op_copy(cx, in);
@@ -777,10 +795,36 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     // g, slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
     const int half = slots / 2;
     const u64 g_half = rot_galois(cx, half);
+    // scalar chains shared by the batch's streams: stream s owns the slots
+    // i = s (mod Sp); packing costs one level, unpacking one level and a
+    // log2(Sp)-step rotate-and-sum
+    const int n_streams = sh.S;
+    const bool shared = pl.shared && n_streams > 1;
+    int Sp = 1, lsp = 0;
+    while (Sp < n_streams) Sp *= 2, lsp++;
+    if (shared && (Sp > slots / 2 || lsp > sh.steps))
+        throw Error{HE_EINVAL, "too many streams to share the scalar chains"};
+    Scratch smask{cx, {}};
+    const double *d_cls = nullptr;
+    if (shared) {
+        std::vector<double> cls((size_t)n_streams * slots, 0.0);
+        for (int st = 0; st < n_streams; st++)
+            for (int i = st; i < slots; i += Sp) cls[(size_t)st * slots + i] = 1.0;
+        d_cls = upload_scaled(cx, smask, cls, 1.0);
+    }
+    auto pack = [&](const he_ct *a) -> Ct {  // S members, replicated scalars -> one ciphertext
+        Ct mk = he.mul_plain_rescale(a, d_cls, slots, -1, n_streams);
+        return op_group(cx, mk.get(), n_streams, true);
+    };
+    auto unpack = [&](const he_ct *a) -> Ct {  // one packed ciphertext -> S members, replicated
+        Ct b = op_group(cx, a, n_streams, false);
+        Ct mk = he.mul_plain_rescale(b.get(), d_cls, slots, -1, n_streams);
+        return he.rotsum(mk.get(), lsp);
+    };
     for (int t = 0; t < pl.T; t++) {
         const int p = pl.p[t], k = pl.k[t];
         const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
-        Y = ensure(std::move(Y), 3);
+        Y = ensure(std::move(Y), 5);
         Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
         Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).get(), true);
         Ct E = he.mul_rescale(D.get(), D.get());
@@ -789,12 +833,19 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
             Ct S2 = he.mul_rescale(S.get(), S.get());
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
         }
-        Ct x = ensure(he.mcr(V.get(), kap), 2);
+        // V (about n^3 sigma^2, far beyond what a bootstrap can refresh) keeps
+        // the 4 levels that Y brought: up to 3 rescales scale it to x ~ 1
+        Ct x = he.mcr_bits(V.get(), kap, -1, 30);
+        if (shared) x = pack(ensure(std::move(x), 1).get());
+        x = ensure(std::move(x), 2);
         const double coef = 2.0 * std::sqrt(kap * pl.n) / pl.c[t] * rn;
+        // D' = D * coef (times the 0/1 slot mask when padded), mask and scalar
+        // applied separately for precision (see cutmax_ct)
         Ct Dp;
         if (m) {
             Scratch s2{cx, {}};
-            Dp = he.mul_plain_rescale(D.get(), upload_scaled(cx, s2, sh.mask, coef), slots, -1, cps);
+            Dp = he.mul_plain_rescale(D.get(), upload_scaled(cx, s2, sh.mask, 1.0), slots, -1, cps);
+            Dp = he.mcr(Dp.get(), coef);
         } else {
             Dp = he.mcr(D.get(), coef);
         }
@@ -807,8 +858,12 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         Ct P = he.mul_plain_rescale(x.get(), d_vlo, slots);
         P = he.add_plain_vec(P.get(), d_vhi, slots);
         P = he.mul_rescale(P.get(), a.get());
+        // one step maps the pair's scale s to s^3 / (q q'): a deviation from
+        // Delta triples every step and a bootstrap only flips its sign, so each
+        // refresh is followed by a multiplication by 1 that lands exactly on
+        // Delta (the spare 13th level of a refresh: 6 steps still fit)
         for (int i = 2; i <= k; i++) {
-            if (P->level < 2) P = bootstrap_ct(cx, P.get());
+            if (P->level < 2) P = he.mcr(bootstrap_ct(cx, P.get()).get(), 1.0);
             Ct Q = he.mul_rescale(P.get(), op_automorph(cx, P.get(), g_half).get());
             P = he.mul_rescale(P.get(), he.add_const(he.neg(Q.get()).get(), 1.5).get());
         }
@@ -816,6 +871,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         for (int i = 0; i < slots; i++) vhi[i] = i < half ? 0.0 : 1.0;
         Ct hm = he.mul_plain_rescale(P.get(), upload_scaled(cx, sv, vhi, 1.0), slots);
         Ct h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
+        if (shared) h = unpack(ensure(std::move(h), 1).get());
         h = ensure(std::move(h), 1);
         Dp = ensure(std::move(Dp), 1);
         Ct u = he.mul_rescale(Dp.get(), stream_bcast(cx, h.get(), cps).get());
@@ -828,9 +884,18 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         u = ensure(std::move(u), power_depth(p));
         Y = he.power(u.get(), p);
     }
-    Y = ensure(std::move(Y), pl.d + 3);
-    Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
-    Ct F = stream_bcast(cx, inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d).get(), cps);
+    Y = ensure(std::move(Y), shared ? 3 : pl.d + 3);
+    Ct Ssum = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+    Ct F;
+    if (shared) {
+        Ct Sp_ct = ensure(pack(ensure(std::move(Ssum), 1).get()), pl.d + 3);
+        Ct Fp = ensure(inverse_goldschmidt(he, Sp_ct.get(), pl.kappa_f, pl.d), 2);
+        F = ensure(unpack(Fp.get()), 1);
+        Y = ensure(std::move(Y), 2);
+    } else {
+        F = inverse_goldschmidt(he, Ssum.get(), pl.kappa_f, pl.d);
+    }
+    F = stream_bcast(cx, F.get(), cps);
     return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());
 }
 

@@ -173,6 +173,7 @@ struct Plan {
     double kappa_f;
     bool bootstrap;
     int cps = 1;  // ciphertexts per stream
+    bool shared = false;  // batched streams share the scalar chains (see he_cutmax_plan)
     int pad(int slots) const;
 };
 Plan plan_from(const he_cutmax_plan *p);

@@ -35,7 +35,8 @@ class CPlan(C.Structure):
     _fields_ = [("n", C.c_uint32), ("packing", C.c_uint32), ("T", C.c_uint32), ("power", C.POINTER(C.c_uint32)),
                 ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_uint32)), ("kappa", C.POINTER(C.c_double)),
                 ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double),
-                ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32), ("cts", C.c_uint32)]
+                ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32), ("cts", C.c_uint32),
+                ("shared", C.c_uint32)]
 
 
 _lib = None
@@ -186,7 +187,7 @@ def plan_struct(plan):
     s = CPlan(n=plan.n, packing=0 if plan.packing == "replicate" else 1, T=T, power=arrs["power"], c=arrs["c"],
               k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f,
               norm=arrs["norm"], bootstrap=int(bool(getattr(plan, "bootstrap", False))),
-              cts=int(getattr(plan, "cts", 1)))
+              cts=int(getattr(plan, "cts", 1)), shared=int(bool(getattr(plan, "shared", False))))
     return s, arrs
 
 

@@ -139,9 +139,12 @@ class Sim:
         return c - 3
 
 
-def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
-    """Key switches per level and bootstraps of one CutMax (library circuit)."""
+def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
+    """Key switches per level and bootstraps of one CutMax (library circuit).
+    qbits: bit sizes of the Q primes (default 40 each), for the number of
+    rescales the range-scale multiplication x = kappa V takes."""
     sim = Sim(nq, log_n, boot)
+    qb = list(qbits) if qbits is not None else [40] * nq
     steps = plan.rotsum_steps
     m = plan.pad
 
@@ -152,6 +155,14 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
 
     def mcr(a):
         return a - 1
+
+    def mcr_bits(a, c, min_bits=30):
+        # the integer multiplier c * q_a * ... (scale ~ target) keeps min_bits bits
+        r, e = 1, qb[a]
+        while abs(c) * 2.0 ** e < 2.0 ** min_bits and r < 3 and a - r >= 1:
+            e += qb[a - r]
+            r += 1
+        return a - r
 
     def power(u, p):
         sq, acc, pp = u, None, int(p)
@@ -173,7 +184,7 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
     for t in range(plan.T):
         p, k = plan.p[t], plan.k[t]
         if plan.bootstrap:
-            Y = ensure(Y, 3)
+            Y = ensure(Y, 5)
         rotsum(Y)
         D = Y
         E = sim.mul(D, D)
@@ -181,13 +192,13 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
         if m:
             sim.mul(Y, Y)
         if plan.bootstrap:
-            x = ensure(mcr(V), 2)
-            Dp = mcr(D)
+            x = ensure(mcr_bits(V, plan.kappa[t]), 2)
+            Dp = mcr(mcr(D)) if m else mcr(D)
             a = mcr(x)
             P = sim.mul(mcr(x), a)            # packed [g | h]
             for i in range(2, k + 1):
                 if P < 2:
-                    P = sim.bootstrap(P)
+                    P = mcr(sim.bootstrap(P))
                 Q = sim.mul(P, sim.rot(P))
                 P = sim.mul(P, Q)
             P = ensure(P, 1)
@@ -205,7 +216,7 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None):
                 if i < k:
                     g = sim.mul(g, a)
                 h = sim.mul(h, a)
-            Dp = mcr(D)
+            Dp = mcr(mcr(D)) if m else mcr(D)
             u = sim.mul(Dp, h)
         Y = power(u, p)
     if plan.bootstrap:

@@ -49,6 +49,7 @@ class CutMaxPlan:
     norm: List[float] = None
     extra: dict = field(default_factory=dict)
     cts: int = 1                # ciphertexts per stream (n > slots spreads over several)
+    shared: bool = False        # batched streams share the scalar chains (bootstrapped plans)
 
     def __post_init__(self):
         if self.norm is None:

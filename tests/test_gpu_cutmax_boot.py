@@ -87,6 +87,6 @@ def test_ledger_model_matches_library(setup):
     g.ledger(reset=True)
     g.cutmax(ct, pl)
     ks, nb = g.ledger(reset=True)
-    model, nb_model = ledger.cutmax_ledger(pl, len(QB), LOG_N, boot=(K, R, D))
+    model, nb_model = ledger.cutmax_ledger(pl, len(QB), LOG_N, boot=(K, R, D), qbits=QB)
     assert nb == nb_model
     assert {i: int(v) for i, v in enumerate(ks) if v} == model
