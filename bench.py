@@ -25,6 +25,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "encrypted CutMax decodes/sec (vocab 32k, N=2^16), 1 GB300"
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of both NTT passes per limb at
+# N=2^16 (90-limb forward / 30-limb inverse launches of one rotation)
+NTT_DRAM_PER_LIMB = {0: (47.9e6 + 102.0e6) / 90, 1: (47.1e6 + 0.3e6 + 15.9e6) / 30}
 PROF_NAMES = {0: "ntt_forward (k_ntt_cols+k_ntt_rows)", 1: "ntt_inverse (k_ntt_rows+k_ntt_cols)",
               2: "keyswitch_inner (k_keyswitch_inner)", 3: "bconv (k_bconv)"}
 
@@ -61,7 +64,7 @@ def workload(name):
                          tol_d=INVSQRT_TOL, bootstrap=True)
         desc = {"workload": "CutMax T=4 p=[16,4,4,6] c=[5,3,3,3], 32000 logits N(0,9) + 50 heavy-tail "
                             "Exp(1.5), top-1 gap in {0.05,0.2,1.0}, zero-padded in N=2^16 slots, CKKS "
-                            "bootstrapping when levels run out (logQ=1534, dnum=3, h=192)",
+                            "bootstrapping when levels run out (logQ<=1521, dnum=3, h=192)",
                 "log_n": log_n, "n": n, "T": 4, "k": pl.k, "d": pl.d}
         return log_n, CFG2_Q, CFG2_P, 3, pl, gen, desc, (192, 24, 4, 31)
     if name == "cfg1":
@@ -391,9 +394,13 @@ def run_micro(args):
     with ClockSampler(0) as clk:
         for s in range(nsteps):
             flush.zero_()
+            if s >= args.warmup:
+                torch.cuda.nvtx.range_push("timed_step")
             ev[s][0].record(stream)
             z = op()
             ev[s][1].record(stream)
+            if s >= args.warmup:
+                torch.cuda.nvtx.range_pop()
             del z
         torch.cuda.synchronize()
     ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
@@ -489,8 +496,13 @@ def main():
     he.profile_enable(-1)
     peak, peak_kind = measured_peaks()
     achieved = (bytes_dom / n_dom) / (ms_dom / n_dom * 1e-3) / 1e9 if n_dom else 0.0
+    # DRAM bytes per launch of the dominant class, from ncu counters at N=2^16
+    # (profiles/kernels_rotation_n65536.md), scaled by the limbs a launch moves
+    traffic = None
+    if dom in NTT_DRAM_PER_LIMB and log_n == 16 and n_dom:
+        traffic = NTT_DRAM_PER_LIMB[dom] * (bytes_dom / n_dom) / (16.0 * (1 << log_n))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": PROF_NAMES[dom], "launches": n_dom,
+                "traffic": traffic, "kernel": PROF_NAMES[dom], "launches": n_dom,
                 "avg_launch_us": 1000.0 * ms_dom / max(n_dom, 1),
                 "algorithmic_bytes_per_launch": bytes_dom / max(n_dom, 1),
                 "share_of_step": (ms_dom / args.steps) / ms if ms else None, "peak_source": peak_kind,
