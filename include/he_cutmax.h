@@ -239,7 +239,11 @@ int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out)
  * into one ciphertext (slot i carries stream i mod S', S' = S rounded up to a
  * power of two, S' <= N/4), and are handed back to the streams by a slot mask
  * and a log2(S')-step rotate-and-sum; engineering beyond the paper, which
- * evaluates one stream at a time. */
+ * evaluates one stream at a time.
+ * learned: NULL, or [T][3] coefficients {A, B, C} of learned quadratics
+ * (he_learn_invsqrt); at an iteration with k[t] = 0 the inverse square root is
+ * h = (A x^2 + B x + C) / 2 of x = kappa V (two levels after x) instead of the
+ * Goldschmidt iteration.  k[t] = 0 without `learned` is HE_ERANGE. */
 typedef struct {
     uint32_t n, packing, T;
     const uint32_t *power;
@@ -253,7 +257,20 @@ typedef struct {
     int32_t bootstrap;
     uint32_t cts;
     uint32_t shared;
+    const double *learned;
 } he_cutmax_plan;
+
+/* Learned inverse-square-root stand-in (engineering on top of Sect. 3.2,
+ * whose inverse square root is the generic approximation of App. B): trains
+ * a 1 -> 16 -> 1 network with square activations in FP32 on the GPU
+ * (full-batch Adam, `steps` steps from rate lr decayed by a half cosine,
+ * initial weights from seed) to
+ * minimise mean (f(x) sqrt(x) - 1)^2 over the n host values x (> 0, the
+ * range-scaled variances kappa V of the circuit), and returns its quadratic
+ * form abc = {A, B, C}: f(x) = A x^2 + B x + C; loss (may be NULL) is the final
+ * mean squared relative error.  HE_ERANGE for a non-positive x. */
+int he_learn_invsqrt(he_ctx *ctx, const float *x, size_t n, uint32_t steps, float lr, uint64_t seed,
+                     double *abc, double *loss);
 
 /* Generate every key the plan needs (rotations 2^i, relinearisation and,
  * with bootstrapping, its rotations and conjugation). */

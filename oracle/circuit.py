@@ -128,6 +128,17 @@ def invsqrt_goldschmidt(he, V, kappa, y0, k):
     return h
 
 
+def learned_half(he, x, abc):
+    """(A x^2 + B x + C)/2: the learned inverse square root, two levels."""
+    A, B, C = abc
+    t2 = he.mcr_bits(he.mul_rescale(x, x), A / 2.0, None, 24)
+    t1 = he.mcr_bits(x, B / 2.0, None, 24)
+    l = min(t2.level, t1.level)
+    t2 = he.ctx.drop(t2, l) if t2.level > l else t2
+    t1 = he.ctx.drop(t1, l) if t1.level > l else t1
+    return he.add_const(he.ctx.add(t2, t1), C / 2.0)
+
+
 def inverse_goldschmidt(he, S, kappa_f, d):
     """F ~ 1/(kappa_f S) by prod_{i<=d}(1 + (1 - kappa_f S)^(2^i)); d + 2 levels."""
     a = he.add_const(he.mcr(S, -kappa_f), 1.0)
@@ -172,7 +183,10 @@ def cutmax_he(he, ct, plan, bootstrap=None):
         V = he.rotsum(_vsum(ctx, Es), steps)
         if m:
             V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
-        h = invsqrt_goldschmidt(he, V, plan.kappa[t], plan.y0[t], plan.k[t])
+        if plan.k[t]:
+            h = invsqrt_goldschmidt(he, V, plan.kappa[t], plan.y0[t], plan.k[t])
+        else:
+            h = learned_half(he, he.mcr_bits(V, plan.kappa[t], None, 30), plan.lq[t])
         coef = 2.0 * math.sqrt(plan.kappa[t] * n) / plan.c[t]
         new = []
         for c, D in enumerate(Ds):
@@ -231,6 +245,13 @@ def cutmax_he_boot(he, ct, plan, boot):
         x = ensure(he.mcr_bits(V, kap, None, 30), 2)
         coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
         Dp = he.mcr(he.mul_plain_rescale(D, mask), coef) if m else he.mcr(D, coef)
+        if k == 0:
+            h, Dp = ensure(learned_half(he, x, plan.lq[t]), 1), ensure(Dp, 1)
+            u = he.mul_rescale(Dp, h)
+            u = he.add_plain_vec(u, rn * mask) if m else he.add_const(u, rn)
+            u = ensure(u, (p - 1).bit_length())
+            Y = he.power(u, p)
+            continue
         # Goldschmidt pair packed in one ciphertext: slots [0, s/2) hold g,
         # slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
         half = plan.slots // 2

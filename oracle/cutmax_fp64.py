@@ -132,7 +132,11 @@ def cutmax_circuit(x, plan, return_trace=False):
         trace["V"].append(V)
         kap, y0, k = plan.kappa[t], plan.y0[t], plan.k[t]
         rn = plan.norm[t] ** (1.0 / plan.p[t]) if boot else 1.0
-        if boot:                      # bootstrapped circuit: x = kappa V first
+        if k == 0:                    # learned quadratic (A x^2 + B x + C)/2 of x = kappa V
+            A, B, C = plan.lq[t]
+            xx = kap * V
+            h = (A * xx * xx + B * xx + C) / 2.0
+        elif boot:                    # bootstrapped circuit: x = kappa V first
             xx = kap * V
             a = 1.5 - (y0 * y0 / 2.0) * xx
             h = (y0 / 2.0) * a
@@ -141,7 +145,7 @@ def cutmax_circuit(x, plan, return_trace=False):
             a = 1.5 - (kap * y0 * y0 / 2.0) * V
             h = (y0 / 2.0) * a
             g = (kap * y0 * V) * a
-        for i in range(2, k + 1):
+        for i in range(2, k + 1) if k else ():
             a = 1.5 - g * h
             if i < k:
                 g = g * a

@@ -1,4 +1,5 @@
 // extern "C" entry points declared in include/he_cutmax.h.
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -427,6 +428,16 @@ int he_bootstrap_stage(he_ctx *cx, const he_ct *in, int32_t stage, he_ct **out) 
     Ct r = bootstrap_stage(cx, in, stage);
     launched(cx, "bootstrap stage");
     *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_learn_invsqrt(he_ctx *cx, const float *x, size_t n, uint32_t steps, float lr, uint64_t seed, double *abc,
+                     double *loss) {
+    if (!cx || !x || !abc) return HE_EINVAL;
+    API_TRY
+    need(lr > 0.f && std::isfinite(lr), "learning rate must be positive");
+    learn_invsqrt(cx, x, n, (int)steps, lr, seed, abc, loss);
+    launched(cx, "invsqrt training");
     API_CATCH(cx)
 }
 

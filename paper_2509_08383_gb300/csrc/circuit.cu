@@ -57,6 +57,12 @@ struct HE {
     }
     Ct add_const(const he_ct *ct, double c) { return op_add_intd(cx, ct, std::rint(c * ct->scale)); }
     Ct neg(const he_ct *ct) { return op_mul_int(cx, ct, -1); }
+    // learned inverse square root: (A x^2 + B x + C) / 2, two levels
+    Ct learned_half(const he_ct *x, const double *abc) {
+        Ct x2 = mul_rescale(x, x);
+        Ct t2 = mcr_bits(x2.get(), abc[0] / 2.0, -1, 24), t1 = mcr_bits(x, abc[1] / 2.0, -1, 24);
+        return add_const(op_add(cx, t2.get(), t1.get(), false).get(), abc[2] / 2.0);
+    }
     Ct mul_rescale(const he_ct *a, const he_ct *b) {
         Ct t = op_mul(cx, a, b);
         return op_rescale(cx, t.get());
@@ -143,8 +149,12 @@ Plan plan_from(const he_cutmax_plan *p) {
     pl.packing = (int)p->packing;
     pl.T = (int)p->T;
     for (uint32_t t = 0; t < p->T; t++) {
-        if (p->power[t] < 1 || p->k[t] < 1 || !(p->c[t] > 0) || !(p->kappa[t] > 0) || !(p->y0[t] > 0))
+        if (p->power[t] < 1 || (p->k[t] < 1 && !p->learned) || !(p->c[t] > 0) || !(p->kappa[t] > 0) ||
+            !(p->y0[t] > 0))
             throw Error{HE_ERANGE, "plan constants out of range"};
+        if (p->k[t] == 0)
+            for (int i = 0; i < 3; i++)
+                if (!std::isfinite(p->learned[3 * t + i])) throw Error{HE_ERANGE, "learned coefficients must be finite"};
         pl.p.push_back((int)p->power[t]);
         pl.c.push_back(p->c[t]);
         pl.k.push_back((int)p->k[t]);
@@ -157,6 +167,7 @@ Plan plan_from(const he_cutmax_plan *p) {
     pl.bootstrap = p->bootstrap != 0;
     pl.cps = p->cts ? (int)p->cts : 1;
     pl.shared = p->shared != 0;
+    if (p->learned) pl.lq.assign(p->learned, p->learned + 3 * p->T);
     if (pl.cps > 64) throw Error{HE_EINVAL, "more than 64 ciphertexts per stream"};
     pl.d = (int)p->d;
     pl.kappa_f = p->kappa_f;
@@ -228,7 +239,7 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
     if (pl.bootstrap) return cutmax_boot(cx, in, pl);
     StreamShape sh = stream_shape(cx, in, pl);
     int depth = pl.d + 3;
-    for (int t = 0; t < pl.T; t++) depth += 2 + 2 * pl.k[t] + power_depth(pl.p[t]);
+    for (int t = 0; t < pl.T; t++) depth += 2 + (pl.k[t] ? 2 * pl.k[t] : 5) + power_depth(pl.p[t]);
     if (depth > in->level) throw Error{HE_ELEVEL, "circuit depth " + std::to_string(depth) + " exceeds level " +
                                                    std::to_string(in->level)};
     HE he{cx, cx->delta};
@@ -245,7 +256,11 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
             Ct S2 = he.mul_rescale(S.get(), S.get());
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
         }
-        Ct h = stream_bcast(cx, invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t]).get(), cps);
+        Ct h = stream_bcast(cx,
+                            (pl.k[t] ? invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t])
+                                     : he.learned_half(he.mcr_bits(V.get(), pl.kappa[t], -1, 30).get(), &pl.lq[3 * t]))
+                                .get(),
+                            cps);
         double coef = 2.0 * std::sqrt(pl.kappa[t] * pl.n) / pl.c[t];
         // D' = D * coef (times the 0/1 slot mask when padded): the mask is a
         // plaintext of O(1) slot values and coef (~1e-5 for tens of thousands of
@@ -849,6 +864,11 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         } else {
             Dp = he.mcr(D.get(), coef);
         }
+        Ct h;
+        if (k == 0) {  // learned quadratic in place of the Goldschmidt iteration
+            h = he.learned_half(x.get(), &pl.lq[3 * t]);
+            if (shared) h = unpack(ensure(std::move(h), 1).get());
+        } else {
         std::vector<double> vlo(slots, 0.0), vhi(slots, 0.0);
         for (int i = 0; i < half; i++) vlo[i] = y0;
         for (int i = half; i < slots; i++) vhi[i] = y0 / 2.0;
@@ -870,8 +890,9 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         P = ensure(std::move(P), 1);
         for (int i = 0; i < slots; i++) vhi[i] = i < half ? 0.0 : 1.0;
         Ct hm = he.mul_plain_rescale(P.get(), upload_scaled(cx, sv, vhi, 1.0), slots);
-        Ct h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
+        h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
         if (shared) h = unpack(ensure(std::move(h), 1).get());
+        }
         h = ensure(std::move(h), 1);
         Dp = ensure(std::move(Dp), 1);
         Ct u = he.mul_rescale(Dp.get(), stream_bcast(cx, h.get(), cps).get());

@@ -174,6 +174,7 @@ struct Plan {
     bool bootstrap;
     int cps = 1;  // ciphertexts per stream
     bool shared = false;  // batched streams share the scalar chains (see he_cutmax_plan)
+    std::vector<double> lq;  // [T][3] learned quadratics (used where k[t] == 0)
     int pad(int slots) const;
 };
 Plan plan_from(const he_cutmax_plan *p);
@@ -182,6 +183,12 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl);
 void boot_prepare(he_ctx *cx, int K, int r, int d);
 Ct bootstrap_ct(he_ctx *cx, const he_ct *in);
 Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage);
+
+// learned inverse-square-root stand-in (learn.cu): trains the 1 -> 16 -> 1
+// square-activation network on host variances x (> 0) and returns its
+// quadratic form A x^2 + B x + C
+void learn_invsqrt(he_ctx *cx, const float *x_host, size_t n, int steps, float lr, u64 seed, double *abc,
+                   double *loss);
 
 void check_cuda(cudaError_t e, const char *what);
 void release_slot(int slot);

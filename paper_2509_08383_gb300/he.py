@@ -36,7 +36,7 @@ class CPlan(C.Structure):
                 ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_uint32)), ("kappa", C.POINTER(C.c_double)),
                 ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double),
                 ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32), ("cts", C.c_uint32),
-                ("shared", C.c_uint32)]
+                ("shared", C.c_uint32), ("learned", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -100,6 +100,7 @@ def lib():
             "he_bootstrap": [VP, VP, PP],
             "he_bootstrap_stage": [VP, VP, i32, PP],
             "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
+            "he_learn_invsqrt": [VP, C.POINTER(C.c_float), sz, u32, C.c_float, u64, pd, pd],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
             "nucleus_sample": [VP, VP, VP, C.POINTER(CPlan), PP],
         }
@@ -184,10 +185,13 @@ def plan_struct(plan):
     norm = list(plan.norm) if getattr(plan, "norm", None) is not None else [1.0] * T
     arrs = dict(power=(C.c_uint32 * T)(*plan.p), c=(C.c_double * T)(*plan.c), k=(C.c_uint32 * T)(*plan.k),
                 kappa=(C.c_double * T)(*plan.kappa), y0=(C.c_double * T)(*plan.y0), norm=(C.c_double * T)(*norm))
+    lq = getattr(plan, "lq", None)
+    arrs["learned"] = (C.c_double * (3 * T))(*[float(v) for row in lq for v in row]) if lq else None
     s = CPlan(n=plan.n, packing=0 if plan.packing == "replicate" else 1, T=T, power=arrs["power"], c=arrs["c"],
               k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f,
               norm=arrs["norm"], bootstrap=int(bool(getattr(plan, "bootstrap", False))),
-              cts=int(getattr(plan, "cts", 1)), shared=int(bool(getattr(plan, "shared", False))))
+              cts=int(getattr(plan, "cts", 1)), shared=int(bool(getattr(plan, "shared", False))),
+              learned=arrs["learned"])
     return s, arrs
 
 
@@ -383,6 +387,16 @@ class Context:
 
     def bootstrap_stage(self, ct, stage):
         return self._ct(lib().he_bootstrap_stage, ct.ptr, int(stage))
+
+    def learn_invsqrt(self, xs, steps=3000, lr=1e-2, seed=0):
+        """Train the learned inverse-square-root network on the GPU (FP32): returns
+        ([A, B, C], final mean squared relative error) of f(x) = A x^2 + B x + C ~ 1/sqrt(x)."""
+        x = np.ascontiguousarray(xs, dtype=np.float32)
+        abc = np.zeros(3)
+        loss = C.c_double()
+        self._chk(lib().he_learn_invsqrt(self.ptr, x.ctypes.data_as(C.POINTER(C.c_float)), x.size, int(steps),
+                                         float(lr), int(seed), _dptr(abc), C.byref(loss)))
+        return [float(v) for v in abc], float(loss.value)
 
     # CutMax / nucleus
     def cutmax_prepare(self, plan):

@@ -194,6 +194,13 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
         if plan.bootstrap:
             x = ensure(mcr_bits(V, plan.kappa[t]), 2)
             Dp = mcr(mcr(D)) if m else mcr(D)
+            if k == 0:                        # learned quadratic: x^2, then constants
+                h = mcr(sim.mul(x, x))
+                h, Dp = ensure(h, 1), ensure(Dp, 1)
+                u = sim.mul(Dp, h)
+                u = ensure(u, (p - 1).bit_length())
+                Y = power(u, p)
+                continue
             a = mcr(x)
             P = sim.mul(mcr(x), a)            # packed [g | h]
             for i in range(2, k + 1):
@@ -207,6 +214,10 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
             h, Dp = ensure(h, 1), ensure(Dp, 1)
             u = sim.mul(Dp, h)
             u = ensure(u, (p - 1).bit_length())
+        elif k == 0:
+            h = mcr(sim.mul(mcr_bits(V, plan.kappa[t]), mcr_bits(V, plan.kappa[t])))
+            Dp = mcr(mcr(D)) if m else mcr(D)
+            u = sim.mul(Dp, h)
         else:
             a = mcr(V)
             h = mcr(a)

@@ -50,6 +50,7 @@ class CutMaxPlan:
     extra: dict = field(default_factory=dict)
     cts: int = 1                # ciphertexts per stream (n > slots spreads over several)
     shared: bool = False        # batched streams share the scalar chains (bootstrapped plans)
+    lq: List = None             # per iteration [A, B, C] of a learned quadratic (used where k[t] == 0)
 
     def __post_init__(self):
         if self.norm is None:
@@ -65,10 +66,11 @@ class CutMaxPlan:
         return 0 if self.packing == "replicate" else self.cts * self.slots - self.n
 
     def depth(self) -> int:
-        """Levels consumed without bootstrapping (see the circuit description)."""
+        """Levels consumed without bootstrapping (see the circuit description;
+        a learned iteration counts 2 levels for the quadratic and 3 for x)."""
         dep = 0
         for t in range(self.T):
-            dep += 2 + 2 * self.k[t] + power_depth(self.p[t])
+            dep += 2 + (2 * self.k[t] if self.k[t] else 5) + power_depth(self.p[t])
         return dep + self.d + 3
 
     def to_dict(self):
@@ -146,6 +148,15 @@ def _invsqrt_half(x, k, y0):
     return h
 
 
+def invsqrt_half_at(plan_k, plan_y0, lq, t, x):
+    """h of iteration t of the circuit: Goldschmidt (k[t] >= 1) or the learned
+    quadratic (A x^2 + B x + C)/2 (k[t] == 0)."""
+    if plan_k[t] == 0:
+        A, B, C = lq[t]
+        return (A * x * x + B * x + C) / 2.0
+    return _invsqrt_half(x, plan_k[t], plan_y0[t])
+
+
 def _invsqrt_err(x, k, y0):
     return np.abs(2.0 * _invsqrt_half(x, k, y0) * np.sqrt(x) - 1.0).max()
 
@@ -189,14 +200,17 @@ def _power(u, p):
 
 
 def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1e-7,
-              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False, norm_margin=1.25):
+              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False, norm_margin=1.25, learn=None):
     """Pick kappa/y0/k per iteration and kappa_f/d from `n_cal` draws of ``sample(i)``,
     following the circuit's own iterates; with bootstrap=True also the
-    normalisers norm[t] that keep max Y_(t+1) at about 1/norm_margin."""
+    normalisers norm[t] that keep max Y_(t+1) at about 1/norm_margin.
+    learn(t, kappa_t, xs, (a, b)) -> [A, B, C] or None: offered the iteration-t
+    range scale, the inputs x of the calibration draws and the margin range; a
+    quadratic it returns replaces that iteration's Goldschmidt steps (k[t] = 0)."""
     p = [int(v) for v in (p if not np.isscalar(p) else [p] * T)]
     c = [float(v) for v in (c if not np.isscalar(c) else [c] * T)]
     ys = [np.asarray(sample(i), dtype=np.float64).copy() for i in range(n_cal)]
-    kappa, y0s, ks, norms, vr = [], [], [], [], []
+    kappa, y0s, ks, norms, vr, lqs = [], [], [], [], [], []
     for t in range(T):
         Vs, Ds = [], []
         for y in ys:
@@ -214,9 +228,13 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
             k = int(k_fixed if np.isscalar(k_fixed) else k_fixed[t])
         else:
             k, y0 = _fewest_iterations(xs, k_max, tol_k, y0)
+        q = learn(t, kap, kap * Vs, (a * kap, b * kap)) if learn is not None else None
+        lqs.append(list(q) if q is not None else [0.0, 0.0, 0.0])
+        if q is not None:
+            k = 0
         new = []
         for D, V in zip(Ds, Vs):
-            h = _invsqrt_half(kap * V, k, y0)
+            h = invsqrt_half_at([k], [y0], [q], 0, kap * V)
             u = D * (2.0 * math.sqrt(kap * n) / c[t]) * h + 1.0
             new.append(_power(u, p[t]))
         nm = 1.0
@@ -241,5 +259,6 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
                 break
     return CutMaxPlan(n=n, slots=slots, packing=packing_for(n, slots), T=T, p=p, c=c, k=ks,
                       kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap, norm=norms, cts=cts_for(n, slots),
+                      lq=lqs if any(kk == 0 for kk in ks) else None,
                       extra={"V_range": vr, "S_range": [float(Ss.min()), float(Ss.max())], "margin": margin,
                              "n_cal": n_cal})

@@ -36,3 +36,24 @@ def uniforms(seed, n):
     rng = np.random.default_rng([0x5A5A, int(seed)])
     u = rng.random(n)
     return np.clip(u, 2.0 ** -53, 1.0 - 2.0 ** -53)
+
+
+class HeavyTail:
+    """Picklable generator of the full-vocabulary workload: logits_heavy_tail
+    with the top-1 gap cycling through `gaps` by seed."""
+
+    def __init__(self, n=32000, gaps=(0.05, 0.2, 1.0), heavy=50):
+        self.n, self.gaps, self.heavy = int(n), tuple(gaps), int(heavy)
+
+    def __call__(self, seed):
+        return logits_heavy_tail(seed, n=self.n, heavy=self.heavy, gap=self.gaps[int(seed) % len(self.gaps)])
+
+
+class Gaussian:
+    """Picklable generator: logits_gaussian with fixed n, sd and gap."""
+
+    def __init__(self, n=1024, sd=2.0, gap=0.5):
+        self.n, self.sd, self.gap = int(n), float(sd), float(gap)
+
+    def __call__(self, seed):
+        return logits_gaussian(seed, n=self.n, sd=self.sd, gap=self.gap)
