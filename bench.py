@@ -1,6 +1,6 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|mul16|rot16|ntt16|boot16]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|cfg5|mul16|rot16|ntt16|boot16]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
@@ -409,6 +409,114 @@ def run_cfg4(args):
     print(json.dumps(out))
 
 
+def _nucleus_set(x, p):
+    """Smallest top-probability token set with softmax mass >= p."""
+    pr = np.exp(x - x.max())
+    pr /= pr.sum()
+    order = np.argsort(-pr, kind="stable")
+    return set(order[:int(np.searchsorted(np.cumsum(pr[order]), p) + 1)].tolist())
+
+
+def run_cfg5(args):
+    """HE nucleus (top-p) sampling decode loop (Alg. 3): 16 streams of 128,256
+    logits (4 ciphertexts each) at N=2^16, 8 streams at p = 0.9 and 8 at
+    p = 0.95 (one batch per p, alpha = ln(1-p)/ln(p)).  Per token the client
+    encrypts each stream's logits (regenerated from the seed: N(0, 2^2), top
+    gap 0.5) and uniforms U; the server draws G = U^(1/alpha) from them
+    (he_beta_noise) and samples CutMax(X + G) with bootstrapping and shared
+    scalar chains; the client decrypts and takes the argmax as the token.  The
+    plain plan and the learned plan (learned inverse square root) run side by
+    side.  Reported: tokens/s of the server work (CUDA events) and end to end,
+    agreement of the tokens with the FP64 sampler argmax(x + U^(1/alpha)), and
+    tokens outside the top-p nucleus of softmax(x)."""
+    from paper_2509_08383_gb300 import learned
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    n, per, slots, deg = 128256, 8, 1 << 15, 31
+    ps = [0.9, 0.95]
+    alphas = [math.log(1.0 - p) / math.log(p) for p in ps]
+
+    def logits(stream, step):
+        return synth.logits_gaussian(1000003 * (stream + 1) + step, n=n, sd=2.0, gap=0.5)
+
+    gen = synth.Gaussian(n, 2.0, 0.5)
+    # plan on logits plus cut noise (the circuit's input is x + G)
+    calib_kw = dict(sample=lambda i: gen(300000 + i) + synth.uniforms(300000 + i, n) ** (1.0 / alphas[i % 2]),
+                    n_cal=60, n=n, slots=slots, T=4, p=[16, 4, 4, 6], c=[5.0, 3.0, 3.0, 3.0], margin=2.0,
+                    tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True)
+    plain = P.calibrate(**calib_kw)
+    plain.shared = True
+    logged = learned.log_variances(plain, gen, range(500000, 505000))  # spawn pool, before CUDA
+    import torch
+    from paper_2509_08383_gb300 import build, he
+    build.build_library()
+    torch.cuda.set_device(0)
+    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=160 << 30)
+    g.bootstrap_prepare(24, 4, 31)
+    lpl, report = learned.learned_plan(g, plain, calib_kw, logged)
+    lpl.shared = True
+    stream = torch.cuda.current_stream()
+    out_level = None
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, pl in (("plain", plain), ("learned", lpl)):
+            g.cutmax_prepare(pl)
+            t_dev, t_e2e, agree, agree_poly, outside, total = 0.0, 0.0, 0, 0, 0, 0
+            for step in range(args.warmup + args.tokens):
+                timed = step >= args.warmup
+                for b, (p, alpha) in enumerate(zip(ps, alphas)):
+                    t0 = time.perf_counter()
+                    xs, us, cts, uts = [], [], [], []
+                    for sidx in range(per):
+                        st = b * per + sidx
+                        x, u = logits(st, step), synth.uniforms(7000003 * (st + 1) + step, n)
+                        xs.append(x)
+                        us.append(u)
+                        for c, v in enumerate(P.pack_cts(x, slots)):
+                            cts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + c, level=13))
+                        for c, v in enumerate(P.pack_cts(u, slots)):
+                            uts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + 4 + c, level=13))
+                    X, U = g.batch_pack(cts), g.batch_pack(uts)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    Z = g.nucleus_sample(X, g.beta_noise(U, alpha, deg), pl)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    toks = []
+                    for sidx in range(per):
+                        dec = np.concatenate([g.decrypt(g.batch_member(Z, sidx * 4 + c)) for c in range(4)])[:n]
+                        toks.append(int(np.argmax(dec)))
+                    t1 = time.perf_counter()
+                    if timed:
+                        t_dev += e0.elapsed_time(e1) / 1000.0
+                        t_e2e += t1 - t0
+                        th = np.pi * (np.arange(deg + 1) + 0.5) / (deg + 1)
+                        f = ((np.cos(th) + 1) / 2) ** (1 / alpha)
+                        cc = np.array([2 / (deg + 1) * np.sum(f * np.cos(k * th)) for k in range(deg + 1)])
+                        cc[0] /= 2
+                        for x, u, tok in zip(xs, us, toks):
+                            agree += tok == int(np.argmax(x + u ** (1.0 / alpha)))
+                            agree_poly += tok == int(np.argmax(x + np.polynomial.chebyshev.chebval(2 * u - 1, cc)))
+                            outside += tok not in _nucleus_set(x, p)
+                            total += 1
+            res[name] = {"tokens_per_s": total / t_dev, "tokens_per_s_e2e": total / t_e2e,
+                         "ms_per_token_step": 1000.0 * t_dev / args.tokens, "tokens": total,
+                         "agree_fp64_sampler": agree, "agree_fp64_same_noise_polynomial": agree_poly,
+                         "outside_top_p_nucleus": outside, "k": list(pl.k), "levels": pl.depth()}
+    out = {"metric": "encrypted nucleus-sampling tokens/sec, 16 streams x vocab 128,256 (N=2^16), 1 GB300",
+           "value": res["learned"]["tokens_per_s"], "unit": "tokens/s", "n_gpus": 1, "steps": args.tokens,
+           "warmup": args.warmup, "ms_per_step": res["learned"]["ms_per_token_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "Alg. 3 decode loop: 16 streams (8 at top-p 0.9, 8 at 0.95) x 128,256 logits "
+                                  "N(0,4) top gap 0.5 in 4 ciphertexts, G = U^(1/alpha) from encrypted uniforms "
+                                  "(degree-31 Chebyshev), CutMax T=4 p=[16,4,4,6] c=[5,3,3,3], bootstrapping, "
+                                  "shared scalar chains", "tokens": args.tokens, "streams": 2 * per},
+           "plain": res["plain"], "learned": res["learned"],
+           "training": {str(t): {k: v for k, v in r.items() if k != "abc"} for t, r in report.items()},
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def run_micro(args):
     """Micro workloads for kernel profiles at the N=2^16 parameter set (the
     same kernels as a CutMax step at full size): mul16 = one homomorphic
@@ -489,8 +597,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "mul16", "rot16",
-                                                           "ntt16", "boot16"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "mul16",
+                                                           "rot16", "ntt16", "boot16"])
+    ap.add_argument("--tokens", type=int, default=32, help="cfg5: tokens decoded per stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -501,6 +610,8 @@ def main():
         return run_cfg3(args)
     if args.workload == "cfg4":
         return run_cfg4(args)
+    if args.workload == "cfg5":
+        return run_cfg5(args)
 
     import torch
     dist, rank, ws = dist_setup(args)

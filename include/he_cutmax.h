@@ -283,6 +283,14 @@ int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out
 /* Nucleus one-shot sampling (Alg. 3): out = CutMax(logits + rand_ct), where
  * rand_ct encrypts the cut noise G_i = U_i^(1/alpha), alpha = ln(1-q)/ln(p)
  * (Lemma 2 / Observation 1), drawn and encrypted by the client. */
+/* Cut noise drawn by the server from encrypted uniforms (Alg. 3 with
+ * Lemma 2 / Observation 1): out = G = U^(1/alpha) slot by slot, U in [0, 1]
+ * encrypted by the client, by the degree-`degree` Chebyshev interpolant of
+ * ((t+1)/2)^(1/alpha) on t = 2U - 1 (1 + about log2(degree) + 1 levels).
+ * Accurate to ~1e-2 for U >= 1e-3 at degree 31 (alpha ~ 22); the interpolant
+ * cannot follow the cusp of U^(1/alpha) at U = 0.  HE_EINVAL for alpha <= 0 or
+ * degree outside 2..127.  Works on batches. */
+int he_beta_noise(he_ctx *ctx, const he_ct *u, double alpha, uint32_t degree, he_ct **out);
 int nucleus_sample(he_ctx *ctx, const he_ct *logits, const he_ct *rand_ct,
                    const he_cutmax_plan *plan, he_ct **out);
 

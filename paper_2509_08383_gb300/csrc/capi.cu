@@ -464,6 +464,16 @@ int cutmax(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out)
     API_CATCH(cx)
 }
 
+int he_beta_noise(he_ctx *cx, const he_ct *u, double alpha, uint32_t degree, he_ct **out) {
+    if (!cx || !u || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, u);
+    Ct r = beta_noise(cx, u, alpha, (int)degree);
+    launched(cx, "beta noise");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
 int nucleus_sample(he_ctx *cx, const he_ct *logits, const he_ct *rand_ct, const he_cutmax_plan *plan, he_ct **out) {
     if (!cx || !logits || !rand_ct || !out) return HE_EINVAL;
     API_TRY

@@ -634,9 +634,20 @@ struct ChebEval {
     }
 };
 
+// Chebyshev series sum_k c_k T_k(x) of a ciphertext x with slots in [-1, 1]
+// (baby steps T_1..T_(m-1), giants T_m, T_2m, ...), landing on `target`.
+static Ct cheb_series(HE &he, const he_ct *x, const std::vector<double> &cheb, double target);
+
 static Ct evalmod(HE &he, const he_ct *x, const Boot &B) {
+    Ct c = cheb_series(he, x, B.cheb, B.em_scale);
+    for (int i = 0; i < B.r; i++)
+        c = he.add_const(op_mul_int(he.cx, he.mul_rescale(c.get(), c.get()).get(), 2).get(), -1.0);
+    return c;
+}
+
+static Ct cheb_series(HE &he, const he_ct *x, const std::vector<double> &cheb, double target) {
     he_ctx *cx = he.cx;
-    const int d = B.d;
+    const int d = (int)cheb.size() - 1;
     int m = 1;
     while (m * m <= d + 1) m *= 2;  // baby steps T_1..T_(m-1)
     int top = m;
@@ -656,9 +667,31 @@ static Ct evalmod(HE &he, const he_ct *x, const Boot &B) {
     };
     for (int k = 2; k < m; k++) make(k);
     for (int g = m; g <= top; g *= 2) make(g);
-    Ct c = ce.eval(B.cheb, B.em_scale);
-    for (int i = 0; i < B.r; i++) c = he.add_const(op_mul_int(cx, he.mul_rescale(c.get(), c.get()).get(), 2).get(), -1.0);
-    return c;
+    return ce.eval(cheb, target);
+}
+
+// Beta(alpha, 1) cut noise of Alg. 3 from an encrypted uniform (Lemma 2 /
+// Observation 1: G = U^(1/alpha), alpha = ln(1-q)/ln(p)): the degree-d
+// Chebyshev interpolant (Chebyshev nodes) of f(t) = ((t + 1)/2)^(1/alpha) on
+// t = 2U - 1, so that the server draws the noise from the client's uniforms.
+// The interpolant follows U^(1/alpha) to ~1e-2 for U >= 1e-3 at d = 31; it
+// cannot follow the cusp at U = 0.
+Ct beta_noise(he_ctx *cx, const he_ct *u, double alpha, int d) {
+    if (!(alpha > 0) || d < 2 || d > 127) throw Error{HE_EINVAL, "noise needs alpha > 0 and degree 2..127"};
+    HE he{cx, cx->delta};
+    std::vector<double> c(d + 1), fx(d + 1), th(d + 1);
+    for (int j = 0; j <= d; j++) {
+        th[j] = M_PI * (j + 0.5) / (d + 1);
+        fx[j] = std::pow((std::cos(th[j]) + 1.0) / 2.0, 1.0 / alpha);
+    }
+    for (int k = 0; k <= d; k++) {
+        double acc = 0;
+        for (int j = 0; j <= d; j++) acc += fx[j] * std::cos(k * th[j]);
+        c[k] = 2.0 / (d + 1) * acc;
+    }
+    c[0] /= 2;
+    Ct t = he.add_const(he.mcr(u, 2.0).get(), -1.0);
+    return cheb_series(he, t.get(), c, cx->delta);
 }
 
 // Level bookkeeping of evalmod(): the baby-step giant-step series can use

@@ -103,6 +103,7 @@ def lib():
             "he_learn_invsqrt": [VP, C.POINTER(C.c_float), sz, u32, C.c_float, u64, pd, pd],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
             "nucleus_sample": [VP, VP, VP, C.POINTER(CPlan), PP],
+            "he_beta_noise": [VP, VP, dbl, u32, PP],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -406,6 +407,10 @@ class Context:
     def cutmax(self, ct, plan):
         s, keep = plan_struct(plan)
         return self._ct(lib().cutmax, ct.ptr, C.byref(s))
+
+    def beta_noise(self, u_ct, alpha, degree=31):
+        """G = U^(1/alpha) of encrypted uniforms (Chebyshev interpolant)."""
+        return self._ct(lib().he_beta_noise, u_ct.ptr, float(alpha), int(degree))
 
     def nucleus_sample(self, ct, rand_ct, plan):
         s, keep = plan_struct(plan)

@@ -111,3 +111,28 @@ def test_bootstrapped_learned_plan():
         dec = g.decrypt(z, nv)
         assert np.abs(dec - F.cutmax_circuit(x, lpl)).max() < 1e-3, s
         assert int(np.argmax(dec)) == int(np.argmax(x))
+
+
+@pytest.mark.parametrize("alpha", [21.85, 58.4])
+def test_beta_noise_from_encrypted_uniforms(alpha):
+    """G = U^(1/alpha) (Lemma 2 / Observation 1) from encrypted uniforms: the
+    GPU evaluates the degree-31 Chebyshev interpolant at Chebyshev nodes; its
+    values match the same series in FP64 (CKKS noise) and U^(1/alpha) within
+    the interpolation error for U >= 1e-2."""
+    g = he.Context(LOG_N, [60] + [40] * 12, [60, 60], dnum=13, seed=17)
+    g.gen_relin_key()
+    d = 31
+    u = synth.uniforms(4, SLOTS)
+    G = g.decrypt(g.beta_noise(g.encrypt(u, DELTA, 7), alpha, d))
+    th = np.pi * (np.arange(d + 1) + 0.5) / (d + 1)
+    f = ((np.cos(th) + 1) / 2) ** (1 / alpha)
+    c = np.array([2 / (d + 1) * np.sum(f * np.cos(k * th)) for k in range(d + 1)])
+    c[0] /= 2
+    series = np.polynomial.chebyshev.chebval(2 * u - 1, c)
+    assert np.abs(G - series).max() < 1e-4
+    big = u >= 1e-2
+    bound = float(np.abs(np.polynomial.chebyshev.chebval(2 * np.linspace(1e-2, 1, 100001) - 1, c)
+                         - np.linspace(1e-2, 1, 100001) ** (1 / alpha)).max())
+    assert np.abs(G[big] - u[big] ** (1 / alpha)).max() < bound + 1e-4
+    with pytest.raises(he.HeError):
+        g.beta_noise(g.encrypt(u, DELTA, 8), -1.0)
