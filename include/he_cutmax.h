@@ -169,6 +169,10 @@ int he_drop(he_ctx *ctx, const he_ct *a, uint32_t level, he_ct **out);
 int he_rotate(he_ctx *ctx, const he_ct *a, int32_t r, he_ct **out);
 int he_conjugate(he_ctx *ctx, const he_ct *a, he_ct **out);
 int he_automorphism(he_ctx *ctx, const he_ct *a, uint64_t g, he_ct **out);
+/* multiplication by the monomial X^e (e taken mod 2N; X^N = -1), exact and
+ * without a key: X^(N/2) is i in every slot, so e = N/2 multiplies the
+ * message by i and e = 3N/2 by -i */
+int he_mul_monomial(he_ctx *ctx, const he_ct *a, uint64_t e, he_ct **out);
 /* rotate-and-sum over 2^steps consecutive slots (App. D): log2 rotations */
 int he_rotsum(he_ctx *ctx, const he_ct *a, uint32_t steps, he_ct **out);
 /* Hybrid key switch of a raw polynomial: host d[(level+1)*N] coefficient
@@ -215,6 +219,18 @@ int he_bootstrap(he_ctx *ctx, const he_ct *in, he_ct **out);
  * real / imaginary part, 6 / 7 those after EvalMod, 8 recombined, 9 / 10 after
  * the first two SlotToCoeff levels, 11 the result. */
 int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out);
+/* Refresh a ciphertext whose slots all hold one complex value a + i b (the
+ * plaintext polynomial a + b X^(N/2), e.g. a scalar of the CutMax circuit),
+ * at about half the cost of he_bootstrap: after ModRaise, the trace over the
+ * automorphisms X -> X^(5^k) (a log2(N/2)-step rotate-and-sum with the
+ * rotation keys of 1, 2, ..., N/4, which he_cutmax_prepare of a bootstrapped
+ * plan generates) keeps the coefficients of 1 and X^(N/2) only; both go
+ * through one EvalMod, packed into the two halves of the slots.  Output at
+ * he_bootstrap's output level.  Slots that do not hold one common value come
+ * out as their average (the trace is a projection): the result is then not
+ * the input's message, and no error is raised.  HE_EINVAL without
+ * he_bootstrap_prepare; HE_EKEY (or the missing-key error) without the keys. */
+int he_bootstrap_const(he_ctx *ctx, const he_ct *in, he_ct **out);
 
 /* ---- CutMax (Alg. 2) and nucleus sampling (Alg. 3) ------------------- */
 /* Circuit plan: the range-scaling constants of Sect. 3.2's obligations.
@@ -231,7 +247,8 @@ int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out)
  * any phase that needs more levels than it has (Y before the statistics: 5,
  * since V = sum (n y - S)^2 is scaled to x = kappa V by up to 3 rescales that
  * keep a 30-bit multiplier, and V itself is too large to refresh;
- * x: 2; g and h between Goldschmidt steps: 2; D' and h: 1; u before the
+ * x: 2; the Goldschmidt pair z = g + i h, one complex constant refreshed
+ * by he_bootstrap_const, between steps: 2; D' and h: 1; u before the
  * power: ceil(log2 p); Y before the final normalisation: d + 3).
  * shared != 0 (bootstrapped plans, batches of S > 1 streams): the per-stream
  * scalar chains (the Goldschmidt inverse square root and the final inverse,

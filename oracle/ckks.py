@@ -59,6 +59,7 @@ def lib():
             "or_add_plain": (vp, [vp, vp, pdbl]),
             "or_mul_plain": (vp, [vp, vp, pdbl, dbl]),
             "or_keyswitch": (ip, [vp, pu64, ip, u64, pu64, pu64]),
+            "or_moddown": (None, [vp, pu64, pu64, ip, pu64, pu64]),
             "or_mul": (vp, [vp, vp, vp]),
             "or_rescale": (vp, [vp, vp]),
             "or_automorphism": (vp, [vp, vp, u64]),
@@ -294,6 +295,17 @@ class Context:
 
     def mul_monomial(self, a, e):
         return Ciphertext(self, lib().or_mul_monomial(self.ptr, a.ptr, int(e)))
+
+    def moddown(self, acc0, acc1, level):
+        """round(acc / P) mod q_0..q_level of two polynomials given over
+        q_0..q_level, p_0..p_(K-1) ([(level+1+K)][N] residues each)."""
+        a0 = np.ascontiguousarray(acc0, dtype=np.uint64).reshape(-1)
+        a1 = np.ascontiguousarray(acc1, dtype=np.uint64).reshape(-1)
+        assert a0.size == a1.size == (level + 1 + self.np_) * self.n
+        o0 = np.zeros((level + 1) * self.n, dtype=np.uint64)
+        o1 = np.zeros_like(o0)
+        lib().or_moddown(self.ptr, a0, a1, level, o0, o1)
+        return o0.reshape(level + 1, self.n), o1.reshape(level + 1, self.n)
 
     def keyswitch(self, d, level, g):
         d = np.ascontiguousarray(d, dtype=np.uint64).reshape(-1)

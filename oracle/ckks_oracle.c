@@ -680,12 +680,10 @@ or_ct *or_mul_plain(or_ctx *cx, const or_ct *a, const double *pt, double scale_o
     return r;
 }
 
-/* Hybrid key switching of the coefficient-form polynomial d at level l.
- * ModUp per digit by the approximate basis conversion
- *   [x]_t = sum_{i in D_j} [x_i * (Qhat_i)^-1]_{q_i} * Qhat_i  mod t,
- * inner product with the key over Q_l u P, then ModDown
- *   out_i = (acc_i - [acc_P]_{q_i}) * P^-1 mod q_i
- * with the same conversion from P to q_i. */
+/* ModUp of one digit: the approximate basis conversion
+ *   [x]_t = sum_{i in D_j} [x_i * (Qhat_i)^-1]_{q_i} * Qhat_i  mod t
+ * (its overflow, a small multiple of the digit modulus, is divided away by
+ * P with the key's error), then the product with the key, accumulated. */
 typedef struct {
     or_ctx *cx; const u64 *d; const or_key *key; int j, lo, hi, cnt; const u64 *qhinv; const int *pidx;
     u64 *acc0, *acc1;
@@ -731,39 +729,98 @@ static void it_body(void *vp, int t) {
     u64 *p = (t < A->ext ? A->acc0 + (u64)t * A->cx->n : A->acc1 + (u64)(t - A->ext) * A->cx->n);
     poly_intt(A->cx, p, A->pidx[t % A->ext]);
 }
-typedef struct { or_ctx *cx; const u64 *acc0, *acc1; u64 *out0, *out1; int l, K; const u64 *phinv; } md_args;
+/* ModDown is the rounded division out = round(acc / P) mod q_i.  For every
+ * coefficient x (known mod P by its residues), Garner's algorithm gives the
+ * mixed-radix digits x mod P = m_0 + m_1 p_0 + m_2 p_0 p_1 + ... (m_k < p_k);
+ * comparing them, most significant first, with the digits of (P-1)/2 picks
+ * the centred representative x_c = x mod P, or that minus P; then
+ *   out_i = (acc_i - x_c) * P^-1 mod q_i,
+ * exact, with x_c reduced mod q_i from its digits. */
+typedef struct {
+    or_ctx *cx; const u64 *acc0, *acc1; int l, K, chunk; u64 *dig0, *dig1; unsigned char *hi0, *hi1;
+    const u64 *pjinv, *hdig;
+} gd_args;
+static void gd_body(void *vp, int job) {
+    gd_args *A = (gd_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K, l = A->l;
+    int nch = (int)((n + A->chunk - 1) / A->chunk), w = job / nch;
+    u64 c0 = (u64)(job % nch) * A->chunk, c1 = c0 + A->chunk < n ? c0 + A->chunk : n;
+    const u64 *acc = w ? A->acc1 : A->acc0;
+    u64 *dig = w ? A->dig1 : A->dig0;
+    unsigned char *hi = w ? A->hi1 : A->hi0;
+    for (u64 c = c0; c < c1; c++) {
+        for (int k = 0; k < K; k++) {
+            u64 pk = cx->primes[cx->nq + k], t = acc[(u64)(l + 1 + k) * n + c];
+            for (int j = 0; j < k; j++) t = mulmod(submod(t, dig[(u64)j * n + c] % pk, pk), A->pjinv[j * K + k], pk);
+            dig[(u64)k * n + c] = t;
+        }
+        int above = 0;
+        for (int k = K - 1; k >= 0; k--) {
+            u64 m = dig[(u64)k * n + c];
+            if (m != A->hdig[k]) { above = m > A->hdig[k]; break; }
+        }
+        hi[c] = (unsigned char)above;
+    }
+}
+typedef struct {
+    or_ctx *cx; const u64 *acc0, *acc1; u64 *out0, *out1; int l, K; const u64 *dig0, *dig1;
+    const unsigned char *hi0, *hi1;
+} md_args;
 static void md_body(void *vp, int i) {
     md_args *A = (md_args *)vp;
-    or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K, l = A->l;
-    u64 qi = cx->primes[i], pinv = 1, *ph = malloc(8 * K);
-    for (int a = 0; a < K; a++) pinv = mulmod(pinv, cx->primes[cx->nq + a] % qi, qi);
-    pinv = or_invmod(pinv, qi);
-    for (int a = 0; a < K; a++) {
-        u64 v = 1;
-        for (int b = 0; b < K; b++) if (b != a) v = mulmod(v, cx->primes[cx->nq + b] % qi, qi);
-        ph[a] = v;
+    or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K;
+    u64 qi = cx->primes[i], pm = 1, *radix = malloc(8 * K);
+    for (int a = 0; a < K; a++) {  /* radix[a] = p_0 ... p_(a-1) mod q_i */
+        radix[a] = pm;
+        pm = mulmod(pm, cx->primes[cx->nq + a] % qi, qi);
     }
+    u64 pinv = or_invmod(pm, qi);
     for (int w = 0; w < 2; w++) {
-        const u64 *acc = w ? A->acc1 : A->acc0; u64 *out = w ? A->out1 : A->out0;
+        const u64 *acc = w ? A->acc1 : A->acc0, *dig = w ? A->dig1 : A->dig0;
+        const unsigned char *hi = w ? A->hi1 : A->hi0;
+        u64 *out = w ? A->out1 : A->out0;
         for (u64 c = 0; c < n; c++) {
-            u64 s = 0;
-            for (int a = 0; a < K; a++) {
-                u64 pa = cx->primes[cx->nq + a];
-                u64 y = mulmod(acc[(u64)(l + 1 + a) * n + c], A->phinv[a], pa);
-                s = addmod(s, mulmod(y % qi, ph[a], qi), qi);
-            }
-            out[(u64)i * n + c] = mulmod(submod(acc[(u64)i * n + c], s, qi), pinv, qi);
+            u64 xc = 0;
+            for (int a = 0; a < K; a++) xc = addmod(xc, mulmod(dig[(u64)a * n + c] % qi, radix[a], qi), qi);
+            if (hi[c]) xc = submod(xc, pm, qi);
+            out[(u64)i * n + c] = mulmod(submod(acc[(u64)i * n + c], xc, qi), pinv, qi);
         }
     }
-    free(ph);
+    free(radix);
+}
+
+/* mixed-radix digits of (P-1)/2 (residues (p_k - 1)/2) and p_j^-1 mod p_k */
+static void moddown_consts(or_ctx *cx, int K, u64 *pjinv, u64 *hdig) {
+    for (int j = 0; j < K; j++)
+        for (int k = 0; k < K; k++) {
+            u64 pk = cx->primes[cx->nq + k];
+            pjinv[j * K + k] = j == k ? 0 : or_invmod(cx->primes[cx->nq + j] % pk, pk);
+        }
+    for (int k = 0; k < K; k++) {
+        u64 pk = cx->primes[cx->nq + k], t = (pk - 1) / 2;
+        for (int j = 0; j < k; j++) t = mulmod(submod(t, hdig[j] % pk, pk), pjinv[j * K + k], pk);
+        hdig[k] = t;
+    }
+}
+
+static void moddown_exact(or_ctx *cx, const u64 *acc0, const u64 *acc1, int l, u64 *out0, u64 *out1) {
+    u64 n = cx->n; int K = cx->np, chunk = 1024;
+    u64 *pjinv = malloc(8 * K * K), *hdig = malloc(8 * K);
+    moddown_consts(cx, K, pjinv, hdig);
+    u64 *dig0 = malloc((u64)K * n * 8), *dig1 = malloc((u64)K * n * 8);
+    unsigned char *hi0 = malloc(n), *hi1 = malloc(n);
+    gd_args G = {cx, acc0, acc1, l, K, chunk, dig0, dig1, hi0, hi1, pjinv, hdig};
+    parallel_for(2 * (int)((n + chunk - 1) / chunk), gd_body, &G);
+    md_args M = {cx, acc0, acc1, out0, out1, l, K, dig0, dig1, hi0, hi1};
+    parallel_for(l + 1, md_body, &M);
+    free(pjinv); free(hdig); free(dig0); free(dig1); free(hi0); free(hi1);
 }
 
 /* Hybrid key switching of the coefficient-form polynomial d at level l.
  * ModUp per digit by the approximate basis conversion
  *   [x]_t = sum_{i in D_j} [x_i * (Qhat_i)^-1]_{q_i} * Qhat_i  mod t,
- * inner product with the key over Q_l u P, then ModDown
- *   out_i = (acc_i - [acc_P]_{q_i}) * P^-1 mod q_i
- * with the same conversion from P to q_i. */
+ * inner product with the key over Q_l u P, then ModDown, the rounded
+ * division by P (moddown_exact). */
 static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *out0, u64 *out1) {
     u64 n = cx->n; int K = cx->np, ext = l + 1 + K;
     int beta = (l + 1 + cx->alpha - 1) / cx->alpha;
@@ -786,15 +843,14 @@ static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *o
     }
     it_args B = {cx, acc0, acc1, ext, pidx};
     parallel_for(2 * ext, it_body, &B);
-    u64 *phinv = malloc(8 * K);
-    for (int a = 0; a < K; a++) {
-        u64 q = cx->primes[cx->nq + a], v = 1;
-        for (int b = 0; b < K; b++) if (b != a) v = mulmod(v, cx->primes[cx->nq + b] % q, q);
-        phinv[a] = or_invmod(v, q);
-    }
-    md_args M = {cx, acc0, acc1, out0, out1, l, K, phinv};
-    parallel_for(l + 1, md_body, &M);
-    free(phinv); free(acc0); free(acc1); free(pidx);
+    moddown_exact(cx, acc0, acc1, l, out0, out1);
+    free(acc0); free(acc1); free(pidx);
+}
+
+/* ModDown exposed for tests: acc0/acc1 coefficient form over q_0..q_l then
+ * p_0..p_(K-1), [(l+1+K)][N] each; out0/out1 [(l+1)][N] */
+void or_moddown(or_ctx *cx, const u64 *acc0, const u64 *acc1, int l, u64 *out0, u64 *out1) {
+    moddown_exact(cx, acc0, acc1, l, out0, out1);
 }
 
 /* key switch exposed for tests: d coefficient form at level l */

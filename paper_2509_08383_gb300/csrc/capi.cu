@@ -334,6 +334,7 @@ UNARY_OP(he_drop(he_ctx *cx, const he_ct *a, uint32_t level, he_ct **out), op_dr
 UNARY_OP(he_rotate(he_ctx *cx, const he_ct *a, int32_t r, he_ct **out), op_automorph(cx, a, rot_galois(cx, r)))
 UNARY_OP(he_conjugate(he_ctx *cx, const he_ct *a, he_ct **out), op_automorph(cx, a, 2 * cx->N() - 1))
 UNARY_OP(he_automorphism(he_ctx *cx, const he_ct *a, uint64_t g, he_ct **out), op_automorph(cx, a, g))
+UNARY_OP(he_mul_monomial(he_ctx *cx, const he_ct *a, uint64_t e, he_ct **out), op_mul_monomial(cx, a, e))
 
 int he_mul_const(he_ctx *cx, const he_ct *a, double c, double target, he_ct **out) {
     if (!cx || !a || !out) return HE_EINVAL;
@@ -427,6 +428,16 @@ int he_bootstrap_stage(he_ctx *cx, const he_ct *in, int32_t stage, he_ct **out) 
     own(cx, in);
     Ct r = bootstrap_stage(cx, in, stage);
     launched(cx, "bootstrap stage");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_bootstrap_const(he_ctx *cx, const he_ct *in, he_ct **out) {
+    if (!cx || !in || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, in);
+    Ct r = bootstrap_const(cx, in);
+    launched(cx, "constant bootstrap");
     *out = r.release();
     API_CATCH(cx)
 }

@@ -78,6 +78,18 @@ struct HE {
         Ct t = op_mul_plain(cx, ct, d_pt, ct->scale * E, n_pt);
         return op_rescale(cx, t.get());
     }
+    // ct + (re + i im) in every slot
+    Ct add_complex_const(const he_ct *ct, double re, double im) {
+        const int slots = cx->n / 2;
+        std::vector<double> v(2 * (size_t)slots);
+        for (int i = 0; i < slots; i++) v[i] = re, v[slots + i] = im;
+        Scratch sc{cx, {}};
+        double *d_v = (double *)sc.get(v.size());
+        check_cuda(cudaMemcpyAsync(d_v, v.data(), v.size() * 8, cudaMemcpyHostToDevice, cx->stream), "constant");
+        double *d_pt = cx->d_dbl + cx->N();
+        encode_dev(cx, d_v, d_v + slots, slots, ct->scale, d_pt);
+        return op_add_plain(cx, ct, d_pt);
+    }
     Ct add_plain_vec(const he_ct *ct, const double *d_vec, int n_slots, int n_pt = 1) {
         Scratch sc{cx, {}};
         double *d_pt = n_pt == 1 ? cx->d_dbl + cx->N() : (double *)sc.get((size_t)n_pt * cx->N());
@@ -183,6 +195,7 @@ static int power_depth(int p) {
 
 void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois) {
     int steps = rotsum_steps(pl, cx->n / 2);
+    if (pl.bootstrap) steps = cx->log_n - 1;  // the constant bootstrap's trace rotates by every 2^i
     for (int i = 0; i < steps; i++) galois.push_back(rot_galois(cx, (i64)1 << i));
     if (pl.bootstrap) galois.push_back(rot_galois(cx, cx->n / 4));  // packed Goldschmidt pair
 }
@@ -825,6 +838,56 @@ Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
     return w;
 }
 
+// Bootstrapping of a ciphertext whose slots all hold one complex value z (the
+// polynomial a + b X^(N/2)), at about half the cost of bootstrap_stage: after
+// ModRaise, t = m + q0 I is projected onto {1, X^(N/2)} by the trace over the
+// automorphisms X -> X^(5^k) (a log2(N/2)-step rotate-and-sum, exact: every
+// other monomial's orbit sums to 0) instead of CoeffToSlot; its two
+// coefficients, scaled, become the real and the imaginary part of every
+// slot, are packed into the two slot halves for one EvalMod, and are put
+// back as a complex constant, in place of the second EvalMod and of
+// SlotToCoeff.  Returns the refreshed ciphertext at the bootstrap output level.
+Ct bootstrap_const(he_ctx *cx, const he_ct *in) {
+    auto B = cx->boot_state;
+    if (!B) throw Error{HE_EINVAL, "bootstrapping not prepared"};
+    HE he{cx, B->em_scale};
+    cx->n_boot += (uint64_t)in->batch;
+    const u64 q0 = cx->primes[0];
+    const int slots = cx->n / 2, half = slots / 2;
+    const double ratio = in->scale / B->s_fix;
+    Ct low = in->level ? op_drop(cx, in, 0) : op_copy(cx, in);
+    // raised to 2 levels below the top, so that the packing mask lands the
+    // EvalMod input on the level (and scale) where bootstrap_stage has it
+    Ct x = op_mod_raise(cx, low.get(), cx->nq - 3);
+    x->scale = (double)q0 * (double)(B->K + 1);
+    for (int st = 1; st < slots; st *= 2)  // trace: N/2 (t_0 + t_(N/2) X^(N/2))
+        x = op_add(cx, x.get(), op_automorph(cx, x.get(), rot_galois(cx, st)).get(), false);
+    x->scale *= (double)slots;
+    // slots read (t_0 + i t_(N/2)) / (q0 (K+1)): real and imaginary parts, packed
+    Ct xc = op_automorph(cx, x.get(), 2 * cx->N() - 1);
+    Ct re = op_add(cx, x.get(), xc.get(), false);
+    re->scale *= 2;
+    Ct im = op_mul_monomial(cx, op_add(cx, x.get(), xc.get(), true).get(), 3 * cx->N() / 2);
+    im->scale *= 2;
+    std::vector<double> lo(slots, 0.0), hi(slots, 0.0);
+    for (int i = 0; i < half; i++) lo[i] = 1.0, hi[half + i] = 1.0;
+    Scratch sc{cx, {}};
+    const double *d_lo = upload_scaled(cx, sc, lo, 1.0), *d_hi = upload_scaled(cx, sc, hi, 1.0);
+    Ct y = op_add(cx, he.mul_plain_rescale(re.get(), d_lo, slots, B->em_scale).get(),
+                  he.mul_plain_rescale(im.get(), d_hi, slots, B->em_scale).get(), false);
+    y = evalmod(he, y.get(), *B);
+    // w = y + i rot(y, s/2): the lower half holds re + i im; keep it, spread it
+    Ct w = op_add(cx, y.get(), op_mul_monomial(cx, op_automorph(cx, y.get(), rot_galois(cx, half)).get(),
+                                                 cx->N() / 2).get(), false);
+    // the mask aims at q0 / (2 pi), so that the read-out below lands on s_fix
+    w = he.mul_plain_rescale(w.get(), d_lo, slots, (double)q0 / (2.0 * M_PI));
+    w = op_add(cx, w.get(), op_automorph(cx, w.get(), rot_galois(cx, half)).get(), false);
+    // values sin(2 pi t/q0) ~ 2 pi m/q0: read them as m / s_fix, then as m / scale(in)
+    w->scale = w->scale * (2.0 * M_PI * B->s_fix) / (double)q0 / ratio;
+    const int out = boot_out_level(cx);
+    return w->level > out ? op_drop(cx, w.get(), out) : std::move(w);
+}
+
 // Alg. 2 with bootstrapping when levels run out (same steps as cutmax_ct;
 // the Goldschmidt input is x = kappa V and Y_(t+1) is scaled by norm[t]
 // through u' = norm^(1/p) u, so that every refreshed ciphertext is bounded).
@@ -901,6 +964,28 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         if (k == 0) {  // learned quadratic in place of the Goldschmidt iteration
             h = he.learned_half(x.get(), &pl.lq[3 * t]);
             if (shared) h = unpack(ensure(std::move(h), 1).get());
+        } else if (!shared) {
+            // Goldschmidt pair as one complex constant z = g + i h/4 in every
+            // slot (the polynomial g + (h/4) X^(N/2)): 2 Im(z^2) = g h by one
+            // conjugation, z <- z (1.5 - g h), h = 4 Im(z); the 1/4 keeps
+            // every step's scale at s^3 / (q q'), as for a real pair.
+            // Refreshed by the constant bootstrap (bootstrap_const), then
+            // landed on Delta.
+            const u64 g_conj = 2 * cx->N() - 1, e_mi = 3 * cx->N() / 2;  // X -> X^-1; X^(3N/2) = -i
+            auto imag2 = [&](const he_ct *a) {  // 2 Im(a) as a real constant: (a - conj a)(-i)
+                return op_mul_monomial(cx, op_add(cx, a, op_automorph(cx, a, g_conj).get(), true).get(), e_mi);
+            };
+            Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), 1.5);
+            Ct z = he.add_complex_const(he.mcr(x.get(), y0).get(), 0.0, y0 / 8.0);
+            z = he.mul_rescale(z.get(), a.get());
+            for (int i = 2; i <= k; i++) {
+                if (z->level < 2) z = he.mcr(bootstrap_const(cx, z.get()).get(), 1.0);
+                Ct gh = imag2(he.mul_rescale(z.get(), z.get()).get());
+                z = he.mul_rescale(z.get(), he.add_const(he.neg(gh.get()).get(), 1.5).get());
+            }
+            if (z->level < 1) z = bootstrap_const(cx, z.get());
+            // on z's level: no level spent on reading h out
+            h = op_mul_int(cx, imag2(z.get()).get(), 2);
         } else {
         std::vector<double> vlo(slots, 0.0), vhi(slots, 0.0);
         for (int i = 0; i < half; i++) vlo[i] = y0;

@@ -431,6 +431,20 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     for (int a = 0; a < K; a++)
         for (int i = 0; i < cx->nq; i++)  // Montgomery form
             tab.push_back((u64)(((u128)tab[md_qhat + (size_t)a * cx->nq + i] << 64) % cx->primes[i]));
+    // rounding: 1 / p_a as doubles, and (-P mod q_i) in Montgomery form
+    size_t md_inv = tab.size();
+    for (int a = 0; a < K; a++) {
+        const double inv = 1.0 / (double)cx->primes[cx->nq + a];
+        u64 bits;
+        memcpy(&bits, &inv, 8);
+        tab.push_back(bits);
+    }
+    size_t md_negp = tab.size();
+    for (int i = 0; i < cx->nq; i++) {
+        u64 q = cx->primes[i], P = 1;
+        for (int b = 0; b < K; b++) P = mulmod_host(P, cx->primes[cx->nq + b] % q, q);
+        tab.push_back((u64)(((u128)((q - P) % q) << 64) % q));
+    }
     memset(&cx->p_inv, 0, sizeof(cx->p_inv));
     memset(&cx->p_mod, 0, sizeof(cx->p_mod));
     for (int i = 0; i < cx->nq; i++) {
@@ -466,6 +480,8 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     cx->moddown.n_in = K;
     cx->moddown.n_out = cx->nq;
     cx->moddown.stride = cx->nq;
+    cx->moddown.inv_q = reinterpret_cast<const double *>(cx->d_tabs + md_inv);
+    cx->moddown.negq_mont = cx->d_tabs + md_negp;
 
     // secret
     make_secret(cx);

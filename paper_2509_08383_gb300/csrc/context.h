@@ -183,6 +183,7 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl);
 void boot_prepare(he_ctx *cx, int K, int r, int d);
 Ct bootstrap_ct(he_ctx *cx, const he_ct *in);
 Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage);
+Ct bootstrap_const(he_ctx *cx, const he_ct *in);  // one complex value in every slot
 Ct beta_noise(he_ctx *cx, const he_ct *u, double alpha, int d);
 
 // learned inverse-square-root stand-in (learn.cu): trains the 1 -> 16 -> 1

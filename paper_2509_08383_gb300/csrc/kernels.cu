@@ -743,7 +743,12 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 
 // ------------------------------------------------------------------ key switching
 // Approximate basis conversion: for every coefficient, y_a = [x_a*qhinv_a]_{q_a},
-// out_t = sum_a y_a * qhat[a][t] mod p_t.
+// out_t = sum_a y_a * qhat[a][t] mod p_t  (= x + v Q for some 0 <= v < n_in).
+// Rounding mode (tab.inv_q set, used by ModDown): v = rint(sum_a y_a / q_a),
+// computed in double beside the integer sums, and out_t - v Q mod p_t is the
+// centred representative of x mod Q (|.| <= Q/2), so that ModDown's
+// (acc - out) / Q is the rounded division.  The double sum is off by a few
+// ulps of n_in, so only an x within ~1e-15 Q of +-Q/2 could round the other way.
 // One thread per (coefficient, chunk of BCONV_CHUNK output rows).  The
 // products y_a * w_a,t with w = qhat[a][t] 2^64 mod p_t are summed exactly in
 // a 128-bit accumulator of four 32-bit words (n_in <= 16 terms below 2^122
@@ -773,6 +778,9 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     __shared__ const u64 *s_in[BCONV_MAX_IN];
     __shared__ u64 *s_out[BCONV_CHUNK];
     __shared__ int s_p[BCONV_CHUNK];
+    __shared__ double s_inv[BCONV_MAX_IN];
+    __shared__ uint2 s_wn[BCONV_CHUNK];
+    const bool rnd = tab.inv_q != nullptr;
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
@@ -790,12 +798,15 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         s_qis[a] = ok ? tab.qhinv_sh[a] : 0;
         s_q[a] = ok ? pc.m[in.prime(poly * tab.n_in + a)].q : 1;
         s_in[a] = ok ? in.row(poly * tab.n_in + a, log_n) : nullptr;
+        s_inv[a] = ok && rnd ? tab.inv_q[a] : 0.0;
     }
     if (threadIdx.x < BCONV_CHUNK) {
         const int c = threadIdx.x, r = poly * tab.n_out + t0 + c;
         const bool ok = c < nt && poly < n_polys;
         s_out[c] = ok ? out.row(r, log_n) : nullptr;
         s_p[c] = ok ? out.prime(r) : 0;
+        const u64 wn = ok && rnd ? tab.negq_mont[t0 + c] : 0;
+        s_wn[c] = make_uint2((u32)wn, (u32)(wn >> 32));
     }
     __syncthreads();
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -803,15 +814,23 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     u32 acc[BCONV_CHUNK][4];
 #pragma unroll
     for (int c = 0; c < BCONV_CHUNK; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
+    double r = 0.0;
 #pragma unroll 2
     for (int a = 0; a < tab.n_in; a++) {
         const u64 y = shoup_mul(s_in[a][k], s_qi[a], s_qis[a], s_q[a]);
         const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
+        r = fma((double)y, s_inv[a], r);
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++) {
             const uint2 w = s_w[a * BCONV_CHUNK + c];
             mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], y0, y1, w.x, w.y);
         }
+    }
+    if (rnd) {  // + v (-Q): v <= n_in, one more term below 2^66
+        const u32 v = (u32)rint(r);
+#pragma unroll
+        for (int c = 0; c < BCONV_CHUNK; c++)
+            mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], v, 0u, s_wn[c].x, s_wn[c].y);
     }
 #pragma unroll
     for (int c = 0; c < BCONV_CHUNK; c++) {

@@ -25,6 +25,10 @@ struct BConvTab {
     const u64 *qhinv, *qhinv_sh;    // [n_in]
     const u64 *qhat, *qhat_mont;    // [n_in][stride]
     int n_in, n_out, stride;
+    // rounding mode (ModDown): 1 / q_a [n_in] and (-Q mod p_t) 2^64 mod p_t
+    // [stride], Q the product of the input primes; null: approximate conversion
+    const double *inv_q = nullptr;
+    const u64 *negq_mont = nullptr;
 };
 
 // number of kernels launched by this library so far (all contexts)

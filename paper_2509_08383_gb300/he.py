@@ -92,6 +92,7 @@ def lib():
             "he_rotate": [VP, VP, i32, PP],
             "he_conjugate": [VP, VP, PP],
             "he_automorphism": [VP, VP, u64, PP],
+            "he_mul_monomial": [VP, VP, u64, PP],
             "he_rotsum": [VP, VP, u32, PP],
             "he_keyswitch_raw": [VP, pu64, u32, u64, pu64, pu64],
             "he_ntt_device": [VP, VP, u32, u32, i32],
@@ -99,6 +100,7 @@ def lib():
             "he_bootstrap_prepare": [VP, u32, u32, u32],
             "he_bootstrap": [VP, VP, PP],
             "he_bootstrap_stage": [VP, VP, i32, PP],
+            "he_bootstrap_const": [VP, VP, PP],
             "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
             "he_learn_invsqrt": [VP, C.POINTER(C.c_float), sz, u32, C.c_float, u64, pd, pd],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
@@ -356,6 +358,9 @@ class Context:
     def automorphism(self, a, g):
         return self._ct(lib().he_automorphism, a.ptr, int(g))
 
+    def mul_monomial(self, a, e):
+        return self._ct(lib().he_mul_monomial, a.ptr, int(e))
+
     def rotsum(self, a, steps):
         return self._ct(lib().he_rotsum, a.ptr, int(steps))
 
@@ -388,6 +393,10 @@ class Context:
 
     def bootstrap_stage(self, ct, stage):
         return self._ct(lib().he_bootstrap_stage, ct.ptr, int(stage))
+
+    def bootstrap_const(self, ct):
+        """Refresh a ciphertext holding one complex value in every slot."""
+        return self._ct(lib().he_bootstrap_const, ct.ptr)
 
     def learn_invsqrt(self, xs, steps=3000, lr=1e-2, seed=0):
         """Train the learned inverse-square-root network on the GPU (FP32): returns

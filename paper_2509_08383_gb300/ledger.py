@@ -138,6 +138,20 @@ class Sim:
             self.ks[c - i] += stc[i]
         return c - 3
 
+    def bootstrap_const(self, a):
+        """Bootstrapping of one complex value in every slot: trace, one EvalMod
+        on the packed real and imaginary parts, unpacking; handed back at the
+        general bootstrap's output level."""
+        K, r, d = self.boot
+        out = Sim(self.nq, self.log_n, self.boot).bootstrap(0)
+        self.n_boot += 1
+        L = self.nq - 3                   # raised 2 levels below the top
+        self.ks[L] += self.log_n - 1 + 1  # trace, conjugation
+        c = self._evalmod(L - 1, d, r)    # after the packing mask
+        self.ks[c] += 1                   # rotation by N/4 lining up the halves
+        self.ks[c - 1] += 1               # replication after the mask
+        return min(c - 1, out)
+
 
 def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
     """Key switches per level and bootstraps of one CutMax (library circuit).
@@ -202,15 +216,15 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
                 Y = power(u, p)
                 continue
             a = mcr(x)
-            P = sim.mul(mcr(x), a)            # packed [g | h]
+            z = sim.mul(mcr(x), a)            # complex pair z = g + i h
             for i in range(2, k + 1):
-                if P < 2:
-                    P = mcr(sim.bootstrap(P))
-                Q = sim.mul(P, sim.rot(P))
-                P = sim.mul(P, Q)
-            P = ensure(P, 1)
-            hm = mcr(P)
-            h = sim.rot(hm)
+                if z < 2:
+                    z = mcr(sim.bootstrap_const(z))
+                Q = sim.rot(sim.mul(z, z))        # z^2, conjugated for g h
+                z = sim.mul(z, Q)
+            if z < 1:
+                z = sim.bootstrap_const(z)
+            h = sim.rot(z)                    # h = Im z by one conjugation
             h, Dp = ensure(h, 1), ensure(Dp, 1)
             u = sim.mul(Dp, h)
             u = ensure(u, (p - 1).bit_length())

@@ -108,3 +108,33 @@ def test_bootstrap_stages(boot_pair):
     d8 = g.decrypt(g.bootstrap_stage(ct, 8), complex_out=True)
     mvec = ((pt[:h] + 1j * pt[h:]) / delta)[br]
     assert np.abs(d8 - mvec).max() < 1e-7
+
+
+def test_constant_bootstrap(boot_pair):
+    """Bootstrapping of one complex value in every slot by the trace over
+    X -> X^(5^k): the value comes back within the bootstrapping error at the
+    general bootstrap's output level; for a slot vector that is not constant
+    the trace is the projection onto the constants, so the result is the slot
+    average (coefficient 0 of the plaintext is the mean real part, coefficient
+    N/2 the mean imaginary part); a batch gives each member's own result."""
+    g, _, _ = boot_pair
+    h = g.slots
+    g.gen_rot_keys([1 << i for i in range(LOG_N - 1)])
+    delta = 2.0 ** 40
+    val = 0.3 - 0.7j
+    pt = oenc.encode(np.full(h, val), LOG_N, delta)
+    others = np.delete(np.arange(2 * h), [0, h])
+    assert np.abs(pt[others]).max() == 0 and pt[0] == round(0.3 * delta) and pt[h] == round(-0.7 * delta)
+    c1 = g.encrypt_poly(pt, delta, 21, level=0)
+    b1 = g.bootstrap_const(c1)
+    assert b1.level == len(QB) - 1 - 16
+    assert abs(b1.scale / delta - 1) < 1e-9          # lands on the input's scale, as he_bootstrap does
+    assert np.abs(g.decrypt(b1, complex_out=True) - val).max() < 1e-6
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, h) + 1j * rng.uniform(-1, 1, h)
+    c2 = g.encrypt_poly(oenc.encode(z, LOG_N, delta), delta, 22, level=3)
+    b2 = g.bootstrap_const(c2)
+    assert np.abs(g.decrypt(b2, complex_out=True) - z.mean()).max() < 1e-6
+    bb = g.bootstrap_const(g.batch_pack([c1, g.drop(c2, 0)]))
+    for i, b in enumerate((b1, b2)):
+        assert (g.batch_member(bb, i).export() == b.export()).all()

@@ -243,6 +243,35 @@ def test_keyswitch_relation(small_ctx):
         assert np.abs(diff).max() < 2 ** 20
 
 
+def test_moddown_is_rounded_division():
+    """ModDown of hybrid key switching is the rounded division round(x / P) by
+    the special modulus P, checked with Python integers on random x in
+    (-Q_l P / 2, Q_l P / 2) and on the x whose x / P lies closest to a rounding
+    boundary from either side (x mod P = (P - 1)/2 or (P + 1)/2), and 0, +-1.
+    An approximate conversion from P to Q_l (off by up to one P per special
+    prime) fails this."""
+    import random
+    ctx = ckks.Context(10, [60, 40, 40, 40], [60, 60, 61], dnum=2, seed=3)
+    n, l, K = ctx.n, 2, 3
+    qs, ps = ctx.primes[: l + 1], ctx.primes[ctx.nq:]
+    P, M = math.prod(ps), math.prod(qs) * math.prod(ps)
+    rng = random.Random(7)
+    edge = [0, 1, -1, (P - 1) // 2, (P + 1) // 2, -(P - 1) // 2, -(P + 1) // 2]
+    for _ in range(24):
+        k = rng.randrange(-math.prod(qs) // 2 + 1, math.prod(qs) // 2 - 1)
+        edge += [k * P + (P - 1) // 2, k * P + (P + 1) // 2]
+    xs0 = edge + [rng.randrange(-M // 2 + 1, M // 2) for _ in range(n - len(edge))]
+    xs1 = [rng.randrange(-M // 2 + 1, M // 2) for _ in range(n)]
+    rows = list(qs) + list(ps)
+    acc0 = np.array([[x % p for x in xs0] for p in rows], dtype=np.uint64)
+    acc1 = np.array([[x % p for x in xs1] for p in rows], dtype=np.uint64)
+    o0, o1 = ctx.moddown(acc0, acc1, l)
+    for xs, o in ((xs0, o0), (xs1, o1)):
+        r = [(2 * x + P) // (2 * P) for x in xs]          # round(x / P); P odd: no ties
+        want = np.array([[v % q for v in r] for q in qs], dtype=np.uint64)
+        assert (o == want).all()
+
+
 def test_rescale_divides_by_last_prime(small_ctx):
     ctx = small_ctx
     rng = np.random.default_rng(5)
