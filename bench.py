@@ -1,6 +1,6 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|cfg5|mul16|rot16|ntt16|boot16]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|cfg5|mul16|rot16|ntt16|boot16|bootc16]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
@@ -524,17 +524,26 @@ def run_micro(args):
     level; rot16 = one rotation (automorphism + hybrid key switch) at the top
     level; ntt16 = a forward and an inverse NTT of one 41-limb block (every
     prime of the chain, 21 MB); boot16 = one bootstrapping of a level-0
-    ciphertext."""
+    ciphertext; bootc16 = one constant bootstrapping (trace form) of a level-0
+    ciphertext holding one complex value in every slot."""
     import torch
     from paper_2509_08383_gb300 import build, he
     build.build_library()
     torch.cuda.set_device(0)
-    boot = args.workload == "boot16"
+    boot = args.workload in ("boot16", "bootc16")
     g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=(24 << 30) if boot else (4 << 30))
     rng = np.random.default_rng(0)
     slots = 1 << 15
     roof = None
-    if boot:
+    if args.workload == "bootc16":
+        g.bootstrap_prepare(24, 4, 31)
+        g.gen_rot_keys([1 << i for i in range(15)])
+        cts = [g.encrypt(np.full(slots, 0.9 + 0.2j), g.delta, 0, level=0)]
+        op = lambda: g.bootstrap_const(cts[0])
+        metric, unit = "constant bootstraps/s (N=2^16, K=24, r=4, d=31, dnum=3)", "boot/s"
+        wl = ("CKKS bootstrapping of a level-0 ciphertext holding one complex value in every slot "
+              "(trace form), N=2^16, 31 primes + 10 special primes, h=192")
+    elif boot:
         g.bootstrap_prepare(24, 4, 31)
         cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, 0, level=0)]
         op = lambda: g.bootstrap(cts[0])
@@ -598,13 +607,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "mul16",
-                                                           "rot16", "ntt16", "boot16"])
+                                                           "rot16", "ntt16", "boot16", "bootc16"])
     ap.add_argument("--tokens", type=int, default=32, help="cfg5: tokens decoded per stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("mul16", "rot16", "ntt16", "boot16"):
+    if args.workload in ("mul16", "rot16", "ntt16", "boot16", "bootc16"):
         return run_micro(args)
     if args.workload == "cfg3":
         return run_cfg3(args)
