@@ -821,9 +821,19 @@ Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
     Ct im = op_mul_monomial(cx, op_add(cx, x.get(), xc.get(), true).get(), 3 * cx->N() / 2);
     im->scale *= 2;
     if (stage == 5) return im;
-    re = evalmod(he, re.get(), *B);
+    if (in->batch <= 2) {
+        // both parts as one batch: every launch carries twice the rows and
+        // every key word read serves both (members are bit-identical to
+        // separate evaluations); larger batches fill the GPU by themselves
+        const he_ct *parts[2] = {re.get(), im.get()};
+        Ct both = evalmod(he, op_batch_pack(cx, parts, 2).get(), *B);
+        re = op_batch_member(cx, both.get(), 0, in->batch);
+        im = op_batch_member(cx, both.get(), in->batch, in->batch);
+    } else {
+        re = evalmod(he, re.get(), *B);
+        im = evalmod(he, im.get(), *B);
+    }
     if (stage == 6) return re;
-    im = evalmod(he, im.get(), *B);
     if (stage == 7) return im;
     Ct w = op_add(cx, re.get(), op_mul_monomial(cx, im.get(), cx->N() / 2).get(), false);
     // values sin(2 pi t/q0) ~ 2 pi m/q0: read them as m / s_fix

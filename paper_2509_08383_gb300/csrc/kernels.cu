@@ -111,13 +111,16 @@ static inline unsigned grid_for(size_t total, int per_block) {
 // Local stage s of a sub-transform is global stage s (column pass) or
 // LOGR + s (row pass); its twiddle index is 2^s + grp (column) or
 // 2^s (R + row) + grp (row), grp < 2^s.
-// The CTA first stages its tile and every twiddle pair (value, Shoup
-// companion) it will use in shared memory with asynchronous 16-byte copies:
-// the column pass shares the R - 1 twiddles of its stages among all columns;
-// the row pass needs, for stage s, the 16 * 2^s consecutive table entries
-// starting at 2^s (R + first row).  The butterflies then read only shared
-// memory.  Row-pass tiles carry two pad words per 16 entries, which keeps
-// 16-byte alignment and spreads round B's 16-byte reads over the banks.
+// The CTA stages its tile and the twiddle pairs (value, Shoup companion) in
+// shared memory with asynchronous 16-byte copies: the column pass shares the
+// R - 1 twiddles of its stages among all columns; the row pass needs, for
+// stage s, the 16 * 2^s consecutive table entries starting at 2^s (R + first
+// row).  The butterflies then read only shared memory.  The row pass stages
+// round A's twiddles with the tile, and round B's (15/16 of them) only once
+// the tile sits in registers, into the same buffer: 65 KB instead of 102 KB
+// per CTA at C = 256, so that three CTAs share an SM.  Row-pass tiles carry
+// two pad words per 16 entries, which keeps 16-byte alignment and spreads
+// round B's 16-byte reads over the banks.
 constexpr int NTT_TILE = 16;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -130,8 +133,14 @@ template <int LOGR, int LOGC, bool COLS>
 struct NttShape {
     static constexpr int LOGM = COLS ? LOGR : LOGC, M = 1 << LOGM;
     static constexpr int DATA = COLS ? 16 * M : 18 * M;       // u64 words
-    static constexpr int TW = COLS ? M : 16 * (M - 1);         // twiddle pairs
-    static constexpr size_t SMEM = (size_t)DATA * 8 + (size_t)TW * 16;
+    // twiddle pairs: column pass all M - 1 (one per group, shared by the
+    // columns); row pass, round A (stages 0..3) 16 * 15, round B 16 * (M - 16)
+    static constexpr int TWA = COLS ? M : 16 * 15;
+    static constexpr int TWB = COLS ? 0 : 16 * (M - 16);
+    // row pass: the tile and round B's twiddles share the first region
+    static constexpr size_t U = COLS ? (size_t)DATA * 8
+                                     : ((size_t)DATA * 8 > (size_t)TWB * 16 ? (size_t)DATA * 8 : (size_t)TWB * 16);
+    static constexpr size_t SMEM = U + (size_t)TWA * 16;
 };
 
 template <bool FWD>
@@ -150,13 +159,14 @@ __device__ __forceinline__ void bfly(u64 &X, u64 &Y, ulonglong2 w, u64 q, u64 q2
 }
 
 template <int LOGR, int LOGC, bool FWD, bool COLS>
-__global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Rows src, NttTables tw) {
+__global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC), 3) k_ntt(Rows rows, Rows src, NttTables tw) {
     using S = NttShape<LOGR, LOGC, COLS>;
     constexpr int LOGN = LOGR + LOGC, R = 1 << LOGR, C = 1 << LOGC;
     constexpr int LOGM = S::LOGM, M = S::M, TPS = M / 16;
     extern __shared__ __align__(16) unsigned char ntt_smem[];
     u64 *sm = reinterpret_cast<u64 *>(ntt_smem);
-    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(ntt_smem + (size_t)S::DATA * 8);
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(ntt_smem + S::U);       // column pass; row pass round A
+    ulonglong2 *stwb = reinterpret_cast<ulonglong2 *>(ntt_smem);             // row pass round B (over the tile)
     const PrimeConsts &pc = c_pcs[rows.slot];
     const int rb = blockIdx.y;
     u64 *x = rows.row(rb, LOGN);
@@ -188,23 +198,37 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Ro
         }
         const size_t r0 = (size_t)blockIdx.x * 16;
 #pragma unroll
-        for (int s = 0; s < LOGM; s++) {
+        for (int s = 0; s < 4; s++) {  // round A: one group per thread group of a row (broadcast reads)
             const ulonglong2 *ws = W + ((R + r0) << s);
             ulonglong2 *ds = stw + 16 * ((1 << s) - 1);
-            if (s < 4) {  // round A: one group per thread group of a row (broadcast reads)
-                for (int k = tid; k < (16 << s); k += M) cp_async16(ds + k, ws + k);
-            } else {      // round B: group j G + g of row `sub` stored at g TPS + j
-                constexpr int LT = LOGM - 4;  // log2 TPS
-                for (int k = tid; k < (16 << s); k += M) {
-                    const int sub_k = k >> s, grp = k & ((1 << s) - 1);
-                    const int jj = grp >> (s - LT), g = grp & ((1 << (s - LT)) - 1);
-                    cp_async16(ds + (sub_k << s) + (g << LT) + jj, ws + k);
-                }
-            }
+            for (int k = tid; k < (16 << s); k += M) cp_async16(ds + k, ws + k);
         }
     }
     cp_async_wait_all();
     __syncthreads();
+    // row pass, round B's twiddles: group j G + g of row `sub` stored at g TPS + j,
+    // stage s at 16 (2^s - 16); called once the tile is in registers
+    auto stage_b = [&]() {
+        if (COLS) return;
+        __syncthreads();  // every thread has read its entries of the tile
+        const size_t r0 = (size_t)blockIdx.x * 16;
+        constexpr int LT = LOGM - 4;  // log2 TPS
+#pragma unroll
+        for (int s = 4; s < LOGM; s++) {
+            const ulonglong2 *ws = W + ((R + r0) << s);
+            ulonglong2 *ds = stwb + 16 * ((1 << s) - 16);
+            for (int k = tid; k < (16 << s); k += M) {
+                const int sub_k = k >> s, grp = k & ((1 << s) - 1);
+                const int jj = grp >> (s - LT), g = grp & ((1 << (s - LT)) - 1);
+                cp_async16(ds + (sub_k << s) + (g << LT) + jj, ws + k);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    };
+    auto release_b = [&]() {  // round B done with its twiddles: the tile may return
+        if (!COLS) __syncthreads();
+    };
     // thread -> (sub-transform, position)
     const int sub = COLS ? (tid & 15) : (tid / TPS);
     const int j = COLS ? (tid >> 4) : (tid % TPS);
@@ -215,7 +239,7 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Ro
     // row pass, round B: group j G + g (G = 2^s / TPS), stored transposed
     auto twl_b = [&](int s, int g) -> ulonglong2 {
         if (COLS) return stw[(1 << s) - 1 + j * ((1 << s) / TPS) + g];
-        return stw[16 * ((1 << s) - 1) + (sub << s) + g * TPS + j];
+        return stwb[16 * ((1 << s) - 16) + (sub << s) + g * TPS + j];
     };
     u64 v[16];
     auto round_a = [&]() {  // stages 0..3, entries j + TPS i
@@ -276,6 +300,7 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Ro
         store_a();
         __syncthreads();
         load_b();
+        stage_b();
         round_b();
         if (!COLS) {  // last stage of the forward transform: reduce to [0, q)
 #pragma unroll
@@ -286,10 +311,13 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC)) k_ntt(Rows rows, Ro
                 v[i] = t;
             }
         }
+        release_b();
         store_b();
     } else {
         load_b();
+        stage_b();
         round_b();
+        release_b();
         store_b();
         __syncthreads();
         load_a();
