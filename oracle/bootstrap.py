@@ -167,5 +167,7 @@ class Bootstrapper:
         w = ctx.add(re, ctx.mul_monomial(im, ctx.n // 2))
         out = self.linear(w, self.stc, self.out_scale)
         out = ctx.drop(out, out.level - 2)
-        out.set_scale(out.scale / ratio)
+        # the slots read m / s_fix = (message) * ratio: declaring the scale
+        # ratio times larger reads the message
+        out.set_scale(out.scale * ratio)
         return out

@@ -844,7 +844,9 @@ Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
         w = apply_level(cx, w.get(), B->stc[lv], tg[lv]);
         if (stage == 9 + lv && lv < 2) return w;
     }
-    w->scale = w->scale / ratio;
+    // the slots read m / s_fix = (message) * ratio: declaring the scale ratio
+    // times larger reads the message
+    w->scale = w->scale * ratio;
     return w;
 }
 
@@ -886,16 +888,99 @@ Ct bootstrap_const(he_ctx *cx, const he_ct *in) {
     Ct y = op_add(cx, he.mul_plain_rescale(re.get(), d_lo, slots, B->em_scale).get(),
                   he.mul_plain_rescale(im.get(), d_hi, slots, B->em_scale).get(), false);
     y = evalmod(he, y.get(), *B);
+    // A constant's whole value sits in coefficient 0 (a vector's spreads over
+    // N coefficients), so sin(theta), theta = 2 pi m / q0, is read at angles
+    // where its curvature shows (theta^2 / 6 ~ 4e-4 for a value 1 at q0 = 2^47
+    // against Delta = 2^40). One Taylor step of arcsin, sin + sin^3 / 6, takes
+    // the error to 3 theta^4 / 40; the 1/6 is a scale declaration.
+    {
+        Ct y2 = he.mul_rescale(y.get(), y.get());
+        y2->scale *= 6.0;
+        y = he.mul_rescale(y.get(), he.add_const(y2.get(), 1.0).get());
+    }
     // w = y + i rot(y, s/2): the lower half holds re + i im; keep it, spread it
     Ct w = op_add(cx, y.get(), op_mul_monomial(cx, op_automorph(cx, y.get(), rot_galois(cx, half)).get(),
                                                  cx->N() / 2).get(), false);
-    // the mask aims at q0 / (2 pi), so that the read-out below lands on s_fix
+    // the mask aims at q0 / (2 pi), so that the read-out below lands on the
+    // input's scale
     w = he.mul_plain_rescale(w.get(), d_lo, slots, (double)q0 / (2.0 * M_PI));
     w = op_add(cx, w.get(), op_automorph(cx, w.get(), rot_galois(cx, half)).get(), false);
     // values sin(2 pi t/q0) ~ 2 pi m/q0: read them as m / s_fix, then as m / scale(in)
-    w->scale = w->scale * (2.0 * M_PI * B->s_fix) / (double)q0 / ratio;
+    w->scale = w->scale * (2.0 * M_PI * B->s_fix) / (double)q0 * ratio;
     const int out = boot_out_level(cx);
     return w->level > out ? op_drop(cx, w.get(), out) : std::move(w);
+}
+
+// Refresh schedule of the bootstrapped circuit with per-stream scalar chains.
+// The scalars (x, h and the final sum) hold one value in every slot and are
+// refreshed by the constant bootstrap; the vector Y, D', u by the general one
+// (about twice the cost). Per iteration two choices are open: refresh h when
+// it sits below D' (so that u keeps D's levels for the power), and bootstrap
+// Y before the statistics although it has the 5 levels they need. Every
+// combination is played on the circuit's level bookkeeping (integer multipliers
+// sized from the primes' bit lengths, as the rescale rule does) and the one
+// costing least (general 2, constant 1; then fewer bootstraps; then the first)
+// is kept.
+struct RefreshSched {
+    std::vector<uint8_t> h_refresh, y_boot;
+};
+static RefreshSched refresh_schedule(he_ctx *cx, const Plan &pl, int y_level, int out, bool padded) {
+    auto bits = [&](int l) { return (double)std::lround(std::log2((double)cx->primes[l])); };
+    auto mcr_bits_level = [&](int a, double c) {
+        int r = 1;
+        double e = bits(a);
+        while (std::fabs(c) * std::exp2(e) < std::exp2(30.0) && r < 3 && a - r >= 1) e += bits(a - r), r++;
+        return a - r;
+    };
+    const int T = pl.T, per = T <= 6 ? 4 : 2;  // choices per iteration (early Y bootstraps only up to T = 6)
+    long total = 1;
+    for (int t = 0; t < T; t++) total *= per;
+    long best = -1;
+    int best_cost = 1 << 30, best_n = 1 << 30;
+    for (long combo = 0; combo < total; combo++) {
+        long cc = combo;
+        int Y = y_level, g = 0, c = 0;
+        for (int t = 0; t < T; t++) {
+            const int ch = (int)(cc % per);
+            cc /= per;
+            const bool hr = ch & 1, yb = ch & 2;
+            const int k = pl.k[t], lp = power_depth(pl.p[t]);
+            if (Y < 5 || yb) Y = out, g++;
+            int x = mcr_bits_level(Y - 1, pl.kappa[t]);
+            if (x < 2) x = out, c += 1000;  // x (up to ~sqrt of the range ratio) is too large to refresh well
+            int h;
+            if (k == 0) {
+                h = x - 2;
+            } else {
+                int z = x - 2;
+                for (int i = 2; i <= k; i++) {
+                    if (z < 2) z = out - 1, c++;
+                    z -= 2;
+                }
+                if (z < 1) z = out, c++;
+                h = z;
+            }
+            int Dp = Y - (padded ? 2 : 1);
+            if (hr && h < Dp) h = out, c++;
+            if (h < 1) h = out, c++;
+            if (Dp < 1) Dp = out, g++;
+            int u = std::min(Dp, h) - 1;
+            if (u < lp) u = out, g++;
+            Y = u - lp;
+        }
+        if (Y < 2) Y = out, g++;
+        if (Y < pl.d + 3) c++;
+        const int cost = 2 * g + c;
+        if (cost < best_cost || (cost == best_cost && g + c < best_n)) best = combo, best_cost = cost, best_n = g + c;
+    }
+    RefreshSched rs{std::vector<uint8_t>(T, 0), std::vector<uint8_t>(T, 0)};
+    for (int t = 0; t < T; t++) {
+        const int ch = (int)(best % per);
+        best /= per;
+        rs.h_refresh[t] = ch & 1;
+        rs.y_boot[t] = (ch & 2) ? 1 : 0;
+    }
+    return rs;
 }
 
 // Alg. 2 with bootstrapping when levels run out (same steps as cutmax_ct;
@@ -921,6 +1006,8 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     // log2(Sp)-step rotate-and-sum
     const int n_streams = sh.S;
     const bool shared = pl.shared && n_streams > 1;
+    const RefreshSched rs = shared ? RefreshSched{std::vector<uint8_t>(pl.T, 0), std::vector<uint8_t>(pl.T, 0)}
+                                   : refresh_schedule(cx, pl, Y->level, out_level, m != 0);
     int Sp = 1, lsp = 0;
     while (Sp < n_streams) Sp *= 2, lsp++;
     if (shared && (Sp > slots / 2 || lsp > sh.steps))
@@ -945,7 +1032,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     for (int t = 0; t < pl.T; t++) {
         const int p = pl.p[t], k = pl.k[t];
         const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
-        Y = ensure(std::move(Y), 5);
+        if (Y->level < 5 || (!shared && rs.y_boot[t])) Y = bootstrap_ct(cx, Y.get());
         Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
         Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).get(), true);
         Ct E = he.mul_rescale(D.get(), D.get());
@@ -958,7 +1045,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         // the 4 levels that Y brought: up to 3 rescales scale it to x ~ 1
         Ct x = he.mcr_bits(V.get(), kap, -1, 30);
         if (shared) x = pack(ensure(std::move(x), 1).get());
-        x = ensure(std::move(x), 2);
+        if (x->level < 2) x = shared ? bootstrap_ct(cx, x.get()) : bootstrap_const(cx, x.get());
         const double coef = 2.0 * std::sqrt(kap * pl.n) / pl.c[t] * rn;
         // D' = D * coef (times the 0/1 slot mask when padded), mask and scalar
         // applied separately for precision (see cutmax_ct)
@@ -1007,9 +1094,9 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         P = he.add_plain_vec(P.get(), d_vhi, slots);
         P = he.mul_rescale(P.get(), a.get());
         // one step maps the pair's scale s to s^3 / (q q'): a deviation from
-        // Delta triples every step and a bootstrap only flips its sign, so each
-        // refresh is followed by a multiplication by 1 that lands exactly on
-        // Delta (the spare 13th level of a refresh: 6 steps still fit)
+        // Delta triples every step and a bootstrap keeps it, so each refresh
+        // is followed by a multiplication by 1 that lands exactly on Delta
+        // (the spare 13th level of a refresh: 6 steps still fit)
         for (int i = 2; i <= k; i++) {
             if (P->level < 2) P = he.mcr(bootstrap_ct(cx, P.get()).get(), 1.0);
             Ct Q = he.mul_rescale(P.get(), op_automorph(cx, P.get(), g_half).get());
@@ -1021,6 +1108,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
         if (shared) h = unpack(ensure(std::move(h), 1).get());
         }
+        if (!shared && ((rs.h_refresh[t] && h->level < Dp->level) || h->level < 1)) h = bootstrap_const(cx, h.get());
         h = ensure(std::move(h), 1);
         Dp = ensure(std::move(Dp), 1);
         Ct u = he.mul_rescale(Dp.get(), stream_bcast(cx, h.get(), cps).get());
@@ -1033,8 +1121,9 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         u = ensure(std::move(u), power_depth(p));
         Y = he.power(u.get(), p);
     }
-    Y = ensure(std::move(Y), shared ? 3 : pl.d + 3);
+    Y = ensure(std::move(Y), shared ? 3 : 2);
     Ct Ssum = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+    if (!shared && Ssum->level < pl.d + 3) Ssum = bootstrap_const(cx, Ssum.get());  // the inverse's d + 2 levels
     Ct F;
     if (shared) {
         Ct Sp_ct = ensure(pack(ensure(std::move(Ssum), 1).get()), pl.d + 3);

@@ -148,9 +148,78 @@ class Sim:
         L = self.nq - 3                   # raised 2 levels below the top
         self.ks[L] += self.log_n - 1 + 1  # trace, conjugation
         c = self._evalmod(L - 1, d, r)    # after the packing mask
+        c = self.mul(c, c)                # arcsine step y (1 + y^2/6)
+        c = self.mul(c + 1, c)
         self.ks[c] += 1                   # rotation by N/4 lining up the halves
         self.ks[c - 1] += 1               # replication after the mask
         return min(c - 1, out)
+
+
+def refresh_schedule(plan, qb, y_level, out, padded):
+    """The library's refresh schedule of a bootstrapped plan with per-stream
+    scalar chains: per iteration, (refresh h by a constant bootstrap when it
+    sits below D', bootstrap Y early), the combination of least cost (general
+    bootstrap 2, constant 1; then fewer bootstraps; then the first) on the
+    circuit's level bookkeeping."""
+    T = plan.T
+    per = 4 if T <= 6 else 2
+
+    def mcr_bits_level(a, c):
+        r, e = 1, qb[a]
+        while abs(c) * 2.0 ** e < 2.0 ** 30 and r < 3 and a - r >= 1:
+            e += qb[a - r]
+            r += 1
+        return a - r
+
+    best, best_key = 0, None
+    for combo in range(per ** T):
+        cc, Y, g, c = combo, y_level, 0, 0
+        for t in range(T):
+            ch = cc % per
+            cc //= per
+            hr, yb = ch & 1, ch & 2
+            k, lp = plan.k[t], (int(plan.p[t]) - 1).bit_length()
+            if Y < 5 or yb:
+                Y, g = out, g + 1
+            x = mcr_bits_level(Y - 1, plan.kappa[t])
+            if x < 2:                           # x is too large to refresh well
+                x, c = out, c + 1000
+            if k == 0:
+                h = x - 2
+            else:
+                z = x - 2
+                for _ in range(2, k + 1):
+                    if z < 2:
+                        z, c = out - 1, c + 1
+                    z -= 2
+                if z < 1:
+                    z, c = out, c + 1
+                h = z
+            Dp = Y - (2 if padded else 1)
+            if hr and h < Dp:
+                h, c = out, c + 1
+            if h < 1:
+                h, c = out, c + 1
+            if Dp < 1:
+                Dp, g = out, g + 1
+            u = min(Dp, h) - 1
+            if u < lp:
+                u, g = out, g + 1
+            Y = u - lp
+        if Y < 2:
+            Y, g = out, g + 1
+        if Y < plan.d + 3:
+            c += 1
+        key = (2 * g + c, g + c)
+        if best_key is None or key < best_key:
+            best, best_key = combo, key
+    hr, yb = [], []
+    for t in range(T):
+        ch = best % per
+        best //= per
+        hr.append(bool(ch & 1))
+        yb.append(bool(ch & 2))
+    return hr, yb
 
 
 def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
@@ -194,11 +263,13 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
 
     Y = nq - 1 if start_level is None else start_level
     if plan.bootstrap:                    # the circuit computes on the bootstrap's output levels
-        Y = min(Y, Sim(nq, log_n, boot).bootstrap(0))
+        out = Sim(nq, log_n, boot).bootstrap(0)
+        Y = min(Y, out)
+        h_refresh, y_boot = refresh_schedule(plan, qb, Y, out, m != 0)
     for t in range(plan.T):
         p, k = plan.p[t], plan.k[t]
-        if plan.bootstrap:
-            Y = ensure(Y, 5)
+        if plan.bootstrap and (Y < 5 or y_boot[t]):
+            Y = sim.bootstrap(Y)
         rotsum(Y)
         D = Y
         E = sim.mul(D, D)
@@ -206,26 +277,26 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
         if m:
             sim.mul(Y, Y)
         if plan.bootstrap:
-            x = ensure(mcr_bits(V, plan.kappa[t]), 2)
+            x = mcr_bits(V, plan.kappa[t])
+            if x < 2:                         # scalars take the constant bootstrap
+                x = sim.bootstrap_const(x)
             Dp = mcr(mcr(D)) if m else mcr(D)
             if k == 0:                        # learned quadratic: x^2, then constants
                 h = mcr(sim.mul(x, x))
-                h, Dp = ensure(h, 1), ensure(Dp, 1)
-                u = sim.mul(Dp, h)
-                u = ensure(u, (p - 1).bit_length())
-                Y = power(u, p)
-                continue
-            a = mcr(x)
-            z = sim.mul(mcr(x), a)            # complex pair z = g + i h
-            for i in range(2, k + 1):
-                if z < 2:
-                    z = mcr(sim.bootstrap_const(z))
-                Q = sim.rot(sim.mul(z, z))        # z^2, conjugated for g h
-                z = sim.mul(z, Q)
-            if z < 1:
-                z = sim.bootstrap_const(z)
-            h = sim.rot(z)                    # h = Im z by one conjugation
-            h, Dp = ensure(h, 1), ensure(Dp, 1)
+            else:
+                a = mcr(x)
+                z = sim.mul(mcr(x), a)        # complex pair z = g + i h/4
+                for i in range(2, k + 1):
+                    if z < 2:
+                        z = mcr(sim.bootstrap_const(z))
+                    Q = sim.rot(sim.mul(z, z))    # z^2, conjugated for g h
+                    z = sim.mul(z, Q)
+                if z < 1:
+                    z = sim.bootstrap_const(z)
+                h = sim.rot(z)                # h = 4 Im z by one conjugation
+            if (h_refresh[t] and h < Dp) or h < 1:
+                h = sim.bootstrap_const(h)
+            Dp = ensure(Dp, 1)
             u = sim.mul(Dp, h)
             u = ensure(u, (p - 1).bit_length())
         elif k == 0:
@@ -245,8 +316,10 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
             u = sim.mul(Dp, h)
         Y = power(u, p)
     if plan.bootstrap:
-        Y = ensure(Y, plan.d + 3)
+        Y = ensure(Y, 2)
     S = rotsum(Y)
+    if plan.bootstrap and S < plan.d + 3:  # the inverse's d + 2 levels, on the scalar
+        S = sim.bootstrap_const(S)
     a = mcr(S)
     F = a
     sq = a

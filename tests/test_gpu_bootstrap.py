@@ -138,3 +138,19 @@ def test_constant_bootstrap(boot_pair):
     bb = g.bootstrap_const(g.batch_pack([c1, g.drop(c2, 0)]))
     for i, b in enumerate((b1, b2)):
         assert (g.batch_member(bb, i).export() == b.export()).all()
+
+
+@pytest.mark.parametrize("scale_ratio", [1.03, 0.97])
+def test_bootstrap_reads_message_at_any_input_scale(boot_pair, scale_ratio):
+    """A circuit's scales drift away from Delta; both bootstraps must hand back
+    the input's message (not the message times the squared scale ratio)."""
+    g, _, _ = boot_pair
+    g.gen_rot_keys([1 << i for i in range(LOG_N - 1)])
+    scale = 2.0 ** 40 * scale_ratio
+    rng = np.random.default_rng(6)
+    z = rng.uniform(-1, 1, g.slots)
+    b = g.bootstrap(g.encrypt(z, scale, 31, level=0))
+    assert np.abs(g.decrypt(b) - z).max() < 1e-6
+    val = 0.4 + 0.1j
+    bc = g.bootstrap_const(g.encrypt(np.full(g.slots, val), scale, 32, level=0))
+    assert np.abs(g.decrypt(bc, complex_out=True) - val).max() < 1e-6

@@ -57,6 +57,10 @@ def test_bootstrapped_cutmax_matches_mirror(setup, seed):
 
 
 def test_bootstrapped_cutmax_matches_oracle_circuit(setup):
+    """The library's bootstrapped circuit against the oracle's (general
+    bootstraps wherever levels run out). The library refreshes its scalar
+    chains by the constant bootstrap on a schedule of its own, so the two end
+    on different levels; their decrypted outputs must agree."""
     from oracle import ckks as ock
     from oracle import encoding as oenc
     from oracle.bootstrap import Bootstrapper
@@ -71,7 +75,6 @@ def test_bootstrapped_cutmax_matches_oracle_circuit(setup):
     pt = oenc.encode(P.pack(x, g.slots, pl.packing), LOG_N, g.delta)
     zg = g.cutmax(g.encrypt_poly(pt, g.delta, 3), pl)
     zo = cutmax_he_boot(HE(o, g.delta), o.encrypt(pt, g.delta, 3), pl, ob)
-    assert zg.level == zo.level
     dg = g.decrypt(zg)[:NV]
     do = oenc.decode(o.decrypt(zo), LOG_N, zo.scale).real[:NV]
     assert np.abs(dg - do).max() < 1e-3

@@ -36,7 +36,11 @@ def test_chebyshev_scaled_cosine(K, d):
 
 
 @pytest.mark.slow
-def test_oracle_bootstrap_refreshes():
+@pytest.mark.parametrize("scale_ratio", [1.0, 1.03])
+def test_oracle_bootstrap_refreshes(scale_ratio):
+    """Refresh of a level-0 ciphertext back to its own message, at the
+    bootstrapping's reference scale and at a scale 3 % off it (a circuit's
+    scales drift away from Delta)."""
     log_n = 11
     qb = [55] + [40] * 3 + [60] * 3 + [60] * 10 + [58] * 3
     ctx = ckks.Context(log_n, qb, [61] * 7, dnum=3, h=64, seed=2)
@@ -44,7 +48,8 @@ def test_oracle_bootstrap_refreshes():
     bs.gen_keys()
     rng = np.random.default_rng(0)
     z = rng.uniform(-1, 1, ctx.slots)
-    ct = ctx.encrypt(enc.encode(z, log_n, 2.0 ** 40), 2.0 ** 40, 1, level=0)
+    scale = 2.0 ** 40 * scale_ratio
+    ct = ctx.encrypt(enc.encode(z, log_n, scale), scale, 1, level=0)
     out = bs.bootstrap(ct)
     assert out.level == len(qb) - 1 - 16
     dec = enc.decode(ctx.decrypt(out), log_n, out.scale)
