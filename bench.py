@@ -29,6 +29,12 @@ METRIC = "encrypted CutMax decodes/sec (vocab 32k, N=2^16), 1 GB300"
 # N=2^16 (90-limb forward / 30-limb inverse launches of one rotation; the row
 # pass with round-B twiddles staged over its tile)
 NTT_DRAM_PER_LIMB = {0: (47.39e6 + 0.33e6 + 93.81e6 + 7.25e6) / 90, 1: (47.11e6 + 0.04e6 + 15.91e6) / 30}
+# integer-pipe ceiling of the NTT: a Shoup butterfly on 64-bit words takes 1.04
+# warp instructions (33 thread instructions: ncu sm__inst_executed of a 90-limb
+# forward transform / its 90 x 2^19 butterflies), and an SM issues at most 4
+# warp instructions per clock: 152 SMs x 4 x 2.07 GHz / 1.04
+NTT_WARP_INSTR_PER_BUTTERFLY = 1.04
+ALU_ISSUE_PEAK = 152 * 4 * 2.07e9
 PROF_NAMES = {0: "ntt_forward (k_ntt_cols+k_ntt_rows)", 1: "ntt_inverse (k_ntt_rows+k_ntt_cols)",
               2: "keyswitch_inner (k_keyswitch_inner)", 3: "bconv (k_bconv)"}
 
@@ -698,6 +704,15 @@ def main():
                 "algorithmic_bytes_per_launch": bytes_dom / max(n_dom, 1),
                 "share_of_step": (ms_dom / args.steps) / ms if ms else None, "peak_source": peak_kind,
                 "class_ms_per_step": {PROF_NAMES[c]: v for c, v in share.items()}}
+    if dom in NTT_DRAM_PER_LIMB and n_dom:
+        # the NTT binds on integer issue, not on HBM: butterflies per second
+        # against the issue ceiling
+        fly = (bytes_dom / n_dom) / (16.0 * (1 << log_n)) * (1 << (log_n - 1)) * log_n
+        fly_s = fly / (ms_dom / n_dom * 1e-3)
+        ceil = ALU_ISSUE_PEAK / NTT_WARP_INSTR_PER_BUTTERFLY
+        roofline["alu"] = {"achieved": fly_s, "peak": ceil, "unit": "butterflies/s", "frac": fly_s / ceil,
+                           "peak_source": "152 SMs x 4 warp instructions per clock x 2.07 GHz / 1.04 warp "
+                                          "instructions per butterfly (ncu)"}
     value = ws * 1000.0 / ms
 
     # end to end through the C ABI: pinned host logits -> host outputs
