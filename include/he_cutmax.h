@@ -211,8 +211,9 @@ int he_ntt_device(he_ctx *ctx, uint64_t *data, uint32_t n_limbs, uint32_t prime_
  * Level-consuming steps use the chain from the top down, so the top
  * primes should be the large (about 60-bit) ones. */
 int he_bootstrap_prepare(he_ctx *ctx, uint32_t K, uint32_t r, uint32_t d);
-/* Refresh a ciphertext (any level; only limb q0 is used) to a high level,
- * encrypting the same message up to the bootstrapping error. */
+/* Refresh a ciphertext (any level, any scale; only limb q0 is used) to a high
+ * level, encrypting the same message at the input's scale, up to the
+ * bootstrapping error. */
 int he_bootstrap(he_ctx *ctx, const he_ct *in, he_ct **out);
 /* The ciphertext after one stage of he_bootstrap, for inspection: 0 ModRaise
  * (scale declared q0 (K+1)), 1..3 after each CoeffToSlot level, 4 / 5 the
@@ -225,8 +226,11 @@ int he_bootstrap_stage(he_ctx *ctx, const he_ct *in, int32_t stage, he_ct **out)
  * automorphisms X -> X^(5^k) (a log2(N/2)-step rotate-and-sum with the
  * rotation keys of 1, 2, ..., N/4, which he_cutmax_prepare of a bootstrapped
  * plan generates) keeps the coefficients of 1 and X^(N/2) only; both go
- * through one EvalMod, packed into the two halves of the slots.  Output at
- * he_bootstrap's output level.  Slots that do not hold one common value come
+ * through one EvalMod, packed into the two halves of the slots, followed by
+ * one Taylor step of arcsin (a constant's value sits whole in coefficient 0,
+ * where the sine's curvature would otherwise show: relative error ~4e-7 v^4
+ * for a value v at q0 / Delta = 2^7).  Output at he_bootstrap's output level
+ * and at the input's scale.  Slots that do not hold one common value come
  * out as their average (the trace is a projection): the result is then not
  * the input's message, and no error is raised.  HE_EINVAL without
  * he_bootstrap_prepare; HE_EKEY (or the missing-key error) without the keys. */

@@ -856,9 +856,10 @@ Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage) {
 // automorphisms X -> X^(5^k) (a log2(N/2)-step rotate-and-sum, exact: every
 // other monomial's orbit sums to 0) instead of CoeffToSlot; its two
 // coefficients, scaled, become the real and the imaginary part of every
-// slot, are packed into the two slot halves for one EvalMod, and are put
-// back as a complex constant, in place of the second EvalMod and of
-// SlotToCoeff.  Returns the refreshed ciphertext at the bootstrap output level.
+// slot, are packed into the two slot halves for one EvalMod (followed by one
+// arcsine step), and are put back as a complex constant, in place of the
+// second EvalMod and of SlotToCoeff.  Returns the refreshed ciphertext at the
+// bootstrap output level and the input's scale.
 Ct bootstrap_const(he_ctx *cx, const he_ct *in) {
     auto B = cx->boot_state;
     if (!B) throw Error{HE_EINVAL, "bootstrapping not prepared"};
