@@ -181,36 +181,16 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC), 3) k_ntt(Rows rows,
         int a = sub * M + e;
         return a + 2 * (a >> 4);
     };
-    if (COLS) {
-        const int c0 = blockIdx.x * 16;
-#pragma unroll 4
-        for (int idx = tid; idx < 8 * M; idx += M) {  // row r of the tile: 16 words at xin[r C + c0]
-            int r = idx >> 3, h = idx & 7;
-            cp_async16(sm + r * 16 + 2 * h, xin + (size_t)r * C + c0 + 2 * h);
-        }
-        if (tid + 1 < M) cp_async16(stw + tid, W + tid + 1);
-    } else {
-        const u64 *xr = xin + (size_t)blockIdx.x * 16 * C;
-#pragma unroll 4
-        for (int idx = tid; idx < 8 * M; idx += M) {
-            int a = 2 * idx;
-            cp_async16(sm + a + 2 * (a >> 4), xr + a);
-        }
-        const size_t r0 = (size_t)blockIdx.x * 16;
-#pragma unroll
-        for (int s = 0; s < 4; s++) {  // round A: one group per thread group of a row (broadcast reads)
-            const ulonglong2 *ws = W + ((R + r0) << s);
-            ulonglong2 *ds = stw + 16 * ((1 << s) - 1);
-            for (int k = tid; k < (16 << s); k += M) cp_async16(ds + k, ws + k);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
+    // thread -> (sub-transform, position)
+    const int sub = COLS ? (tid & 15) : (tid / TPS);
+    const int j = COLS ? (tid >> 4) : (tid % TPS);
+    // the inverse row pass starts with round B, whose 16 entries per thread
+    // are consecutive words: it reads them straight into registers and stages
+    // round B's twiddles at once, in the buffer the tile would otherwise take
+    constexpr bool direct_b = !FWD && !COLS;
     // row pass, round B's twiddles: group j G + g of row `sub` stored at g TPS + j,
-    // stage s at 16 (2^s - 16); called once the tile is in registers
-    auto stage_b = [&]() {
-        if (COLS) return;
-        __syncthreads();  // every thread has read its entries of the tile
+    // stage s at 16 (2^s - 16)
+    auto issue_b = [&]() {
         const size_t r0 = (size_t)blockIdx.x * 16;
         constexpr int LT = LOGM - 4;  // log2 TPS
 #pragma unroll
@@ -223,15 +203,56 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC), 3) k_ntt(Rows rows,
                 cp_async16(ds + (sub_k << s) + (g << LT) + jj, ws + k);
             }
         }
+    };
+    u64 v[16];
+    if (COLS) {
+        const int c0 = blockIdx.x * 16;
+#pragma unroll 4
+        for (int idx = tid; idx < 8 * M; idx += M) {  // row r of the tile: 16 words at xin[r C + c0]
+            int r = idx >> 3, h = idx & 7;
+            cp_async16(sm + r * 16 + 2 * h, xin + (size_t)r * C + c0 + 2 * h);
+        }
+        if (tid + 1 < M) cp_async16(stw + tid, W + tid + 1);
+    } else {
+        const u64 *xr = xin + (size_t)blockIdx.x * 16 * C;
+        if (!direct_b) {
+#pragma unroll 4
+            for (int idx = tid; idx < 8 * M; idx += M) {
+                int a = 2 * idx;
+                cp_async16(sm + a + 2 * (a >> 4), xr + a);
+            }
+        }
+        const size_t r0 = (size_t)blockIdx.x * 16;
+#pragma unroll
+        for (int s = 0; s < 4; s++) {  // round A: one group per thread group of a row (broadcast reads)
+            const ulonglong2 *ws = W + ((R + r0) << s);
+            ulonglong2 *ds = stw + 16 * ((1 << s) - 1);
+            for (int k = tid; k < (16 << s); k += M) cp_async16(ds + k, ws + k);
+        }
+        if (direct_b) {
+            issue_b();
+            const ulonglong2 *p2 = reinterpret_cast<const ulonglong2 *>(xr + (size_t)sub * M + 16 * j);
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const ulonglong2 t2 = p2[i];
+                v[2 * i] = t2.x;
+                v[2 * i + 1] = t2.y;
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // forward row pass: round B's twiddles once the tile is in registers
+    auto stage_b = [&]() {
+        if (COLS || direct_b) return;
+        __syncthreads();  // every thread has read its entries of the tile
+        issue_b();
         cp_async_wait_all();
         __syncthreads();
     };
     auto release_b = [&]() {  // round B done with its twiddles: the tile may return
         if (!COLS) __syncthreads();
     };
-    // thread -> (sub-transform, position)
-    const int sub = COLS ? (tid & 15) : (tid / TPS);
-    const int j = COLS ? (tid >> 4) : (tid % TPS);
     auto twl = [&](int s, int grp) -> ulonglong2 {  // local stage s, group grp
         if (COLS) return stw[(1 << s) - 1 + grp];
         return stw[16 * ((1 << s) - 1) + (sub << s) + grp];
@@ -241,7 +262,6 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC), 3) k_ntt(Rows rows,
         if (COLS) return stw[(1 << s) - 1 + j * ((1 << s) / TPS) + g];
         return stwb[16 * ((1 << s) - 16) + (sub << s) + g * TPS + j];
     };
-    u64 v[16];
     auto round_a = [&]() {  // stages 0..3, entries j + TPS i
 #pragma unroll
         for (int st = 0; st < 4; st++) {
@@ -314,7 +334,7 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC), 3) k_ntt(Rows rows,
         release_b();
         store_b();
     } else {
-        load_b();
+        if (!direct_b) load_b();
         stage_b();
         round_b();
         release_b();
