@@ -75,6 +75,7 @@ class Sim:
         self.nq, self.log_n, self.boot = nq, log_n, boot
         self.ks = Counter()
         self.n_boot = 0
+        self.n_boot_const = 0             # of which constant bootstraps
 
     def mul(self, a, b):
         l = min(a, b)
@@ -145,6 +146,7 @@ class Sim:
         K, r, d = self.boot
         out = Sim(self.nq, self.log_n, self.boot).bootstrap(0)
         self.n_boot += 1
+        self.n_boot_const += 1
         L = self.nq - 3                   # raised 2 levels below the top
         self.ks[L] += self.log_n - 1 + 1  # trace, conjugation
         c = self._evalmod(L - 1, d, r)    # after the packing mask
@@ -222,7 +224,7 @@ def refresh_schedule(plan, qb, y_level, out, padded):
     return hr, yb
 
 
-def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
+def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None, detail=False):
     """Key switches per level and bootstraps of one CutMax (library circuit).
     qbits: bit sizes of the Q primes (default 40 each), for the number of
     rescales the range-scale multiplication x = kappa V takes."""
@@ -327,4 +329,6 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None):
         sq = sim.mul(sq, sq)
         F = sim.mul(F, sq)
     sim.mul(mcr(Y), F)
+    if detail:                            # (key switches, bootstraps, constant bootstraps among them)
+        return dict(sim.ks), sim.n_boot, sim.n_boot_const
     return dict(sim.ks), sim.n_boot

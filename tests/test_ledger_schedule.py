@@ -1,0 +1,49 @@
+"""The refresh schedule of the bootstrapped circuit (host logic, CPU).
+
+The library and the operation-count model pick, per iteration, whether to
+refresh h by a constant bootstrap and whether to bootstrap Y early, by
+playing every combination on the level bookkeeping.  Whatever they pick must
+cost no more (general bootstrap 2, constant 1) than making no optional
+refresh at all, and must leave every level non-negative.
+"""
+import pytest
+
+from paper_2509_08383_gb300 import ledger
+from paper_2509_08383_gb300 import plan as P
+from paper_2509_08383_gb300 import synth
+
+QB = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+BOOT = (14, 4, 31)
+
+
+@pytest.fixture(scope="module")
+def plan_boot():
+    n = 1000
+
+    def gen(i):
+        return synth.logits_heavy_tail(i, n=n, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+
+    return P.calibrate(lambda i: gen(1000 + i), 200, n, 1024, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
+                       tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True)
+
+
+def _cost(pl):
+    ks, nb, nc = ledger.cutmax_ledger(pl, len(QB), 11, boot=BOOT, qbits=QB, detail=True)
+    assert all(level >= 0 for level in ks)
+    return 2 * (nb - nc) + nc, nb, nc
+
+
+def test_schedule_costs_no_more_than_no_optional_refresh(plan_boot, monkeypatch):
+    chosen = _cost(plan_boot)
+    monkeypatch.setattr(ledger, "refresh_schedule",
+                        lambda plan, qb, y, out, padded: ([False] * plan.T, [False] * plan.T))
+    plain = _cost(plan_boot)
+    assert chosen[0] <= plain[0]
+    assert chosen[2] >= 1                                  # scalars do take the constant bootstrap
+
+
+def test_schedule_is_deterministic_and_sized(plan_boot):
+    out = ledger.Sim(len(QB), 11, BOOT).bootstrap(0)
+    a = ledger.refresh_schedule(plan_boot, QB, out, out, plan_boot.pad != 0)
+    b = ledger.refresh_schedule(plan_boot, QB, out, out, plan_boot.pad != 0)
+    assert a == b and len(a[0]) == len(a[1]) == plan_boot.T
