@@ -21,6 +21,14 @@ real messages:
              angles c <- 2c^2 - 1, giving sin(2 pi t/q0) ~ 2 pi (t/q0 - I).
   SlotToCoeff  slots <- (q0/(2 pi S)) V w', dense, BSGS, two levels dropped.
 The output encrypts the input message at a known scale.
+
+For a ciphertext whose slots all hold one complex value (the plaintext
+a + b X^(N/2), a scalar of the CutMax circuit), `bootstrap_const` replaces
+CoeffToSlot by the trace over the automorphisms X -> X^(5^k), k < N/2, which
+keeps exactly the coefficients of 1 and X^(N/2) of t, puts their real and
+imaginary parts into the two slot halves for one EvalMod, corrects the sine
+by one Taylor step of arcsin (a constant's value sits whole in coefficient 0),
+and puts the value back in every slot.
 """
 import math
 
@@ -51,6 +59,18 @@ def chebyshev_coeffs(f, d):
     c = np.array([2.0 / (d + 1) * np.sum(fx * np.cos(k * th)) for k in range(d + 1)])
     c[0] /= 2
     return c
+
+
+def trace(ctx, ct):
+    """Sum over k < N/2 of the automorphism X -> X^(5^k) applied to ct, as
+    the doubling sum x <- x + rot(x, 2^i), i < log2(N/2) (5 has order N/2 mod
+    2N).  Its plaintext is (N/2) (t_0 + t_(N/2) X^(N/2)): the orbit sum of any
+    other monomial vanishes at every root of X^N + 1."""
+    x, r = ct, 1
+    while r < ctx.n // 2:
+        x = ctx.add(x, ctx.rotate(x, r))
+        r *= 2
+    return x
 
 
 def evalmod_function(K, r):
@@ -171,3 +191,40 @@ class Bootstrapper:
         # ratio times larger reads the message
         out.set_scale(out.scale * ratio)
         return out
+
+    def gen_const_keys(self):
+        """Rotation keys of the trace (1, 2, ..., N/4)."""
+        r = 1
+        while r < self.h:
+            self.ctx.gen_rot_key(r)
+            r *= 2
+
+    def bootstrap_const(self, ct):
+        """Refresh of one complex value in every slot; output at out_level()
+        and at the input's scale."""
+        ctx, he = self.ctx, self.he
+        q0 = ctx.primes[0]
+        ratio = ct.scale / self.s_fix
+        low = ctx.drop(ct, 0) if ct.level else ct
+        up = ctx.mod_raise(low, ctx.nq - 3)
+        up.set_scale(q0 * (self.K + 1))
+        x = trace(ctx, up)
+        x.set_scale(x.scale * self.h)           # slots: (t_0 + i t_(N/2)) / (q0 (K+1))
+        xc = ctx.conj(x)
+        re = ctx.add(x, xc)
+        re.set_scale(2 * re.scale)
+        im = ctx.mul_monomial(ctx.sub(x, xc), 3 * ctx.n // 2)
+        im.set_scale(2 * im.scale)
+        half = self.h // 2
+        lo = np.concatenate([np.ones(half), np.zeros(half)])
+        y = ctx.add(he.mul_plain_rescale(re, lo, self.target), he.mul_plain_rescale(im, 1.0 - lo, self.target))
+        y = self.evalmod(y)                     # sin(theta), theta = 2 pi m / q0
+        y2 = he.mul_rescale(y, y)
+        y2.set_scale(6 * y2.scale)
+        y = he.mul_rescale(y, he.add_const(y2, 1.0))   # arcsin to third order
+        w = ctx.add(y, ctx.mul_monomial(ctx.rotate(y, half), ctx.n // 2))
+        w = he.mul_plain_rescale(w, lo, q0 / (2 * np.pi))
+        w = ctx.add(w, ctx.rotate(w, half))
+        w.set_scale(w.scale * 2 * np.pi * self.s_fix / q0 * ratio)
+        out = self.out_level()
+        return ctx.drop(w, out) if w.level > out else w

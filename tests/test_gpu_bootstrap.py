@@ -154,3 +154,24 @@ def test_bootstrap_reads_message_at_any_input_scale(boot_pair, scale_ratio):
     val = 0.4 + 0.1j
     bc = g.bootstrap_const(g.encrypt(np.full(g.slots, val), scale, 32, level=0))
     assert np.abs(g.decrypt(bc, complex_out=True) - val).max() < 1e-6
+
+
+def test_constant_bootstrap_matches_oracle(boot_pair):
+    """GPU and oracle constant bootstraps of the same ciphertext (bit-identical
+    inputs) both return the value, to each other's precision."""
+    g, o, ob = boot_pair
+    g.gen_rot_keys([1 << i for i in range(LOG_N - 1)])
+    ob.gen_const_keys()
+    delta = 2.0 ** 40
+    val = 0.45 + 0.2j
+    pt = oenc.encode(np.full(g.slots, val), LOG_N, delta)
+    cg = g.encrypt_poly(pt, delta, 41, level=0)
+    co = o.encrypt(pt, delta, 41, level=0)
+    assert (cg.export() == co.export()).all()
+    bg = g.bootstrap_const(cg)
+    bo = ob.bootstrap_const(co)
+    assert bg.level == bo.level
+    dg = g.decrypt(bg, complex_out=True)
+    do = oenc.decode(o.decrypt(bo), LOG_N, bo.scale)
+    assert np.abs(dg - val).max() < 1e-6 and np.abs(do - val).max() < 1e-6
+    assert np.abs(dg - do).max() < 1e-6
