@@ -921,7 +921,7 @@ Ct bootstrap_const(he_ctx *cx, const he_ct *in) {
 // combination is played on the circuit's level bookkeeping (integer multipliers
 // sized from the primes' bit lengths, as the rescale rule does) and the one
 // costing least (general 2, constant 1; then fewer bootstraps; then the first)
-// is kept.
+// is kept.  Plans of more than 16 iterations make no optional refresh.
 struct RefreshSched {
     std::vector<uint8_t> h_refresh, y_boot;
 };
@@ -934,6 +934,7 @@ static RefreshSched refresh_schedule(he_ctx *cx, const Plan &pl, int y_level, in
         return a - r;
     };
     const int T = pl.T, per = T <= 6 ? 4 : 2;  // choices per iteration (early Y bootstraps only up to T = 6)
+    if (T > 16) return RefreshSched{std::vector<uint8_t>(T, 0), std::vector<uint8_t>(T, 0)};  // no search
     long total = 1;
     for (int t = 0; t < T; t++) total *= per;
     long best = -1;

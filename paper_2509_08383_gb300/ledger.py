@@ -162,8 +162,10 @@ def refresh_schedule(plan, qb, y_level, out, padded):
     scalar chains: per iteration, (refresh h by a constant bootstrap when it
     sits below D', bootstrap Y early), the combination of least cost (general
     bootstrap 2, constant 1; then fewer bootstraps; then the first) on the
-    circuit's level bookkeeping."""
+    circuit's level bookkeeping (plans of more than 16 iterations: none)."""
     T = plan.T
+    if T > 16:                            # no search: no optional refresh
+        return [False] * T, [False] * T
     per = 4 if T <= 6 else 2
 
     def mcr_bits_level(a, c):
