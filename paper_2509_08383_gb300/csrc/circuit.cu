@@ -999,8 +999,9 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     // would shrink the scale
     const int out_level = boot_out_level(cx);
     Ct Y = in->level > out_level ? op_drop(cx, in, out_level) : op_copy(cx, in);
-    // Goldschmidt pair packed in one ciphertext per stream: slots [0, s/2) hold
-    // g, slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
+    // shared scalar chains: the Goldschmidt pair packed in one ciphertext,
+    // slots [0, s/2) holding g, slots [s/2, s) h; one rotation by s/2 lines
+    // them up for g*h (per-stream chains carry it as one complex constant)
     const int half = slots / 2;
     const u64 g_half = rot_galois(cx, half);
     // scalar chains shared by the batch's streams: stream s owns the slots
