@@ -126,6 +126,13 @@ def philox(ctr, key):
     return out
 
 
+def gauss_cdt(sigma):
+    """The sampler's 19 thresholds: floor(2^64 P(|e| <= k)), k = 0..18."""
+    out = np.zeros(19, dtype=np.uint64)
+    lib().or_gauss_cdt(float(sigma), out)
+    return out
+
+
 def sample_secret(seed, log_n, h):
     out = np.zeros(1 << log_n, dtype=np.int8)
     lib().or_sample_secret(seed, log_n, h, out)

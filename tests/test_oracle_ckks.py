@@ -107,6 +107,78 @@ def test_philox_bijective_and_uniform():
         assert 30 < flips < 98
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = []
+    with open(path) as f:
+        for ln in f:
+            ln = ln.split("#")[0].split()
+            if ln:
+                rows.append(ln)
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the published known-answer vectors of Salmon et
+    al. (SC'11, Random123): a wrong multiplier, Weyl constant, round count or
+    word order fails at least one of them."""
+    rows = _golden("philox_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(v, 16) for v in r]
+        ctr, key, want = w[0:4], w[4:6], w[6:10]
+        assert [int(v) for v in ckks.philox(ctr, key)] == want
+
+
+def _discrete_gauss_cdf(sigma, bound=19):
+    """P(|e| <= k), k = 0..bound-1, of the discrete Gaussian
+    rho(x) = exp(-x^2 / (2 sigma^2)) on the integers |x| <= bound, 60 digits."""
+    import mpmath
+    mpmath.mp.dps = 60
+    rho = [mpmath.exp(-mpmath.mpf(k) ** 2 / (2 * mpmath.mpf(sigma) ** 2)) for k in range(bound + 1)]
+    z = rho[0] + 2 * sum(rho[1:])
+    out, acc = [], mpmath.mpf(0)
+    for k in range(bound):
+        acc += rho[k] if k == 0 else 2 * rho[k]
+        out.append(acc / z)
+    return out
+
+
+def test_gaussian_cdt_is_the_discrete_gaussian():
+    """The error sampler's thresholds are floor(2^64 P(|e| <= k)) of the
+    discrete Gaussian of width 3.2 truncated to |e| <= 19, up to float64
+    accumulation (a relative 7e-15).  A rounded continuous Gaussian differs by
+    ~6e-4 in P(e = 0), a dropped factor 2 or a wrong width by far more."""
+    import mpmath
+    cdt = ckks.gauss_cdt(3.2)
+    cdf = _discrete_gauss_cdf(3.2)
+    for k in range(19):
+        exact = int(mpmath.floor(cdf[k] * mpmath.mpf(2) ** 64))
+        assert abs(int(cdt[k]) - exact) <= 1 << 17, k
+    # the continuous Gaussian rounded to the nearest integer is a different table
+    cont0 = mpmath.erf(mpmath.mpf(0.5) / (mpmath.mpf(3.2) * mpmath.sqrt(2)))
+    assert abs(float(cdf[0]) - float(cont0)) > 5e-4
+
+
+def test_gaussian_sampler_maps_philox_words_through_the_table():
+    """Each error e_k takes one Philox block with counter (k, 0, object,
+    domain) under the seed's key: |e_k| = #{j : cdt_j <= word1:word0} and the
+    sign is bit 0 of word 2; recomputed here from the pinned Philox and the
+    exact mpmath thresholds."""
+    import mpmath
+    seed, obj, dom, log_n = 0x0123456789ABCDEF, 7, 2, 12
+    e = ckks.sample_gauss(seed, obj, dom, 3.2, log_n)
+    cdf = _discrete_gauss_cdf(3.2)
+    thr = [int(mpmath.floor(c * mpmath.mpf(2) ** 64)) for c in cdf]
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for k in range(1 << log_n):
+        w = [int(v) for v in ckks.philox([k, 0, obj, dom], key)]
+        u = (w[1] << 32) | w[0]
+        mag = sum(1 for t in thr if t <= u)
+        assert int(e[k]) == (-mag if w[2] & 1 else mag)
+
+
 def test_secret_distributions():
     s = ckks.sample_secret(11, 14, 0)
     counts = np.bincount(s.astype(np.int64) + 1, minlength=3) / len(s)
