@@ -430,7 +430,8 @@ def run_cfg5(args):
     p = 0.95 (one batch per p, alpha = ln(1-p)/ln(p)).  Per token the client
     encrypts each stream's logits (regenerated from the seed: N(0, 2^2), top
     gap 0.5) and uniforms U; the server draws G = U^(1/alpha) from them
-    (he_beta_noise) and samples CutMax(X + G) with bootstrapping and shared
+    (nucleus_sample with HE_RAND_UNIFORM: alpha = ln(1-p)/ln(p) in the library,
+    degree-31 Chebyshev) and samples CutMax(X + G) with bootstrapping and shared
     scalar chains; the client decrypts and takes the argmax as the token.  The
     plain plan and the learned plan (learned inverse square root) run side by
     side.  Reported: tokens/s of the server work (CUDA events) and end to end,
@@ -439,7 +440,8 @@ def run_cfg5(args):
     from paper_2509_08383_gb300 import learned
     from paper_2509_08383_gb300 import plan as P
     from paper_2509_08383_gb300 import synth
-    n, per, slots, deg = 128256, 8, 1 << 15, 31
+    n, per, slots = 128256, 8, 1 << 15
+    deg = 31  # the library's HE_NUCLEUS_DEGREE (checked against he.HE_NUCLEUS_DEGREE below)
     ps = [0.9, 0.95]
     alphas = [math.log(1.0 - p) / math.log(p) for p in ps]
 
@@ -460,6 +462,7 @@ def run_cfg5(args):
     torch.cuda.set_device(0)
     g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=160 << 30)
     g.bootstrap_prepare(24, 4, 31)
+    assert he.HE_NUCLEUS_DEGREE == deg
     lpl, report = learned.learned_plan(g, plain, calib_kw, logged)
     lpl.shared = True
     stream = torch.cuda.current_stream()
@@ -486,7 +489,7 @@ def run_cfg5(args):
                     X, U = g.batch_pack(cts), g.batch_pack(uts)
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    Z = g.nucleus_sample(X, g.beta_noise(U, alpha, deg), pl)
+                    Z = g.nucleus_sample(X, U, pl, p, kind="uniform")
                     e1.record(stream)
                     torch.cuda.synchronize()
                     toks = []

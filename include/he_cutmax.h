@@ -178,6 +178,16 @@ int he_rotsum(he_ctx *ctx, const he_ct *a, uint32_t steps, he_ct **out);
 /* Hybrid key switch of a raw polynomial: host d[(level+1)*N] coefficient
  * form -> host out0/out1[(level+1)*N] coefficient form, with key g. */
 int he_keyswitch_raw(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out0, uint64_t *out1);
+/* ModDown of hybrid key switching alone: the rounded division
+ * out = round(acc / P) mod q_0..q_level of two polynomials given over the
+ * key-switching basis, P the product of the special primes.  Host
+ * acc0/acc1[(level+1+n_p)*N] in coefficient form (rows q_0..q_level, then
+ * p_0..p_(n_p-1), residues in [0, prime)) -> host out0/out1[(level+1)*N] in
+ * coefficient form.  Exact for every input, including x within one unit of
+ * +-P/2 (the float64 estimate of the rounding is replaced by an exact
+ * mixed-radix comparison where it cannot decide). */
+int he_moddown_raw(he_ctx *ctx, const uint64_t *acc0, const uint64_t *acc1, uint32_t level, uint64_t *out0,
+                   uint64_t *out1);
 /* Key switch that allocates nothing, for callers that cannot allocate device
  * memory on demand: cudaMalloc/cudaFree synchronise the device and can fail
  * under fragmentation, so latency-critical serving code, or a process whose
@@ -192,7 +202,10 @@ int he_keyswitch_raw(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g,
  * call on a device looks the array's address up (cudaGetSymbolAddress with
  * that device current), so make that first call before any stream capture.
  * All calls share the array and nothing in it needs clearing (every word is
- * written before it is read); calls whose GPU work overlaps race on it. */
+ * written before it is read); calls whose GPU work overlaps race on it.
+ * During the call the context's own key-switch scratch is pointed at the
+ * array (and restored before return), so no other host thread may use the
+ * same context meanwhile (contexts are not thread-safe in any case). */
 int he_keyswitch_noalloc(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out);
 /* Negacyclic NTT (inverse != 0: INTT) in place on DEVICE data[n_limbs][N];
  * limb t uses prime prime_idx0 + t.  NTT form: position i holds
@@ -301,9 +314,6 @@ int he_cutmax_prepare(he_ctx *ctx, const he_cutmax_plan *plan);
  * stream-major; every step then runs once for the whole batch, and the
  * output is the batch of the streams' results in the same order. */
 int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out);
-/* Nucleus one-shot sampling (Alg. 3): out = CutMax(logits + rand_ct), where
- * rand_ct encrypts the cut noise G_i = U_i^(1/alpha), alpha = ln(1-q)/ln(p)
- * (Lemma 2 / Observation 1), drawn and encrypted by the client. */
 /* Cut noise drawn by the server from encrypted uniforms (Alg. 3 with
  * Lemma 2 / Observation 1): out = G = U^(1/alpha) slot by slot, U in [0, 1]
  * encrypted by the client, by the degree-`degree` Chebyshev interpolant of
@@ -312,8 +322,27 @@ int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out
  * cannot follow the cusp of U^(1/alpha) at U = 0.  HE_EINVAL for alpha <= 0 or
  * degree outside 2..127.  Works on batches. */
 int he_beta_noise(he_ctx *ctx, const he_ct *u, double alpha, uint32_t degree, he_ct **out);
-int nucleus_sample(he_ctx *ctx, const he_ct *logits, const he_ct *rand_ct,
-                   const he_cutmax_plan *plan, he_ct **out);
+
+/* Kinds of the randomness handed to nucleus_sample. */
+#define HE_RAND_BETA 0    /* rand_ct encrypts the cut noise G = U^(1/alpha) itself (client-side draw) */
+#define HE_RAND_UNIFORM 1 /* rand_ct encrypts uniforms U in [0, 1]; the library evaluates G = U^(1/alpha) */
+/* Chebyshev degree of the library's U^(1/alpha) for HE_RAND_UNIFORM (7 levels) */
+#define HE_NUCLEUS_DEGREE 31
+
+/* Nucleus one-shot sampling (Alg. 3, Sect. 3.3): out = CutMax(logits + G),
+ * an encrypted near-one-hot vector at the sampled token, where G_i are
+ * Beta(alpha, 1) cut variables with alpha = ln(1-q)/ln(top_p), so that
+ * P(G_i > top_p) = q (Lemma 2 for q = top_p, Observation 1 for any q); q = 0
+ * reads as q = top_p.  rand_kind HE_RAND_BETA: rand_ct already encrypts G
+ * (drawn by the client for this top_p and q; 0 levels).  HE_RAND_UNIFORM:
+ * rand_ct encrypts uniforms U and the library evaluates G = U^(1/alpha) by
+ * he_beta_noise of degree HE_NUCLEUS_DEGREE (7 levels, taken from rand_ct's
+ * level before the addition).  logits and rand_ct follow the layout of the
+ * plan (one ciphertext or a batch, as for cutmax) and must share one scale.
+ * HE_EINVAL for top_p outside (0, 1), q outside [0, 1), an unknown kind or
+ * operands of different scales. */
+int nucleus_sample(he_ctx *ctx, const he_ct *logits, double top_p, double q, const he_ct *rand_ct,
+                   int32_t rand_kind, const he_cutmax_plan *plan, he_ct **out);
 
 #ifdef __cplusplus
 }

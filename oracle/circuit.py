@@ -282,6 +282,65 @@ def cutmax_he_boot(he, ct, plan, boot):
     return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
 
 
-def nucleus_he(he, ct_logits, ct_noise, plan):
-    """Alg. 3: X~ = X + G (G = U^(1/alpha) supplied encrypted), then CutMax."""
-    return cutmax_he(he, he.ctx.add(ct_logits, ct_noise), plan)
+def chebyshev_interpolant(f, d):
+    """c_0..c_d with f(t) ~ sum_k c_k T_k(t) on [-1, 1]: the interpolant of f
+    at the d + 1 Chebyshev nodes t_j = cos(pi (j + 1/2) / (d + 1)), whose
+    coefficients follow from the discrete orthogonality of T_0..T_d there."""
+    j = np.arange(d + 1)
+    th = np.pi * (j + 0.5) / (d + 1)
+    fx = f(np.cos(th))
+    c = np.array([2.0 / (d + 1) * np.sum(fx * np.cos(k * th)) for k in range(d + 1)])
+    c[0] /= 2
+    return c
+
+
+def chebyshev_sum(he, x, c, target):
+    """sum_k c_k T_k(x) of a ciphertext whose slots lie in [-1, 1]: every T_k
+    by T_(a+b) = 2 T_a T_b - T_(a-b) with a = ceil(k/2), b = floor(k/2)
+    (depth ceil(log2 k)), each term c_k T_k multiplied towards `target`, the
+    terms summed on the lowest level, then c_0 added."""
+    ctx = he.ctx
+    T = {1: x}
+    for k in range(2, len(c)):
+        a, b = (k + 1) // 2, k // 2
+        P2 = ctx.mul_int(he.mul_rescale(T[a], T[b]), 2)
+        if a == b:
+            T[k] = he.add_const(P2, -1.0)
+        else:
+            xm = he.mcr(T[1], 1.0, P2.scale)
+            T[k] = ctx.sub(P2, ctx.drop(xm, P2.level) if xm.level > P2.level else xm)
+    terms = [he.mcr(T[k], float(c[k]), target) for k in range(1, len(c)) if c[k] != 0.0]
+    low = min(t.level for t in terms)
+    acc = None
+    for t in terms:
+        t = ctx.drop(t, low) if t.level > low else t
+        acc = t if acc is None else ctx.add(acc, t)
+    return he.add_const(acc, float(c[0]))
+
+
+def beta_noise_he(he, u, alpha, d):
+    """Alg. 3's cut noise G = U^(1/alpha) (the inverse CDF of Beta(alpha, 1),
+    Lemma 2 / Observation 1) evaluated on encrypted uniforms U in [0, 1]:
+    t = 2U - 1, then the degree-d Chebyshev interpolant of ((t + 1)/2)^(1/alpha)."""
+    if not alpha > 0 or not 2 <= d <= 127:
+        raise ValueError("alpha must be positive and the degree in 2..127")
+    c = chebyshev_interpolant(lambda t: ((t + 1.0) / 2.0) ** (1.0 / alpha), d)
+    t = he.add_const(he.mcr(u, 2.0), -1.0)
+    return chebyshev_sum(he, t, c, he.delta)
+
+
+def nucleus_alpha(top_p, q=0.0):
+    """alpha = ln(1 - q) / ln(p), so that P(G > p) = q for G ~ Beta(alpha, 1)
+    (Lemma 2 with q = p, Observation 1 for any q; q = 0 reads as q = p)."""
+    q = top_p if not q else q
+    return math.log(1.0 - q) / math.log(top_p)
+
+
+def nucleus_he(he, ct_logits, ct_rand, plan, top_p=None, q=0.0, kind="beta", degree=31):
+    """Alg. 3: X~ = X + G, then CutMax.  kind "beta": ct_rand encrypts G
+    itself; "uniform": ct_rand encrypts uniforms U and G = U^(1/alpha) is
+    evaluated here (beta_noise_he, alpha from top_p and q)."""
+    G = ct_rand
+    if kind == "uniform":
+        G = beta_noise_he(he, ct_rand, nucleus_alpha(top_p, q), degree)
+    return cutmax_he(he, he.ctx.add(ct_logits, G), plan)

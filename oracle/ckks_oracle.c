@@ -546,6 +546,7 @@ static void enc_body(void *vp, int i) {
 }
 
 or_ct *or_encrypt(or_ctx *cx, const double *m, double scale, u32 ctr, int level) {
+    if (level < 0 || level >= cx->nq) return NULL;  /* no such level: the caller raises */
     u64 n = cx->n;
     or_ct *ct = or_ct_new(cx, level, scale);
     u64 cdt[GAUSS_BOUND]; or_gauss_cdt(cx->sigma, cdt);

@@ -393,6 +393,25 @@ int he_keyswitch_raw(he_ctx *cx, const uint64_t *d, uint32_t level, uint64_t g, 
     API_CATCH(cx)
 }
 
+int he_moddown_raw(he_ctx *cx, const uint64_t *acc0, const uint64_t *acc1, uint32_t level, uint64_t *out0,
+                   uint64_t *out1) {
+    if (!cx || !acc0 || !acc1 || !out0 || !out1) return HE_EINVAL;
+    API_TRY
+    need((int)level < cx->nq, "level out of range");
+    const int l = (int)level, ne = cx->lv[l].n_ext;
+    const size_t N = cx->N(), m = (size_t)(l + 1) * N, me = (size_t)ne * N;
+    check_cuda(cudaMemcpyAsync(cx->ks_acc, acc0, me * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    check_cuda(cudaMemcpyAsync(cx->ks_acc + me, acc1, me * 8, cudaMemcpyHostToDevice, cx->stream), "H2D");
+    ntt_forward(make_rows(cx->ks_acc, me, ne, l + 1, cx->nq), 2 * ne, cx->tw, cx->log_n, cx->stream);
+    Rows o = make_rows(cx->sc_b, m, l + 1, l + 1, cx->nq);
+    moddown(cx, cx->ks_acc, l, o, o, 0);
+    ntt_inverse(o, 2 * (l + 1), cx->tw, cx->log_n, cx->stream);
+    check_cuda(cudaMemcpyAsync(out0, cx->sc_b, m * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    check_cuda(cudaMemcpyAsync(out1, cx->sc_b + m, m * 8, cudaMemcpyDeviceToHost, cx->stream), "D2H");
+    sync(cx, "moddown");
+    API_CATCH(cx)
+}
+
 int he_ntt_device(he_ctx *cx, uint64_t *data, uint32_t n_limbs, uint32_t prime_idx0, int32_t inverse) {
     if (!cx || !data) return HE_EINVAL;
     API_TRY
@@ -485,13 +504,22 @@ int he_beta_noise(he_ctx *cx, const he_ct *u, double alpha, uint32_t degree, he_
     API_CATCH(cx)
 }
 
-int nucleus_sample(he_ctx *cx, const he_ct *logits, const he_ct *rand_ct, const he_cutmax_plan *plan, he_ct **out) {
+int nucleus_sample(he_ctx *cx, const he_ct *logits, double top_p, double q, const he_ct *rand_ct, int32_t rand_kind,
+                   const he_cutmax_plan *plan, he_ct **out) {
     if (!cx || !logits || !rand_ct || !out) return HE_EINVAL;
     API_TRY
     own(cx, logits);
     own(cx, rand_ct);
+    need(top_p > 0.0 && top_p < 1.0, "top-p mass must lie in (0, 1)");
+    need(q >= 0.0 && q < 1.0, "q must lie in [0, 1) (0: q = top_p)");
+    need(rand_kind == HE_RAND_BETA || rand_kind == HE_RAND_UNIFORM, "unknown noise kind");
+    const double qq = q > 0.0 ? q : top_p;
+    const double alpha = std::log(1.0 - qq) / std::log(top_p);  // Lemma 2 / Observation 1
+    need(std::isfinite(alpha) && alpha > 0.0, "alpha = ln(1-q)/ln(p) must be positive");
     Plan pl = plan_from(plan);
-    Ct x = op_add(cx, logits, rand_ct, false);
+    Ct g;
+    if (rand_kind == HE_RAND_UNIFORM) g = beta_noise(cx, rand_ct, alpha, HE_NUCLEUS_DEGREE);
+    Ct x = op_add(cx, logits, g ? g.get() : rand_ct, false);
     Ct r = cutmax_ct(cx, x.get(), pl);
     launched(cx, "nucleus_sample");
     *out = r.release();

@@ -445,6 +445,22 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
         for (int b = 0; b < K; b++) P = mulmod_host(P, cx->primes[cx->nq + b] % q, q);
         tab.push_back((u64)(((u128)((q - P) % q) << 64) % q));
     }
+    // exact rounding where the float64 estimate cannot decide: p_j^-1 mod p_i
+    // (j < i) and the mixed-radix digits of (P-1)/2, whose residue mod p_i is
+    // (p_i - 1)/2 (twice it is P - 1 = -1 mod p_i)
+    size_t md_mrinv = tab.size();
+    for (int i = 0; i < K; i++)
+        for (int j = 0; j < K; j++) {
+            u64 pi = cx->primes[cx->nq + i];
+            tab.push_back(j < i ? invmod_host(cx->primes[cx->nq + j] % pi, pi) : 0);
+        }
+    size_t md_half = tab.size();
+    for (int i = 0; i < K; i++) {
+        u64 pi = cx->primes[cx->nq + i], t = (pi - 1) / 2;
+        for (int j = 0; j < i; j++)
+            t = mulmod_host((t + pi - tab[md_half + j] % pi) % pi, tab[md_mrinv + (size_t)i * K + j], pi);
+        tab.push_back(t);
+    }
     memset(&cx->p_inv, 0, sizeof(cx->p_inv));
     memset(&cx->p_mod, 0, sizeof(cx->p_mod));
     for (int i = 0; i < cx->nq; i++) {
@@ -482,6 +498,8 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     cx->moddown.stride = cx->nq;
     cx->moddown.inv_q = reinterpret_cast<const double *>(cx->d_tabs + md_inv);
     cx->moddown.negq_mont = cx->d_tabs + md_negp;
+    cx->moddown.mr_inv = cx->d_tabs + md_mrinv;
+    cx->moddown.mr_half = cx->d_tabs + md_half;
 
     // secret
     make_secret(cx);
@@ -613,8 +631,19 @@ Ct op_copy(he_ctx *cx, const he_ct *a) {
     return out;
 }
 
+// Operands of an addition must encrypt their messages at one scale: the sum
+// of m_a s_a and m_b s_b read at s_a is m_a + m_b s_b / s_a.  Scales that the
+// circuits line up agree to float64 rounding (~1e-15 relative); 1e-9 leaves
+// room for that and rejects a ciphertext one rescale apart (~1e-5 and more).
+static void same_scale(const he_ct *a, const he_ct *b) {
+    if (!(std::fabs(a->scale - b->scale) <= 1e-9 * std::fabs(a->scale)))
+        throw Error{HE_EINVAL, "operands of an addition have different scales (" + std::to_string(a->scale) +
+                                   " and " + std::to_string(b->scale) + ")"};
+}
+
 Ct op_add(he_ctx *cx, const he_ct *a, const he_ct *b, bool sub) {
     same_batch(a, b);
+    same_scale(a, b);
     int l = std::min(a->level, b->level);
     Ct out(ct_alloc(cx, l, a->scale, a->batch));
     ew_add(ct_rows(out.get()), ct_rows(a, l), ct_rows(b, l), nrows(a, l), sub ? 1 : 0, cx->log_n, cx->stream);

@@ -795,8 +795,12 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // Rounding mode (tab.inv_q set, used by ModDown): v = rint(sum_a y_a / q_a),
 // computed in double beside the integer sums, and out_t - v Q mod p_t is the
 // centred representative of x mod Q (|.| <= Q/2), so that ModDown's
-// (acc - out) / Q is the rounded division.  The double sum is off by a few
-// ulps of n_in, so only an x within ~1e-15 Q of +-Q/2 could round the other way.
+// (acc - out) / Q is the rounded division.  The double sum r is off by a few
+// ulps of n_in; where its fractional part lies within 1e-9 of 1/2 (x within
+// ~1e-9 Q of Q/2, a rare case) the decision is taken exactly instead: floor(r)
+// is still right, and whether x mod Q exceeds (Q-1)/2 follows from the
+// mixed-radix digits of x (Garner's algorithm), compared with those of
+// (Q-1)/2 from the most significant down.
 // One thread per (coefficient, chunk of BCONV_CHUNK output rows).  The
 // products y_a * w_a,t with w = qhat[a][t] 2^64 mod p_t are summed exactly in
 // a 128-bit accumulator of four 32-bit words (n_in <= 16 terms below 2^122
@@ -820,10 +824,29 @@ __device__ __forceinline__ void mac128_words(u32 &a0, u32 &a1, u32 &a2, u32 &a3,
         : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
         : "r"(y0), "r"(y1), "r"(w0), "r"(w1));
 }
+// 1 if the integer x with residues x_a = s_in[a][k] (a < n_in, primes
+// s_pidx[a]) exceeds (Q-1)/2 as an element of [0, Q), else 0: mixed-radix
+// digits m_i = (((x_i - m_0) q_0^-1 - m_1) q_1^-1 - ...) mod q_i, compared
+// from m_(n_in-1) down with the digits of (Q-1)/2.
+__device__ __noinline__ u32 bconv_above_half(const u64 *const *s_in, const int *s_pidx, size_t k, int n_in,
+                                             const BConvTab &tab, const PrimeConsts &pc) {
+    u64 m[BCONV_MAX_IN];
+    for (int i = 0; i < n_in; i++) {
+        const ModQ mi = pc.m[s_pidx[i]];
+        u64 t = s_in[i][k];
+        for (int j = 0; j < i; j++)
+            t = mul_mod(sub_mod(t, barrett_reduce(m[j], 0, mi), mi.q), tab.mr_inv[i * n_in + j], mi);
+        m[i] = t;
+    }
+    for (int i = n_in - 1; i >= 0; i--)
+        if (m[i] != tab.mr_half[i]) return m[i] > tab.mr_half[i] ? 1u : 0u;
+    return 0u;  // x = (Q-1)/2 itself rounds down
+}
 __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
     __shared__ uint2 s_w[BCONV_MAX_IN * BCONV_CHUNK];
     __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
     __shared__ const u64 *s_in[BCONV_MAX_IN];
+    __shared__ int s_pidx[BCONV_MAX_IN];
     __shared__ u64 *s_out[BCONV_CHUNK];
     __shared__ int s_p[BCONV_CHUNK];
     __shared__ double s_inv[BCONV_MAX_IN];
@@ -846,6 +869,7 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         s_qis[a] = ok ? tab.qhinv_sh[a] : 0;
         s_q[a] = ok ? pc.m[in.prime(poly * tab.n_in + a)].q : 1;
         s_in[a] = ok ? in.row(poly * tab.n_in + a, log_n) : nullptr;
+        s_pidx[a] = ok ? in.prime(poly * tab.n_in + a) : 0;
         s_inv[a] = ok && rnd ? tab.inv_q[a] : 0.0;
     }
     if (threadIdx.x < BCONV_CHUNK) {
@@ -875,7 +899,9 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         }
     }
     if (rnd) {  // + v (-Q): v <= n_in, one more term below 2^66
-        const u32 v = (u32)rint(r);
+        const double fl = floor(r), fr = r - fl;
+        u32 v = (u32)fl + (fr > 0.5 ? 1u : 0u);
+        if (fabs(fr - 0.5) < 1e-9) v = (u32)fl + bconv_above_half(s_in, s_pidx, k, tab.n_in, tab, pc);
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++)
             mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], v, 0u, s_wn[c].x, s_wn[c].y);

@@ -29,6 +29,11 @@ struct BConvTab {
     // [stride], Q the product of the input primes; null: approximate conversion
     const double *inv_q = nullptr;
     const u64 *negq_mont = nullptr;
+    // exact rounding where the float64 estimate cannot decide (x within
+    // ~1e-9 Q of Q/2): q_j^-1 mod q_i at [i*n_in + j] (j < i) and the
+    // mixed-radix digits of (Q-1)/2 [n_in]
+    const u64 *mr_inv = nullptr;
+    const u64 *mr_half = nullptr;
 };
 
 // number of kernels launched by this library so far (all contexts)

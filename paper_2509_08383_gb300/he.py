@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhecutmax.so")
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ELEVEL, HE_ERANGE, HE_ECUDA, HE_ETIMEOUT, HE_ENOKEY = range(8)
+HE_RAND_BETA, HE_RAND_UNIFORM = 0, 1
+HE_NUCLEUS_DEGREE = 31
 _NAMES = {0: "HE_OK", 1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ELEVEL", 4: "HE_ERANGE", 5: "HE_ECUDA",
           6: "HE_ETIMEOUT", 7: "HE_ENOKEY"}
 
@@ -95,6 +97,7 @@ def lib():
             "he_mul_monomial": [VP, VP, u64, PP],
             "he_rotsum": [VP, VP, u32, PP],
             "he_keyswitch_raw": [VP, pu64, u32, u64, pu64, pu64],
+            "he_moddown_raw": [VP, pu64, pu64, u32, pu64, pu64],
             "he_ntt_device": [VP, VP, u32, u32, i32],
             "he_keyswitch_noalloc": [VP, VP, u32, u64, VP],
             "he_bootstrap_prepare": [VP, u32, u32, u32],
@@ -104,7 +107,7 @@ def lib():
             "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
             "he_learn_invsqrt": [VP, C.POINTER(C.c_float), sz, u32, C.c_float, u64, pd, pd],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
-            "nucleus_sample": [VP, VP, VP, C.POINTER(CPlan), PP],
+            "nucleus_sample": [VP, VP, dbl, dbl, VP, i32, C.POINTER(CPlan), PP],
             "he_beta_noise": [VP, VP, dbl, u32, PP],
         }
         for name, args in sig.items():
@@ -370,6 +373,17 @@ class Context:
         self._chk(lib().he_keyswitch_raw(self.ptr, _u64ptr(d), int(level), int(g), _u64ptr(o0), _u64ptr(o1)))
         return o0.reshape(level + 1, self.n), o1.reshape(level + 1, self.n)
 
+    def moddown(self, acc0, acc1, level):
+        """round(acc / P) mod q_0..q_level of two polynomials given in coefficient
+        form over q_0..q_level, p_0..p_(K-1) ([(level+1+K)][N] each)."""
+        a0 = np.ascontiguousarray(acc0, dtype=np.uint64).reshape(-1)
+        a1 = np.ascontiguousarray(acc1, dtype=np.uint64).reshape(-1)
+        assert a0.size == a1.size == (level + 1 + self.np_) * self.n
+        o0 = np.zeros((level + 1) * self.n, dtype=np.uint64)
+        o1 = np.zeros_like(o0)
+        self._chk(lib().he_moddown_raw(self.ptr, _u64ptr(a0), _u64ptr(a1), int(level), _u64ptr(o0), _u64ptr(o1)))
+        return o0.reshape(level + 1, self.n), o1.reshape(level + 1, self.n)
+
     def keyswitch_noalloc(self, d_tensor, level, g, out_tensor):
         """Key switch on device tensors with the library's static scratch (no allocation):
         d (level+1, N) NTT form -> out (2, level+1, N) NTT form."""
@@ -421,6 +435,10 @@ class Context:
         """G = U^(1/alpha) of encrypted uniforms (Chebyshev interpolant)."""
         return self._ct(lib().he_beta_noise, u_ct.ptr, float(alpha), int(degree))
 
-    def nucleus_sample(self, ct, rand_ct, plan):
+    def nucleus_sample(self, ct, rand_ct, plan, top_p, q=0.0, kind="beta"):
+        """Alg. 3: CutMax(ct + G), P(G_i > top_p) = q (q = 0: q = top_p).  kind
+        "beta": rand_ct encrypts G itself; "uniform": rand_ct encrypts uniforms U
+        and the library evaluates G = U^(1/alpha)."""
         s, keep = plan_struct(plan)
-        return self._ct(lib().nucleus_sample, ct.ptr, rand_ct.ptr, C.byref(s))
+        k = {"beta": HE_RAND_BETA, "uniform": HE_RAND_UNIFORM}[kind]
+        return self._ct(lib().nucleus_sample, ct.ptr, float(top_p), float(q), rand_ct.ptr, k, C.byref(s))

@@ -175,6 +175,47 @@ def test_keyswitch_raw_bit_exact(small, level):
     assert (og[0] == oo[0]).all() and (og[1] == oo[1]).all()
 
 
+def _moddown_inputs(ctx, l, seed):
+    """Accumulators over q_0..q_l, p_0..p_(K-1) holding random x in
+    (-Q_l P/2, Q_l P/2) and, in polynomial 0, every x whose x / P lies closest
+    to a rounding boundary (x mod P = (P -+ 1)/2, near several multiples of P)."""
+    import math
+    import random
+    qs, ps = ctx.primes[: l + 1], ctx.primes[ctx.nq:]
+    P, M = math.prod(ps), math.prod(qs) * math.prod(ps)
+    rng = random.Random(seed)
+    edge = [0, 1, -1, (P - 1) // 2, (P + 1) // 2, -(P - 1) // 2, -(P + 1) // 2]
+    for _ in range(60):
+        k = rng.randrange(-math.prod(qs) // 2 + 1, math.prod(qs) // 2 - 1)
+        edge += [k * P + (P - 1) // 2, k * P + (P + 1) // 2, k * P - (P - 1) // 2, k * P - (P + 1) // 2]
+    xs0 = edge + [rng.randrange(-M // 2 + 1, M // 2) for _ in range(ctx.n - len(edge))]
+    xs1 = [rng.randrange(-M // 2 + 1, M // 2) for _ in range(ctx.n)]
+    rows = list(qs) + list(ps)
+    acc0 = np.array([[x % p for x in xs0] for p in rows], dtype=np.uint64)
+    acc1 = np.array([[x % p for x in xs1] for p in rows], dtype=np.uint64)
+    want = []
+    for xs in (xs0, xs1):
+        r = [(2 * x + P) // (2 * P) for x in xs]          # round(x / P); P odd: no ties
+        want.append(np.array([[v % q for v in r] for q in qs], dtype=np.uint64))
+    return acc0, acc1, want
+
+
+@pytest.mark.parametrize("pbits", [[60, 60, 61], [61] * 10])
+def test_moddown_exact_at_rounding_boundaries(pbits):
+    """ModDown is the rounded division by P on the GPU too, including the x
+    nearest to +-P/2, where the float64 estimate of the rounding cannot decide
+    and the exact mixed-radix comparison takes over; bit-exact to the oracle."""
+    qb = [60, 40, 40, 40]
+    g = he.Context(10, qb, pbits, dnum=2, seed=3, arena_bytes=256 << 20)
+    o = ock.Context(10, qb, pbits, dnum=2, seed=3)
+    for l in (0, 2, 3):
+        acc0, acc1, want = _moddown_inputs(o, l, 7 + l)
+        g0, g1 = g.moddown(acc0, acc1, l)
+        o0, o1 = o.moddown(acc0, acc1, l)
+        assert (g0 == want[0]).all() and (g1 == want[1]).all()
+        assert (o0 == g0).all() and (o1 == g1).all()
+
+
 def test_rescale_chain_to_zero(small):
     g, o = small
     rng = np.random.default_rng(6)
@@ -261,7 +302,8 @@ def test_cutmax_padded_packing():
 
 
 def test_nucleus_bit_exact():
-    """Alg. 3 with client-encrypted Beta(alpha,1) cut noise: bit-exact to the oracle."""
+    """Alg. 3 with client-encrypted Beta(alpha,1) cut noise (HE_RAND_BETA):
+    bit-exact to the oracle."""
     g, o = _circuit_pair(11, seed=8)
     pl = _cfg1_plan(g.slots)
     x = synth.logits_gaussian(3)
@@ -274,10 +316,71 @@ def test_nucleus_bit_exact():
     o.gen_relin_key()
     for r in required_rotations(pl):
         o.gen_rot_key(r)
-    zg = g.nucleus_sample(g.encrypt_poly(ptx, delta, 1), g.encrypt_poly(ptg, delta, 2), pl)
+    zg = g.nucleus_sample(g.encrypt_poly(ptx, delta, 1), g.encrypt_poly(ptg, delta, 2), pl, 0.9)
     zo = nucleus_he(HE(o, delta), o.encrypt(ptx, delta, 1), o.encrypt(ptg, delta, 2), pl)
     assert (zg.export() == zo.export()).all()
     assert np.argmax(g.decrypt(zg, pl.n)) == np.argmax(x + G)
+
+
+@pytest.mark.parametrize("top_p,q", [(0.9, 0.0), (0.95, 0.9)])
+def test_nucleus_uniform_noise_matches_oracle(top_p, q):
+    """Alg. 3 with the cut noise drawn by the server (HE_RAND_UNIFORM): the
+    library takes alpha = ln(1-q)/ln(p) (Lemma 2 / Observation 1) and evaluates
+    G = U^(1/alpha) on the encrypted uniforms, then CutMax(X + G).  The oracle
+    runs the same steps with its own Chebyshev evaluation (each T_k by
+    recurrence), so the ciphertexts differ in rounding: the noise agrees within
+    1e-5, the sample within 1e-3, and the argmax is the one of x + the noise
+    polynomial in float64."""
+    from oracle.circuit import beta_noise_he, chebyshev_interpolant, nucleus_alpha
+    qb, pb = [60] + [40] * 28, [60, 60, 60]
+    g, o = pair(11, qb, pb, dnum=10, seed=12)
+    pl = _cfg1_plan(g.slots)
+    x = synth.logits_gaussian(21)
+    u = synth.uniforms(21, pl.n)
+    delta = 2.0 ** 40
+    ptx = oenc.encode(P.pack(x, g.slots, pl.packing), g.log_n, delta)
+    ptu = oenc.encode(P.pack(u, g.slots, pl.packing), g.log_n, delta)
+    g.cutmax_prepare(pl)
+    o.gen_relin_key()
+    for r in required_rotations(pl):
+        o.gen_rot_key(r)
+    xg, ug = g.encrypt_poly(ptx, delta, 1), g.encrypt_poly(ptu, delta, 2)
+    xo, uo = o.encrypt(ptx, delta, 1), o.encrypt(ptu, delta, 2)
+    alpha = nucleus_alpha(top_p, q)
+    Gg = g.decrypt(g.beta_noise(ug, alpha, he.HE_NUCLEUS_DEGREE), pl.n)
+    Go_ct = beta_noise_he(HE(o, delta), uo, alpha, he.HE_NUCLEUS_DEGREE)
+    Go = oenc.decode(o.decrypt(Go_ct), g.log_n, Go_ct.scale).real[: pl.n]
+    assert np.abs(Gg - Go).max() < 1e-5
+    zg = g.nucleus_sample(xg, ug, pl, top_p, q, kind="uniform")
+    zo = nucleus_he(HE(o, delta), xo, uo, pl, top_p, q, kind="uniform", degree=he.HE_NUCLEUS_DEGREE)
+    assert zg.level == zo.level and zg.scale == pytest.approx(zo.scale, rel=1e-12)
+    dg = g.decrypt(zg, pl.n)
+    do = oenc.decode(o.decrypt(zo), g.log_n, zo.scale).real[: pl.n]
+    assert np.abs(dg - do).max() < 1e-3
+    c = chebyshev_interpolant(lambda t: ((t + 1) / 2) ** (1 / alpha), he.HE_NUCLEUS_DEGREE)
+    want = int(np.argmax(x + np.polynomial.chebyshev.chebval(2 * u - 1, c)))
+    assert int(np.argmax(dg)) == int(np.argmax(do)) == want
+
+
+def test_nucleus_and_add_reject_bad_arguments(small):
+    """Top-p mass outside (0, 1), an unknown noise kind and operands of
+    different scales are HE_EINVAL (an addition of mismatched scales would
+    silently change the message)."""
+    g, _ = small
+    rng = np.random.default_rng(9)
+    a = g.encrypt(rng.normal(size=g.slots), 2.0 ** 40, 31)
+    b = g.encrypt(rng.normal(size=g.slots), 2.0 ** 40 * (1 + 1e-6), 32)
+    with pytest.raises(he.HeError) as ei:
+        g.add(a, b)
+    assert ei.value.code == he.HE_EINVAL
+    pl = _cfg1_plan(g.slots)
+    for top_p, q in ((1.0, 0.0), (0.0, 0.0), (0.9, 1.0)):
+        with pytest.raises(he.HeError) as ei:
+            g.nucleus_sample(a, a, pl, top_p, q)
+        assert ei.value.code == he.HE_EINVAL
+    with pytest.raises(he.HeError) as ei:
+        g.nucleus_sample(a, b, pl, 0.9)
+    assert ei.value.code == he.HE_EINVAL
 
 
 def test_circuit_too_deep_is_an_error():

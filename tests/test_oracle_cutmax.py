@@ -208,3 +208,47 @@ def test_encrypted_circuit_on_oracle(packing_slots):
     ref = F.cutmax_circuit(x, pl)
     assert np.abs(dec - ref).max() < 1e-3
     assert np.argmax(dec) == np.argmax(x)
+
+
+def test_chebyshev_interpolant_definition():
+    """The interpolant passes through f at the d + 1 Chebyshev nodes, and a
+    polynomial of degree <= d is reproduced exactly (T_3 -> e_3); numpy's
+    Chebyshev fit at the same nodes gives the same coefficients."""
+    from oracle.circuit import chebyshev_interpolant
+    d = 15
+    f = lambda t: np.exp(0.7 * t) / (2.0 + t)
+    c = chebyshev_interpolant(f, d)
+    nodes = np.cos(np.pi * (np.arange(d + 1) + 0.5) / (d + 1))
+    assert np.abs(np.polynomial.chebyshev.chebval(nodes, c) - f(nodes)).max() < 1e-13
+    assert np.abs(c - np.polynomial.chebyshev.chebfit(nodes, f(nodes), d)).max() < 1e-12
+    e3 = chebyshev_interpolant(lambda t: 4 * t ** 3 - 3 * t, d)
+    assert np.abs(e3 - np.eye(d + 1)[3]).max() < 1e-14
+
+
+@pytest.mark.slow
+def test_beta_noise_on_oracle_ciphertexts():
+    """Alg. 3's cut noise G = U^(1/alpha) evaluated on oracle ciphertexts of
+    uniforms (Lemma 2 / Observation 1): its decryption equals the degree-31
+    Chebyshev series evaluated in float64 (up to CKKS noise) and U^(1/alpha)
+    within the interpolation error for U >= 1e-2; 7 levels are spent."""
+    from oracle import ckks
+    from oracle import encoding as enc
+    from oracle.circuit import HE, beta_noise_he, chebyshev_interpolant, nucleus_alpha
+    log_n, delta, d = 10, 2.0 ** 40, 31
+    ctx = ckks.Context(log_n, [60] + [40] * 8, [60, 60], dnum=3, seed=5)
+    ctx.gen_relin_key()
+    he = HE(ctx, delta)
+    alpha = nucleus_alpha(0.9)
+    assert alpha == pytest.approx(math.log(0.1) / math.log(0.9))
+    assert nucleus_alpha(0.9, 0.95) == pytest.approx(math.log(0.05) / math.log(0.9))
+    u = synth.uniforms(11, 1 << (log_n - 1))
+    ct = ctx.encrypt(enc.encode(u, log_n, delta), delta, 3)
+    G = beta_noise_he(he, ct, alpha, d)
+    assert G.level == ctx.top_level - 7
+    got = enc.decode(ctx.decrypt(G), log_n, G.scale).real
+    c = chebyshev_interpolant(lambda t: ((t + 1) / 2) ** (1 / alpha), d)
+    assert np.abs(got - np.polynomial.chebyshev.chebval(2 * u - 1, c)).max() < 1e-5
+    big = u >= 1e-2
+    grid = np.linspace(1e-2, 1, 20001)
+    bound = np.abs(np.polynomial.chebyshev.chebval(2 * grid - 1, c) - grid ** (1 / alpha)).max()
+    assert np.abs(got[big] - u[big] ** (1 / alpha)).max() < bound + 1e-5

@@ -26,17 +26,28 @@ def test_keyswitch_noalloc_matches_regular_twice():
     g.gen_relin_key()
     rng = np.random.default_rng(3)
     n = g.n
+    d_first = None
+    ref_first = None
     for call in range(2):
         d = np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in g.primes[: level + 1]])
         ref0, ref1 = g.keyswitch(d, level, 0)                    # coefficient form in and out
+        if call == 0:
+            d_first, ref_first = d, (ref0, ref1)
         dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
         g.ntt_device(dt, 0)                                      # to NTT form
         out = torch.empty((2, level + 1, n), dtype=torch.int64, device="cuda")
+        mem_before = g.memory()
         g.keyswitch_noalloc(dt, level, 0, out)
+        torch.cuda.synchronize()
+        # the library's device arena is neither drawn on nor grown by the call
+        assert g.memory() == mem_before, f"call {call}"
         g.ntt_device(out[0], 0, inverse=True)
         g.ntt_device(out[1], 0, inverse=True)
         got = out.cpu().numpy().view(np.uint64)
         assert (got[0] == ref0).all() and (got[1] == ref1).all(), f"call {call}"
+    # the context's own key switch still works after the calls
+    again = g.keyswitch(d_first, level, 0)
+    assert (again[0] == ref_first[0]).all() and (again[1] == ref_first[1]).all()
 
 
 def test_keyswitch_noalloc_rejects_oversized():
