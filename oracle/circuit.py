@@ -86,12 +86,12 @@ class HE:
         target = self.delta if target is None else target
         q = float(self.q(ct.level))
         E = (target * q) / ct.scale
-        pt = enc.encode(vec, self.ctx.log_n, E)
+        pt = None if getattr(self.ctx, "dry", False) else enc.encode(vec, self.ctx.log_n, E)
         t = self.ctx.mul_plain(ct, pt, ct.scale * E)
         return self.ctx.rescale(t)
 
     def add_plain_vec(self, ct, vec):
-        pt = enc.encode(vec, self.ctx.log_n, ct.scale)
+        pt = None if getattr(self.ctx, "dry", False) else enc.encode(vec, self.ctx.log_n, ct.scale)
         return self.ctx.add_plain(ct, pt)
 
     def rotsum(self, ct, steps):
@@ -203,83 +203,281 @@ def cutmax_he(he, ct, plan, bootstrap=None):
     return Z if many else Z[0]
 
 
-def cutmax_he_boot(he, ct, plan, boot):
-    """Alg. 2 with bootstrapping when levels run out.
+# ------------------------------------------------------------------ bootstrapped form
+class _SimCt:
+    """Level and scale of a ciphertext, nothing else (see LevelSim)."""
+    __slots__ = ("level", "scale")
 
-    Same steps as cutmax_he, with two changes that keep every refreshed
-    ciphertext bounded: the Goldschmidt input is x = kappa V (one level) and
-    Y_(t+1) is scaled by plan.norm[t] through u' = norm^(1/p) u.
-    The input is first dropped to the bootstrap's output level.  Before each
-    phase a ciphertext with fewer levels than the phase needs is bootstrapped:
-    Y before the statistics (5: the variance sum V, far too large to refresh,
-    needs up to 3 rescales to reach x = kappa V ~ 1 with a 30-bit multiplier),
-    x before the iteration (2), the packed
-    Goldschmidt pair [g | h] between steps (2) and before h is extracted (1),
-    D' and h before the product (1), u before the power (ceil log2 p), Y before
-    the final normalisation (d + 3).
-    """
+    def __init__(self, level, scale):
+        self.level, self.scale = level, float(scale)
+
+    def set_scale(self, s):
+        self.scale = float(s)
+
+
+class LevelSim:
+    """A Context that keeps only the level and scale of every ciphertext
+    (each operation updates them exactly as the real one does) and counts key
+    switches by level: one per product, one per rotation or conjugation.  The
+    refresh schedule plays the circuit on it."""
+    dry = True
+
+    def __init__(self, primes, nq, log_n):
+        self.primes, self.nq, self.log_n = list(primes), nq, log_n
+        self.n, self.slots, self.top_level = 1 << log_n, 1 << (log_n - 1), nq - 1
+        self.ks = {}
+
+    def _ks(self, level):
+        self.ks[level] = self.ks.get(level, 0) + 1
+
+    def mul_intd(self, a, K, scale_out):
+        return _SimCt(a.level, scale_out)
+
+    def mul_plain(self, a, pt, scale_out):
+        return _SimCt(a.level, scale_out)
+
+    def mul_int(self, a, k):
+        return _SimCt(a.level, a.scale)
+
+    def add_intd(self, a, K):
+        return _SimCt(a.level, a.scale)
+
+    def add_plain(self, a, pt):
+        return _SimCt(a.level, a.scale)
+
+    def mul_monomial(self, a, e):
+        return _SimCt(a.level, a.scale)
+
+    def rescale(self, a):
+        if a.level < 1:
+            raise ValueError("rescale at level 0")
+        return _SimCt(a.level - 1, a.scale / float(self.primes[a.level]))
+
+    def drop(self, a, level):
+        return _SimCt(level, a.scale)
+
+    def add(self, a, b):
+        return _SimCt(min(a.level, b.level), a.scale)
+
+    sub = add
+
+    def mul(self, a, b):
+        l = min(a.level, b.level)
+        self._ks(l)
+        return _SimCt(l, a.scale * b.scale)
+
+    def automorphism(self, a, g):
+        self._ks(a.level)
+        return _SimCt(a.level, a.scale)
+
+    def rotate(self, a, r):
+        return self.automorphism(a, 0)
+
+    def conj(self, a):
+        return self.automorphism(a, 0)
+
+
+class _DryBoot:
+    """Bootstrapping stand-in for LevelSim: output level, input scale, counts."""
+
+    def __init__(self, out_level):
+        self._out = out_level
+        self.general = self.const = 0
+
+    def out_level(self):
+        return self._out
+
+    def bootstrap(self, ct):
+        self.general += 1
+        return _SimCt(self._out, ct.scale)
+
+    def bootstrap_const(self, ct):
+        self.const += 1
+        return _SimCt(self._out, ct.scale)
+
+
+class CountingBoot:
+    """Wraps a Bootstrapper and counts its general and constant refreshes."""
+
+    def __init__(self, boot):
+        self.boot = boot
+        self.general = self.const = 0
+
+    def out_level(self):
+        return self.boot.out_level()
+
+    def bootstrap(self, ct):
+        self.general += 1
+        return self.boot.bootstrap(ct)
+
+    def bootstrap_const(self, ct):
+        self.const += 1
+        return self.boot.bootstrap_const(ct)
+
+
+class CountingCtx:
+    """Forwards to a Context and counts the circuit's own key switches by
+    level (the bootstrapper keeps the bare Context, so its rotations are not
+    counted here)."""
+
+    def __init__(self, ctx):
+        self._ctx = ctx
+        self.ks = {}
+
+    def __getattr__(self, name):
+        return getattr(self._ctx, name)
+
+    def _ks(self, level):
+        self.ks[level] = self.ks.get(level, 0) + 1
+
+    def mul(self, a, b):
+        self._ks(min(a.level, b.level))
+        return self._ctx.mul(a, b)
+
+    def automorphism(self, a, g):
+        self._ks(a.level)
+        return self._ctx.automorphism(a, g)
+
+    def rotate(self, a, r):
+        self._ks(a.level)
+        return self._ctx.rotate(a, r)
+
+    def conj(self, a):
+        self._ks(a.level)
+        return self._ctx.conj(a)
+
+
+def _imag2(ctx, a):
+    """2 Im(a) of a complex constant a, as a real constant: (a - conj a)(-i),
+    -i being the monomial X^(3N/2)."""
+    return ctx.mul_monomial(ctx.sub(a, ctx.conj(a)), 3 * ctx.n // 2)
+
+
+def _boot_circuit(he, ct, plan, boot, h_refresh, y_boot, tally):
+    """The bootstrapped CutMax of one stream (one ciphertext): Alg. 2 with
+    refreshes, the Goldschmidt input x = kappa V, Y_(t+1) scaled by norm[t]
+    through u' = norm^(1/p) u.  The vectors (Y, D', u) take the general
+    bootstrap; the scalars (x, the Goldschmidt pair, h, the final sum), which
+    hold one value in every slot, the constant bootstrap.  The Goldschmidt
+    pair (g, h) travels as one complex constant z = g + i h/4: one product z^2,
+    one conjugation (2 Im(z^2) = g h, the 1/4 keeping the scale of every step
+    at s^3/(q q')), then z <- z (1.5 - g h); h = 4 Im z.  Each refresh inside
+    the iteration is followed by a multiplication by 1 that lands on Delta.
+    Refreshes: Y before the statistics when it has fewer than 5 levels (V
+    needs up to 3 rescales to reach x ~ 1 with a 30-bit multiplier) or when
+    y_boot[t] asks; x when it has fewer than 2 (tally['x'] counts these); z
+    between steps when it has fewer than 2 and before h is read when it has
+    none; h when it has none, or when h_refresh[t] asks and h sits below D';
+    D' and h before their product (1), u before the power (ceil log2 p), Y
+    before the final sum (2), the final sum before the inverse (d + 3)."""
     ctx = he.ctx
     n, steps, m = plan.n, plan.rotsum_steps, plan.pad
-
-    def ensure(c, need):
-        return boot.bootstrap(c) if c.level < need else c
-
     mask = None
     if m:
         mask = np.zeros(plan.slots)
         mask[:n] = 1.0
-    # compute only on the levels a bootstrap hands back (the primes above are
-    # the bootstrapping primes, where products of Delta-scale ciphertexts
-    # would shrink the scale)
+
+    def ensure(c, need):
+        return boot.bootstrap(c) if c.level < need else c
+
     Y = ctx.drop(ct, boot.out_level()) if ct.level > boot.out_level() else ct
     for t in range(plan.T):
         p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
         rn = plan.norm[t] ** (1.0 / p)
-        Y = ensure(Y, 5)
+        if Y.level < 5 or y_boot[t]:
+            Y = boot.bootstrap(Y)
         S = he.rotsum(Y, steps)
         D = ctx.sub(ctx.mul_int(Y, n), S)
         E = he.mul_rescale(D, D)
         V = he.rotsum(E, steps)
         if m:
             V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
-        x = ensure(he.mcr_bits(V, kap, None, 30), 2)
+        x = he.mcr_bits(V, kap, None, 30)
+        if x.level < 2:
+            tally["x"] = tally.get("x", 0) + 1
+            x = boot.bootstrap_const(x)
         coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
         Dp = he.mcr(he.mul_plain_rescale(D, mask), coef) if m else he.mcr(D, coef)
         if k == 0:
-            h, Dp = ensure(learned_half(he, x, plan.lq[t]), 1), ensure(Dp, 1)
-            u = he.mul_rescale(Dp, h)
-            u = he.add_plain_vec(u, rn * mask) if m else he.add_const(u, rn)
-            u = ensure(u, (p - 1).bit_length())
-            Y = he.power(u, p)
-            continue
-        # Goldschmidt pair packed in one ciphertext: slots [0, s/2) hold g,
-        # slots [s/2, s) hold h; one rotation by s/2 lines them up for g*h
-        half = plan.slots // 2
-        lo = np.zeros(plan.slots)
-        lo[:half] = 1.0
-        hi = 1.0 - lo
-        a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), 1.5)
-        P = he.add_plain_vec(he.mul_plain_rescale(x, y0 * lo), (y0 / 2.0) * hi)
-        P = he.mul_rescale(P, a)
-        for i in range(2, k + 1):
-            if P.level < 2:
-                # a step maps the pair's scale s to s^3/(q q'): the refresh is
-                # followed by a multiplication by 1 landing exactly on Delta
-                P = he.mcr(boot.bootstrap(P), 1.0)
-            Q = he.mul_rescale(P, ctx.rotate(P, half))
-            P = he.mul_rescale(P, he.add_const(he.neg(Q), 1.5))
-        P = ensure(P, 1)
-        hm = he.mul_plain_rescale(P, hi)
-        h = ctx.add(hm, ctx.rotate(hm, half))
+            h = learned_half(he, x, plan.lq[t])
+        else:
+            a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), 1.5)
+            z = he.add_plain_vec(he.mcr(x, y0), np.full(plan.slots, 1j * y0 / 8.0))
+            z = he.mul_rescale(z, a)
+            for _ in range(2, k + 1):
+                if z.level < 2:
+                    z = he.mcr(boot.bootstrap_const(z), 1.0)
+                gh = _imag2(ctx, he.mul_rescale(z, z))
+                z = he.mul_rescale(z, he.add_const(he.neg(gh), 1.5))
+            if z.level < 1:
+                z = boot.bootstrap_const(z)
+            h = ctx.mul_int(_imag2(ctx, z), 2)
+        if (h_refresh[t] and h.level < Dp.level) or h.level < 1:
+            h = boot.bootstrap_const(h)
         h, Dp = ensure(h, 1), ensure(Dp, 1)
         u = he.mul_rescale(Dp, h)
         u = he.add_plain_vec(u, rn * mask) if m else he.add_const(u, rn)
         u = ensure(u, (p - 1).bit_length())
         Y = he.power(u, p)
-    Y = ensure(Y, plan.d + 3)
+    Y = ensure(Y, 2)
     S = he.rotsum(Y, steps)
+    if S.level < plan.d + 3:
+        S = boot.bootstrap_const(S)
     F = inverse_goldschmidt(he, S, plan.kappa_f, plan.d)
     return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
+
+
+def refresh_schedule(he, ct, plan, out_level):
+    """The optional refreshes of the bootstrapped circuit, chosen by playing
+    every combination on LevelSim: per iteration t, refresh h when it sits
+    below D' (h_refresh[t]), and bootstrap Y before the statistics although it
+    has the levels they need (y_boot[t]); 4^T combinations for T <= 6, 2^T
+    (h only) for 6 < T <= 16, none beyond.  The cheapest counts a general
+    bootstrap 2, a constant one 1 and a refresh of x 1000 (x reaches tens,
+    beyond what a refresh of a constant keeps accurate); ties go to fewer
+    bootstraps, then to the first combination (t = 0 the least significant
+    digit, bit 0 h_refresh, bit 1 y_boot)."""
+    T = plan.T
+    if T > 16:
+        return [0] * T, [0] * T
+    per = 4 if T <= 6 else 2
+    ctx = he.ctx
+    primes = list(ctx.primes)
+    start = _SimCt(min(ct.level, out_level), ct.scale)
+    best, best_key = None, None
+    for combo in range(per ** T):
+        cc, hr, yb = combo, [], []
+        for _ in range(T):
+            ch = cc % per
+            cc //= per
+            hr.append(ch & 1)
+            yb.append(1 if ch & 2 else 0)
+        sim = LevelSim(primes, ctx.nq, ctx.log_n)
+        dry = _DryBoot(out_level)
+        tally = {}
+        _boot_circuit(HE(sim, he.delta), start, plan, dry, hr, yb, tally)
+        cost = 2 * dry.general + dry.const + 1000 * tally.get("x", 0)
+        key = (cost, dry.general + dry.const)
+        if best_key is None or key < best_key:
+            best, best_key = (hr, yb), key
+    return best
+
+
+def cutmax_he_boot(he, ct, plan, boot, stats=None):
+    """Alg. 2 with bootstrapping (see _boot_circuit), the optional refreshes
+    picked by refresh_schedule.  boot: a Bootstrapper (oracle/bootstrap.py).
+    stats (a dict, optional) receives the schedule, the general and constant
+    refreshes made and the circuit's own key switches by level."""
+    if getattr(plan, "cts", 1) != 1:
+        raise ValueError("the oracle's bootstrapped circuit takes one ciphertext per stream")
+    hr, yb = refresh_schedule(he, ct, plan, boot.out_level())
+    cctx, cboot = CountingCtx(he.ctx), CountingBoot(boot)
+    tally = {}
+    out = _boot_circuit(HE(cctx, he.delta), ct, plan, cboot, hr, yb, tally)
+    if stats is not None:
+        stats.update(h_refresh=hr, y_boot=yb, general=cboot.general, const=cboot.const, x_refresh=tally.get("x", 0),
+                     ks=dict(cctx.ks))
+    return out
 
 
 def chebyshev_interpolant(f, d):

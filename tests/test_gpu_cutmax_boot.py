@@ -4,7 +4,8 @@ Config-2 shape at a reduced ring: heavy-tailed logits, T = 4,
 p = [16, 4, 4, 6], c = [5, 3, 3, 3] (the paper's HE setting, Sect. 4.2),
 zero-padded packing, bootstrapping whenever a phase runs out of levels.
 Checked against the FP64 mirror of the same circuit (max-abs 1e-3), the exact
-Alg. 1 argmax, and, on one input, the oracle's own bootstrapped circuit.
+Alg. 1 argmax, and, on one input, the oracle's bootstrapped circuit, which
+takes the same steps on the oracle's operations and bootstrapping.
 """
 import numpy as np
 import pytest
@@ -57,10 +58,14 @@ def test_bootstrapped_cutmax_matches_mirror(setup, seed):
 
 
 def test_bootstrapped_cutmax_matches_oracle_circuit(setup):
-    """The library's bootstrapped circuit against the oracle's (general
-    bootstraps wherever levels run out). The library refreshes its scalar
-    chains by the constant bootstrap on a schedule of its own, so the two end
-    on different levels; their decrypted outputs must agree."""
+    """The library's bootstrapped circuit against the oracle's, which takes the
+    same steps (complex Goldschmidt pair, constant bootstrap for the scalars,
+    general bootstrap for the vectors, the refresh schedule found by playing
+    every combination on its own circuit): same output level and scale, decrypted outputs within 1e-3 of each other (the two
+    bootstrapping implementations differ in rounding), the same argmax, and the
+    same key switches at every level once each side's bootstraps are counted
+    in (the library's own bootstrap costs measured here through its ledger),
+    which also makes the two refresh schedules the same."""
     from oracle import ckks as ock
     from oracle import encoding as oenc
     from oracle.bootstrap import Bootstrapper
@@ -69,16 +74,35 @@ def test_bootstrapped_cutmax_matches_oracle_circuit(setup):
     o = ock.Context(LOG_N, QB, PB, dnum=3, h=H, seed=21)
     ob = Bootstrapper(o, K=K, r=R, d=D)
     ob.gen_keys()
+    ob.gen_const_keys()
     for r in required_rotations(pl):
         o.gen_rot_key(r)
     x = gen(7)
     pt = oenc.encode(P.pack(x, g.slots, pl.packing), LOG_N, g.delta)
-    zg = g.cutmax(g.encrypt_poly(pt, g.delta, 3), pl)
-    zo = cutmax_he_boot(HE(o, g.delta), o.encrypt(pt, g.delta, 3), pl, ob)
+    ct = g.encrypt_poly(pt, g.delta, 3)
+    g.ledger(reset=True)
+    zg = g.cutmax(ct, pl)
+    ks_g, nb_g = g.ledger(reset=True)
+    st = {}
+    zo = cutmax_he_boot(HE(o, g.delta), o.encrypt(pt, g.delta, 3), pl, ob, stats=st)
+    assert zg.level == zo.level
+    assert zg.scale == pytest.approx(zo.scale, rel=1e-9)
     dg = g.decrypt(zg)[:NV]
     do = oenc.decode(o.decrypt(zo), LOG_N, zo.scale).real[:NV]
     assert np.abs(dg - do).max() < 1e-3
     assert int(np.argmax(dg)) == int(np.argmax(do)) == int(np.argmax(x))
+    assert st["x_refresh"] == 0 and nb_g == st["general"] + st["const"]
+    # the library's key switches per general and per constant bootstrap
+    low = g.encrypt(np.full(g.slots, 0.5), g.delta, 9, level=0)
+    g.ledger(reset=True)
+    g.bootstrap(low)
+    ks_gen, _ = g.ledger(reset=True)
+    g.bootstrap_const(low)
+    ks_const, _ = g.ledger(reset=True)
+    want = ks_gen * st["general"] + ks_const * st["const"]
+    for lv, c in st["ks"].items():
+        want[lv] += c
+    assert (ks_g == want).all(), {i: (int(a), int(b)) for i, (a, b) in enumerate(zip(ks_g, want)) if a != b}
 
 
 def test_ledger_model_matches_library(setup):

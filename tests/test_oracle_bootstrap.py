@@ -126,3 +126,50 @@ def test_oracle_constant_bootstrap():
     z = rng.uniform(-1, 1, ctx.slots) + 1j * rng.uniform(-1, 1, ctx.slots)
     out = bs.bootstrap_const(ctx.encrypt(enc.encode(z, log_n, 2.0 ** 40), 2.0 ** 40, 2, level=0))
     assert np.abs(enc.decode(ctx.decrypt(out), log_n, out.scale) - z.mean()).max() < 1e-6
+
+
+@pytest.mark.slow
+def test_oracle_bootstrapped_circuit_replays_on_levels():
+    """The oracle's bootstrapped CutMax (Alg. 2 with refreshes) at N = 2^11:
+    the level-only replay that picks its refresh schedule predicts the real
+    run exactly (output level, scale, general and constant refreshes, and the
+    circuit's key switches at every level), the schedule is no costlier than
+    making no optional refresh, and the decrypted output is the FP64 mirror of
+    the same circuit within 1e-6, with the argmax of the logits."""
+    from oracle import cutmax_fp64 as F
+    from oracle.circuit import (HE, LevelSim, _boot_circuit, _DryBoot, _SimCt, cutmax_he_boot,
+                                refresh_schedule, required_rotations)
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    log_n, nv, delta = 11, 1000, 2.0 ** 40
+    qb = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+    gen = lambda i: synth.logits_heavy_tail(i, n=nv, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+    pl = P.calibrate(lambda i: gen(1000 + i), 200, nv, 1 << (log_n - 1), 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0],
+                     margin=2.0, tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True)
+    ctx = ckks.Context(log_n, qb, [61] * 10, dnum=3, h=64, seed=21)
+    bs = Bootstrapper(ctx, K=14, r=4, d=31)
+    bs.gen_keys()
+    bs.gen_const_keys()
+    for r in required_rotations(pl):
+        ctx.gen_rot_key(r)
+    x = gen(7)
+    ct = ctx.encrypt(enc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, 3)
+    he = HE(ctx, delta)
+    st = {}
+    out = cutmax_he_boot(he, ct, pl, bs, stats=st)
+    # the replay of the chosen schedule
+    sim = LevelSim(ctx.primes, ctx.nq, log_n)
+    dry = _DryBoot(bs.out_level())
+    start = _SimCt(min(ct.level, bs.out_level()), ct.scale)
+    rep = _boot_circuit(HE(sim, delta), start, pl, dry, st["h_refresh"], st["y_boot"], {})
+    assert rep.level == out.level and rep.scale == pytest.approx(out.scale, rel=1e-9)
+    assert (dry.general, dry.const) == (st["general"], st["const"]) and st["x_refresh"] == 0
+    assert sim.ks == st["ks"]
+    # no optional refresh at all costs at least as much
+    sim0, dry0 = LevelSim(ctx.primes, ctx.nq, log_n), _DryBoot(bs.out_level())
+    _boot_circuit(HE(sim0, delta), start, pl, dry0, [0] * pl.T, [0] * pl.T, {})
+    assert 2 * dry.general + dry.const <= 2 * dry0.general + dry0.const
+    assert refresh_schedule(he, ct, pl, bs.out_level()) == (st["h_refresh"], st["y_boot"])
+    dec = enc.decode(ctx.decrypt(out), log_n, out.scale).real[:nv]
+    assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-6
+    assert int(np.argmax(dec)) == int(np.argmax(x))
