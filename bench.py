@@ -26,9 +26,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted CutMax decodes/sec (vocab 32k, N=2^16), 1 GB300"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of both NTT passes per limb at
-# N=2^16 (90-limb forward / 30-limb inverse launches of one rotation; the row
-# pass with round-B twiddles staged over its tile)
-NTT_DRAM_PER_LIMB = {0: (47.39e6 + 0.33e6 + 93.81e6 + 7.25e6) / 90, 1: (47.11e6 + 0.04e6 + 15.91e6) / 30}
+# N=2^16, from one capture of the NTT source whose hash is `src`; once the
+# source changes (ntt_source_hash() differs) the bench reports traffic null
+NTT_DRAM = {"src": None, "per_limb": {0: None, 1: None}}
 # integer-pipe ceiling of the NTT: a Shoup butterfly on 64-bit words takes 1.04
 # warp instructions (33 thread instructions: ncu sm__inst_executed of a 90-limb
 # forward transform / its 90 x 2^19 butterflies), and an SM issues at most 4
@@ -37,6 +37,18 @@ NTT_WARP_INSTR_PER_BUTTERFLY = 1.04
 ALU_ISSUE_PEAK = 152 * 4 * 2.07e9
 PROF_NAMES = {0: "ntt_forward (k_ntt_cols+k_ntt_rows)", 1: "ntt_inverse (k_ntt_rows+k_ntt_cols)",
               2: "keyswitch_inner (k_keyswitch_inner)", 3: "bconv (k_bconv)"}
+
+
+def ntt_source_hash():
+    """Hash of the NTT kernels' source (their section of kernels.cu and the
+    shared arithmetic header) that the DRAM traffic figures were taken on."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2509_08383_gb300", "csrc")
+    k = open(os.path.join(csrc, "kernels.cu")).read()
+    a, b = k.find("// ------------------------------------------------------------------ NTT"), \
+        k.find("// ------------------------------------------------------------------ elementwise")
+    body = k[a:b] + open(os.path.join(csrc, "common.cuh")).read()
+    return hashlib.sha256(body.encode()).hexdigest()[:16]
 
 
 def measured_peaks():
@@ -152,30 +164,83 @@ def dist_setup(args):
     return None, rank, ws
 
 
-def oracle_ks_model(log_n, qb, pb, dnum, h, levels, reps=1):
-    """Oracle key-switch seconds at the given levels (bounded sample)."""
-    from oracle import ckks as ock
-    o = ock.Context(log_n, qb, pb, dnum, h=h, seed=1)
-    o.gen_relin_key()
-    rng = np.random.default_rng(0)
-    out = {}
-    for l in levels:
-        d = np.stack([rng.integers(0, q, 1 << log_n, dtype=np.uint64) for q in o.primes[: l + 1]])
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            o.keyswitch(d, l, 0)
-        out[l] = (time.perf_counter() - t0) / reps
-    return out
+OP_CLASSES = ("rot", "mul", "rescale", "plain_mul", "add")
 
 
-def extrapolate(ks_by_level, model):
-    """sum_l count_l * t(l), t linear between the measured levels."""
-    lv = sorted(model)
+class OracleOps:
+    """The oracle's operations at the bench parameter set, timed one by one
+    (a bounded sample: one of each class per level).  Each class stands for a
+    row of the library's ledger: rot = automorphism + key switch (every key
+    switch that is not a relinearisation), mul = tensor product + key switch,
+    rescale, plain_mul = product with an encoded plaintext, add."""
+
+    def __init__(self, log_n, qb, pb, dnum, h):
+        from oracle import ckks as ock
+        self.ock = ock
+        self.log_n = log_n
+        self.o = ock.Context(log_n, qb, pb, dnum, h=h, seed=1)
+        self.o.gen_relin_key()
+        self.o.gen_rot_key(1)
+        self.nq = len(qb)
+
+    def time_level(self, level, threads=0):
+        """{class: seconds} of one operation of each class at `level` on
+        `threads` threads (0: every core of this process)."""
+        ock, o = self.ock, self.o
+        old = ock.get_threads()
+        ock.set_threads(threads)
+        try:
+            rng = np.random.default_rng(level)
+            n = 1 << self.log_n
+            m = np.rint(rng.normal(size=n) * 2.0 ** 40)
+            a, b = o.encrypt(m, 2.0 ** 40, 1, level), o.encrypt(m, 2.0 ** 40, 2, level)
+            pt = np.rint(rng.normal(size=n) * 2.0 ** 20)
+            ops = {"rot": lambda: o.rotate(a, 1), "mul": lambda: o.mul(a, b), "rescale": lambda: o.rescale(a),
+                   "plain_mul": lambda: o.mul_plain(a, pt, 2.0 ** 60), "add": lambda: o.add(a, b)}
+            out = {}
+            for cls in OP_CLASSES:
+                t0 = time.perf_counter()
+                ops[cls]()
+                out[cls] = time.perf_counter() - t0
+            return out
+        finally:
+            ock.set_threads(old)
+
+
+def census_seconds(census, times):
+    """Seconds of one decode: sum over levels and classes of count x the time
+    per operation at that level, linear between the timed levels.  census:
+    {"ks", "tensor", "rescale", "plain_mul", "add"} -> {level: count}."""
+    lv = sorted(times)
+
+    def t(cls, l):
+        return float(np.interp(l, lv, [times[x][cls] for x in lv]))
+
     tot = 0.0
-    for l, cnt in ks_by_level.items():
-        t = float(np.interp(l, lv, [model[x] for x in lv]))
-        tot += cnt * t
+    for l, c in census["ks"].items():
+        tot += (c - census["tensor"].get(l, 0)) * t("rot", l)
+    for cls, key in (("mul", "tensor"), ("rescale", "rescale"), ("plain_mul", "plain_mul"), ("add", "add")):
+        for l, c in census[key].items():
+            tot += c * t(cls, l)
     return tot
+
+
+def census_levels(census, nq):
+    """Three timing levels spanning the census: the lowest level with a
+    rescale's worth of limbs (>= 1), the middle, the top."""
+    used = [l for k in census.values() for l, c in k.items() if c]
+    lo = max(1, min(used))
+    return [lo, (lo + nq - 1) // 2, nq - 1]
+
+
+def cfg2_census():
+    """Key switches and bootstraps of one config-2 decode from the circuit's
+    level model (ledger.py), for the reference arm, which runs no GPU code;
+    the other op classes are not in that model and count zero there."""
+    from paper_2509_08383_gb300 import ledger
+    log_n, qb, pb, dnum, pl, gen, desc, boot = workload("cfg2")
+    ks, nb = ledger.cutmax_ledger(pl, len(qb), log_n, boot=boot[1:], qbits=qb)
+    return {"ks": ks, "tensor": {}, "rescale": {}, "plain_mul": {}, "add": {}}, nb
 
 
 def run_reference(args):
@@ -186,10 +251,9 @@ def run_reference(args):
     from oracle import ckks as ock
     from oracle import encoding as oenc
     from oracle.circuit import HE, cutmax_he, required_rotations
-    from paper_2509_08383_gb300 import ledger
     from paper_2509_08383_gb300 import plan as P
     log_n, qb, pb, dnum, pl, gen, desc, boot = workload(args.workload)
-    times = []
+    times, cpu_s = [], 0.0
     if boot is None:
         o = ock.Context(log_n, qb, pb, dnum, seed=1)
         o.gen_relin_key()
@@ -202,32 +266,41 @@ def run_reference(args):
             ct = o.encrypt(oenc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, step)
             z = cutmax_he(HE(o, delta), ct, pl)
             oenc.decode(o.decrypt(z), log_n, z.scale)
+            dt = time.perf_counter() - t0
+            cpu_s += dt
             if step >= args.warmup:
-                times.append(time.perf_counter() - t0)
+                times.append(dt)
         sample = f"{args.steps} full CutMax decodes (encrypt + CutMax + decrypt) on the oracle"
+        extrapolated = False
     else:
-        ks, nb = ledger.cutmax_ledger(pl, len(qb), log_n, boot=boot[1:], qbits=qb)
-        levels = [min(ks), (min(ks) + len(qb) - 1) // 2, len(qb) - 1]
+        census, nb = cfg2_census()
+        levels = census_levels(census, len(qb))
+        ops = OracleOps(log_n, qb, pb, dnum, boot[0])
         for step in range(args.warmup + args.steps):
-            model = oracle_ks_model(log_n, qb, pb, dnum, boot[0], levels)
+            t0 = time.perf_counter()
+            tl = {l: ops.time_level(l) for l in levels}
+            cpu_s += time.perf_counter() - t0
             if step >= args.warmup:
-                times.append(extrapolate(ks, model))
-        sample = (f"per step, oracle key switches timed at levels {levels} and scaled by the circuit's "
-                  f"{sum(ks.values())} key switches per decode ({nb} bootstraps); a full decode on the oracle "
-                  "is hours")
+                times.append(census_seconds(census, tl))
+        sample = (f"each step times one oracle rotation and one product (each with its key switch), a rescale, a "
+                  f"plaintext product and an addition at levels {levels} ({cpu_s / (args.warmup + args.steps):.1f} s "
+                  f"per step), and scales them by one decode's {sum(census['ks'].values())} key switches by level "
+                  f"({nb} bootstraps) from the circuit's level model; extrapolated: a full decode on the oracle is "
+                  "hours, its dense bootstrap does not fit at N=2^16")
+        extrapolated = True
     T = sum(times)
     val = args.steps / T
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "decodes/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-           "config": desc,
+           "config": desc, "extrapolated": extrapolated, "cpu_seconds_run": cpu_s,
            "cpu_baseline": {"value": val, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": val, "unit": "decodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def cpu_baseline(args, ks_by_level=None):
+def cpu_baseline(args, census=None):
     """Bounded oracle sample of the bench workload, in decodes/s."""
     from oracle import ckks as ock
     from oracle import encoding as oenc
@@ -235,12 +308,29 @@ def cpu_baseline(args, ks_by_level=None):
     from paper_2509_08383_gb300 import plan as P
     log_n, qb, pb, dnum, pl, gen, _, boot = workload(args.workload)
     if boot is not None:
-        levels = [min(ks_by_level), (min(ks_by_level) + len(qb) - 1) // 2, len(qb) - 1]
-        model = oracle_ks_model(log_n, qb, pb, dnum, boot[0], levels)
-        t = extrapolate(ks_by_level, model)
-        return {"value": 1.0 / t, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
-                "sample": f"oracle key switches timed at levels {levels}, scaled by the {sum(ks_by_level.values())} "
-                          "key switches of one decode (the library's ledger); extrapolated, key switching only"}
+        levels = census_levels(census, len(qb))
+        ops = OracleOps(log_n, qb, pb, dnum, boot[0])
+        t0 = time.perf_counter()
+        tl = {l: ops.time_level(l) for l in levels}
+        t_all = census_seconds(census, tl)
+        mid = levels[1]
+        one = ops.time_level(mid, threads=1)
+        # single thread: the middle level timed on one core, the other levels
+        # scaled by the all-core level profile of each class
+        t1 = {l: {c: one[c] * tl[l][c] / tl[mid][c] for c in OP_CLASSES} for l in levels}
+        t_one = census_seconds(census, t1)
+        per = {c: sum(census[k].values()) for c, k in (("ks", "ks"), ("tensor", "tensor"), ("rescale", "rescale"),
+                                                        ("plain_mul", "plain_mul"), ("add", "add"))}
+        return {"value": 1.0 / t_all, "unit": "decodes/s", "cores": ock.get_threads(), "kind": "oracle",
+                "sample": f"one oracle rotation and one product (each with its key switch), a rescale, a plaintext "
+                          f"product and an addition timed at levels {levels} ({time.perf_counter() - t0:.1f} s of "
+                          "CPU work), scaled by the per-level counts of every op class of one decode in the library's "
+                          f"ledger ({per}); extrapolated",
+                "single_thread": {"value": 1.0 / t_one, "unit": "decodes/s", "cores": 1,
+                                  "sample": f"the level-{mid} operations on one core, other levels scaled by the "
+                                            "all-core profile"},
+                "per_op_seconds_all_cores": {str(l): tl[l] for l in levels},
+                "per_op_seconds_one_core": {str(mid): one}}
     o = ock.Context(log_n, qb, pb, dnum, seed=1)
     o.gen_relin_key()
     for r in required_rotations(pl):
@@ -610,6 +700,49 @@ def run_micro(args):
     print(json.dumps(out))
 
 
+def keyswitch_block(g, ks_by_level, log_n, qb, pb, dnum, stream, flush, peak, reps=10, warm=3):
+    """Whole rotations (automorphism + hybrid key switch) timed with CUDA events
+    at the top level and at the median level of the decode's key switches, L2
+    flushed before each.  Algorithmic bytes per the key switch's definition:
+    the input polynomial (l+1) N words, the beta key digits (b and a over
+    l+1+K primes), the two outputs; plus the automorphism's read and write of
+    both polynomials."""
+    import torch
+    n, K = 1 << log_n, len(pb)
+    alpha = -(-len(qb) // dnum)
+    lv = sorted(ks_by_level)
+    acc, tot, med = 0, sum(ks_by_level.values()), lv[0]
+    for l in lv:
+        acc += ks_by_level[l]
+        if 2 * acc >= tot:
+            med = l
+            break
+    out = []
+    for l in (len(qb) - 1, med):
+        ct = g.encrypt(np.linspace(-1, 1, n // 2), g.delta, 4242, level=l)
+        ts = []
+        for i in range(warm + reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            z = g.rotate(ct, 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            del z
+            if i >= warm:
+                ts.append(e0.elapsed_time(e1))
+        ms = float(np.mean(ts))
+        beta = -(-(l + 1) // alpha)
+        ks_bytes = 8.0 * n * ((l + 1) + 2 * beta * (l + 1 + K) + 2 * (l + 1))
+        rot_bytes = ks_bytes + 8.0 * n * 4 * (l + 1)
+        gbs = rot_bytes / (ms * 1e-3) / 1e9
+        out.append({"level": l, "op": "rotation (automorphism + hybrid key switch)", "ms": ms,
+                    "keyswitch_bytes": ks_bytes, "algorithmic_bytes": rot_bytes, "achieved_gbs": gbs,
+                    "peak_gbs": peak, "frac": gbs / peak, "what": "top level" if l == len(qb) - 1 else
+                    "median level of the decode's key switches"})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -661,11 +794,12 @@ def main():
         torch.cuda.synchronize()
         share[cls] = he.profile_read(cls)[1]
         del z
+    he.profile_enable(-1)
     dom = max(share, key=share.get)
-    he.profile_enable(dom)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # timed region: no instrumentation; CUDA events on the library's stream
     g.ledger(reset=True)
     l0 = he.launch_count()
     with ClockSampler(local) as clk:
@@ -682,40 +816,63 @@ def main():
                 torch.cuda.synchronize()
                 l0 = he.launch_count()
                 g.ledger(reset=True)
-                he.profile_enable(dom)
             del z
         torch.cuda.synchronize()
     launches = he.launch_count() - l0
+    ops = g.ledger_ops()
     ks_led, nboot = g.ledger(reset=True)
-    ks_by_level = {i: int(v) // args.steps for i, v in enumerate(ks_led) if v}
+    census = {"ks": {i: int(v) // args.steps for i, v in enumerate(ks_led) if v}}
+    for k, v in ops.items():
+        census[k] = {i: int(c) // args.steps for i, c in enumerate(v) if c}
+    ks_by_level = census["ks"]
     ms = sum(ev[s][0].elapsed_time(ev[s][1]) for s in range(args.warmup, nsteps)) / args.steps
     ms = replicas.max_over_ranks(ms, dist, device="cuda")
     if dist:
         dist.barrier()
+    # roofline of the dominant class: the same timed steps again with CUDA
+    # events around every launch of that class (on the launch stream); these
+    # instrumented steps are not part of `value`
+    he.profile_enable(dom)
+    t_ins = []
+    for s in range(args.warmup, nsteps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        z = g.cutmax(cts[s], pl)
+        e1.record(stream)
+        del z
+        torch.cuda.synchronize()
+        t_ins.append(e0.elapsed_time(e1))
     n_dom, ms_dom, bytes_dom = he.profile_read(dom)
     he.profile_enable(-1)
     peak, peak_kind = measured_peaks()
     achieved = (bytes_dom / n_dom) / (ms_dom / n_dom * 1e-3) / 1e9 if n_dom else 0.0
-    # DRAM bytes per launch of the dominant class, from ncu counters at N=2^16
-    # (profiles/kernels_rotation_n65536.md), scaled by the limbs a launch moves
+    # DRAM bytes per launch of the dominant class from the ncu capture of the
+    # current NTT source (null once that source has changed), scaled by the
+    # limbs a launch moves
     traffic = None
-    if dom in NTT_DRAM_PER_LIMB and log_n == 16 and n_dom:
-        traffic = NTT_DRAM_PER_LIMB[dom] * (bytes_dom / n_dom) / (16.0 * (1 << log_n))
+    if (dom in (0, 1) and log_n == 16 and n_dom and NTT_DRAM["src"] == ntt_source_hash()
+            and NTT_DRAM["per_limb"][dom]):
+        traffic = NTT_DRAM["per_limb"][dom] * (bytes_dom / n_dom) / (16.0 * (1 << log_n))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": PROF_NAMES[dom], "launches": n_dom,
                 "avg_launch_us": 1000.0 * ms_dom / max(n_dom, 1),
                 "algorithmic_bytes_per_launch": bytes_dom / max(n_dom, 1),
                 "share_of_step": (ms_dom / args.steps) / ms if ms else None, "peak_source": peak_kind,
+                "measured_over": f"{args.steps} instrumented repeats of the timed steps (CUDA events around every "
+                                 f"launch of the class, {float(np.mean(t_ins)):.1f} ms per step with them); `value` "
+                                 "comes from the uninstrumented steps",
                 "class_ms_per_step": {PROF_NAMES[c]: v for c, v in share.items()}}
-    if dom in NTT_DRAM_PER_LIMB and n_dom:
+    if dom in (0, 1) and n_dom:
         # the NTT binds on integer issue, not on HBM: butterflies per second
         # against the issue ceiling
         fly = (bytes_dom / n_dom) / (16.0 * (1 << log_n)) * (1 << (log_n - 1)) * log_n
         fly_s = fly / (ms_dom / n_dom * 1e-3)
         ceil = ALU_ISSUE_PEAK / NTT_WARP_INSTR_PER_BUTTERFLY
         roofline["alu"] = {"achieved": fly_s, "peak": ceil, "unit": "butterflies/s", "frac": fly_s / ceil,
-                           "peak_source": "152 SMs x 4 warp instructions per clock x 2.07 GHz / 1.04 warp "
-                                          "instructions per butterfly (ncu)"}
+                           "peak_source": "152 SMs x 4 warp instructions per clock x 2.07 GHz / "
+                                          f"{NTT_WARP_INSTR_PER_BUTTERFLY} warp instructions per butterfly (ncu)"}
+    ks_block = keyswitch_block(g, ks_by_level, log_n, qb, pb, dnum, stream, flush, peak) if log_n == 16 else None
     value = ws * 1000.0 / ms
 
     # end to end through the C ABI: pinned host logits -> host outputs
@@ -749,10 +906,13 @@ def main():
            "check": {"argmax_correct": argmax_ok, "decodes": nsteps, "mean_max_z": float(np.mean(top_z)),
                      "what": "decrypted end-to-end outputs: argmax vs the plaintext logits, mean of max Z"},
            "ledger": {"keyswitches_per_decode": int(sum(ks_by_level.values())),
-                      "bootstraps_per_decode": nboot / args.steps}}
+                      "bootstraps_per_decode": nboot / args.steps,
+                      "ops_per_decode": {k: int(sum(v.values())) for k, v in census.items() if k != "ks"}}}
+    if ks_block:
+        res["keyswitch"] = ks_block
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
-            res["cpu_baseline"] = cpu_baseline(args, ks_by_level)
+            res["cpu_baseline"] = cpu_baseline(args, census)
         print(json.dumps(res))
 
 

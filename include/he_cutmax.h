@@ -100,6 +100,13 @@ int he_profile_enable(int32_t kernel_class);
  * ks_by_level[n_q] = key switches performed at each level, *n_boot = number of
  * bootstraps.  reset != 0 zeroes the ledger after reading. */
 int he_ledger_read(he_ctx *ctx, uint64_t *ks_by_level, uint64_t *n_boot, int32_t reset);
+/* The rest of the ledger, read without resetting (he_ledger_read resets all of
+ * it): host by_level[n_q] = operations of one kind performed at each level,
+ * counting every member of a batch: kind 0 rescales, 1 ciphertext (tensor)
+ * products, 2 plaintext products (a bootstrap's transform diagonals
+ * included), 3 additions and subtractions of ciphertexts.  HE_EINVAL for
+ * another kind. */
+int he_ledger_ops(const he_ctx *ctx, uint32_t kind, uint64_t *by_level);
 int he_profile_read(int32_t kernel_class, uint64_t *launches, double *ms, double *bytes);
 
 /* ---- keys (Sect. 2.1 rotations; hybrid key switching) ---------------- */

@@ -103,8 +103,15 @@ int he_ledger_read(he_ctx *cx, uint64_t *ks_by_level, uint64_t *n_boot, int32_t 
     if (n_boot) *n_boot = cx->n_boot;
     if (reset) {
         memset(cx->ks_by_level, 0, sizeof(cx->ks_by_level));
+        memset(cx->ops_by_level, 0, sizeof(cx->ops_by_level));
         cx->n_boot = 0;
     }
+    return HE_OK;
+}
+
+int he_ledger_ops(const he_ctx *cx, uint32_t kind, uint64_t *by_level) {
+    if (!cx || !by_level || kind > 3) return HE_EINVAL;
+    memcpy(by_level, cx->ops_by_level[kind], sizeof(uint64_t) * cx->nq);
     return HE_OK;
 }
 

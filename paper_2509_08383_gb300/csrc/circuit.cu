@@ -541,6 +541,7 @@ static Ct apply_level(he_ctx *cx, const he_ct *x, LinLevel &L, double target) {
         dm.out0 = dst;
         dm.out1 = dst + (size_t)ne * N;
         ew_diag_mac(dm, ne, cx->log_n, s);
+        cx->ops_by_level[2][l] += (uint64_t)dm.n * (uint64_t)B;
         if (!rot) {
             if (have) ew_add(qp(tot), qp(tot), qp(inner), 2 * B * ne, 0, cx->log_n, s);
             have = true;

@@ -645,6 +645,7 @@ Ct op_add(he_ctx *cx, const he_ct *a, const he_ct *b, bool sub) {
     same_batch(a, b);
     same_scale(a, b);
     int l = std::min(a->level, b->level);
+    cx->ops_by_level[3][l] += (uint64_t)a->batch;
     Ct out(ct_alloc(cx, l, a->scale, a->batch));
     ew_add(ct_rows(out.get()), ct_rows(a, l), ct_rows(b, l), nrows(a, l), sub ? 1 : 0, cx->log_n, cx->stream);
     return out;
@@ -688,6 +689,7 @@ static Rows plain_rows(he_ctx *cx, Scratch &sc, const double *d_pt, int n_pt, in
 
 Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt) {
     int l = a->level;
+    cx->ops_by_level[2][l] += (uint64_t)a->batch;
     Scratch sc{cx, {}};
     Rows pt = plain_rows(cx, sc, d_pt, n_pt, l);
     Ct out(ct_alloc(cx, l, scale_out, a->batch));
@@ -805,6 +807,7 @@ Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
     if (!rk) throw Error{HE_ENOKEY, "relinearisation key not generated"};
     const int l = std::min(a->level, b->level), B = a->batch;
     const size_t N = cx->N();
+    cx->ops_by_level[1][l] += (uint64_t)B;
     Ct out(ct_alloc(cx, l, a->scale * b->scale, B));
     Scratch sc{cx, {}};
     u64 *d2 = B == 1 ? cx->sc_a : sc.get((size_t)B * (l + 1) * N);
@@ -819,6 +822,7 @@ Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
 Ct op_rescale(he_ctx *cx, const he_ct *a) {
     int l = a->level;
     if (l < 1) throw Error{HE_ELEVEL, "cannot rescale a level-0 ciphertext"};
+    cx->ops_by_level[0][l] += (uint64_t)a->batch;
     const size_t N = cx->N();
     const int np2 = 2 * a->batch;
     cudaStream_t s = cx->stream;

@@ -78,9 +78,11 @@ struct he_ctx {
     std::vector<he::KeyDev> keys;
     std::unordered_set<he_ct *> live;      // ciphertexts handed out and not yet freed
     std::shared_ptr<he::Boot> boot_state;  // bootstrapping tables, when prepared
-    // operation ledger: key switches by level, bootstraps
+    // operation ledger: key switches by level, bootstraps, and the other
+    // ciphertext operations by level (he_ledger_ops)
     uint64_t ks_by_level[HE_MAX_PRIMES] = {0};
     uint64_t n_boot = 0;
+    uint64_t ops_by_level[4][HE_MAX_PRIMES] = {{0}};  // rescales, tensor products, plaintext products, additions
 
     ~he_ctx();
     size_t N() const { return (size_t)n; }

@@ -64,6 +64,7 @@ def lib():
             "he_launch_count": [],
             "he_profile_enable": [i32],
             "he_ledger_read": [VP, pu64, pu64, i32],
+            "he_ledger_ops": [VP, u32, pu64],
             "he_profile_read": [i32, C.POINTER(u64), pd, pd],
             "he_keygen_relin": [VP],
             "he_keygen_galois": [VP, u64],
@@ -254,6 +255,18 @@ class Context:
         nb = np.zeros(1, dtype=np.uint64)
         self._chk(lib().he_ledger_read(self.ptr, _u64ptr(ks), _u64ptr(nb), int(bool(reset))))
         return ks.astype(np.int64), int(nb[0])
+
+    LEDGER_KINDS = ("rescale", "tensor", "plain_mul", "add")
+
+    def ledger_ops(self):
+        """{kind: operations per level [n_q]} since the last ledger reset, for
+        kind in rescale, tensor, plain_mul, add (read before ledger(reset=True))."""
+        out = {}
+        for i, name in enumerate(self.LEDGER_KINDS):
+            v = np.zeros(self.nq, dtype=np.uint64)
+            self._chk(lib().he_ledger_ops(self.ptr, i, _u64ptr(v)))
+            out[name] = v.astype(np.int64)
+        return out
 
     def memory(self):
         a, b = C.c_size_t(), C.c_size_t()
