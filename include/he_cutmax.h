@@ -180,8 +180,29 @@ int he_automorphism(he_ctx *ctx, const he_ct *a, uint64_t g, he_ct **out);
  * without a key: X^(N/2) is i in every slot, so e = N/2 multiplies the
  * message by i and e = 3N/2 by -i */
 int he_mul_monomial(he_ctx *ctx, const he_ct *a, uint64_t e, he_ct **out);
-/* rotate-and-sum over 2^steps consecutive slots (App. D): log2 rotations */
+/* rotate-and-sum over 2^steps consecutive slots (App. D): every slot i gets
+ * the sum of slots i .. i + 2^steps - 1 (cyclically).  Computed in hoisted
+ * stages of radix R = 2^L (he_ctx_set_rotsum_radix, default L = 3): stage s
+ * covers the doublings [s L, min((s+1) L, steps)) and adds to x its
+ * rotations by r 2^(s L), 0 < r < 2^len (he_rotsum_stage), which needs the
+ * rotation keys of those amounts (he_cutmax_prepare generates them).  With
+ * L = 1 its stages are the textbook doublings x += rot(x, 2^i), each hoisted. */
 int he_rotsum(he_ctx *ctx, const he_ct *a, uint32_t steps, he_ct **out);
+/* One hoisted stage: out = a + sum_r rot(a, rots[r]) for n_rots (1..15)
+ * rotation amounts, with ONE ModUp of a's c1 shared by every rotation (the
+ * digits read through each automorphism), the key inner products of all of
+ * them and P (c0 + sum_r sigma_r(c0)) summed in the key-switching basis,
+ * and ONE ModDown (hoisting: Halevi-Shoup).  It encrypts the same message as
+ * the rotations and additions one by one, with key-switching noise of the
+ * same size; the ciphertexts differ (the automorphism meets the approximate
+ * basis conversion after it instead of before it, and one ModDown rounds
+ * the summed products).  HE_ENOKEY when a rotation key is missing. */
+int he_rotsum_stage(he_ctx *ctx, const he_ct *a, const int32_t *rots, size_t n_rots, he_ct **out);
+/* log2 of the rotate-and-sum radix (1..4: radix 2, 4, 8, 16) used by
+ * he_rotsum, cutmax, nucleus_sample and the constant bootstrap's trace; set
+ * it before he_cutmax_prepare / he_bootstrap_prepare, which generate the
+ * rotation keys its stages need.  HE_EINVAL outside 1..4. */
+int he_ctx_set_rotsum_radix(he_ctx *ctx, uint32_t log2_radix);
 /* Hybrid key switch of a raw polynomial: host d[(level+1)*N] coefficient
  * form -> host out0/out1[(level+1)*N] coefficient form, with key g. */
 int he_keyswitch_raw(he_ctx *ctx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out0, uint64_t *out1);

@@ -34,12 +34,27 @@ import numpy as np
 from . import encoding as enc
 
 
+ROTSUM_LOG_RADIX = 3
+
+
+def rotsum_stages(steps, log_radix=ROTSUM_LOG_RADIX):
+    """The rotate-and-sum over 2^steps slots as hoisted stages: stage i covers
+    the doublings [i L, min((i+1) L, steps)) and adds the rotations by
+    r 2^(i L), 0 < r < 2^len (L = log_radix)."""
+    out = []
+    for start in range(0, steps, log_radix):
+        ln = min(log_radix, steps - start)
+        out.append([r << start for r in range(1, 1 << ln)])
+    return out
+
+
 class HE:
     """Helpers implementing the scale rule over an oracle Context."""
 
-    def __init__(self, ctx, delta):
+    def __init__(self, ctx, delta, rotsum_log_radix=ROTSUM_LOG_RADIX):
         self.ctx = ctx
         self.delta = float(delta)
+        self.rotsum_log_radix = rotsum_log_radix
 
     def q(self, level):
         return self.ctx.primes[level]
@@ -95,8 +110,11 @@ class HE:
         return self.ctx.add_plain(ct, pt)
 
     def rotsum(self, ct, steps):
-        for i in range(steps):
-            ct = self.ctx.add(ct, self.ctx.rotate(ct, 1 << i))
+        """Every slot i gets the sum of slots i .. i + 2^steps - 1 (App. D), in
+        hoisted stages (each x + sum_r rot(x, r) through one ModUp and one
+        ModDown)."""
+        for rots in rotsum_stages(steps, self.rotsum_log_radix):
+            ct = self.ctx.rotsum_stage(ct, rots)
         return ct
 
     def power(self, u, p):
@@ -111,8 +129,8 @@ class HE:
         return acc
 
 
-def required_rotations(plan):
-    return [1 << i for i in range(plan.rotsum_steps)]
+def required_rotations(plan, log_radix=ROTSUM_LOG_RADIX):
+    return sorted({r for rots in rotsum_stages(plan.rotsum_steps, log_radix) for r in rots})
 
 
 def invsqrt_goldschmidt(he, V, kappa, y0, k):
@@ -273,6 +291,10 @@ class LevelSim:
     def rotate(self, a, r):
         return self.automorphism(a, 0)
 
+    def rotsum_stage(self, a, rots):
+        self.ks[a.level] = self.ks.get(a.level, 0) + len(rots)
+        return _SimCt(a.level, a.scale)
+
     def conj(self, a):
         return self.automorphism(a, 0)
 
@@ -341,6 +363,10 @@ class CountingCtx:
     def rotate(self, a, r):
         self._ks(a.level)
         return self._ctx.rotate(a, r)
+
+    def rotsum_stage(self, a, rots):
+        self.ks[a.level] = self.ks.get(a.level, 0) + len(rots)
+        return self._ctx.rotsum_stage(a, rots)
 
     def conj(self, a):
         self._ks(a.level)
@@ -455,7 +481,7 @@ def refresh_schedule(he, ct, plan, out_level):
         sim = LevelSim(primes, ctx.nq, ctx.log_n)
         dry = _DryBoot(out_level)
         tally = {}
-        _boot_circuit(HE(sim, he.delta), start, plan, dry, hr, yb, tally)
+        _boot_circuit(HE(sim, he.delta, he.rotsum_log_radix), start, plan, dry, hr, yb, tally)
         cost = 2 * dry.general + dry.const + 1000 * tally.get("x", 0)
         key = (cost, dry.general + dry.const)
         if best_key is None or key < best_key:
@@ -473,7 +499,7 @@ def cutmax_he_boot(he, ct, plan, boot, stats=None):
     hr, yb = refresh_schedule(he, ct, plan, boot.out_level())
     cctx, cboot = CountingCtx(he.ctx), CountingBoot(boot)
     tally = {}
-    out = _boot_circuit(HE(cctx, he.delta), ct, plan, cboot, hr, yb, tally)
+    out = _boot_circuit(HE(cctx, he.delta, he.rotsum_log_radix), ct, plan, cboot, hr, yb, tally)
     if stats is not None:
         stats.update(h_refresh=hr, y_boot=yb, general=cboot.general, const=cboot.const, x_refresh=tally.get("x", 0),
                      ks=dict(cctx.ks))

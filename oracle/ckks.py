@@ -63,6 +63,7 @@ def lib():
             "or_mul": (vp, [vp, vp, vp]),
             "or_rescale": (vp, [vp, vp]),
             "or_automorphism": (vp, [vp, vp, u64]),
+            "or_rotsum_stage": (vp, [vp, vp, P(np.int64, flags="C"), ip]),
             "or_rot_galois": (u64, [ip, i64]),
             "or_mod_raise": (vp, [vp, vp, ip]),
             "or_mul_monomial": (vp, [vp, vp, u64]),
@@ -160,7 +161,7 @@ class Ciphertext:
         self.ptr = ptr
 
     def __del__(self):
-        if self.ptr and _lib is not None:
+        if getattr(self, "ptr", None) and _lib is not None:
             _lib.or_ct_free(self.ptr)
             self.ptr = None
 
@@ -289,6 +290,12 @@ class Context:
 
     def automorphism(self, a, g):
         return Ciphertext(self, lib().or_automorphism(self.ptr, a.ptr, int(g)))
+
+    def rotsum_stage(self, a, rots):
+        """a + sum_r rot(a, r) as one hoisted stage (one ModUp of c1, the key
+        products of every rotation summed, one ModDown)."""
+        arr = np.ascontiguousarray(rots, dtype=np.int64)
+        return Ciphertext(self, lib().or_rotsum_stage(self.ptr, a.ptr, arr, len(arr)))
 
     def rotate(self, a, r):
         return self.automorphism(a, rot_galois(self.log_n, r))

@@ -950,6 +950,112 @@ u64 or_rot_galois(int log_n, i64 r) {
     return g;
 }
 
+/* One hoisted rotate-and-sum stage (App. D's rotate-and-sum, hoisted as by
+ * Halevi and Shoup): out = a + sum_r rot(a, rots[r]).
+ *   ext_j = ModUp of c1 for digit j (coefficient form; the digit's own rows
+ *           are c1 itself), computed ONCE;
+ *   acc   = sum_r sum_j NTT(sigma_r(ext_j)) * key_r,j  over Q_l u P, plus
+ *           P * (c0 + sum_r sigma_r(c0)) on the Q rows;
+ *   out   = (ModDown(acc_0), ModDown(acc_1) + c1).
+ * sigma_r is X -> X^g_r applied to each row's coefficients mod its prime.
+ * Returns NULL when a rotation key is missing. */
+typedef struct {
+    or_ctx *cx; const or_ct *a; int l, ext, beta, nr; const u64 *gal; or_key *const *keys; const int *pidx;
+    const u64 *ecoef; u64 *acc0, *acc1;
+} rs_args;
+static void rs_ext_body(void *vp, int t) {
+    /* ext rows of every digit for target row t (coefficient form) */
+    rs_args *A = (rs_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n; int pt = A->pidx[t]; u64 qt = cx->primes[pt];
+    const u64 *d = A->a->c[1];
+    u64 *ec = (u64 *)A->ecoef;
+    for (int j = 0; j < A->beta; j++) {
+        int lo = j * cx->alpha, hi = lo + cx->alpha; if (hi > A->l + 1) hi = A->l + 1;
+        int cnt = hi - lo;
+        u64 *e = ec + ((u64)j * A->ext + t) * n;
+        if (pt >= lo && pt < hi) { memcpy(e, d + (u64)pt * n, n * 8); continue; }
+        u64 *qhinv = malloc(8 * cnt), *qh = malloc(8 * cnt);
+        for (int a = 0; a < cnt; a++) {
+            u64 q = cx->primes[lo + a], v = 1, w = 1;
+            for (int b = 0; b < cnt; b++)
+                if (b != a) { v = mulmod(v, cx->primes[lo + b] % q, q); w = mulmod(w, cx->primes[lo + b] % qt, qt); }
+            qhinv[a] = or_invmod(v, q);
+            qh[a] = w;
+        }
+        for (u64 c = 0; c < n; c++) {
+            u64 sum = 0;
+            for (int a = 0; a < cnt; a++) {
+                u64 qa = cx->primes[lo + a];
+                u64 y = mulmod(d[(u64)(lo + a) * n + c], qhinv[a], qa);
+                sum = addmod(sum, mulmod(y % qt, qh[a], qt), qt);
+            }
+            e[c] = sum;
+        }
+        free(qhinv); free(qh);
+    }
+}
+static void rs_acc_body(void *vp, int t) {
+    rs_args *A = (rs_args *)vp;
+    or_ctx *cx = A->cx; u64 n = cx->n; int pt = A->pidx[t]; u64 q = cx->primes[pt];
+    u64 *e = malloc(n * 8), *y = malloc(n * 8);
+    u64 *a0 = A->acc0 + (u64)t * n, *a1 = A->acc1 + (u64)t * n;
+    for (int r = 0; r < A->nr; r++)
+        for (int j = 0; j < A->beta; j++) {
+            automorph(A->ecoef + ((u64)j * A->ext + t) * n, e, n, A->gal[r], q);
+            poly_ntt(cx, e, pt);
+            const u64 *kb = A->keys[r]->b[j] + (u64)pt * n, *ka = A->keys[r]->a[j] + (u64)pt * n;
+            for (u64 c = 0; c < n; c++) {
+                a0[c] = addmod(a0[c], mulmod(e[c], kb[c], q), q);
+                a1[c] = addmod(a1[c], mulmod(e[c], ka[c], q), q);
+            }
+        }
+    if (t <= A->l) {
+        const u64 *c0 = A->a->c[0] + (u64)t * n;
+        memcpy(y, c0, n * 8);
+        for (int r = 0; r < A->nr; r++) {
+            automorph(c0, e, n, A->gal[r], q);
+            for (u64 c = 0; c < n; c++) y[c] = addmod(y[c], e[c], q);
+        }
+        u64 pm = 1;
+        for (int p = 0; p < cx->np; p++) pm = mulmod(pm, cx->primes[cx->nq + p] % q, q);
+        for (u64 c = 0; c < n; c++) y[c] = mulmod(y[c], pm, q);
+        poly_ntt(cx, y, pt);
+        for (u64 c = 0; c < n; c++) a0[c] = addmod(a0[c], y[c], q);
+    }
+    free(e); free(y);
+}
+or_ct *or_rotsum_stage(or_ctx *cx, const or_ct *a, const i64 *rots, int n_rots) {
+    if (n_rots < 1) return NULL;
+    int l = a->level, K = cx->np, ext = l + 1 + K; u64 n = cx->n;
+    int beta = (l + 1 + cx->alpha - 1) / cx->alpha;
+    u64 *gal = malloc(8 * n_rots);
+    or_key **keys = malloc(sizeof(or_key *) * n_rots);
+    for (int r = 0; r < n_rots; r++) {
+        gal[r] = or_rot_galois(cx->log_n, rots[r]);
+        keys[r] = find_key(cx, gal[r]);
+        if (!keys[r]) { free(gal); free(keys); return NULL; }
+    }
+    int *pidx = malloc(sizeof(int) * ext);
+    for (int t = 0; t <= l; t++) pidx[t] = t;
+    for (int t = 0; t < K; t++) pidx[l + 1 + t] = cx->nq + t;
+    u64 *ecoef = malloc((u64)beta * ext * n * 8);
+    u64 *acc0 = calloc((u64)ext * n, 8), *acc1 = calloc((u64)ext * n, 8);
+    rs_args A = {cx, a, l, ext, beta, n_rots, gal, keys, pidx, ecoef, acc0, acc1};
+    parallel_for(ext, rs_ext_body, &A);
+    parallel_for(ext, rs_acc_body, &A);
+    it_args B = {cx, acc0, acc1, ext, pidx};
+    parallel_for(2 * ext, it_body, &B);
+    or_ct *r = or_ct_new(cx, l, a->scale);
+    moddown_exact(cx, acc0, acc1, l, r->c[0], r->c[1]);
+    for (int i = 0; i <= l; i++) {
+        u64 q = cx->primes[i];
+        for (u64 c = 0; c < n; c++)
+            r->c[1][(u64)i * n + c] = addmod(r->c[1][(u64)i * n + c], a->c[1][(u64)i * n + c], q);
+    }
+    free(gal); free(keys); free(pidx); free(ecoef); free(acc0); free(acc1);
+    return r;
+}
+
 /* Raise a level-0 ciphertext to the top level: centred lift of each
  * coefficient of both polynomials modulo q0, reduced modulo every q_i. */
 or_ct *or_mod_raise(or_ctx *cx, const or_ct *a, int level) {

@@ -370,14 +370,33 @@ int he_rotsum(he_ctx *cx, const he_ct *a, uint32_t steps, he_ct **out) {
     if (!cx || !a || !out) return HE_EINVAL;
     API_TRY
     own(cx, a);
-    Ct cur = op_copy(cx, a);
-    for (uint32_t i = 0; i < steps; i++) {
-        Ct r = op_automorph(cx, cur.get(), rot_galois(cx, (i64)1 << i));
-        cur = op_add(cx, cur.get(), r.get(), false);
-    }
+    need(steps < 32, "too many rotate-and-sum steps");
+    Ct cur = op_rotsum(cx, a, (int)steps);
     launched(cx, "rotsum");
     *out = cur.release();
     API_CATCH(cx)
+}
+
+int he_rotsum_stage(he_ctx *cx, const he_ct *a, const int32_t *rots, size_t n_rots, he_ct **out) {
+    if (!cx || !a || !rots || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, a);
+    need(n_rots >= 1 && n_rots <= 15, "a hoisted stage takes 1..15 rotations");
+    std::vector<i64> r(rots, rots + n_rots);
+    Ct res = op_rotsum_stage(cx, a, r);
+    launched(cx, "rotsum stage");
+    *out = res.release();
+    API_CATCH(cx)
+}
+
+int he_ctx_set_rotsum_radix(he_ctx *cx, uint32_t log2_radix) {
+    if (!cx) return HE_EINVAL;
+    if (log2_radix < 1 || log2_radix > 4) {
+        cx->err = "rotate-and-sum radix must be 2, 4, 8 or 16 (log2 1..4)";
+        return HE_EINVAL;
+    }
+    cx->rotsum_log_radix = (int)log2_radix;
+    return HE_OK;
 }
 
 int he_keyswitch_raw(he_ctx *cx, const uint64_t *d, uint32_t level, uint64_t g, uint64_t *out0, uint64_t *out1) {

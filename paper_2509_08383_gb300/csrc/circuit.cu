@@ -97,14 +97,8 @@ struct HE {
             encode_dev(cx, d_vec + (size_t)i * n_slots, nullptr, n_slots, ct->scale, d_pt + i * cx->N());
         return op_add_plain(cx, ct, d_pt, n_pt);
     }
-    Ct rotsum(const he_ct *ct, int steps) {
-        Ct cur = op_copy(cx, ct);
-        for (int i = 0; i < steps; i++) {
-            Ct r = op_automorph(cx, cur.get(), rot_galois(cx, (i64)1 << i));
-            cur = op_add(cx, cur.get(), r.get(), false);
-        }
-        return cur;
-    }
+    // rotate-and-sum in hoisted stages of the context's radix (op_rotsum)
+    Ct rotsum(const he_ct *ct, int steps) { return op_rotsum(cx, ct, steps); }
     Ct power(const he_ct *u, int p) {
         Ct sq = op_copy(cx, u), acc;
         int pp = p;
@@ -194,10 +188,16 @@ static int power_depth(int p) {
 }
 
 void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois) {
-    int steps = rotsum_steps(pl, cx->n / 2);
-    if (pl.bootstrap) steps = cx->log_n - 1;  // the constant bootstrap's trace rotates by every 2^i
-    for (int i = 0; i < steps; i++) galois.push_back(rot_galois(cx, (i64)1 << i));
+    // the rotate-and-sum stages; with bootstrapping also those of the constant
+    // bootstrap's trace (every slot) and the rotation by N/4
+    std::vector<int> all_steps = {rotsum_steps(pl, cx->n / 2)};
+    if (pl.bootstrap) all_steps.push_back(cx->log_n - 1);
+    for (int steps : all_steps)
+        for (const auto &rots : rotsum_stages(steps, cx->rotsum_log_radix))
+            for (i64 r : rots) galois.push_back(rot_galois(cx, r));
     if (pl.bootstrap) galois.push_back(rot_galois(cx, cx->n / 4));  // packed Goldschmidt pair
+    std::sort(galois.begin(), galois.end());
+    galois.erase(std::unique(galois.begin(), galois.end()), galois.end());
 }
 
 static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl);
@@ -786,6 +786,10 @@ void boot_prepare(he_ctx *cx, int K, int r, int d) {
                 if (g % h) gs.push_back(rot_galois(cx, g));
         }
     gs.push_back(2 * cx->N() - 1);
+    // the constant bootstrap's trace: a rotate-and-sum over every slot
+    for (const auto &rots : rotsum_stages(cx->log_n - 1, cx->rotsum_log_radix))
+        for (i64 r : rots) gs.push_back(rot_galois(cx, r));
+    gs.push_back(rot_galois(cx, h / 2));
     std::sort(gs.begin(), gs.end());
     gs.erase(std::unique(gs.begin(), gs.end()), gs.end());
     B->galois = gs;
@@ -874,8 +878,7 @@ Ct bootstrap_const(he_ctx *cx, const he_ct *in) {
     // EvalMod input on the level (and scale) where bootstrap_stage has it
     Ct x = op_mod_raise(cx, low.get(), cx->nq - 3);
     x->scale = (double)q0 * (double)(B->K + 1);
-    for (int st = 1; st < slots; st *= 2)  // trace: N/2 (t_0 + t_(N/2) X^(N/2))
-        x = op_add(cx, x.get(), op_automorph(cx, x.get(), rot_galois(cx, st)).get(), false);
+    x = op_rotsum(cx, x.get(), cx->log_n - 1);  // trace: N/2 (t_0 + t_(N/2) X^(N/2))
     x->scale *= (double)slots;
     // slots read (t_0 + i t_(N/2)) / (q0 (K+1)): real and imaginary parts, packed
     Ct xc = op_automorph(cx, x.get(), 2 * cx->N() - 1);

@@ -801,6 +801,74 @@ void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Row
     keyswitch_ext(cx, d_ntt, ext, l, key, 0, out, add, add_mask, B, d_stride);
 }
 
+std::vector<std::vector<i64>> rotsum_stages(int steps, int log_radix) {
+    if (log_radix < 1 || log_radix > 4) throw Error{HE_EINVAL, "rotate-and-sum radix must be 2, 4, 8 or 16"};
+    std::vector<std::vector<i64>> st;
+    for (int start = 0; start < steps; start += log_radix) {
+        const int len = std::min(log_radix, steps - start);
+        std::vector<i64> rots;
+        for (i64 r = 1; r < ((i64)1 << len); r++) rots.push_back(r << start);
+        st.push_back(rots);
+    }
+    return st;
+}
+
+// x + sum_r rot(x, r): the rotations share one ModUp of c1; the key inner
+// products of all of them (digits read through each automorphism) and
+// P (c0 + sum_r sigma_r(c0)) are summed in the QP basis; one ModDown, then
+// + c1 on the second polynomial.  The same message as the rotations and
+// additions one by one, with key-switching noise of the same size (the
+// automorphism acts after the approximate basis conversion instead of before
+// it, and one ModDown rounds the summed products).
+Ct op_rotsum_stage(he_ctx *cx, const he_ct *a, const std::vector<i64> &rots) {
+    const int n_keys = (int)rots.size();
+    if (n_keys < 1 || n_keys > ROTSUM_MAX_KEYS) throw Error{HE_EINVAL, "a hoisted stage takes 1..15 rotations"};
+    const int l = a->level, B = a->batch;
+    const LevelTabs &T = cx->lv[l];
+    const size_t N = cx->N(), ms = ct_member_stride(a);
+    KeyIPMulti kp;
+    for (int r = 0; r < n_keys; r++) {
+        const u64 g = rot_galois(cx, rots[r]);
+        const KeyDev *key = find_key(cx, g);
+        if (!key) throw Error{HE_ENOKEY, "rotation key for " + std::to_string(rots[r]) + " not generated"};
+        kp.keys[r] = key->data;
+        kp.gal[r] = g;
+    }
+    Scratch sc{cx, {}};
+    u64 *ext = B == 1 ? cx->ks_ext : sc.get((size_t)B * ks_ext_words(cx, l));
+    u64 *acc = B == 1 ? cx->ks_acc : sc.get((size_t)B * ks_acc_words(cx, l));
+    modup(cx, ct_poly(a, 1), l, ext, B, ms);
+    kp.d_ntt = ct_poly(a, 1);
+    kp.ext = ext;
+    kp.c0 = ct_poly(a, 0);
+    kp.acc = acc;
+    kp.n_rows = T.n_ext;
+    kp.l1 = l + 1;
+    kp.nq = cx->nq;
+    kp.np = cx->np;
+    kp.alpha = cx->alpha;
+    kp.beta = T.beta;
+    kp.key_limbs = cx->nq + cx->np;
+    kp.slot = cx->slot;
+    kp.n_keys = n_keys;
+    kp.pmod = cx->p_mod;
+    kp.batch = B;
+    kp.d_stride = kp.c0_stride = B == 1 ? 0 : ms;
+    kp.ext_stride = ks_ext_words(cx, l);
+    kp.acc_stride = ks_acc_words(cx, l);
+    keyswitch_inner_multi(kp, cx->log_n, cx->stream);
+    cx->ks_by_level[l] += (uint64_t)n_keys * (uint64_t)B;
+    Ct out(ct_alloc(cx, l, a->scale, B));
+    moddown(cx, acc, l, ct_rows(out.get()), ct_rows(a), 2, B);
+    return out;
+}
+
+Ct op_rotsum(he_ctx *cx, const he_ct *a, int steps) {
+    Ct cur = op_copy(cx, a);
+    for (const auto &rots : rotsum_stages(steps, cx->rotsum_log_radix)) cur = op_rotsum_stage(cx, cur.get(), rots);
+    return cur;
+}
+
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
     same_batch(a, b);
     const KeyDev *rk = find_key(cx, 0);

@@ -83,6 +83,7 @@ struct he_ctx {
     uint64_t ks_by_level[HE_MAX_PRIMES] = {0};
     uint64_t n_boot = 0;
     uint64_t ops_by_level[4][HE_MAX_PRIMES] = {{0}};  // rescales, tensor products, plaintext products, additions
+    int rotsum_log_radix = 3;              // rotate-and-sum stages of 2^this slots (he_ctx_set_rotsum_radix)
 
     ~he_ctx();
     size_t N() const { return (size_t)n; }
@@ -165,6 +166,13 @@ void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev 
 void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask, int B = 1);
 void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
                    const Rows &out, const Rows &add, int add_mask, int B = 1, size_t d_stride = 0);
+// rotate-and-sum (App. D) over 2^steps consecutive slots in hoisted stages:
+// stage i covers doublings [i L, min((i+1) L, steps)) (L = the context's
+// log2 radix) and adds to x its rotations by r 2^(i L), 0 < r < 2^len, all
+// through one ModUp of c1 and one ModDown of the summed inner products
+std::vector<std::vector<i64>> rotsum_stages(int steps, int log_radix);
+Ct op_rotsum_stage(he_ctx *cx, const he_ct *a, const std::vector<i64> &rots);
+Ct op_rotsum(he_ctx *cx, const he_ct *a, int steps);
 
 // ---- circuits (circuit.cu)
 struct Plan {

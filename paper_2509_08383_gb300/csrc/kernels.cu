@@ -1002,6 +1002,102 @@ void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
              8.0 * (2.0 * k.beta + (k.beta + 2.0) * k.batch) * (double)k.n_rows * (double)(1 << log_n));
 }
 
+// Hoisted rotate-and-sum stage (see KeyIPMulti): for each key r the beta
+// digit products (read through the automorphism's permutation) are summed in
+// 128 bits and reduced once, then added mod q across keys; the Q rows take
+// P * (c0 + sum_r sigma_r(c0)) on top, so that ModDown returns the rotations'
+// c0 parts exactly.  MB members per thread share every key word loaded.
+template <int MB>
+__global__ void __launch_bounds__(EW_T) k_keyswitch_inner_multi(KeyIPMulti kp, int log_n) {
+    const PrimeConsts &pc = c_pcs[kp.slot];
+    const int t = blockIdx.y, b0 = blockIdx.z * MB, nb = min(MB, kp.batch - b0);
+    const bool q_row = t < kp.l1;
+    const int p = q_row ? t : kp.nq + (t - kp.l1);
+    const u64 q = pc.m[p].q, qn = pc.mont_qinv[p];
+    const int jt = q_row ? t / kp.alpha : -1;
+    const size_t row = (size_t)t << log_n;
+    EW_PAIRS_FOR(k, log_n) {
+        u64 sum[MB][4];  // (b part at k, k+1; a part at k, k+1)
+#pragma unroll
+        for (int m = 0; m < MB; m++)
+#pragma unroll
+            for (int i = 0; i < 4; i++) sum[m][i] = 0;
+        for (int r = 0; r < kp.n_keys; r++) {
+            const size_t s0 = automorph_src((u32)k, kp.gal[r], log_n), s1 = automorph_src((u32)k + 1, kp.gal[r], log_n);
+            const u64 *key = kp.keys[r];
+            u64 acc[MB][8];
+#pragma unroll
+            for (int m = 0; m < MB; m++)
+#pragma unroll
+                for (int i = 0; i < 8; i++) acc[m][i] = 0;
+            for (int j = 0; j < kp.beta; j++) {
+                const ulonglong2 kb = ld2(key + ((((size_t)(2 * j) * kp.key_limbs + p)) << log_n) + k);
+                const ulonglong2 ka = ld2(key + ((((size_t)(2 * j + 1) * kp.key_limbs + p)) << log_n) + k);
+#pragma unroll
+                for (int m = 0; m < MB; m++) {
+                    if (m >= nb) break;
+                    const size_t mb = (size_t)(b0 + m);
+                    const u64 *xs = (j == jt) ? kp.d_ntt + mb * kp.d_stride + row
+                                              : kp.ext + mb * kp.ext_stride + (((size_t)j * kp.n_rows + t) << log_n);
+                    const u64 x0 = xs[s0], x1 = xs[s1];
+                    mac128(acc[m][0], acc[m][1], x0, kb.x);
+                    mac128(acc[m][2], acc[m][3], x1, kb.y);
+                    mac128(acc[m][4], acc[m][5], x0, ka.x);
+                    mac128(acc[m][6], acc[m][7], x1, ka.y);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < MB; m++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) sum[m][i] = add_mod(sum[m][i], mont_reduce(acc[m][2 * i], acc[m][2 * i + 1], q, qn), q);
+        }
+        if (q_row) {  // + P (c0 + sum_r sigma_r(c0)); P = 0 on the special rows
+            const u64 w = kp.pmod.v[p], ws = kp.pmod.s[p];
+#pragma unroll
+            for (int m = 0; m < MB; m++) {
+                if (m >= nb) break;
+                const u64 *c = kp.c0 + (size_t)(b0 + m) * kp.c0_stride + row;
+                const ulonglong2 cv = ld2(c + k);
+                u64 y0 = cv.x, y1 = cv.y;
+                for (int r = 0; r < kp.n_keys; r++) {
+                    y0 = add_mod(y0, c[automorph_src((u32)k, kp.gal[r], log_n)], q);
+                    y1 = add_mod(y1, c[automorph_src((u32)k + 1, kp.gal[r], log_n)], q);
+                }
+                sum[m][0] = add_mod(sum[m][0], shoup_mul(y0, w, ws, q), q);
+                sum[m][1] = add_mod(sum[m][1], shoup_mul(y1, w, ws, q), q);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < MB; m++) {
+            if (m >= nb) break;
+            u64 *acc_m = kp.acc + (size_t)(b0 + m) * kp.acc_stride;
+            st2(acc_m + row + k, sum[m][0], sum[m][1]);
+            st2(acc_m + (((size_t)kp.n_rows + t) << log_n) + k, sum[m][2], sum[m][3]);
+        }
+    }
+}
+void keyswitch_inner_multi(const KeyIPMulti &k, int log_n, cudaStream_t s) {
+    need16(k.d_ntt);
+    need16(k.ext);
+    need16(k.c0);
+    need16(k.acc);
+    if (k.n_keys < 1 || k.n_keys > ROTSUM_MAX_KEYS) throw Error{HE_EINVAL, "hoisted stage: 1..15 keys"};
+    for (int r = 0; r < k.n_keys; r++) need16(k.keys[r]);
+    if (k.batch < 1 || (k.batch > 1 && ((k.d_stride | k.ext_stride | k.acc_stride | k.c0_stride) & 1)))
+        throw Error{HE_EINVAL, "hoisted stage: bad batch layout"};
+    constexpr int MB = 2;
+    dim3 grid = ew_grid(k.n_rows, log_n);
+    grid.z = (unsigned)(k.batch == 1 ? 1 : (k.batch + MB - 1) / MB);
+    prof_begin(PROF_KS_INNER, s);
+    if (k.batch == 1) k_keyswitch_inner_multi<1><<<grid, EW_T, 0, s>>>(k, log_n);
+    else k_keyswitch_inner_multi<MB><<<grid, EW_T, 0, s>>>(k, log_n);
+    // algorithmic bytes: every key digit (b and a) once, per member the beta
+    // input digits, c0 on the Q rows and the two outputs
+    prof_end(PROF_KS_INNER, s,
+             8.0 * (double)(1 << log_n) *
+                 ((2.0 * k.beta * k.n_keys + (k.beta + 2.0) * k.batch) * (double)k.n_rows + (double)k.batch * k.l1));
+}
+
 __global__ void __launch_bounds__(EW_T) k_moddown_finish(Rows out, Rows acc, Rows conv, ScalarTab pinv,
                                                          Rows add_to, int add_mask, int log_n) {
     const int r = blockIdx.y, p = out.prime(r);

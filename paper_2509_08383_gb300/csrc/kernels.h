@@ -116,6 +116,27 @@ struct KeyIP {
     size_t d_stride = 0, ext_stride = 0, acc_stride = 0;
 };
 void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s);
+// Hoisted rotate-and-sum stage: the sum over n_keys rotations r of the key
+// inner products of sigma_r(ext) (one shared ModUp of c1, read through
+// X -> X^gal[r] in NTT form), plus P * (c0 + sum_r sigma_r(c0)) on the Q rows,
+// for `batch` members; acc = [2][n_rows][N] per member.  Products are summed
+// per key in 128 bits (keys in Montgomery form), reduced, then added mod q.
+constexpr int ROTSUM_MAX_KEYS = 15;
+struct KeyIPMulti {
+    const u64 *d_ntt;     // c1, level limbs (NTT form)
+    const u64 *ext;       // [beta][n_rows][N] hoisted digits (rows inside the digit unused)
+    const u64 *c0;        // c0, level limbs (NTT form)
+    u64 *acc;             // [2][n_rows][N]
+    int n_rows, l1, nq, np, alpha, beta, key_limbs;
+    int slot;
+    int n_keys;
+    const u64 *keys[ROTSUM_MAX_KEYS];  // [beta][2][nq+np][N] each, Montgomery form
+    u64 gal[ROTSUM_MAX_KEYS];
+    ScalarTab pmod;       // P mod q_i
+    int batch = 1;
+    size_t d_stride = 0, ext_stride = 0, acc_stride = 0, c0_stride = 0;
+};
+void keyswitch_inner_multi(const KeyIPMulti &k, int log_n, cudaStream_t s);
 // out_i = (acc_i - conv_i) * pinv_i; polynomial p of the batch (row / lpp)
 // also adds add_to's row when bit p of add_mask is set.
 void moddown_finish(const Rows &out, const Rows &acc, const Rows &conv, const ScalarTab &pinv, int n_rows,

@@ -97,6 +97,8 @@ def lib():
             "he_automorphism": [VP, VP, u64, PP],
             "he_mul_monomial": [VP, VP, u64, PP],
             "he_rotsum": [VP, VP, u32, PP],
+            "he_rotsum_stage": [VP, VP, C.POINTER(i32), sz, PP],
+            "he_ctx_set_rotsum_radix": [VP, u32],
             "he_keyswitch_raw": [VP, pu64, u32, u64, pu64, pu64],
             "he_moddown_raw": [VP, pu64, pu64, u32, pu64, pu64],
             "he_ntt_device": [VP, VP, u32, u32, i32],
@@ -379,6 +381,16 @@ class Context:
 
     def rotsum(self, a, steps):
         return self._ct(lib().he_rotsum, a.ptr, int(steps))
+
+    def rotsum_stage(self, a, rots):
+        """a + sum_r rot(a, r): one hoisted stage (one ModUp, one ModDown)."""
+        arr = (C.c_int32 * len(rots))(*[int(r) for r in rots])
+        return self._ct(lib().he_rotsum_stage, a.ptr, arr, len(rots))
+
+    def set_rotsum_radix(self, log2_radix):
+        """Radix 2^log2_radix of the rotate-and-sum stages (default 8); set before
+        generating keys with cutmax_prepare / bootstrap_prepare."""
+        self._chk(lib().he_ctx_set_rotsum_radix(self.ptr, int(log2_radix)))
 
     def keyswitch(self, d, level, g):
         d = np.ascontiguousarray(d, dtype=np.uint64).reshape(-1)

@@ -68,11 +68,21 @@ def transform_rotations(log_n):
     return cts, stc
 
 
+ROTSUM_LOG_RADIX = 3
+
+
+def rotsum_keys(steps, log_radix=ROTSUM_LOG_RADIX):
+    """Key applications of a rotate-and-sum over 2^steps slots in hoisted
+    stages of radix 2^log_radix (the library's he_rotsum): 2^len - 1 per stage."""
+    return sum((1 << min(log_radix, steps - s)) - 1 for s in range(0, steps, log_radix))
+
+
 class Sim:
     """Level-only stand-in for a ciphertext context."""
 
-    def __init__(self, nq, log_n, boot=None):
+    def __init__(self, nq, log_n, boot=None, log_radix=ROTSUM_LOG_RADIX):
         self.nq, self.log_n, self.boot = nq, log_n, boot
+        self.log_radix = log_radix
         self.ks = Counter()
         self.n_boot = 0
         self.n_boot_const = 0             # of which constant bootstraps
@@ -148,7 +158,7 @@ class Sim:
         self.n_boot += 1
         self.n_boot_const += 1
         L = self.nq - 3                   # raised 2 levels below the top
-        self.ks[L] += self.log_n - 1 + 1  # trace, conjugation
+        self.ks[L] += rotsum_keys(self.log_n - 1, self.log_radix) + 1  # trace, conjugation
         c = self._evalmod(L - 1, d, r)    # after the packing mask
         c = self.mul(c, c)                # arcsine step y (1 + y^2/6)
         c = self.mul(c + 1, c)
@@ -236,8 +246,7 @@ def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None, deta
     m = plan.pad
 
     def rotsum(a):
-        for _ in range(steps):
-            sim.rot(a)
+        sim.ks[a] += rotsum_keys(steps, sim.log_radix)
         return a
 
     def mcr(a):

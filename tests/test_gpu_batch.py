@@ -38,7 +38,7 @@ DELTA = 2.0 ** 40
 def small():
     g = he.Context(LOG_N, CFG1_Q, CFG1_P, dnum=11, seed=7)
     g.gen_relin_key()
-    g.gen_rot_keys([1, 3, -2, 2, 4])
+    g.gen_rot_keys([1, 3, -2, 2, 4, 5, 6, 7])
     g.gen_galois_key(2 * g.n - 1)
     return g
 
@@ -78,6 +78,7 @@ OPS = {
     "add_const": lambda g, x, y: g.add_const(x, 0.3),
     "mul_int": lambda g, x, y: g.mul_int(x, -5),
     "rotsum_3": lambda g, x, y: g.rotsum(x, 3),
+    "rotsum_stage_3": lambda g, x, y: g.rotsum_stage(x, [1, 3, 4]),
     "drop_5": lambda g, x, y: g.drop(x, 5),
 }
 

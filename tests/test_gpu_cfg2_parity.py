@@ -97,6 +97,19 @@ def test_cfg2_product_relin_rescale_bit_exact(cfg2, level):
     assert _same(r_g, r_o) and r_g.scale == r_o.scale
 
 
+def test_cfg2_rotsum_stage_bit_exact(cfg2):
+    """One hoisted stage of seven rotations (radix 8) at level 13: the fused
+    seven-key inner product over 24 + 10 rows, one ModDown."""
+    g, o = cfg2
+    rots = list(range(1, 8))
+    g.gen_rot_keys(rots)
+    for r in rots[1:]:
+        o.gen_rot_key(r)
+    a_g, a_o = _pair_ct(g, o, 13, 90, 5000)
+    s_g, s_o = g.rotsum_stage(a_g, rots), o.rotsum_stage(a_o, rots)
+    assert _same(s_g, s_o) and s_g.scale == s_o.scale
+
+
 def test_cfg2_decrypt_bit_exact(cfg2):
     g, o = cfg2
     a_g, a_o = _pair_ct(g, o, 13, 77, 4000)

@@ -165,6 +165,44 @@ def test_conjugation_and_low_level_rotation(small):
     assert (g.rotate(a0_g, 1).export() == o.rotate(a0_o, 1).export()).all()
 
 
+@pytest.mark.parametrize("rots", [[3], [1, 2, 3, 4, 5, 6, 7], [8, 16, 24, 32, 40, 48, 56], [-2, 5, 511]])
+def test_rotsum_stage_bit_exact(small, rots):
+    """A hoisted stage a + sum_r rot(a, r) (one shared ModUp, the key products
+    of every rotation summed by the fused inner-product kernel, one ModDown):
+    bit-exact to the oracle's, written from the definition."""
+    g, o = small
+    rng = np.random.default_rng(len(rots) + sum(rots))
+    a_g, a_o = _same_ct(g, o, rng, ctr=41)
+    g.gen_rot_keys(rots)
+    for r in rots:
+        o.gen_rot_key(r)
+    s_g, s_o = g.rotsum_stage(a_g, rots), o.rotsum_stage(a_o, rots)
+    assert s_g.level == s_o.level and s_g.scale == s_o.scale
+    assert (s_g.export() == s_o.export()).all()
+
+
+@pytest.mark.parametrize("log_radix", [1, 2, 3, 4])
+def test_rotsum_radix_bit_exact(log_radix):
+    """he_rotsum over 10 doublings in hoisted stages of radix 2, 4, 8 and 16:
+    bit-exact to the oracle's stages, and every slot holds the total."""
+    from oracle.circuit import rotsum_stages
+    g, o = pair(11, CFG1_Q, CFG1_P, dnum=11, seed=19)
+    g.set_rotsum_radix(log_radix)
+    rots = sorted({r for st in rotsum_stages(10, log_radix) for r in st})
+    g.gen_rot_keys(rots)
+    for r in rots:
+        o.gen_rot_key(r)
+    rng = np.random.default_rng(5)
+    z = rng.uniform(-1, 1, g.slots)
+    pt = oenc.encode(z, g.log_n, 2.0 ** 40)
+    s_g = g.rotsum(g.encrypt_poly(pt, 2.0 ** 40, 3), 10)
+    s_o = HE(o, 2.0 ** 40, log_radix).rotsum(o.encrypt(pt, 2.0 ** 40, 3), 10)
+    assert (s_g.export() == s_o.export()).all()
+    assert np.abs(g.decrypt(s_g) - z.sum()).max() < 1e-5
+    with pytest.raises(he.HeError):
+        g.set_rotsum_radix(5)
+
+
 @pytest.mark.parametrize("level", [0, 1, 9, 21])
 def test_keyswitch_raw_bit_exact(small, level):
     g, o = small

@@ -397,3 +397,35 @@ def test_mod_raise_adds_multiple_of_q0():
     for k in range(n):
         I, r = divmod(t[k] - int(lo[k]), q[0])
         assert r == 0 and abs(I) <= (h + 1) // 2 + 1
+
+
+def test_hoisted_rotsum_stage():
+    """A hoisted stage a + sum_r rot(a, r) (one ModUp of c1 whose digits are
+    read through each automorphism, the key products summed, one ModDown) is
+    a valid key switch: with one rotation its decryption equals that of
+    add(a, rot(a, r)) up to key-switching noise (exact integers; the two
+    differ only in where the approximate basis conversion meets the
+    automorphism's sign flips); with seven it decrypts to the sum of the
+    rotated slot vectors (App. D), and a full rotate-and-sum in stages of 8
+    puts the total in every slot."""
+    from oracle.circuit import HE, rotsum_stages
+    ctx = ckks.Context(10, [60, 40, 40, 40], [60, 60], dnum=2, seed=13)
+    rots = sorted({r for st in rotsum_stages(9, 3) for r in st} | {5})
+    for r in rots:
+        ctx.gen_rot_key(r)
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, ctx.slots)
+    scale = 2.0 ** 40
+    a = ctx.encrypt(enc.encode(z, 10, scale), scale, 7)
+    one = ctx.rotsum_stage(a, [5])
+    ref = ctx.add(a, ctx.rotate(a, 5))
+    assert one.level == ref.level and one.scale == ref.scale
+    assert np.abs(ctx.decrypt(one) - ctx.decrypt(ref)).max() < 2 ** 20
+    assert not (one.export() == ref.export()).all()    # a different, equally valid key switch
+    seven = ctx.rotsum_stage(a, list(range(1, 8)))
+    want = sum(np.roll(z, -r) for r in range(8))
+    assert np.abs(enc.decode(ctx.decrypt(seven), 10, seven.scale).real - want).max() < 1e-6
+    full = HE(ctx, scale).rotsum(a, 9)
+    assert np.abs(enc.decode(ctx.decrypt(full), 10, full.scale).real - z.sum()).max() < 1e-5
+    with pytest.raises(RuntimeError):
+        ctx.rotsum_stage(a, [11])                    # no key for 11
