@@ -605,21 +605,30 @@ struct ChebEval {
         return std::min(out_level(deg - G), T[G]->level) - 1;
     }
 
+    // sum_k c_k T_k + c_0 with one rescale for all terms: every T_k is
+    // dropped to the lowest level l among them and multiplied by the integer
+    // K_k = rint(c_k E_k), E_k = target q_l / scale(T_k), so that every term
+    // sits at the scale target q_l; the sum is rescaled once, onto target
     Ct baby_sum(const std::vector<double> &c, double target) {
         he_ctx *cx = he.cx;
-        Ct acc;
         int low = 1 << 30;
-        std::vector<Ct> terms;
+        for (size_t k = 1; k < c.size(); k++)
+            if (c[k] != 0.0) low = std::min(low, T[k]->level);
+        if (low == (1 << 30)) throw Error{HE_EINVAL, "empty Chebyshev series"};
+        const double sc = target * (double)he.q(low);
+        Ct acc;
         for (size_t k = 1; k < c.size(); k++) {
             if (c[k] == 0.0) continue;
-            terms.push_back(he.mcr(T[k].get(), c[k], target));
-            low = std::min(low, terms.back()->level);
-        }
-        for (auto &t : terms) {
-            Ct u = t->level > low ? op_drop(cx, t.get(), low) : std::move(t);
+            Ct dropped;
+            const he_ct *t = T[k].get();
+            if (t->level > low) {
+                dropped = op_drop(cx, t, low);
+                t = dropped.get();
+            }
+            Ct u = op_mul_intd(cx, t, std::rint(c[k] * (sc / t->scale)), sc);
             acc = acc ? op_add(cx, acc.get(), u.get(), false) : std::move(u);
         }
-        if (!acc) throw Error{HE_EINVAL, "empty Chebyshev series"};
+        acc = op_rescale(cx, acc.get());
         return he.add_const(acc.get(), c[0]);
     }
 
