@@ -438,13 +438,12 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     for (int a = 0; a < K; a++)
         for (int i = 0; i < cx->nq; i++)  // Montgomery form
             tab.push_back((u64)(((u128)tab[md_qhat + (size_t)a * cx->nq + i] << 64) % cx->primes[i]));
-    // rounding: 1 / p_a as doubles, and (-P mod q_i) in Montgomery form
+    // rounding: floor(2^128 / p_a) (low, high words), and (-P mod q_i) in Montgomery form
     size_t md_inv = tab.size();
     for (int a = 0; a < K; a++) {
-        const double inv = 1.0 / (double)cx->primes[cx->nq + a];
-        u64 bits;
-        memcpy(&bits, &inv, 8);
-        tab.push_back(bits);
+        const u128 m = ~(u128)0 / cx->primes[cx->nq + a];  // = floor(2^128 / p_a): p_a is odd
+        tab.push_back((u64)m);
+        tab.push_back((u64)(m >> 64));
     }
     size_t md_negp = tab.size();
     for (int i = 0; i < cx->nq; i++) {
@@ -503,7 +502,7 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     cx->moddown.n_in = K;
     cx->moddown.n_out = cx->nq;
     cx->moddown.stride = cx->nq;
-    cx->moddown.inv_q = reinterpret_cast<const double *>(cx->d_tabs + md_inv);
+    cx->moddown.inv_fix = cx->d_tabs + md_inv;
     cx->moddown.negq_mont = cx->d_tabs + md_negp;
     cx->moddown.mr_inv = cx->d_tabs + md_mrinv;
     cx->moddown.mr_half = cx->d_tabs + md_half;

@@ -474,8 +474,10 @@ static bool ntt_fused_launch(const Rows &rows, const Rows &src, int n_rows, cons
         per_sm = std::max(1, occ) * std::max(1, sms);
         resident[dev & 63].store(per_sm, std::memory_order_relaxed);
     }
-    const long items = 2L * n_rows * (M / 16);
-    const unsigned grid = (unsigned)std::min<long>(items, per_sm);
+    // at most one block per first-pass tile: blocks beyond that would only
+    // share SMs with the first pass and slow it down
+    const long first = (long)n_rows * (M / 16);
+    const unsigned grid = (unsigned)std::min<long>(first, per_sm);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k_ntt_fused<LOG><<<grid, M, SMEM, s>>>(rows, src, tw, n_rows, fwd ? 1 : 0);
     return true;
@@ -896,13 +898,15 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // ------------------------------------------------------------------ key switching
 // Approximate basis conversion: for every coefficient, y_a = [x_a*qhinv_a]_{q_a},
 // out_t = sum_a y_a * qhat[a][t] mod p_t  (= x + v Q for some 0 <= v < n_in).
-// Rounding mode (tab.inv_q set, used by ModDown): v = rint(sum_a y_a / q_a),
-// computed in double beside the integer sums, and out_t - v Q mod p_t is the
-// centred representative of x mod Q (|.| <= Q/2), so that ModDown's
-// (acc - out) / Q is the rounded division.  The double sum r is off by a few
-// ulps of n_in; where its fractional part lies within 1e-9 of 1/2 (x within
-// ~1e-9 Q of Q/2, a rare case) the decision is taken exactly instead: floor(r)
-// is still right, and whether x mod Q exceeds (Q-1)/2 follows from the
+// Rounding mode (tab.inv_fix set, used by ModDown): v = round(sum_a y_a / q_a)
+// = round(S / Q), S = sum_a y_a Qhat_a, so that out_t - v Q mod p_t is the
+// centred representative of x mod Q (|.| <= Q/2) and ModDown's (acc - out) / Q
+// is the rounded division.  The sum is estimated in 64-bit fixed point with
+// integer multiplies: each term floor(y_a m_a / 2^64), m_a = floor(2^128 / q_a),
+// is (y_a / q_a) 2^64 less at most 2 units, the carries out of the 64-bit sum
+// count the integer part.  Where the fraction lies within 2^20 units
+// (~6e-14) of 1/2, the decision is taken exactly instead: the integer part is
+// still right, and whether x mod Q exceeds (Q-1)/2 follows from the
 // mixed-radix digits of x (Garner's algorithm), compared with those of
 // (Q-1)/2 from the most significant down.
 // One thread per (coefficient, chunk of BCONV_CHUNK output rows).  The
@@ -946,6 +950,7 @@ __device__ __noinline__ u32 bconv_above_half(const u64 *const *s_in, const int *
         if (m[i] != tab.mr_half[i]) return m[i] > tab.mr_half[i] ? 1u : 0u;
     return 0u;  // x = (Q-1)/2 itself rounds down
 }
+template <bool RND>
 __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
     __shared__ uint2 s_w[BCONV_MAX_IN * BCONV_CHUNK];
     __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
@@ -953,9 +958,9 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     __shared__ int s_pidx[BCONV_MAX_IN];
     __shared__ u64 *s_out[BCONV_CHUNK];
     __shared__ int s_p[BCONV_CHUNK];
-    __shared__ double s_inv[BCONV_MAX_IN];
+    __shared__ u64 s_mlo[BCONV_MAX_IN], s_mhi[BCONV_MAX_IN];
     __shared__ uint2 s_wn[BCONV_CHUNK];
-    const bool rnd = tab.inv_q != nullptr;
+    constexpr bool rnd = RND;
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
@@ -974,7 +979,8 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         s_q[a] = ok ? pc.m[in.prime(poly * tab.n_in + a)].q : 1;
         s_in[a] = ok ? in.row(poly * tab.n_in + a, log_n) : nullptr;
         s_pidx[a] = ok ? in.prime(poly * tab.n_in + a) : 0;
-        s_inv[a] = ok && rnd ? tab.inv_q[a] : 0.0;
+        s_mlo[a] = ok && rnd ? tab.inv_fix[2 * a] : 0;
+        s_mhi[a] = ok && rnd ? tab.inv_fix[2 * a + 1] : 0;
     }
     if (threadIdx.x < BCONV_CHUNK) {
         const int c = threadIdx.x, r = poly * tab.n_out + t0 + c;
@@ -990,12 +996,17 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     u32 acc[BCONV_CHUNK][4];
 #pragma unroll
     for (int c = 0; c < BCONV_CHUNK; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
-    double r = 0.0;
+    u64 flo = 0;  // fraction of sum_a y_a / q_a in units of 2^-64
+    u32 fhi = 0;  // its integer part
 #pragma unroll 2
     for (int a = 0; a < tab.n_in; a++) {
         const u64 y = shoup_mul(s_in[a][k], s_qi[a], s_qis[a], s_q[a]);
         const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
-        r = fma((double)y, s_inv[a], r);
+        if (RND) {  // floor(y m / 2^64) with m = floor(2^128 / q_a) < 2^128: (y / q_a) 2^64 - [0, 2)
+            const u64 t = __umul64hi(y, s_mlo[a]) + y * s_mhi[a];
+            flo += t;
+            fhi += flo < t ? 1u : 0u;
+        }
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++) {
             const uint2 w = s_w[a * BCONV_CHUNK + c];
@@ -1003,9 +1014,9 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         }
     }
     if (rnd) {  // + v (-Q): v <= n_in, one more term below 2^66
-        const double fl = floor(r), fr = r - fl;
-        u32 v = (u32)fl + (fr > 0.5 ? 1u : 0u);
-        if (fabs(fr - 0.5) < 1e-9) v = (u32)fl + bconv_above_half(s_in, s_pidx, k, tab.n_in, tab, pc);
+        constexpr u64 half = 1ull << 63, win = 1ull << 20;
+        u32 v = fhi + (flo > half ? 1u : 0u);
+        if ((flo > half ? flo - half : half - flo) < win) v = fhi + bconv_above_half(s_in, s_pidx, k, tab.n_in, tab, pc);
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++)
             mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], v, 0u, s_wn[c].x, s_wn[c].y);
@@ -1026,7 +1037,8 @@ void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, in
     dim3 grid((unsigned)((n + 127) / 128), (unsigned)(n_chunks * n_polys));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     prof_begin(PROF_BCONV, s);
-    k_bconv<<<grid, 128, 0, s>>>(out, in, tab, n_polys, log_n);
+    if (tab.inv_fix) k_bconv<true><<<grid, 128, 0, s>>>(out, in, tab, n_polys, log_n);
+    else k_bconv<false><<<grid, 128, 0, s>>>(out, in, tab, n_polys, log_n);
     prof_end(PROF_BCONV, s, 8.0 * (tab.n_in + tab.n_out) * (double)n_polys * (double)n);
 }
 

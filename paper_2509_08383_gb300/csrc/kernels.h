@@ -32,12 +32,13 @@ struct BConvTab {
     const u64 *qhinv, *qhinv_sh;    // [n_in]
     const u64 *qhat, *qhat_mont;    // [n_in][stride]
     int n_in, n_out, stride;
-    // rounding mode (ModDown): 1 / q_a [n_in] and (-Q mod p_t) 2^64 mod p_t
-    // [stride], Q the product of the input primes; null: approximate conversion
-    const double *inv_q = nullptr;
+    // rounding mode (ModDown): floor(2^128 / q_a) as (low, high) words [n_in][2]
+    // and (-Q mod p_t) 2^64 mod p_t [stride], Q the product of the input
+    // primes; null: approximate conversion
+    const u64 *inv_fix = nullptr;
     const u64 *negq_mont = nullptr;
-    // exact rounding where the float64 estimate cannot decide (x within
-    // ~1e-9 Q of Q/2): q_j^-1 mod q_i at [i*n_in + j] (j < i) and the
+    // exact rounding where the fixed-point estimate cannot decide (x within
+    // ~1e-13 Q of Q/2): q_j^-1 mod q_i at [i*n_in + j] (j < i) and the
     // mixed-radix digits of (Q-1)/2 [n_in]
     const u64 *mr_inv = nullptr;
     const u64 *mr_half = nullptr;
