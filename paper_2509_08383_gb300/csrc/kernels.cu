@@ -917,21 +917,9 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // step and a Barrett correction.  The chunk's constants sit in shared memory
 // (every thread reads the same word: broadcasts).
 constexpr int BCONV_CHUNK = 8, BCONV_MAX_IN = 16;
-// (a3:a2:a1:a0) += (y1:y0) * (w1:w0)  (no carry out of a3: the caller's sums stay below 2^128)
-__device__ __forceinline__ void mac128_words(u32 &a0, u32 &a1, u32 &a2, u32 &a3, u32 y0, u32 y1, u32 w0, u32 w1) {
-    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
-        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
-        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
-        "madc.hi.u32 %3, %5, %7, %3;\n\t"
-        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
-        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
-        "addc.u32 %3, %3, 0;\n\t"
-        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
-        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
-        : "r"(y0), "r"(y1), "r"(w0), "r"(w1));
-}
+// each block converts BCONV_CPT coefficients per thread, one after another,
+// so that its table set-up is paid once for all of them
+constexpr int BCONV_CPT = 2;
 // 1 if the integer x with residues x_a = s_in[a][k] (a < n_in, primes
 // s_pidx[a]) exceeds (Q-1)/2 as an element of [0, Q), else 0: mixed-radix
 // digits m_i = (((x_i - m_0) q_0^-1 - m_1) q_1^-1 - ...) mod q_i, compared
@@ -952,14 +940,14 @@ __device__ __noinline__ u32 bconv_above_half(const u64 *const *s_in, const int *
 }
 template <bool RND>
 __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
-    __shared__ uint2 s_w[BCONV_MAX_IN * BCONV_CHUNK];
+    __shared__ u64 s_w[BCONV_MAX_IN * BCONV_CHUNK];
     __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
     __shared__ const u64 *s_in[BCONV_MAX_IN];
     __shared__ int s_pidx[BCONV_MAX_IN];
     __shared__ u64 *s_out[BCONV_CHUNK];
     __shared__ int s_p[BCONV_CHUNK];
     __shared__ u64 s_mlo[BCONV_MAX_IN], s_mhi[BCONV_MAX_IN];
-    __shared__ uint2 s_wn[BCONV_CHUNK];
+    __shared__ u64 s_wn[BCONV_CHUNK];
     constexpr bool rnd = RND;
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
@@ -968,8 +956,7 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     const int t0 = chunk * BCONV_CHUNK, nt = min(BCONV_CHUNK, tab.n_out - t0);
     for (int i = threadIdx.x; i < BCONV_MAX_IN * BCONV_CHUNK; i += blockDim.x) {
         const int a = i / BCONV_CHUNK, c = i % BCONV_CHUNK;
-        const u64 w = (a < tab.n_in && c < nt) ? tab.qhat_mont[a * tab.stride + t0 + c] : 0;
-        s_w[i] = make_uint2((u32)w, (u32)(w >> 32));
+        s_w[i] = (a < tab.n_in && c < nt) ? tab.qhat_mont[a * tab.stride + t0 + c] : 0;
     }
     if (threadIdx.x < BCONV_MAX_IN) {
         const int a = threadIdx.x;
@@ -987,46 +974,45 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
         const bool ok = c < nt && poly < n_polys;
         s_out[c] = ok ? out.row(r, log_n) : nullptr;
         s_p[c] = ok ? out.prime(r) : 0;
-        const u64 wn = ok && rnd ? tab.negq_mont[t0 + c] : 0;
-        s_wn[c] = make_uint2((u32)wn, (u32)(wn >> 32));
+        s_wn[c] = ok && rnd ? tab.negq_mont[t0 + c] : 0;
     }
     __syncthreads();
-    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n || poly >= n_polys) return;
-    u32 acc[BCONV_CHUNK][4];
+    if (poly >= n_polys) return;
+    for (int ci = 0; ci < BCONV_CPT; ci++) {
+        const size_t k = ((size_t)blockIdx.x * BCONV_CPT + ci) * blockDim.x + threadIdx.x;
+        if (k >= n) return;
+        // 128-bit sums (hi:lo) of the products, one per output row: plain
+        // 64-bit multiplies and adds, independent chains the scheduler interleaves
+        u64 alo[BCONV_CHUNK], ahi[BCONV_CHUNK];
 #pragma unroll
-    for (int c = 0; c < BCONV_CHUNK; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
-    u64 flo = 0;  // fraction of sum_a y_a / q_a in units of 2^-64
-    u32 fhi = 0;  // its integer part
+        for (int c = 0; c < BCONV_CHUNK; c++) alo[c] = ahi[c] = 0;
+        u64 flo = 0;  // fraction of sum_a y_a / q_a in units of 2^-64
+        u32 fhi = 0;  // its integer part
 #pragma unroll 2
-    for (int a = 0; a < tab.n_in; a++) {
-        const u64 y = shoup_mul(s_in[a][k], s_qi[a], s_qis[a], s_q[a]);
-        const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
-        if (RND) {  // floor(y m / 2^64) with m = floor(2^128 / q_a) < 2^128: (y / q_a) 2^64 - [0, 2)
-            const u64 t = __umul64hi(y, s_mlo[a]) + y * s_mhi[a];
-            flo += t;
-            fhi += flo < t ? 1u : 0u;
+        for (int a = 0; a < tab.n_in; a++) {
+            const u64 y = shoup_mul(s_in[a][k], s_qi[a], s_qis[a], s_q[a]);
+            if (RND) {  // floor(y m / 2^64) with m = floor(2^128 / q_a) < 2^128: (y / q_a) 2^64 - [0, 2)
+                const u64 t = __umul64hi(y, s_mlo[a]) + y * s_mhi[a];
+                flo += t;
+                fhi += flo < t ? 1u : 0u;
+            }
+#pragma unroll
+            for (int c = 0; c < BCONV_CHUNK; c++) mac128(alo[c], ahi[c], y, s_w[a * BCONV_CHUNK + c]);
+        }
+        if (RND) {  // + v (-Q): v <= n_in, one more term below 2^66
+            constexpr u64 half = 1ull << 63, win = 1ull << 20;
+            u32 v = fhi + (flo > half ? 1u : 0u);
+            if ((flo > half ? flo - half : half - flo) < win)
+                v = fhi + bconv_above_half(s_in, s_pidx, k, tab.n_in, tab, pc);
+#pragma unroll
+            for (int c = 0; c < BCONV_CHUNK; c++) mac128(alo[c], ahi[c], (u64)v, s_wn[c]);
         }
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++) {
-            const uint2 w = s_w[a * BCONV_CHUNK + c];
-            mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], y0, y1, w.x, w.y);
-        }
-    }
-    if (rnd) {  // + v (-Q): v <= n_in, one more term below 2^66
-        constexpr u64 half = 1ull << 63, win = 1ull << 20;
-        u32 v = fhi + (flo > half ? 1u : 0u);
-        if ((flo > half ? flo - half : half - flo) < win) v = fhi + bconv_above_half(s_in, s_pidx, k, tab.n_in, tab, pc);
-#pragma unroll
-        for (int c = 0; c < BCONV_CHUNK; c++)
-            mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], v, 0u, s_wn[c].x, s_wn[c].y);
-    }
-#pragma unroll
-    for (int c = 0; c < BCONV_CHUNK; c++) {
-        if (c < nt) {
-            const int p = s_p[c];
-            const u64 lo = ((u64)acc[c][1] << 32) | acc[c][0], hi = ((u64)acc[c][3] << 32) | acc[c][2];
-            s_out[c][k] = mont_reduce_wide(lo, hi, pc.m[p], pc.mont_qinv[p]);
+            if (c < nt) {
+                const int p = s_p[c];
+                s_out[c][k] = mont_reduce_wide(alo[c], ahi[c], pc.m[p], pc.mont_qinv[p]);
+            }
         }
     }
 }
@@ -1034,7 +1020,7 @@ void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, in
     if (tab.n_in > BCONV_MAX_IN) throw Error{HE_EINVAL, "basis conversion from more than 16 primes"};
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
-    dim3 grid((unsigned)((n + 127) / 128), (unsigned)(n_chunks * n_polys));
+    dim3 grid((unsigned)((n + 128 * BCONV_CPT - 1) / (128 * BCONV_CPT)), (unsigned)(n_chunks * n_polys));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     prof_begin(PROF_BCONV, s);
     if (tab.inv_fix) k_bconv<true><<<grid, 128, 0, s>>>(out, in, tab, n_polys, log_n);
