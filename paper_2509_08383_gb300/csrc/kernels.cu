@@ -920,6 +920,21 @@ constexpr int BCONV_CHUNK = 8, BCONV_MAX_IN = 16;
 // each block converts BCONV_CPT coefficients per thread, one after another,
 // so that its table set-up is paid once for all of them
 constexpr int BCONV_CPT = 2;
+// (a3:a2:a1:a0) += (y1:y0) * (w1:w0)  (no carry out of a3: the caller's sums stay below 2^128)
+__device__ __forceinline__ void mac128_words(u32 &a0, u32 &a1, u32 &a2, u32 &a3, u32 y0, u32 y1, u32 w0, u32 w1) {
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
+        : "r"(y0), "r"(y1), "r"(w0), "r"(w1));
+}
 // 1 if the integer x with residues x_a = s_in[a][k] (a < n_in, primes
 // s_pidx[a]) exceeds (Q-1)/2 as an element of [0, Q), else 0: mixed-radix
 // digits m_i = (((x_i - m_0) q_0^-1 - m_1) q_1^-1 - ...) mod q_i, compared
@@ -939,7 +954,7 @@ __device__ __noinline__ u32 bconv_above_half(const u64 *const *s_in, const int *
     return 0u;  // x = (Q-1)/2 itself rounds down
 }
 template <bool RND>
-__global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
+__global__ void __launch_bounds__(128, 4) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
     __shared__ u64 s_w[BCONV_MAX_IN * BCONV_CHUNK];
     __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
     __shared__ const u64 *s_in[BCONV_MAX_IN];
@@ -981,11 +996,9 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
     for (int ci = 0; ci < BCONV_CPT; ci++) {
         const size_t k = ((size_t)blockIdx.x * BCONV_CPT + ci) * blockDim.x + threadIdx.x;
         if (k >= n) return;
-        // 128-bit sums (hi:lo) of the products, one per output row: plain
-        // 64-bit multiplies and adds, independent chains the scheduler interleaves
-        u64 alo[BCONV_CHUNK], ahi[BCONV_CHUNK];
+        u32 acc[BCONV_CHUNK][4];
 #pragma unroll
-        for (int c = 0; c < BCONV_CHUNK; c++) alo[c] = ahi[c] = 0;
+        for (int c = 0; c < BCONV_CHUNK; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
         u64 flo = 0;  // fraction of sum_a y_a / q_a in units of 2^-64
         u32 fhi = 0;  // its integer part
 #pragma unroll 2
@@ -996,8 +1009,12 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
                 flo += t;
                 fhi += flo < t ? 1u : 0u;
             }
+            const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
 #pragma unroll
-            for (int c = 0; c < BCONV_CHUNK; c++) mac128(alo[c], ahi[c], y, s_w[a * BCONV_CHUNK + c]);
+            for (int c = 0; c < BCONV_CHUNK; c++) {
+                const u64 w = s_w[a * BCONV_CHUNK + c];
+                mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], y0, y1, (u32)w, (u32)(w >> 32));
+            }
         }
         if (RND) {  // + v (-Q): v <= n_in, one more term below 2^66
             constexpr u64 half = 1ull << 63, win = 1ull << 20;
@@ -1005,13 +1022,15 @@ __global__ void __launch_bounds__(128) k_bconv(Rows out, Rows in, BConvTab tab, 
             if ((flo > half ? flo - half : half - flo) < win)
                 v = fhi + bconv_above_half(s_in, s_pidx, k, tab.n_in, tab, pc);
 #pragma unroll
-            for (int c = 0; c < BCONV_CHUNK; c++) mac128(alo[c], ahi[c], (u64)v, s_wn[c]);
+            for (int c = 0; c < BCONV_CHUNK; c++)
+                mac128_words(acc[c][0], acc[c][1], acc[c][2], acc[c][3], v, 0u, (u32)s_wn[c], (u32)(s_wn[c] >> 32));
         }
 #pragma unroll
         for (int c = 0; c < BCONV_CHUNK; c++) {
             if (c < nt) {
                 const int p = s_p[c];
-                s_out[c][k] = mont_reduce_wide(alo[c], ahi[c], pc.m[p], pc.mont_qinv[p]);
+                const u64 lo = ((u64)acc[c][1] << 32) | acc[c][0], hi = ((u64)acc[c][3] << 32) | acc[c][2];
+                s_out[c][k] = mont_reduce_wide(lo, hi, pc.m[p], pc.mont_qinv[p]);
             }
         }
     }
