@@ -917,9 +917,9 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // step and a Barrett correction.  The chunk's constants sit in shared memory
 // (every thread reads the same word: broadcasts).
 constexpr int BCONV_CHUNK = 8, BCONV_MAX_IN = 16;
-// each block converts BCONV_CPT coefficients per thread, one after another,
-// so that its table set-up is paid once for all of them
-constexpr int BCONV_CPT = 2;
+// each thread converts BCONV_CPT coefficients, one after another (1: looping
+// over more, to share the block's table set-up, measured slower)
+constexpr int BCONV_CPT = 1;
 // (a3:a2:a1:a0) += (y1:y0) * (w1:w0)  (no carry out of a3: the caller's sums stay below 2^128)
 __device__ __forceinline__ void mac128_words(u32 &a0, u32 &a1, u32 &a2, u32 &a3, u32 y0, u32 y1, u32 w0, u32 w1) {
     asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
