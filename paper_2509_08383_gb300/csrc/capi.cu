@@ -25,15 +25,6 @@ using namespace he;
 static void sync(he_ctx *cx, const char *what) {
     check_cuda(cudaGetLastError(), what);
     check_cuda(cudaStreamSynchronize(cx->stream), what);
-    if (cx->tw.err) {  // a bounded wait inside a transform gave up since the last check
-        int e = 0;
-        check_cuda(cudaMemcpy(&e, cx->tw.err, sizeof(int), cudaMemcpyDeviceToHost), what);
-        if (e) {
-            check_cuda(cudaMemset(cx->tw.err, 0, sizeof(int)), what);
-            throw Error{HE_ETIMEOUT, std::string(what) + ": a wait inside an NTT gave up; results since the last "
-                                                        "synchronising call are not reliable"};
-        }
-    }
 }
 static void need(bool ok, const char *msg) {
     if (!ok) throw Error{HE_EINVAL, msg};

@@ -323,13 +323,6 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
         check_cuda(cudaMemcpy(cx->d_tw, h.data(), h.size() * 8, cudaMemcpyHostToDevice), "upload twiddles");
         cx->tw.fwd = reinterpret_cast<const ulonglong2 *>(cx->d_tw);
         cx->tw.inv = reinterpret_cast<const ulonglong2 *>(cx->d_tw + (size_t)2 * tot * N);
-        // counters of the one-launch transforms (zero between launches) and
-        // the flag of a wait that gave up
-        const int cap = 8192;
-        cx->tw.sync = (unsigned *)cx->arena.alloc((size_t)(cap + 2) * 4 + 16);
-        cx->tw.err = (int *)(cx->tw.sync + cap + 2);
-        cx->tw.sync_cap = cap;
-        check_cuda(cudaMemset(cx->tw.sync, 0, (size_t)(cap + 2) * 4 + 16), "NTT counters");
     }
 
     // scratch

@@ -376,71 +376,6 @@ __global__ void __launch_bounds__(1 << (COLS ? LOGR : LOGC), 3) k_ntt(Rows rows,
     ntt_tile<LOGR, LOGC, FWD, COLS>(rows, src, tw, blockIdx.x, blockIdx.y, ntt_smem);
 }
 
-// Both passes of the transforms of n_rows limbs in one launch (R = C = 2^LOG):
-// blocks fetch tiles from a work counter, every first-pass tile (columns for
-// the forward transform, rows for the inverse) before any second-pass tile;
-// a second-pass tile of limb rb waits until the TILES first-pass tiles of rb
-// are done.  Those were fetched earlier by running blocks whose work never
-// waits, so the wait ends without any co-residency guarantee; it is bounded
-// all the same (about a second, then tw.err is set and the block goes on).
-__device__ __forceinline__ void ntt_wait_count(const unsigned *p, unsigned target, int *err) {
-    unsigned v;
-    for (unsigned it = 0;; it++) {
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-        if (v >= target) return;
-        if (it >= (1u << 23)) {
-            atomicExch(err, 1);
-            return;
-        }
-        __nanosleep(64);
-    }
-}
-template <int LOG>
-__global__ void __launch_bounds__(1 << LOG, 3) k_ntt_fused(Rows rows, Rows src, NttTables tw, int n_rows, int fwd) {
-    constexpr int TILES = (1 << LOG) / 16;
-    extern __shared__ __align__(16) unsigned char ntt_smem[];
-    __shared__ unsigned s_item, s_last;
-    unsigned *work = tw.sync, *exitc = tw.sync + 1, *done = tw.sync + 2;
-    const unsigned first_n = (unsigned)n_rows * TILES, total = 2 * first_n;
-    Rows none = rows;
-    none.base = nullptr;
-    for (;;) {
-        __syncthreads();  // every thread has read s_item and left the last tile's shared memory
-        if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
-        __syncthreads();
-        const unsigned it = s_item;
-        if (it >= total) break;
-        const bool first = it < first_n;
-        const unsigned w = first ? it : it - first_n;
-        const int rb = (int)(w / TILES), tile = (int)(w % TILES);
-        if (!first) {
-            if (threadIdx.x == 0) ntt_wait_count(done + rb, TILES, tw.err);
-            __syncthreads();
-        }
-        if (fwd) {
-            if (first) ntt_tile<LOG, LOG, true, true>(rows, src, tw, tile, rb, ntt_smem);
-            else ntt_tile<LOG, LOG, true, false>(rows, none, tw, tile, rb, ntt_smem);
-        } else {
-            if (first) ntt_tile<LOG, LOG, false, false>(rows, src, tw, tile, rb, ntt_smem);
-            else ntt_tile<LOG, LOG, false, true>(rows, none, tw, tile, rb, ntt_smem);
-        }
-        if (first) {  // this tile's stores, then its count
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) atomicAdd(done + rb, 1u);
-        }
-    }
-    if (threadIdx.x == 0) s_last = atomicAdd(exitc, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (s_last) {  // every block has left the loop: reset the counters for the next launch
-        for (int i = threadIdx.x; i < n_rows; i += blockDim.x) done[i] = 0;
-        if (threadIdx.x == 0) {
-            *work = 0;
-            *exitc = 0;
-        }
-    }
-}
-
 // dynamic shared memory above 48 KB is an opt-in attribute, set once per device
 template <typename K>
 static void ntt_smem_attr(K kern, size_t bytes, std::atomic<unsigned long long> &done) {
@@ -453,44 +388,11 @@ static void ntt_smem_attr(K kern, size_t bytes, std::atomic<unsigned long long> 
     done.fetch_or(bit, std::memory_order_release);
 }
 
-template <int LOG>
-static bool ntt_fused_launch(const Rows &rows, const Rows &src, int n_rows, const NttTables &tw, bool fwd,
-                             cudaStream_t s) {
-    if (!tw.sync || n_rows > tw.sync_cap) return false;
-    using SC = NttShape<LOG, LOG, true>;
-    using SR = NttShape<LOG, LOG, false>;
-    constexpr size_t SMEM = SC::SMEM > SR::SMEM ? SC::SMEM : SR::SMEM;
-    constexpr int M = 1 << LOG;
-    static std::atomic<unsigned long long> attr_done{0};
-    static std::atomic<int> resident[64];
-    ntt_smem_attr(k_ntt_fused<LOG>, SMEM, attr_done);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int per_sm = resident[dev & 63].load(std::memory_order_relaxed);
-    if (per_sm == 0) {  // blocks per SM and SMs, once per device
-        int occ = 0, sms = 0;
-        check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ntt_fused<LOG>, M, SMEM), "NTT occupancy");
-        check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-        per_sm = std::max(1, occ) * std::max(1, sms);
-        resident[dev & 63].store(per_sm, std::memory_order_relaxed);
-    }
-    // at most one block per first-pass tile: blocks beyond that would only
-    // share SMs with the first pass and slow it down
-    const long first = (long)n_rows * (M / 16);
-    const unsigned grid = (unsigned)std::min<long>(first, per_sm);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_ntt_fused<LOG><<<grid, M, SMEM, s>>>(rows, src, tw, n_rows, fwd ? 1 : 0);
-    return true;
-}
-
 template <int LOGR, int LOGC>
 static void ntt_launch(const Rows &rows, const Rows &src, int n_rows, const NttTables &tw, bool fwd, cudaStream_t s) {
     constexpr int R = 1 << LOGR, C = 1 << LOGC;
     using SC = NttShape<LOGR, LOGC, true>;
     using SR = NttShape<LOGR, LOGC, false>;
-    if constexpr (LOGR == LOGC) {
-        if (ntt_fused_launch<LOGR>(rows, src, n_rows, tw, fwd, s)) return;
-    }
     static std::atomic<unsigned long long> done[4];
     dim3 gc(C / NTT_TILE, n_rows), gr(R / NTT_TILE, n_rows);
     Rows none = rows;

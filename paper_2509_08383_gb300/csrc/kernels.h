@@ -10,13 +10,6 @@ namespace he {
 
 struct NttTables {
     const ulonglong2 *fwd, *inv;  // [prime][N] pairs (twiddle, Shoup companion)
-    // both passes in one launch (even log2 N): a work counter, an exit counter
-    // and sync_cap per-row counters of finished first-pass tiles, zero between
-    // launches (the last block out resets them); err is set when a wait for
-    // another block's tiles gives up
-    unsigned *sync = nullptr;
-    int *err = nullptr;
-    int sync_cap = 0;
 };
 
 // Residues of one constant for every prime (value and Shoup companion).
