@@ -26,9 +26,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted CutMax decodes/sec (vocab 32k, N=2^16), 1 GB300"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of both NTT passes per limb at
-# N=2^16, from one capture of the NTT source whose hash is `src`; once the
-# source changes (ntt_source_hash() differs) the bench reports traffic null
-NTT_DRAM = {"src": None, "per_limb": {0: None, 1: None}}
+# N=2^16 (40-limb forward and inverse of `--workload ntt16`; ncu starts each
+# pass with cold caches, so the data is counted once per pass), from one
+# capture of the NTT source whose hash is `src`; once the source changes
+# (ntt_source_hash() differs) the bench reports traffic null
+NTT_DRAM = {"src": "06cea59ef67fbd85",
+            "per_limb": {0: (21175040 + 0 + 62799872 + 23296) / 40, 1: (62797056 + 3840 + 21181696 + 0) / 40}}
 # integer-pipe ceiling of the NTT: a Shoup butterfly on 64-bit words takes 1.04
 # warp instructions (33 thread instructions: ncu sm__inst_executed of a 90-limb
 # forward transform / its 90 x 2^19 butterflies), and an SM issues at most 4
@@ -622,7 +625,7 @@ def run_micro(args):
     same kernels as a CutMax step at full size): mul16 = one homomorphic
     multiplication (tensor product, hybrid key switch, rescale) at the top
     level; rot16 = one rotation (automorphism + hybrid key switch) at the top
-    level; ntt16 = a forward and an inverse NTT of one 41-limb block (every
+    level; ntt16 = a forward and an inverse NTT of one 40-limb block (every
     prime of the chain, 21 MB); boot16 = one bootstrapping of a level-0
     ciphertext; bootc16 = one constant bootstrapping (trace form) of a level-0
     ciphertext holding one complex value in every slot."""
@@ -653,8 +656,8 @@ def run_micro(args):
         limbs = len(CFG2_Q) + len(CFG2_P)
         blk = torch.randint(0, 1 << 39, (limbs, 1 << 16), dtype=torch.int64, device="cuda")
         op = lambda: (g.ntt_device(blk, 0), g.ntt_device(blk, 0, inverse=True))
-        metric, unit = "NTT forward + inverse, 41 limbs (N=2^16)", "pairs/s"
-        wl = "negacyclic NTT then INTT of a 41-limb block (every prime of the N=2^16 chain), in place"
+        metric, unit = "NTT forward + inverse, 40 limbs (N=2^16)", "pairs/s"
+        wl = "negacyclic NTT then INTT of a 40-limb block (every prime of the N=2^16 chain), in place"
         roof = 2 * 16.0 * limbs * (1 << 16)  # algorithmic bytes per step: read + write each limb, twice
     elif args.workload == "rot16":
         g.gen_rot_keys([1])
