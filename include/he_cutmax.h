@@ -171,6 +171,14 @@ int he_add_const(he_ctx *ctx, const he_ct *a, double c, he_ct **out);
 /* tensor product and relinearisation, no rescale */
 int he_mul(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out);
+/* Product, relinearisation and rescale with ONE rounding: for the tensor
+ * product (d0, d1, d2) at level l and the key products acc of d2 over the
+ * key-switching basis, out_k = round((P d_k + acc_k) / (q_l P)) at level l-1,
+ * scale(a) scale(b) / q_l: the message of he_rescale(he_mul(a, b)), without the
+ * separate rescale's transforms (the ciphertexts differ by that rounding).
+ * HE_ELEVEL at level 0; with more than 15 special primes it falls back to
+ * he_mul then he_rescale. */
+int he_mul_rescale(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 int he_drop(he_ctx *ctx, const he_ct *a, uint32_t level, he_ct **out);
 /* left slot rotation by r (g = 5^r mod 2N); conjugation; general X -> X^g */
 int he_rotate(he_ctx *ctx, const he_ct *a, int32_t r, he_ct **out);

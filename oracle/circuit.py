@@ -89,13 +89,14 @@ class HE:
         return self.ctx.mul_int(ct, -1)
 
     def mul_rescale(self, a, b):
+        """Product, relinearisation and rescale in one rounded division by q_l P."""
         ctx = self.ctx
         l = min(a.level, b.level)
         if a.level > l:
             a = ctx.drop(a, l)
         if b.level > l:
             b = ctx.drop(b, l)
-        return ctx.rescale(ctx.mul(a, b))
+        return ctx.mul_rescale(a, b)
 
     def mul_plain_rescale(self, ct, vec, target=None):
         target = self.delta if target is None else target
@@ -284,6 +285,9 @@ class LevelSim:
         self._ks(l)
         return _SimCt(l, a.scale * b.scale)
 
+    def mul_rescale(self, a, b):
+        return self.rescale(self.mul(a, b))
+
     def automorphism(self, a, g):
         self._ks(a.level)
         return _SimCt(a.level, a.scale)
@@ -355,6 +359,10 @@ class CountingCtx:
     def mul(self, a, b):
         self._ks(min(a.level, b.level))
         return self._ctx.mul(a, b)
+
+    def mul_rescale(self, a, b):
+        self._ks(min(a.level, b.level))
+        return self._ctx.mul_rescale(a, b)
 
     def automorphism(self, a, g):
         self._ks(a.level)

@@ -61,6 +61,7 @@ def lib():
             "or_keyswitch": (ip, [vp, pu64, ip, u64, pu64, pu64]),
             "or_moddown": (None, [vp, pu64, pu64, ip, pu64, pu64]),
             "or_mul": (vp, [vp, vp, vp]),
+            "or_mul_rescale": (vp, [vp, vp, vp]),
             "or_rescale": (vp, [vp, vp]),
             "or_automorphism": (vp, [vp, vp, u64]),
             "or_rotsum_stage": (vp, [vp, vp, P(np.int64, flags="C"), ip]),
@@ -287,6 +288,10 @@ class Context:
 
     def rescale(self, a):
         return Ciphertext(self, lib().or_rescale(self.ptr, a.ptr))
+
+    def mul_rescale(self, a, b):
+        """Product, relinearisation and rescale with one rounded division by q_l P."""
+        return Ciphertext(self, lib().or_mul_rescale(self.ptr, a.ptr, b.ptr))
 
     def automorphism(self, a, g):
         return Ciphertext(self, lib().or_automorphism(self.ptr, a.ptr, int(g)))

@@ -730,20 +730,23 @@ static void it_body(void *vp, int t) {
     u64 *p = (t < A->ext ? A->acc0 + (u64)t * A->cx->n : A->acc1 + (u64)(t - A->ext) * A->cx->n);
     poly_intt(A->cx, p, A->pidx[t % A->ext]);
 }
-/* ModDown is the rounded division out = round(acc / P) mod q_i.  For every
- * coefficient x (known mod P by its residues), Garner's algorithm gives the
- * mixed-radix digits x mod P = m_0 + m_1 p_0 + m_2 p_0 p_1 + ... (m_k < p_k);
- * comparing them, most significant first, with the digits of (P-1)/2 picks
- * the centred representative x_c = x mod P, or that minus P; then
- *   out_i = (acc_i - x_c) * P^-1 mod q_i,
+/* Rounded division by a product M of some of the basis primes: ModDown
+ * divides by P (the special primes), the product with its rescale by P q_l.
+ * The rows d0 .. d0+K-1 of the accumulators hold x mod the divisor primes
+ * dp[0..K-1]; for every coefficient Garner's algorithm gives the mixed-radix
+ * digits x mod M = m_0 + m_1 dp_0 + m_2 dp_0 dp_1 + ... (m_k < dp_k);
+ * comparing them, most significant first, with the digits of (M-1)/2 picks
+ * the centred representative x_c = x mod M, or that minus M; then for the
+ * output rows i < n_out
+ *   out_i = (acc_i - x_c) * M^-1 mod q_i = round(x / M) mod q_i,
  * exact, with x_c reduced mod q_i from its digits. */
 typedef struct {
-    or_ctx *cx; const u64 *acc0, *acc1; int l, K, chunk; u64 *dig0, *dig1; unsigned char *hi0, *hi1;
-    const u64 *pjinv, *hdig;
+    or_ctx *cx; const u64 *acc0, *acc1; int d0, K, chunk; const u64 *dp; u64 *dig0, *dig1;
+    unsigned char *hi0, *hi1; const u64 *pjinv, *hdig;
 } gd_args;
 static void gd_body(void *vp, int job) {
     gd_args *A = (gd_args *)vp;
-    or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K, l = A->l;
+    or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K;
     int nch = (int)((n + A->chunk - 1) / A->chunk), w = job / nch;
     u64 c0 = (u64)(job % nch) * A->chunk, c1 = c0 + A->chunk < n ? c0 + A->chunk : n;
     const u64 *acc = w ? A->acc1 : A->acc0;
@@ -751,7 +754,7 @@ static void gd_body(void *vp, int job) {
     unsigned char *hi = w ? A->hi1 : A->hi0;
     for (u64 c = c0; c < c1; c++) {
         for (int k = 0; k < K; k++) {
-            u64 pk = cx->primes[cx->nq + k], t = acc[(u64)(l + 1 + k) * n + c];
+            u64 pk = A->dp[k], t = acc[(u64)(A->d0 + k) * n + c];
             for (int j = 0; j < k; j++) t = mulmod(submod(t, dig[(u64)j * n + c] % pk, pk), A->pjinv[j * K + k], pk);
             dig[(u64)k * n + c] = t;
         }
@@ -764,16 +767,16 @@ static void gd_body(void *vp, int job) {
     }
 }
 typedef struct {
-    or_ctx *cx; const u64 *acc0, *acc1; u64 *out0, *out1; int l, K; const u64 *dig0, *dig1;
+    or_ctx *cx; const u64 *acc0, *acc1; u64 *out0, *out1; int K; const u64 *dp; const u64 *dig0, *dig1;
     const unsigned char *hi0, *hi1;
 } md_args;
 static void md_body(void *vp, int i) {
     md_args *A = (md_args *)vp;
     or_ctx *cx = A->cx; u64 n = cx->n; int K = A->K;
     u64 qi = cx->primes[i], pm = 1, *radix = malloc(8 * K);
-    for (int a = 0; a < K; a++) {  /* radix[a] = p_0 ... p_(a-1) mod q_i */
+    for (int a = 0; a < K; a++) {  /* radix[a] = dp_0 ... dp_(a-1) mod q_i */
         radix[a] = pm;
-        pm = mulmod(pm, cx->primes[cx->nq + a] % qi, qi);
+        pm = mulmod(pm, A->dp[a] % qi, qi);
     }
     u64 pinv = or_invmod(pm, qi);
     for (int w = 0; w < 2; w++) {
@@ -790,31 +793,34 @@ static void md_body(void *vp, int i) {
     free(radix);
 }
 
-/* mixed-radix digits of (P-1)/2 (residues (p_k - 1)/2) and p_j^-1 mod p_k */
-static void moddown_consts(or_ctx *cx, int K, u64 *pjinv, u64 *hdig) {
+/* mixed-radix digits of (M-1)/2 (residues (dp_k - 1)/2) and dp_j^-1 mod dp_k */
+static void divide_consts(const u64 *dp, int K, u64 *pjinv, u64 *hdig) {
     for (int j = 0; j < K; j++)
-        for (int k = 0; k < K; k++) {
-            u64 pk = cx->primes[cx->nq + k];
-            pjinv[j * K + k] = j == k ? 0 : or_invmod(cx->primes[cx->nq + j] % pk, pk);
-        }
+        for (int k = 0; k < K; k++) pjinv[j * K + k] = j == k ? 0 : or_invmod(dp[j] % dp[k], dp[k]);
     for (int k = 0; k < K; k++) {
-        u64 pk = cx->primes[cx->nq + k], t = (pk - 1) / 2;
+        u64 pk = dp[k], t = (pk - 1) / 2;
         for (int j = 0; j < k; j++) t = mulmod(submod(t, hdig[j] % pk, pk), pjinv[j * K + k], pk);
         hdig[k] = t;
     }
 }
 
-static void moddown_exact(or_ctx *cx, const u64 *acc0, const u64 *acc1, int l, u64 *out0, u64 *out1) {
-    u64 n = cx->n; int K = cx->np, chunk = 1024;
+static void divide_round_exact(or_ctx *cx, const u64 *acc0, const u64 *acc1, int d0, const u64 *dp, int K,
+                               int n_out, u64 *out0, u64 *out1) {
+    u64 n = cx->n; int chunk = 1024;
     u64 *pjinv = malloc(8 * K * K), *hdig = malloc(8 * K);
-    moddown_consts(cx, K, pjinv, hdig);
+    divide_consts(dp, K, pjinv, hdig);
     u64 *dig0 = malloc((u64)K * n * 8), *dig1 = malloc((u64)K * n * 8);
     unsigned char *hi0 = malloc(n), *hi1 = malloc(n);
-    gd_args G = {cx, acc0, acc1, l, K, chunk, dig0, dig1, hi0, hi1, pjinv, hdig};
+    gd_args G = {cx, acc0, acc1, d0, K, chunk, dp, dig0, dig1, hi0, hi1, pjinv, hdig};
     parallel_for(2 * (int)((n + chunk - 1) / chunk), gd_body, &G);
-    md_args M = {cx, acc0, acc1, out0, out1, l, K, dig0, dig1, hi0, hi1};
-    parallel_for(l + 1, md_body, &M);
+    md_args M = {cx, acc0, acc1, out0, out1, K, dp, dig0, dig1, hi0, hi1};
+    parallel_for(n_out, md_body, &M);
     free(pjinv); free(hdig); free(dig0); free(dig1); free(hi0); free(hi1);
+}
+
+/* ModDown: the rounded division by P of accumulators over q_0..q_l, p_0..p_(K-1) */
+static void moddown_exact(or_ctx *cx, const u64 *acc0, const u64 *acc1, int l, u64 *out0, u64 *out1) {
+    divide_round_exact(cx, acc0, acc1, l + 1, cx->primes + cx->nq, cx->np, l + 1, out0, out1);
 }
 
 /* Hybrid key switching of the coefficient-form polynomial d at level l.
@@ -822,13 +828,17 @@ static void moddown_exact(or_ctx *cx, const u64 *acc0, const u64 *acc1, int l, u
  *   [x]_t = sum_{i in D_j} [x_i * (Qhat_i)^-1]_{q_i} * Qhat_i  mod t,
  * inner product with the key over Q_l u P, then ModDown, the rounded
  * division by P (moddown_exact). */
-static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *out0, u64 *out1) {
+/* The key products of hybrid key switching, before ModDown: acc0/acc1
+ * [(l+1+K)][N] in coefficient form over q_0..q_l, p_0..p_(K-1) (caller's
+ * buffers, zeroed here). */
+static void ks_accumulate(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *acc0, u64 *acc1) {
     u64 n = cx->n; int K = cx->np, ext = l + 1 + K;
     int beta = (l + 1 + cx->alpha - 1) / cx->alpha;
     int *pidx = malloc(sizeof(int) * ext);
     for (int t = 0; t <= l; t++) pidx[t] = t;
     for (int t = 0; t < K; t++) pidx[l + 1 + t] = cx->nq + t;
-    u64 *acc0 = calloc((u64)ext * n, 8), *acc1 = calloc((u64)ext * n, 8);
+    memset(acc0, 0, (u64)ext * n * 8);
+    memset(acc1, 0, (u64)ext * n * 8);
     for (int j = 0; j < beta; j++) {
         int lo = j * cx->alpha, hi = lo + cx->alpha; if (hi > l + 1) hi = l + 1;
         int cnt = hi - lo;
@@ -844,8 +854,15 @@ static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *o
     }
     it_args B = {cx, acc0, acc1, ext, pidx};
     parallel_for(2 * ext, it_body, &B);
+    free(pidx);
+}
+
+static void keyswitch(or_ctx *cx, const u64 *d, int l, const or_key *key, u64 *out0, u64 *out1) {
+    u64 ext = (u64)(l + 1 + cx->np) * cx->n;
+    u64 *acc0 = malloc(ext * 8), *acc1 = malloc(ext * 8);
+    ks_accumulate(cx, d, l, key, acc0, acc1);
     moddown_exact(cx, acc0, acc1, l, out0, out1);
-    free(acc0); free(acc1); free(pidx);
+    free(acc0); free(acc1);
 }
 
 /* ModDown exposed for tests: acc0/acc1 coefficient form over q_0..q_l then
@@ -901,6 +918,41 @@ or_ct *or_mul(or_ctx *cx, const or_ct *a, const or_ct *b) {
         }
     }
     free(d2); free(o0); free(o1);
+    return r;
+}
+
+/* Product, relinearisation and rescale with ONE rounding: the tensor product
+ * (d0, d1, d2) at level l, the key products acc of d2 over Q_l u P, then
+ *   out_k = round((P d_k + acc_k) / (P q_l))  mod q_0..q_(l-1),
+ * the exact rounded division by P q_l (q_l's row and the special rows are the
+ * divisor; divide_round_exact).  The message is that of rescale(mul(a, b))
+ * at the same level and scale; the ciphertext differs by that rounding. */
+or_ct *or_mul_rescale(or_ctx *cx, const or_ct *a, const or_ct *b) {
+    or_key *rk = find_key(cx, 0);
+    int l = a->level < b->level ? a->level : b->level;
+    if (!rk || l < 1) return NULL;
+    u64 n = cx->n; int K = cx->np; u64 ext = (u64)(l + 1 + K) * n;
+    or_ct *t = or_ct_new(cx, l, a->scale * b->scale);
+    u64 *d2 = malloc((l + 1) * n * 8);
+    tp_args A = {cx, a, b, t, d2};
+    parallel_for(l + 1, tp_body, &A);
+    u64 *acc0 = malloc(ext * 8), *acc1 = malloc(ext * 8);
+    ks_accumulate(cx, d2, l, rk, acc0, acc1);
+    for (int i = 0; i <= l; i++) {
+        u64 q = cx->primes[i], pm = 1;
+        for (int p = 0; p < K; p++) pm = mulmod(pm, cx->primes[cx->nq + p] % q, q);
+        for (u64 c = 0; c < n; c++) {
+            u64 x = (u64)i * n + c;
+            acc0[x] = addmod(acc0[x], mulmod(t->c[0][x], pm, q), q);
+            acc1[x] = addmod(acc1[x], mulmod(t->c[1][x], pm, q), q);
+        }
+    }
+    u64 *dp = malloc(8 * (K + 1));
+    dp[0] = cx->primes[l];
+    for (int p = 0; p < K; p++) dp[1 + p] = cx->primes[cx->nq + p];
+    or_ct *r = or_ct_new(cx, l - 1, a->scale * b->scale / (double)cx->primes[l]);
+    divide_round_exact(cx, acc0, acc1, l, dp, K + 1, l, r->c[0], r->c[1]);
+    free(dp); free(d2); free(acc0); free(acc1); or_ct_free(t);
     return r;
 }
 

@@ -336,6 +336,7 @@ UNARY_OP(he_add(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(
 UNARY_OP(he_sub(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), own(cx, b), op_add(cx, a, b, true)))
 UNARY_OP(he_mul_int(he_ctx *cx, const he_ct *a, int64_t k, he_ct **out), op_mul_int(cx, a, k))
 UNARY_OP(he_mul(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), own(cx, b), op_mul(cx, a, b)))
+UNARY_OP(he_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b, he_ct **out), (need(b, "null b"), own(cx, b), op_mul_rescale(cx, a, b)))
 UNARY_OP(he_rescale(he_ctx *cx, const he_ct *a, he_ct **out), op_rescale(cx, a))
 UNARY_OP(he_drop(he_ctx *cx, const he_ct *a, uint32_t level, he_ct **out), op_drop(cx, a, (int)level))
 UNARY_OP(he_rotate(he_ctx *cx, const he_ct *a, int32_t r, he_ct **out), op_automorph(cx, a, rot_galois(cx, r)))

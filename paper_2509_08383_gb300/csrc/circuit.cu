@@ -63,10 +63,8 @@ struct HE {
         Ct t2 = mcr_bits(x2.get(), abc[0] / 2.0, -1, 24), t1 = mcr_bits(x, abc[1] / 2.0, -1, 24);
         return add_const(op_add(cx, t2.get(), t1.get(), false).get(), abc[2] / 2.0);
     }
-    Ct mul_rescale(const he_ct *a, const he_ct *b) {
-        Ct t = op_mul(cx, a, b);
-        return op_rescale(cx, t.get());
-    }
+    // product, relinearisation and rescale in one rounded division by q_l P
+    Ct mul_rescale(const he_ct *a, const he_ct *b) { return op_mul_rescale(cx, a, b); }
     // n_pt device slot vectors (n_pt x n_slots doubles; member m of a batch
     // uses vector m % n_pt) encoded at scale E, multiply, rescale
     Ct mul_plain_rescale(const he_ct *ct, const double *d_vec, int n_slots, double target = -1, int n_pt = 1) {

@@ -470,6 +470,64 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
         cx->p_inv.v[i] = invmod_host(P, q);
         cx->p_inv.s[i] = shoup_host(cx->p_inv.v[i], q);
     }
+    // product with its rescale: division by M = q_l P, inputs {q_l, p_0..p_(K-1)}
+    // (the rows l .. l+K of a key-switch accumulator), outputs q_0..q_(l-1)
+    struct MulRes { size_t qhinv, qhat, inv, negm, mrinv, half; };
+    std::vector<MulRes> mres(cx->nq);
+    const int KM = K + 1;
+    const bool have_mres = KM <= 16;
+    for (int l = 1; have_mres && l < cx->nq; l++) {
+        std::vector<u64> m(KM);
+        m[0] = cx->primes[l];
+        for (int a = 0; a < K; a++) m[1 + a] = cx->primes[cx->nq + a];
+        MulRes &R = mres[l];
+        R.qhinv = tab.size();
+        for (int a = 0; a < KM; a++) {  // (M / m_a)^-1 mod m_a
+            u64 v = 1;
+            for (int b = 0; b < KM; b++)
+                if (b != a) v = mulmod_host(v, m[b] % m[a], m[a]);
+            tab.push_back(invmod_host(v, m[a]));
+        }
+        for (int a = 0; a < KM; a++) tab.push_back(shoup_host(tab[R.qhinv + a], m[a]));
+        R.qhat = tab.size();
+        std::vector<u64> qh((size_t)KM * l);
+        for (int a = 0; a < KM; a++)
+            for (int t = 0; t < l; t++) {  // M / m_a mod q_t
+                u64 q = cx->primes[t], v = 1;
+                for (int b = 0; b < KM; b++)
+                    if (b != a) v = mulmod_host(v, m[b] % q, q);
+                qh[(size_t)a * l + t] = v;
+            }
+        for (u64 v : qh) tab.push_back(v);
+        for (int a = 0; a < KM; a++)
+            for (int t = 0; t < l; t++) tab.push_back((u64)(((u128)qh[(size_t)a * l + t] << 64) % cx->primes[t]));
+        R.inv = tab.size();
+        for (int a = 0; a < KM; a++) {
+            const u128 f = ~(u128)0 / m[a];
+            tab.push_back((u64)f);
+            tab.push_back((u64)(f >> 64));
+        }
+        R.negm = tab.size();
+        ScalarTab &mi = cx->lv[l].mulres_inv;
+        memset(&mi, 0, sizeof(mi));
+        for (int t = 0; t < l; t++) {
+            u64 q = cx->primes[t], M = 1;
+            for (int b = 0; b < KM; b++) M = mulmod_host(M, m[b] % q, q);
+            tab.push_back((u64)(((u128)((q - M) % q) << 64) % q));
+            mi.v[t] = invmod_host(M, q);
+            mi.s[t] = shoup_host(mi.v[t], q);
+        }
+        R.mrinv = tab.size();
+        for (int i = 0; i < KM; i++)
+            for (int j = 0; j < KM; j++) tab.push_back(j < i ? invmod_host(m[j] % m[i], m[i]) : 0);
+        R.half = tab.size();
+        for (int i = 0; i < KM; i++) {  // mixed-radix digits of (M - 1)/2, whose residue mod m_i is (m_i - 1)/2
+            u64 t = (m[i] - 1) / 2;
+            for (int j = 0; j < i; j++)
+                t = mulmod_host((t + m[i] - tab[R.half + j] % m[i]) % m[i], tab[R.mrinv + (size_t)i * KM + j], m[i]);
+            tab.push_back(t);
+        }
+    }
     size_t desc_bytes = desc_all.size() * sizeof(int2);
     cx->d_tabs = (u64 *)cx->arena.alloc(tab.size() * 8 + desc_bytes + 16);
     check_cuda(cudaMemcpy(cx->d_tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice), "upload tables");
@@ -499,6 +557,21 @@ void ctx_init(he_ctx *cx, const he_params *p, void *arena, size_t arena_bytes) {
     cx->moddown.negq_mont = cx->d_tabs + md_negp;
     cx->moddown.mr_inv = cx->d_tabs + md_mrinv;
     cx->moddown.mr_half = cx->d_tabs + md_half;
+    for (int l = 1; have_mres && l < cx->nq; l++) {
+        const MulRes &R = mres[l];
+        BConvTab &bt = cx->lv[l].mulres;
+        bt.qhinv = cx->d_tabs + R.qhinv;
+        bt.qhinv_sh = cx->d_tabs + R.qhinv + KM;
+        bt.qhat = cx->d_tabs + R.qhat;
+        bt.qhat_mont = cx->d_tabs + R.qhat + (size_t)KM * l;
+        bt.n_in = KM;
+        bt.n_out = l;
+        bt.stride = l;
+        bt.inv_fix = cx->d_tabs + R.inv;
+        bt.negq_mont = cx->d_tabs + R.negm;
+        bt.mr_inv = cx->d_tabs + R.mrinv;
+        bt.mr_half = cx->d_tabs + R.half;
+    }
 
     // secret
     make_secret(cx);
@@ -883,6 +956,53 @@ Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {
               ct_polys(b, 0, l), ct_polys(b, 1, l), B * (l + 1), cx->log_n, cx->stream);
     Rows o = ct_rows(out.get());
     keyswitch(cx, d2, l, *rk, o, o, 3, B, (size_t)(l + 1) * N);
+    return out;
+}
+
+// Product, relinearisation and rescale with one rounding.  The tensor
+// product (d0, d1, d2) at level l; the key products acc of d2 (ModUp, inner
+// product) over Q_l u P; P d_k added on the Q rows; then the rounded
+// division by M = q_l P: INTT of the rows of q_l and the special primes,
+// basis conversion from them (exact rounding) to q_0..q_(l-1), NTT, and
+// out_i = (acc_i - conv_i) M^-1.  The same message, level and scale as
+// rescale(mul(a, b)), without the rescale's own INTT, lift and NTT.
+Ct op_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b) {
+    same_batch(a, b);
+    const int l = std::min(a->level, b->level), B = a->batch;
+    if (l < 1) throw Error{HE_ELEVEL, "cannot rescale a level-0 product"};
+    const LevelTabs &T = cx->lv[l];
+    if (T.mulres.n_in == 0) return op_rescale(cx, op_mul(cx, a, b).get());
+    const KeyDev *rk = find_key(cx, 0);
+    if (!rk) throw Error{HE_ENOKEY, "relinearisation key not generated"};
+    const size_t N = cx->N(), ne = (size_t)T.n_ext, qp_w = 2 * ne * N;
+    const int K = cx->np, log_n = cx->log_n;
+    cudaStream_t s = cx->stream;
+    cx->ops_by_level[1][l] += (uint64_t)B;
+    cx->ops_by_level[0][l] += (uint64_t)B;
+    Scratch sc{cx, {}};
+    Ct t(ct_alloc(cx, l, a->scale * b->scale, B));
+    u64 *d2 = B == 1 ? cx->sc_a : sc.get((size_t)B * (l + 1) * N);
+    Rows r2 = make_rows(d2, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
+    ew_tensor(ct_polys(t.get(), 0), ct_polys(t.get(), 1), r2, ct_polys(a, 0, l), ct_polys(a, 1, l), ct_polys(b, 0, l),
+              ct_polys(b, 1, l), B * (l + 1), log_n, s);
+    u64 *ext = B == 1 ? cx->ks_ext : sc.get((size_t)B * ks_ext_words(cx, l));
+    u64 *acc = B == 1 ? cx->ks_acc : sc.get((size_t)B * ks_acc_words(cx, l));
+    modup(cx, d2, l, ext, B, (size_t)(l + 1) * N);
+    ks_inner(cx, d2, ext, l, *rk, 0, acc, B, (size_t)(l + 1) * N);
+    const size_t ts = ct_member_stride(t.get());
+    for (int k = 0; k < 2; k++)  // + P d_k on the Q rows
+        ew_qp_lift(acc + (size_t)k * ne * N, ct_poly(t.get(), k), l + 1, (int)ne, 0, 1, cx->p_mod, cx->slot, log_n, s,
+                   B, qp_w, ts);
+    // rows l .. l+K of each polynomial: q_l, then the special primes
+    Rows div = make_rows(acc + (size_t)l * N, ne * N, K + 1, 1, cx->nq, l);
+    ntt_inverse(div, 2 * B * (K + 1), cx->tw, log_n, s);
+    u64 *cv = B == 1 ? cx->ks_conv : sc.get((size_t)2 * B * l * N);
+    Rows conv = make_rows(cv, (size_t)l * N, l, l, cx->nq);
+    bconv(conv, div, T.mulres, 2 * B, log_n, s);
+    ntt_forward(conv, 2 * B * l, cx->tw, log_n, s);
+    Ct out(ct_alloc(cx, l - 1, a->scale * b->scale / (double)cx->primes[l], B));
+    Rows accQ = make_rows(acc, ne * N, l, l, cx->nq);
+    moddown_finish(ct_rows(out.get()), accQ, conv, T.mulres_inv, 2 * B * l, accQ, 0, log_n, s);
     return out;
 }
 

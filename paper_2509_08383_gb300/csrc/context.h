@@ -29,6 +29,10 @@ struct LevelTabs {
     int n_desc = 0;
     std::vector<BConvTab> modup;  // per digit
     ScalarTab ql_inv;             // q_l^-1 mod q_i, i < l (for rescale)
+    // product with its rescale: rounded division by M = q_l P, from the basis
+    // {q_l, p_0..p_(K-1)} to q_0..q_(l-1) (l >= 1; n_in = 0: not available)
+    BConvTab mulres;
+    ScalarTab mulres_inv;         // M^-1 mod q_i, i < l
 };
 
 }  // namespace he
@@ -139,6 +143,8 @@ Ct op_add_intd(he_ctx *cx, const he_ct *a, double K);
 Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt = 1);
 Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt, int n_pt = 1);
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b);
+// product, relinearisation and rescale with one rounding: round((P d + acc) / (q_l P))
+Ct op_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b);
 Ct op_rescale(he_ctx *cx, const he_ct *a);
 Ct op_drop(he_ctx *cx, const he_ct *a, int level);
 Ct op_automorph(he_ctx *cx, const he_ct *a, u64 g);

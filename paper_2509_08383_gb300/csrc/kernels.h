@@ -22,9 +22,9 @@ struct ScalarTab {
 // qhat[a*stride + t] and its Montgomery form qhat * 2^64 mod p_t, and
 // qhinv[a] (+ Shoup), device memory.
 struct BConvTab {
-    const u64 *qhinv, *qhinv_sh;    // [n_in]
-    const u64 *qhat, *qhat_mont;    // [n_in][stride]
-    int n_in, n_out, stride;
+    const u64 *qhinv = nullptr, *qhinv_sh = nullptr;  // [n_in]
+    const u64 *qhat = nullptr, *qhat_mont = nullptr;  // [n_in][stride]
+    int n_in = 0, n_out = 0, stride = 0;
     // rounding mode (ModDown): floor(2^128 / q_a) as (low, high) words [n_in][2]
     // and (-Q mod p_t) 2^64 mod p_t [stride], Q the product of the input
     // primes; null: approximate conversion

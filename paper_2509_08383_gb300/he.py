@@ -90,6 +90,7 @@ def lib():
             "he_mul_const": [VP, VP, dbl, dbl, PP],
             "he_add_const": [VP, VP, dbl, PP],
             "he_mul": [VP, VP, VP, PP],
+            "he_mul_rescale": [VP, VP, VP, PP],
             "he_rescale": [VP, VP, PP],
             "he_drop": [VP, VP, u32, PP],
             "he_rotate": [VP, VP, i32, PP],
@@ -363,6 +364,10 @@ class Context:
 
     def rescale(self, a):
         return self._ct(lib().he_rescale, a.ptr)
+
+    def mul_rescale(self, a, b):
+        """Product, relinearisation and rescale with one rounding (by q_l P)."""
+        return self._ct(lib().he_mul_rescale, a.ptr, b.ptr)
 
     def drop(self, a, level):
         return self._ct(lib().he_drop, a.ptr, int(level))

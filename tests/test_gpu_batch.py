@@ -71,6 +71,7 @@ OPS = {
     "sub": lambda g, x, y: g.sub(x, y),
     "mul_relin": lambda g, x, y: g.mul(x, y),
     "mul_rescale": lambda g, x, y: g.rescale(g.mul(x, y)),
+    "mul_rescale_fused": lambda g, x, y: g.mul_rescale(x, y),
     "rotate_1": lambda g, x, y: g.rotate(x, 1),
     "rotate_-2": lambda g, x, y: g.rotate(x, -2),
     "conjugate": lambda g, x, y: g.conj(x),

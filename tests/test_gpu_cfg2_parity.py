@@ -95,6 +95,9 @@ def test_cfg2_product_relin_rescale_bit_exact(cfg2, level):
     assert _same(p_g, p_o)
     r_g, r_o = g.rescale(p_g), o.rescale(p_o)
     assert _same(r_g, r_o) and r_g.scale == r_o.scale
+    # the same product with its rescale in one rounded division by q_l P (11 divisor primes)
+    f_g, f_o = g.mul_rescale(a_g, b_g), o.mul_rescale(a_o, b_o)
+    assert _same(f_g, f_o) and f_g.scale == f_o.scale == r_o.scale
 
 
 def test_cfg2_rotsum_stage_bit_exact(cfg2):

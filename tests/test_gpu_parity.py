@@ -130,6 +130,9 @@ def test_ops_bit_exact(small):
     assert eq(prod_g, prod_o)
     rs_g, rs_o = g.rescale(prod_g), o.rescale(prod_o)
     assert eq(rs_g, rs_o) and rs_g.scale == rs_o.scale
+    # product and rescale in one rounded division by q_l P
+    mr_g, mr_o = g.mul_rescale(a_g, b_g), o.mul_rescale(a_o, b_o)
+    assert eq(mr_g, mr_o) and mr_g.scale == mr_o.scale == rs_o.scale
     # constant multiplication with the scale rule
     c, target = -0.3125, 2.0 ** 40
     E = (target * float(o.primes[a_o.level])) / a_o.scale

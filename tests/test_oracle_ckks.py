@@ -429,3 +429,26 @@ def test_hoisted_rotsum_stage():
     assert np.abs(enc.decode(ctx.decrypt(full), 10, full.scale).real - z.sum()).max() < 1e-5
     with pytest.raises(RuntimeError):
         ctx.rotsum_stage(a, [11])                    # no key for 11
+
+
+def test_mul_rescale_one_rounding():
+    """The product with its rescale in one rounded division by q_l P decrypts
+    like rescale(mul(a, b)) (they differ by the rounding of one division
+    instead of two: a few units per coefficient), at the same level and scale,
+    and to the slot-wise product of the messages."""
+    ctx = ckks.Context(10, [60, 40, 40, 40], [60, 60, 61], dnum=2, seed=23)
+    ctx.gen_relin_key()
+    rng = np.random.default_rng(8)
+    za, zb = rng.uniform(-1, 1, ctx.slots), rng.uniform(-1, 1, ctx.slots)
+    scale = 2.0 ** 40
+    a = ctx.encrypt(enc.encode(za, 10, scale), scale, 1)
+    b = ctx.encrypt(enc.encode(zb, 10, scale), scale, 2)
+    fused, ref = ctx.mul_rescale(a, b), ctx.rescale(ctx.mul(a, b))
+    assert fused.level == ref.level == ctx.top_level - 1 and fused.scale == ref.scale
+    d = np.abs(ctx.decrypt(fused) - ctx.decrypt(ref))
+    assert d.max() <= 0.5 * (1 + np.abs(ctx.secret()).sum()) + 1
+    got = enc.decode(ctx.decrypt(fused), 10, fused.scale).real
+    assert np.abs(got - za * zb).max() < 1e-6
+    low = ctx.drop(a, 0)
+    with pytest.raises(RuntimeError):
+        ctx.mul_rescale(low, low)                    # level 0 cannot be rescaled
