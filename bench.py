@@ -1,6 +1,6 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|cfg5|mul16|rot16|ntt16|boot16|bootc16]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|cfg5|tune|mul16|rot16|ntt16|boot16|bootc16]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
@@ -356,33 +356,28 @@ def run_cfg3(args):
     (1/1/2/4 ciphertexts each at N=2^16), logits N(0, 2^2) with the top
     entry 0.5 above the second, the paper's HE circuit (T=4, p=[16,4,4,6],
     c=[5,3,3,3]) with bootstrapping.  Batched: one batch per vocabulary size,
-    every homomorphic step one launch for all its streams, the streams' scalar
-    chains shared.  Sequential: one stream at a time; every stream of a
-    vocabulary costs the same, so one stream per vocabulary is timed and
-    counted 16 times."""
+    every homomorphic step one launch for all its streams; the scalar chains
+    shared across the batch's streams or kept per stream, the rotate-and-sum
+    radix and dnum as the autotuner picked them (`--workload tune`; without
+    its file: shared chains, radix 8, dnum 3).  Sequential: one stream at a
+    time; every stream of a vocabulary costs the same, so one stream per
+    vocabulary is timed and counted 16 times."""
     import torch
-    from paper_2509_08383_gb300 import build, he
+    from paper_2509_08383_gb300 import autotune, build, he
     from paper_2509_08383_gb300 import plan as P
-    from paper_2509_08383_gb300 import synth
     build.build_library()
     torch.cuda.set_device(0)
     per = 16
-    slots = 1 << 15
-    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=200 << 30)
+    tuned = autotune.load(16, CFG2_Q, CFG2_P, 192)
+    dnum = tuned["dnum"] if tuned else 3
+    chains = dict(tuned["chains"]) if tuned else {}
+    if args.chains != "tuned":
+        chains = {str(v): args.chains for v in CFG3_VOCABS}
+    g = he.Context(16, CFG2_Q, CFG2_P, dnum, h=192, seed=1, arena_bytes=200 << 30)
     g.bootstrap_prepare(24, 4, 31)
-    groups = []
-    for v in CFG3_VOCABS:
-        gen = (lambda s, v=v: synth.logits_gaussian(s, n=v, sd=2.0, gap=0.5))
-        pl = P.calibrate(lambda i: gen(100000 + i), 60, v, slots, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
-                         tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True)
-        pl.shared = True
-        g.cutmax_prepare(pl)
-        xs = [gen(s) for s in range(per)]
-        cts = []
-        for s, x in enumerate(xs):
-            vecs = P.pack_cts(x, slots) if pl.cts > 1 else [P.pack(x, slots, pl.packing)]
-            cts += [g.encrypt(vv, g.delta, 1000 * v + 10 * s + c) for c, vv in enumerate(vecs)]
-        groups.append((v, pl, xs, g.batch_pack(cts), cts[:pl.cts]))
+    if tuned:
+        g.set_rotsum_radix(tuned["rotsum_log_radix"])
+    groups = cfg3_batches(g, per, CFG3_VOCABS, chains)
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -406,10 +401,7 @@ def run_cfg3(args):
                 if it >= args.warmup:
                     t_batch += ms / args.steps
             # argmax of every stream of the batch
-            ok = 0
-            for s, x in enumerate(xs):
-                dec = np.concatenate([g.decrypt(g.batch_member(Z, s * pl.cts + c)) for c in range(pl.cts)])[:v]
-                ok += int(np.argmax(dec)) == int(np.argmax(x))
+            ok = batch_argmax_ok(g, Z, xs, pl)
             acc.append(ok)
             pl1 = P.CutMaxPlan(**{**pl.to_dict(), "shared": False})
             b1 = g.batch_pack(one)
@@ -420,7 +412,8 @@ def run_cfg3(args):
                 _, nb1 = g.ledger(reset=True)
                 if it >= args.warmup:
                     t_seq += per * ms1 / args.steps
-            res[str(v)] = {"cts_per_stream": pl.cts, "batched_ms": ms, "batched_bootstraps": nb,
+            res[str(v)] = {"cts_per_stream": pl.cts, "chains": "shared" if pl.shared else "stream",
+                           "batched_ms": ms, "batched_bootstraps": nb,
                            "single_stream_ms": ms1, "single_stream_bootstraps": nb1, "argmax_ok": ok, "k": pl.k,
                            "d": pl.d}
             del Z
@@ -431,13 +424,83 @@ def run_cfg3(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": {"workload": "64 decode streams, 16 per vocabulary 8192/32000/50257/128256 (1/1/2/4 "
                                   "ciphertexts), N(0,4) logits with top gap 0.5, T=4 p=[16,4,4,6] c=[5,3,3,3], "
-                                  "bootstrapping, one batch per vocabulary with shared scalar chains",
+                                  "bootstrapping, one batch per vocabulary (scalar chain mode per vocabulary "
+                                  "in per_vocabulary)",
+                      "dnum": dnum, "rotsum_radix": 1 << (tuned["rotsum_log_radix"] if tuned else 3),
+                      "tuned": bool(tuned),
                       "l2": "flushed between steps (256 MiB write)"},
            "sequential": {"value": 1000.0 * n_streams / t_seq, "unit": "decodes/s", "ms_per_step": t_seq,
                           "how": "one stream per vocabulary timed alone, times 16"},
            "speedup_vs_sequential": t_seq / t_batch, "argmax_correct": sum(acc), "streams": n_streams,
            "per_vocabulary": res, "clocks": clk.summary()}
     print(json.dumps(out))
+
+
+def cfg3_batches(g, per, vocabs, chains=None):
+    """Per vocabulary size: its calibrated plan, the batch of `per` encrypted
+    streams, the plaintext logits and the member count per stream."""
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    slots = g.n // 2
+    groups = []
+    for v in vocabs:
+        gen = (lambda s, v=v: synth.logits_gaussian(s, n=v, sd=2.0, gap=0.5))
+        pl = P.calibrate(lambda i: gen(100000 + i), 60, v, slots, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
+                         tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True)
+        pl.shared = (chains or {}).get(str(v), "shared") == "shared"
+        g.cutmax_prepare(pl)
+        xs = [gen(s) for s in range(per)]
+        cts = []
+        for s, x in enumerate(xs):
+            vecs = P.pack_cts(x, slots) if pl.cts > 1 else [P.pack(x, slots, pl.packing)]
+            cts += [g.encrypt(vv, g.delta, 1000 * v + 10 * s + c) for c, vv in enumerate(vecs)]
+        groups.append((v, pl, xs, g.batch_pack(cts), cts[:pl.cts]))
+    return groups
+
+
+def batch_argmax_ok(g, Z, xs, pl):
+    ok = 0
+    for s, x in enumerate(xs):
+        dec = np.concatenate([g.decrypt(g.batch_member(Z, s * pl.cts + c)) for c in range(pl.cts)])[:len(x)]
+        ok += int(np.argmax(dec)) == int(np.argmax(x))
+    return ok
+
+
+def run_tune(args):
+    """Autotune the runtime choices (rotate-and-sum radix, dnum, batch chain
+    mode) on full decodes of the benchmark's workloads and write the JSON the
+    other workloads read: the radix and dnum on the 32,000-logit decode, the
+    chain mode per vocabulary on 16-stream batches of the four vocabulary
+    sizes."""
+    import torch
+    from paper_2509_08383_gb300 import autotune, build, he
+    from paper_2509_08383_gb300 import plan as P
+    build.build_library()
+    torch.cuda.set_device(0)
+    log_n, qb, pb, dnum, pl, gen, desc, boot = workload("cfg2")
+    slots = 1 << (log_n - 1)
+    xs = [gen(30000 + s) for s in range(4)]
+
+    def make_ctx(d):
+        g = he.Context(log_n, qb, pb, d, h=boot[0], seed=1, arena_bytes=64 << 30)
+        g.bootstrap_prepare(*boot[1:])
+        return g
+
+    inputs = lambda g: [g.encrypt(P.pack(x, slots, pl.packing), g.delta, 7 + s) for s, x in enumerate(xs)]
+    check = lambda g, i, z: int(np.argmax(g.decrypt(z, pl.n))) == int(np.argmax(xs[i]))
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    choice, table = autotune.tune_decode(make_ctx, pl, inputs, check, dnums=(3, 4, 5), log=log)
+    g = he.Context(log_n, qb, pb, choice["dnum"], h=boot[0], seed=1, arena_bytes=200 << 30)
+    g.bootstrap_prepare(*boot[1:])
+    g.set_rotsum_radix(choice["rotsum_log_radix"])
+    batches = {}
+    for v, bpl, bxs, batch, _ in cfg3_batches(g, 16, CFG3_VOCABS):
+        batches[str(v)] = (bpl, batch, lambda Z, bxs=bxs, bpl=bpl: batch_argmax_ok(g, Z, bxs, bpl) == len(bxs))
+    choice["chains"], table["chains"] = autotune.tune_chains(g, batches, log=log)
+    rec = autotune.save(autotune.default_path(log_n), log_n, qb, pb, boot[0], choice, table,
+                        {"decode": desc["workload"], "batches": "16 streams per vocabulary "
+                         + "/".join(map(str, CFG3_VOCABS)) + ", N(0,4) logits, top gap 0.5"})
+    print(json.dumps(rec))
 
 
 def run_cfg4(args):
@@ -623,8 +686,8 @@ def run_cfg5(args):
 def run_micro(args):
     """Micro workloads for kernel profiles at the N=2^16 parameter set (the
     same kernels as a CutMax step at full size): mul16 = one homomorphic
-    multiplication (tensor product, hybrid key switch, rescale) at the top
-    level; rot16 = one rotation (automorphism + hybrid key switch) at the top
+    multiplication (tensor product, hybrid key switch and rescale in one
+    rounded division by q_l P) at the top level; rot16 = one rotation (automorphism + hybrid key switch) at the top
     level; ntt16 = a forward and an inverse NTT of one 40-limb block (every
     prime of the chain, 21 MB); boot16 = one bootstrapping of a level-0
     ciphertext; bootc16 = one constant bootstrapping (trace form) of a level-0
@@ -645,13 +708,13 @@ def run_micro(args):
         op = lambda: g.bootstrap_const(cts[0])
         metric, unit = "constant bootstraps/s (N=2^16, K=24, r=4, d=31, dnum=3)", "boot/s"
         wl = ("CKKS bootstrapping of a level-0 ciphertext holding one complex value in every slot "
-              "(trace form), N=2^16, 31 primes + 10 special primes, h=192")
+              "(trace form), N=2^16, 30 primes + 10 special primes, h=192")
     elif boot:
         g.bootstrap_prepare(24, 4, 31)
         cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, 0, level=0)]
         op = lambda: g.bootstrap(cts[0])
         metric, unit = "bootstraps/s (N=2^16, K=24, r=4, d=31, dnum=3)", "boot/s"
-        wl = "CKKS bootstrapping of a level-0 ciphertext, N=2^16, 31 primes + 10 special primes, h=192"
+        wl = "CKKS bootstrapping of a level-0 ciphertext, N=2^16, 30 primes + 10 special primes, h=192"
     elif args.workload == "ntt16":
         limbs = len(CFG2_Q) + len(CFG2_P)
         blk = torch.randint(0, 1 << 39, (limbs, 1 << 16), dtype=torch.int64, device="cuda")
@@ -663,8 +726,8 @@ def run_micro(args):
         g.gen_rot_keys([1])
         cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, 0)]
         op = lambda: g.rotate(cts[0], 1)
-        metric, unit = "homomorphic rotations/s (N=2^16, level 30, dnum=3)", "rot/s"
-        wl = "slot rotation by 1 (automorphism + hybrid key switch), N=2^16, 31 primes + 10 special primes"
+        metric, unit = "homomorphic rotations/s (N=2^16, level 29, dnum=3)", "rot/s"
+        wl = "slot rotation by 1 (automorphism + hybrid key switch), N=2^16, 30 primes + 10 special primes"
         l1, K, beta = len(CFG2_Q), len(CFG2_P), 3
         # automorphism (read + write both polynomials) + key switch: d in, beta key digits
         # (b and a over l+1+K primes), two output polynomials
@@ -672,9 +735,10 @@ def run_micro(args):
     else:
         g.gen_relin_key()
         cts = [g.encrypt(rng.uniform(-1, 1, slots), g.delta, s) for s in range(2)]
-        op = lambda: g.rescale(g.mul(cts[0], cts[1]))
-        metric, unit = "homomorphic multiplications/s (N=2^16, level 30, dnum=3)", "mul/s"
-        wl = "ciphertext product + relinearisation + rescale, N=2^16, 31 primes + 10 special primes"
+        op = lambda: g.mul_rescale(cts[0], cts[1])
+        metric, unit = "homomorphic multiplications/s (N=2^16, level 29, dnum=3)", "mul/s"
+        wl = ("ciphertext product + relinearisation + rescale (one rounded division by q_l P), N=2^16, "
+              "30 primes + 10 special primes")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     nsteps = args.warmup + args.steps
@@ -752,10 +816,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "mul16",
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5", "tune", "mul16",
                                                            "rot16", "ntt16", "boot16", "bootc16"])
     ap.add_argument("--tokens", type=int, default=32, help="cfg5: tokens decoded per stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chains", default="tuned", choices=["tuned", "shared", "stream"],
+                    help="cfg3: scalar chains packed across a batch's streams (general bootstraps), kept per "
+                         "stream (constant bootstraps, one launch for the batch), or as the autotuner chose")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -763,6 +830,8 @@ def main():
         return run_micro(args)
     if args.workload == "cfg3":
         return run_cfg3(args)
+    if args.workload == "tune":
+        return run_tune(args)
     if args.workload == "cfg4":
         return run_cfg4(args)
     if args.workload == "cfg5":
