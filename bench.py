@@ -490,6 +490,8 @@ def run_tune(args):
     check = lambda g, i, z: int(np.argmax(g.decrypt(z, pl.n))) == int(np.argmax(xs[i]))
     log = lambda m: print(m, file=sys.stderr, flush=True)
     choice, table = autotune.tune_decode(make_ctx, pl, inputs, check, dnums=(3, 4, 5), log=log)
+    free, total = torch.cuda.mem_get_info()
+    log(f"device memory free after the decode search: {free / 2**30:.1f} of {total / 2**30:.1f} GiB")
     g = he.Context(log_n, qb, pb, choice["dnum"], h=boot[0], seed=1, arena_bytes=200 << 30)
     g.bootstrap_prepare(*boot[1:])
     g.set_rotsum_radix(choice["rotsum_log_radix"])

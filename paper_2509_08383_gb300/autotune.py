@@ -27,6 +27,7 @@ timing next to the choices, the device and the parameter set it was measured
 on; ``load`` returns the choices only for a matching device and parameter
 set.
 """
+import gc
 import hashlib
 import json
 import os
@@ -115,6 +116,7 @@ def tune_decode(make_ctx, plan, inputs, check, dnums=(3, 4, 5), radices=RADICES,
         raise RuntimeError("no rotate-and-sum radix kept every argmax")
     table["dnum"][str(d0)] = {"ms": best_ms, "argmax_ok": True}
     del cts, g
+    gc.collect()  # the context's device memory goes back before the next one
     best_d = d0
     for d in dnums[1:]:
         t0 = time.perf_counter()
@@ -128,6 +130,7 @@ def tune_decode(make_ctx, plan, inputs, check, dnums=(3, 4, 5), radices=RADICES,
         if ok and ms < best_ms:
             best_d, best_ms = d, ms
         del cts, g
+        gc.collect()
     return {"rotsum_log_radix": best_r, "dnum": best_d}, table
 
 
