@@ -350,6 +350,26 @@ int he_cutmax_prepare(he_ctx *ctx, const he_cutmax_plan *plan);
  * stream-major; every step then runs once for the whole batch, and the
  * output is the batch of the streams' results in the same order. */
 int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out);
+/* cutmax through a CUDA graph (engineering; the paper evaluates Alg. 2 op by
+ * op).  Same arguments, result and errors as cutmax, bit for bit.  The first
+ * call with a given plan and input shape (level, scale, batch size, the
+ * context's rotate-and-sum radix) runs directly and then captures the whole
+ * call -- every iteration, refresh and the final normalisation -- as one CUDA
+ * graph; every buffer of the graph comes from a block of the context's arena
+ * that the graph keeps until he_cutmax_graph_clear or he_ctx_destroy (about
+ * 1.25x the device memory one call takes).  Later calls with the same key copy
+ * `in` into the graph's input buffer, launch the graph on the context's stream
+ * and copy its output into *out (owned by the caller).  Ledger counts and the
+ * launch count advance as for a direct call.  Where a call cannot be captured
+ * (or while a kernel class is being profiled) it runs directly.  Calls on one
+ * context must not overlap (the graph's buffers are shared); graphs that hold
+ * bootstrap tables or rotation choices that have since changed are retired. */
+int he_cutmax_graph(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out);
+/* Calls of he_cutmax_graph so far: graphs captured, graph launches, direct
+ * runs after a capture that failed or under profiling (any pointer may be NULL). */
+int he_cutmax_graph_stats(he_ctx *ctx, uint64_t *captured, uint64_t *replayed, uint64_t *direct);
+/* Frees every captured graph and its arena block (waits for the context's stream). */
+int he_cutmax_graph_clear(he_ctx *ctx);
 /* Cut noise drawn by the server from encrypted uniforms (Alg. 3 with
  * Lemma 2 / Observation 1): out = G = U^(1/alpha) slot by slot, U in [0, 1]
  * encrypted by the client, by the degree-`degree` Chebyshev interpolant of

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhecutmax.so")
-SOURCES = ["kernels.cu", "context.cu", "circuit.cu", "capi.cu", "noalloc.cu", "learn.cu"]
+SOURCES = ["kernels.cu", "context.cu", "circuit.cu", "graph.cu", "capi.cu", "noalloc.cu", "learn.cu"]
 HEADERS = ["common.cuh", "kernels.h", "context.h", "arena.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -396,6 +396,7 @@ int he_ctx_set_rotsum_radix(he_ctx *cx, uint32_t log2_radix) {
         cx->err = "rotate-and-sum radix must be 2, 4, 8 or 16 (log2 1..4)";
         return HE_EINVAL;
     }
+    if (cx->rotsum_log_radix != (int)log2_radix) cx->gen++;
     cx->rotsum_log_radix = (int)log2_radix;
     return HE_OK;
 }
@@ -518,6 +519,32 @@ int cutmax(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out)
     Ct r = cutmax_ct(cx, in, pl);
     launched(cx, "cutmax");
     *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_cutmax_graph(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out) {
+    if (!cx || !in || !out) return HE_EINVAL;
+    API_TRY
+    own(cx, in);
+    Plan pl = plan_from(plan);
+    Ct r = cutmax_graph(cx, in, pl);
+    launched(cx, "cutmax graph");
+    *out = r.release();
+    API_CATCH(cx)
+}
+
+int he_cutmax_graph_stats(he_ctx *cx, uint64_t *captured, uint64_t *replayed, uint64_t *direct) {
+    if (!cx) return HE_EINVAL;
+    if (captured) *captured = cx->graph_stats[0];
+    if (replayed) *replayed = cx->graph_stats[1];
+    if (direct) *direct = cx->graph_stats[2];
+    return HE_OK;
+}
+
+int he_cutmax_graph_clear(he_ctx *cx) {
+    if (!cx) return HE_EINVAL;
+    API_TRY
+    graphs_release(cx);
     API_CATCH(cx)
 }
 

@@ -18,10 +18,35 @@
 //   Z = (kappa_f Y) F   (Goldschmidt inverse, App. B.1)
 #include <algorithm>
 #include <cmath>
+#include <string_view>
 
 #include "context.h"
 
 namespace he {
+
+// Device copy of a constant slot vector, uploaded on first use and kept for
+// the context's life (keyed by content): the circuits use the same masks and
+// constants on every call, and a CUDA graph capture cannot upload from
+// pageable host memory.  Above 4096 vectors the cache starts over, which
+// retires the captured graphs that point into it.
+const double *device_const(he_ctx *cx, const std::vector<double> &v) {
+    const size_t bytes = v.size() * sizeof(double);
+    const uint64_t h = std::hash<std::string_view>{}(std::string_view(reinterpret_cast<const char *>(v.data()), bytes));
+    auto r = cx->const_cache.equal_range(h);
+    for (auto it = r.first; it != r.second; ++it)
+        if (it->second.host == v) return it->second.d;
+    if (cx->capturing) throw Error{HE_EINVAL, "a constant vector first seen during a graph capture"};
+    if (cx->const_cache.size() >= 4096) {
+        for (auto &e : cx->const_cache) cx->arena.release(e.second.d, e.second.host.size() * sizeof(double));
+        cx->const_cache.clear();
+        cx->gen++;
+    }
+    double *d = (double *)cx->arena.alloc(bytes);
+    // a pageable source is staged before the call returns
+    check_cuda(cudaMemcpyAsync(d, v.data(), bytes, cudaMemcpyHostToDevice, cx->stream), "constant vector");
+    cx->const_cache.emplace(h, he_ctx::ConstVec{d, v});
+    return d;
+}
 
 namespace {
 
@@ -81,9 +106,7 @@ struct HE {
         const int slots = cx->n / 2;
         std::vector<double> v(2 * (size_t)slots);
         for (int i = 0; i < slots; i++) v[i] = re, v[slots + i] = im;
-        Scratch sc{cx, {}};
-        double *d_v = (double *)sc.get(v.size());
-        check_cuda(cudaMemcpyAsync(d_v, v.data(), v.size() * 8, cudaMemcpyHostToDevice, cx->stream), "constant");
+        const double *d_v = device_const(cx, v);
         double *d_pt = cx->d_dbl + cx->N();
         encode_dev(cx, d_v, d_v + slots, slots, ct->scale, d_pt);
         return op_add_plain(cx, ct, d_pt);
@@ -235,15 +258,11 @@ static Ct stream_sum(he_ctx *cx, const he_ct *a, int cps) {
 static Ct stream_bcast(he_ctx *cx, const he_ct *a, int cps) {
     return cps > 1 ? op_group(cx, a, cps, false) : op_copy(cx, a);
 }
-// device copy of `vals` scaled by c, in scratch
-static double *upload_scaled(he_ctx *cx, Scratch &sc, const std::vector<double> &vals, double c) {
+// device copy of `vals` scaled by c (see device_const)
+static const double *upload_scaled(he_ctx *cx, Scratch &, const std::vector<double> &vals, double c) {
     std::vector<double> v(vals);
     for (double &x : v) x *= c;
-    double *d = (double *)sc.get(v.size());
-    // a pageable source is staged before the call returns, so v may go
-    check_cuda(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, cx->stream),
-               "upload mask");
-    return d;
+    return device_const(cx, v);
 }
 
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
@@ -256,7 +275,7 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
     HE he{cx, cx->delta};
     const int cps = sh.cps, m = sh.m;
     Scratch sc{cx, {}};
-    double *d_mask = m ? upload_scaled(cx, sc, sh.mask, 1.0) : nullptr;
+    const double *d_mask = m ? upload_scaled(cx, sc, sh.mask, 1.0) : nullptr;
     Ct Y = op_copy(cx, in);
     for (int t = 0; t < pl.T; t++) {
         Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
@@ -803,6 +822,7 @@ void boot_prepare(he_ctx *cx, int K, int r, int d) {
     gen_relin_key(cx);
     for (u64 g : gs) gen_galois_key(cx, g);
     cx->boot_state = B;
+    cx->gen++;  // graphs that point into the previous tables retire
 }
 
 Ct bootstrap_ct(he_ctx *cx, const he_ct *in) { return bootstrap_stage(cx, in, 100); }

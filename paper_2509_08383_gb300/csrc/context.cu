@@ -1123,6 +1123,7 @@ Ct op_group(he_ctx *cx, const he_ct *a, int g, bool sum) {
 }  // namespace he
 
 he_ctx::~he_ctx() {
+    he::graphs_release(this);
     for (he_ct *c : live) c->ctx = nullptr;
     he::release_slot(slot);
     for (auto &k : keys) arena.release(k.data, k.bytes);

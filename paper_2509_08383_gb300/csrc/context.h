@@ -3,6 +3,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -12,6 +13,7 @@
 
 namespace he {
 struct Boot;
+struct CutmaxGraph;
 
 struct KeyDev {
     u64 g;       // Galois element, 0 = relinearisation
@@ -88,6 +90,17 @@ struct he_ctx {
     uint64_t n_boot = 0;
     uint64_t ops_by_level[4][HE_MAX_PRIMES] = {{0}};  // rescales, tensor products, plaintext products, additions
     int rotsum_log_radix = 3;              // rotate-and-sum stages of 2^this slots (he_ctx_set_rotsum_radix)
+    // device copies of the circuits' constant slot vectors (masks, constants),
+    // keyed by content; they live as long as the context
+    struct ConstVec { double *d; std::vector<double> host; };
+    std::unordered_multimap<uint64_t, ConstVec> const_cache;
+    // CutMax calls captured as CUDA graphs (graph.cu); `gen` changes whenever
+    // something a graph holds by address may change (bootstrap tables,
+    // rotate-and-sum radix), which retires every graph
+    std::vector<std::shared_ptr<he::CutmaxGraph>> graphs;
+    uint64_t gen = 0;
+    bool capturing = false;                // a CUDA graph capture is under way
+    uint64_t graph_stats[3] = {0, 0, 0};   // captured, replayed, run directly after a failed capture
 
     ~he_ctx();
     size_t N() const { return (size_t)n; }
@@ -196,6 +209,10 @@ struct Plan {
 Plan plan_from(const he_cutmax_plan *p);
 void plan_keys(he_ctx *cx, const Plan &pl, std::vector<u64> &galois);
 Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl);
+// CutMax through a CUDA graph captured per plan and input shape (graph.cu)
+Ct cutmax_graph(he_ctx *cx, const he_ct *in, const Plan &pl);
+void graphs_release(he_ctx *cx);
+const double *device_const(he_ctx *cx, const std::vector<double> &v);
 void boot_prepare(he_ctx *cx, int K, int r, int d);
 Ct bootstrap_ct(he_ctx *cx, const he_ct *in);
 Ct bootstrap_stage(he_ctx *cx, const he_ct *in, int stage);

@@ -33,6 +33,7 @@ void upload_constants(int slot, const PrimeConsts &pc_in, const u64 *cdt, int n_
 
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long launch_count() { return g_launches.load(); }
+void launches_add(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- profiling
 // When a kernel class is enabled, its launchers bracket each launch with a
@@ -55,6 +56,7 @@ void prof_enable(int cls) {
     g_prof.bytes.clear();
 }
 bool prof_on(int cls) { return cls == g_prof.cls; }
+bool prof_any() { return g_prof.cls >= 0; }
 void prof_begin(int cls, cudaStream_t s) {
     if (cls != g_prof.cls) return;
     if (g_prof.used * 2 + 2 > g_prof.ev.size()) {

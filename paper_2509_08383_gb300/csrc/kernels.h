@@ -39,10 +39,12 @@ struct BConvTab {
 
 // number of kernels launched by this library so far (all contexts)
 unsigned long long launch_count();
+void launches_add(long long n);  // launches made (or, negative, taken back) around CUDA graphs
 
 // CUDA-event timing of one kernel class at a time (see he_profile_enable)
 enum ProfClass { PROF_NTT_FWD = 0, PROF_NTT_INV = 1, PROF_KS_INNER = 2, PROF_BCONV = 3 };
 void prof_enable(int cls);
+bool prof_any();  // some kernel class is instrumented
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s, double bytes);
 void prof_read(int cls, unsigned long long *launches, double *ms, double *bytes);

@@ -111,6 +111,9 @@ def lib():
             "he_cutmax_prepare": [VP, C.POINTER(CPlan)],
             "he_learn_invsqrt": [VP, C.POINTER(C.c_float), sz, u32, C.c_float, u64, pd, pd],
             "cutmax": [VP, VP, C.POINTER(CPlan), PP],
+            "he_cutmax_graph": [VP, VP, C.POINTER(CPlan), PP],
+            "he_cutmax_graph_stats": [VP, pu64, pu64, pu64],
+            "he_cutmax_graph_clear": [VP],
             "nucleus_sample": [VP, VP, dbl, dbl, VP, i32, C.POINTER(CPlan), PP],
             "he_beta_noise": [VP, VP, dbl, u32, PP],
         }
@@ -460,6 +463,20 @@ class Context:
     def cutmax(self, ct, plan):
         s, keep = plan_struct(plan)
         return self._ct(lib().cutmax, ct.ptr, C.byref(s))
+
+    def cutmax_graph(self, ct, plan):
+        """cutmax through a CUDA graph captured per plan and input shape."""
+        s, keep = plan_struct(plan)
+        return self._ct(lib().he_cutmax_graph, ct.ptr, C.byref(s))
+
+    def graph_stats(self):
+        """(graphs captured, graph launches, direct runs) of cutmax_graph."""
+        v = [C.c_uint64(0) for _ in range(3)]
+        self._chk(lib().he_cutmax_graph_stats(self.ptr, *[C.byref(x) for x in v]))
+        return tuple(int(x.value) for x in v)
+
+    def graph_clear(self):
+        self._chk(lib().he_cutmax_graph_clear(self.ptr))
 
     def beta_noise(self, u_ct, alpha, degree=31):
         """G = U^(1/alpha) of encrypted uniforms (Chebyshev interpolant)."""
