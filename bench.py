@@ -413,6 +413,7 @@ def run_cfg3(args):
                 _, nb1 = g.ledger(reset=True)
                 if it >= args.warmup:
                     t_seq += per * ms1 / args.steps
+            g.graph_clear()  # this vocabulary's graphs give their memory back
             res[str(v)] = {"cts_per_stream": pl.cts, "chains": "shared" if pl.shared else "stream",
                            "batched_ms": ms, "batched_bootstraps": nb,
                            "single_stream_ms": ms1, "single_stream_bootstraps": nb1, "argmax_ok": ok, "k": pl.k,
@@ -486,6 +487,7 @@ def run_tune(args):
     def make_ctx(d):
         g = he.Context(log_n, qb, pb, d, h=boot[0], seed=1, arena_bytes=64 << 30)
         g.bootstrap_prepare(*boot[1:])
+        g.set_graphs(args.graph)  # candidates are timed as the benches run them
         return g
 
     inputs = lambda g: [g.encrypt(P.pack(x, slots, pl.packing), g.delta, 7 + s) for s, x in enumerate(xs)]
@@ -496,6 +498,7 @@ def run_tune(args):
     log(f"device memory free after the decode search: {free / 2**30:.1f} of {total / 2**30:.1f} GiB")
     g = he.Context(log_n, qb, pb, choice["dnum"], h=boot[0], seed=1, arena_bytes=200 << 30)
     g.bootstrap_prepare(*boot[1:])
+    g.set_graphs(args.graph)
     g.set_rotsum_radix(choice["rotsum_log_radix"])
     batches = {}
     for v, bpl, bxs, batch, _ in cfg3_batches(g, 16, CFG3_VOCABS):
@@ -533,6 +536,7 @@ def run_cfg4(args):
     torch.cuda.set_device(0)
     g = he.Context(log_n, qb, pb, dnum, h=boot[0], seed=1, arena_bytes=48 << 30)
     g.bootstrap_prepare(*boot[1:])
+    g.set_graphs(args.graph)
     t0 = time.perf_counter()
     lpl, report = learned.learned_plan(g, plain, calib_kw, logged)
     t_train = time.perf_counter() - t0
@@ -569,7 +573,8 @@ def run_cfg4(args):
            "warmup": args.warmup, "ms_per_step": res["learned"]["ms_per_decode"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": {"workload": desc["workload"] + "; learned 1-16-1 square-activation inverse square root",
-                      "variances_logged": int(logged.size), "log_seconds": t_log, "train_seconds": t_train},
+                      "variances_logged": int(logged.size), "log_seconds": t_log, "train_seconds": t_train,
+                      "cuda_graph": bool(args.graph)},
            "training": {str(t): v for t, v in report.items()}, "plain": res["plain"], "learned": res["learned"],
            "speedup_vs_plain": res["plain"]["ms_per_decode"] / res["learned"]["ms_per_decode"],
            "clocks": clk.summary()}
@@ -622,6 +627,7 @@ def run_cfg5(args):
     torch.cuda.set_device(0)
     g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=160 << 30)
     g.bootstrap_prepare(24, 4, 31)
+    g.set_graphs(args.graph)
     assert he.HE_NUCLEUS_DEGREE == deg
     lpl, report = learned.learned_plan(g, plain, calib_kw, logged)
     lpl.shared = True
@@ -680,7 +686,8 @@ def run_cfg5(args):
            "config": {"workload": "Alg. 3 decode loop: 16 streams (8 at top-p 0.9, 8 at 0.95) x 128,256 logits "
                                   "N(0,4) top gap 0.5 in 4 ciphertexts, G = U^(1/alpha) from encrypted uniforms "
                                   "(degree-31 Chebyshev), CutMax T=4 p=[16,4,4,6] c=[5,3,3,3], bootstrapping, "
-                                  "shared scalar chains", "tokens": args.tokens, "streams": 2 * per},
+                                  "shared scalar chains", "tokens": args.tokens, "streams": 2 * per,
+                      "cuda_graph": bool(args.graph)},
            "plain": res["plain"], "learned": res["learned"],
            "training": {str(t): {k: v for k, v in r.items() if k != "abc"} for t, r in report.items()},
            "clocks": clk.summary()}
@@ -825,7 +832,7 @@ def main():
     ap.add_argument("--tokens", type=int, default=32, help="cfg5: tokens decoded per stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
-                    help="cfg1/cfg2/cfg3: call cutmax directly instead of replaying its CUDA graph")
+                    help="call cutmax / nucleus_sample directly instead of replaying their CUDA graphs")
     ap.add_argument("--chains", default="tuned", choices=["tuned", "shared", "stream"],
                     help="cfg3: scalar chains packed across a batch's streams (general bootstraps), kept per "
                          "stream (constant bootstraps, one launch for the batch), or as the autotuner chose")

@@ -370,6 +370,9 @@ int he_cutmax_graph(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he
 int he_cutmax_graph_stats(he_ctx *ctx, uint64_t *captured, uint64_t *replayed, uint64_t *direct);
 /* Frees every captured graph and its arena block (waits for the context's stream). */
 int he_cutmax_graph_clear(he_ctx *ctx);
+/* on != 0: cutmax and nucleus_sample run their CutMax as he_cutmax_graph does
+ * (same results, bit for bit); 0 (the default): directly. */
+int he_ctx_set_graphs(he_ctx *ctx, int32_t on);
 /* Cut noise drawn by the server from encrypted uniforms (Alg. 3 with
  * Lemma 2 / Observation 1): out = G = U^(1/alpha) slot by slot, U in [0, 1]
  * encrypted by the client, by the degree-`degree` Chebyshev interpolant of

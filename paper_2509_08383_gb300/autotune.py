@@ -147,6 +147,8 @@ def tune_chains(g, batches, reps=2, warm=1, log=print, timer=time_decodes):
             ms, ok = timer(g, [batch], p, lambda i, z: check(z), reps, warm)
             row[mode] = {"ms": ms, "argmax_ok": ok}
             log(f"batch {name}, chains {mode}: {ms:.1f} ms, argmax {'ok' if ok else 'LOST'}")
+        if hasattr(g, "graph_clear"):
+            g.graph_clear()  # the batch's CUDA graphs give their memory back
         good = [m for m in row if row[m]["argmax_ok"]] or list(row)
         choice[name] = min(good, key=lambda m: row[m]["ms"])
         table[name] = row

@@ -516,7 +516,7 @@ int cutmax(he_ctx *cx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out)
     API_TRY
     own(cx, in);
     Plan pl = plan_from(plan);
-    Ct r = cutmax_ct(cx, in, pl);
+    Ct r = cx->use_graphs ? cutmax_graph(cx, in, pl) : cutmax_ct(cx, in, pl);
     launched(cx, "cutmax");
     *out = r.release();
     API_CATCH(cx)
@@ -538,6 +538,12 @@ int he_cutmax_graph_stats(he_ctx *cx, uint64_t *captured, uint64_t *replayed, ui
     if (captured) *captured = cx->graph_stats[0];
     if (replayed) *replayed = cx->graph_stats[1];
     if (direct) *direct = cx->graph_stats[2];
+    return HE_OK;
+}
+
+int he_ctx_set_graphs(he_ctx *cx, int32_t on) {
+    if (!cx) return HE_EINVAL;
+    cx->use_graphs = on != 0;
     return HE_OK;
 }
 
@@ -574,7 +580,7 @@ int nucleus_sample(he_ctx *cx, const he_ct *logits, double top_p, double q, cons
     Ct g;
     if (rand_kind == HE_RAND_UNIFORM) g = beta_noise(cx, rand_ct, alpha, HE_NUCLEUS_DEGREE);
     Ct x = op_add(cx, logits, g ? g.get() : rand_ct, false);
-    Ct r = cutmax_ct(cx, x.get(), pl);
+    Ct r = cx->use_graphs ? cutmax_graph(cx, x.get(), pl) : cutmax_ct(cx, x.get(), pl);
     launched(cx, "nucleus_sample");
     *out = r.release();
     API_CATCH(cx)

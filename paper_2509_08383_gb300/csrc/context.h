@@ -100,6 +100,7 @@ struct he_ctx {
     std::vector<std::shared_ptr<he::CutmaxGraph>> graphs;
     uint64_t gen = 0;
     bool capturing = false;                // a CUDA graph capture is under way
+    bool use_graphs = false;               // cutmax and nucleus_sample go through cutmax_graph
     uint64_t graph_stats[3] = {0, 0, 0};   // captured, replayed, run directly after a failed capture
 
     ~he_ctx();

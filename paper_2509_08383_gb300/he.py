@@ -114,6 +114,7 @@ def lib():
             "he_cutmax_graph": [VP, VP, C.POINTER(CPlan), PP],
             "he_cutmax_graph_stats": [VP, pu64, pu64, pu64],
             "he_cutmax_graph_clear": [VP],
+            "he_ctx_set_graphs": [VP, i32],
             "nucleus_sample": [VP, VP, dbl, dbl, VP, i32, C.POINTER(CPlan), PP],
             "he_beta_noise": [VP, VP, dbl, u32, PP],
         }
@@ -477,6 +478,10 @@ class Context:
 
     def graph_clear(self):
         self._chk(lib().he_cutmax_graph_clear(self.ptr))
+
+    def set_graphs(self, on):
+        """cutmax and nucleus_sample through CUDA graphs (on) or directly."""
+        self._chk(lib().he_ctx_set_graphs(self.ptr, int(bool(on))))
 
     def beta_noise(self, u_ct, alpha, degree=31):
         """G = U^(1/alpha) of encrypted uniforms (Chebyshev interpolant)."""

@@ -159,3 +159,26 @@ def test_graph_bootstrapped_bit_identical():
         dec = g.decrypt(z)
         assert np.abs(dec[:NV] - F.cutmax_circuit(x, pl)).max() < 1e-3
         assert int(np.argmax(dec[:NV])) == int(np.argmax(x))
+
+
+def test_context_switch_routes_cutmax_and_nucleus_through_graphs(leveled):
+    """he_ctx_set_graphs: cutmax and nucleus_sample (client-drawn noise) give
+    the direct calls' bits, through replayed graphs."""
+    g, pl = leveled
+    x = synth.logits_gaussian(60)
+    G = F.beta_noise(synth.uniforms(60, pl.n), F.beta_alpha(0.9))
+    ct = g.encrypt(P.pack(x, g.slots, pl.packing), g.delta, 60)
+    gb = g.encrypt(P.pack(G, g.slots, pl.packing), g.delta, 62)
+    d = [g.cutmax(ct, pl), g.nucleus_sample(ct, gb, pl, 0.9)]
+    c0 = g.graph_stats()
+    g.set_graphs(True)
+    try:
+        for _ in range(2):
+            r = [g.cutmax(ct, pl), g.nucleus_sample(ct, gb, pl, 0.9)]
+            for a, b in zip(r, d):
+                assert _same(a, b)
+    finally:
+        g.set_graphs(False)
+    c1 = g.graph_stats()
+    assert c1[1] - c0[1] >= 2      # the second round replays
+    assert int(np.argmax(g.decrypt(d[1], pl.n))) == int(np.argmax(x + G))
