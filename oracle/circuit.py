@@ -467,7 +467,8 @@ def refresh_schedule(he, ct, plan, out_level):
     below D' (h_refresh[t]), and bootstrap Y before the statistics although it
     has the levels they need (y_boot[t]); 4^T combinations for T <= 6, 2^T
     (h only) for 6 < T <= 16, none beyond.  The cheapest counts a general
-    bootstrap 2, a constant one 1 and a refresh of x 1000 (x reaches tens,
+    bootstrap 7, a constant one 3 (their cost ratio on the GPU the circuit
+    targets) and a refresh of x 3000 (x reaches tens,
     beyond what a refresh of a constant keeps accurate); ties go to fewer
     bootstraps, then to the first combination (t = 0 the least significant
     digit, bit 0 h_refresh, bit 1 y_boot)."""
@@ -490,7 +491,7 @@ def refresh_schedule(he, ct, plan, out_level):
         dry = _DryBoot(out_level)
         tally = {}
         _boot_circuit(HE(sim, he.delta, he.rotsum_log_radix), start, plan, dry, hr, yb, tally)
-        cost = 2 * dry.general + dry.const + 1000 * tally.get("x", 0)
+        cost = 7 * dry.general + 3 * dry.const + 3000 * tally.get("x", 0)
         key = (cost, dry.general + dry.const)
         if best_key is None or key < best_key:
             best, best_key = (hr, yb), key

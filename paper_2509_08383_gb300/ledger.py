@@ -171,7 +171,7 @@ def refresh_schedule(plan, qb, y_level, out, padded):
     """The library's refresh schedule of a bootstrapped plan with per-stream
     scalar chains: per iteration, (refresh h by a constant bootstrap when it
     sits below D', bootstrap Y early), the combination of least cost (general
-    bootstrap 2, constant 1; then fewer bootstraps; then the first) on the
+    bootstrap 7, constant 3; then fewer bootstraps; then the first) on the
     circuit's level bookkeeping (plans of more than 16 iterations: none)."""
     T = plan.T
     if T > 16:                            # no search: no optional refresh
@@ -224,7 +224,7 @@ def refresh_schedule(plan, qb, y_level, out, padded):
             Y, g = out, g + 1
         if Y < plan.d + 3:
             c += 1
-        key = (2 * g + c, g + c)
+        key = (7 * g + 3 * c, g + c)
         if best_key is None or key < best_key:
             best, best_key = combo, key
     hr, yb = [], []
