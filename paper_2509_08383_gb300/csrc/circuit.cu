@@ -36,15 +36,19 @@ const double *device_const(he_ctx *cx, const std::vector<double> &v) {
     for (auto it = r.first; it != r.second; ++it)
         if (it->second.host == v) return it->second.d;
     if (cx->capturing) throw Error{HE_EINVAL, "a constant vector first seen during a graph capture"};
-    if (cx->const_cache.size() >= 4096) {
+    if (cx->const_cache.size() >= 4096) {  // the encodings keyed by these vectors go too
         for (auto &e : cx->const_cache) cx->arena.release(e.second.d, e.second.host.size() * sizeof(double));
+        for (auto &e : cx->plain_cache) cx->arena.release(e.d, e.bytes);
         cx->const_cache.clear();
+        cx->const_ptrs.clear();
+        cx->plain_cache.clear();
         cx->gen++;
     }
     double *d = (double *)cx->arena.alloc(bytes);
     // a pageable source is staged before the call returns
     check_cuda(cudaMemcpyAsync(d, v.data(), bytes, cudaMemcpyHostToDevice, cx->stream), "constant vector");
     cx->const_cache.emplace(h, he_ctx::ConstVec{d, v});
+    cx->const_ptrs.insert(d);
     return d;
 }
 
@@ -95,6 +99,8 @@ struct HE {
     Ct mul_plain_rescale(const he_ct *ct, const double *d_vec, int n_slots, double target = -1, int n_pt = 1) {
         if (target < 0) target = delta;
         double E = (target * (double)q(ct->level)) / ct->scale;
+        if (const u64 *pt = encoded_plain(cx, d_vec, nullptr, n_slots, n_pt, E, ct->level))
+            return op_rescale(cx, op_mul_plain_ntt(cx, ct, pt, ct->scale * E, n_pt).get());
         Scratch sc{cx, {}};
         double *d_pt = n_pt == 1 ? cx->d_dbl + cx->N() : (double *)sc.get((size_t)n_pt * cx->N());
         for (int i = 0; i < n_pt; i++) encode_dev(cx, d_vec + (size_t)i * n_slots, nullptr, n_slots, E, d_pt + i * cx->N());
@@ -107,11 +113,15 @@ struct HE {
         std::vector<double> v(2 * (size_t)slots);
         for (int i = 0; i < slots; i++) v[i] = re, v[slots + i] = im;
         const double *d_v = device_const(cx, v);
+        if (const u64 *pt = encoded_plain(cx, d_v, d_v + slots, slots, 1, ct->scale, ct->level))
+            return op_add_plain_ntt(cx, ct, pt);
         double *d_pt = cx->d_dbl + cx->N();
         encode_dev(cx, d_v, d_v + slots, slots, ct->scale, d_pt);
         return op_add_plain(cx, ct, d_pt);
     }
     Ct add_plain_vec(const he_ct *ct, const double *d_vec, int n_slots, int n_pt = 1) {
+        if (const u64 *pt = encoded_plain(cx, d_vec, nullptr, n_slots, n_pt, ct->scale, ct->level))
+            return op_add_plain_ntt(cx, ct, pt, n_pt);
         Scratch sc{cx, {}};
         double *d_pt = n_pt == 1 ? cx->d_dbl + cx->N() : (double *)sc.get((size_t)n_pt * cx->N());
         for (int i = 0; i < n_pt; i++)
@@ -250,14 +260,23 @@ static StreamShape stream_shape(he_ctx *cx, const he_ct *in, const Plan &pl) {
     }
     return sh;
 }
-// per-stream sum of a batch (a copy when streams hold one ciphertext) and the
-// broadcast of a per-stream batch back to the streams' ciphertexts
-static Ct stream_sum(he_ctx *cx, const he_ct *a, int cps) {
-    return cps > 1 ? op_group(cx, a, cps, true) : op_copy(cx, a);
+// per-stream sum of a batch and the broadcast of a per-stream batch back to
+// the streams' ciphertexts.  With one ciphertext per stream both are the
+// identity: the view then points at the input itself (no copy), and an owned
+// ciphertext is passed through.
+struct CtView {
+    Ct own;
+    const he_ct *p;
+};
+static CtView stream_group_view(he_ctx *cx, const he_ct *a, int cps, bool sum) {
+    if (cps == 1) return {nullptr, a};
+    Ct g = op_group(cx, a, cps, sum);
+    const he_ct *p = g.get();
+    return {std::move(g), p};
 }
-static Ct stream_bcast(he_ctx *cx, const he_ct *a, int cps) {
-    return cps > 1 ? op_group(cx, a, cps, false) : op_copy(cx, a);
-}
+static CtView stream_sum(he_ctx *cx, const he_ct *a, int cps) { return stream_group_view(cx, a, cps, true); }
+static CtView stream_bcast(he_ctx *cx, const he_ct *a, int cps) { return stream_group_view(cx, a, cps, false); }
+static Ct stream_bcast(he_ctx *cx, Ct a, int cps) { return cps > 1 ? op_group(cx, a.get(), cps, false) : std::move(a); }
 // device copy of `vals` scaled by c (see device_const)
 static const double *upload_scaled(he_ctx *cx, Scratch &, const std::vector<double> &vals, double c) {
     std::vector<double> v(vals);
@@ -278,18 +297,17 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
     const double *d_mask = m ? upload_scaled(cx, sc, sh.mask, 1.0) : nullptr;
     Ct Y = op_copy(cx, in);
     for (int t = 0; t < pl.T; t++) {
-        Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
-        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).get(), true);
+        Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).p, sh.steps);
+        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).p, true);
         Ct E = he.mul_rescale(D.get(), D.get());
-        Ct V = he.rotsum(stream_sum(cx, E.get(), cps).get(), sh.steps);
+        Ct V = he.rotsum(stream_sum(cx, E.get(), cps).p, sh.steps);
         if (m) {
             Ct S2 = he.mul_rescale(S.get(), S.get());
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
         }
         Ct h = stream_bcast(cx,
-                            (pl.k[t] ? invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t])
-                                     : he.learned_half(he.mcr_bits(V.get(), pl.kappa[t], -1, 30).get(), &pl.lq[3 * t]))
-                                .get(),
+                            pl.k[t] ? invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t])
+                                    : he.learned_half(he.mcr_bits(V.get(), pl.kappa[t], -1, 30).get(), &pl.lq[3 * t]),
                             cps);
         double coef = 2.0 * std::sqrt(pl.kappa[t] * pl.n) / pl.c[t];
         // D' = D * coef (times the 0/1 slot mask when padded): the mask is a
@@ -303,8 +321,8 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
         u = m ? he.add_plain_vec(u.get(), d_mask, sh.slots, cps) : he.add_const(u.get(), 1.0);
         Y = he.power(u.get(), pl.p[t]);
     }
-    Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
-    Ct F = stream_bcast(cx, inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d).get(), cps);
+    Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).p, sh.steps);
+    Ct F = stream_bcast(cx, inverse_goldschmidt(he, S.get(), pl.kappa_f, pl.d), cps);
     return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());
 }
 
@@ -1068,10 +1086,10 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         const int p = pl.p[t], k = pl.k[t];
         const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
         if (Y->level < 5 || (!shared && rs.y_boot[t])) Y = bootstrap_ct(cx, Y.get());
-        Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
-        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).get(), true);
+        Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).p, sh.steps);
+        Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).p, true);
         Ct E = he.mul_rescale(D.get(), D.get());
-        Ct V = he.rotsum(stream_sum(cx, E.get(), cps).get(), sh.steps);
+        Ct V = he.rotsum(stream_sum(cx, E.get(), cps).p, sh.steps);
         if (m) {
             Ct S2 = he.mul_rescale(S.get(), S.get());
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
@@ -1146,7 +1164,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         if (!shared && ((rs.h_refresh[t] && h->level < Dp->level) || h->level < 1)) h = bootstrap_const(cx, h.get());
         h = ensure(std::move(h), 1);
         Dp = ensure(std::move(Dp), 1);
-        Ct u = he.mul_rescale(Dp.get(), stream_bcast(cx, h.get(), cps).get());
+        Ct u = he.mul_rescale(Dp.get(), stream_bcast(cx, h.get(), cps).p);
         if (m) {
             Scratch s3{cx, {}};
             u = he.add_plain_vec(u.get(), upload_scaled(cx, s3, sh.mask, rn), slots, cps);
@@ -1157,7 +1175,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         Y = he.power(u.get(), p);
     }
     Y = ensure(std::move(Y), shared ? 3 : 2);
-    Ct Ssum = he.rotsum(stream_sum(cx, Y.get(), cps).get(), sh.steps);
+    Ct Ssum = he.rotsum(stream_sum(cx, Y.get(), cps).p, sh.steps);
     if (!shared && Ssum->level < pl.d + 3) Ssum = bootstrap_const(cx, Ssum.get());  // the inverse's d + 2 levels
     Ct F;
     if (shared) {
@@ -1168,7 +1186,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     } else {
         F = inverse_goldschmidt(he, Ssum.get(), pl.kappa_f, pl.d);
     }
-    F = stream_bcast(cx, F.get(), cps);
+    F = stream_bcast(cx, std::move(F), cps);
     return he.mul_rescale(he.mcr(Y.get(), pl.kappa_f).get(), F.get());
 }
 

@@ -759,24 +759,65 @@ static Rows plain_rows(he_ctx *cx, Scratch &sc, const double *d_pt, int n_pt, in
     return shared_rows(all, n_pt);
 }
 
-Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt) {
+static Ct mul_plain_rows(he_ctx *cx, const he_ct *a, const Rows &pt, double scale_out) {
     int l = a->level;
     cx->ops_by_level[2][l] += (uint64_t)a->batch;
-    Scratch sc{cx, {}};
-    Rows pt = plain_rows(cx, sc, d_pt, n_pt, l);
     Ct out(ct_alloc(cx, l, scale_out, a->batch));
     for (int k = 0; k < 2; k++) ew_mul(ct_polys(out.get(), k), ct_polys(a, k), pt, a->batch * (l + 1), cx->log_n, cx->stream);
     return out;
 }
-
-Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt, int n_pt) {
+// c0 + pt into the output directly, c1 copied
+static Ct add_plain_rows(he_ctx *cx, const he_ct *a, const Rows &pt) {
     int l = a->level;
-    Scratch sc{cx, {}};
-    Rows pt = plain_rows(cx, sc, d_pt, n_pt, l);
-    Ct out = op_copy(cx, a);
-    Rows o = ct_polys(out.get(), 0);
-    ew_add(o, o, pt, a->batch * (l + 1), 0, cx->log_n, cx->stream);
+    Ct out(ct_alloc(cx, l, a->scale, a->batch));
+    ew_add(ct_polys(out.get(), 0), ct_polys(a, 0, l), pt, a->batch * (l + 1), 0, cx->log_n, cx->stream);
+    ew_copy(ct_polys(out.get(), 1), ct_polys(a, 1, l), a->batch * (l + 1), cx->log_n, cx->stream);
     return out;
+}
+static Rows ntt_plain_rows(he_ctx *cx, const u64 *pt, int n_pt, int l) {
+    return shared_rows(make_rows(const_cast<u64 *>(pt), (size_t)(l + 1) * cx->N(), l + 1, l + 1, cx->nq), n_pt);
+}
+
+Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt) {
+    Scratch sc{cx, {}};
+    return mul_plain_rows(cx, a, plain_rows(cx, sc, d_pt, n_pt, a->level), scale_out);
+}
+Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt, int n_pt) {
+    Scratch sc{cx, {}};
+    return add_plain_rows(cx, a, plain_rows(cx, sc, d_pt, n_pt, a->level));
+}
+Ct op_mul_plain_ntt(he_ctx *cx, const he_ct *a, const u64 *pt, double scale_out, int n_pt) {
+    return mul_plain_rows(cx, a, ntt_plain_rows(cx, pt, n_pt, a->level), scale_out);
+}
+Ct op_add_plain_ntt(he_ctx *cx, const he_ct *a, const u64 *pt, int n_pt) {
+    return add_plain_rows(cx, a, ntt_plain_rows(cx, pt, n_pt, a->level));
+}
+
+// Encoded plaintexts of the circuits' constant vectors, kept on the device
+// per (vector, encoding scale, level): the same masks and constants are
+// encoded at the same scales on every call.  Only vectors that device_const
+// holds qualify (their addresses stay theirs); nothing is added during a graph
+// capture (capture runs nothing, so the entry would stay unwritten).  Above
+// 512 entries the cache starts over, which retires the captured graphs.
+const u64 *encoded_plain(he_ctx *cx, const double *re, const double *im, int n_slots, int n_pt, double E, int l) {
+    for (const auto &e : cx->plain_cache)
+        if (e.re == re && e.im == im && e.n_slots == n_slots && e.n_pt == n_pt && e.E == E && e.level == l) return e.d;
+    if (cx->capturing || !cx->const_ptrs.count(re)) return nullptr;
+    if (cx->plain_cache.size() >= 512) {
+        for (auto &e : cx->plain_cache) cx->arena.release(e.d, e.bytes);
+        cx->plain_cache.clear();
+        cx->gen++;
+    }
+    const size_t N = cx->N(), bytes = (size_t)n_pt * (l + 1) * N * 8;
+    u64 *d = (u64 *)cx->arena.alloc(bytes);
+    double *tmp = cx->d_dbl + N;
+    for (int i = 0; i < n_pt; i++) {
+        encode_dev(cx, re + (size_t)i * n_slots, im ? im + (size_t)i * n_slots : nullptr, n_slots, E, tmp);
+        load_intd(make_rows(d + (size_t)i * (l + 1) * N, 0, l + 1, l + 1, cx->nq), l + 1, tmp, cx->log_n, cx->stream);
+    }
+    ntt_forward(make_rows(d, (l + 1) * N, l + 1, l + 1, cx->nq), n_pt * (l + 1), cx->tw, cx->log_n, cx->stream);
+    cx->plain_cache.push_back(he_ctx::PlainVec{re, im, n_slots, n_pt, l, E, d, bytes});
+    return d;
 }
 
 // ModUp of B members (member m's limbs 0..l at d_ntt + m*d_stride, NTT form)
@@ -936,9 +977,10 @@ Ct op_rotsum_stage(he_ctx *cx, const he_ct *a, const std::vector<i64> &rots) {
 }
 
 Ct op_rotsum(he_ctx *cx, const he_ct *a, int steps) {
-    Ct cur = op_copy(cx, a);
-    for (const auto &rots : rotsum_stages(steps, cx->rotsum_log_radix)) cur = op_rotsum_stage(cx, cur.get(), rots);
-    return cur;
+    Ct cur;
+    for (const auto &rots : rotsum_stages(steps, cx->rotsum_log_radix))
+        cur = op_rotsum_stage(cx, cur ? cur.get() : a, rots);
+    return cur ? std::move(cur) : op_copy(cx, a);
 }
 
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b) {

@@ -94,6 +94,16 @@ struct he_ctx {
     // keyed by content; they live as long as the context
     struct ConstVec { double *d; std::vector<double> host; };
     std::unordered_multimap<uint64_t, ConstVec> const_cache;
+    std::unordered_set<const double *> const_ptrs;  // the device vectors of const_cache
+    // their encodings (encoded_plain): vector, scale E, level -> NTT-form rows
+    struct PlainVec {
+        const double *re, *im;
+        int n_slots, n_pt, level;
+        double E;
+        u64 *d;
+        size_t bytes;
+    };
+    std::vector<PlainVec> plain_cache;
     // CutMax calls captured as CUDA graphs (graph.cu); `gen` changes whenever
     // something a graph holds by address may change (bootstrap tables,
     // rotate-and-sum radix), which retires every graph
@@ -156,6 +166,13 @@ Ct op_add_intd(he_ctx *cx, const he_ct *a, double K);
 // n_pt plaintexts (n_pt x N integer-valued doubles); member m uses plaintext m % n_pt
 Ct op_mul_plain(he_ctx *cx, const he_ct *a, const double *d_pt, double scale_out, int n_pt = 1);
 Ct op_add_plain(he_ctx *cx, const he_ct *a, const double *d_pt, int n_pt = 1);
+// the same with a plaintext already in NTT form on limbs 0..level of `a`
+// (n_pt of them back to back, member m takes m % n_pt)
+Ct op_mul_plain_ntt(he_ctx *cx, const he_ct *a, const u64 *pt, double scale_out, int n_pt = 1);
+Ct op_add_plain_ntt(he_ctx *cx, const he_ct *a, const u64 *pt, int n_pt = 1);
+// NTT-form plaintext of device_const slot vectors encoded at scale E on limbs
+// 0..l, cached per context; nullptr when it cannot be cached (see context.cu)
+const u64 *encoded_plain(he_ctx *cx, const double *re, const double *im, int n_slots, int n_pt, double E, int l);
 Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b);
 // product, relinearisation and rescale with one rounding: round((P d + acc) / (q_l P))
 Ct op_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b);
