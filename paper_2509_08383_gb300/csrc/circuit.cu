@@ -64,8 +64,7 @@ struct HE {
         if (target < 0) target = delta;
         double E = (target * (double)q(ct->level)) / ct->scale;
         double K = std::rint(c * E);
-        Ct t = op_mul_intd(cx, ct, K, ct->scale * E);
-        return op_rescale(cx, t.get());
+        return op_mul_intd_rescale(cx, ct, K, ct->scale * E);
     }
     // c * ct with the integer multiplier K = rint(c E) carrying at least
     // min_bits bits: a tiny c against a large scale (the range scale kappa of
@@ -80,8 +79,8 @@ struct HE {
             r++;
         }
         double K = std::rint(c * E);
-        Ct t = op_mul_intd(cx, ct, K, ct->scale * E);
-        for (int i = 0; i < r; i++) t = op_rescale(cx, t.get());
+        Ct t = op_mul_intd_rescale(cx, ct, K, ct->scale * E);
+        for (int i = 1; i < r; i++) t = op_rescale(cx, t.get());
         return t;
     }
     Ct add_const(const he_ct *ct, double c) { return op_add_intd(cx, ct, std::rint(c * ct->scale)); }

@@ -834,11 +834,16 @@ void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext, int B, size_t d_stride
     if (B == 1) d_stride = 0;
     Rows crow = make_rows(coef, (size_t)(l + 1) * N, l + 1, l + 1, cx->nq);
     ntt_inverse_from(crow, make_rows((u64 *)d_ntt, d_stride, l + 1, l + 1, cx->nq), B * (l + 1), cx->tw, log_n, s);
-    for (int j = 0; j < T.beta; j++) {
-        int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
-        Rows in = make_rows(coef + (size_t)lo * N, (size_t)(l + 1) * N, cnt, cnt, cx->nq, lo);
-        Rows o = desc_rows(ext, T.desc + T.digit_off[j], T.digit_nout[j], ext_w);
-        bconv(o, in, T.modup[j], B, log_n, s);
+    // every digit's conversion in one launch (at most BCONV_SET_MAX at a time)
+    for (int j0 = 0; j0 < T.beta; j0 += BCONV_SET_MAX) {
+        BConvSet set;
+        for (int j = j0; j < std::min(T.beta, j0 + BCONV_SET_MAX); j++, set.n++) {
+            int lo = T.digit_lo[j], cnt = T.digit_cnt[j];
+            set.in[set.n] = make_rows(coef + (size_t)lo * N, (size_t)(l + 1) * N, cnt, cnt, cx->nq, lo);
+            set.out[set.n] = desc_rows(ext, T.desc + T.digit_off[j], T.digit_nout[j], ext_w);
+            set.tab[set.n] = T.modup[j];
+        }
+        bconv_set(set, B, log_n, s);
     }
     ntt_forward(desc_rows(ext, T.desc, T.n_desc, ext_w), B * T.n_desc, cx->tw, log_n, s);
 }
@@ -848,7 +853,7 @@ void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext, int B, size_t d_stride
 // polynomials of n_ext rows each (Q limbs 0..l, then the special primes), for
 // B members (member m's acc at + m*2*n_ext*N).
 void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc, int B,
-              size_t d_stride) {
+              size_t d_stride, const u64 *lift, size_t lift_poly) {
     const LevelTabs &T = cx->lv[l];
     const size_t N = cx->N();
     cx->ks_by_level[l] += (uint64_t)B;
@@ -870,7 +875,15 @@ void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev 
     kp.d_stride = B == 1 ? 0 : d_stride;
     kp.ext_stride = (size_t)T.beta * T.n_ext * N;
     kp.acc_stride = (size_t)2 * T.n_ext * N;
-    keyswitch_inner(kp, cx->log_n, cx->stream);
+    if (lift) {
+        KeyLift lf;
+        lf.d = lift;
+        lf.poly_stride = lift_poly;
+        lf.pmod = cx->p_mod;
+        keyswitch_inner(kp, cx->log_n, cx->stream, &lf);
+    } else {
+        keyswitch_inner(kp, cx->log_n, cx->stream);
+    }
 }
 
 // ModDown of B two-polynomial QP accumulators (destroys their special-prime
@@ -1030,11 +1043,19 @@ Ct op_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b) {
     u64 *ext = B == 1 ? cx->ks_ext : sc.get((size_t)B * ks_ext_words(cx, l));
     u64 *acc = B == 1 ? cx->ks_acc : sc.get((size_t)B * ks_acc_words(cx, l));
     modup(cx, d2, l, ext, B, (size_t)(l + 1) * N);
-    ks_inner(cx, d2, ext, l, *rk, 0, acc, B, (size_t)(l + 1) * N);
+    // + P d_k on the Q rows of output polynomial k: inside the inner product
+    // for one member, as its own pass for a batch (where the extra registers
+    // would halve the batched kernel's occupancy)
     const size_t ts = ct_member_stride(t.get());
-    for (int k = 0; k < 2; k++)  // + P d_k on the Q rows
-        ew_qp_lift(acc + (size_t)k * ne * N, ct_poly(t.get(), k), l + 1, (int)ne, 0, 1, cx->p_mod, cx->slot, log_n, s,
-                   B, qp_w, ts);
+    if (B == 1) {
+        ks_inner(cx, d2, ext, l, *rk, 0, acc, B, (size_t)(l + 1) * N, ct_poly(t.get(), 0),
+                 (size_t)(ct_poly(t.get(), 1) - ct_poly(t.get(), 0)));
+    } else {
+        ks_inner(cx, d2, ext, l, *rk, 0, acc, B, (size_t)(l + 1) * N);
+        for (int k = 0; k < 2; k++)
+            ew_qp_lift(acc + (size_t)k * ne * N, ct_poly(t.get(), k), l + 1, (int)ne, 0, 1, cx->p_mod, cx->slot, log_n,
+                       s, B, qp_w, ts);
+    }
     // rows l .. l+K of each polynomial: q_l, then the special primes
     Rows div = make_rows(acc + (size_t)l * N, ne * N, K + 1, 1, cx->nq, l);
     ntt_inverse(div, 2 * B * (K + 1), cx->tw, log_n, s);
@@ -1048,7 +1069,8 @@ Ct op_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b) {
     return out;
 }
 
-Ct op_rescale(he_ctx *cx, const he_ct *a) {
+// rescale of K a (kmul: K mod q_i; null: K = 1) whose scale is `scale`
+static Ct rescale_times(he_ctx *cx, const he_ct *a, const ScalarTab *kmul, double scale) {
     int l = a->level;
     if (l < 1) throw Error{HE_ELEVEL, "cannot rescale a level-0 ciphertext"};
     cx->ops_by_level[0][l] += (uint64_t)a->batch;
@@ -1056,7 +1078,7 @@ Ct op_rescale(he_ctx *cx, const he_ct *a) {
     const int np2 = 2 * a->batch;
     cudaStream_t s = cx->stream;
     u64 ql = cx->primes[l];
-    Ct out(ct_alloc(cx, l - 1, a->scale / (double)ql, a->batch));
+    Ct out(ct_alloc(cx, l - 1, scale / (double)ql, a->batch));
     Scratch sc{cx, {}};
     u64 *lastb = a->batch == 1 ? cx->sc_a : sc.get((size_t)np2 * N);
     u64 *liftb = a->batch == 1 ? cx->sc_b : sc.get((size_t)np2 * l * N);
@@ -1065,10 +1087,15 @@ Ct op_rescale(he_ctx *cx, const he_ct *a) {
     Rows src = make_rows(ct_poly(a, 0) + (size_t)l * N, (size_t)a->cap * N, 1, 1, cx->nq, l);
     ntt_inverse_from(last, src, np2, cx->tw, cx->log_n, s);
     Rows lift = make_rows(liftb, (size_t)l * N, l, l, cx->nq);
-    rescale_lift(lift, lastb, np2, ql, l, cx->log_n, s);
+    rescale_lift(lift, lastb, np2, ql, l, cx->log_n, s, kmul);
     ntt_forward(lift, np2 * l, cx->tw, cx->log_n, s);
-    rescale_finish(ct_rows(out.get()), ct_rows(a, l - 1), lift, cx->lv[l].ql_inv, np2 * l, cx->log_n, s);
+    rescale_finish(ct_rows(out.get()), ct_rows(a, l - 1), lift, cx->lv[l].ql_inv, np2 * l, cx->log_n, s, kmul);
     return out;
+}
+Ct op_rescale(he_ctx *cx, const he_ct *a) { return rescale_times(cx, a, nullptr, a->scale); }
+Ct op_mul_intd_rescale(he_ctx *cx, const he_ct *a, double K, double scale_mid) {
+    const ScalarTab k = scalar_intd(cx, K, a->level + 1);
+    return rescale_times(cx, a, &k, scale_mid);
 }
 
 Ct op_drop(he_ctx *cx, const he_ct *a, int level) {

@@ -177,6 +177,10 @@ Ct op_mul(he_ctx *cx, const he_ct *a, const he_ct *b);
 // product, relinearisation and rescale with one rounding: round((P d + acc) / (q_l P))
 Ct op_mul_rescale(he_ctx *cx, const he_ct *a, const he_ct *b);
 Ct op_rescale(he_ctx *cx, const he_ct *a);
+// rescale(K a) in one pass: the product by the integer K (rint of a double,
+// any size) folded into the rescale's lift and finish; scale_mid = a's scale
+// times K's encoding scale
+Ct op_mul_intd_rescale(he_ctx *cx, const he_ct *a, double K, double scale_mid);
 Ct op_drop(he_ctx *cx, const he_ct *a, int level);
 Ct op_automorph(he_ctx *cx, const he_ct *a, u64 g);
 Ct op_mod_raise(he_ctx *cx, const he_ct *a, int level);
@@ -198,8 +202,10 @@ void keyswitch(he_ctx *cx, const u64 *d_ntt, int l, const KeyDev &key, const Row
 size_t ks_ext_words(he_ctx *cx, int l);
 size_t ks_acc_words(he_ctx *cx, int l);
 void modup(he_ctx *cx, const u64 *d_ntt, int l, u64 *ext, int B = 1, size_t d_stride = 0);
+// (lift, one member only: + P * d_k on the Q rows of output polynomial k, d_k
+// at lift + k lift_poly)
 void ks_inner(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois, u64 *acc,
-              int B = 1, size_t d_stride = 0);
+              int B = 1, size_t d_stride = 0, const u64 *lift = nullptr, size_t lift_poly = 0);
 void moddown(he_ctx *cx, u64 *acc, int l, const Rows &out, const Rows &add, int add_mask, int B = 1);
 void keyswitch_ext(he_ctx *cx, const u64 *d_ntt, const u64 *ext, int l, const KeyDev &key, u64 galois,
                    const Rows &out, const Rows &add, int add_mask, int B = 1, size_t d_stride = 0);

@@ -857,8 +857,11 @@ __device__ __noinline__ u32 bconv_above_half(const u64 *const *s_in, const int *
         if (m[i] != tab.mr_half[i]) return m[i] > tab.mr_half[i] ? 1u : 0u;
     return 0u;  // x = (Q-1)/2 itself rounds down
 }
+// One block of a conversion: 128 coefficients of polynomial by / n_chunks,
+// output chunk by % n_chunks.
 template <bool RND>
-__global__ void __launch_bounds__(128, 4) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
+__device__ __forceinline__ void bconv_block(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys,
+                                            int log_n, int by) {
     __shared__ u64 s_w[BCONV_MAX_IN * BCONV_CHUNK];
     __shared__ u64 s_qi[BCONV_MAX_IN], s_qis[BCONV_MAX_IN], s_q[BCONV_MAX_IN];
     __shared__ const u64 *s_in[BCONV_MAX_IN];
@@ -871,7 +874,7 @@ __global__ void __launch_bounds__(128, 4) k_bconv(Rows out, Rows in, BConvTab ta
     const PrimeConsts &pc = c_pcs[out.slot];
     const size_t n = (size_t)1 << log_n;
     const int n_chunks = (tab.n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
-    const int chunk = blockIdx.y % n_chunks, poly = blockIdx.y / n_chunks;
+    const int chunk = by % n_chunks, poly = by / n_chunks;
     const int t0 = chunk * BCONV_CHUNK, nt = min(BCONV_CHUNK, tab.n_out - t0);
     for (int i = threadIdx.x; i < BCONV_MAX_IN * BCONV_CHUNK; i += blockDim.x) {
         const int a = i / BCONV_CHUNK, c = i % BCONV_CHUNK;
@@ -939,6 +942,35 @@ __global__ void __launch_bounds__(128, 4) k_bconv(Rows out, Rows in, BConvTab ta
         }
     }
 }
+template <bool RND>
+__global__ void __launch_bounds__(128, 4) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
+    bconv_block<RND>(out, in, tab, n_polys, log_n, blockIdx.y);
+}
+// several conversions of one shape in one launch (blockIdx.z selects one):
+// the digits of a ModUp
+__global__ void __launch_bounds__(128, 7) k_bconv_set(BConvSet set, int n_polys, int log_n) {
+    const int j = blockIdx.z;
+    const int n_chunks = (set.tab[j].n_out + BCONV_CHUNK - 1) / BCONV_CHUNK;
+    if ((int)blockIdx.y >= n_chunks * n_polys) return;  // this conversion has fewer output chunks
+    bconv_block<false>(set.out[j], set.in[j], set.tab[j], n_polys, log_n, blockIdx.y);
+}
+void bconv_set(const BConvSet &set, int n_polys, int log_n, cudaStream_t s) {
+    if (set.n < 1 || set.n > BCONV_SET_MAX) throw Error{HE_EINVAL, "basis conversion set: 1..8 conversions"};
+    int max_chunks = 0;
+    double bytes = 0;
+    for (int j = 0; j < set.n; j++) {
+        if (set.tab[j].n_in > BCONV_MAX_IN || set.tab[j].inv_fix)
+            throw Error{HE_EINVAL, "basis conversion set: more than 16 primes or a rounding table"};
+        max_chunks = std::max(max_chunks, (set.tab[j].n_out + BCONV_CHUNK - 1) / BCONV_CHUNK);
+        bytes += 8.0 * (set.tab[j].n_in + set.tab[j].n_out) * (double)n_polys * (double)(1 << log_n);
+    }
+    const size_t n = (size_t)1 << log_n;
+    dim3 grid((unsigned)((n + 127) / 128), (unsigned)(max_chunks * n_polys), (unsigned)set.n);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    prof_begin(PROF_BCONV, s);
+    k_bconv_set<<<grid, 128, 0, s>>>(set, n_polys, log_n);
+    prof_end(PROF_BCONV, s, bytes);
+}
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s) {
     if (tab.n_in > BCONV_MAX_IN) throw Error{HE_EINVAL, "basis conversion from more than 16 primes"};
     const size_t n = (size_t)1 << log_n;
@@ -953,8 +985,8 @@ void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, in
 
 // Batch members are processed KS_MB at a time per thread, so that every key
 // word loaded serves KS_MB members from registers (KS_MB = 1 for one member).
-template <int KS_MB>
-__global__ void __launch_bounds__(EW_T) k_keyswitch_inner(KeyIP kp, int log_n) {
+template <int KS_MB, bool LIFT>
+__global__ void __launch_bounds__(EW_T) k_keyswitch_inner(KeyIP kp, int log_n, KeyLift lf) {
     const PrimeConsts &pc = c_pcs[kp.slot];
     const int t = blockIdx.y, b0 = blockIdx.z * KS_MB, nb = min(KS_MB, kp.batch - b0);
     const int p = t < kp.l1 ? t : kp.nq + (t - kp.l1);
@@ -1002,29 +1034,52 @@ __global__ void __launch_bounds__(EW_T) k_keyswitch_inner(KeyIP kp, int log_n) {
         for (int m = 0; m < KS_MB; m++) {
             if (m >= nb) break;
             u64 *acc_m = kp.acc + (size_t)(b0 + m) * kp.acc_stride;
-            st2(acc_m + row + k, mont_reduce(acc[m][0], acc[m][1], q, qn), mont_reduce(acc[m][2], acc[m][3], q, qn));
-            st2(acc_m + (((size_t)kp.n_rows + t) << log_n) + k, mont_reduce(acc[m][4], acc[m][5], q, qn),
-                mont_reduce(acc[m][6], acc[m][7], q, qn));
+            if constexpr (!LIFT) {
+                st2(acc_m + row + k, mont_reduce(acc[m][0], acc[m][1], q, qn), mont_reduce(acc[m][2], acc[m][3], q, qn));
+                st2(acc_m + (((size_t)kp.n_rows + t) << log_n) + k, mont_reduce(acc[m][4], acc[m][5], q, qn),
+                    mont_reduce(acc[m][6], acc[m][7], q, qn));
+            } else {
+                u64 r0 = mont_reduce(acc[m][0], acc[m][1], q, qn), r1 = mont_reduce(acc[m][2], acc[m][3], q, qn);
+                u64 r2 = mont_reduce(acc[m][4], acc[m][5], q, qn), r3 = mont_reduce(acc[m][6], acc[m][7], q, qn);
+                if (t < kp.l1) {  // + P d_k (P = 0 mod the special primes)
+                    const u64 w = lf.pmod.v[p], ws = lf.pmod.s[p];
+                    const u64 *dk = lf.d + row;
+                    const ulonglong2 u0 = ld2(dk + k), u1 = ld2(dk + lf.poly_stride + k);
+                    r0 = add_mod(r0, shoup_mul(u0.x, w, ws, q), q);
+                    r1 = add_mod(r1, shoup_mul(u0.y, w, ws, q), q);
+                    r2 = add_mod(r2, shoup_mul(u1.x, w, ws, q), q);
+                    r3 = add_mod(r3, shoup_mul(u1.y, w, ws, q), q);
+                }
+                st2(acc_m + row + k, r0, r1);
+                st2(acc_m + (((size_t)kp.n_rows + t) << log_n) + k, r2, r3);
+            }
         }
     }
 }
-void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s) {
+void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s, const KeyLift *lift) {
     need16(k.d_ntt);
     need16(k.ext);
     need16(k.key);
     need16(k.acc);
+    if (lift) {
+        need16(lift->d);
+        if ((lift->poly_stride & 1) || k.batch != 1) throw Error{HE_EINVAL, "key inner product: bad lift"};
+    }
     if (k.batch < 1 || (k.batch > 1 && ((k.d_stride | k.ext_stride | k.acc_stride) & 1)))
         throw Error{HE_EINVAL, "key inner product: bad batch layout"};
     constexpr int MB = 4;
     dim3 grid = ew_grid(k.n_rows, log_n);
     grid.z = (unsigned)(k.batch == 1 ? 1 : (k.batch + MB - 1) / MB);
     prof_begin(PROF_KS_INNER, s);
-    if (k.batch == 1) k_keyswitch_inner<1><<<grid, EW_T, 0, s>>>(k, log_n);
-    else k_keyswitch_inner<MB><<<grid, EW_T, 0, s>>>(k, log_n);
+    static const KeyLift none{};
+    if (lift) k_keyswitch_inner<1, true><<<grid, EW_T, 0, s>>>(k, log_n, *lift);
+    else if (k.batch == 1) k_keyswitch_inner<1, false><<<grid, EW_T, 0, s>>>(k, log_n, none);
+    else k_keyswitch_inner<MB, false><<<grid, EW_T, 0, s>>>(k, log_n, none);
     // algorithmic bytes: the beta key digits (b and a) once, then per member the
-    // beta input digits and the two outputs
+    // beta input digits and the two outputs (and the two lifted polynomials)
     prof_end(PROF_KS_INNER, s,
-             8.0 * (2.0 * k.beta + (k.beta + 2.0) * k.batch) * (double)k.n_rows * (double)(1 << log_n));
+             8.0 * (double)(1 << log_n) *
+                 ((2.0 * k.beta + (k.beta + 2.0) * k.batch) * (double)k.n_rows + (lift ? 2.0 * k.l1 : 0.0)));
 }
 
 // Hoisted rotate-and-sum stage (see KeyIPMulti): for each key r the beta
@@ -1158,7 +1213,12 @@ __device__ __forceinline__ u64 centred_mod(u64 v, u64 q_src, u64 q_src_mod_m, co
     if (v > (q_src - 1) / 2) vm = sub_mod(vm, q_src_mod_m, m.q);
     return vm;
 }
-__global__ void __launch_bounds__(EW_T) k_rescale_lift(Rows lift, const u64 *last, u64 ql, int l, int log_n) {
+// MUL: the rescaled ciphertext is K a (K mod q_l in kl, its Shoup companion
+// kls): the last limb's coefficients are multiplied by K before the lift
+// (the INTT is linear, so K INTT(a_l) = INTT(K a_l) mod q_l)
+template <bool MUL>
+__global__ void __launch_bounds__(EW_T) k_rescale_lift(Rows lift, const u64 *last, u64 ql, int l, u64 kl, u64 kls,
+                                                       int log_n) {
     const int r = blockIdx.y;  // polynomial r / l, target prime r % l
     const int poly = r / l, i = r % l;
     const ModQ m = c_pcs[lift.slot].m[i];
@@ -1166,31 +1226,51 @@ __global__ void __launch_bounds__(EW_T) k_rescale_lift(Rows lift, const u64 *las
     const u64 *src = last + ((size_t)poly << log_n);
     u64 *o = lift.row(r, log_n);
     EW_PAIRS_FOR(k, log_n) {
-        const ulonglong2 v = ld2(src + k);
+        ulonglong2 v = ld2(src + k);
+        if (MUL) {
+            v.x = shoup_mul(v.x, kl, kls, ql);
+            v.y = shoup_mul(v.y, kl, kls, ql);
+        }
         st2(o + k, centred_mod(v.x, ql, qlm, m), centred_mod(v.y, ql, qlm, m));
     }
 }
-void rescale_lift(const Rows &lift, const u64 *last, int n_polys, u64 ql, int l, int log_n, cudaStream_t s) {
+void rescale_lift(const Rows &lift, const u64 *last, int n_polys, u64 ql, int l, int log_n, cudaStream_t s,
+                  const ScalarTab *kmul) {
     need16(lift);
     need16(last);
-    k_rescale_lift<<<ew_grid(n_polys * l, log_n), EW_T, 0, s>>>(lift, last, ql, l, log_n);
+    if (kmul)
+        k_rescale_lift<true><<<ew_grid(n_polys * l, log_n), EW_T, 0, s>>>(lift, last, ql, l, kmul->v[l], kmul->s[l],
+                                                                          log_n);
+    else
+        k_rescale_lift<false><<<ew_grid(n_polys * l, log_n), EW_T, 0, s>>>(lift, last, ql, l, 0, 0, log_n);
 }
-__global__ void __launch_bounds__(EW_T) k_rescale_finish(Rows out, Rows in, Rows lift, ScalarTab qlinv, int log_n) {
+// out = (K a - lift) q_l^-1 (MUL; else K = 1)
+template <bool MUL>
+__global__ void __launch_bounds__(EW_T) k_rescale_finish(Rows out, Rows in, Rows lift, ScalarTab qlinv, ScalarTab kmul,
+                                                         int log_n) {
     const int r = blockIdx.y, p = out.prime(r);
     const u64 q = c_pcs[out.slot].m[p].q, w = qlinv.v[p], ws = qlinv.s[p];
     u64 *o = out.row(r, log_n);
     const u64 *x = in.row(r, log_n), *y = lift.row(r, log_n);
     EW_PAIRS_FOR(k, log_n) {
-        const ulonglong2 a = ld2(x + k), b = ld2(y + k);
+        ulonglong2 a = ld2(x + k);
+        const ulonglong2 b = ld2(y + k);
+        if (MUL) {
+            a.x = shoup_mul(a.x, kmul.v[p], kmul.s[p], q);
+            a.y = shoup_mul(a.y, kmul.v[p], kmul.s[p], q);
+        }
         st2(o + k, shoup_mul(sub_mod(a.x, b.x, q), w, ws, q), shoup_mul(sub_mod(a.y, b.y, q), w, ws, q));
     }
 }
 void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const ScalarTab &qlinv, int n_rows,
-                    int log_n, cudaStream_t s) {
+                    int log_n, cudaStream_t s, const ScalarTab *kmul) {
     need16(out);
     need16(in);
     need16(lift);
-    k_rescale_finish<<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, in, lift, qlinv, log_n);
+    if (kmul)
+        k_rescale_finish<true><<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, in, lift, qlinv, *kmul, log_n);
+    else
+        k_rescale_finish<false><<<ew_grid(n_rows, log_n), EW_T, 0, s>>>(out, in, lift, qlinv, qlinv, log_n);
 }
 __global__ void __launch_bounds__(EW_T) k_modraise_lift(Rows out, const u64 *src0, u64 q0, int log_n) {
     const int r = blockIdx.y;

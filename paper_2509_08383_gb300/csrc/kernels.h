@@ -105,6 +105,15 @@ void ew_automorph_ntt(const Rows &out, const Rows &a, int n_rows, u64 g, int log
 // Key-switch pieces
 // out row (poly*n_out + t) = sum_a [in_a * qhinv_a] * qhat[a][t], in row (poly*n_in + a)
 void bconv(const Rows &out, const Rows &in, const BConvTab &tab, int n_polys, int log_n, cudaStream_t s);
+// up to BCONV_SET_MAX conversions without rounding in one launch (out[j] <- in[j]
+// by tab[j], n_polys polynomials each)
+constexpr int BCONV_SET_MAX = 8;
+struct BConvSet {
+    Rows out[BCONV_SET_MAX], in[BCONV_SET_MAX];
+    BConvTab tab[BCONV_SET_MAX];
+    int n = 0;
+};
+void bconv_set(const BConvSet &set, int n_polys, int log_n, cudaStream_t s);
 // acc0/acc1 rows t < n_rows: sum_j x_j[t] * key_j[t], x_j = (t in digit j) ? d[t] : ext_j[t],
 // for `batch` members (member m's d, ext and acc at + m * the stride)
 struct KeyIP {
@@ -118,7 +127,14 @@ struct KeyIP {
     int batch = 1;
     size_t d_stride = 0, ext_stride = 0, acc_stride = 0;
 };
-void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s);
+// + P * d_k on the Q rows (t < l1) of output polynomial k of one member: the
+// addend rows d_k at d + k * poly_stride, P mod q_i in pmod
+struct KeyLift {
+    const u64 *d = nullptr;
+    size_t poly_stride = 0;
+    ScalarTab pmod;
+};
+void keyswitch_inner(const KeyIP &k, int log_n, cudaStream_t s, const KeyLift *lift = nullptr);
 // Hoisted rotate-and-sum stage: the sum over n_keys rotations r of the key
 // inner products of sigma_r(ext) (one shared ModUp of c1, read through
 // X -> X^gal[r] in NTT form), plus P * (c0 + sum_r sigma_r(c0)) on the Q rows,
@@ -147,9 +163,11 @@ void moddown_finish(const Rows &out, const Rows &acc, const Rows &conv, const Sc
 // rescale: from coefficient-form last limbs (n_polys rows at last + poly*N,
 // prime ql) write the centred lift into rows of `lift` (n_polys*l targets,
 // row r: polynomial r / l, prime r % l)
-void rescale_lift(const Rows &lift, const u64 *last, int n_polys, u64 ql, int l, int log_n, cudaStream_t s);
+// (kmul: rescale K a instead of a, K mod q_i in kmul, limbs 0..l)
+void rescale_lift(const Rows &lift, const u64 *last, int n_polys, u64 ql, int l, int log_n, cudaStream_t s,
+                  const ScalarTab *kmul = nullptr);
 void rescale_finish(const Rows &out, const Rows &in, const Rows &lift, const ScalarTab &qlinv, int n_rows,
-                    int log_n, cudaStream_t s);
+                    int log_n, cudaStream_t s, const ScalarTab *kmul = nullptr);
 // mod-raise: from coefficient-form level-0 limbs (prime q0; polynomial p's at
 // src + p*N) write the centred lift into the rows of out (coefficient form)
 void modraise_lift(const Rows &out, const u64 *src, u64 q0, int n_rows, int log_n, cudaStream_t s);
