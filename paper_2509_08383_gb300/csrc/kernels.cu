@@ -942,8 +942,8 @@ __device__ __forceinline__ void bconv_block(const Rows &out, const Rows &in, con
         }
     }
 }
-template <bool RND>
 // the rounding variant at seven blocks per SM (72 registers instead of 88)
+template <bool RND>
 __global__ void __launch_bounds__(128, RND ? 7 : 4) k_bconv(Rows out, Rows in, BConvTab tab, int n_polys, int log_n) {
     bconv_block<RND>(out, in, tab, n_polys, log_n, blockIdx.y);
 }
