@@ -363,7 +363,8 @@ int cutmax(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out
  * launch count advance as for a direct call.  Where a call cannot be captured
  * (or while a kernel class is being profiled) it runs directly.  Calls on one
  * context must not overlap (the graph's buffers are shared); graphs that hold
- * bootstrap tables or rotation choices that have since changed are retired. */
+ * bootstrap tables or rotation choices that have since changed are retired,
+ * and a context keeps at most 16 graphs (the least recently used one goes). */
 int he_cutmax_graph(he_ctx *ctx, const he_ct *in, const he_cutmax_plan *plan, he_ct **out);
 /* Calls of he_cutmax_graph so far: graphs captured, graph launches, direct
  * runs after a capture that failed or under profiling (any pointer may be NULL). */

@@ -112,6 +112,7 @@ struct he_ctx {
     bool capturing = false;                // a CUDA graph capture is under way
     bool use_graphs = false;               // cutmax and nucleus_sample go through cutmax_graph
     uint64_t graph_stats[3] = {0, 0, 0};   // captured, replayed, run directly after a failed capture
+    uint64_t graph_calls = 0;              // calls of cutmax_graph (the graphs' use clock)
 
     ~he_ctx();
     size_t N() const { return (size_t)n; }

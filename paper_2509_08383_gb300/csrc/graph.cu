@@ -31,7 +31,11 @@ struct CutmaxGraph {
     uint64_t ks[HE_MAX_PRIMES] = {0}, ops[4][HE_MAX_PRIMES] = {{0}}, boots = 0;
     unsigned long long launches = 0;
     bool failed = false;
+    uint64_t last_use = 0;  // call counter at the graph's last launch (least recently used goes first)
 };
+
+// graphs a context keeps at once (each holds its own arena block)
+constexpr size_t GRAPHS_MAX = 16;
 
 static std::vector<double> graph_key(he_ctx *cx, const he_ct *in, const Plan &pl) {
     std::vector<double> k = {(double)pl.n,         (double)pl.packing, (double)pl.T,      (double)pl.d,
@@ -166,9 +170,11 @@ Ct cutmax_graph(he_ctx *cx, const he_ct *in, const Plan &pl) {
             i++;
         }
     const std::vector<double> key = graph_key(cx, in, pl);
+    const uint64_t now = ++cx->graph_calls;
     for (auto &gp : cx->graphs) {
         CutmaxGraph &g = *gp;
         if (g.key != key) continue;
+        g.last_use = now;
         if (g.failed) {
             cx->graph_stats[2]++;
             return cutmax_ct(cx, in, pl);
@@ -186,6 +192,16 @@ Ct cutmax_graph(he_ctx *cx, const he_ct *in, const Plan &pl) {
         cx->graph_stats[1]++;
         return out;
     }
+    // a new key: the least recently used graph gives way when the context holds
+    // GRAPHS_MAX of them
+    if (cx->graphs.size() >= GRAPHS_MAX) {
+        size_t lru = 0;
+        for (size_t i = 1; i < cx->graphs.size(); i++)
+            if (cx->graphs[i]->last_use < cx->graphs[lru]->last_use) lru = i;
+        cudaStreamSynchronize(cx->stream);  // no launch of it may still read its block
+        graph_free(cx, *cx->graphs[lru]);
+        cx->graphs.erase(cx->graphs.begin() + (long)lru);
+    }
     // first call with this key: run directly, measuring the memory it takes,
     // then capture the graph for the calls after it
     const size_t base = cx->arena.in_use, peak0 = cx->arena.peak;
@@ -196,6 +212,7 @@ Ct cutmax_graph(he_ctx *cx, const he_ct *in, const Plan &pl) {
     auto g = std::make_shared<CutmaxGraph>();
     g->key = key;
     g->gen = cx->gen;
+    g->last_use = now;
     if (capture(cx, in, pl, need, *g)) {
         cx->graph_stats[0]++;
     } else {

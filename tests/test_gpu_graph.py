@@ -182,3 +182,25 @@ def test_context_switch_routes_cutmax_and_nucleus_through_graphs(leveled):
     c1 = g.graph_stats()
     assert c1[1] - c0[1] >= 2      # the second round replays
     assert int(np.argmax(g.decrypt(d[1], pl.n))) == int(np.argmax(x + G))
+
+
+def test_graph_count_is_bounded_least_recently_used_first(leveled):
+    """A context keeps at most 16 graphs: after 17 plans the first one's graph
+    is gone (using it again captures anew), the most recent ones replay, and
+    every output still equals the direct call's bits."""
+    g, pl = leveled
+    g.graph_clear()
+    ct = g.encrypt(P.pack(synth.logits_gaussian(70), g.slots, pl.packing), g.delta, 70)
+    plans = [P.CutMaxPlan(**{**pl.to_dict(), "c": [5.0 + 0.25 * i, 5.0]}) for i in range(17)]
+    for p in plans:
+        g.cutmax_prepare(p)
+    c0 = g.graph_stats()
+    for p in plans:                                   # 17 captures; the 17th evicts plans[0]
+        g.cutmax_graph(ct, p)
+    c1 = g.graph_stats()
+    assert c1[0] - c0[0] == 17
+    z = g.cutmax_graph(ct, plans[16])                 # still held: a replay
+    assert g.graph_stats()[1] - c1[1] == 1 and _same(z, g.cutmax(ct, plans[16]))
+    z = g.cutmax_graph(ct, plans[0])                  # evicted: captured again
+    assert g.graph_stats()[0] - c1[0] == 1 and _same(z, g.cutmax(ct, plans[0]))
+    g.graph_clear()
