@@ -1034,6 +1034,80 @@ static RefreshSched refresh_schedule(he_ctx *cx, const Plan &pl, int y_level, in
     return rs;
 }
 
+// Refresh schedule of the bootstrapped circuit with scalar chains shared by the
+// batch's streams.  A refresh of a vector (Y, D', u) bootstraps every one of
+// the batch's `members` ciphertexts, one of a per-stream scalar (x before
+// packing, h after unpacking) one ciphertext per stream, one of the packed
+// chain a single ciphertext.  Per iteration two choices
+// are open: refresh the packed h before unpacking it when it would arrive
+// below D' (u then keeps D's levels for the power), and bootstrap Y before the
+// statistics although it has the levels they need.  Every combination is
+// played on the shared circuit's level bookkeeping and the one that
+// bootstraps fewest ciphertexts is kept (then the first).
+static RefreshSched refresh_schedule_shared(he_ctx *cx, const Plan &pl, int y_level, int out, bool padded,
+                                            int members, int streams) {
+    auto bits = [&](int l) { return (double)std::lround(std::log2((double)cx->primes[l])); };
+    auto mcr_bits_level = [&](int a, double c) {
+        int r = 1;
+        double e = bits(a);
+        while (std::fabs(c) * std::exp2(e) < std::exp2(30.0) && r < 3 && a - r >= 1) e += bits(a - r), r++;
+        return a - r;
+    };
+    const int T = pl.T, per = T <= 6 ? 4 : 2;
+    if (T > 16) return RefreshSched{std::vector<uint8_t>(T, 0), std::vector<uint8_t>(T, 0)};
+    long total = 1;
+    for (int t = 0; t < T; t++) total *= per;
+    long best = -1, best_cost = 1L << 40;
+    for (long combo = 0; combo < total; combo++) {
+        long cc = combo, cost = 0;
+        int Y = y_level;
+        for (int t = 0; t < T; t++) {
+            const int ch = (int)(cc % per);
+            cc /= per;
+            const bool hr = ch & 1, yb = ch & 2;
+            const int k = pl.k[t], lp = power_depth(pl.p[t]);
+            if (Y < 5 || yb) Y = out, cost += members;
+            int x = mcr_bits_level(Y - 1, pl.kappa[t]);
+            if (x < 1) x = out, cost += streams;
+            x -= 1;                                   // pack: the class mask
+            if (x < 2) x = out, cost += 1;
+            int h;
+            if (k == 0) {
+                h = x - 2;
+            } else {
+                int P = x - 2;                        // start: constant products, then P a
+                for (int i = 2; i <= k; i++) {
+                    if (P < 2) P = out - 1, cost += 1;
+                    P -= 2;
+                }
+                if (P < 1) P = out, cost += 1;
+                h = P - 1;                            // h's half of the pair
+            }
+            const int Dp = Y - (padded ? 2 : 1);
+            if (hr && h - 1 < Dp) h = out, cost += 1;  // refresh the packed h
+            if (h < 1) h = out, cost += 1;
+            h -= 1;                                   // unpack: the class mask
+            if (h < 1) h = out, cost += streams;
+            int d = Dp;
+            if (d < 1) d = out, cost += members;
+            int u = std::min(d, h) - 1;
+            if (u < lp) u = out, cost += members;
+            Y = u - lp;
+        }
+        if (Y < 3) Y = out, cost += members;
+        if (Y - 1 < pl.d + 3) cost += 1;              // the packed final sum before the inverse
+        if (cost < best_cost) best = combo, best_cost = cost;
+    }
+    RefreshSched rs{std::vector<uint8_t>(T, 0), std::vector<uint8_t>(T, 0)};
+    for (int t = 0; t < T; t++) {
+        const int ch = (int)(best % per);
+        best /= per;
+        rs.h_refresh[t] = ch & 1;
+        rs.y_boot[t] = (ch & 2) ? 1 : 0;
+    }
+    return rs;
+}
+
 // Alg. 2 with bootstrapping when levels run out (same steps as cutmax_ct;
 // the Goldschmidt input is x = kappa V and Y_(t+1) is scaled by norm[t]
 // through u' = norm^(1/p) u, so that every refreshed ciphertext is bounded).
@@ -1058,7 +1132,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     // log2(Sp)-step rotate-and-sum
     const int n_streams = sh.S;
     const bool shared = pl.shared && n_streams > 1;
-    const RefreshSched rs = shared ? RefreshSched{std::vector<uint8_t>(pl.T, 0), std::vector<uint8_t>(pl.T, 0)}
+    const RefreshSched rs = shared ? refresh_schedule_shared(cx, pl, Y->level, out_level, m != 0, in->batch, sh.S)
                                    : refresh_schedule(cx, pl, Y->level, out_level, m != 0);
     int Sp = 1, lsp = 0;
     while (Sp < n_streams) Sp *= 2, lsp++;
@@ -1084,7 +1158,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
     for (int t = 0; t < pl.T; t++) {
         const int p = pl.p[t], k = pl.k[t];
         const double kap = pl.kappa[t], y0 = pl.y0[t], rn = std::pow(pl.norm[t], 1.0 / p);
-        if (Y->level < 5 || (!shared && rs.y_boot[t])) Y = bootstrap_ct(cx, Y.get());
+        if (Y->level < 5 || rs.y_boot[t]) Y = bootstrap_ct(cx, Y.get());
         Ct S = he.rotsum(stream_sum(cx, Y.get(), cps).p, sh.steps);
         Ct D = op_add(cx, op_mul_int(cx, Y.get(), pl.n).get(), stream_bcast(cx, S.get(), cps).p, true);
         Ct E = he.mul_rescale(D.get(), D.get());
@@ -1109,10 +1183,16 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         } else {
             Dp = he.mcr(D.get(), coef);
         }
+        // shared chains: the packed h, refreshed first when the schedule says so
+        // and it would arrive below D', back to the streams
+        auto unpack_h = [&](Ct hp) -> Ct {
+            if (rs.h_refresh[t] && hp->level - 1 < Dp->level) hp = bootstrap_ct(cx, hp.get());
+            return unpack(ensure(std::move(hp), 1).get());
+        };
         Ct h;
         if (k == 0) {  // learned quadratic in place of the Goldschmidt iteration
             h = he.learned_half(x.get(), &pl.lq[3 * t]);
-            if (shared) h = unpack(ensure(std::move(h), 1).get());
+            if (shared) h = unpack_h(std::move(h));
         } else if (!shared) {
             // Goldschmidt pair as one complex constant z = g + i h/4 in every
             // slot (the polynomial g + (h/4) X^(N/2)): 2 Im(z^2) = g h by one
@@ -1158,7 +1238,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         for (int i = 0; i < slots; i++) vhi[i] = i < half ? 0.0 : 1.0;
         Ct hm = he.mul_plain_rescale(P.get(), upload_scaled(cx, sv, vhi, 1.0), slots);
         h = op_add(cx, hm.get(), op_automorph(cx, hm.get(), g_half).get(), false);
-        if (shared) h = unpack(ensure(std::move(h), 1).get());
+        if (shared) h = unpack_h(std::move(h));
         }
         if (!shared && ((rs.h_refresh[t] && h->level < Dp->level) || h->level < 1)) h = bootstrap_const(cx, h.get());
         h = ensure(std::move(h), 1);
