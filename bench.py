@@ -592,12 +592,13 @@ def _nucleus_set(x, p):
 def run_cfg5(args):
     """HE nucleus (top-p) sampling decode loop (Alg. 3): 16 streams of 128,256
     logits (4 ciphertexts each) at N=2^16, 8 streams at p = 0.9 and 8 at
-    p = 0.95 (one batch per p, alpha = ln(1-p)/ln(p)).  Per token the client
-    encrypts each stream's logits (regenerated from the seed: N(0, 2^2), top
-    gap 0.5) and uniforms U; the server draws G = U^(1/alpha) from them
-    (nucleus_sample with HE_RAND_UNIFORM: alpha = ln(1-p)/ln(p) in the library,
-    degree-31 Chebyshev) and samples CutMax(X + G) with bootstrapping and shared
-    scalar chains; the client decrypts and takes the argmax as the token.  The
+    p = 0.95 in one batch (alpha = ln(1-p)/ln(p) per group).  Per token the
+    client encrypts each stream's logits (regenerated from the seed: N(0, 2^2),
+    top gap 0.5) and uniforms U; the server draws G = U^(1/alpha) from them
+    (nucleus_sample_groups with HE_RAND_UNIFORM: alpha per group in the library,
+    degree-31 Chebyshev) and samples CutMax(X + G) for all 16 streams at once,
+    with bootstrapping and shared scalar chains; the client decrypts and takes
+    the argmax as the token.  The
     plain plan and the learned plan (learned inverse square root) run side by
     side.  Reported: tokens/s of the server work (CUDA events) and end to end,
     agreement of the tokens with the FP64 sampler argmax(x + U^(1/alpha)), and
@@ -625,7 +626,7 @@ def run_cfg5(args):
     from paper_2509_08383_gb300 import build, he
     build.build_library()
     torch.cuda.set_device(0)
-    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=160 << 30)
+    g = he.Context(16, CFG2_Q, CFG2_P, 3, h=192, seed=1, arena_bytes=200 << 30)
     g.bootstrap_prepare(24, 4, 31)
     g.set_graphs(args.graph)
     assert he.HE_NUCLEUS_DEGREE == deg
@@ -638,43 +639,43 @@ def run_cfg5(args):
         for name, pl in (("plain", plain), ("learned", lpl)):
             g.cutmax_prepare(pl)
             t_dev, t_e2e, agree, agree_poly, outside, total = 0.0, 0.0, 0, 0, 0, 0
+            th = np.pi * (np.arange(deg + 1) + 0.5) / (deg + 1)
             for step in range(args.warmup + args.tokens):
                 timed = step >= args.warmup
-                for b, (p, alpha) in enumerate(zip(ps, alphas)):
-                    t0 = time.perf_counter()
-                    xs, us, cts, uts = [], [], [], []
-                    for sidx in range(per):
-                        st = b * per + sidx
-                        x, u = logits(st, step), synth.uniforms(7000003 * (st + 1) + step, n)
-                        xs.append(x)
-                        us.append(u)
-                        for c, v in enumerate(P.pack_cts(x, slots)):
-                            cts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + c, level=13))
-                        for c, v in enumerate(P.pack_cts(u, slots)):
-                            uts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + 4 + c, level=13))
-                    X, U = g.batch_pack(cts), g.batch_pack(uts)
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    Z = g.nucleus_sample(X, U, pl, p, kind="uniform")
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    toks = []
-                    for sidx in range(per):
-                        dec = np.concatenate([g.decrypt(g.batch_member(Z, sidx * 4 + c)) for c in range(4)])[:n]
-                        toks.append(int(np.argmax(dec)))
-                    t1 = time.perf_counter()
-                    if timed:
-                        t_dev += e0.elapsed_time(e1) / 1000.0
-                        t_e2e += t1 - t0
-                        th = np.pi * (np.arange(deg + 1) + 0.5) / (deg + 1)
+                t0 = time.perf_counter()
+                xs, us, cts, uts = [], [], [], []
+                for st in range(2 * per):  # streams 0..per-1 at ps[0], per..2per-1 at ps[1]
+                    x, u = logits(st, step), synth.uniforms(7000003 * (st + 1) + step, n)
+                    xs.append(x)
+                    us.append(u)
+                    for c, v in enumerate(P.pack_cts(x, slots)):
+                        cts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + c, level=13))
+                    for c, v in enumerate(P.pack_cts(u, slots)):
+                        uts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + 4 + c, level=13))
+                X, U = g.batch_pack(cts), g.batch_pack(uts)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                Z = g.nucleus_sample_groups(X, U, pl, ps, kind="uniform")  # one CutMax for all 16 streams
+                e1.record(stream)
+                torch.cuda.synchronize()
+                toks = []
+                for st in range(2 * per):
+                    dec = np.concatenate([g.decrypt(g.batch_member(Z, st * 4 + c)) for c in range(4)])[:n]
+                    toks.append(int(np.argmax(dec)))
+                t1 = time.perf_counter()
+                if timed:
+                    t_dev += e0.elapsed_time(e1) / 1000.0
+                    t_e2e += t1 - t0
+                    for st, (x, u, tok) in enumerate(zip(xs, us, toks)):
+                        p, alpha = ps[st // per], alphas[st // per]
                         f = ((np.cos(th) + 1) / 2) ** (1 / alpha)
                         cc = np.array([2 / (deg + 1) * np.sum(f * np.cos(k * th)) for k in range(deg + 1)])
                         cc[0] /= 2
-                        for x, u, tok in zip(xs, us, toks):
-                            agree += tok == int(np.argmax(x + u ** (1.0 / alpha)))
-                            agree_poly += tok == int(np.argmax(x + np.polynomial.chebyshev.chebval(2 * u - 1, cc)))
-                            outside += tok not in _nucleus_set(x, p)
-                            total += 1
+                        agree += tok == int(np.argmax(x + u ** (1.0 / alpha)))
+                        agree_poly += tok == int(np.argmax(x + np.polynomial.chebyshev.chebval(2 * u - 1, cc)))
+                        outside += tok not in _nucleus_set(x, p)
+                        total += 1
+            g.graph_clear()  # this plan's graph gives its memory back
             res[name] = {"tokens_per_s": total / t_dev, "tokens_per_s_e2e": total / t_e2e,
                          "ms_per_token_step": 1000.0 * t_dev / args.tokens, "tokens": total,
                          "agree_fp64_sampler": agree, "agree_fp64_same_noise_polynomial": agree_poly,
@@ -686,7 +687,8 @@ def run_cfg5(args):
            "config": {"workload": "Alg. 3 decode loop: 16 streams (8 at top-p 0.9, 8 at 0.95) x 128,256 logits "
                                   "N(0,4) top gap 0.5 in 4 ciphertexts, G = U^(1/alpha) from encrypted uniforms "
                                   "(degree-31 Chebyshev), CutMax T=4 p=[16,4,4,6] c=[5,3,3,3], bootstrapping, "
-                                  "shared scalar chains", "tokens": args.tokens, "streams": 2 * per,
+                                  "shared scalar chains, one batch of 16 streams (nucleus_sample_groups)",
+                      "tokens": args.tokens, "streams": 2 * per,
                       "cuda_graph": bool(args.graph)},
            "plain": res["plain"], "learned": res["learned"],
            "training": {str(t): {k: v for k, v in r.items() if k != "abc"} for t, r in report.items()},

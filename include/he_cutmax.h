@@ -403,6 +403,18 @@ int he_beta_noise(he_ctx *ctx, const he_ct *u, double alpha, uint32_t degree, he
  * operands of different scales. */
 int nucleus_sample(he_ctx *ctx, const he_ct *logits, double top_p, double q, const he_ct *rand_ct,
                    int32_t rand_kind, const he_cutmax_plan *plan, he_ct **out);
+/* Nucleus sampling for a batch whose streams use different top-p masses (Alg. 3
+ * per stream, one CutMax for all): logits and rand_ct are batches split into
+ * n_groups equal runs of members, group j taking top_p[j] (alpha_j =
+ * ln(1-q)/ln(top_p[j]); q = 0 reads as q = top_p[j]).  Each group's cut noise is
+ * drawn as nucleus_sample draws it, the noisy logits of every group are joined
+ * into one batch, and CutMax runs once over it (shared scalar chains then serve
+ * every stream of the batch).  The output is the batch of all streams' results
+ * in order.  With one group this is nucleus_sample.  HE_EINVAL as for
+ * nucleus_sample, for n_groups < 1, a batch not divisible into n_groups whole
+ * groups of streams, or a null top_p. */
+int nucleus_sample_groups(he_ctx *ctx, const he_ct *logits, const double *top_p, uint32_t n_groups, double q,
+                          const he_ct *rand_ct, int32_t rand_kind, const he_cutmax_plan *plan, he_ct **out);
 
 #ifdef __cplusplus
 }

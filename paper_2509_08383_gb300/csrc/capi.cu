@@ -564,26 +564,52 @@ int he_beta_noise(he_ctx *cx, const he_ct *u, double alpha, uint32_t degree, he_
     API_CATCH(cx)
 }
 
-int nucleus_sample(he_ctx *cx, const he_ct *logits, double top_p, double q, const he_ct *rand_ct, int32_t rand_kind,
-                   const he_cutmax_plan *plan, he_ct **out) {
-    if (!cx || !logits || !rand_ct || !out) return HE_EINVAL;
+// alpha = ln(1-q)/ln(top_p) (Lemma 2 / Observation 1; q = 0 reads as q = top_p)
+static double nucleus_alpha(double top_p, double q) {
+    need(top_p > 0.0 && top_p < 1.0, "top-p mass must lie in (0, 1)");
+    need(q >= 0.0 && q < 1.0, "q must lie in [0, 1) (0: q = top_p)");
+    const double qq = q > 0.0 ? q : top_p;
+    const double alpha = std::log(1.0 - qq) / std::log(top_p);
+    need(std::isfinite(alpha) && alpha > 0.0, "alpha = ln(1-q)/ln(p) must be positive");
+    return alpha;
+}
+
+int nucleus_sample_groups(he_ctx *cx, const he_ct *logits, const double *top_p, uint32_t n_groups, double q,
+                          const he_ct *rand_ct, int32_t rand_kind, const he_cutmax_plan *plan, he_ct **out) {
+    if (!cx || !logits || !rand_ct || !out || !top_p) return HE_EINVAL;
     API_TRY
     own(cx, logits);
     own(cx, rand_ct);
-    need(top_p > 0.0 && top_p < 1.0, "top-p mass must lie in (0, 1)");
-    need(q >= 0.0 && q < 1.0, "q must lie in [0, 1) (0: q = top_p)");
+    need(n_groups >= 1, "at least one group");
     need(rand_kind == HE_RAND_BETA || rand_kind == HE_RAND_UNIFORM, "unknown noise kind");
-    const double qq = q > 0.0 ? q : top_p;
-    const double alpha = std::log(1.0 - qq) / std::log(top_p);  // Lemma 2 / Observation 1
-    need(std::isfinite(alpha) && alpha > 0.0, "alpha = ln(1-q)/ln(p) must be positive");
     Plan pl = plan_from(plan);
-    Ct g;
-    if (rand_kind == HE_RAND_UNIFORM) g = beta_noise(cx, rand_ct, alpha, HE_NUCLEUS_DEGREE);
-    Ct x = op_add(cx, logits, g ? g.get() : rand_ct, false);
+    const int B = logits->batch, G = (int)n_groups;
+    need(rand_ct->batch == B, "logits and noise batches differ in size");
+    need(B % G == 0 && (B / G) % pl.cps == 0, "the batch does not split into whole groups of streams");
+    std::vector<double> alpha(G);
+    for (int j = 0; j < G; j++) alpha[j] = nucleus_alpha(top_p[j], q);
+    Ct noise;
+    if (rand_kind == HE_RAND_UNIFORM) {
+        const int per = B / G;
+        std::vector<Ct> parts;
+        std::vector<const he_ct *> ptrs;
+        for (int j = 0; j < G; j++) {
+            Ct u = G == 1 ? Ct() : op_batch_member(cx, rand_ct, j * per, per);
+            parts.push_back(beta_noise(cx, u ? u.get() : rand_ct, alpha[j], HE_NUCLEUS_DEGREE));
+            ptrs.push_back(parts.back().get());
+        }
+        noise = G == 1 ? std::move(parts[0]) : op_batch_pack(cx, ptrs.data(), G);
+    }
+    Ct x = op_add(cx, logits, noise ? noise.get() : rand_ct, false);
     Ct r = cx->use_graphs ? cutmax_graph(cx, x.get(), pl) : cutmax_ct(cx, x.get(), pl);
-    launched(cx, "nucleus_sample");
+    launched(cx, "nucleus_sample_groups");
     *out = r.release();
     API_CATCH(cx)
+}
+
+int nucleus_sample(he_ctx *cx, const he_ct *logits, double top_p, double q, const he_ct *rand_ct, int32_t rand_kind,
+                   const he_cutmax_plan *plan, he_ct **out) {
+    return nucleus_sample_groups(cx, logits, &top_p, 1, q, rand_ct, rand_kind, plan, out);
 }
 
 }  // extern "C"

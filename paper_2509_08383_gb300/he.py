@@ -116,6 +116,7 @@ def lib():
             "he_cutmax_graph_clear": [VP],
             "he_ctx_set_graphs": [VP, i32],
             "nucleus_sample": [VP, VP, dbl, dbl, VP, i32, C.POINTER(CPlan), PP],
+            "nucleus_sample_groups": [VP, VP, pd, u32, dbl, VP, i32, C.POINTER(CPlan), PP],
             "he_beta_noise": [VP, VP, dbl, u32, PP],
         }
         for name, args in sig.items():
@@ -494,3 +495,11 @@ class Context:
         s, keep = plan_struct(plan)
         k = {"beta": HE_RAND_BETA, "uniform": HE_RAND_UNIFORM}[kind]
         return self._ct(lib().nucleus_sample, ct.ptr, float(top_p), float(q), rand_ct.ptr, k, C.byref(s))
+
+    def nucleus_sample_groups(self, ct, rand_ct, plan, top_ps, q=0.0, kind="beta"):
+        """Alg. 3 for a batch split into len(top_ps) equal groups of streams,
+        group j at top-p mass top_ps[j]; one CutMax for the whole batch."""
+        s, keep = plan_struct(plan)
+        k = {"beta": HE_RAND_BETA, "uniform": HE_RAND_UNIFORM}[kind]
+        tp = (C.c_double * len(top_ps))(*[float(x) for x in top_ps])
+        return self._ct(lib().nucleus_sample_groups, ct.ptr, tp, len(top_ps), float(q), rand_ct.ptr, k, C.byref(s))

@@ -403,6 +403,30 @@ def test_nucleus_uniform_noise_matches_oracle(top_p, q):
     assert int(np.argmax(dg)) == int(np.argmax(do)) == want
 
 
+def test_nucleus_groups_equal_per_group_calls():
+    """nucleus_sample_groups: two streams at top-p 0.9 and 0.95 in one batch
+    (server-drawn noise, per-stream scalar chains) give each stream the bits
+    of nucleus_sample on it alone; bad groupings are HE_EINVAL."""
+    qb, pb = [60] + [40] * 28, [60, 60, 60]
+    g = he.Context(11, qb, pb, dnum=10, seed=12)
+    pl = _cfg1_plan(g.slots)
+    g.cutmax_prepare(pl)
+    xs = [synth.logits_gaussian(30 + s) for s in range(2)]
+    us = [synth.uniforms(30 + s, pl.n) for s in range(2)]
+    X = [g.encrypt(P.pack(x, g.slots, pl.packing), g.delta, 40 + s) for s, x in enumerate(xs)]
+    U = [g.encrypt(P.pack(u, g.slots, pl.packing), g.delta, 50 + s) for s, u in enumerate(us)]
+    ps = [0.9, 0.95]
+    Z = g.nucleus_sample_groups(g.batch_pack(X), g.batch_pack(U), pl, ps, kind="uniform")
+    for s in range(2):
+        z1 = g.nucleus_sample(X[s], U[s], pl, ps[s], kind="uniform")
+        zs = g.batch_member(Z, s)
+        assert zs.level == z1.level and zs.scale == z1.scale and (zs.export() == z1.export()).all()
+    for bad in ([0.9, 0.95, 0.9], [0.9, 1.5]):
+        with pytest.raises(he.HeError) as e:
+            g.nucleus_sample_groups(g.batch_pack(X), g.batch_pack(U), pl, bad, kind="uniform")
+        assert e.value.code == he.HE_EINVAL
+
+
 def test_nucleus_and_add_reject_bad_arguments(small):
     """Top-p mass outside (0, 1), an unknown noise kind and operands of
     different scales are HE_EINVAL (an addition of mismatched scales would
