@@ -1094,7 +1094,7 @@ static RefreshSched refresh_schedule_shared(he_ctx *cx, const Plan &pl, int y_le
             if (u < lp) u = out, cost += members;
             Y = u - lp;
         }
-        if (Y < 3) Y = out, cost += members;
+        if (Y < 2) Y = out, cost += members;           // the final mcr and product
         if (Y - 1 < pl.d + 3) cost += 1;              // the packed final sum before the inverse
         if (cost < best_cost) best = combo, best_cost = cost;
     }
@@ -1253,7 +1253,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         u = ensure(std::move(u), power_depth(p));
         Y = he.power(u.get(), p);
     }
-    Y = ensure(std::move(Y), shared ? 3 : 2);
+    Y = ensure(std::move(Y), 2);
     Ct Ssum = he.rotsum(stream_sum(cx, Y.get(), cps).p, sh.steps);
     if (!shared && Ssum->level < pl.d + 3) Ssum = bootstrap_const(cx, Ssum.get());  // the inverse's d + 2 levels
     Ct F;
