@@ -313,7 +313,14 @@ int he_bootstrap_const(he_ctx *ctx, const he_ct *in, he_ct **out);
  * learned: NULL, or [T][3] coefficients {A, B, C} of learned quadratics
  * (he_learn_invsqrt); at an iteration with k[t] = 0 the inverse square root is
  * h = (A x^2 + B x + C) / 2 of x = kappa V (two levels after x) instead of the
- * Goldschmidt iteration.  k[t] = 0 without `learned` is HE_ERANGE. */
+ * Goldschmidt iteration.  k[t] = 0 without `learned` is HE_ERANGE.
+ * relax: NULL, or the additive constant of every Goldschmidt step, k[0] +
+ * ... + k[T-1] doubles in iteration order (none for k[t] = 0): step i of
+ * iteration t multiplies the running estimate by a = relax[...] - g h instead
+ * of Newton's 3/2 - g h (App. B's inverse square root with the per-step
+ * over-relaxation of the implementation it cites; a relaxed step costs the
+ * levels of a plain one).  NULL is 3/2 for every step; a constant outside
+ * [1, 4] is HE_ERANGE. */
 typedef struct {
     uint32_t n, packing, T;
     const uint32_t *power;
@@ -328,6 +335,7 @@ typedef struct {
     uint32_t cts;
     uint32_t shared;
     const double *learned;
+    const double *relax;
 } he_cutmax_plan;
 
 /* Learned inverse-square-root stand-in (engineering on top of Sect. 3.2,

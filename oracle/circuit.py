@@ -32,6 +32,7 @@ import math
 import numpy as np
 
 from . import encoding as enc
+from .cutmax_fp64 import relax_constants
 
 
 ROTSUM_LOG_RADIX = 3
@@ -134,13 +135,16 @@ def required_rotations(plan, log_radix=ROTSUM_LOG_RADIX):
     return sorted({r for rots in rotsum_stages(plan.rotsum_steps, log_radix) for r in rots})
 
 
-def invsqrt_goldschmidt(he, V, kappa, y0, k):
-    """h ~ 1/(2 sqrt(kappa V)), coupled Goldschmidt, 2k levels."""
-    a = he.add_const(he.mcr(V, -kappa * y0 * y0 / 2.0), 1.5)
+def invsqrt_goldschmidt(he, V, kappa, y0, k, alphas=None):
+    """h ~ 1/(2 sqrt(kappa V)), coupled Goldschmidt, 2k levels.  Step i
+    multiplies by a = alpha_i - g h (alpha_i = 3/2 for Newton's step; other
+    values are relaxation constants of the over-relaxed form App. B cites)."""
+    al = [1.5] * max(k, 1) if alphas is None else list(alphas)
+    a = he.add_const(he.mcr(V, -kappa * y0 * y0 / 2.0), al[0])
     h = he.mcr(a, y0 / 2.0)
     g = he.mul_rescale(he.mcr(V, kappa * y0), a) if k >= 2 else None
     for i in range(2, k + 1):
-        a = he.add_const(he.neg(he.mul_rescale(g, h)), 1.5)
+        a = he.add_const(he.neg(he.mul_rescale(g, h)), al[i - 1])
         if i < k:
             g = he.mul_rescale(g, a)
         h = he.mul_rescale(h, a)
@@ -203,7 +207,7 @@ def cutmax_he(he, ct, plan, bootstrap=None):
         if m:
             V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
         if plan.k[t]:
-            h = invsqrt_goldschmidt(he, V, plan.kappa[t], plan.y0[t], plan.k[t])
+            h = invsqrt_goldschmidt(he, V, plan.kappa[t], plan.y0[t], plan.k[t], relax_constants(plan, t))
         else:
             h = learned_half(he, he.mcr_bits(V, plan.kappa[t], None, 30), plan.lq[t])
         coef = 2.0 * math.sqrt(plan.kappa[t] * n) / plan.c[t]
@@ -435,14 +439,15 @@ def _boot_circuit(he, ct, plan, boot, h_refresh, y_boot, tally):
         if k == 0:
             h = learned_half(he, x, plan.lq[t])
         else:
-            a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), 1.5)
+            al = relax_constants(plan, t)
+            a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), al[0])
             z = he.add_plain_vec(he.mcr(x, y0), np.full(plan.slots, 1j * y0 / 8.0))
             z = he.mul_rescale(z, a)
-            for _ in range(2, k + 1):
+            for i in range(2, k + 1):
                 if z.level < 2:
                     z = he.mcr(boot.bootstrap_const(z), 1.0)
                 gh = _imag2(ctx, he.mul_rescale(z, z))
-                z = he.mul_rescale(z, he.add_const(he.neg(gh), 1.5))
+                z = he.mul_rescale(z, he.add_const(he.neg(gh), al[i - 1]))
             if z.level < 1:
                 z = boot.bootstrap_const(z)
             h = ctx.mul_int(_imag2(ctx, z), 2)

@@ -8,7 +8,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 ``cutmax_circuit`` the same polynomial steps the encrypted circuit evaluates
                    (Alg. 2, Sect. 3.2): integer-centred D = n*Y - S, the
                    rotate-and-sum sums, the coupled Goldschmidt inverse square
-                   root (App. B.1, after Panda 2022) and the Goldschmidt inverse
+                   root (App. B.1, after Panda 2022; with a plan's relaxation
+                   constants each step's 3/2 becomes that step's alpha, the
+                   over-relaxed form App. B cites) and the Goldschmidt inverse
                    prod_{i<=d} (1 + (1-x)^(2^i)) (equation in App. B.1).
 Also: the convergence bound and T_min of Theorem 1 / App. E table, the Beta
 cut-noise exponent of Lemma 2 / Observation 1 and the Gumbel noise of Def. 3.1.
@@ -81,18 +83,21 @@ def goldschmidt_inv(x, d):
     return f
 
 
-def goldschmidt_invsqrt(x, k, y0):
+def goldschmidt_invsqrt(x, k, y0, alphas=None):
     """Coupled Goldschmidt iteration for 1/sqrt(x) (k >= 1 iterations).
 
     g0 = x*y0, h0 = y0/2; repeat: r = 1/2 - g*h, g <- g*(1+r), h <- h*(1+r);
     return 2*h.  Written with the same grouping as the encrypted circuit.
+    alphas: step i's 1 + r is alphas[i-1] - g*h instead of 3/2 - g*h (the
+    over-relaxed form; 3/2 is Newton's step).
     """
     x = np.asarray(x, dtype=np.float64)
-    a = 1.5 - (y0 * y0 / 2.0) * x
+    al = [1.5] * max(k, 1) if alphas is None else list(alphas)
+    a = al[0] - (y0 * y0 / 2.0) * x
     h = (y0 / 2.0) * a
     g = (x * y0) * a
     for i in range(2, k + 1):
-        a = 1.5 - g * h
+        a = al[i - 1] - g * h
         if i < k:
             g = g * a
         h = h * a
@@ -114,6 +119,18 @@ def power_by_squaring(u, p):
     return acc
 
 
+def relax_constants(plan, t):
+    """The additive constant of each Goldschmidt step of iteration t: 3/2
+    (Newton's step for x^(-1/2)) unless the plan carries relaxation constants
+    (plan.relax[t], one per step)."""
+    k = plan.k[t]
+    r = getattr(plan, "relax", None)
+    if r is None or r[t] is None or len(r[t]) == 0:
+        return [1.5] * max(k, 1)
+    assert len(r[t]) == k
+    return [float(v) for v in r[t]]
+
+
 def cutmax_circuit(x, plan, return_trace=False):
     """FP64 mirror of the encrypted circuit, on the n real entries.
 
@@ -131,6 +148,7 @@ def cutmax_circuit(x, plan, return_trace=False):
         V = (D * D).sum()
         trace["V"].append(V)
         kap, y0, k = plan.kappa[t], plan.y0[t], plan.k[t]
+        al = relax_constants(plan, t)
         rn = plan.norm[t] ** (1.0 / plan.p[t]) if boot else 1.0
         if k == 0:                    # learned quadratic (A x^2 + B x + C)/2 of x = kappa V
             A, B, C = plan.lq[t]
@@ -138,15 +156,15 @@ def cutmax_circuit(x, plan, return_trace=False):
             h = (A * xx * xx + B * xx + C) / 2.0
         elif boot:                    # bootstrapped circuit: x = kappa V first
             xx = kap * V
-            a = 1.5 - (y0 * y0 / 2.0) * xx
+            a = al[0] - (y0 * y0 / 2.0) * xx
             h = (y0 / 2.0) * a
             g = (xx * y0) * a
         else:
-            a = 1.5 - (kap * y0 * y0 / 2.0) * V
+            a = al[0] - (kap * y0 * y0 / 2.0) * V
             h = (y0 / 2.0) * a
             g = (kap * y0 * V) * a
         for i in range(2, k + 1) if k else ():
-            a = 1.5 - g * h
+            a = al[i - 1] - g * h
             if i < k:
                 g = g * a
             h = h * a

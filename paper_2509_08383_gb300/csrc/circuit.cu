@@ -142,13 +142,15 @@ struct HE {
     }
 };
 
-Ct invsqrt_goldschmidt(HE &he, const he_ct *V, double kappa, double y0, int k) {
-    Ct a = he.add_const(he.mcr(V, -kappa * y0 * y0 / 2.0).get(), 1.5);
+// step i multiplies by a = alpha[i-1] - g h (3/2: Newton's step; larger
+// values over-relax the steps where x y^2 is still small)
+Ct invsqrt_goldschmidt(HE &he, const he_ct *V, double kappa, double y0, int k, const double *alpha) {
+    Ct a = he.add_const(he.mcr(V, -kappa * y0 * y0 / 2.0).get(), alpha[0]);
     Ct h = he.mcr(a.get(), y0 / 2.0);
     Ct g;
     if (k >= 2) g = he.mul_rescale(he.mcr(V, kappa * y0).get(), a.get());
     for (int i = 2; i <= k; i++) {
-        a = he.add_const(he.neg(he.mul_rescale(g.get(), h.get()).get()).get(), 1.5);
+        a = he.add_const(he.neg(he.mul_rescale(g.get(), h.get()).get()).get(), alpha[i - 1]);
         if (i < k) g = he.mul_rescale(g.get(), a.get());
         h = he.mul_rescale(h.get(), a.get());
     }
@@ -204,6 +206,14 @@ Plan plan_from(const he_cutmax_plan *p) {
     pl.cps = p->cts ? (int)p->cts : 1;
     pl.shared = p->shared != 0;
     if (p->learned) pl.lq.assign(p->learned, p->learned + 3 * p->T);
+    for (uint32_t t = 0; t < p->T; t++) {
+        pl.relax_at.push_back((int)pl.relax.size());
+        for (uint32_t i = 0; i < p->k[t]; i++) {
+            const double a = p->relax ? p->relax[pl.relax.size()] : 1.5;
+            if (!(a >= 1.0 && a <= 4.0)) throw Error{HE_ERANGE, "relaxation constants must lie in [1, 4]"};
+            pl.relax.push_back(a);
+        }
+    }
     if (pl.cps > 64) throw Error{HE_EINVAL, "more than 64 ciphertexts per stream"};
     pl.d = (int)p->d;
     pl.kappa_f = p->kappa_f;
@@ -305,7 +315,8 @@ Ct cutmax_ct(he_ctx *cx, const he_ct *in, const Plan &pl) {
             V = op_add(cx, V.get(), op_mul_int(cx, S2.get(), m).get(), true);
         }
         Ct h = stream_bcast(cx,
-                            pl.k[t] ? invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t])
+                            pl.k[t] ? invsqrt_goldschmidt(he, V.get(), pl.kappa[t], pl.y0[t], pl.k[t],
+                                                              pl.relax.data() + pl.relax_at[t])
                                     : he.learned_half(he.mcr_bits(V.get(), pl.kappa[t], -1, 30).get(), &pl.lq[3 * t]),
                             cps);
         double coef = 2.0 * std::sqrt(pl.kappa[t] * pl.n) / pl.c[t];
@@ -1204,13 +1215,13 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
             auto imag2 = [&](const he_ct *a) {  // 2 Im(a) as a real constant: (a - conj a)(-i)
                 return op_mul_monomial(cx, op_add(cx, a, op_automorph(cx, a, g_conj).get(), true).get(), e_mi);
             };
-            Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), 1.5);
+            Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), pl.alpha(t, 0));
             Ct z = he.add_complex_const(he.mcr(x.get(), y0).get(), 0.0, y0 / 8.0);
             z = he.mul_rescale(z.get(), a.get());
             for (int i = 2; i <= k; i++) {
                 if (z->level < 2) z = he.mcr(bootstrap_const(cx, z.get()).get(), 1.0);
                 Ct gh = imag2(he.mul_rescale(z.get(), z.get()).get());
-                z = he.mul_rescale(z.get(), he.add_const(he.neg(gh.get()).get(), 1.5).get());
+                z = he.mul_rescale(z.get(), he.add_const(he.neg(gh.get()).get(), pl.alpha(t, i - 1)).get());
             }
             if (z->level < 1) z = bootstrap_const(cx, z.get());
             // on z's level: no level spent on reading h out
@@ -1221,7 +1232,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         for (int i = half; i < slots; i++) vhi[i] = y0 / 2.0;
         Scratch sv{cx, {}};
         const double *d_vlo = upload_scaled(cx, sv, vlo, 1.0), *d_vhi = upload_scaled(cx, sv, vhi, 1.0);
-        Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), 1.5);
+        Ct a = he.add_const(he.mcr(x.get(), -y0 * y0 / 2.0).get(), pl.alpha(t, 0));
         Ct P = he.mul_plain_rescale(x.get(), d_vlo, slots);
         P = he.add_plain_vec(P.get(), d_vhi, slots);
         P = he.mul_rescale(P.get(), a.get());
@@ -1232,7 +1243,7 @@ static Ct cutmax_boot(he_ctx *cx, const he_ct *in, const Plan &pl) {
         for (int i = 2; i <= k; i++) {
             if (P->level < 2) P = he.mcr(bootstrap_ct(cx, P.get()).get(), 1.0);
             Ct Q = he.mul_rescale(P.get(), op_automorph(cx, P.get(), g_half).get());
-            P = he.mul_rescale(P.get(), he.add_const(he.neg(Q.get()).get(), 1.5).get());
+            P = he.mul_rescale(P.get(), he.add_const(he.neg(Q.get()).get(), pl.alpha(t, i - 1)).get());
         }
         P = ensure(std::move(P), 1);
         for (int i = 0; i < slots; i++) vhi[i] = i < half ? 0.0 : 1.0;

@@ -229,6 +229,11 @@ struct Plan {
     int cps = 1;  // ciphertexts per stream
     bool shared = false;  // batched streams share the scalar chains (see he_cutmax_plan)
     std::vector<double> lq;  // [T][3] learned quadratics (used where k[t] == 0)
+    // additive constant of each Goldschmidt step (3/2 unless the plan relaxes
+    // them): iteration t's k[t] steps start at relax_at[t]
+    std::vector<double> relax;
+    std::vector<int> relax_at;
+    double alpha(int t, int i) const { return relax[(size_t)relax_at[t] + i]; }
     int pad(int slots) const;
 };
 Plan plan_from(const he_cutmax_plan *p);

@@ -52,6 +52,7 @@ static std::vector<double> graph_key(he_ctx *cx, const he_ct *in, const Plan &pl
     add(pl.y0);
     add(pl.norm);
     add(pl.lq);
+    add(pl.relax);
     return k;
 }
 

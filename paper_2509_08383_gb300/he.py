@@ -38,7 +38,7 @@ class CPlan(C.Structure):
                 ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_uint32)), ("kappa", C.POINTER(C.c_double)),
                 ("y0", C.POINTER(C.c_double)), ("d", C.c_uint32), ("kappa_f", C.c_double),
                 ("norm", C.POINTER(C.c_double)), ("bootstrap", C.c_int32), ("cts", C.c_uint32),
-                ("shared", C.c_uint32), ("learned", C.POINTER(C.c_double))]
+                ("shared", C.c_uint32), ("learned", C.POINTER(C.c_double)), ("relax", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -202,11 +202,20 @@ def plan_struct(plan):
                 kappa=(C.c_double * T)(*plan.kappa), y0=(C.c_double * T)(*plan.y0), norm=(C.c_double * T)(*norm))
     lq = getattr(plan, "lq", None)
     arrs["learned"] = (C.c_double * (3 * T))(*[float(v) for row in lq for v in row]) if lq else None
+    rel = getattr(plan, "relax", None)
+    if rel is not None:
+        flat = []
+        for t in range(T):
+            row = list(rel[t]) if rel[t] else []
+            flat += row if row else [1.5] * int(plan.k[t])
+        arrs["relax"] = (C.c_double * max(1, len(flat)))(*flat)
+    else:
+        arrs["relax"] = None
     s = CPlan(n=plan.n, packing=0 if plan.packing == "replicate" else 1, T=T, power=arrs["power"], c=arrs["c"],
               k=arrs["k"], kappa=arrs["kappa"], y0=arrs["y0"], d=plan.d, kappa_f=plan.kappa_f,
               norm=arrs["norm"], bootstrap=int(bool(getattr(plan, "bootstrap", False))),
               cts=int(getattr(plan, "cts", 1)), shared=int(bool(getattr(plan, "shared", False))),
-              learned=arrs["learned"])
+              learned=arrs["learned"], relax=arrs["relax"])
     return s, arrs
 
 

@@ -36,7 +36,7 @@ def _trace_chunk(args):
             V = float((D * D).sum())
             x = pl.kappa[t] * V
             out[r, t] = x
-            h = P.invsqrt_half_at(pl.k, pl.y0, pl.lq, t, x)
+            h = P.invsqrt_half_at(pl.k, pl.y0, pl.lq, t, x, pl.relax)
             rn = pl.norm[t] ** (1.0 / pl.p[t]) if pl.bootstrap else 1.0
             u = D * (2.0 * math.sqrt(pl.kappa[t] * n) / pl.c[t] * rn) * h + rn
             y = P._power(u, pl.p[t])
@@ -66,7 +66,7 @@ def _acc_chunk(args):
             S = y.sum()
             D = n * y - S
             V = float((D * D).sum())
-            h = P.invsqrt_half_at(pl.k, pl.y0, pl.lq, t, pl.kappa[t] * V)
+            h = P.invsqrt_half_at(pl.k, pl.y0, pl.lq, t, pl.kappa[t] * V, pl.relax)
             rn = pl.norm[t] ** (1.0 / pl.p[t]) if pl.bootstrap else 1.0
             u = D * (2.0 * math.sqrt(pl.kappa[t] * n) / pl.c[t] * rn) * h + rn
             y = P._power(u, pl.p[t])

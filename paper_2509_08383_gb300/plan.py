@@ -51,6 +51,7 @@ class CutMaxPlan:
     cts: int = 1                # ciphertexts per stream (n > slots spreads over several)
     shared: bool = False        # batched streams share the scalar chains (bootstrapped plans)
     lq: List = None             # per iteration [A, B, C] of a learned quadratic (used where k[t] == 0)
+    relax: List = None          # per iteration the k[t] Goldschmidt steps' additive constants (None: 3/2)
 
     def __post_init__(self):
         if self.norm is None:
@@ -135,30 +136,73 @@ def _exact_stats(x, T, p, c):
     return Vs, float(y.sum())
 
 
-def _invsqrt_half(x, k, y0):
-    """The circuit's Goldschmidt output h ~ 1/(2 sqrt(x)) (k iterations)."""
-    a = 1.5 - (y0 * y0 / 2.0) * x
+def _invsqrt_half(x, k, y0, alphas=None):
+    """The circuit's Goldschmidt output h ~ 1/(2 sqrt(x)) (k iterations; step i
+    multiplies by alpha_i - g h, alpha_i = 3/2 unless relaxation constants are
+    given)."""
+    al = [1.5] * max(k, 1) if alphas is None else alphas
+    a = al[0] - (y0 * y0 / 2.0) * x
     h = (y0 / 2.0) * a
     g = (x * y0) * a
     for i in range(2, k + 1):
-        a = 1.5 - g * h
+        a = al[i - 1] - g * h
         if i < k:
             g = g * a
         h = h * a
     return h
 
 
-def invsqrt_half_at(plan_k, plan_y0, lq, t, x):
-    """h of iteration t of the circuit: Goldschmidt (k[t] >= 1) or the learned
-    quadratic (A x^2 + B x + C)/2 (k[t] == 0)."""
+def invsqrt_half_at(plan_k, plan_y0, lq, t, x, relax=None):
+    """h of iteration t of the circuit: Goldschmidt (k[t] >= 1, with the
+    plan's relaxation constants if any) or the learned quadratic
+    (A x^2 + B x + C)/2 (k[t] == 0)."""
     if plan_k[t] == 0:
         A, B, C = lq[t]
         return (A * x * x + B * x + C) / 2.0
-    return _invsqrt_half(x, plan_k[t], plan_y0[t])
+    al = relax[t] if relax is not None and relax[t] else None
+    return _invsqrt_half(x, plan_k[t], plan_y0[t], al)
 
 
-def _invsqrt_err(x, k, y0):
-    return np.abs(2.0 * _invsqrt_half(x, k, y0) * np.sqrt(x) - 1.0).max()
+def _invsqrt_err(x, k, y0, alphas=None):
+    return np.abs(2.0 * _invsqrt_half(x, k, y0, alphas) * np.sqrt(x) - 1.0).max()
+
+
+def _relaxed_steps(xs, k_max, tol, c_maxes=(2.0, 2.5)):
+    """Fewest relaxed Goldschmidt steps reaching tol on xs, and their start.
+
+    With u = x y^2 a step maps u to u (alpha - u/2)^2: alpha = 3/2 is Newton's
+    step (quadratic convergence at u = 1), a larger alpha multiplies a small u
+    by alpha^2 instead of 9/4, so a wide range climbs to 1 in fewer steps.
+    Only the additive constant changes, so a relaxed step costs the levels of
+    a plain one.  Greedy per step: while u_min < 1/4 take the alpha that lifts
+    u_min most with every image in (0, c_max]; after that the one with the
+    least error.  Starts put x_max y0^2 in [0.3, c_max]; the plan keeps the
+    start with the fewest steps (then the least error), checked with the
+    circuit's own iteration."""
+    grid = np.linspace(1.5, 3.5, 201)
+    best = None
+    for cmax in c_maxes:
+        for c in np.linspace(0.3, cmax, 40):
+            y0 = math.sqrt(c / xs[-1])
+            u = xs * y0 * y0
+            al = []
+            while np.abs(np.sqrt(u) - 1.0).max() >= tol and len(al) < k_max:
+                key_best, a_best = None, 1.5
+                for a in grid:
+                    v = u * (a - 0.5 * u) ** 2
+                    if v.max() > cmax or v.min() <= 0.0:
+                        continue
+                    key = -v.min() if u.min() < 0.25 else np.abs(np.sqrt(v) - 1.0).max()
+                    if key_best is None or key < key_best:
+                        key_best, a_best = key, float(a)
+                al.append(a_best)
+                u = u * (a_best - 0.5 * u) ** 2
+            if not al:
+                continue
+            err = _invsqrt_err(xs, len(al), y0, al)
+            if err < tol and (best is None or (len(al), err) < (len(best[1]), best[2])):
+                best = (y0, al, err)
+    return None if best is None else (best[0], best[1])
 
 
 def _fewest_iterations(xs, k_max, tol, y0_default):
@@ -200,17 +244,20 @@ def _power(u, p):
 
 
 def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1e-7,
-              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False, norm_margin=1.25, learn=None):
+              k_max=8, d_max=12, k_fixed=None, d_fixed=None, bootstrap=False, norm_margin=1.25, learn=None,
+              relax=False):
     """Pick kappa/y0/k per iteration and kappa_f/d from `n_cal` draws of ``sample(i)``,
     following the circuit's own iterates; with bootstrap=True also the
     normalisers norm[t] that keep max Y_(t+1) at about 1/norm_margin.
     learn(t, kappa_t, xs, (a, b)) -> [A, B, C] or None: offered the iteration-t
     range scale, the inputs x of the calibration draws and the margin range; a
-    quadratic it returns replaces that iteration's Goldschmidt steps (k[t] = 0)."""
+    quadratic it returns replaces that iteration's Goldschmidt steps (k[t] = 0).
+    relax=True: where relaxation constants (one per Goldschmidt step) reach
+    tol_k in fewer steps than Newton's 3/2, the iteration takes them."""
     p = [int(v) for v in (p if not np.isscalar(p) else [p] * T)]
     c = [float(v) for v in (c if not np.isscalar(c) else [c] * T)]
     ys = [np.asarray(sample(i), dtype=np.float64).copy() for i in range(n_cal)]
-    kappa, y0s, ks, norms, vr, lqs = [], [], [], [], [], []
+    kappa, y0s, ks, norms, vr, lqs, rels = [], [], [], [], [], [], []
     for t in range(T):
         Vs, Ds = [], []
         for y in ys:
@@ -228,13 +275,20 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
             k = int(k_fixed if np.isscalar(k_fixed) else k_fixed[t])
         else:
             k, y0 = _fewest_iterations(xs, k_max, tol_k, y0)
+        al = [1.5] * k
+        if relax and k_fixed is None:
+            r = _relaxed_steps(xs, k_max, tol_k)
+            if r is not None and len(r[1]) < k:
+                y0, al = r
+                k = len(al)
         q = learn(t, kap, kap * Vs, (a * kap, b * kap)) if learn is not None else None
         lqs.append(list(q) if q is not None else [0.0, 0.0, 0.0])
         if q is not None:
-            k = 0
+            k, al = 0, []
+        rels.append(al)
         new = []
         for D, V in zip(Ds, Vs):
-            h = invsqrt_half_at([k], [y0], [q], 0, kap * V)
+            h = invsqrt_half_at([k], [y0], [q], 0, kap * V, [al])
             u = D * (2.0 * math.sqrt(kap * n) / c[t]) * h + 1.0
             new.append(_power(u, p[t]))
         nm = 1.0
@@ -259,6 +313,6 @@ def calibrate(sample, n_cal, n, slots, T, p, c, margin=1.25, tol_k=1e-7, tol_d=1
                 break
     return CutMaxPlan(n=n, slots=slots, packing=packing_for(n, slots), T=T, p=p, c=c, k=ks,
                       kappa=kappa, y0=y0s, d=d, kappa_f=kf, bootstrap=bootstrap, norm=norms, cts=cts_for(n, slots),
-                      lq=lqs if any(kk == 0 for kk in ks) else None,
+                      lq=lqs if any(kk == 0 for kk in ks) else None, relax=rels if relax else None,
                       extra={"V_range": vr, "S_range": [float(Ss.min()), float(Ss.max())], "margin": margin,
                              "n_cal": n_cal})

@@ -66,11 +66,39 @@ def test_bootstrapped_cutmax_matches_oracle_circuit(setup):
     same key switches at every level once each side's bootstraps are counted
     in (the library's own bootstrap costs measured here through its ledger),
     which also makes the two refresh schedules the same."""
+    _check_against_oracle_circuit(*setup)
+
+
+@pytest.fixture(scope="module")
+def setup_relaxed(setup):
+    """The same workload with relaxed Goldschmidt steps (calibrate(relax=True))."""
+    g, _ = setup
+    pl = P.calibrate(lambda i: gen(1000 + i), 200, NV, 1 << (LOG_N - 1), T, PW, CC, margin=2.0, tol_k=1e-6,
+                     k_max=20, d_max=14, tol_d=1e-6, bootstrap=True, relax=True)
+    assert any(a != 1.5 for r in pl.relax for a in r)
+    g.cutmax_prepare(pl)
+    return g, pl
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_relaxed_bootstrapped_cutmax_matches_mirror(setup_relaxed, seed):
+    g, pl = setup_relaxed
+    x = gen(seed)
+    dec = g.decrypt(g.cutmax(g.encrypt(P.pack(x, g.slots, pl.packing), g.delta, 1 + seed), pl))
+    assert np.abs(dec[:NV] - F.cutmax_circuit(x, pl)).max() < 1e-3
+    assert int(np.argmax(dec[:NV])) == int(np.argmax(x))
+
+
+def test_relaxed_bootstrapped_cutmax_matches_oracle_circuit(setup_relaxed):
+    """As above, with the relaxed plan: both sides take its per-step constants."""
+    _check_against_oracle_circuit(*setup_relaxed)
+
+
+def _check_against_oracle_circuit(g, pl):
     from oracle import ckks as ock
     from oracle import encoding as oenc
     from oracle.bootstrap import Bootstrapper
     from oracle.circuit import HE, cutmax_he_boot, required_rotations
-    g, pl = setup
     o = ock.Context(LOG_N, QB, PB, dnum=3, h=H, seed=21)
     ob = Bootstrapper(o, K=K, r=R, d=D)
     ob.gen_keys()

@@ -315,6 +315,26 @@ def test_cutmax_bit_exact_small(seed):
     assert np.argmax(dec) == np.argmax(x)
 
 
+def test_cutmax_relaxed_bit_exact():
+    """Leveled CutMax with relaxed Goldschmidt steps (per-step constants in
+    place of 3/2), N = 2^11: bit-exact ciphertexts, the FP64 mirror within 1e-3."""
+    g, o = _circuit_pair(11)
+    pl = P.CutMaxPlan(**{**_cfg1_plan(g.slots).to_dict(), "relax": [[1.8, 1.5], [1.7, 1.55]]})
+    x = synth.logits_gaussian(8)
+    zg, zo = _run_cutmax_pair(g, o, pl, x)
+    assert zg.level == zo.level == 0 and zg.scale == zo.scale
+    assert (zg.export() == zo.export()).all()
+    assert np.abs(g.decrypt(zg, pl.n) - F.cutmax_circuit(x, pl)).max() < 1e-3
+
+
+def test_relax_constant_out_of_range_is_an_error():
+    g = he.Context(11, CFG1_Q, CFG1_P, dnum=11, seed=4)
+    pl = P.CutMaxPlan(**{**_cfg1_plan(g.slots).to_dict(), "relax": [[0.5, 1.5], [1.5, 1.5]]})
+    with pytest.raises(he.HeError) as ei:
+        g.cutmax_prepare(pl)
+    assert ei.value.code == he.HE_ERANGE
+
+
 def test_cutmax_cfg1_full_size():
     """Config 1: N = 2^14, 1024 logits replicated 8x, T = 2, p = 3: bit-exact."""
     g, o = _circuit_pair(14)

@@ -252,3 +252,78 @@ def test_beta_noise_on_oracle_ciphertexts():
     grid = np.linspace(1e-2, 1, 20001)
     bound = np.abs(np.polynomial.chebyshev.chebval(2 * grid - 1, c) - grid ** (1 / alpha)).max()
     assert np.abs(got[big] - u[big] ** (1 / alpha)).max() < bound + 1e-5
+
+
+# ------------------------------------------------ relaxed Goldschmidt steps (App. B)
+def test_relaxed_goldschmidt_is_the_relaxed_newton_recursion():
+    """With per-step constants alpha_i the coupled pair (g = x y, h = y/2) runs
+    y <- y (alpha_i - x y^2 / 2): the recursion on y alone, written here without
+    the pair, gives the same values; alpha_i = 3/2 is the plain iteration."""
+    rng = np.random.default_rng(3)
+    x = np.geomspace(1e-3, 2.0, 200)
+    for k in (1, 2, 5, 9):
+        al = list(rng.uniform(1.5, 2.2, size=k))
+        y0 = 0.6
+        y = np.full_like(x, y0)
+        for a in al:
+            y = y * (a - x * y * y / 2.0)
+        assert np.allclose(F.goldschmidt_invsqrt(x, k, y0, al), y, rtol=1e-12, atol=0)
+        assert (F.goldschmidt_invsqrt(x, k, y0, [1.5] * k) == F.goldschmidt_invsqrt(x, k, y0)).all()
+
+
+def test_relaxed_plan_mirror_equals_plain_at_newton_constants():
+    """The FP64 mirror with relaxation constants all 3/2 is the plain circuit, bit for bit."""
+    pl = _cfg1_plan(8192)
+    x = synth.logits_gaussian(4)
+    rel = P.CutMaxPlan(**{**pl.to_dict(), "relax": [[1.5] * k for k in pl.k]})
+    assert (F.cutmax_circuit(x, rel) == F.cutmax_circuit(x, pl)).all()
+
+
+def test_relaxed_calibration_reaches_tolerance_in_fewer_steps():
+    """calibrate(relax=True) on heavy-tailed logits (the config-2 shape, 2,000
+    entries): every Goldschmidt iteration reaches the tolerance over the whole
+    calibrated margin range (checked here against 1/sqrt(x) itself), in fewer
+    steps in total than Newton's constant, with the argmax of the plan's FP64
+    circuit correct on held-out vectors."""
+    n, tol = 2000, 2.0 ** -10
+
+    def gen(i):
+        return synth.logits_heavy_tail(i, n=n, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+
+    kw = dict(margin=2.0, tol_k=tol, k_max=20, d_max=14, tol_d=tol, bootstrap=True)
+    plain = P.calibrate(lambda i: gen(100 + i), 60, n, 2048, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], **kw)
+    rel = P.calibrate(lambda i: gen(100 + i), 60, n, 2048, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], relax=True, **kw)
+    assert sum(rel.k) < sum(plain.k)
+    for t in range(4):
+        a, b = rel.extra["V_range"][t]
+        xs = np.geomspace(a * rel.kappa[t] / 2.0, b * rel.kappa[t] * 2.0, 3001)
+        y = F.goldschmidt_invsqrt(xs, rel.k[t], rel.y0[t], rel.relax[t])
+        assert np.abs(y * np.sqrt(xs) - 1.0).max() < tol
+        assert len(rel.relax[t]) == rel.k[t] and all(1.5 <= v <= 3.5 for v in rel.relax[t])
+    for s in range(30):
+        x = gen(5000 + s)
+        assert np.argmax(F.cutmax_circuit(x, rel)) == np.argmax(x)
+
+
+def test_encrypted_relaxed_circuit_on_oracle():
+    """Alg. 2 on oracle CKKS with relaxed Goldschmidt steps: the same levels
+    as the plain plan, decrypted within 1e-3 of the relaxed FP64 mirror."""
+    from oracle import ckks
+    from oracle import encoding as enc
+    from oracle.circuit import HE, cutmax_he, required_rotations
+    log_n = 11
+    slots = 1 << (log_n - 1)
+    pl = P.CutMaxPlan(**{**_cfg1_plan(slots).to_dict(), "relax": [[1.8, 1.5], [1.7, 1.55]]})
+    ctx = ckks.Context(log_n, [60] + [40] * 21, [60, 60], dnum=11, seed=3)
+    ctx.gen_relin_key()
+    for r in required_rotations(pl):
+        ctx.gen_rot_key(r)
+    x = synth.logits_gaussian(6, n=pl.n)
+    delta = 2.0 ** 40
+    ct = ctx.encrypt(enc.encode(P.pack(x, slots, pl.packing), log_n, delta), delta, 1)
+    z = cutmax_he(HE(ctx, delta), ct, pl)
+    assert ctx.top_level - z.level == pl.depth()
+    dec = enc.decode(ctx.decrypt(z), log_n, z.scale).real[: pl.n]
+    ref = F.cutmax_circuit(x, pl)
+    assert np.abs(dec - ref).max() < 1e-3
+    assert np.abs(ref - F.cutmax_circuit(x, _cfg1_plan(slots))).max() > 1e-6   # the constants take effect
