@@ -73,6 +73,11 @@ INVSQRT_TOL = 2.0 ** -10
 CFG2_P = [61] * 10
 
 
+# Goldschmidt's inverse square root with calibrated per-step relaxation
+# constants (App. B); --newton keeps Newton's 3/2 in every step
+RELAX = True
+
+
 def workload(name):
     """(log_n, q bits, p bits, dnum, plan, logits generator, description, bootstrap (h, K, r, d) or None)."""
     from paper_2509_08383_gb300 import plan as P
@@ -82,11 +87,12 @@ def workload(name):
         gen = synth.HeavyTail(n, (0.05, 0.2, 1.0))
         pl = P.calibrate(lambda i: gen(100000 + i), 200, n, 1 << (log_n - 1), 4, [16, 4, 4, 6],
                          [5.0, 3.0, 3.0, 3.0], margin=2.0, tol_k=INVSQRT_TOL, k_max=20, d_max=14,
-                         tol_d=INVSQRT_TOL, bootstrap=True)
+                         tol_d=INVSQRT_TOL, bootstrap=True, relax=RELAX)
         desc = {"workload": "CutMax T=4 p=[16,4,4,6] c=[5,3,3,3], 32000 logits N(0,9) + 50 heavy-tail "
                             "Exp(1.5), top-1 gap in {0.05,0.2,1.0}, zero-padded in N=2^16 slots, CKKS "
                             "bootstrapping when levels run out (logQ<=1521, dnum=3, h=192)",
-                "log_n": log_n, "n": n, "T": 4, "k": pl.k, "d": pl.d}
+                "log_n": log_n, "n": n, "T": 4, "k": pl.k, "d": pl.d,
+                "goldschmidt": "relaxed" if pl.relax is not None else "newton"}
         return log_n, CFG2_Q, CFG2_P, 3, pl, gen, desc, (192, 24, 4, 31)
     if name == "cfg1":
         log_n, qb, pb, dnum = 14, [60] + [40] * 21, [60, 60], 11
@@ -449,7 +455,7 @@ def cfg3_batches(g, per, vocabs, chains=None):
     for v in vocabs:
         gen = (lambda s, v=v: synth.logits_gaussian(s, n=v, sd=2.0, gap=0.5))
         pl = P.calibrate(lambda i: gen(100000 + i), 60, v, slots, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
-                         tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True)
+                         tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True, relax=RELAX)
         pl.shared = (chains or {}).get(str(v), "shared") == "shared"
         g.cutmax_prepare(pl)
         xs = [gen(s) for s in range(per)]
@@ -525,7 +531,7 @@ def run_cfg4(args):
     log_n, qb, pb, dnum, plain, gen, desc, boot = workload("cfg2")
     calib_kw = dict(sample=lambda i: gen(100000 + i), n_cal=200, n=plain.n, slots=plain.slots, T=4,
                     p=[16, 4, 4, 6], c=[5.0, 3.0, 3.0, 3.0], margin=2.0, tol_k=INVSQRT_TOL, k_max=20, d_max=14,
-                    tol_d=INVSQRT_TOL, bootstrap=True)
+                    tol_d=INVSQRT_TOL, bootstrap=True, relax=RELAX)
     t0 = time.perf_counter()
     logged = learned.log_variances(plain, gen, range(600000, 625000))  # spawn pool, before CUDA
     t_log = time.perf_counter() - t0
@@ -618,7 +624,7 @@ def run_cfg5(args):
     # plan on logits plus cut noise (the circuit's input is x + G)
     calib_kw = dict(sample=lambda i: gen(300000 + i) + synth.uniforms(300000 + i, n) ** (1.0 / alphas[i % 2]),
                     n_cal=60, n=n, slots=slots, T=4, p=[16, 4, 4, 6], c=[5.0, 3.0, 3.0, 3.0], margin=2.0,
-                    tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True)
+                    tol_k=INVSQRT_TOL, k_max=20, d_max=14, tol_d=INVSQRT_TOL, bootstrap=True, relax=RELAX)
     plain = P.calibrate(**calib_kw)
     plain.shared = True
     logged = learned.log_variances(plain, gen, range(500000, 505000))  # spawn pool, before CUDA
@@ -833,12 +839,16 @@ def main():
                                                            "rot16", "ntt16", "boot16", "bootc16"])
     ap.add_argument("--tokens", type=int, default=32, help="cfg5: tokens decoded per stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--newton", action="store_true",
+                    help="Goldschmidt steps with Newton's constant 3/2 only (no calibrated relaxation)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="call cutmax / nucleus_sample directly instead of replaying their CUDA graphs")
     ap.add_argument("--chains", default="tuned", choices=["tuned", "shared", "stream"],
                     help="cfg3: scalar chains packed across a batch's streams (general bootstraps), kept per "
                          "stream (constant bootstraps, one launch for the batch), or as the autotuner chose")
     args = ap.parse_args()
+    global RELAX
+    RELAX = not args.newton
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in ("mul16", "rot16", "ntt16", "boot16", "bootc16"):
