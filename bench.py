@@ -600,7 +600,9 @@ def run_cfg5(args):
     logits (4 ciphertexts each) at N=2^16, 8 streams at p = 0.9 and 8 at
     p = 0.95 in one batch (alpha = ln(1-p)/ln(p) per group).  Per token the
     client encrypts each stream's logits (regenerated from the seed: N(0, 2^2),
-    top gap 0.5) and uniforms U; the server draws G = U^(1/alpha) from them
+    top gap 0.5) at the bootstrap output level and its uniforms U seven levels
+    higher at scale 2^60, on the 60-bit primes, so that the noise's seven levels
+    come on top of the circuit's; the server draws G = U^(1/alpha) from them
     (nucleus_sample_groups with HE_RAND_UNIFORM: alpha per group in the library,
     degree-31 Chebyshev) and samples CutMax(X + G) for all 16 streams at once,
     with bootstrapping and shared scalar chains; the client decrypts and takes
@@ -656,8 +658,8 @@ def run_cfg5(args):
                     us.append(u)
                     for c, v in enumerate(P.pack_cts(x, slots)):
                         cts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + c, level=13))
-                    for c, v in enumerate(P.pack_cts(u, slots)):
-                        uts.append(g.encrypt(v, g.delta, (st * 64 + step) * 8 + 4 + c, level=13))
+                    for c, v in enumerate(P.pack_cts(u, slots)):  # seven levels up, on the 60-bit primes
+                        uts.append(g.encrypt(v, 2.0 ** 60, (st * 64 + step) * 8 + 4 + c, level=13 + 7))
                 X, U = g.batch_pack(cts), g.batch_pack(uts)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)

@@ -387,8 +387,12 @@ int he_ctx_set_graphs(he_ctx *ctx, int32_t on);
  * encrypted by the client, by the degree-`degree` Chebyshev interpolant of
  * ((t+1)/2)^(1/alpha) on t = 2U - 1 (1 + about log2(degree) + 1 levels).
  * Accurate to ~1e-2 for U >= 1e-3 at degree 31 (alpha ~ 22); the interpolant
- * cannot follow the cusp of U^(1/alpha) at U = 0.  HE_EINVAL for alpha <= 0 or
- * degree outside 2..127.  Works on batches. */
+ * cannot follow the cusp of U^(1/alpha) at U = 0.  The series runs at U's own
+ * scale and G comes out at the context's scale Delta: uniforms encrypted on
+ * large primes (e.g. at scale 2^60 on the 60-bit bootstrapping primes, 7
+ * levels above the bootstrap output level) keep their scale through the
+ * products, and G lands on the circuit's levels with all of them left.
+ * HE_EINVAL for alpha <= 0 or degree outside 2..127.  Works on batches. */
 int he_beta_noise(he_ctx *ctx, const he_ct *u, double alpha, uint32_t degree, he_ct **out);
 
 /* Kinds of the randomness handed to nucleus_sample. */
@@ -405,8 +409,9 @@ int he_beta_noise(he_ctx *ctx, const he_ct *u, double alpha, uint32_t degree, he
  * (drawn by the client for this top_p and q; 0 levels).  HE_RAND_UNIFORM:
  * rand_ct encrypts uniforms U and the library evaluates G = U^(1/alpha) by
  * he_beta_noise of degree HE_NUCLEUS_DEGREE (7 levels, taken from rand_ct's
- * level before the addition).  logits and rand_ct follow the layout of the
- * plan (one ciphertext or a batch, as for cutmax) and must share one scale.
+ * level before the addition; G at the context's scale Delta, see
+ * he_beta_noise).  logits and rand_ct follow the layout of the plan (one
+ * ciphertext or a batch, as for cutmax); logits and G must share one scale.
  * HE_EINVAL for top_p outside (0, 1), q outside [0, 1), an unknown kind or
  * operands of different scales. */
 int nucleus_sample(he_ctx *ctx, const he_ct *logits, double top_p, double q, const he_ct *rand_ct,

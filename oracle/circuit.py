@@ -559,11 +559,14 @@ def chebyshev_sum(he, x, c, target):
 def beta_noise_he(he, u, alpha, d):
     """Alg. 3's cut noise G = U^(1/alpha) (the inverse CDF of Beta(alpha, 1),
     Lemma 2 / Observation 1) evaluated on encrypted uniforms U in [0, 1]:
-    t = 2U - 1, then the degree-d Chebyshev interpolant of ((t + 1)/2)^(1/alpha)."""
+    t = 2U - 1 at U's own scale, then the degree-d Chebyshev interpolant of
+    ((t + 1)/2)^(1/alpha), landing on he.delta.  (The paper fixes no scale for
+    this step; working at U's scale lets uniforms encrypted on large primes keep
+    their scale through the products.)"""
     if not alpha > 0 or not 2 <= d <= 127:
         raise ValueError("alpha must be positive and the degree in 2..127")
     c = chebyshev_interpolant(lambda t: ((t + 1.0) / 2.0) ** (1.0 / alpha), d)
-    t = he.add_const(he.mcr(u, 2.0), -1.0)
+    t = he.add_const(he.mcr(u, 2.0, u.scale), -1.0)
     return chebyshev_sum(he, t, c, he.delta)
 
 

@@ -743,7 +743,10 @@ static Ct cheb_series(HE &he, const he_ct *x, const std::vector<double> &cheb, d
 // Chebyshev interpolant (Chebyshev nodes) of f(t) = ((t + 1)/2)^(1/alpha) on
 // t = 2U - 1, so that the server draws the noise from the client's uniforms.
 // The interpolant follows U^(1/alpha) to ~1e-2 for U >= 1e-3 at d = 31; it
-// cannot follow the cusp at U = 0.
+// cannot follow the cusp at U = 0.  The series works at U's own scale (t =
+// 2U - 1 keeps it), so uniforms encrypted above the circuit's levels at the
+// size of the primes there keep that scale through the products, and the
+// noise lands on the context's scale Delta, d's depth plus one below U.
 Ct beta_noise(he_ctx *cx, const he_ct *u, double alpha, int d) {
     if (!(alpha > 0) || d < 2 || d > 127) throw Error{HE_EINVAL, "noise needs alpha > 0 and degree 2..127"};
     HE he{cx, cx->delta};
@@ -758,7 +761,7 @@ Ct beta_noise(he_ctx *cx, const he_ct *u, double alpha, int d) {
         c[k] = 2.0 / (d + 1) * acc;
     }
     c[0] /= 2;
-    Ct t = he.add_const(he.mcr(u, 2.0).get(), -1.0);
+    Ct t = he.add_const(he.mcr(u, 2.0, u->scale).get(), -1.0);
     return cheb_series(he, t.get(), c, cx->delta);
 }
 

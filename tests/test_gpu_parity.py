@@ -423,6 +423,33 @@ def test_nucleus_uniform_noise_matches_oracle(top_p, q):
     assert int(np.argmax(dg)) == int(np.argmax(do)) == want
 
 
+def test_beta_noise_at_the_uniforms_scale_on_60bit_levels():
+    """The cut noise from uniforms encrypted at scale 2^60 seven levels above
+    the 40-bit levels (on the 60-bit primes of the bootstrapping chain, where
+    a product keeps a 2^60 scale): the series works at U's scale and lands on
+    the 40-bit levels at Delta, seven levels lower; GPU and oracle agree
+    within 1e-5 and follow the interpolant of U^(1/alpha) in float64."""
+    from oracle.circuit import beta_noise_he, chebyshev_interpolant, nucleus_alpha
+    qb, pb = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3, [61] * 10
+    g, o = pair(11, qb, pb, dnum=3, h=64, seed=14)
+    g.gen_relin_key()
+    o.gen_relin_key()
+    u = synth.uniforms(33, g.slots)
+    su, lu = 2.0 ** 60, 20
+    ptu = oenc.encode(u, g.log_n, su)
+    ug, uo = g.encrypt_poly(ptu, su, 5, level=lu), o.encrypt(ptu, su, 5, level=lu)
+    alpha = nucleus_alpha(0.9)
+    Gg_ct = g.beta_noise(ug, alpha, he.HE_NUCLEUS_DEGREE)
+    Go_ct = beta_noise_he(HE(o, 2.0 ** 40), uo, alpha, he.HE_NUCLEUS_DEGREE)
+    assert Gg_ct.level == Go_ct.level == lu - 7
+    assert Gg_ct.scale == pytest.approx(2.0 ** 40, rel=1e-9) and Go_ct.scale == pytest.approx(2.0 ** 40, rel=1e-9)
+    Gg = g.decrypt(Gg_ct)
+    Go = oenc.decode(o.decrypt(Go_ct), g.log_n, Go_ct.scale).real
+    assert np.abs(Gg - Go).max() < 1e-5
+    c = chebyshev_interpolant(lambda t: ((t + 1) / 2) ** (1 / alpha), he.HE_NUCLEUS_DEGREE)
+    assert np.abs(Gg - np.polynomial.chebyshev.chebval(2 * u - 1, c)).max() < 1e-5
+
+
 def test_nucleus_groups_equal_per_group_calls():
     """nucleus_sample_groups: two streams at top-p 0.9 and 0.95 in one batch
     (server-drawn noise, per-stream scalar chains) give each stream the bits
