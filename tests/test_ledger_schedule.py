@@ -47,3 +47,31 @@ def test_schedule_is_deterministic_and_sized(plan_boot):
     a = ledger.refresh_schedule(plan_boot, QB, out, out, plan_boot.pad != 0)
     b = ledger.refresh_schedule(plan_boot, QB, out, out, plan_boot.pad != 0)
     assert a == b and len(a[0]) == len(a[1]) == plan_boot.T
+
+
+@pytest.mark.parametrize("relax", [False, True])
+def test_ledger_agrees_with_the_oracle_circuit_on_levels(relax):
+    """Two independent level bookkeepings of the bootstrapped circuit: the
+    operation-count model (ledger.py, the library's rules) and the oracle's
+    circuit played on LevelSim with its own refresh schedule.  For a plan with
+    Newton's constant and a relaxed one (their Goldschmidt steps differ in
+    count, not in levels per step) they bootstrap the same number of
+    ciphertexts of each kind."""
+    from oracle import ckks as ock
+    from oracle.circuit import HE, LevelSim, _DryBoot, _SimCt, _boot_circuit, refresh_schedule
+    n = 1000
+
+    def gen(i):
+        return synth.logits_heavy_tail(i, n=n, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+
+    pl = P.calibrate(lambda i: gen(1000 + i), 200, n, 1024, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
+                     tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True, relax=relax)
+    ctx = ock.Context(11, QB, [61] * 10, dnum=3, h=64, seed=21)
+    out = ledger.Sim(len(QB), 11, BOOT).bootstrap(0)
+    delta = 2.0 ** 40
+    ct = _SimCt(len(QB) - 1, delta)
+    hr, yb = refresh_schedule(HE(ctx, delta), ct, pl, out)
+    dry = _DryBoot(out)
+    _boot_circuit(HE(LevelSim(ctx.primes, ctx.nq, ctx.log_n), delta), _SimCt(out, delta), pl, dry, hr, yb, {})
+    ks, nb, nc = ledger.cutmax_ledger(pl, len(QB), 11, boot=BOOT, qbits=QB, detail=True)
+    assert (dry.general, dry.const) == (nb - nc, nc)
