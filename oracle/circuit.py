@@ -585,3 +585,155 @@ def nucleus_he(he, ct_logits, ct_rand, plan, top_p=None, q=0.0, kind="beta", deg
     if kind == "uniform":
         G = beta_noise_he(he, ct_rand, nucleus_alpha(top_p, q), degree)
     return cutmax_he(he, he.ctx.add(ct_logits, G), plan)
+
+
+def _shared_circuit(he, cts, plan, boot, h_refresh, y_boot):
+    """The bootstrapped CutMax of S streams (one ciphertext each, S >= 2) with
+    the scalar chains shared: the scalars that every stream holds in all of its
+    slots (x, the Goldschmidt pair and h, the final sum and its inverse) are
+    packed into one ciphertext, stream s in the slot class i = s (mod S'),
+    S' = S rounded up to a power of two (a 0/1 class mask per stream, then the
+    sum over the streams: 1 level); one chain serves them all, and each stream
+    takes its value back (its class mask, then a log2 S'-step rotate-and-sum:
+    1 level).  The packed Goldschmidt pair lies in the slot halves, g = x y0 in
+    [0, s/2) and h = y0/2 in [s/2, s); a rotation by s/2 lines the halves up
+    for g h.  Every refresh is the general bootstrap: the vectors' (one per
+    stream), the packed chain's (one), a stream's x before packing (one per
+    stream).  Engineering beyond the paper (which evaluates one stream at a
+    time); the steps are those of cutmax_he_boot otherwise (Alg. 2, Sect. 3.2;
+    App. B's Goldschmidt steps with the plan's relaxation constants).
+    Refreshes: Y before the statistics when it has fewer than 5 levels or
+    y_boot[t] asks; each stream's x when it has none, the packed x when it has
+    fewer than 2; the pair between steps when it has fewer than 2 (then
+    multiplied by 1 to land on Delta) and when it has none before h is read;
+    the packed h before unpacking when it has none, or when h_refresh[t] asks
+    and it would arrive below D'; an unpacked h and D' before their product
+    (1); u before the power (ceil log2 p); Y before the final sum (2); the
+    packed final sum before the inverse (d + 3); the inverse after it (2) and
+    once unpacked (1)."""
+    ctx = he.ctx
+    S = len(cts)
+    n, steps, m = plan.n, plan.rotsum_steps, plan.pad
+    slots, half = plan.slots, plan.slots // 2
+    Sp, lsp = 1, 0
+    while Sp < S:
+        Sp, lsp = 2 * Sp, lsp + 1
+    mask = None
+    if m:
+        mask = np.zeros(slots)
+        mask[:n] = 1.0
+    cls = []
+    for s in range(S):
+        c = np.zeros(slots)
+        c[s::Sp] = 1.0
+        cls.append(c)
+
+    def ensure(c, need):
+        return boot.bootstrap(c) if c.level < need else c
+
+    def ensure_all(cs, need):
+        return [ensure(c, need) for c in cs]
+
+    def pack(cs):
+        acc = None
+        for s, c in enumerate(cs):
+            t = he.mul_plain_rescale(c, cls[s])
+            acc = t if acc is None else ctx.add(acc, t)
+        return acc
+
+    def unpack(c):
+        return [he.rotsum(he.mul_plain_rescale(c, cls[s]), lsp) for s in range(S)]
+
+    out = boot.out_level()
+    Y = [ctx.drop(c, out) if c.level > out else c for c in cts]
+    for t in range(plan.T):
+        p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
+        rn = plan.norm[t] ** (1.0 / p)
+        if Y[0].level < 5 or y_boot[t]:
+            Y = [boot.bootstrap(y) for y in Y]
+        Ssum = [he.rotsum(y, steps) for y in Y]
+        D = [ctx.sub(ctx.mul_int(y, n), s_) for y, s_ in zip(Y, Ssum)]
+        V = [he.rotsum(he.mul_rescale(d, d), steps) for d in D]
+        if m:
+            V = [ctx.sub(v, ctx.mul_int(he.mul_rescale(s_, s_), m)) for v, s_ in zip(V, Ssum)]
+        x = pack(ensure_all([he.mcr_bits(v, kap, None, 30) for v in V], 1))
+        if x.level < 2:
+            x = boot.bootstrap(x)
+        coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
+        Dp = [he.mcr(he.mul_plain_rescale(d, mask), coef) if m else he.mcr(d, coef) for d in D]
+        if k == 0:
+            hp = learned_half(he, x, plan.lq[t])
+        else:
+            al = relax_constants(plan, t)
+            vlo, vhi = np.zeros(slots), np.zeros(slots)
+            vlo[:half], vhi[half:] = y0, y0 / 2.0
+            a = he.add_const(he.mcr(x, -y0 * y0 / 2.0), al[0])
+            P = he.mul_rescale(he.add_plain_vec(he.mul_plain_rescale(x, vlo), vhi), a)
+            for i in range(2, k + 1):
+                if P.level < 2:
+                    P = he.mcr(boot.bootstrap(P), 1.0)
+                Q = he.mul_rescale(P, ctx.rotate(P, half))
+                P = he.mul_rescale(P, he.add_const(he.neg(Q), al[i - 1]))
+            P = ensure(P, 1)
+            hi = np.zeros(slots)
+            hi[half:] = 1.0
+            hm = he.mul_plain_rescale(P, hi)
+            hp = ctx.add(hm, ctx.rotate(hm, half))
+        if h_refresh[t] and hp.level - 1 < Dp[0].level:
+            hp = boot.bootstrap(hp)
+        h = ensure_all(unpack(ensure(hp, 1)), 1)
+        Dp = ensure_all(Dp, 1)
+        u = [he.mul_rescale(d, hh) for d, hh in zip(Dp, h)]
+        u = [he.add_plain_vec(uu, rn * mask) if m else he.add_const(uu, rn) for uu in u]
+        u = ensure_all(u, (p - 1).bit_length())
+        Y = [he.power(uu, p) for uu in u]
+    Y = ensure_all(Y, 2)
+    Sp_ct = ensure(pack(ensure_all([he.rotsum(y, steps) for y in Y], 1)), plan.d + 3)
+    Fp = ensure(inverse_goldschmidt(he, Sp_ct, plan.kappa_f, plan.d), 2)
+    F = ensure_all(unpack(Fp), 1)
+    Y = ensure_all(Y, 2)
+    return [he.mul_rescale(he.mcr(y, plan.kappa_f), f) for y, f in zip(Y, F)]
+
+
+def refresh_schedule_shared(he, cts, plan, out_level):
+    """The optional refreshes of the shared-chain circuit, chosen by playing
+    every combination of (h_refresh[t], y_boot[t]) on LevelSim (4^T for
+    T <= 6, 2^T beyond, none past 16): the one that bootstraps the fewest
+    ciphertexts wins (a refresh of the vectors counts one per stream, of the
+    packed chain one); ties go to the first combination (t = 0 the least
+    significant digit, bit 0 h_refresh, bit 1 y_boot)."""
+    T = plan.T
+    if T > 16:
+        return [0] * T, [0] * T
+    per = 4 if T <= 6 else 2
+    ctx = he.ctx
+    start = [_SimCt(min(c.level, out_level), c.scale) for c in cts]
+    best, best_cost = None, None
+    for combo in range(per ** T):
+        cc, hr, yb = combo, [], []
+        for _ in range(T):
+            ch = cc % per
+            cc //= per
+            hr.append(ch & 1)
+            yb.append(1 if ch & 2 else 0)
+        dry = _DryBoot(out_level)
+        _shared_circuit(HE(LevelSim(ctx.primes, ctx.nq, ctx.log_n), he.delta, he.rotsum_log_radix), start, plan,
+                        dry, hr, yb)
+        cost = dry.general + dry.const
+        if best_cost is None or cost < best_cost:
+            best, best_cost = (hr, yb), cost
+    return best
+
+
+def cutmax_he_boot_shared(he, cts, plan, boot, stats=None):
+    """_shared_circuit with the refreshes refresh_schedule_shared picks; returns
+    one output ciphertext per stream.  stats (a dict, optional) receives the
+    schedule and the number of ciphertexts bootstrapped."""
+    if getattr(plan, "cts", 1) != 1 or len(cts) < 2:
+        raise ValueError("the shared circuit takes two or more streams of one ciphertext each")
+    hr, yb = refresh_schedule_shared(he, cts, plan, boot.out_level())
+    cboot = CountingBoot(boot)
+    out = _shared_circuit(he, cts, plan, cboot, hr, yb)
+    if stats is not None:
+        stats.update(h_refresh=hr, y_boot=yb, bootstrapped=cboot.general + cboot.const)
+    return out

@@ -236,6 +236,82 @@ def refresh_schedule(plan, qb, y_level, out, padded):
     return hr, yb
 
 
+def refresh_schedule_shared(plan, qb, y_level, out, padded, members, streams):
+    """The library's refresh schedule of a bootstrapped plan whose batch of
+    `streams` streams (`members` ciphertexts) shares its scalar chains: per
+    iteration, (refresh the packed h before unpacking it when it would arrive
+    below D', bootstrap Y early), the combination that bootstraps the fewest
+    ciphertexts (a vector refresh counts one per member, a stream's x before
+    packing one per stream, the packed chain one; then the first).  Returns
+    (h_refresh, y_boot, bootstrapped ciphertexts)."""
+    T = plan.T
+    if T > 16:
+        return [False] * T, [False] * T, None
+    per = 4 if T <= 6 else 2
+
+    def mcr_bits_level(a, c):
+        r, e = 1, qb[a]
+        while abs(c) * 2.0 ** e < 2.0 ** 30 and r < 3 and a - r >= 1:
+            e += qb[a - r]
+            r += 1
+        return a - r
+
+    best, best_cost = 0, None
+    for combo in range(per ** T):
+        cc, Y, cost = combo, y_level, 0
+        for t in range(T):
+            ch = cc % per
+            cc //= per
+            hr, yb = ch & 1, ch & 2
+            k, lp = plan.k[t], (int(plan.p[t]) - 1).bit_length()
+            if Y < 5 or yb:
+                Y, cost = out, cost + members
+            x = mcr_bits_level(Y - 1, plan.kappa[t])
+            if x < 1:
+                x, cost = out, cost + streams
+            x -= 1                                  # pack: the class mask
+            if x < 2:
+                x, cost = out, cost + 1
+            if k == 0:
+                h = x - 2
+            else:
+                z = x - 2                           # the pair after its start
+                for _ in range(2, k + 1):
+                    if z < 2:
+                        z, cost = out - 1, cost + 1
+                    z -= 2
+                if z < 1:
+                    z, cost = out, cost + 1
+                h = z - 1                           # h's half of the pair
+            Dp = Y - (2 if padded else 1)
+            if hr and h - 1 < Dp:
+                h, cost = out, cost + 1
+            if h < 1:
+                h, cost = out, cost + 1
+            h -= 1                                  # unpack: the class mask
+            if h < 1:
+                h, cost = out, cost + streams
+            if Dp < 1:
+                Dp, cost = out, cost + members
+            u = min(Dp, h) - 1
+            if u < lp:
+                u, cost = out, cost + members
+            Y = u - lp
+        if Y < 2:
+            Y, cost = out, cost + members
+        if Y - 1 < plan.d + 3:
+            cost += 1                               # the packed final sum before the inverse
+        if best_cost is None or cost < best_cost:
+            best, best_cost = combo, cost
+    hr, yb = [], []
+    for t in range(T):
+        ch = best % per
+        best //= per
+        hr.append(bool(ch & 1))
+        yb.append(bool(ch & 2))
+    return hr, yb, best_cost
+
+
 def cutmax_ledger(plan, nq, log_n, boot=None, start_level=None, qbits=None, detail=False):
     """Key switches per level and bootstraps of one CutMax (library circuit).
     qbits: bit sizes of the Q primes (default 40 each), for the number of

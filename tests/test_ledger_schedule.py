@@ -75,3 +75,30 @@ def test_ledger_agrees_with_the_oracle_circuit_on_levels(relax):
     _boot_circuit(HE(LevelSim(ctx.primes, ctx.nq, ctx.log_n), delta), _SimCt(out, delta), pl, dry, hr, yb, {})
     ks, nb, nc = ledger.cutmax_ledger(pl, len(QB), 11, boot=BOOT, qbits=QB, detail=True)
     assert (dry.general, dry.const) == (nb - nc, nc)
+
+
+@pytest.mark.parametrize("relax", [False, True])
+def test_shared_schedule_agrees_with_the_oracle_circuit(relax):
+    """Shared scalar chains: the library's schedule rule (ledger.py, written
+    after the circuit's level rules) and the oracle's shared circuit played on
+    LevelSim with its own schedule bootstrap the same number of ciphertexts,
+    for batches of 2, 4 and 16 streams."""
+    from oracle import ckks as ock
+    from oracle.circuit import HE, LevelSim, _DryBoot, _shared_circuit, _SimCt, refresh_schedule_shared
+    n = 1000
+
+    def gen(i):
+        return synth.logits_heavy_tail(i, n=n, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+
+    pl = P.calibrate(lambda i: gen(1000 + i), 200, n, 1024, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0,
+                     tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True, relax=relax)
+    ctx = ock.Context(11, QB, [61] * 10, dnum=3, h=64, seed=21)
+    out = ledger.Sim(len(QB), 11, BOOT).bootstrap(0)
+    delta = 2.0 ** 40
+    for S in (2, 4, 16):
+        hr, yb = refresh_schedule_shared(HE(ctx, delta), [_SimCt(len(QB) - 1, delta)] * S, pl, out)
+        dry = _DryBoot(out)
+        _shared_circuit(HE(LevelSim(ctx.primes, ctx.nq, ctx.log_n), delta), [_SimCt(out, delta)] * S, pl, dry,
+                        hr, yb)
+        lhr, lyb, cost = ledger.refresh_schedule_shared(pl, QB, out, out, pl.pad != 0, S, S)
+        assert dry.general == cost, (S, dry.general, cost)

@@ -173,3 +173,52 @@ def test_oracle_bootstrapped_circuit_replays_on_levels():
     dec = enc.decode(ctx.decrypt(out), log_n, out.scale).real[:nv]
     assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-6
     assert int(np.argmax(dec)) == int(np.argmax(x))
+
+
+@pytest.mark.slow
+def test_oracle_shared_chains_circuit():
+    """The oracle's bootstrapped CutMax for a batch of streams with the scalar
+    chains shared (packed into slot classes, one chain for the batch, handed
+    back per stream), N = 2^11, two streams of 1,000 heavy-tailed logits with
+    relaxed Goldschmidt steps: each stream's output is its own FP64 mirror
+    within 1e-5 with the argmax of its logits; the level-only replay of the
+    chosen schedule predicts the real run's levels, scales and bootstrapped
+    ciphertexts; and the batch bootstraps fewer ciphertexts than two runs of
+    the one-stream circuit would."""
+    from oracle import cutmax_fp64 as F
+    from oracle.circuit import (HE, LevelSim, _DryBoot, _shared_circuit, _SimCt, cutmax_he_boot_shared,
+                                refresh_schedule, required_rotations, _boot_circuit)
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    log_n, nv, delta = 11, 1000, 2.0 ** 40
+    qb = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+    gen = lambda i: synth.logits_heavy_tail(i, n=nv, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+    pl = P.calibrate(lambda i: gen(1000 + i), 200, nv, 1 << (log_n - 1), 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0],
+                     margin=2.0, tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True, relax=True)
+    pl.shared = True
+    ctx = ckks.Context(log_n, qb, [61] * 10, dnum=3, h=64, seed=22)
+    bs = Bootstrapper(ctx, K=14, r=4, d=31)
+    bs.gen_keys()
+    for r in required_rotations(pl):
+        ctx.gen_rot_key(r)
+    xs = [gen(11), gen(12)]
+    cts = [ctx.encrypt(enc.encode(P.pack(x, 1 << (log_n - 1), pl.packing), log_n, delta), delta, 40 + s)
+           for s, x in enumerate(xs)]
+    he = HE(ctx, delta)
+    st = {}
+    outs = cutmax_he_boot_shared(he, cts, pl, bs, stats=st)
+    dry = _DryBoot(bs.out_level())
+    start = [_SimCt(min(c.level, bs.out_level()), c.scale) for c in cts]
+    rep = _shared_circuit(HE(LevelSim(ctx.primes, ctx.nq, log_n), delta), start, pl, dry, st["h_refresh"],
+                          st["y_boot"])
+    for r, o in zip(rep, outs):
+        assert r.level == o.level and r.scale == pytest.approx(o.scale, rel=1e-9)
+    assert dry.general == st["bootstrapped"]
+    one = _DryBoot(bs.out_level())
+    hr1, yb1 = refresh_schedule(he, cts[0], pl, bs.out_level())
+    _boot_circuit(HE(LevelSim(ctx.primes, ctx.nq, log_n), delta), start[0], pl, one, hr1, yb1, {})
+    assert st["bootstrapped"] < 2 * (one.general + one.const)
+    for x, o in zip(xs, outs):
+        dec = enc.decode(ctx.decrypt(o), log_n, o.scale).real[:nv]
+        assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-5
+        assert int(np.argmax(dec)) == int(np.argmax(x))
