@@ -392,11 +392,16 @@ def _imag2(ctx, a):
 
 
 def _boot_circuit(he, ct, plan, boot, h_refresh, y_boot, tally):
-    """The bootstrapped CutMax of one stream (one ciphertext): Alg. 2 with
-    refreshes, the Goldschmidt input x = kappa V, Y_(t+1) scaled by norm[t]
-    through u' = norm^(1/p) u.  The vectors (Y, D', u) take the general
-    bootstrap; the scalars (x, the Goldschmidt pair, h, the final sum), which
-    hold one value in every slot, the constant bootstrap.  The Goldschmidt
+    """The bootstrapped CutMax of one stream: Alg. 2 with refreshes, the
+    Goldschmidt input x = kappa V, Y_(t+1) scaled by norm[t] through
+    u' = norm^(1/p) u.  The stream is one ciphertext, or a list of plan.cts
+    zero-padded ones (a vocabulary longer than the slot count; the sums add
+    the ciphertexts before the rotate-and-sum, the scalars serve all of them,
+    and the result is then a list).  The vectors (Y, D', u) take the general
+    bootstrap (all of a stream's ciphertexts at once: tally['vector'] counts
+    these refreshes, one per event); the scalars (x, the Goldschmidt pair, h,
+    the final sum), which hold one value in every slot, the constant
+    bootstrap.  The Goldschmidt
     pair (g, h) travels as one complex constant z = g + i h/4: one product z^2,
     one conjugation (2 Im(z^2) = g h, the 1/4 keeping the scale of every step
     at s^3/(q q')), then z <- z (1.5 - g h); h = 4 Im z.  Each refresh inside
@@ -409,25 +414,31 @@ def _boot_circuit(he, ct, plan, boot, h_refresh, y_boot, tally):
     D' and h before their product (1), u before the power (ceil log2 p), Y
     before the final sum (2), the final sum before the inverse (d + 3)."""
     ctx = he.ctx
+    many = isinstance(ct, (list, tuple))
+    cts = list(ct) if many else [ct]
     n, steps, m = plan.n, plan.rotsum_steps, plan.pad
-    mask = None
-    if m:
-        mask = np.zeros(plan.slots)
-        mask[:n] = 1.0
+    masks = _masks(plan)
 
     def ensure(c, need):
         return boot.bootstrap(c) if c.level < need else c
 
-    Y = ctx.drop(ct, boot.out_level()) if ct.level > boot.out_level() else ct
+    def vrefresh(cs):
+        tally["vector"] = tally.get("vector", 0) + 1
+        return [boot.bootstrap(c) for c in cs]
+
+    def vensure(cs, need):
+        return vrefresh(cs) if cs[0].level < need else cs
+
+    out = boot.out_level()
+    Y = [ctx.drop(c, out) if c.level > out else c for c in cts]
     for t in range(plan.T):
         p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
         rn = plan.norm[t] ** (1.0 / p)
-        if Y.level < 5 or y_boot[t]:
-            Y = boot.bootstrap(Y)
-        S = he.rotsum(Y, steps)
-        D = ctx.sub(ctx.mul_int(Y, n), S)
-        E = he.mul_rescale(D, D)
-        V = he.rotsum(E, steps)
+        if Y[0].level < 5 or y_boot[t]:
+            Y = vrefresh(Y)
+        S = he.rotsum(_vsum(ctx, Y), steps)
+        D = [ctx.sub(ctx.mul_int(y, n), S) for y in Y]
+        V = he.rotsum(_vsum(ctx, [he.mul_rescale(d, d) for d in D]), steps)
         if m:
             V = ctx.sub(V, ctx.mul_int(he.mul_rescale(S, S), m))
         x = he.mcr_bits(V, kap, None, 30)
@@ -435,7 +446,7 @@ def _boot_circuit(he, ct, plan, boot, h_refresh, y_boot, tally):
             tally["x"] = tally.get("x", 0) + 1
             x = boot.bootstrap_const(x)
         coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
-        Dp = he.mcr(he.mul_plain_rescale(D, mask), coef) if m else he.mcr(D, coef)
+        Dp = [he.mcr(he.mul_plain_rescale(d, masks[c]), coef) if m else he.mcr(d, coef) for c, d in enumerate(D)]
         if k == 0:
             h = learned_half(he, x, plan.lq[t])
         else:
@@ -451,19 +462,20 @@ def _boot_circuit(he, ct, plan, boot, h_refresh, y_boot, tally):
             if z.level < 1:
                 z = boot.bootstrap_const(z)
             h = ctx.mul_int(_imag2(ctx, z), 2)
-        if (h_refresh[t] and h.level < Dp.level) or h.level < 1:
+        if (h_refresh[t] and h.level < Dp[0].level) or h.level < 1:
             h = boot.bootstrap_const(h)
-        h, Dp = ensure(h, 1), ensure(Dp, 1)
-        u = he.mul_rescale(Dp, h)
-        u = he.add_plain_vec(u, rn * mask) if m else he.add_const(u, rn)
-        u = ensure(u, (p - 1).bit_length())
-        Y = he.power(u, p)
-    Y = ensure(Y, 2)
-    S = he.rotsum(Y, steps)
+        h, Dp = ensure(h, 1), vensure(Dp, 1)
+        u = [he.mul_rescale(d, h) for d in Dp]
+        u = [he.add_plain_vec(uu, rn * masks[c]) if m else he.add_const(uu, rn) for c, uu in enumerate(u)]
+        u = vensure(u, (p - 1).bit_length())
+        Y = [he.power(uu, p) for uu in u]
+    Y = vensure(Y, 2)
+    S = he.rotsum(_vsum(ctx, Y), steps)
     if S.level < plan.d + 3:
         S = boot.bootstrap_const(S)
     F = inverse_goldschmidt(he, S, plan.kappa_f, plan.d)
-    return he.mul_rescale(he.mcr(Y, plan.kappa_f), F)
+    Z = [he.mul_rescale(he.mcr(y, plan.kappa_f), F) for y in Y]
+    return Z if many else Z[0]
 
 
 def refresh_schedule(he, ct, plan, out_level):
@@ -483,7 +495,9 @@ def refresh_schedule(he, ct, plan, out_level):
     per = 4 if T <= 6 else 2
     ctx = he.ctx
     primes = list(ctx.primes)
-    start = _SimCt(min(ct.level, out_level), ct.scale)
+    many = isinstance(ct, (list, tuple))
+    start = [_SimCt(min(c.level, out_level), c.scale) for c in ct] if many else _SimCt(min(ct.level, out_level),
+                                                                                       ct.scale)
     best, best_key = None, None
     for combo in range(per ** T):
         cc, hr, yb = combo, [], []
@@ -496,8 +510,9 @@ def refresh_schedule(he, ct, plan, out_level):
         dry = _DryBoot(out_level)
         tally = {}
         _boot_circuit(HE(sim, he.delta, he.rotsum_log_radix), start, plan, dry, hr, yb, tally)
-        cost = 7 * dry.general + 3 * dry.const + 3000 * tally.get("x", 0)
-        key = (cost, dry.general + dry.const)
+        general = tally.get("vector", 0)          # a stream's vector refresh is one event
+        cost = 7 * general + 3 * dry.const + 3000 * tally.get("x", 0)
+        key = (cost, general + dry.const)
         if best_key is None or key < best_key:
             best, best_key = (hr, yb), key
     return best
@@ -508,15 +523,16 @@ def cutmax_he_boot(he, ct, plan, boot, stats=None):
     picked by refresh_schedule.  boot: a Bootstrapper (oracle/bootstrap.py).
     stats (a dict, optional) receives the schedule, the general and constant
     refreshes made and the circuit's own key switches by level."""
-    if getattr(plan, "cts", 1) != 1:
-        raise ValueError("the oracle's bootstrapped circuit takes one ciphertext per stream")
+    many = isinstance(ct, (list, tuple))
+    if (len(ct) if many else 1) != getattr(plan, "cts", 1):
+        raise ValueError("a stream is plan.cts ciphertexts (a list when more than one)")
     hr, yb = refresh_schedule(he, ct, plan, boot.out_level())
     cctx, cboot = CountingCtx(he.ctx), CountingBoot(boot)
     tally = {}
     out = _boot_circuit(HE(cctx, he.delta, he.rotsum_log_radix), ct, plan, cboot, hr, yb, tally)
     if stats is not None:
         stats.update(h_refresh=hr, y_boot=yb, general=cboot.general, const=cboot.const, x_refresh=tally.get("x", 0),
-                     ks=dict(cctx.ks))
+                     vector_refreshes=tally.get("vector", 0), ks=dict(cctx.ks))
     return out
 
 

@@ -222,3 +222,44 @@ def test_oracle_shared_chains_circuit():
         dec = enc.decode(ctx.decrypt(o), log_n, o.scale).real[:nv]
         assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-5
         assert int(np.argmax(dec)) == int(np.argmax(x))
+
+
+@pytest.mark.slow
+def test_oracle_bootstrapped_circuit_multi_ciphertext_stream():
+    """A vocabulary longer than the slot count (2,500 logits in three
+    zero-padded ciphertexts of 1,024 slots, N = 2^11) through the oracle's
+    bootstrapped circuit with relaxed steps: the sums add the three
+    ciphertexts before the rotate-and-sum and the scalars serve all three;
+    the outputs are the FP64 mirror within 1e-5 with the argmax of the
+    logits, and the level-only replay of the schedule predicts the run."""
+    from oracle import cutmax_fp64 as F
+    from oracle.circuit import HE, LevelSim, _boot_circuit, _DryBoot, _SimCt, cutmax_he_boot, required_rotations
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    log_n, nv, delta = 11, 2500, 2.0 ** 40
+    slots = 1 << (log_n - 1)
+    qb = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+    gen = lambda i: synth.logits_heavy_tail(i, n=nv, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+    pl = P.calibrate(lambda i: gen(1000 + i), 120, nv, slots, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0],
+                     margin=2.0, tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True, relax=True)
+    assert pl.cts == 3
+    ctx = ckks.Context(log_n, qb, [61] * 10, dnum=3, h=64, seed=23)
+    bs = Bootstrapper(ctx, K=14, r=4, d=31)
+    bs.gen_keys()
+    bs.gen_const_keys()
+    for r in required_rotations(pl):
+        ctx.gen_rot_key(r)
+    x = gen(8)
+    cts = [ctx.encrypt(enc.encode(v, log_n, delta), delta, 60 + c) for c, v in enumerate(P.pack_cts(x, slots))]
+    st = {}
+    outs = cutmax_he_boot(HE(ctx, delta), cts, pl, bs, stats=st)
+    dry = _DryBoot(bs.out_level())
+    start = [_SimCt(min(c.level, bs.out_level()), c.scale) for c in cts]
+    rep = _boot_circuit(HE(LevelSim(ctx.primes, ctx.nq, log_n), delta), start, pl, dry, st["h_refresh"],
+                        st["y_boot"], {})
+    assert [r.level for r in rep] == [o.level for o in outs]
+    assert (dry.general, dry.const) == (st["general"], st["const"])
+    assert st["general"] == 3 * st["vector_refreshes"]
+    dec = np.concatenate([enc.decode(ctx.decrypt(o), log_n, o.scale).real for o in outs])[:nv]
+    assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-5
+    assert int(np.argmax(dec)) == int(np.argmax(x))
