@@ -604,20 +604,23 @@ def nucleus_he(he, ct_logits, ct_rand, plan, top_p=None, q=0.0, kind="beta", deg
 
 
 def _shared_circuit(he, cts, plan, boot, h_refresh, y_boot):
-    """The bootstrapped CutMax of S streams (one ciphertext each, S >= 2) with
-    the scalar chains shared: the scalars that every stream holds in all of its
-    slots (x, the Goldschmidt pair and h, the final sum and its inverse) are
-    packed into one ciphertext, stream s in the slot class i = s (mod S'),
-    S' = S rounded up to a power of two (a 0/1 class mask per stream, then the
-    sum over the streams: 1 level); one chain serves them all, and each stream
-    takes its value back (its class mask, then a log2 S'-step rotate-and-sum:
-    1 level).  The packed Goldschmidt pair lies in the slot halves, g = x y0 in
-    [0, s/2) and h = y0/2 in [s/2, s); a rotation by s/2 lines the halves up
-    for g h.  Every refresh is the general bootstrap: the vectors' (one per
-    stream), the packed chain's (one), a stream's x before packing (one per
-    stream).  Engineering beyond the paper (which evaluates one stream at a
-    time); the steps are those of cutmax_he_boot otherwise (Alg. 2, Sect. 3.2;
-    App. B's Goldschmidt steps with the plan's relaxation constants).
+    """The bootstrapped CutMax of S streams (S >= 2) with the scalar chains
+    shared; cts[s] is stream s: one ciphertext, or a list of plan.cts
+    zero-padded ones (its sums add them before the rotate-and-sum, its
+    scalars serve all of them; the result per stream then is a list).  The
+    scalars that every stream holds in all of its slots (x, the Goldschmidt
+    pair and h, the final sum and its inverse) are packed into one ciphertext,
+    stream s in the slot class i = s (mod S'), S' = S rounded up to a power of
+    two (a 0/1 class mask per stream, then the sum over the streams: 1 level);
+    one chain serves them all, and each stream takes its value back (its class
+    mask, then a log2 S'-step rotate-and-sum: 1 level).  The packed Goldschmidt
+    pair lies in the slot halves, g = x y0 in [0, s/2) and h = y0/2 in
+    [s/2, s); a rotation by s/2 lines the halves up for g h.  Every refresh is
+    the general bootstrap: the vectors' (one per ciphertext of every stream),
+    the packed chain's (one), a stream's x before packing (one per stream).
+    Engineering beyond the paper (which evaluates one stream at a time); the
+    steps are those of cutmax_he_boot otherwise (Alg. 2, Sect. 3.2; App. B's
+    Goldschmidt steps with the plan's relaxation constants).
     Refreshes: Y before the statistics when it has fewer than 5 levels or
     y_boot[t] asks; each stream's x when it has none, the packed x when it has
     fewer than 2; the pair between steps when it has fewer than 2 (then
@@ -629,15 +632,14 @@ def _shared_circuit(he, cts, plan, boot, h_refresh, y_boot):
     once unpacked (1)."""
     ctx = he.ctx
     S = len(cts)
+    many = isinstance(cts[0], (list, tuple))
+    Ys = [list(c) if many else [c] for c in cts]
     n, steps, m = plan.n, plan.rotsum_steps, plan.pad
     slots, half = plan.slots, plan.slots // 2
+    masks = _masks(plan)
     Sp, lsp = 1, 0
     while Sp < S:
         Sp, lsp = 2 * Sp, lsp + 1
-    mask = None
-    if m:
-        mask = np.zeros(slots)
-        mask[:n] = 1.0
     cls = []
     for s in range(S):
         c = np.zeros(slots)
@@ -650,6 +652,9 @@ def _shared_circuit(he, cts, plan, boot, h_refresh, y_boot):
     def ensure_all(cs, need):
         return [ensure(c, need) for c in cs]
 
+    def ensure_streams(streams, need):
+        return [ensure_all(cs, need) for cs in streams]
+
     def pack(cs):
         acc = None
         for s, c in enumerate(cs):
@@ -661,22 +666,23 @@ def _shared_circuit(he, cts, plan, boot, h_refresh, y_boot):
         return [he.rotsum(he.mul_plain_rescale(c, cls[s]), lsp) for s in range(S)]
 
     out = boot.out_level()
-    Y = [ctx.drop(c, out) if c.level > out else c for c in cts]
+    Y = [[ctx.drop(c, out) if c.level > out else c for c in cs] for cs in Ys]
     for t in range(plan.T):
         p, k, kap, y0 = plan.p[t], plan.k[t], plan.kappa[t], plan.y0[t]
         rn = plan.norm[t] ** (1.0 / p)
-        if Y[0].level < 5 or y_boot[t]:
-            Y = [boot.bootstrap(y) for y in Y]
-        Ssum = [he.rotsum(y, steps) for y in Y]
-        D = [ctx.sub(ctx.mul_int(y, n), s_) for y, s_ in zip(Y, Ssum)]
-        V = [he.rotsum(he.mul_rescale(d, d), steps) for d in D]
+        if Y[0][0].level < 5 or y_boot[t]:
+            Y = [[boot.bootstrap(y) for y in cs] for cs in Y]
+        Ssum = [he.rotsum(_vsum(ctx, cs), steps) for cs in Y]
+        D = [[ctx.sub(ctx.mul_int(y, n), Ssum[s]) for y in cs] for s, cs in enumerate(Y)]
+        V = [he.rotsum(_vsum(ctx, [he.mul_rescale(d, d) for d in ds]), steps) for ds in D]
         if m:
             V = [ctx.sub(v, ctx.mul_int(he.mul_rescale(s_, s_), m)) for v, s_ in zip(V, Ssum)]
         x = pack(ensure_all([he.mcr_bits(v, kap, None, 30) for v in V], 1))
         if x.level < 2:
             x = boot.bootstrap(x)
         coef = 2.0 * math.sqrt(kap * n) / plan.c[t] * rn
-        Dp = [he.mcr(he.mul_plain_rescale(d, mask), coef) if m else he.mcr(d, coef) for d in D]
+        Dp = [[he.mcr(he.mul_plain_rescale(d, masks[c]), coef) if m else he.mcr(d, coef) for c, d in enumerate(ds)]
+              for ds in D]
         if k == 0:
             hp = learned_half(he, x, plan.lq[t])
         else:
@@ -695,20 +701,22 @@ def _shared_circuit(he, cts, plan, boot, h_refresh, y_boot):
             hi[half:] = 1.0
             hm = he.mul_plain_rescale(P, hi)
             hp = ctx.add(hm, ctx.rotate(hm, half))
-        if h_refresh[t] and hp.level - 1 < Dp[0].level:
+        if h_refresh[t] and hp.level - 1 < Dp[0][0].level:
             hp = boot.bootstrap(hp)
         h = ensure_all(unpack(ensure(hp, 1)), 1)
-        Dp = ensure_all(Dp, 1)
-        u = [he.mul_rescale(d, hh) for d, hh in zip(Dp, h)]
-        u = [he.add_plain_vec(uu, rn * mask) if m else he.add_const(uu, rn) for uu in u]
-        u = ensure_all(u, (p - 1).bit_length())
-        Y = [he.power(uu, p) for uu in u]
-    Y = ensure_all(Y, 2)
-    Sp_ct = ensure(pack(ensure_all([he.rotsum(y, steps) for y in Y], 1)), plan.d + 3)
+        Dp = ensure_streams(Dp, 1)
+        u = [[he.mul_rescale(d, h[s]) for d in ds] for s, ds in enumerate(Dp)]
+        u = [[he.add_plain_vec(uu, rn * masks[c]) if m else he.add_const(uu, rn) for c, uu in enumerate(us)]
+             for us in u]
+        u = ensure_streams(u, (p - 1).bit_length())
+        Y = [[he.power(uu, p) for uu in us] for us in u]
+    Y = ensure_streams(Y, 2)
+    Sp_ct = ensure(pack(ensure_all([he.rotsum(_vsum(ctx, cs), steps) for cs in Y], 1)), plan.d + 3)
     Fp = ensure(inverse_goldschmidt(he, Sp_ct, plan.kappa_f, plan.d), 2)
     F = ensure_all(unpack(Fp), 1)
-    Y = ensure_all(Y, 2)
-    return [he.mul_rescale(he.mcr(y, plan.kappa_f), f) for y, f in zip(Y, F)]
+    Y = ensure_streams(Y, 2)
+    Z = [[he.mul_rescale(he.mcr(y, plan.kappa_f), F[s]) for y in cs] for s, cs in enumerate(Y)]
+    return Z if many else [z[0] for z in Z]
 
 
 def refresh_schedule_shared(he, cts, plan, out_level):
@@ -723,7 +731,9 @@ def refresh_schedule_shared(he, cts, plan, out_level):
         return [0] * T, [0] * T
     per = 4 if T <= 6 else 2
     ctx = he.ctx
-    start = [_SimCt(min(c.level, out_level), c.scale) for c in cts]
+    many = isinstance(cts[0], (list, tuple))
+    start = [[_SimCt(min(c.level, out_level), c.scale) for c in cs] if many else _SimCt(min(cs.level, out_level),
+                                                                                          cs.scale) for cs in cts]
     best, best_cost = None, None
     for combo in range(per ** T):
         cc, hr, yb = combo, [], []
@@ -743,10 +753,11 @@ def refresh_schedule_shared(he, cts, plan, out_level):
 
 def cutmax_he_boot_shared(he, cts, plan, boot, stats=None):
     """_shared_circuit with the refreshes refresh_schedule_shared picks; returns
-    one output ciphertext per stream.  stats (a dict, optional) receives the
+    one output per stream (a ciphertext, or a list for multi-ciphertext streams).  stats (a dict, optional) receives the
     schedule and the number of ciphertexts bootstrapped."""
-    if getattr(plan, "cts", 1) != 1 or len(cts) < 2:
-        raise ValueError("the shared circuit takes two or more streams of one ciphertext each")
+    many = isinstance(cts[0], (list, tuple))
+    if len(cts) < 2 or any((len(c) if many else 1) != getattr(plan, "cts", 1) for c in cts):
+        raise ValueError("the shared circuit takes two or more streams of plan.cts ciphertexts each")
     hr, yb = refresh_schedule_shared(he, cts, plan, boot.out_level())
     cboot = CountingBoot(boot)
     out = _shared_circuit(he, cts, plan, cboot, hr, yb)

@@ -82,7 +82,8 @@ def test_shared_schedule_agrees_with_the_oracle_circuit(relax):
     """Shared scalar chains: the library's schedule rule (ledger.py, written
     after the circuit's level rules) and the oracle's shared circuit played on
     LevelSim with its own schedule bootstrap the same number of ciphertexts,
-    for batches of 2, 4 and 16 streams."""
+    for batches of 2, 4 and 16 streams of one ciphertext and of 2 and 4
+    streams of two."""
     from oracle import ckks as ock
     from oracle.circuit import HE, LevelSim, _DryBoot, _shared_circuit, _SimCt, refresh_schedule_shared
     n = 1000
@@ -101,4 +102,18 @@ def test_shared_schedule_agrees_with_the_oracle_circuit(relax):
         _shared_circuit(HE(LevelSim(ctx.primes, ctx.nq, ctx.log_n), delta), [_SimCt(out, delta)] * S, pl, dry,
                         hr, yb)
         lhr, lyb, cost = ledger.refresh_schedule_shared(pl, QB, out, out, pl.pad != 0, S, S)
+        assert dry.general == cost, (S, dry.general, cost)
+    # streams of two zero-padded ciphertexts (1,500 logits in 1,024 slots each)
+    n2 = 1500
+    pl2 = P.calibrate(lambda i: synth.logits_heavy_tail(2000 + i, n=n2, heavy=5, gap=[0.05, 0.2, 1.0][i % 3]), 100,
+                      n2, 1024, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0], margin=2.0, tol_k=1e-6, k_max=20, d_max=14,
+                      tol_d=1e-6, bootstrap=True, relax=relax)
+    assert pl2.cts == 2
+    for S in (2, 4):
+        streams = [[_SimCt(len(QB) - 1, delta)] * 2 for _ in range(S)]
+        hr, yb = refresh_schedule_shared(HE(ctx, delta), streams, pl2, out)
+        dry = _DryBoot(out)
+        _shared_circuit(HE(LevelSim(ctx.primes, ctx.nq, ctx.log_n), delta), [[_SimCt(out, delta)] * 2] * S, pl2,
+                        dry, hr, yb)
+        lhr, lyb, cost = ledger.refresh_schedule_shared(pl2, QB, out, out, True, 2 * S, S)
         assert dry.general == cost, (S, dry.general, cost)

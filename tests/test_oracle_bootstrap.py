@@ -263,3 +263,36 @@ def test_oracle_bootstrapped_circuit_multi_ciphertext_stream():
     dec = np.concatenate([enc.decode(ctx.decrypt(o), log_n, o.scale).real for o in outs])[:nv]
     assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-5
     assert int(np.argmax(dec)) == int(np.argmax(x))
+
+
+@pytest.mark.slow
+def test_oracle_shared_chains_multi_ciphertext_streams():
+    """Shared scalar chains over two streams of 1,500 logits, each in two
+    zero-padded ciphertexts (N = 2^11, relaxed steps): every stream's output
+    is its FP64 mirror within 1e-5 with the argmax of its logits."""
+    from oracle import cutmax_fp64 as F
+    from oracle.circuit import HE, cutmax_he_boot_shared, required_rotations
+    from paper_2509_08383_gb300 import plan as P
+    from paper_2509_08383_gb300 import synth
+    log_n, nv, delta = 11, 1500, 2.0 ** 40
+    slots = 1 << (log_n - 1)
+    qb = [55] + [40] * 13 + [60] * 3 + [60] * 10 + [58] * 3
+    gen = lambda i: synth.logits_heavy_tail(i, n=nv, heavy=5, gap=[0.05, 0.2, 1.0][i % 3])
+    pl = P.calibrate(lambda i: gen(1000 + i), 100, nv, slots, 4, [16, 4, 4, 6], [5.0, 3.0, 3.0, 3.0],
+                     margin=2.0, tol_k=1e-6, k_max=20, d_max=14, tol_d=1e-6, bootstrap=True, relax=True)
+    pl.shared = True
+    assert pl.cts == 2
+    ctx = ckks.Context(log_n, qb, [61] * 10, dnum=3, h=64, seed=24)
+    bs = Bootstrapper(ctx, K=14, r=4, d=31)
+    bs.gen_keys()
+    for r in required_rotations(pl):
+        ctx.gen_rot_key(r)
+    xs = [gen(13), gen(14)]
+    streams = [[ctx.encrypt(enc.encode(v, log_n, delta), delta, 70 + 4 * s + c)
+                for c, v in enumerate(P.pack_cts(x, slots))] for s, x in enumerate(xs)]
+    st = {}
+    outs = cutmax_he_boot_shared(HE(ctx, delta), streams, pl, bs, stats=st)
+    for x, o in zip(xs, outs):
+        dec = np.concatenate([enc.decode(ctx.decrypt(c), log_n, c.scale).real for c in o])[:nv]
+        assert np.abs(dec - F.cutmax_circuit(x, pl)).max() < 1e-5
+        assert int(np.argmax(dec)) == int(np.argmax(x))
