@@ -207,6 +207,8 @@ def plan_struct(plan):
         flat = []
         for t in range(T):
             row = list(rel[t]) if rel[t] else []
+            if row and len(row) != int(plan.k[t]):
+                raise ValueError(f"iteration {t}: {len(row)} relaxation constants for {plan.k[t]} Goldschmidt steps")
             flat += row if row else [1.5] * int(plan.k[t])
         arrs["relax"] = (C.c_double * max(1, len(flat)))(*flat)
     else:

@@ -58,3 +58,5 @@ def test_plan_struct_matches_the_header_layout_and_flattens_relax():
     assert [s.learned[i] for i in range(9)] == [0, 0, 0, 1.0, 2.0, 3.0, 0, 0, 0]
     s2, _ = he.plan_struct(P.CutMaxPlan(**{**pl.to_dict(), "relax": None}))
     assert not s2.relax
+    with pytest.raises(ValueError):
+        he.plan_struct(P.CutMaxPlan(**{**pl.to_dict(), "relax": [[1.9], [], None]}))
