@@ -1,6 +1,7 @@
 """Benchmark: encrypted CutMax decodes/s on synthetic LLM-shaped logits.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cfg1|cfg2|cfg3|cfg4|cfg5|tune|mul16|rot16|ntt16|boot16|bootc16]
+                [--newton] [--no-graph] [--chains tuned|shared|stream] [--tokens T] [--no-cpu-baseline]
 
 One step = one encrypted CutMax (Alg. 2) over one freshly encrypted logit
 vector.  `value` times the device work with CUDA events on the library's
